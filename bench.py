@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Benchmark: sntrup761 batch key generation (B = 4096 keys per step) on GB300.
+
+One step = one snt_batch_keygen call: B fresh key pairs from a 64-bit seed
+(sampling, per-key R/3 inversions, the R/q product tree with its root
+inversion, h, Rq_encode, sk assembly and SHA-512), all on the device.  The
+line also reports the per-key GPU path (snt_keygen_perkey) on the same
+workload, the end-to-end rate through the host-buffer call, the ALU roofline
+of the dominant kernel against measured integer-pipe peaks, and the CPU
+oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as independent replicas (one tree per GPU, no
+data-path collective); value = keys of all ranks / max time over ranks.
+"""
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sntrup761 keygens/s on 1 GB300, batched vs per-key GPU path; p50/p99 serve ms"
+P, Q, W = 761, 4591, 286
+WORDS = (P + 1 + 31) // 32
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+LAUNCHES_FIXED = 5           # sample_f, r3, root, finalize, sha512 (+ 2 per tree level)
+
+# DRAM traffic per launch of the dominant kernel from the committed ncu
+# capture (profiles/); None until a capture of the current kernel exists.
+NCU_TRAFFIC_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--seed", type=lambda s: int(s, 0), default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--perkey-steps", type=int, default=None)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ CPU side
+def _oracle_keys(args):
+    seed, first, n = args
+    import oracle
+    for k in range(first, first + n):
+        oracle.keygen(P, seed, k)
+    return n
+
+
+def cpu_pool():
+    cores = os.cpu_count() or 1
+    return mp.get_context("spawn").Pool(cores), cores
+
+
+def oracle_rate(pool, cores, seed, first, keys_per_core):
+    """Keys/s of the CPU oracle with keys split across all host cores."""
+    jobs = [(seed, first + i * keys_per_core, keys_per_core) for i in range(cores)]
+    t0 = time.perf_counter()
+    n = sum(pool.map(_oracle_keys, jobs))
+    return n / (time.perf_counter() - t0), n
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------- algorithmic ops
+def ops_per_call(B, p=P):
+    """Algorithmic integer operations of each phase for one call of B keys.
+
+    R/q products count p^2 multiply-adds (the Toeplitz/schoolbook form every
+    product kernel computes); the R/3 divsteps count 6 word operations per
+    32-trit word for each of the two polynomial updates per step (bit-sliced
+    F_3 multiply-add); the root inversion counts 2 multiply-reduce updates of
+    p + 1 coefficients per step."""
+    steps = 2 * p - 1
+    mac = p * p
+    return {
+        "r3_inv": B * steps * 2 * WORDS * 6,
+        "tree_up": (B - 1) * mac,
+        "tree_down": 2 * (B - 1) * mac,
+        "h_encode": B * mac,
+        "root_inv": steps * 2 * (p + 1),
+    }
+
+
+PIPE_OF = {"r3_inv": "lop3", "tree_up": "imad", "tree_down": "imad", "h_encode": "imad",
+           "root_inv": "imad"}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    do_cpu = (rank == 0 and world == 1 and not args.no_cpu_baseline)
+    pool = None
+    if do_cpu:
+        pool, cores = cpu_pool()  # spawned before the first GPU call
+        pool.map(_oracle_keys, [(1, 0, 1)] * cores)  # import + build in workers
+
+    import numpy as np
+    import torch
+    import paper_2106_08759_gb300 as snt
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    B = args.batch
+    pkb, skb, _, _ = snt.snt_param_sizes(P)
+    ctx = snt.Context(local, 256 << 20)
+    pk = torch.empty(B * pkb, dtype=torch.uint8, device=dev)
+    sk = torch.empty(B * skb, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    base = (rank << 40)
+
+    lop3_peak, sms = snt.snt_measure_int_peak(local, 0)
+    imad_peak, _ = snt.snt_measure_int_peak(local, 1)
+
+    L = 0
+    n = B
+    while n > 1:
+        n = (n + 1) // 2
+        L += 1
+    launches_per_step = LAUNCHES_FIXED + 2 * L
+
+    def timed(fn, steps, warmup, phases=False):
+        ctx.set_timing(phases)
+        for i in range(warmup):
+            fn(base + (10**9) + i * B)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        acc = {}
+        total_ms = 0.0
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()  # evict L2 between steps (not timed)
+            evs[i][0].record(stream)
+            fn(base + i * B)
+            evs[i][1].record(stream)
+            if phases:
+                for k, v in ctx.phase_times().items():
+                    acc[k] = acc.get(k, 0.0) + v
+        torch.cuda.synchronize()
+        ctx.sync()
+        total_ms = sum(a.elapsed_time(b) for a, b in evs)
+        if dist:
+            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return total_ms, {k: v / steps for k, v in acc.items()}
+
+    def batched(first):
+        snt.snt_batch_keygen(ctx, P, args.seed, first, B, pk, sk, stream)
+
+    def perkey(first):
+        snt.snt_keygen_perkey(ctx, P, args.seed, first, B, pk, sk, stream)
+
+    with ClockSampler(local) as clk:
+        total_ms, phase = timed(batched, args.steps, max(3, args.warmup), phases=True)
+    clocks = clk.summary()
+    ms_per_step = total_ms / args.steps
+    value = world * B * args.steps / (total_ms * 1e-3)
+
+    pk_steps = args.perkey_steps or max(3, args.steps // 10)
+    pk_ms, _ = timed(perkey, pk_steps, 3)
+    perkey_rate = world * B * pk_steps / (pk_ms * 1e-3)
+
+    # end to end through the host-buffer entry point (device->host copy of
+    # every key pair inside the timed region; the only inputs are the seed and
+    # key index, passed by value)
+    hpk = torch.empty(B * pkb, dtype=torch.uint8, pin_memory=True).numpy().reshape(B, pkb)
+    hsk = torch.empty(B * skb, dtype=torch.uint8, pin_memory=True).numpy().reshape(B, skb)
+    ctx.set_timing(False)
+    for i in range(3):
+        snt.snt_batch_keygen_host(ctx, P, args.seed, base + (2 * 10**9) + i * B, B, hpk, hsk)
+    e2e_steps = max(3, args.steps // 5)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        snt.snt_batch_keygen_host(ctx, P, args.seed, base + (3 * 10**9) + i * B, B, hpk, hsk)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_rate = world * B * e2e_steps / e2e_s
+
+    # roofline of the dominant kernel (largest phase time), ALU bound
+    ops = ops_per_call(B)
+    kernels = {k: phase.get(k, 0.0) for k in ops}
+    dom = max(kernels, key=kernels.get)
+    dom_ms = kernels[dom]
+    achieved = ops[dom] / (dom_ms * 1e-3) / 1e12
+    peak = (lop3_peak if PIPE_OF[dom] == "lop3" else imad_peak) / 1e12
+    launches_of = {"r3_inv": 1, "tree_up": L, "tree_down": L, "h_encode": 1, "root_inv": 1}
+    roofline = {
+        "bound": "alu", "kernel": dom, "pipe": PIPE_OF[dom],
+        "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
+        "frac": round(achieved / peak, 4),
+        "peak_source": "measured on this GPU by snt_measure_int_peak (%s stream, %d SMs)"
+                       % (PIPE_OF[dom].upper(), sms),
+        "ops_per_call": ops[dom], "launches_per_call": launches_of[dom],
+        "ms_per_call": round(dom_ms, 4),
+        "traffic": NCU_TRAFFIC_BYTES,
+    }
+
+    cpu = None
+    if do_cpu:
+        rate, nkeys = oracle_rate(pool, cores, args.seed, 5 * 10**9, 24)
+        cpu = {"value": round(rate, 2), "unit": "keys/s", "cores": cores, "kind": "oracle",
+               "sample": "%d sntrup761 keys (24 per core), plain C oracle: schoolbook products, "
+                         "extended-Euclid inversions, per key" % nkeys}
+        pool.close()
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "keys/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "sntrup761 batch keygen, B=%d keys per launch, seeded "
+                               "(seed %d), fresh key indices every step" % (B, args.seed),
+                   "p": P, "q": Q, "w": W, "B": B, "parallelism": "replicas" if world > 1 else "1gpu",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "perkey_gpu": {"value": round(perkey_rate, 1), "unit": "keys/s",
+                       "ms_per_step": round(pk_ms / pk_steps, 4),
+                       "batched_speedup": round(value / perkey_rate, 3)},
+        "phases_ms": {k: round(v, 4) for k, v in phase.items()},
+        "int_peaks_tops": {"lop3": round(lop3_peak / 1e12, 3), "imad": round(imad_peak / 1e12, 3),
+                           "sms": sms},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_rate, 1), "unit": "keys/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": B * (pkb + skb)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "paper_context": "156317 Haswell cycles/key at n=32 (E3-1275 v3, 3.5 GHz: ~22.4k keys/s/core)",
+    }
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The oracle (the deliberately slow CPU definition) on the host cores,
+    same metric and workload, each step a bounded sample of keys."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pool, cores = cpu_pool()
+    pool.map(_oracle_keys, [(1, 0, 1)] * cores)
+    per_core = 2
+    for i in range(max(3, args.warmup) if args.warmup else 0):
+        oracle_rate(pool, cores, args.seed, 7 * 10**9 + i * cores * per_core, per_core)
+    total_keys, t0 = 0, time.perf_counter()
+    for i in range(args.steps):
+        _, n = oracle_rate(pool, cores, args.seed, i * cores * per_core, per_core)
+        total_keys += n
+    el = time.perf_counter() - t0
+    pool.close()
+    value = total_keys / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "keys/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * el / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "sntrup761 batch keygen, B=%d keys per launch, seeded "
+                               "(seed %d)" % (args.batch, args.seed),
+                   "p": P, "q": Q, "w": W, "B": args.batch},
+        "cpu_baseline": {"value": round(value, 2), "unit": "keys/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": "each step %d keys (%d per core) of the workload" % (
+                             cores * per_core, per_core)},
+        "e2e": {"value": round(value, 2), "unit": "keys/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * sntrup_gb300.h -- C ABI of the GB300 (sm_103a) batch key generation library
+ * for Streamlined NTRU Prime (sntrup653, sntrup761, sntrup857).
+ *
+ * Method: arXiv 2106.08759 ("OpenSSLNTRU: Faster post-quantum TLS key
+ * exchange"), Sec. 3.1 KeyGen and Algorithm 1 (BatchKeyGen): per key a small g
+ * invertible in R/3 and a Short f; v = 1/g in R/3; the inverses of all 3f in
+ * R/q at once by Montgomery's trick (Sec. 2.2), run as a product tree with one
+ * root inversion; h = g / (3f); pk = Rq_encode(h); sk = Small_encode(f) |
+ * Small_encode(v) | pk | rho | Hash_prefix(4, pk).
+ *
+ * Conventions shared by every call:
+ *   - All functions return snt_status: SNT_OK (0) or a negative code.  On any
+ *     error the output buffers are undefined and must not be used;
+ *     snt_last_error_string() gives a one-line reason (per host thread).
+ *   - Buffers named *_dev are device pointers on the context's device, owned
+ *     by the caller; *_host are host pointers owned by the caller.  The library
+ *     owns only the scratch memory inside a context.
+ *   - Calls taking a stream are asynchronous on that stream (NULL = the legacy
+ *     default stream).  Device-side failures (exhausted resampling, a bounded
+ *     wait that gave up) are recorded in a per-context error word that
+ *     snt_ctx_sync() reads; it returns the failure as SNT_EINTERNAL /
+ *     SNT_ETIMEOUT and clears the word.
+ *   - A context is used by one host thread at a time.
+ *   - Key i of a call uses randomness (seed, first_key_index + i) only, so a
+ *     batch split into sub-batches of any sizes yields identical bytes.
+ *
+ * Randomness (the paper only says "uniform random", Algorithm 1): word j of
+ * stream s at attempt a for key index k is lane (j mod 4) of Philox4x32-10
+ * with key (seed mod 2^32, seed >> 32) and counter ((s << 16) | (j / 4), a,
+ * k mod 2^32, k >> 32); stream 0 draws g, 1 draws f, 2 draws rho.
+ */
+#ifndef SNTRUP_GB300_H
+#define SNTRUP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SNT_OK = 0,
+    SNT_EINVAL = -1,     /* null pointer, zero or oversized count, unknown parameter set */
+    SNT_ENOMEM = -2,     /* request exceeds the context's memory budget */
+    SNT_ECUDA = -3,      /* a CUDA runtime call failed */
+    SNT_ETIMEOUT = -4,   /* a bounded device-side wait gave up */
+    SNT_EINTERNAL = -5   /* device self-check failed (e.g. g resampling exhausted) */
+} snt_status;
+
+/* Parameter sets (p, q, w), Sec. 2.1: (653,4621,288), (761,4591,286), (857,5167,322). */
+typedef enum { SNTRUP653 = 653, SNTRUP761 = 761, SNTRUP857 = 857 } snt_param;
+
+typedef struct snt_ctx snt_ctx;
+typedef struct CUstream_st *snt_stream; /* same type as cudaStream_t */
+
+/* Byte sizes of one public key, secret key, ciphertext and session key.
+ * For sntrup761: 1158, 1763, 1039, 32.  pk + sk matches the per-key storage of
+ * Table 4 (2512 / 2921 / 3321 bytes); any pointer may be NULL. */
+snt_status snt_param_sizes(int P, size_t *pk_bytes, size_t *sk_bytes,
+                           size_t *ct_bytes, size_t *ss_bytes);
+
+/* Create a context on CUDA device `device` whose scratch memory never exceeds
+ * mem_budget bytes (0 selects 256 MiB).  Scratch is allocated once, here.
+ * The largest batch a context accepts is reported by snt_ctx_max_batch. */
+snt_status snt_ctx_create(int device, size_t mem_budget, snt_ctx **out);
+
+/* Zero the context's secret-bearing scratch, wait for its work, free it. */
+snt_status snt_ctx_destroy(snt_ctx *ctx);
+
+/* Largest B accepted by the keygen calls of this context for parameter set P. */
+snt_status snt_ctx_max_batch(snt_ctx *ctx, int P, size_t *max_B);
+
+/* Wait for all work the context issued on `stream` and read (then clear) the
+ * device error word.  Returns SNT_OK if no device-side failure occurred. */
+snt_status snt_ctx_sync(snt_ctx *ctx, snt_stream stream);
+
+/* Batch key generation (Algorithm 1 with a product tree for batchInv in R/q).
+ * Writes B public keys (pk_dev, B * pk_bytes, key-major, contiguous) and B
+ * secret keys (sk_dev, B * sk_bytes).  Key i uses key index
+ * first_key_index + i.  1 <= B <= snt_ctx_max_batch(P).  Outputs are
+ * byte-identical to snt_keygen_perkey and to any split of the batch. */
+snt_status snt_batch_keygen(snt_ctx *ctx, int P, uint64_t seed,
+                            uint64_t first_key_index, size_t B,
+                            uint8_t *pk_dev, uint8_t *sk_dev, snt_stream stream);
+
+/* Same outputs as snt_batch_keygen, computed without batching the R/q
+ * inversion: every key inverts its own 3f by divsteps (Sec. 3.1 KeyGen). */
+snt_status snt_keygen_perkey(snt_ctx *ctx, int P, uint64_t seed,
+                             uint64_t first_key_index, size_t B,
+                             uint8_t *pk_dev, uint8_t *sk_dev, snt_stream stream);
+
+/* Host-memory convenience form of snt_batch_keygen: generates on the device,
+ * copies B * pk_bytes and B * sk_bytes into the caller's host buffers and
+ * returns when they are complete (synchronous; includes snt_ctx_sync). */
+snt_status snt_batch_keygen_host(snt_ctx *ctx, int P, uint64_t seed,
+                                 uint64_t first_key_index, size_t B,
+                                 uint8_t *pk_host, uint8_t *sk_host);
+
+/* ---- Building blocks (kernel microbenchmarks; same kernels as keygen) ---- */
+
+/* c_i = a_i * b_i in R/q for i < n.  a_dev, b_dev, c_dev: n * p int16
+ * coefficients each, key-major, centred in [-(q-1)/2, (q-1)/2] (inputs may
+ * be any int16 with |x| <= (q-1)/2); outputs centred. */
+snt_status snt_rq_mul(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev,
+                      const int16_t *b_dev, int16_t *c_dev, snt_stream stream);
+
+/* out_i = 1/a_i in R/q by divsteps (Bernstein-Yang), one CTA per element.
+ * a_dev, out_dev: n * p int16 centred; ok_dev: n int32, 1 if invertible
+ * (a_i != 0), else 0 and out_i = 0. */
+snt_status snt_rq_inv(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev,
+                      int16_t *out_dev, int32_t *ok_dev, snt_stream stream);
+
+/* out_i = 1/g_i in R/3 by bit-sliced divsteps, one warp per element.
+ * g_dev, out_dev: n * p int8 in {-1,0,1}; ok_dev: n int32, 1 if g_i is
+ * invertible in R/3, else 0 and out_i = 0. */
+snt_status snt_r3_inv(snt_ctx *ctx, int P, size_t n, const int8_t *g_dev,
+                      int8_t *out_dev, int32_t *ok_dev, snt_stream stream);
+
+/* Test hook for the resampling path (Algorithm 1 skips g that fail the
+ * invertibility check): for the next keygen calls on this context, attempt 0
+ * of key index key_index_host[j] uses g_host[j * p .. j * p + p) (int8 in
+ * {-1,0,1}) instead of its random draw.  n = 0 clears the list.  n <= 64. */
+snt_status snt_debug_inject_g(snt_ctx *ctx, int P, size_t n,
+                              const uint64_t *key_index_host,
+                              const int8_t *g_host);
+
+/* ---- Tracing ---- */
+
+/* Phases reported by snt_ctx_phase_times, in this order: sampling of f and the
+ * leaves 3f; sampling of g with its R/3 inversion (auxiliary stream); tree
+ * up-sweep (per-key path: all per-key R/q inversions); root inversion;
+ * down-sweep; h = g/(3f) with Rq_encode; SHA-512 of the public keys; whole
+ * call (main stream, start to end). */
+#define SNT_NPHASES 8
+
+/* Turn per-phase CUDA events on (on != 0) or off for later keygen calls. */
+snt_status snt_ctx_set_timing(snt_ctx *ctx, int on);
+
+/* Waits for the last keygen call issued with timing on and writes its phase
+ * durations in milliseconds to ms[0 .. SNT_NPHASES). n >= SNT_NPHASES. */
+snt_status snt_ctx_phase_times(snt_ctx *ctx, float *ms, int n);
+
+/* ---- Measurement utility (not part of key generation) ---- */
+
+/* Measures the device's integer-pipe throughput with a register-resident
+ * stream of independent instructions: kind 0 = LOP3 (3-input logic, the
+ * bit-sliced R/3 work), kind 1 = IMAD (32-bit multiply-add, the R/q products).
+ * Writes instructions per second (summed over all SMs) to *ops_per_s and the
+ * SM count to *sms.  Synchronous; uses no scratch. */
+snt_status snt_measure_int_peak(int device, int kind, double *ops_per_s, int *sms);
+
+/* One-line description of the last error on this host thread. */
+const char *snt_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNTRUP_GB300_H */

@@ -1,0 +1,225 @@
+"""Python binding of libsntrup_gb300 (sntrup batch key generation on GB300).
+
+Argument marshalling only: every step of key generation runs in the CUDA
+kernels behind the C ABI declared in include/sntrup_gb300.h.  PyTorch is used
+for device memory and streams.  The functions keep the C names; device
+buffers are torch CUDA tensors (contiguous, of the dtype the C call expects),
+host buffers are numpy arrays.
+
+There is no fallback: if the shared library has not been built, importing
+the functions raises with instructions to build it.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsntrup_gb300.so")
+
+SNTRUP653, SNTRUP761, SNTRUP857 = 653, 761, 857
+PARAMS = {653: (653, 4621, 288), 761: (761, 4591, 286), 857: (857, 5167, 322)}
+
+# phase names of snt_ctx_phase_times (SNT_NPHASES entries)
+PHASES = ("sample_f", "r3_inv", "tree_up", "root_inv", "tree_down", "h_encode", "sha512",
+          "total")
+NPHASES = len(PHASES)
+
+STATUS = {0: "SNT_OK", -1: "SNT_EINVAL", -2: "SNT_ENOMEM", -3: "SNT_ECUDA",
+          -4: "SNT_ETIMEOUT", -5: "SNT_EINTERNAL"}
+
+
+class SntError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load the CUDA library (built by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libsntrup_gb300.so is not built (expected at %s); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P, sz, u64, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int
+    szp = ctypes.POINTER(ctypes.c_size_t)
+    sigs = {
+        "snt_param_sizes": [i32, szp, szp, szp, szp],
+        "snt_ctx_create": [i32, sz, ctypes.POINTER(ctypes.c_void_p)],
+        "snt_ctx_destroy": [P],
+        "snt_ctx_max_batch": [P, i32, szp],
+        "snt_ctx_sync": [P, P],
+        "snt_batch_keygen": [P, i32, u64, u64, sz, P, P, P],
+        "snt_keygen_perkey": [P, i32, u64, u64, sz, P, P, P],
+        "snt_batch_keygen_host": [P, i32, u64, u64, sz, P, P],
+        "snt_rq_mul": [P, i32, sz, P, P, P, P],
+        "snt_rq_inv": [P, i32, sz, P, P, P, P],
+        "snt_r3_inv": [P, i32, sz, P, P, P, P],
+        "snt_debug_inject_g": [P, i32, sz, P, P],
+        "snt_ctx_set_timing": [P, i32],
+        "snt_ctx_phase_times": [P, P, i32],
+        "snt_measure_int_peak": [i32, i32, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_int)],
+    }
+    for name, args in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.snt_last_error_string.argtypes = []
+    L.snt_last_error_string.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != 0:
+        raise SntError(status, load().snt_last_error_string().decode())
+    return status
+
+
+def _dptr(t, dtype=None):
+    """Device pointer of a contiguous torch CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("expected dtype %s, got %s" % (dtype, t.dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def snt_param_sizes(P):
+    """(pk_bytes, sk_bytes, ct_bytes, ss_bytes) of parameter set P."""
+    v = [ctypes.c_size_t() for _ in range(4)]
+    _check(load().snt_param_sizes(P, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+class Context:
+    """Owns an snt_ctx (device scratch within a memory budget)."""
+
+    def __init__(self, device=0, mem_budget=0):
+        h = ctypes.c_void_p()
+        _check(load().snt_ctx_create(device, mem_budget, ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            _check(load().snt_ctx_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def max_batch(self, P):
+        v = ctypes.c_size_t()
+        _check(load().snt_ctx_max_batch(self.handle, P, ctypes.byref(v)))
+        return v.value
+
+    def sync(self, stream=None):
+        _check(load().snt_ctx_sync(self.handle, _stream(stream)))
+
+    def set_timing(self, on=True):
+        _check(load().snt_ctx_set_timing(self.handle, 1 if on else 0))
+
+    def phase_times(self):
+        """Phase durations (ms) of the last keygen call issued with timing on."""
+        out = (ctypes.c_float * NPHASES)()
+        _check(load().snt_ctx_phase_times(self.handle, out, NPHASES))
+        return dict(zip(PHASES, [float(x) for x in out]))
+
+
+def snt_ctx_create(device=0, mem_budget=0):
+    return Context(device, mem_budget)
+
+
+def snt_ctx_sync(ctx, stream=None):
+    ctx.sync(stream)
+
+
+def snt_batch_keygen(ctx, P, seed, first_key_index, B, pk, sk, stream=None):
+    import torch
+    _check(load().snt_batch_keygen(ctx.handle, P, seed, first_key_index, B,
+                                   _dptr(pk, torch.uint8), _dptr(sk, torch.uint8),
+                                   _stream(stream)))
+
+
+def snt_keygen_perkey(ctx, P, seed, first_key_index, B, pk, sk, stream=None):
+    import torch
+    _check(load().snt_keygen_perkey(ctx.handle, P, seed, first_key_index, B,
+                                    _dptr(pk, torch.uint8), _dptr(sk, torch.uint8),
+                                    _stream(stream)))
+
+
+def snt_batch_keygen_host(ctx, P, seed, first_key_index, B, pk_host=None, sk_host=None):
+    """Generates B keys into host numpy buffers (allocated if not given)."""
+    pkb, skb, _, _ = snt_param_sizes(P)
+    if pk_host is None:
+        pk_host = np.empty((B, pkb), np.uint8)
+    if sk_host is None:
+        sk_host = np.empty((B, skb), np.uint8)
+    assert pk_host.flags.c_contiguous and pk_host.nbytes >= B * pkb
+    assert sk_host.flags.c_contiguous and sk_host.nbytes >= B * skb
+    _check(load().snt_batch_keygen_host(ctx.handle, P, seed, first_key_index, B,
+                                        pk_host.ctypes.data_as(ctypes.c_void_p),
+                                        sk_host.ctypes.data_as(ctypes.c_void_p)))
+    return pk_host, sk_host
+
+
+def snt_rq_mul(ctx, P, n, a, b, c, stream=None):
+    import torch
+    _check(load().snt_rq_mul(ctx.handle, P, n, _dptr(a, torch.int16), _dptr(b, torch.int16),
+                             _dptr(c, torch.int16), _stream(stream)))
+
+
+def snt_rq_inv(ctx, P, n, a, out, ok, stream=None):
+    import torch
+    _check(load().snt_rq_inv(ctx.handle, P, n, _dptr(a, torch.int16), _dptr(out, torch.int16),
+                             _dptr(ok, torch.int32), _stream(stream)))
+
+
+def snt_r3_inv(ctx, P, n, g, out, ok, stream=None):
+    import torch
+    _check(load().snt_r3_inv(ctx.handle, P, n, _dptr(g, torch.int8), _dptr(out, torch.int8),
+                             _dptr(ok, torch.int32), _stream(stream)))
+
+
+def snt_measure_int_peak(device=0, kind=0):
+    """(instructions/s, SM count) of the LOP3 (kind 0) or IMAD (kind 1) stream."""
+    v = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(load().snt_measure_int_peak(device, kind, ctypes.byref(v), ctypes.byref(n)))
+    return v.value, n.value
+
+
+def snt_debug_inject_g(ctx, P, key_indices, gs):
+    """Replace attempt 0 of the given key indices by the given g (test hook)."""
+    idx = np.ascontiguousarray(key_indices, dtype=np.uint64)
+    g = np.ascontiguousarray(gs, dtype=np.int8)
+    n = idx.size
+    _check(load().snt_debug_inject_g(ctx.handle, P, n,
+                                     idx.ctypes.data_as(ctypes.c_void_p) if n else None,
+                                     g.ctypes.data_as(ctypes.c_void_p) if n else None))

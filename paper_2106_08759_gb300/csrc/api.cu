@@ -1,0 +1,478 @@
+// api.cu -- the C ABI (include/sntrup_gb300.h) and the host-side orchestration
+// of batch key generation: scratch layout, product-tree schedule, the two
+// streams, argument checks and the device error word.
+//
+// Call graph of snt_batch_keygen (arXiv 2106.08759, Algorithm 1):
+//   stream S : sample f -> leaves 3f ---------------- tree up (ceil(log2 B)
+//              levels) -> root inversion -> tree down -> [wait R/3] ->
+//              h = g / (3f) + Rq_encode -> SHA-512(4 | pk)
+//   stream X : (after the fork) sample g + R/3 divstep inverse per key
+// The two branches only meet at the h stage, so the per-key R/3 inversions
+// overlap the latency-bound top of the tree and the root inversion.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "sntrup_gb300.h"
+
+using namespace snt;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+snt_status fail(snt_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+snt_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(SNT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SNT_CUDA(call)                                         \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+    } while (0)
+
+// Rq_encode schedule (see encode.cu) for p entries of radix m.
+bool build_sched(int p, uint32_t m0, EncSched &S) {
+    std::memset(&S, 0, sizeof(S));
+    int n = p, off = 0;
+    uint64_t mu = m0, ml = m0;
+    while (n > 1) {
+        if (S.nlev >= 16) return false;
+        EncLevel &L = S.lev[S.nlev++];
+        L.n = n;
+        L.mu = (uint32_t)mu;
+        L.mlast = (uint32_t)ml;
+        L.boff = off;
+        uint64_t m = mu * mu;
+        int eu = 0;
+        while (m >= 16384) { ++eu; m = (m + 255) >> 8; }
+        const uint64_t mu2 = m;
+        uint64_t ml2 = ml;
+        int el = eu;
+        const int npairs = n / 2;
+        if (n % 2 == 0) {
+            uint64_t m2 = mu * ml;
+            el = 0;
+            while (m2 >= 16384) { ++el; m2 = (m2 + 255) >> 8; }
+            ml2 = m2;
+            off += (npairs - 1) * eu + el;
+        } else {
+            off += npairs * eu;
+        }
+        L.eu = eu;
+        L.elast = el;
+        n = (n + 1) / 2;
+        mu = mu2;
+        ml = ml2;
+    }
+    int e = 0;
+    for (uint64_t m = ml; m > 1; m = (m + 255) >> 8) ++e;
+    S.efinal = e;
+    S.foff = off;
+    S.total = off + e;
+    return true;
+}
+
+struct ParamInfo {
+    int P, p, q, w, pad;
+    int small_bytes, pk_bytes, sk_bytes, ct_bytes;
+    EncSched sched;
+};
+
+bool param_info(int P, ParamInfo &pi) {
+    int p, q, w, pad;
+    switch (P) {
+        case 653: p = Geo<653>::p; q = Geo<653>::q; w = Geo<653>::w; pad = Geo<653>::pad; break;
+        case 761: p = Geo<761>::p; q = Geo<761>::q; w = Geo<761>::w; pad = Geo<761>::pad; break;
+        case 857: p = Geo<857>::p; q = Geo<857>::q; w = Geo<857>::w; pad = Geo<857>::pad; break;
+        default: return false;
+    }
+    pi.P = P; pi.p = p; pi.q = q; pi.w = w; pi.pad = pad;
+    pi.small_bytes = (p + 3) / 4;
+    if (!build_sched(p, (uint32_t)q, pi.sched)) return false;
+    pi.pk_bytes = pi.sched.total;
+    // sk = Small_encode(f) | Small_encode(1/g) | pk | rho | Hash_prefix(4, pk)
+    pi.sk_bytes = 3 * pi.small_bytes + pi.pk_bytes + 32;
+    // ct = Rounded encoding (radix (q+2)/3) | 32-byte confirmation hash
+    EncSched rs;
+    if (!build_sched(p, (uint32_t)((q + 2) / 3), rs)) return false;
+    pi.ct_bytes = rs.total + 32;
+    return true;
+}
+
+// Product-tree levels over B leaves: level 0 = leaves, level l has
+// ceil(n_(l-1) / 2) nodes, the last level has one.  Offsets in nodes.
+struct Tree {
+    std::vector<int> n, off;
+    size_t total = 0;
+};
+
+Tree make_tree(size_t B) {
+    Tree t;
+    size_t n = B, off = 0;
+    for (;;) {
+        t.n.push_back((int)n);
+        t.off.push_back((int)off);
+        off += n;
+        if (n == 1) break;
+        n = (n + 1) / 2;
+    }
+    t.total = off;
+    return t;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch bytes for one keygen call: every tree node (int16, stride pad) and
+// g (int8, stride pad) for each key; host_out adds device staging for pk/sk.
+size_t keygen_scratch(const ParamInfo &pi, size_t B, bool host_out) {
+    const Tree t = make_tree(B);
+    size_t bytes = align256(t.total * pi.pad * sizeof(int16_t)) + align256(B * pi.pad);
+    if (host_out) bytes += align256(B * pi.pk_bytes) + align256(B * pi.sk_bytes);
+    return bytes;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+constexpr int kMaxInject = 64;
+// Phase events of one keygen call (snt_ctx_set_timing): on the main stream
+// 0 start, 1 after sampling f, 4 after the up-sweep (or per-key R/q
+// inversions), 5 after the root, 6 after the down-sweep, 7 after the join,
+// 8 after h/encode, 9 after SHA-512; on the auxiliary stream 2 / 3 around the
+// R/3 kernel.
+constexpr int kPhaseEvents = 10;
+constexpr size_t kMaxB = (size_t)1 << 24;
+
+}  // namespace
+
+struct snt_ctx {
+    int device = 0;
+    size_t budget = 0;
+    uint8_t *arena = nullptr;
+    int *d_err = nullptr;
+    uint64_t *d_inj_idx = nullptr;
+    int8_t *d_inj_g = nullptr;
+    int n_inj = 0;
+    int inj_P = 0;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool timing = false;
+    cudaEvent_t ev_phase[kPhaseEvents] = {};
+};
+
+namespace {
+
+template <int P>
+snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t first, size_t B,
+                      uint8_t *pk, uint8_t *sk, cudaStream_t st, bool batched, uint8_t *arena) {
+    const Tree t = make_tree(B);
+    int16_t *nodes = reinterpret_cast<int16_t *>(arena);
+    int8_t *gbuf = reinterpret_cast<int8_t *>(arena + align256(t.total * pi.pad * sizeof(int16_t)));
+    int16_t *leaves = nodes;
+    const int Bi = (int)B;
+    const int sb = pi.small_bytes;
+    cudaEvent_t *ev = ctx->ev_phase;
+    const bool tm = ctx->timing;
+    if (tm) SNT_CUDA(cudaEventRecord(ev[0], st));
+    SNT_CUDA(launch_sample_f<P>(seed, first, Bi, leaves, sk, pi.sk_bytes, 2 * sb + pi.pk_bytes, st));
+    // fork: per-key R/3 inversions on the auxiliary stream
+    if (tm) SNT_CUDA(cudaEventRecord(ev[1], st));
+    SNT_CUDA(cudaEventRecord(ctx->ev_fork, st));
+    SNT_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    const int n_inj = (ctx->inj_P == P) ? ctx->n_inj : 0;
+    if (tm) SNT_CUDA(cudaEventRecord(ev[2], ctx->aux));
+    SNT_CUDA(launch_r3_keygen<P>(seed, first, Bi, gbuf, sk, pi.sk_bytes, sb, ctx->d_inj_idx,
+                                 ctx->d_inj_g, n_inj, ctx->d_err, ctx->aux));
+    if (tm) SNT_CUDA(cudaEventRecord(ev[3], ctx->aux));
+    SNT_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
+    if (batched) {
+        const int L = (int)t.n.size() - 1;
+        for (int l = 1; l <= L; ++l)
+            SNT_CUDA(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1],
+                                       nodes + (size_t)t.off[l] * pi.pad, st));
+        if (tm) SNT_CUDA(cudaEventRecord(ev[4], st));
+        int16_t *root = nodes + (size_t)t.off[L] * pi.pad;
+        SNT_CUDA(launch_rq_inv<P>(1, root, pi.pad, root, pi.pad, nullptr, ctx->d_err, ERR_ROOT, st));
+        if (tm) SNT_CUDA(cudaEventRecord(ev[5], st));
+        for (int l = L; l >= 1; --l)
+            SNT_CUDA(launch_tree_down<P>(nodes + (size_t)t.off[l] * pi.pad,
+                                         nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1], st));
+        if (tm) SNT_CUDA(cudaEventRecord(ev[6], st));
+    } else {
+        SNT_CUDA(launch_rq_inv<P>(Bi, leaves, pi.pad, leaves, pi.pad, nullptr, ctx->d_err, ERR_ROOT,
+                                  st));
+        if (tm) {
+            SNT_CUDA(cudaEventRecord(ev[4], st));
+            SNT_CUDA(cudaEventRecord(ev[5], st));
+            SNT_CUDA(cudaEventRecord(ev[6], st));
+        }
+    }
+    SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    if (tm) SNT_CUDA(cudaEventRecord(ev[7], st));
+    SNT_CUDA(launch_finalize<P>(Bi, gbuf, leaves, pk, pi.pk_bytes, sk, pi.sk_bytes, 2 * sb,
+                                pi.sched, st));
+    if (tm) SNT_CUDA(cudaEventRecord(ev[8], st));
+    SNT_CUDA(launch_sha512_pk(Bi, pk, pi.pk_bytes, sk, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
+    if (tm) SNT_CUDA(cudaEventRecord(ev[9], st));
+    return SNT_OK;
+}
+
+snt_status keygen_common(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, size_t B,
+                         uint8_t *pk, uint8_t *sk, snt_stream stream, bool batched,
+                         bool host_out) {
+    if (!ctx) return fail(SNT_EINVAL, "null context");
+    ParamInfo pi;
+    if (!param_info(P, pi)) return fail(SNT_EINVAL, "unknown parameter set %d", P);
+    if (B == 0 || B > kMaxB) return fail(SNT_EINVAL, "batch size %zu outside [1, %zu]", B, kMaxB);
+    if (!pk || !sk) return fail(SNT_EINVAL, "null output buffer");
+    const size_t need = keygen_scratch(pi, B, host_out);
+    if (need > ctx->budget)
+        return fail(SNT_ENOMEM, "batch of %zu keys needs %zu scratch bytes, budget %zu", B, need,
+                    ctx->budget);
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return fail(SNT_ECUDA, "cannot select device %d", ctx->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t *dpk = pk, *dsk = sk;
+    if (host_out) {
+        const Tree t = make_tree(B);
+        size_t o = align256(t.total * pi.pad * sizeof(int16_t)) + align256(B * pi.pad);
+        dpk = ctx->arena + o;
+        dsk = ctx->arena + o + align256(B * pi.pk_bytes);
+    }
+    snt_status s;
+    switch (P) {
+        case 653: s = run_keygen<653>(ctx, pi, seed, first, B, dpk, dsk, st, batched, ctx->arena); break;
+        case 761: s = run_keygen<761>(ctx, pi, seed, first, B, dpk, dsk, st, batched, ctx->arena); break;
+        default:  s = run_keygen<857>(ctx, pi, seed, first, B, dpk, dsk, st, batched, ctx->arena); break;
+    }
+    if (s != SNT_OK || !host_out) return s;
+    SNT_CUDA(cudaMemcpyAsync(pk, dpk, B * pi.pk_bytes, cudaMemcpyDeviceToHost, st));
+    SNT_CUDA(cudaMemcpyAsync(sk, dsk, B * pi.sk_bytes, cudaMemcpyDeviceToHost, st));
+    return snt_ctx_sync(ctx, stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+snt_status snt_param_sizes(int P, size_t *pk_bytes, size_t *sk_bytes, size_t *ct_bytes,
+                           size_t *ss_bytes) {
+    ParamInfo pi;
+    if (!param_info(P, pi)) return fail(SNT_EINVAL, "unknown parameter set %d", P);
+    if (pk_bytes) *pk_bytes = (size_t)pi.pk_bytes;
+    if (sk_bytes) *sk_bytes = (size_t)pi.sk_bytes;
+    if (ct_bytes) *ct_bytes = (size_t)pi.ct_bytes;
+    if (ss_bytes) *ss_bytes = 32;
+    return SNT_OK;
+}
+
+snt_status snt_ctx_create(int device, size_t mem_budget, snt_ctx **out) {
+    if (!out) return fail(SNT_EINVAL, "null output pointer");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(SNT_ECUDA, "no CUDA device available");
+    if (device < 0 || device >= ndev) return fail(SNT_EINVAL, "device %d out of range", device);
+    DeviceGuard dg(device);
+    if (!dg.ok) return fail(SNT_ECUDA, "cannot select device %d", device);
+    snt_ctx *c = new snt_ctx();
+    c->device = device;
+    c->budget = mem_budget ? mem_budget : ((size_t)256 << 20);
+    cudaError_t e = cudaMalloc(&c->arena, c->budget);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_inj_idx, kMaxInject * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_inj_g, kMaxInject * 1024);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    for (int i = 0; i < kPhaseEvents && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev_phase[i]);
+    if (e != cudaSuccess) {
+        snt_ctx_destroy(c);
+        return cuda_fail(e, "snt_ctx_create");
+    }
+    *out = c;
+    return SNT_OK;
+}
+
+snt_status snt_ctx_destroy(snt_ctx *ctx) {
+    if (!ctx) return SNT_OK;
+    DeviceGuard dg(ctx->device);
+    if (ctx->aux) cudaStreamSynchronize(ctx->aux);
+    cudaDeviceSynchronize();
+    if (ctx->arena) {
+        cudaMemset(ctx->arena, 0, ctx->budget);  // secret-bearing scratch
+        cudaDeviceSynchronize();
+        cudaFree(ctx->arena);
+    }
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_inj_idx) cudaFree(ctx->d_inj_idx);
+    if (ctx->d_inj_g) cudaFree(ctx->d_inj_g);
+    for (int i = 0; i < kPhaseEvents; ++i)
+        if (ctx->ev_phase[i]) cudaEventDestroy(ctx->ev_phase[i]);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    delete ctx;
+    return SNT_OK;
+}
+
+snt_status snt_ctx_max_batch(snt_ctx *ctx, int P, size_t *max_B) {
+    if (!ctx || !max_B) return fail(SNT_EINVAL, "null argument");
+    ParamInfo pi;
+    if (!param_info(P, pi)) return fail(SNT_EINVAL, "unknown parameter set %d", P);
+    size_t lo = 0, hi = kMaxB;
+    while (lo < hi) {
+        const size_t mid = (lo + hi + 1) / 2;
+        if (keygen_scratch(pi, mid, true) <= ctx->budget) lo = mid; else hi = mid - 1;
+    }
+    *max_B = lo;
+    return SNT_OK;
+}
+
+snt_status snt_ctx_sync(snt_ctx *ctx, snt_stream stream) {
+    if (!ctx) return fail(SNT_EINVAL, "null context");
+    DeviceGuard dg(ctx->device);
+    SNT_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    SNT_CUDA(cudaStreamSynchronize(ctx->aux));
+    int err = 0;
+    SNT_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        SNT_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
+        if (err & ERR_TIMEOUT) return fail(SNT_ETIMEOUT, "a bounded device wait gave up (0x%x)", err);
+        if (err & ERR_RESAMPLE)
+            return fail(SNT_EINTERNAL, "a key found no invertible g in %d attempts", kMaxGAttempts);
+        return fail(SNT_EINTERNAL, "device self-check failed (0x%x)", err);
+    }
+    return SNT_OK;
+}
+
+snt_status snt_batch_keygen(snt_ctx *ctx, int P, uint64_t seed, uint64_t first_key_index,
+                            size_t B, uint8_t *pk_dev, uint8_t *sk_dev, snt_stream stream) {
+    return keygen_common(ctx, P, seed, first_key_index, B, pk_dev, sk_dev, stream, true, false);
+}
+
+snt_status snt_keygen_perkey(snt_ctx *ctx, int P, uint64_t seed, uint64_t first_key_index,
+                             size_t B, uint8_t *pk_dev, uint8_t *sk_dev, snt_stream stream) {
+    return keygen_common(ctx, P, seed, first_key_index, B, pk_dev, sk_dev, stream, false, false);
+}
+
+snt_status snt_batch_keygen_host(snt_ctx *ctx, int P, uint64_t seed, uint64_t first_key_index,
+                                 size_t B, uint8_t *pk_host, uint8_t *sk_host) {
+    return keygen_common(ctx, P, seed, first_key_index, B, pk_host, sk_host, nullptr, true, true);
+}
+
+snt_status snt_rq_mul(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev, const int16_t *b_dev,
+                      int16_t *c_dev, snt_stream stream) {
+    if (!ctx) return fail(SNT_EINVAL, "null context");
+    if (n == 0 || n > (size_t)INT32_MAX) return fail(SNT_EINVAL, "count %zu out of range", n);
+    if (!a_dev || !b_dev || !c_dev) return fail(SNT_EINVAL, "null buffer");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (P) {
+        case 653: SNT_CUDA(launch_mul_batch<653>((int)n, a_dev, b_dev, c_dev, st)); break;
+        case 761: SNT_CUDA(launch_mul_batch<761>((int)n, a_dev, b_dev, c_dev, st)); break;
+        case 857: SNT_CUDA(launch_mul_batch<857>((int)n, a_dev, b_dev, c_dev, st)); break;
+        default: return fail(SNT_EINVAL, "unknown parameter set %d", P);
+    }
+    return SNT_OK;
+}
+
+snt_status snt_rq_inv(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev, int16_t *out_dev,
+                      int32_t *ok_dev, snt_stream stream) {
+    if (!ctx) return fail(SNT_EINVAL, "null context");
+    if (n == 0 || n > (size_t)INT32_MAX) return fail(SNT_EINVAL, "count %zu out of range", n);
+    if (!a_dev || !out_dev || !ok_dev) return fail(SNT_EINVAL, "null buffer");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (P) {
+        case 653: SNT_CUDA(launch_rq_inv<653>((int)n, a_dev, 653, out_dev, 653, ok_dev, nullptr, 0, st)); break;
+        case 761: SNT_CUDA(launch_rq_inv<761>((int)n, a_dev, 761, out_dev, 761, ok_dev, nullptr, 0, st)); break;
+        case 857: SNT_CUDA(launch_rq_inv<857>((int)n, a_dev, 857, out_dev, 857, ok_dev, nullptr, 0, st)); break;
+        default: return fail(SNT_EINVAL, "unknown parameter set %d", P);
+    }
+    return SNT_OK;
+}
+
+snt_status snt_r3_inv(snt_ctx *ctx, int P, size_t n, const int8_t *g_dev, int8_t *out_dev,
+                      int32_t *ok_dev, snt_stream stream) {
+    if (!ctx) return fail(SNT_EINVAL, "null context");
+    if (n == 0 || n > (size_t)INT32_MAX - 3) return fail(SNT_EINVAL, "count %zu out of range", n);
+    if (!g_dev || !out_dev || !ok_dev) return fail(SNT_EINVAL, "null buffer");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (P) {
+        case 653: SNT_CUDA(launch_r3_inv<653>((int)n, g_dev, out_dev, ok_dev, st)); break;
+        case 761: SNT_CUDA(launch_r3_inv<761>((int)n, g_dev, out_dev, ok_dev, st)); break;
+        case 857: SNT_CUDA(launch_r3_inv<857>((int)n, g_dev, out_dev, ok_dev, st)); break;
+        default: return fail(SNT_EINVAL, "unknown parameter set %d", P);
+    }
+    return SNT_OK;
+}
+
+snt_status snt_debug_inject_g(snt_ctx *ctx, int P, size_t n, const uint64_t *key_index_host,
+                              const int8_t *g_host) {
+    if (!ctx) return fail(SNT_EINVAL, "null context");
+    ParamInfo pi;
+    if (!param_info(P, pi)) return fail(SNT_EINVAL, "unknown parameter set %d", P);
+    if (n > (size_t)kMaxInject) return fail(SNT_EINVAL, "at most %d injected draws", kMaxInject);
+    if (n && (!key_index_host || !g_host)) return fail(SNT_EINVAL, "null buffer");
+    for (size_t i = 0; i < n * (size_t)pi.p; ++i)
+        if (g_host[i] < -1 || g_host[i] > 1) return fail(SNT_EINVAL, "g coefficient outside {-1,0,1}");
+    DeviceGuard dg(ctx->device);
+    SNT_CUDA(cudaDeviceSynchronize());
+    if (n) {
+        SNT_CUDA(cudaMemcpy(ctx->d_inj_idx, key_index_host, n * sizeof(uint64_t), cudaMemcpyHostToDevice));
+        SNT_CUDA(cudaMemcpy(ctx->d_inj_g, g_host, n * (size_t)pi.p, cudaMemcpyHostToDevice));
+    }
+    ctx->n_inj = (int)n;
+    ctx->inj_P = P;
+    return SNT_OK;
+}
+
+snt_status snt_ctx_set_timing(snt_ctx *ctx, int on) {
+    if (!ctx) return fail(SNT_EINVAL, "null context");
+    ctx->timing = (on != 0);
+    return SNT_OK;
+}
+
+snt_status snt_ctx_phase_times(snt_ctx *ctx, float *ms, int n) {
+    if (!ctx || !ms || n < SNT_NPHASES) return fail(SNT_EINVAL, "need room for %d phases", SNT_NPHASES);
+    if (!ctx->timing) return fail(SNT_EINVAL, "phase timing is off");
+    DeviceGuard dg(ctx->device);
+    cudaEvent_t *ev = ctx->ev_phase;
+    SNT_CUDA(cudaEventSynchronize(ev[9]));
+    SNT_CUDA(cudaEventSynchronize(ev[3]));
+    const int pairs[SNT_NPHASES][2] = {{0, 1}, {2, 3}, {1, 4}, {4, 5}, {5, 6}, {7, 8}, {8, 9}, {0, 9}};
+    for (int i = 0; i < SNT_NPHASES; ++i)
+        SNT_CUDA(cudaEventElapsedTime(&ms[i], ev[pairs[i][0]], ev[pairs[i][1]]));
+    return SNT_OK;
+}
+
+const char *snt_last_error_string(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

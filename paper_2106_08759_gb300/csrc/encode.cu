@@ -1,0 +1,188 @@
+// encode.cu -- public key h = g * (3f)^-1 in R/q (Sec. 3.1 KeyGen step 4,
+// Algorithm 1 "H <- g * f-bar"), its Rq_encode, and the SHA-512 hash of the
+// public key stored at the end of the secret key.
+//
+// Rq_encode (the paper relies on the NTRU Prime encoding; reading: the
+// mixed-radix Encode with every radix q).  Entries (r_i, m_i), r_i in
+// [0, m_i).  One pass merges neighbouring entries into (r_2i + m_2i r_2i+1,
+// m_2i m_2i+1) and, while the merged radix is >= 2^14, emits the low byte and
+// sets radix <- ceil(radix / 256); an unpaired last entry moves up as is.
+// Within a pass every entry but the last has the same radix, so the number
+// of bytes each pair emits and its output offset are fixed: the host
+// computes that schedule once (EncSched) and each pair is one thread.
+#include "common.cuh"
+#include "kernels.h"
+#include "toeplitz.cuh"
+
+namespace snt {
+
+template <int P>
+__global__ void __launch_bounds__(Tp<P>::NT)
+k_finalize(const int8_t *__restrict__ gbuf, const int16_t *__restrict__ ainv,
+           uint8_t *__restrict__ pk, int pk_bytes, uint8_t *__restrict__ sk, int sk_bytes,
+           int sk_pk_off, EncSched S) {
+    using G = Geo<P>;
+    __shared__ __align__(16) int As[Tp<P>::p8];
+    __shared__ __align__(16) int Es[Tp<P>::ESZ];
+    __shared__ uint32_t Rb[2][G::pad];
+    __shared__ uint8_t ob[1344];
+    const int key = blockIdx.x;
+    const int8_t *g = gbuf + (size_t)key * G::pad;
+    const int16_t *inv = ainv + (size_t)key * G::pad;
+    fill_A<P>(g, As);
+    fill_E<P>(inv, Es);
+    __syncthreads();
+    int acc[1][8];
+    const int *const A1[1] = {As};
+    toeplitz_tile<P, 1>(A1, Es, acc);
+    toeplitz_finish<P>(As, (int)inv[P - 1], acc[0]);
+    const int j0 = 8 * threadIdx.x;
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+        if (j0 + t < P) Rb[0][j0 + t] = (uint32_t)(acc[0][t] + G::half);
+    __syncthreads();
+
+    int cur = 0;
+    for (int l = 0; l < S.nlev; ++l) {
+        const EncLevel L = S.lev[l];
+        const uint32_t *rin = Rb[cur];
+        uint32_t *rout = Rb[cur ^ 1];
+        for (int i = threadIdx.x; 2 * i < L.n; i += blockDim.x) {
+            if (2 * i + 1 < L.n) {
+                uint32_t r = rin[2 * i] + L.mu * rin[2 * i + 1];
+                const int e = (2 * i + 1 == L.n - 1) ? L.elast : L.eu;
+                const int off = L.boff + i * L.eu;
+                for (int b = 0; b < e; ++b) { ob[off + b] = (uint8_t)(r & 255u); r >>= 8; }
+                rout[i] = r;
+            } else {
+                rout[i] = rin[2 * i];
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    if (threadIdx.x == 0) {
+        uint32_t r = Rb[cur][0];
+        for (int b = 0; b < S.efinal; ++b) { ob[S.foff + b] = (uint8_t)(r & 255u); r >>= 8; }
+    }
+    __syncthreads();
+    uint8_t *pkk = pk + (size_t)key * pk_bytes;
+    uint8_t *skk = sk + (size_t)key * sk_bytes + sk_pk_off;
+    for (int b = threadIdx.x; b < pk_bytes; b += blockDim.x) {
+        pkk[b] = ob[b];
+        skk[b] = ob[b];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SHA-512 (FIPS 180-4) of 0x04 | pk, first 32 bytes into the secret key
+// (Hash_prefix(4, pk) of the NTRU Prime secret key).  One thread per key.
+// ---------------------------------------------------------------------------
+__constant__ uint64_t c_sha512_k[80] = {
+    0x428a2f98d728ae22ULL, 0x7137449123ef65cdULL, 0xb5c0fbcfec4d3b2fULL, 0xe9b5dba58189dbbcULL,
+    0x3956c25bf348b538ULL, 0x59f111f1b605d019ULL, 0x923f82a4af194f9bULL, 0xab1c5ed5da6d8118ULL,
+    0xd807aa98a3030242ULL, 0x12835b0145706fbeULL, 0x243185be4ee4b28cULL, 0x550c7dc3d5ffb4e2ULL,
+    0x72be5d74f27b896fULL, 0x80deb1fe3b1696b1ULL, 0x9bdc06a725c71235ULL, 0xc19bf174cf692694ULL,
+    0xe49b69c19ef14ad2ULL, 0xefbe4786384f25e3ULL, 0x0fc19dc68b8cd5b5ULL, 0x240ca1cc77ac9c65ULL,
+    0x2de92c6f592b0275ULL, 0x4a7484aa6ea6e483ULL, 0x5cb0a9dcbd41fbd4ULL, 0x76f988da831153b5ULL,
+    0x983e5152ee66dfabULL, 0xa831c66d2db43210ULL, 0xb00327c898fb213fULL, 0xbf597fc7beef0ee4ULL,
+    0xc6e00bf33da88fc2ULL, 0xd5a79147930aa725ULL, 0x06ca6351e003826fULL, 0x142929670a0e6e70ULL,
+    0x27b70a8546d22ffcULL, 0x2e1b21385c26c926ULL, 0x4d2c6dfc5ac42aedULL, 0x53380d139d95b3dfULL,
+    0x650a73548baf63deULL, 0x766a0abb3c77b2a8ULL, 0x81c2c92e47edaee6ULL, 0x92722c851482353bULL,
+    0xa2bfe8a14cf10364ULL, 0xa81a664bbc423001ULL, 0xc24b8b70d0f89791ULL, 0xc76c51a30654be30ULL,
+    0xd192e819d6ef5218ULL, 0xd69906245565a910ULL, 0xf40e35855771202aULL, 0x106aa07032bbd1b8ULL,
+    0x19a4c116b8d2d0c8ULL, 0x1e376c085141ab53ULL, 0x2748774cdf8eeb99ULL, 0x34b0bcb5e19b48a8ULL,
+    0x391c0cb3c5c95a63ULL, 0x4ed8aa4ae3418acbULL, 0x5b9cca4f7763e373ULL, 0x682e6ff3d6b2b8a3ULL,
+    0x748f82ee5defb2fcULL, 0x78a5636f43172f60ULL, 0x84c87814a1f0ab72ULL, 0x8cc702081a6439ecULL,
+    0x90befffa23631e28ULL, 0xa4506cebde82bde9ULL, 0xbef9a3f7b2c67915ULL, 0xc67178f2e372532bULL,
+    0xca273eceea26619cULL, 0xd186b8c721c0c207ULL, 0xeada7dd6cde0eb1eULL, 0xf57d4f7fee6ed178ULL,
+    0x06f067aa72176fbaULL, 0x0a637dc5a2c898a6ULL, 0x113f9804bef90daeULL, 0x1b710b35131c471bULL,
+    0x28db77f523047d84ULL, 0x32caab7b40c72493ULL, 0x3c9ebe0a15c9bebcULL, 0x431d67c49c100d4cULL,
+    0x4cc5d4becb3e42b6ULL, 0x597f299cfc657e2aULL, 0x5fcb6fab3ad6faecULL, 0x6c44198c4a475817ULL};
+
+__device__ __forceinline__ uint64_t rotr(uint64_t x, int n) { return (x >> n) | (x << (64 - n)); }
+
+// byte `pos` of the padded message 0x04 | pk | 0x80 | 0... | bitlen (128-bit BE)
+__device__ __forceinline__ uint32_t msg_byte(const uint8_t *pk, int pkb, int nblk, int pos) {
+    const int len = pkb + 1;
+    if (pos == 0) return 4u;
+    if (pos < len) return pk[pos - 1];
+    if (pos == len) return 0x80u;
+    const int tail = nblk * 128 - pos;  // 1 .. 16 for the length field
+    if (tail <= 8) return (uint32_t)(((uint64_t)len * 8u) >> (8 * (tail - 1))) & 255u;
+    return 0u;
+}
+
+__global__ void __launch_bounds__(128)
+k_sha512_pk(int B, const uint8_t *__restrict__ pk, int pk_bytes, uint8_t *__restrict__ sk,
+            int sk_bytes, int hash_off) {
+    const int key = blockIdx.x * blockDim.x + threadIdx.x;
+    if (key >= B) return;
+    const uint8_t *m = pk + (size_t)key * pk_bytes;
+    const int nblk = (pk_bytes + 1 + 1 + 16 + 127) / 128;
+    uint64_t H[8] = {0x6a09e667f3bcc908ULL, 0xbb67ae8584caa73bULL, 0x3c6ef372fe94f82bULL,
+                     0xa54ff53a5f1d36f1ULL, 0x510e527fade682d1ULL, 0x9b05688c2b3e6c1fULL,
+                     0x1f83d9abfb41bd6bULL, 0x5be0cd19137e2179ULL};
+    for (int blk = 0; blk < nblk; ++blk) {
+        uint64_t W[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            uint64_t v = 0;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) v = (v << 8) | msg_byte(m, pk_bytes, nblk, 128 * blk + 8 * t + b);
+            W[t] = v;
+        }
+        uint64_t a = H[0], b = H[1], c = H[2], d = H[3], e = H[4], f = H[5], g = H[6], h = H[7];
+#pragma unroll 16
+        for (int t = 0; t < 80; ++t) {
+            uint64_t w;
+            if (t < 16) {
+                w = W[t & 15];
+            } else {
+                const uint64_t w15 = W[(t - 15) & 15], w2 = W[(t - 2) & 15];
+                const uint64_t s0 = rotr(w15, 1) ^ rotr(w15, 8) ^ (w15 >> 7);
+                const uint64_t s1 = rotr(w2, 19) ^ rotr(w2, 61) ^ (w2 >> 6);
+                w = W[t & 15] + s0 + W[(t - 7) & 15] + s1;
+                W[t & 15] = w;
+            }
+            const uint64_t S1 = rotr(e, 14) ^ rotr(e, 18) ^ rotr(e, 41);
+            const uint64_t ch = (e & f) ^ (~e & g);
+            const uint64_t T1 = h + S1 + ch + c_sha512_k[t] + w;
+            const uint64_t S0 = rotr(a, 28) ^ rotr(a, 34) ^ rotr(a, 39);
+            const uint64_t mj = (a & b) ^ (a & c) ^ (b & c);
+            h = g; g = f; f = e; e = d + T1;
+            d = c; c = b; b = a; a = T1 + S0 + mj;
+        }
+        H[0] += a; H[1] += b; H[2] += c; H[3] += d;
+        H[4] += e; H[5] += f; H[6] += g; H[7] += h;
+    }
+    uint8_t *out = sk + (size_t)key * sk_bytes + hash_off;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) out[8 * i + b] = (uint8_t)(H[i] >> (56 - 8 * b));
+}
+
+template <int P>
+cudaError_t launch_finalize(int B, const int8_t *gbuf, const int16_t *ainv, uint8_t *pk,
+                            int pk_bytes, uint8_t *sk, int sk_bytes, int sk_pk_off,
+                            const EncSched &S, cudaStream_t st) {
+    k_finalize<P><<<B, Tp<P>::NT, 0, st>>>(gbuf, ainv, pk, pk_bytes, sk, sk_bytes, sk_pk_off, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sha512_pk(int B, const uint8_t *pk, int pk_bytes, uint8_t *sk, int sk_bytes,
+                             int hash_off, cudaStream_t st) {
+    k_sha512_pk<<<(B + 127) / 128, 128, 0, st>>>(B, pk, pk_bytes, sk, sk_bytes, hash_off);
+    return cudaGetLastError();
+}
+
+#define SNT_FIN_INST(P)                                                                       \
+    template cudaError_t launch_finalize<P>(int, const int8_t *, const int16_t *, uint8_t *, \
+                                            int, uint8_t *, int, int, const EncSched &,      \
+                                            cudaStream_t);
+SNT_FIN_INST(653)
+SNT_FIN_INST(761)
+SNT_FIN_INST(857)
+
+}  // namespace snt

@@ -1,0 +1,80 @@
+// peak.cu -- integer-pipe throughput microbenchmark used as the denominator
+// of the ALU roofline (LOP3 for the bit-sliced R/3 divsteps, IMAD for the R/q
+// products).  Eight independent register chains per thread, inline PTX so
+// every counted operation is exactly one instruction, grid = 8 CTAs of 256
+// threads per SM.
+#include <cstdio>
+
+#include "sntrup_gb300.h"
+
+namespace {
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_int_peak(int iters, unsigned seed, unsigned *sink) {
+    unsigned a0 = seed ^ threadIdx.x, a1 = a0 * 3u, a2 = a0 * 5u, a3 = a0 * 7u;
+    unsigned a4 = a0 * 11u, a5 = a0 * 13u, a6 = a0 * 17u, a7 = a0 * 19u;
+    const unsigned b = seed | 1u, c = seed >> 3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            if (KIND == 0) {
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a0) : "r"(b), "r"(c));
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a1) : "r"(b), "r"(c));
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a2) : "r"(b), "r"(c));
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a3) : "r"(b), "r"(c));
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a4) : "r"(b), "r"(c));
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a5) : "r"(b), "r"(c));
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a6) : "r"(b), "r"(c));
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a7) : "r"(b), "r"(c));
+            } else {
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a0) : "r"(b), "r"(c));
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a1) : "r"(b), "r"(c));
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a2) : "r"(b), "r"(c));
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a3) : "r"(b), "r"(c));
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a4) : "r"(b), "r"(c));
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a5) : "r"(b), "r"(c));
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a6) : "r"(b), "r"(c));
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a7) : "r"(b), "r"(c));
+            }
+        }
+    }
+    const unsigned x = a0 ^ a1 ^ a2 ^ a3 ^ a4 ^ a5 ^ a6 ^ a7;
+    if (x == 0x12345678u) sink[0] = x;  // keeps the chains live
+}
+
+}  // namespace
+
+extern "C" snt_status snt_measure_int_peak(int device, int kind, double *ops_per_s, int *sms) {
+    if (!ops_per_s || (kind != 0 && kind != 1)) return SNT_EINVAL;
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return SNT_ECUDA;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    unsigned *sink = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    const int blocks = prop.multiProcessorCount * 8, threads = 256, iters = 4096;
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(t0);
+        if (kind == 0) k_int_peak<0><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink);
+        else k_int_peak<1><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink);
+        cudaEventRecord(t1);
+        e = cudaEventSynchronize(t1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (rep > 0 && ms < best) best = ms;  // first launch is warm-up
+    }
+    if (e == cudaSuccess) {
+        const double ops = (double)blocks * threads * iters * 16.0 * 8.0;
+        *ops_per_s = ops / (best * 1e-3);
+        if (sms) *sms = prop.multiProcessorCount;
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (sink) cudaFree(sink);
+    cudaSetDevice(prev);
+    return e == cudaSuccess ? SNT_OK : SNT_ECUDA;
+}

@@ -1,0 +1,135 @@
+// rqinv.cu -- inversion in R/q = (Z/q)[x]/(x^p - x - 1) by divsteps, one CTA
+// per element.
+//
+// Used for the single root inversion of the batch-inversion tree (Sec. 2.2,
+// Montgomery's trick: "compute the single multiplicative inverse"; the paper
+// reports 785909 Haswell cycles for it in sntrup761, Sec. 3.4), for the
+// per-key path (Sec. 3.1 KeyGen step 4 without batching) and for the kernel
+// microbenchmark.  The paper cites Bernstein-Yang divsteps; the iteration on
+// reversed polynomials is
+//     F = 1 - x^(p-1) - x^p,  G = x^(p-1) a(1/x),  V = 0,  R = 1,  delta = 1;
+//     2p - 1 times:  V <- x V;
+//                    if delta > 0 and G(0) != 0: swap (F,G), (V,R), delta <- -delta;
+//                    delta <- delta + 1;
+//                    G <- (F(0) G - G(0) F) / x;  R <- F(0) R - G(0) V;
+//     a is invertible iff delta = 0; then (1/a)_i = V(p-1-i) / F(0).
+//
+// Layout: the four state polynomials live in shared memory as int32 in the
+// lazy range [-q, 2q).  A swap exchanges two buffer pointers, G <- G/x moves
+// G's base up one slot and V <- x V moves V's base down one slot, so no data
+// moves except the two multiply-reduce updates per coefficient.  A buffer's
+// base only moves while it plays G (up) or V (down), at most 2p - 1 times, so
+// 3p slots per buffer suffice; slots are zeroed once and the slots a moving
+// base uncovers were never written.  One barrier per step.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace snt {
+
+template <int P> struct InvGeo {
+    static constexpr int LEN = 3 * P;     // slots per state buffer
+    static constexpr int V0 = 2 * P - 1;  // initial base of the V/R buffers
+};
+
+template <int Q> __device__ __forceinline__ int mulmod_pos(int a, int b) {
+    return (int)(((long long)a * b) % Q);  // a, b in [0, Q)
+}
+
+template <int Q> __device__ __forceinline__ int inv_mod(int a) {  // a^(Q-2), a in [1, Q)
+    int acc = 1, base = a;
+    for (int e = Q - 2; e > 0; e >>= 1) {
+        if (e & 1) acc = mulmod_pos<Q>(acc, base);
+        base = mulmod_pos<Q>(base, base);
+    }
+    return acc;
+}
+
+// in: p centred coefficients (stride-free); out: p centred coefficients.
+template <int P, int NT, typename TIn>
+__device__ __forceinline__ bool rq_inv_cta(const TIn *__restrict__ in, int16_t *__restrict__ out,
+                                           int (*buf)[InvGeo<P>::LEN]) {
+    constexpr int Q = Geo<P>::q;
+    constexpr int LEN = InvGeo<P>::LEN;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 4 * LEN; i += NT) (&buf[0][0])[i] = 0;
+    __syncthreads();
+    // buffers 0/1 play F/G, 2/3 play V/R
+    int *Fb = buf[0], *Gb = buf[1], *Vb = buf[2], *Rb = buf[3];
+    int bf = 0, bg = 0, bv = InvGeo<P>::V0, br = InvGeo<P>::V0;
+    for (int i = tid; i < P; i += NT) Gb[i] = (int)in[P - 1 - i];
+    if (tid == 0) {
+        Fb[0] = 1;
+        Fb[P - 1] = -1;
+        Fb[P] = -1;
+        Rb[br] = 1;
+    }
+    __syncthreads();
+    int delta = 1;
+    for (int step = 0; step < 2 * P - 1; ++step) {
+        --bv;  // V <- x V (the uncovered slot is zero)
+        int f0 = freeze_lazy<Q>(Fb[bf]);
+        int g0 = freeze_lazy<Q>(Gb[bg]);
+        if (delta > 0 && g0 != 0) {  // warp-uniform (all threads read the same values)
+            int *t = Fb; Fb = Gb; Gb = t;
+            int tb = bf; bf = bg; bg = tb;
+            t = Vb; Vb = Rb; Rb = t;
+            tb = bv; bv = br; br = tb;
+            const int tv = f0; f0 = g0; g0 = tv;
+            delta = -delta;
+        }
+        ++delta;
+        const int ng0 = g0 ? Q - g0 : 0;  // -g0 in [0, Q)
+#pragma unroll 4
+        for (int i = tid; i <= P; i += NT) {
+            if (i >= 1) Gb[bg + i] = lazy_red<Q>(f0 * Gb[bg + i] + ng0 * Fb[bf + i]);
+            Rb[br + i] = lazy_red<Q>(f0 * Rb[br + i] + ng0 * Vb[bv + i]);
+        }
+        ++bg;  // G <- G / x (G(0) is zero now)
+        __syncthreads();
+    }
+    const bool ok = (delta == 0);
+    const int f0 = freeze_lazy<Q>(Fb[bf]);
+    const int s = ok ? inv_mod<Q>(f0) : 0;
+    for (int i = tid; i < P; i += NT) {
+        const int v = freeze_lazy<Q>(Vb[bv + P - 1 - i]);
+        out[i] = (int16_t)cmod<Q>(s * v);
+    }
+    return ok;
+}
+
+template <int P> constexpr int inv_threads() { return 256; }
+
+// Element e of n: in + e*in_stride -> out + e*out_stride (p coefficients each;
+// the pads of the output rows are left untouched).  ok[e] = invertible.
+// In-place use (in == out) is safe: the input is read before any output store.
+template <int P, int NT, typename TIn>
+__global__ void __launch_bounds__(NT)
+k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
+         int32_t *__restrict__ okv, int *__restrict__ err, int err_bit) {
+    __shared__ int buf[4][InvGeo<P>::LEN];
+    const int e = blockIdx.x;
+    if (e >= n) return;
+    const bool ok = rq_inv_cta<P, NT, TIn>(in + (size_t)e * in_stride,
+                                           out + (size_t)e * out_stride, buf);
+    if (threadIdx.x == 0) {
+        if (okv) okv[e] = ok ? 1 : 0;
+        if (!ok && err) atomicOr(err, err_bit);
+    }
+}
+
+template <int P>
+cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out,
+                          long out_stride, int32_t *ok, int *err, int err_bit, cudaStream_t st) {
+    constexpr int NT = inv_threads<P>();
+    k_rq_inv<P, NT, int16_t><<<n, NT, 0, st>>>(n, in, in_stride, out, out_stride, ok, err, err_bit);
+    return cudaGetLastError();
+}
+
+#define SNT_INV_INST(P)                                                                    \
+    template cudaError_t launch_rq_inv<P>(int, const int16_t *, long, int16_t *, long,     \
+                                          int32_t *, int *, int, cudaStream_t);
+SNT_INV_INST(653)
+SNT_INV_INST(761)
+SNT_INV_INST(857)
+
+}  // namespace snt

@@ -1,0 +1,128 @@
+// rqmul.cu -- R/q products of the batch-inversion product tree, and a batched
+// product for the kernel microbenchmark.
+//
+// Montgomery's trick (Sec. 2.2) turns n inversions into 3n - 3
+// multiplications and one inversion.  The paper runs it as a prefix chain;
+// here the same multiplications are arranged as a binary product tree so
+// that every level is one parallel launch:
+//   up-sweep:   node(l, j) = node(l-1, 2j) * node(l-1, 2j+1)
+//               (an unpaired last node moves up unchanged);
+//   root:       one inversion (rqinv.cu);
+//   down-sweep: with T = 1/node(l, j),
+//               1/node(l-1, 2j) = T * node(l-1, 2j+1),
+//               1/node(l-1, 2j+1) = T * node(l-1, 2j),
+//               written over the two children in place.
+// For B leaves that is B - 1 products up and 2(B - 1) down: 3B - 3 in total.
+// Every polynomial is int16, centred, stride Geo<P>::pad.
+#include "kernels.h"
+#include "toeplitz.cuh"
+
+namespace snt {
+
+template <int P>
+__global__ void __launch_bounds__(Tp<P>::NT)
+k_tree_up(const int16_t *__restrict__ lin, int n_in, int16_t *__restrict__ lout) {
+    using G = Geo<P>;
+    __shared__ __align__(16) int As[Tp<P>::p8];
+    __shared__ __align__(16) int Es[Tp<P>::ESZ];
+    const int j = blockIdx.x;
+    const int16_t *a = lin + (size_t)(2 * j) * G::pad;
+    int16_t *c = lout + (size_t)j * G::pad;
+    if (2 * j + 1 >= n_in) {  // unpaired: move up unchanged
+        for (int i = threadIdx.x; i < G::pad; i += blockDim.x) c[i] = a[i];
+        return;
+    }
+    const int16_t *b = a + G::pad;
+    fill_A<P>(a, As);
+    fill_E<P>(b, Es);
+    __syncthreads();
+    int acc[1][8];
+    const int *const A1[1] = {As};
+    toeplitz_tile<P, 1>(A1, Es, acc);
+    toeplitz_finish<P>(As, (int)b[P - 1], acc[0]);
+    store_tile<P>(c, acc[0], G::pad);
+}
+
+template <int P>
+__global__ void __launch_bounds__(Tp<P>::NT)
+k_tree_down(const int16_t *__restrict__ lpar, int16_t *__restrict__ lch, int n_ch) {
+    using G = Geo<P>;
+    __shared__ __align__(16) int Xs[Tp<P>::p8];
+    __shared__ __align__(16) int Ys[Tp<P>::p8];
+    __shared__ __align__(16) int Es[Tp<P>::ESZ];
+    const int j = blockIdx.x;
+    const int16_t *T = lpar + (size_t)j * G::pad;
+    int16_t *x = lch + (size_t)(2 * j) * G::pad;
+    if (2 * j + 1 >= n_ch) {  // unpaired child: its inverse is the parent's
+        for (int i = threadIdx.x; i < G::pad; i += blockDim.x) x[i] = T[i];
+        return;
+    }
+    int16_t *y = x + G::pad;
+    fill_A<P>(x, Xs);
+    fill_A<P>(y, Ys);
+    fill_E<P>(T, Es);
+    __syncthreads();  // both children are in shared memory before either is overwritten
+    int acc[2][8];
+    const int *const A2[2] = {Ys, Xs};
+    toeplitz_tile<P, 2>(A2, Es, acc);
+    const int tl = (int)T[P - 1];
+    toeplitz_finish<P>(Ys, tl, acc[0]);
+    toeplitz_finish<P>(Xs, tl, acc[1]);
+    store_tile<P>(x, acc[0], G::pad);  // 1/x = T * y
+    store_tile<P>(y, acc[1], G::pad);  // 1/y = T * x
+}
+
+// c_e = a_e * b_e, n products, all operands stride p (microbenchmark layout).
+template <int P>
+__global__ void __launch_bounds__(Tp<P>::NT)
+k_mul_batch(int n, const int16_t *__restrict__ a, const int16_t *__restrict__ b,
+            int16_t *__restrict__ c) {
+    __shared__ __align__(16) int As[Tp<P>::p8];
+    __shared__ __align__(16) int Es[Tp<P>::ESZ];
+    const int e = blockIdx.x;
+    if (e >= n) return;
+    const int16_t *ae = a + (size_t)e * P, *be = b + (size_t)e * P;
+    fill_A<P>(ae, As);
+    fill_E<P>(be, Es);
+    __syncthreads();
+    int acc[1][8];
+    const int *const A1[1] = {As};
+    toeplitz_tile<P, 1>(A1, Es, acc);
+    toeplitz_finish<P>(As, (int)be[P - 1], acc[0]);
+    const int j0 = 8 * threadIdx.x;
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+        if (j0 + t < P) c[(size_t)e * P + j0 + t] = (int16_t)acc[0][t];
+}
+
+template <int P>
+cudaError_t launch_tree_up(const int16_t *lin, int n_in, int16_t *lout, cudaStream_t st) {
+    const int n_out = (n_in + 1) / 2;
+    k_tree_up<P><<<n_out, Tp<P>::NT, 0, st>>>(lin, n_in, lout);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_tree_down(const int16_t *lpar, int16_t *lch, int n_ch, cudaStream_t st) {
+    const int n_par = (n_ch + 1) / 2;
+    k_tree_down<P><<<n_par, Tp<P>::NT, 0, st>>>(lpar, lch, n_ch);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_mul_batch(int n, const int16_t *a, const int16_t *b, int16_t *c,
+                             cudaStream_t st) {
+    k_mul_batch<P><<<n, Tp<P>::NT, 0, st>>>(n, a, b, c);
+    return cudaGetLastError();
+}
+
+#define SNT_MUL_INST(P)                                                                        \
+    template cudaError_t launch_tree_up<P>(const int16_t *, int, int16_t *, cudaStream_t);     \
+    template cudaError_t launch_tree_down<P>(const int16_t *, int16_t *, int, cudaStream_t);   \
+    template cudaError_t launch_mul_batch<P>(int, const int16_t *, const int16_t *, int16_t *, \
+                                             cudaStream_t);
+SNT_MUL_INST(653)
+SNT_MUL_INST(761)
+SNT_MUL_INST(857)
+
+}  // namespace snt

@@ -1,0 +1,132 @@
+// toeplitz.cuh -- R/q multiplication c = a * b in (Z/q)[x]/(x^p - x - 1)
+// for one CTA of p8/8 threads, each thread owning 8 consecutive outputs.
+//
+// With x^p = x + 1 (Sec. 2.1) every term a_i b_m of the schoolbook product
+// lands in output j = i + m, or, when i + m >= p, in outputs i + m - p and
+// i + m - p + 1.  Grouped by d = j - i this gives, for every output j,
+//     c_j = sum_{i=0}^{p-1} a_i E[d + p - 1]  +  [j >= 1] a_j b_{p-1},
+//     E[d + p - 1] = b_d                      for d >= 0,
+//                  = b_{p+d} + b_{p+d-1}      for d < 0,
+// i.e. exactly p terms per output (a Toeplitz matrix-vector product), so all
+// threads do the same work and no separate reduction pass is needed.
+//
+// Range: operands are centred, |a_i|, |E| <= (q-1)/2 = 2295 for sntrup761, so
+// one term is below 5.27e6 and 256 terms below 1.35e9 < 2^31: the int32
+// accumulators are reduced mod q after every 256 terms (the paper's bound
+// 2295 * 2295 * 761 > 2^31, Sec. 3.3, is why a single pass would overflow).
+#pragma once
+#include "common.cuh"
+
+namespace snt {
+
+template <int P> struct Tp {
+    static constexpr int p8 = Geo<P>::p8;
+    static constexpr int OFF = 8;                                   // zero guard below E
+    static constexpr int ESZ = (OFF + P + p8 - 1 + 3) / 4 * 4;      // E table length
+    static constexpr int NT = p8 / 8;                               // threads per product
+    static_assert((P & 3) == 1, "16-byte aligned windows need p = 1 mod 4");
+};
+
+// E table of b (centred int16, any stride) into shared memory.
+template <int P, typename T>
+__device__ __forceinline__ void fill_E(const T *__restrict__ b, int *Es) {
+    using G = Geo<P>;
+    for (int idx = threadIdx.x; idx < Tp<P>::ESZ; idx += blockDim.x) {
+        const int t = idx - Tp<P>::OFF;
+        int e = 0;
+        if (t >= 0 && t <= 2 * P - 2) {
+            const int d = t - (P - 1);
+            e = (d >= 0) ? (int)b[d] : cmod<G::q>((int)b[P + d] + (int)b[P + d - 1]);
+        }
+        Es[idx] = e;
+    }
+}
+
+// a (int16 or int8, first p entries) into shared int32, zero up to p8.
+template <int P, typename T>
+__device__ __forceinline__ void fill_A(const T *__restrict__ a, int *As) {
+    for (int i = threadIdx.x; i < Tp<P>::p8; i += blockDim.x) As[i] = (i < P) ? (int)a[i] : 0;
+}
+
+// acc[k][t] = sum_i A_k[i] E[j0 + t - i + p - 1] for NA operands sharing E,
+// reduced mod q every 256 terms; j0 = 8 * threadIdx.x.
+template <int P, int NA>
+__device__ __forceinline__ void toeplitz_tile(const int *const (&As)[NA], const int *Es,
+                                              int (&acc)[NA][8]) {
+    constexpr int Q = Geo<P>::q;
+    const int j0 = 8 * threadIdx.x;
+    const int base = Tp<P>::OFF + P - 9 + j0;  // window start for i-block 0
+#pragma unroll
+    for (int k = 0; k < NA; ++k)
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc[k][t] = 0;
+    int whi[8];
+    {
+        const int4 h0 = *reinterpret_cast<const int4 *>(&Es[base + 8]);
+        const int4 h1 = *reinterpret_cast<const int4 *>(&Es[base + 12]);
+        whi[0] = h0.x; whi[1] = h0.y; whi[2] = h0.z; whi[3] = h0.w;
+        whi[4] = h1.x; whi[5] = h1.y; whi[6] = h1.z; whi[7] = h1.w;
+    }
+#pragma unroll 2
+    for (int ib = 0; ib < Tp<P>::p8; ib += 8) {
+        int wlo[8];
+        const int4 l0 = *reinterpret_cast<const int4 *>(&Es[base - ib]);
+        const int4 l1 = *reinterpret_cast<const int4 *>(&Es[base - ib + 4]);
+        wlo[0] = l0.x; wlo[1] = l0.y; wlo[2] = l0.z; wlo[3] = l0.w;
+        wlo[4] = l1.x; wlo[5] = l1.y; wlo[6] = l1.z; wlo[7] = l1.w;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            const int4 a0 = *reinterpret_cast<const int4 *>(&As[k][ib]);
+            const int4 a1 = *reinterpret_cast<const int4 *>(&As[k][ib + 4]);
+            const int a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int wi = 8 + t - u;  // 1 .. 15
+                    const int e = (wi >= 8) ? whi[wi - 8] : wlo[wi];
+                    acc[k][t] += a[u] * e;
+                }
+        }
+#pragma unroll
+        for (int z = 0; z < 8; ++z) whi[z] = wlo[z];
+        if (((ib + 8) & 255) == 0) {
+#pragma unroll
+            for (int k = 0; k < NA; ++k)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc[k][t] = cmod<Q>(acc[k][t]);
+        }
+    }
+}
+
+// Adds the [j >= 1] a_j b_{p-1} term, reduces, and returns centred values
+// (zero for j >= p).
+template <int P>
+__device__ __forceinline__ void toeplitz_finish(const int *As, int blast, int (&acc)[8]) {
+    constexpr int Q = Geo<P>::q;
+    const int j0 = 8 * threadIdx.x;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int j = j0 + t;
+        int v = acc[t];
+        if (j >= 1 && j < P) v += As[j] * blast;
+        acc[t] = (j < P) ? cmod<Q>(v) : 0;
+    }
+}
+
+// Stores 8 outputs (j0 .. j0+7) as int16; pads from p8 to `pad` are zeroed by
+// the threads that own the last tile.
+template <int P>
+__device__ __forceinline__ void store_tile(int16_t *__restrict__ c, const int (&v)[8], int pad) {
+    const int j0 = 8 * threadIdx.x;
+    int4 pk;
+    pk.x = (v[0] & 0xffff) | (v[1] << 16);
+    pk.y = (v[2] & 0xffff) | (v[3] << 16);
+    pk.z = (v[4] & 0xffff) | (v[5] << 16);
+    pk.w = (v[6] & 0xffff) | (v[7] << 16);
+    *reinterpret_cast<int4 *>(&c[j0]) = pk;
+    if (threadIdx.x == blockDim.x - 1)
+        for (int j = Tp<P>::p8; j < pad; ++j) c[j] = 0;
+}
+
+}  // namespace snt

@@ -1,0 +1,156 @@
+"""Building-block kernels (R/q product, R/q and R/3 inversion) vs the oracle,
+on small cases and on the full-size microbenchmark workload (sampled)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def snt():
+    require_gpu()
+    import paper_2106_08759_gb300 as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(snt):
+    c = snt.Context(0, 64 << 20)
+    yield c
+    c.close()
+
+
+def _t(x, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dtype=dtype, device="cuda")
+
+
+def _rq_cases(p, q, rng, n):
+    h = (q - 1) // 2
+    a = rng.integers(-h, h + 1, (n, p))
+    b = rng.integers(-h, h + 1, (n, p))
+    a[0], b[0] = h, h            # all-max coefficients
+    a[1], b[1] = -h, h
+    a[2], b[2] = 0, rng.integers(-h, h + 1, p)
+    a[3] = 0; a[3, p - 1] = 1    # x^(p-1) * x^(p-1)
+    b[3] = 0; b[3, p - 1] = 1
+    a[4] = rng.integers(-1, 2, p)  # ternary operand
+    return a, b
+
+
+@pytest.mark.parametrize("P", [653, 761, 857])
+def test_rq_mul_matches_oracle(snt, ctx, P):
+    import torch
+    p, q, _ = oracle.PARAMS[P]
+    rng = np.random.default_rng(P)
+    n = 40
+    a, b = _rq_cases(p, q, rng, n)
+    c = torch.empty(n * p, dtype=torch.int16, device="cuda")
+    snt.snt_rq_mul(ctx, P, n, _t(a.ravel(), torch.int16), _t(b.ravel(), torch.int16), c)
+    got = c.cpu().numpy().reshape(n, p)
+    for i in range(n):
+        assert np.array_equal(got[i], oracle.ring_mul(p, q, a[i], b[i])), i
+
+
+@pytest.mark.parametrize("P", [653, 761, 857])
+def test_rq_inv_matches_oracle(snt, ctx, P):
+    import torch
+    p, q, _ = oracle.PARAMS[P]
+    rng = np.random.default_rng(P + 1)
+    n = 12
+    h = (q - 1) // 2
+    a = rng.integers(-h, h + 1, (n, p))
+    a[0] = 0                      # not invertible
+    a[1] = 0; a[1, 0] = 1         # 1
+    a[2] = 3 * rng.integers(-1, 2, p)
+    out = torch.empty(n * p, dtype=torch.int16, device="cuda")
+    ok = torch.empty(n, dtype=torch.int32, device="cuda")
+    snt.snt_rq_inv(ctx, P, n, _t(a.ravel(), torch.int16), out, ok)
+    got = out.cpu().numpy().reshape(n, p)
+    okh = ok.cpu().numpy()
+    for i in range(n):
+        rok, ref = oracle.ring_inv(p, q, a[i])
+        assert bool(okh[i]) == rok, i
+        assert np.array_equal(got[i], ref), i
+
+
+def _non_invertible(p, rng):
+    parts = oracle.ddf(p, 3)
+    d, _, f1 = min(parts, key=lambda t: t[0])
+    f1 = f1[: d + 1]
+    r = rng.integers(0, 3, p - d)
+    g = np.convolve(f1, r) % 3
+    return np.where(g == 2, -1, g)
+
+
+@pytest.mark.parametrize("P", [653, 761, 857])
+def test_r3_inv_matches_oracle(snt, ctx, P):
+    import torch
+    p = P
+    rng = np.random.default_rng(P + 2)
+    n = 20
+    g = rng.integers(-1, 2, (n, p))
+    g[0] = 0
+    g[1] = 0; g[1, 0] = 1
+    g[2] = _non_invertible(p, rng)
+    g[3] = 1
+    out = torch.empty(n * p, dtype=torch.int8, device="cuda")
+    ok = torch.empty(n, dtype=torch.int32, device="cuda")
+    snt.snt_r3_inv(ctx, P, n, _t(g.ravel(), torch.int8), out, ok)
+    got = out.cpu().numpy().reshape(n, p)
+    okh = ok.cpu().numpy()
+    assert okh[2] == 0 and okh[0] == 0
+    for i in range(n):
+        rok, ref = oracle.ring_inv(p, 3, g[i])
+        assert bool(okh[i]) == rok, i
+        assert np.array_equal(got[i], ref), i
+
+
+def test_microbench_sizes_sampled(snt, ctx):
+    """Kernel microbenchmark workload at full size, sampled against the oracle:
+    2^20 general x general and 2^20 general x Short products, 2^16 R/3 and
+    2^10 R/q inversions (p = 761)."""
+    import torch
+    p, q, w = oracle.PARAMS[761]
+    from synth import rq_uniform, short_batch, ternary_batch
+    n = 1 << 20
+    a = rq_uniform(761, n, seed=1)
+    b = rq_uniform(761, n, seed=2)
+    s = short_batch(761, n, seed=3)
+    da, db, ds = _t(a.ravel(), torch.int16), _t(b.ravel(), torch.int16), _t(s.ravel(), torch.int16)
+    c = torch.empty(n * p, dtype=torch.int16, device="cuda")
+    c2 = torch.empty(n * p, dtype=torch.int16, device="cuda")
+    snt.snt_rq_mul(ctx, 761, n, da, db, c)
+    snt.snt_rq_mul(ctx, 761, n, da, ds, c2)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    idx = rng.integers(0, n, 64)
+    got = c.view(n, p)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    got2 = c2.view(n, p)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    for k, i in enumerate(idx):
+        assert np.array_equal(got[k], oracle.ring_mul(p, q, a[i], b[i]))
+        assert np.array_equal(got2[k], oracle.ring_mul(p, q, a[i], s[i]))
+    del c, c2, da, db, ds
+    m = 1 << 16
+    g = ternary_batch(761, m, seed=5)
+    out = torch.empty(m * p, dtype=torch.int8, device="cuda")
+    ok = torch.empty(m, dtype=torch.int32, device="cuda")
+    snt.snt_r3_inv(ctx, 761, m, _t(g.ravel(), torch.int8), out, ok)
+    outh = out.cpu().numpy().reshape(m, p)
+    okh = ok.cpu().numpy()
+    for i in rng.integers(0, m, 48):
+        rok, ref = oracle.ring_inv(p, 3, g[i])
+        assert bool(okh[i]) == rok and np.array_equal(outh[i], ref)
+    k = 1 << 10
+    x = rq_uniform(761, k, seed=6)
+    out = torch.empty(k * p, dtype=torch.int16, device="cuda")
+    ok = torch.empty(k, dtype=torch.int32, device="cuda")
+    snt.snt_rq_inv(ctx, 761, k, _t(x.ravel(), torch.int16), out, ok)
+    outh = out.cpu().numpy().reshape(k, p)
+    assert ok.cpu().numpy().all()
+    for i in rng.integers(0, k, 24):
+        assert np.array_equal(outh[i], oracle.ring_inv(p, q, x[i])[1])

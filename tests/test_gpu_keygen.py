@@ -1,0 +1,122 @@
+"""Key generation on the GPU, byte for byte against the CPU oracle.
+
+Batched path (Algorithm 1 with a product tree for batchInv, Sec. 2.2) and
+per-key path (Sec. 3.1 KeyGen) must both reproduce the oracle's keys exactly:
+inverses in the field R/q are unique, so batching cannot change any byte.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import first_mismatch, gpu_keygen, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x0123456789ABCDEF
+
+
+@pytest.fixture(scope="module")
+def snt():
+    require_gpu()
+    import paper_2106_08759_gb300 as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(snt):
+    c = snt.Context(0, 256 << 20)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("perkey", [False, True])
+def test_b32_every_key_matches_oracle(snt, ctx, perkey):
+    # 32 keys of sntrup761 from a fixed 64-bit seed, key indices 0..31
+    pk, sk = gpu_keygen(snt, ctx, 761, SEED, 0, 32, perkey=perkey)
+    rpk, rsk = oracle.keygen_batch(761, SEED, 0, 32)
+    assert first_mismatch(pk, rpk) is None
+    assert first_mismatch(sk, rsk) is None
+
+
+@pytest.mark.parametrize("P", [653, 857])
+def test_other_parameter_sets(snt, ctx, P):
+    pk, sk = gpu_keygen(snt, ctx, P, 77, 1000, 9)
+    rpk, rsk = oracle.keygen_batch(P, 77, 1000, 9)
+    assert first_mismatch(pk, rpk) is None
+    assert first_mismatch(sk, rsk) is None
+
+
+@pytest.mark.parametrize("B", [1, 2, 3, 5, 31, 33])
+def test_ragged_tree_shapes(snt, ctx, B):
+    # non-power-of-two B: unpaired nodes move up unchanged
+    pk, sk = gpu_keygen(snt, ctx, 761, 5, 40, B)
+    rpk, rsk = oracle.keygen_batch(761, 5, 40, B)
+    assert first_mismatch(pk, rpk) is None
+    assert first_mismatch(sk, rsk) is None
+
+
+def test_split_batches_give_identical_bytes(snt, ctx):
+    pk, sk = gpu_keygen(snt, ctx, 761, 9, 100, 37)
+    pk1, sk1 = gpu_keygen(snt, ctx, 761, 9, 100, 20)
+    pk2, sk2 = gpu_keygen(snt, ctx, 761, 9, 120, 17)
+    assert np.array_equal(pk, np.concatenate([pk1, pk2]))
+    assert np.array_equal(sk, np.concatenate([sk1, sk2]))
+
+
+def _non_invertible_g(p=761):
+    parts = oracle.ddf(p, 3)
+    f1 = [poly for d, _, poly in parts if d == 19][0][:20]
+    r = np.random.default_rng(12).integers(0, 3, p - 19)
+    bad = np.convolve(f1, r) % 3
+    return np.where(bad == 2, -1, bad).astype(np.int8)
+
+
+def test_resampling_of_non_invertible_g(snt, ctx):
+    bad = _non_invertible_g()
+    snt.snt_debug_inject_g(ctx, 761, [7, 9], np.stack([bad, bad]))
+    try:
+        pk, sk = gpu_keygen(snt, ctx, 761, 3, 5, 8)  # key indices 5..12
+    finally:
+        snt.snt_debug_inject_g(ctx, 761, [], np.zeros((0, 761), np.int8))
+    rpk, rsk = oracle.keygen_batch(761, 3, 5, 8, g_inject={2: bad, 4: bad})
+    assert first_mismatch(pk, rpk) is None
+    assert first_mismatch(sk, rsk) is None
+    # the injected keys really took the second attempt
+    assert oracle.keygen(761, 3, 7, g_attempt0=bad)[2] == 2
+
+
+def test_b4096_sampled_keys_and_batched_equals_perkey(snt, ctx):
+    B, seed = 4096, 1
+    pk, sk = gpu_keygen(snt, ctx, 761, seed, 0, B)
+    pk2, sk2 = gpu_keygen(snt, ctx, 761, seed, 0, B, perkey=True)
+    assert np.array_equal(pk, pk2) and np.array_equal(sk, sk2)
+    rng = np.random.default_rng(2)
+    idx = sorted(set([0, 1, 2047, 2048, 4094, 4095] + list(rng.integers(0, B, 26))))
+    for i in idx:
+        rpk, rsk, _ = oracle.keygen(761, seed, i)
+        assert np.array_equal(pk[i], rpk), i
+        assert np.array_equal(sk[i], rsk), i
+
+
+def test_invalid_arguments(snt, ctx):
+    torch = require_gpu()
+    pk = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(snt.SntError) as e:
+        snt.snt_batch_keygen(ctx, 761, 0, 0, 0, pk, pk)
+    assert e.value.status == -1
+    with pytest.raises(snt.SntError) as e:
+        snt.snt_batch_keygen(ctx, 760, 0, 0, 1, pk, pk)
+    assert e.value.status == -1
+    small = snt.Context(0, 1 << 20)
+    with pytest.raises(snt.SntError) as e:
+        snt.snt_batch_keygen(small, 761, 0, 0, 4096, pk, pk)
+    assert e.value.status == -2
+    assert small.max_batch(761) >= 1
+    small.close()
+
+
+def test_host_buffer_entry_point(snt, ctx):
+    pk, sk = snt.snt_batch_keygen_host(ctx, 761, SEED, 3, 6)
+    rpk, rsk = oracle.keygen_batch(761, SEED, 3, 6)
+    assert np.array_equal(pk, rpk) and np.array_equal(sk, rsk)
