@@ -35,7 +35,8 @@ k_finalize(const int8_t *__restrict__ gbuf, const int16_t *__restrict__ ainv,
     int acc[1][8];
     const int *const A1[1] = {As};
     toeplitz_tile<P, 1>(A1, Es, acc);
-    toeplitz_finish<P>(As, (int)inv[P - 1], acc[0]);
+    const int bl[1] = {(int)inv[P - 1]};
+    toeplitz_finish<P, 1>(A1, bl, acc);
     const int j0 = 8 * threadIdx.x;
 #pragma unroll
     for (int t = 0; t < 8; ++t)

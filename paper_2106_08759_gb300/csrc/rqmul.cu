@@ -39,7 +39,8 @@ k_tree_up(const int16_t *__restrict__ lin, int n_in, int16_t *__restrict__ lout)
     int acc[1][8];
     const int *const A1[1] = {As};
     toeplitz_tile<P, 1>(A1, Es, acc);
-    toeplitz_finish<P>(As, (int)b[P - 1], acc[0]);
+    const int bl[1] = {(int)b[P - 1]};
+    toeplitz_finish<P, 1>(A1, bl, acc);
     store_tile<P>(c, acc[0], G::pad);
 }
 
@@ -66,8 +67,8 @@ k_tree_down(const int16_t *__restrict__ lpar, int16_t *__restrict__ lch, int n_c
     const int *const A2[2] = {Ys, Xs};
     toeplitz_tile<P, 2>(A2, Es, acc);
     const int tl = (int)T[P - 1];
-    toeplitz_finish<P>(Ys, tl, acc[0]);
-    toeplitz_finish<P>(Xs, tl, acc[1]);
+    const int bl[2] = {tl, tl};
+    toeplitz_finish<P, 2>(A2, bl, acc);
     store_tile<P>(x, acc[0], G::pad);  // 1/x = T * y
     store_tile<P>(y, acc[1], G::pad);  // 1/y = T * x
 }
@@ -88,7 +89,8 @@ k_mul_batch(int n, const int16_t *__restrict__ a, const int16_t *__restrict__ b,
     int acc[1][8];
     const int *const A1[1] = {As};
     toeplitz_tile<P, 1>(A1, Es, acc);
-    toeplitz_finish<P>(As, (int)be[P - 1], acc[0]);
+    const int bl[1] = {(int)be[P - 1]};
+    toeplitz_finish<P, 1>(A1, bl, acc);
     const int j0 = 8 * threadIdx.x;
 #pragma unroll
     for (int t = 0; t < 8; ++t)

@@ -3,12 +3,13 @@
 //
 // With x^p = x + 1 (Sec. 2.1) every term a_i b_m of the schoolbook product
 // lands in output j = i + m, or, when i + m >= p, in outputs i + m - p and
-// i + m - p + 1.  Grouped by d = j - i this gives, for every output j,
-//     c_j = sum_{i=0}^{p-1} a_i E[d + p - 1]  +  [j >= 1] a_j b_{p-1},
+// i + m - p + 1.  Grouped by d = j - i this gives, for every output j >= 1,
+//     c_j = sum_{i=0}^{p-1} a_i E[d + p - 1]  +  a_j b_{p-1},
 //     E[d + p - 1] = b_d                      for d >= 0,
 //                  = b_{p+d} + b_{p+d-1}      for d < 0,
 // i.e. exactly p terms per output (a Toeplitz matrix-vector product), so all
-// threads do the same work and no separate reduction pass is needed.
+// threads do the same work and no separate reduction pass is needed.  Output
+// 0 gets one correction from output p - 1 (toeplitz_finish).
 //
 // Range: operands are centred, |a_i|, |E| <= (q-1)/2 = 2295 for sntrup761, so
 // one term is below 5.27e6 and 256 terms below 1.35e9 < 2^31: the int32
@@ -99,18 +100,34 @@ __device__ __forceinline__ void toeplitz_tile(const int *const (&As)[NA], const 
     }
 }
 
-// Adds the [j >= 1] a_j b_{p-1} term, reduces, and returns centred values
-// (zero for j >= p).
-template <int P>
-__device__ __forceinline__ void toeplitz_finish(const int *As, int blast, int (&acc)[8]) {
+// Adds the [j >= 1] a_j b_{p-1} term, reduces, fixes output 0 and returns
+// centred values (zero for j >= p).  Output 0 needs a fix: the E table also
+// folds the x^(p-1) coefficient c_{p-1} = sum_{i+m=p-1} a_i b_m into row 0,
+// although x^(p-1) is not reduced.  The row-(p-1) result is exactly
+// c_{p-1} + a_{p-1} b_{p-1}, so
+//     c_0 = (row 0) - (row p-1) + (a_0 + a_{p-1}) b_{p-1}.
+// Contains a __syncthreads(): every thread of the CTA must call it.
+template <int P, int NA>
+__device__ __forceinline__ void toeplitz_finish(const int *const (&As)[NA], const int (&blast)[NA],
+                                                int (&acc)[NA][8]) {
     constexpr int Q = Geo<P>::q;
+    __shared__ int last_row[NA];
     const int j0 = 8 * threadIdx.x;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        const int j = j0 + t;
-        int v = acc[t];
-        if (j >= 1 && j < P) v += As[j] * blast;
-        acc[t] = (j < P) ? cmod<Q>(v) : 0;
+    for (int k = 0; k < NA; ++k)
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int j = j0 + t;
+            int v = acc[k][t];
+            if (j >= 1 && j < P) v += As[k][j] * blast[k];
+            acc[k][t] = (j < P) ? cmod<Q>(v) : 0;
+            if (j == P - 1) last_row[k] = acc[k][t];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NA; ++k)
+            acc[k][0] = cmod<Q>(acc[k][0] - last_row[k] + (As[k][0] + As[k][P - 1]) * blast[k]);
     }
 }
 
