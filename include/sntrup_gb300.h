@@ -98,6 +98,30 @@ snt_status snt_batch_keygen_host(snt_ctx *ctx, int P, uint64_t seed,
                                  uint64_t first_key_index, size_t B,
                                  uint8_t *pk_host, uint8_t *sk_host);
 
+/* Batch key generation for callers that cannot allocate device memory (the
+ * paper has no counterpart; it is a deployment variant of snt_batch_keygen).
+ * Who needs it: code running while a framework's caching allocator owns the
+ * free device memory, latency-bound paths where cudaMalloc / cudaFree would
+ * synchronise the device, and processes that may not allocate after start-up.
+ * It takes no context and allocates nothing: its scratch is a fixed 1152 KiB
+ * static device array inside this library, which every GPU that loads the
+ * library holds until the process exits.
+ *   - 1 <= B <= 256 keys per call; larger B returns SNT_EINVAL with a message.
+ *   - Writes the same bytes as snt_batch_keygen (same pk/sk layout).
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture on the device.
+ *   - Every call uses the same scratch, which keeps the previous call's data:
+ *     calls whose GPU work overlaps (different streams, threads or processes
+ *     sharing the library instance without ordering) race and corrupt each
+ *     other's keys.  Order them on one stream or synchronise in between.
+ *   - Returns after the keys are written: it waits for `stream` in order to
+ *     report device-side failures (SNT_EINTERNAL).  No host thread may call it
+ *     concurrently for the same device. */
+snt_status snt_batch_keygen_static(int device, int P, uint64_t seed,
+                                   uint64_t first_key_index, size_t B,
+                                   uint8_t *pk_dev, uint8_t *sk_dev, snt_stream stream);
+
 /* ---- Building blocks (kernel microbenchmarks; same kernels as keygen) ---- */
 
 /* c_i = a_i * b_i in R/q for i < n.  a_dev, b_dev, c_dev: n * p int16

@@ -58,6 +58,7 @@ def load():
         "snt_batch_keygen": [P, i32, u64, u64, sz, P, P, P],
         "snt_keygen_perkey": [P, i32, u64, u64, sz, P, P, P],
         "snt_batch_keygen_host": [P, i32, u64, u64, sz, P, P],
+        "snt_batch_keygen_static": [i32, i32, u64, u64, sz, P, P, P],
         "snt_rq_mul": [P, i32, sz, P, P, P, P],
         "snt_rq_inv": [P, i32, sz, P, P, P, P],
         "snt_r3_inv": [P, i32, sz, P, P, P, P],
@@ -172,6 +173,17 @@ def snt_keygen_perkey(ctx, P, seed, first_key_index, B, pk, sk, stream=None):
     _check(load().snt_keygen_perkey(ctx.handle, P, seed, first_key_index, B,
                                     _dptr(pk, torch.uint8), _dptr(sk, torch.uint8),
                                     _stream(stream)))
+
+
+def snt_batch_keygen_static(device, P, seed, first_key_index, B, pk, sk, stream=None):
+    """Keygen without any device allocation (fixed static scratch, B <= 256).
+
+    For callers that cannot allocate device memory; returns when the keys are
+    written.  See include/sntrup_gb300.h for the sharing rules."""
+    import torch
+    _check(load().snt_batch_keygen_static(device, P, seed, first_key_index, B,
+                                          _dptr(pk, torch.uint8), _dptr(sk, torch.uint8),
+                                          _stream(stream)))
 
 
 def snt_batch_keygen_host(ctx, P, seed, first_key_index, B, pk_host=None, sk_host=None):

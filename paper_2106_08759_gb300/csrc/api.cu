@@ -17,16 +17,17 @@
 #include <vector>
 
 #include "common.cuh"
+#include "host_plan.h"
 #include "kernels.h"
 #include "sntrup_gb300.h"
 
 using namespace snt;
 
 namespace {
-
 thread_local std::string g_last_error = "no error";
+}  // namespace
 
-snt_status fail(snt_status s, const char *fmt, ...) {
+snt_status snt::set_error(snt_status s, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -36,8 +37,10 @@ snt_status fail(snt_status s, const char *fmt, ...) {
     return s;
 }
 
+namespace {
+
 snt_status cuda_fail(cudaError_t e, const char *what) {
-    return fail(SNT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return set_error(SNT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
 #define SNT_CUDA(call)                                         \
@@ -46,117 +49,6 @@ snt_status cuda_fail(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
     } while (0)
 
-// Rq_encode schedule (see encode.cu) for p entries of radix m.
-bool build_sched(int p, uint32_t m0, EncSched &S) {
-    std::memset(&S, 0, sizeof(S));
-    int n = p, off = 0;
-    uint64_t mu = m0, ml = m0;
-    while (n > 1) {
-        if (S.nlev >= 16) return false;
-        EncLevel &L = S.lev[S.nlev++];
-        L.n = n;
-        L.mu = (uint32_t)mu;
-        L.mlast = (uint32_t)ml;
-        L.boff = off;
-        uint64_t m = mu * mu;
-        int eu = 0;
-        while (m >= 16384) { ++eu; m = (m + 255) >> 8; }
-        const uint64_t mu2 = m;
-        uint64_t ml2 = ml;
-        int el = eu;
-        const int npairs = n / 2;
-        if (n % 2 == 0) {
-            uint64_t m2 = mu * ml;
-            el = 0;
-            while (m2 >= 16384) { ++el; m2 = (m2 + 255) >> 8; }
-            ml2 = m2;
-            off += (npairs - 1) * eu + el;
-        } else {
-            off += npairs * eu;
-        }
-        L.eu = eu;
-        L.elast = el;
-        n = (n + 1) / 2;
-        mu = mu2;
-        ml = ml2;
-    }
-    int e = 0;
-    for (uint64_t m = ml; m > 1; m = (m + 255) >> 8) ++e;
-    S.efinal = e;
-    S.foff = off;
-    S.total = off + e;
-    return true;
-}
-
-struct ParamInfo {
-    int P, p, q, w, pad;
-    int small_bytes, pk_bytes, sk_bytes, ct_bytes;
-    EncSched sched;
-};
-
-bool param_info(int P, ParamInfo &pi) {
-    int p, q, w, pad;
-    switch (P) {
-        case 653: p = Geo<653>::p; q = Geo<653>::q; w = Geo<653>::w; pad = Geo<653>::pad; break;
-        case 761: p = Geo<761>::p; q = Geo<761>::q; w = Geo<761>::w; pad = Geo<761>::pad; break;
-        case 857: p = Geo<857>::p; q = Geo<857>::q; w = Geo<857>::w; pad = Geo<857>::pad; break;
-        default: return false;
-    }
-    pi.P = P; pi.p = p; pi.q = q; pi.w = w; pi.pad = pad;
-    pi.small_bytes = (p + 3) / 4;
-    if (!build_sched(p, (uint32_t)q, pi.sched)) return false;
-    pi.pk_bytes = pi.sched.total;
-    // sk = Small_encode(f) | Small_encode(1/g) | pk | rho | Hash_prefix(4, pk)
-    pi.sk_bytes = 3 * pi.small_bytes + pi.pk_bytes + 32;
-    // ct = Rounded encoding (radix (q+2)/3) | 32-byte confirmation hash
-    EncSched rs;
-    if (!build_sched(p, (uint32_t)((q + 2) / 3), rs)) return false;
-    pi.ct_bytes = rs.total + 32;
-    return true;
-}
-
-// Product-tree levels over B leaves: level 0 = leaves, level l has
-// ceil(n_(l-1) / 2) nodes, the last level has one.  Offsets in nodes.
-struct Tree {
-    std::vector<int> n, off;
-    size_t total = 0;
-};
-
-Tree make_tree(size_t B) {
-    Tree t;
-    size_t n = B, off = 0;
-    for (;;) {
-        t.n.push_back((int)n);
-        t.off.push_back((int)off);
-        off += n;
-        if (n == 1) break;
-        n = (n + 1) / 2;
-    }
-    t.total = off;
-    return t;
-}
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// Scratch bytes for one keygen call: every tree node (int16, stride pad) and
-// g (int8, stride pad) for each key; host_out adds device staging for pk/sk.
-size_t keygen_scratch(const ParamInfo &pi, size_t B, bool host_out) {
-    const Tree t = make_tree(B);
-    size_t bytes = align256(t.total * pi.pad * sizeof(int16_t)) + align256(B * pi.pad);
-    if (host_out) bytes += align256(B * pi.pk_bytes) + align256(B * pi.sk_bytes);
-    return bytes;
-}
-
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 constexpr int kMaxInject = 64;
 // Phase events of one keygen call (snt_ctx_set_timing): on the main stream
@@ -244,17 +136,17 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
 snt_status keygen_common(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, size_t B,
                          uint8_t *pk, uint8_t *sk, snt_stream stream, bool batched,
                          bool host_out) {
-    if (!ctx) return fail(SNT_EINVAL, "null context");
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
     ParamInfo pi;
-    if (!param_info(P, pi)) return fail(SNT_EINVAL, "unknown parameter set %d", P);
-    if (B == 0 || B > kMaxB) return fail(SNT_EINVAL, "batch size %zu outside [1, %zu]", B, kMaxB);
-    if (!pk || !sk) return fail(SNT_EINVAL, "null output buffer");
+    if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
+    if (B == 0 || B > kMaxB) return set_error(SNT_EINVAL, "batch size %zu outside [1, %zu]", B, kMaxB);
+    if (!pk || !sk) return set_error(SNT_EINVAL, "null output buffer");
     const size_t need = keygen_scratch(pi, B, host_out);
     if (need > ctx->budget)
-        return fail(SNT_ENOMEM, "batch of %zu keys needs %zu scratch bytes, budget %zu", B, need,
+        return set_error(SNT_ENOMEM, "batch of %zu keys needs %zu scratch bytes, budget %zu", B, need,
                     ctx->budget);
     DeviceGuard dg(ctx->device);
-    if (!dg.ok) return fail(SNT_ECUDA, "cannot select device %d", ctx->device);
+    if (!dg.ok) return set_error(SNT_ECUDA, "cannot select device %d", ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint8_t *dpk = pk, *dsk = sk;
     if (host_out) {
@@ -282,7 +174,7 @@ extern "C" {
 snt_status snt_param_sizes(int P, size_t *pk_bytes, size_t *sk_bytes, size_t *ct_bytes,
                            size_t *ss_bytes) {
     ParamInfo pi;
-    if (!param_info(P, pi)) return fail(SNT_EINVAL, "unknown parameter set %d", P);
+    if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     if (pk_bytes) *pk_bytes = (size_t)pi.pk_bytes;
     if (sk_bytes) *sk_bytes = (size_t)pi.sk_bytes;
     if (ct_bytes) *ct_bytes = (size_t)pi.ct_bytes;
@@ -291,14 +183,14 @@ snt_status snt_param_sizes(int P, size_t *pk_bytes, size_t *sk_bytes, size_t *ct
 }
 
 snt_status snt_ctx_create(int device, size_t mem_budget, snt_ctx **out) {
-    if (!out) return fail(SNT_EINVAL, "null output pointer");
+    if (!out) return set_error(SNT_EINVAL, "null output pointer");
     *out = nullptr;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
-        return fail(SNT_ECUDA, "no CUDA device available");
-    if (device < 0 || device >= ndev) return fail(SNT_EINVAL, "device %d out of range", device);
+        return set_error(SNT_ECUDA, "no CUDA device available");
+    if (device < 0 || device >= ndev) return set_error(SNT_EINVAL, "device %d out of range", device);
     DeviceGuard dg(device);
-    if (!dg.ok) return fail(SNT_ECUDA, "cannot select device %d", device);
+    if (!dg.ok) return set_error(SNT_ECUDA, "cannot select device %d", device);
     snt_ctx *c = new snt_ctx();
     c->device = device;
     c->budget = mem_budget ? mem_budget : ((size_t)256 << 20);
@@ -342,9 +234,9 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
 }
 
 snt_status snt_ctx_max_batch(snt_ctx *ctx, int P, size_t *max_B) {
-    if (!ctx || !max_B) return fail(SNT_EINVAL, "null argument");
+    if (!ctx || !max_B) return set_error(SNT_EINVAL, "null argument");
     ParamInfo pi;
-    if (!param_info(P, pi)) return fail(SNT_EINVAL, "unknown parameter set %d", P);
+    if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     size_t lo = 0, hi = kMaxB;
     while (lo < hi) {
         const size_t mid = (lo + hi + 1) / 2;
@@ -355,7 +247,7 @@ snt_status snt_ctx_max_batch(snt_ctx *ctx, int P, size_t *max_B) {
 }
 
 snt_status snt_ctx_sync(snt_ctx *ctx, snt_stream stream) {
-    if (!ctx) return fail(SNT_EINVAL, "null context");
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
     DeviceGuard dg(ctx->device);
     SNT_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
     SNT_CUDA(cudaStreamSynchronize(ctx->aux));
@@ -363,10 +255,10 @@ snt_status snt_ctx_sync(snt_ctx *ctx, snt_stream stream) {
     SNT_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         SNT_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
-        if (err & ERR_TIMEOUT) return fail(SNT_ETIMEOUT, "a bounded device wait gave up (0x%x)", err);
+        if (err & ERR_TIMEOUT) return set_error(SNT_ETIMEOUT, "a bounded device wait gave up (0x%x)", err);
         if (err & ERR_RESAMPLE)
-            return fail(SNT_EINTERNAL, "a key found no invertible g in %d attempts", kMaxGAttempts);
-        return fail(SNT_EINTERNAL, "device self-check failed (0x%x)", err);
+            return set_error(SNT_EINTERNAL, "a key found no invertible g in %d attempts", kMaxGAttempts);
+        return set_error(SNT_EINTERNAL, "device self-check failed (0x%x)", err);
     }
     return SNT_OK;
 }
@@ -388,61 +280,61 @@ snt_status snt_batch_keygen_host(snt_ctx *ctx, int P, uint64_t seed, uint64_t fi
 
 snt_status snt_rq_mul(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev, const int16_t *b_dev,
                       int16_t *c_dev, snt_stream stream) {
-    if (!ctx) return fail(SNT_EINVAL, "null context");
-    if (n == 0 || n > (size_t)INT32_MAX) return fail(SNT_EINVAL, "count %zu out of range", n);
-    if (!a_dev || !b_dev || !c_dev) return fail(SNT_EINVAL, "null buffer");
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
+    if (n == 0 || n > (size_t)INT32_MAX) return set_error(SNT_EINVAL, "count %zu out of range", n);
+    if (!a_dev || !b_dev || !c_dev) return set_error(SNT_EINVAL, "null buffer");
     DeviceGuard dg(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     switch (P) {
         case 653: SNT_CUDA(launch_mul_batch<653>((int)n, a_dev, b_dev, c_dev, st)); break;
         case 761: SNT_CUDA(launch_mul_batch<761>((int)n, a_dev, b_dev, c_dev, st)); break;
         case 857: SNT_CUDA(launch_mul_batch<857>((int)n, a_dev, b_dev, c_dev, st)); break;
-        default: return fail(SNT_EINVAL, "unknown parameter set %d", P);
+        default: return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     }
     return SNT_OK;
 }
 
 snt_status snt_rq_inv(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev, int16_t *out_dev,
                       int32_t *ok_dev, snt_stream stream) {
-    if (!ctx) return fail(SNT_EINVAL, "null context");
-    if (n == 0 || n > (size_t)INT32_MAX) return fail(SNT_EINVAL, "count %zu out of range", n);
-    if (!a_dev || !out_dev || !ok_dev) return fail(SNT_EINVAL, "null buffer");
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
+    if (n == 0 || n > (size_t)INT32_MAX) return set_error(SNT_EINVAL, "count %zu out of range", n);
+    if (!a_dev || !out_dev || !ok_dev) return set_error(SNT_EINVAL, "null buffer");
     DeviceGuard dg(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     switch (P) {
         case 653: SNT_CUDA(launch_rq_inv<653>((int)n, a_dev, 653, out_dev, 653, ok_dev, nullptr, 0, st)); break;
         case 761: SNT_CUDA(launch_rq_inv<761>((int)n, a_dev, 761, out_dev, 761, ok_dev, nullptr, 0, st)); break;
         case 857: SNT_CUDA(launch_rq_inv<857>((int)n, a_dev, 857, out_dev, 857, ok_dev, nullptr, 0, st)); break;
-        default: return fail(SNT_EINVAL, "unknown parameter set %d", P);
+        default: return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     }
     return SNT_OK;
 }
 
 snt_status snt_r3_inv(snt_ctx *ctx, int P, size_t n, const int8_t *g_dev, int8_t *out_dev,
                       int32_t *ok_dev, snt_stream stream) {
-    if (!ctx) return fail(SNT_EINVAL, "null context");
-    if (n == 0 || n > (size_t)INT32_MAX - 3) return fail(SNT_EINVAL, "count %zu out of range", n);
-    if (!g_dev || !out_dev || !ok_dev) return fail(SNT_EINVAL, "null buffer");
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
+    if (n == 0 || n > (size_t)INT32_MAX - 3) return set_error(SNT_EINVAL, "count %zu out of range", n);
+    if (!g_dev || !out_dev || !ok_dev) return set_error(SNT_EINVAL, "null buffer");
     DeviceGuard dg(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     switch (P) {
         case 653: SNT_CUDA(launch_r3_inv<653>((int)n, g_dev, out_dev, ok_dev, st)); break;
         case 761: SNT_CUDA(launch_r3_inv<761>((int)n, g_dev, out_dev, ok_dev, st)); break;
         case 857: SNT_CUDA(launch_r3_inv<857>((int)n, g_dev, out_dev, ok_dev, st)); break;
-        default: return fail(SNT_EINVAL, "unknown parameter set %d", P);
+        default: return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     }
     return SNT_OK;
 }
 
 snt_status snt_debug_inject_g(snt_ctx *ctx, int P, size_t n, const uint64_t *key_index_host,
                               const int8_t *g_host) {
-    if (!ctx) return fail(SNT_EINVAL, "null context");
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
     ParamInfo pi;
-    if (!param_info(P, pi)) return fail(SNT_EINVAL, "unknown parameter set %d", P);
-    if (n > (size_t)kMaxInject) return fail(SNT_EINVAL, "at most %d injected draws", kMaxInject);
-    if (n && (!key_index_host || !g_host)) return fail(SNT_EINVAL, "null buffer");
+    if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
+    if (n > (size_t)kMaxInject) return set_error(SNT_EINVAL, "at most %d injected draws", kMaxInject);
+    if (n && (!key_index_host || !g_host)) return set_error(SNT_EINVAL, "null buffer");
     for (size_t i = 0; i < n * (size_t)pi.p; ++i)
-        if (g_host[i] < -1 || g_host[i] > 1) return fail(SNT_EINVAL, "g coefficient outside {-1,0,1}");
+        if (g_host[i] < -1 || g_host[i] > 1) return set_error(SNT_EINVAL, "g coefficient outside {-1,0,1}");
     DeviceGuard dg(ctx->device);
     SNT_CUDA(cudaDeviceSynchronize());
     if (n) {
@@ -455,14 +347,14 @@ snt_status snt_debug_inject_g(snt_ctx *ctx, int P, size_t n, const uint64_t *key
 }
 
 snt_status snt_ctx_set_timing(snt_ctx *ctx, int on) {
-    if (!ctx) return fail(SNT_EINVAL, "null context");
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
     ctx->timing = (on != 0);
     return SNT_OK;
 }
 
 snt_status snt_ctx_phase_times(snt_ctx *ctx, float *ms, int n) {
-    if (!ctx || !ms || n < SNT_NPHASES) return fail(SNT_EINVAL, "need room for %d phases", SNT_NPHASES);
-    if (!ctx->timing) return fail(SNT_EINVAL, "phase timing is off");
+    if (!ctx || !ms || n < SNT_NPHASES) return set_error(SNT_EINVAL, "need room for %d phases", SNT_NPHASES);
+    if (!ctx->timing) return set_error(SNT_EINVAL, "phase timing is off");
     DeviceGuard dg(ctx->device);
     cudaEvent_t *ev = ctx->ev_phase;
     SNT_CUDA(cudaEventSynchronize(ev[9]));

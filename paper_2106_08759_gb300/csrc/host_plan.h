@@ -1,0 +1,131 @@
+// host_plan.h -- host-side planning shared by the C-ABI entry points
+// (internal): parameter sizes, the Rq_encode schedule, the product-tree
+// layout, scratch sizes, device selection and the per-thread error string.
+#pragma once
+#include <cstdarg>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "sntrup_gb300.h"
+
+namespace snt {
+
+// Records a one-line error message (snt_last_error_string) and returns s.
+snt_status set_error(snt_status s, const char *fmt, ...);
+
+// Rq_encode schedule (see encode.cu) for p entries of radix m.
+inline bool build_sched(int p, uint32_t m0, EncSched &S) {
+    std::memset(&S, 0, sizeof(S));
+    int n = p, off = 0;
+    uint64_t mu = m0, ml = m0;
+    while (n > 1) {
+        if (S.nlev >= 16) return false;
+        EncLevel &L = S.lev[S.nlev++];
+        L.n = n;
+        L.mu = (uint32_t)mu;
+        L.mlast = (uint32_t)ml;
+        L.boff = off;
+        uint64_t m = mu * mu;
+        int eu = 0;
+        while (m >= 16384) { ++eu; m = (m + 255) >> 8; }
+        const uint64_t mu2 = m;
+        uint64_t ml2 = ml;
+        int el = eu;
+        const int npairs = n / 2;
+        if (n % 2 == 0) {
+            uint64_t m2 = mu * ml;
+            el = 0;
+            while (m2 >= 16384) { ++el; m2 = (m2 + 255) >> 8; }
+            ml2 = m2;
+            off += (npairs - 1) * eu + el;
+        } else {
+            off += npairs * eu;
+        }
+        L.eu = eu;
+        L.elast = el;
+        n = (n + 1) / 2;
+        mu = mu2;
+        ml = ml2;
+    }
+    int e = 0;
+    for (uint64_t m = ml; m > 1; m = (m + 255) >> 8) ++e;
+    S.efinal = e;
+    S.foff = off;
+    S.total = off + e;
+    return true;
+}
+
+struct ParamInfo {
+    int P, p, q, w, pad;
+    int small_bytes, pk_bytes, sk_bytes, ct_bytes;
+    EncSched sched;
+};
+
+inline bool param_info(int P, ParamInfo &pi) {
+    int p, q, w, pad;
+    switch (P) {
+        case 653: p = Geo<653>::p; q = Geo<653>::q; w = Geo<653>::w; pad = Geo<653>::pad; break;
+        case 761: p = Geo<761>::p; q = Geo<761>::q; w = Geo<761>::w; pad = Geo<761>::pad; break;
+        case 857: p = Geo<857>::p; q = Geo<857>::q; w = Geo<857>::w; pad = Geo<857>::pad; break;
+        default: return false;
+    }
+    pi.P = P; pi.p = p; pi.q = q; pi.w = w; pi.pad = pad;
+    pi.small_bytes = (p + 3) / 4;
+    if (!build_sched(p, (uint32_t)q, pi.sched)) return false;
+    pi.pk_bytes = pi.sched.total;
+    // sk = Small_encode(f) | Small_encode(1/g) | pk | rho | Hash_prefix(4, pk)
+    pi.sk_bytes = 3 * pi.small_bytes + pi.pk_bytes + 32;
+    // ct = Rounded encoding (radix (q+2)/3) | 32-byte confirmation hash
+    EncSched rs;
+    if (!build_sched(p, (uint32_t)((q + 2) / 3), rs)) return false;
+    pi.ct_bytes = rs.total + 32;
+    return true;
+}
+
+// Product-tree levels over B leaves: level 0 = leaves, level l has
+// ceil(n_(l-1) / 2) nodes, the last level has one.  Offsets in nodes.
+struct Tree {
+    std::vector<int> n, off;
+    size_t total = 0;
+};
+
+inline Tree make_tree(size_t B) {
+    Tree t;
+    size_t n = B, off = 0;
+    for (;;) {
+        t.n.push_back((int)n);
+        t.off.push_back((int)off);
+        off += n;
+        if (n == 1) break;
+        n = (n + 1) / 2;
+    }
+    t.total = off;
+    return t;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch bytes for one keygen call: every tree node (int16, stride pad) and
+// g (int8, stride pad) for each key; host_out adds device staging for pk/sk.
+inline size_t keygen_scratch(const ParamInfo &pi, size_t B, bool host_out) {
+    const Tree t = make_tree(B);
+    size_t bytes = align256(t.total * pi.pad * sizeof(int16_t)) + align256(B * pi.pad);
+    if (host_out) bytes += align256(B * pi.pk_bytes) + align256(B * pi.sk_bytes);
+    return bytes;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace snt
