@@ -136,6 +136,14 @@ snt_status snt_rq_mul(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev,
 snt_status snt_rq_inv(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev,
                       int16_t *out_dev, int32_t *ok_dev, snt_stream stream);
 
+/* Same result as snt_rq_inv, latency-optimised (the form used for the single
+ * root inversion of the batch tree): jump divsteps, i.e. chunks of 31 steps
+ * run by one warp on the low coefficients, whose 2x2 transition matrix the
+ * whole CTA then applies (Bernstein-Yang's recursive divsteps, the paper's
+ * "jump-div-step" of Table 4's note).  One CTA of 512 threads per element. */
+snt_status snt_rq_inv_latency(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev,
+                              int16_t *out_dev, int32_t *ok_dev, snt_stream stream);
+
 /* out_i = 1/g_i in R/3 by bit-sliced divsteps, one warp per element.
  * g_dev, out_dev: n * p int8 in {-1,0,1}; ok_dev: n int32, 1 if g_i is
  * invertible in R/3, else 0 and out_i = 0. */

@@ -61,6 +61,7 @@ def load():
         "snt_batch_keygen_static": [i32, i32, u64, u64, sz, P, P, P],
         "snt_rq_mul": [P, i32, sz, P, P, P, P],
         "snt_rq_inv": [P, i32, sz, P, P, P, P],
+        "snt_rq_inv_latency": [P, i32, sz, P, P, P, P],
         "snt_r3_inv": [P, i32, sz, P, P, P, P],
         "snt_debug_inject_g": [P, i32, sz, P, P],
         "snt_ctx_set_timing": [P, i32],
@@ -211,6 +212,13 @@ def snt_rq_inv(ctx, P, n, a, out, ok, stream=None):
     import torch
     _check(load().snt_rq_inv(ctx.handle, P, n, _dptr(a, torch.int16), _dptr(out, torch.int16),
                              _dptr(ok, torch.int32), _stream(stream)))
+
+
+def snt_rq_inv_latency(ctx, P, n, a, out, ok, stream=None):
+    import torch
+    _check(load().snt_rq_inv_latency(ctx.handle, P, n, _dptr(a, torch.int16),
+                                     _dptr(out, torch.int16), _dptr(ok, torch.int32),
+                                     _stream(stream)))
 
 
 def snt_r3_inv(ctx, P, n, g, out, ok, stream=None):

@@ -70,8 +70,9 @@ struct snt_ctx {
     int8_t *d_inj_g = nullptr;
     int n_inj = 0;
     int inj_P = 0;
-    cudaStream_t aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t aux = nullptr;   // low priority: per-key R/3 inversions
+    cudaStream_t tree = nullptr;  // high priority: sampling, product tree, h, hash
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr;
     bool timing = false;
     cudaEvent_t ev_phase[kPhaseEvents] = {};
 };
@@ -89,12 +90,18 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     const int sb = pi.small_bytes;
     cudaEvent_t *ev = ctx->ev_phase;
     const bool tm = ctx->timing;
+    // fork from the caller's stream: the tree branch runs on the context's
+    // high-priority stream, the per-key R/3 inversions on its low-priority
+    // stream, so R/3 blocks fill the SMs the narrow tree levels and the root
+    // inversion leave idle instead of delaying the tree.
+    const cudaStream_t caller = st;
+    SNT_CUDA(cudaEventRecord(ctx->ev_fork, caller));
+    SNT_CUDA(cudaStreamWaitEvent(ctx->tree, ctx->ev_fork, 0));
+    SNT_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    st = ctx->tree;
     if (tm) SNT_CUDA(cudaEventRecord(ev[0], st));
     SNT_CUDA(launch_sample_f<P>(seed, first, Bi, leaves, sk, pi.sk_bytes, 2 * sb + pi.pk_bytes, st));
-    // fork: per-key R/3 inversions on the auxiliary stream
     if (tm) SNT_CUDA(cudaEventRecord(ev[1], st));
-    SNT_CUDA(cudaEventRecord(ctx->ev_fork, st));
-    SNT_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
     const int n_inj = (ctx->inj_P == P) ? ctx->n_inj : 0;
     if (tm) SNT_CUDA(cudaEventRecord(ev[2], ctx->aux));
     SNT_CUDA(launch_r3_keygen<P>(seed, first, Bi, gbuf, sk, pi.sk_bytes, sb, ctx->d_inj_idx,
@@ -108,7 +115,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                                        nodes + (size_t)t.off[l] * pi.pad, st));
         if (tm) SNT_CUDA(cudaEventRecord(ev[4], st));
         int16_t *root = nodes + (size_t)t.off[L] * pi.pad;
-        SNT_CUDA(launch_rq_inv<P>(1, root, pi.pad, root, pi.pad, nullptr, ctx->d_err, ERR_ROOT, st));
+        SNT_CUDA(launch_rq_inv_jump<P>(1, root, pi.pad, root, pi.pad, nullptr, ctx->d_err, ERR_ROOT,
+                                       st));
         if (tm) SNT_CUDA(cudaEventRecord(ev[5], st));
         for (int l = L; l >= 1; --l)
             SNT_CUDA(launch_tree_down<P>(nodes + (size_t)t.off[l] * pi.pad,
@@ -130,6 +138,9 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     if (tm) SNT_CUDA(cudaEventRecord(ev[8], st));
     SNT_CUDA(launch_sha512_pk(Bi, pk, pi.pk_bytes, sk, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[9], st));
+    // join back into the caller's stream
+    SNT_CUDA(cudaEventRecord(ctx->ev_done, st));
+    SNT_CUDA(cudaStreamWaitEvent(caller, ctx->ev_done, 0));
     return SNT_OK;
 }
 
@@ -199,7 +210,11 @@ snt_status snt_ctx_create(int device, size_t mem_budget, snt_ctx **out) {
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_inj_idx, kMaxInject * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_inj_g, kMaxInject * 1024);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    int prio_low = 0, prio_high = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_low);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->tree, cudaStreamNonBlocking, prio_high);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     for (int i = 0; i < kPhaseEvents && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev_phase[i]);
@@ -215,6 +230,7 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     if (!ctx) return SNT_OK;
     DeviceGuard dg(ctx->device);
     if (ctx->aux) cudaStreamSynchronize(ctx->aux);
+    if (ctx->tree) cudaStreamSynchronize(ctx->tree);
     cudaDeviceSynchronize();
     if (ctx->arena) {
         cudaMemset(ctx->arena, 0, ctx->budget);  // secret-bearing scratch
@@ -227,6 +243,8 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     for (int i = 0; i < kPhaseEvents; ++i)
         if (ctx->ev_phase[i]) cudaEventDestroy(ctx->ev_phase[i]);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
+    if (ctx->tree) cudaStreamDestroy(ctx->tree);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     delete ctx;
@@ -251,6 +269,7 @@ snt_status snt_ctx_sync(snt_ctx *ctx, snt_stream stream) {
     DeviceGuard dg(ctx->device);
     SNT_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
     SNT_CUDA(cudaStreamSynchronize(ctx->aux));
+    SNT_CUDA(cudaStreamSynchronize(ctx->tree));
     int err = 0;
     SNT_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
@@ -305,6 +324,22 @@ snt_status snt_rq_inv(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev, int16
         case 653: SNT_CUDA(launch_rq_inv<653>((int)n, a_dev, 653, out_dev, 653, ok_dev, nullptr, 0, st)); break;
         case 761: SNT_CUDA(launch_rq_inv<761>((int)n, a_dev, 761, out_dev, 761, ok_dev, nullptr, 0, st)); break;
         case 857: SNT_CUDA(launch_rq_inv<857>((int)n, a_dev, 857, out_dev, 857, ok_dev, nullptr, 0, st)); break;
+        default: return set_error(SNT_EINVAL, "unknown parameter set %d", P);
+    }
+    return SNT_OK;
+}
+
+snt_status snt_rq_inv_latency(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev,
+                              int16_t *out_dev, int32_t *ok_dev, snt_stream stream) {
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
+    if (n == 0 || n > (size_t)INT32_MAX) return set_error(SNT_EINVAL, "count %zu out of range", n);
+    if (!a_dev || !out_dev || !ok_dev) return set_error(SNT_EINVAL, "null buffer");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (P) {
+        case 653: SNT_CUDA(launch_rq_inv_jump<653>((int)n, a_dev, 653, out_dev, 653, ok_dev, nullptr, 0, st)); break;
+        case 761: SNT_CUDA(launch_rq_inv_jump<761>((int)n, a_dev, 761, out_dev, 761, ok_dev, nullptr, 0, st)); break;
+        case 857: SNT_CUDA(launch_rq_inv_jump<857>((int)n, a_dev, 857, out_dev, 857, ok_dev, nullptr, 0, st)); break;
         default: return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     }
     return SNT_OK;

@@ -103,24 +103,31 @@ __constant__ uint64_t c_sha512_k[80] = {
 
 __device__ __forceinline__ uint64_t rotr(uint64_t x, int n) { return (x >> n) | (x << (64 - n)); }
 
-// byte `pos` of the padded message 0x04 | pk | 0x80 | 0... | bitlen (128-bit BE)
-__device__ __forceinline__ uint32_t msg_byte(const uint8_t *pk, int pkb, int nblk, int pos) {
-    const int len = pkb + 1;
-    if (pos == 0) return 4u;
-    if (pos < len) return pk[pos - 1];
-    if (pos == len) return 0x80u;
-    const int tail = nblk * 128 - pos;  // 1 .. 16 for the length field
-    if (tail <= 8) return (uint32_t)(((uint64_t)len * 8u) >> (8 * (tail - 1))) & 255u;
-    return 0u;
-}
-
-__global__ void __launch_bounds__(128)
+// One warp hashes 32 keys, one key per lane.  The 32 messages 0x04 | pk are
+// staged in shared memory by coalesced copies, each row `stride` bytes with
+// stride / 4 odd so that the 32 lanes' reads of the same offset fall in
+// distinct banks.  Message words are read as aligned 32-bit pairs; the
+// padding (0x80, zeros, 128-bit big-endian bit length) is generated.
+__global__ void __launch_bounds__(32)
 k_sha512_pk(int B, const uint8_t *__restrict__ pk, int pk_bytes, uint8_t *__restrict__ sk,
-            int sk_bytes, int hash_off) {
-    const int key = blockIdx.x * blockDim.x + threadIdx.x;
-    if (key >= B) return;
-    const uint8_t *m = pk + (size_t)key * pk_bytes;
-    const int nblk = (pk_bytes + 1 + 1 + 16 + 127) / 128;
+            int sk_bytes, int hash_off, int stride) {
+    extern __shared__ __align__(16) uint8_t msg[];
+    const int lane = threadIdx.x;
+    const int base = blockIdx.x * 32;
+    const int nkeys = min(32, B - base);
+    const int len = pk_bytes + 1;
+    for (int j = 0; j < nkeys; ++j) {
+        const uint8_t *src = pk + (size_t)(base + j) * pk_bytes;
+        uint8_t *dst = msg + j * stride;
+        if (lane == 0) dst[0] = 4;
+        for (int b = lane; b < pk_bytes; b += 32) dst[1 + b] = src[b];
+        for (int b = len + lane; b < stride; b += 32) dst[b] = 0;
+    }
+    __syncwarp();
+    if (lane >= nkeys) return;
+    const uint8_t *m = msg + lane * stride;
+    const int nblk = (len + 1 + 16 + 127) / 128;
+    const uint64_t bitlen = (uint64_t)len * 8u;
     uint64_t H[8] = {0x6a09e667f3bcc908ULL, 0xbb67ae8584caa73bULL, 0x3c6ef372fe94f82bULL,
                      0xa54ff53a5f1d36f1ULL, 0x510e527fade682d1ULL, 0x9b05688c2b3e6c1fULL,
                      0x1f83d9abfb41bd6bULL, 0x5be0cd19137e2179ULL};
@@ -128,27 +135,38 @@ k_sha512_pk(int B, const uint8_t *__restrict__ pk, int pk_bytes, uint8_t *__rest
         uint64_t W[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
-            uint64_t v = 0;
+            const int pos = 128 * blk + 8 * t;
+            uint64_t v;
+            if (pos + 8 <= len) {
+                const uint32_t hi = *reinterpret_cast<const uint32_t *>(m + pos);
+                const uint32_t lo = *reinterpret_cast<const uint32_t *>(m + pos + 4);
+                v = ((uint64_t)__byte_perm(hi, 0, 0x0123) << 32) | __byte_perm(lo, 0, 0x0123);
+            } else {
+                v = 0;
 #pragma unroll
-            for (int b = 0; b < 8; ++b) v = (v << 8) | msg_byte(m, pk_bytes, nblk, 128 * blk + 8 * t + b);
+                for (int b = 0; b < 8; ++b) {
+                    const int q = pos + b;
+                    uint32_t byte = 0;
+                    if (q < len) byte = m[q];
+                    else if (q == len) byte = 0x80u;
+                    else if (q >= nblk * 128 - 8) byte = (uint32_t)(bitlen >> (8 * (nblk * 128 - 1 - q))) & 255u;
+                    v = (v << 8) | byte;
+                }
+            }
             W[t] = v;
         }
         uint64_t a = H[0], b = H[1], c = H[2], d = H[3], e = H[4], f = H[5], g = H[6], h = H[7];
-#pragma unroll 16
+#pragma unroll
         for (int t = 0; t < 80; ++t) {
-            uint64_t w;
-            if (t < 16) {
-                w = W[t & 15];
-            } else {
+            if (t >= 16) {
                 const uint64_t w15 = W[(t - 15) & 15], w2 = W[(t - 2) & 15];
                 const uint64_t s0 = rotr(w15, 1) ^ rotr(w15, 8) ^ (w15 >> 7);
                 const uint64_t s1 = rotr(w2, 19) ^ rotr(w2, 61) ^ (w2 >> 6);
-                w = W[t & 15] + s0 + W[(t - 7) & 15] + s1;
-                W[t & 15] = w;
+                W[t & 15] += s0 + W[(t - 7) & 15] + s1;
             }
             const uint64_t S1 = rotr(e, 14) ^ rotr(e, 18) ^ rotr(e, 41);
             const uint64_t ch = (e & f) ^ (~e & g);
-            const uint64_t T1 = h + S1 + ch + c_sha512_k[t] + w;
+            const uint64_t T1 = h + S1 + ch + c_sha512_k[t] + W[t & 15];
             const uint64_t S0 = rotr(a, 28) ^ rotr(a, 34) ^ rotr(a, 39);
             const uint64_t mj = (a & b) ^ (a & c) ^ (b & c);
             h = g; g = f; f = e; e = d + T1;
@@ -157,7 +175,7 @@ k_sha512_pk(int B, const uint8_t *__restrict__ pk, int pk_bytes, uint8_t *__rest
         H[0] += a; H[1] += b; H[2] += c; H[3] += d;
         H[4] += e; H[5] += f; H[6] += g; H[7] += h;
     }
-    uint8_t *out = sk + (size_t)key * sk_bytes + hash_off;
+    uint8_t *out = sk + (size_t)(base + lane) * sk_bytes + hash_off;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -174,7 +192,10 @@ cudaError_t launch_finalize(int B, const int8_t *gbuf, const int16_t *ainv, uint
 
 cudaError_t launch_sha512_pk(int B, const uint8_t *pk, int pk_bytes, uint8_t *sk, int sk_bytes,
                              int hash_off, cudaStream_t st) {
-    k_sha512_pk<<<(B + 127) / 128, 128, 0, st>>>(B, pk, pk_bytes, sk, sk_bytes, hash_off);
+    int stride = (pk_bytes + 1 + 3) / 4 * 4;
+    if (((stride / 4) & 1) == 0) stride += 4;
+    k_sha512_pk<<<(B + 31) / 32, 32, 32 * stride, st>>>(B, pk, pk_bytes, sk, sk_bytes, hash_off,
+                                                          stride);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,10 @@ template <int P>
 cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out,
                           long out_stride, int32_t *ok, int *err, int err_bit, cudaStream_t st);
 template <int P>
+cudaError_t launch_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
+                               long out_stride, int32_t *ok, int *err, int err_bit,
+                               cudaStream_t st);
+template <int P>
 cudaError_t launch_finalize(int B, const int8_t *gbuf, const int16_t *ainv, uint8_t *pk,
                             int pk_bytes, uint8_t *sk, int sk_bytes, int sk_pk_off,
                             const EncSched &S, cudaStream_t st);

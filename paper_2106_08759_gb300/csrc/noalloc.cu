@@ -73,7 +73,7 @@ snt_status run_static(const snt::ParamInfo &pi, uint64_t seed, uint64_t first, s
         SNT_CUDA_S(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1],
                                      nodes + (size_t)t.off[l] * pi.pad, st));
     int16_t *root = nodes + (size_t)t.off[L] * pi.pad;
-    SNT_CUDA_S(launch_rq_inv<P>(1, root, pi.pad, root, pi.pad, nullptr, err, ERR_ROOT, st));
+    SNT_CUDA_S(launch_rq_inv_jump<P>(1, root, pi.pad, root, pi.pad, nullptr, err, ERR_ROOT, st));
     for (int l = L; l >= 1; --l)
         SNT_CUDA_S(launch_tree_down<P>(nodes + (size_t)t.off[l] * pi.pad,
                                        nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1], st));

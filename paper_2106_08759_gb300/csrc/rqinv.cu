@@ -117,6 +117,136 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Jump divsteps (latency-optimised form for the single root inversion).
+//
+// The first m divsteps of (delta, F, G) depend only on delta and the low m
+// coefficients of F and G.  So warp 0 runs a chunk of m <= 31 steps on those
+// coefficients alone (one coefficient per lane, shuffles for the shifts and
+// for F(0), G(0)) and accumulates the chunk's transition matrix
+//     x^m (F', G') = A (F, G),   A = [[u, v], [w, z]],  deg <= m,
+// built step by step as  row1 <- x * row1,  row2 <- F(0) row2 - G(0) row1
+// (rows exchanged first when the step swaps).  The whole CTA then applies A:
+//     F' = (u F + v G) / x^m,   G' = (w F + z G) / x^m,
+//     V' = u V + (v / x) R,     R' = x w V + z R,
+// the last two because V is multiplied by x before each step's swap, which
+// conjugates A by diag(1, x).  2p - 1 steps take ceil((2p-1)/31) chunks and
+// as many barriers, instead of one barrier per step.  All values are kept
+// centred, so a 64-term application sum stays below 2^31.
+// ---------------------------------------------------------------------------
+template <int P> struct JumpGeo {
+    static constexpr int M = 31;              // steps per chunk
+    static constexpr int OFF = 32;            // zero margin below index 0
+    static constexpr int LEN = OFF + P + 1 + 32;
+};
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT)
+k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_stride,
+              int32_t *__restrict__ okv, int *__restrict__ err, int err_bit) {
+    constexpr int Q = Geo<P>::q;
+    constexpr int LEN = JumpGeo<P>::LEN, OFF = JumpGeo<P>::OFF;
+    __shared__ int st[2][4][LEN];  // [buffer][F, G, V, R][index + OFF]
+    __shared__ int mat[4][33];     // u, v, w, z (coefficient 32 stays zero)
+    __shared__ int s_ok;
+    const int e = blockIdx.x;
+    if (e >= n) return;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int16_t *a = in + (size_t)e * in_stride;
+    for (int i = tid; i < 2 * 4 * LEN; i += NT) (&st[0][0][0])[i] = 0;
+    if (tid < 4) mat[tid][32] = 0;
+    __syncthreads();
+    for (int i = tid; i < P; i += NT) st[0][1][OFF + i] = (int)a[P - 1 - i];
+    if (tid == 0) {
+        st[0][0][OFF] = 1;
+        st[0][0][OFF + P - 1] = -1;
+        st[0][0][OFF + P] = -1;
+        st[0][3][OFF] = 1;
+    }
+    __syncthreads();
+    int delta = 1;  // used by warp 0 only
+    int cur = 0;
+    for (int done = 0; done < 2 * P - 1; done += JumpGeo<P>::M) {
+        const int m = min(JumpGeo<P>::M, 2 * P - 1 - done);
+        if (tid < 32) {
+            int fl = st[cur][0][OFF + lane], gl = st[cur][1][OFF + lane];
+            int u = (lane == 0), v = 0, w = 0, z = (lane == 0);
+            for (int s = 0; s < m; ++s) {
+                int f0 = __shfl_sync(0xffffffffu, fl, 0);
+                int g0 = __shfl_sync(0xffffffffu, gl, 0);
+                if (delta > 0 && g0 != 0) {  // warp-uniform
+                    int t = fl; fl = gl; gl = t;
+                    t = u; u = w; w = t;
+                    t = v; v = z; z = t;
+                    t = f0; f0 = g0; g0 = t;
+                    delta = -delta;
+                }
+                ++delta;
+                const int nw = cmod<Q>(f0 * w - g0 * u);
+                const int nz = cmod<Q>(f0 * z - g0 * v);
+                u = __shfl_up_sync(0xffffffffu, u, 1);
+                v = __shfl_up_sync(0xffffffffu, v, 1);
+                if (lane == 0) { u = 0; v = 0; }
+                w = nw;
+                z = nz;
+                const int ng = cmod<Q>(f0 * gl - g0 * fl);
+                gl = __shfl_down_sync(0xffffffffu, ng, 1);
+                if (lane == 31) gl = 0;
+            }
+            mat[0][lane] = u;
+            mat[1][lane] = v;
+            mat[2][lane] = w;
+            mat[3][lane] = z;
+        }
+        __syncthreads();
+        const int *F = st[cur][0], *G = st[cur][1], *V = st[cur][2], *R = st[cur][3];
+        int *F2 = st[cur ^ 1][0], *G2 = st[cur ^ 1][1], *V2 = st[cur ^ 1][2], *R2 = st[cur ^ 1][3];
+        for (int i = tid; i <= P; i += NT) {
+            int af = 0, ag = 0, av = 0, ar = 0;
+            const int hi = OFF + i + m, lo = OFF + i;
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                const int uk = mat[0][k], vk = mat[1][k], wk = mat[2][k], zk = mat[3][k];
+                const int fv = F[hi - k], gv = G[hi - k];
+                af += uk * fv + vk * gv;
+                ag += wk * fv + zk * gv;
+                const int vv = V[lo - k], rv = R[lo - k];
+                const int vk1 = mat[1][k + 1], wkm = (k > 0) ? mat[2][k - 1] : 0;
+                av += uk * vv + vk1 * rv;
+                ar += wkm * vv + zk * rv;
+            }
+            F2[OFF + i] = cmod<Q>(af);
+            G2[OFF + i] = cmod<Q>(ag);
+            V2[OFF + i] = cmod<Q>(av);
+            R2[OFF + i] = cmod<Q>(ar);
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    if (tid == 0) s_ok = (delta == 0);
+    __syncthreads();
+    const bool ok = s_ok != 0;
+    const int f0 = freeze_lazy<Q>(st[cur][0][OFF]);
+    const int sc = ok ? inv_mod<Q>(f0) : 0;
+    int16_t *o = out + (size_t)e * out_stride;
+    for (int i = tid; i < P; i += NT) {
+        const int v = freeze_lazy<Q>(st[cur][2][OFF + P - 1 - i]);
+        o[i] = (int16_t)cmod<Q>(sc * v);
+    }
+    if (tid == 0) {
+        if (okv) okv[e] = ok ? 1 : 0;
+        if (!ok && err) atomicOr(err, err_bit);
+    }
+}
+
+template <int P>
+cudaError_t launch_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
+                               long out_stride, int32_t *ok, int *err, int err_bit,
+                               cudaStream_t st) {
+    k_rq_inv_jump<P, 512><<<n, 512, 0, st>>>(n, in, in_stride, out, out_stride, ok, err, err_bit);
+    return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out,
                           long out_stride, int32_t *ok, int *err, int err_bit, cudaStream_t st) {
@@ -127,7 +257,9 @@ cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out
 
 #define SNT_INV_INST(P)                                                                    \
     template cudaError_t launch_rq_inv<P>(int, const int16_t *, long, int16_t *, long,     \
-                                          int32_t *, int *, int, cudaStream_t);
+                                          int32_t *, int *, int, cudaStream_t);            \
+    template cudaError_t launch_rq_inv_jump<P>(int, const int16_t *, long, int16_t *, long, \
+                                               int32_t *, int *, int, cudaStream_t);
 SNT_INV_INST(653)
 SNT_INV_INST(761)
 SNT_INV_INST(857)

@@ -56,8 +56,9 @@ def test_rq_mul_matches_oracle(snt, ctx, P):
         assert np.array_equal(got[i], oracle.ring_mul(p, q, a[i], b[i])), i
 
 
+@pytest.mark.parametrize("latency", [False, True])
 @pytest.mark.parametrize("P", [653, 761, 857])
-def test_rq_inv_matches_oracle(snt, ctx, P):
+def test_rq_inv_matches_oracle(snt, ctx, P, latency):
     import torch
     p, q, _ = oracle.PARAMS[P]
     rng = np.random.default_rng(P + 1)
@@ -69,7 +70,8 @@ def test_rq_inv_matches_oracle(snt, ctx, P):
     a[2] = 3 * rng.integers(-1, 2, p)
     out = torch.empty(n * p, dtype=torch.int16, device="cuda")
     ok = torch.empty(n, dtype=torch.int32, device="cuda")
-    snt.snt_rq_inv(ctx, P, n, _t(a.ravel(), torch.int16), out, ok)
+    fn = snt.snt_rq_inv_latency if latency else snt.snt_rq_inv
+    fn(ctx, P, n, _t(a.ravel(), torch.int16), out, ok)
     got = out.cpu().numpy().reshape(n, p)
     okh = ok.cpu().numpy()
     for i in range(n):
