@@ -158,6 +158,23 @@ snt_status snt_debug_inject_g(snt_ctx *ctx, int P, size_t n,
                               const uint64_t *key_index_host,
                               const int8_t *g_host);
 
+/* ---- Tuning options (kernel layouts; outputs never depend on them) ---- */
+
+typedef enum {
+    /* lanes per element of the bit-sliced R/3 divstep kernel: 4, 8 or 32
+     * (32 / value elements share a warp) */
+    SNT_OPT_R3_LANES = 1,
+    /* largest number of thread groups one R/q product of a narrow tree level
+     * is split over: 1, 2, 4 or 8 */
+    SNT_OPT_TREE_SPLIT = 2,
+    /* 1: the per-key R/3 inversions run on a low-priority stream concurrent
+     * with the product tree; 0: they run first, on the tree's stream */
+    SNT_OPT_R3_OVERLAP = 3
+} snt_option;
+
+snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);
+snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
+
 /* ---- Tracing ---- */
 
 /* Phases reported by snt_ctx_phase_times, in this order: sampling of f and the

@@ -20,6 +20,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsntrup_gb300.so")
 SNTRUP653, SNTRUP761, SNTRUP857 = 653, 761, 857
 PARAMS = {653: (653, 4621, 288), 761: (761, 4591, 286), 857: (857, 5167, 322)}
 
+# tuning options (snt_option)
+SNT_OPT_R3_LANES, SNT_OPT_TREE_SPLIT, SNT_OPT_R3_OVERLAP = 1, 2, 3
+
 # phase names of snt_ctx_phase_times (SNT_NPHASES entries)
 PHASES = ("sample_f", "r3_inv", "tree_up", "root_inv", "tree_down", "h_encode", "sha512",
           "total")
@@ -65,6 +68,8 @@ def load():
         "snt_r3_inv": [P, i32, sz, P, P, P, P],
         "snt_debug_inject_g": [P, i32, sz, P, P],
         "snt_ctx_set_timing": [P, i32],
+        "snt_ctx_set_option": [P, i32, i32],
+        "snt_ctx_get_option": [P, i32, ctypes.POINTER(ctypes.c_int)],
         "snt_ctx_phase_times": [P, P, i32],
         "snt_measure_int_peak": [i32, i32, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int)],
@@ -143,6 +148,14 @@ class Context:
 
     def sync(self, stream=None):
         _check(load().snt_ctx_sync(self.handle, _stream(stream)))
+
+    def set_option(self, option, value):
+        _check(load().snt_ctx_set_option(self.handle, option, value))
+
+    def get_option(self, option):
+        v = ctypes.c_int()
+        _check(load().snt_ctx_get_option(self.handle, option, ctypes.byref(v)))
+        return v.value
 
     def set_timing(self, on=True):
         _check(load().snt_ctx_set_timing(self.handle, 1 if on else 0))

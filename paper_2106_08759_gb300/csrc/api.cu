@@ -75,6 +75,9 @@ struct snt_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr;
     bool timing = false;
     cudaEvent_t ev_phase[kPhaseEvents] = {};
+    int r3_lanes = kDefaultR3Lanes;
+    int tree_split = kDefaultTreeSplit;
+    int r3_overlap = kDefaultR3Overlap;
 };
 
 namespace {
@@ -91,28 +94,31 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     cudaEvent_t *ev = ctx->ev_phase;
     const bool tm = ctx->timing;
     // fork from the caller's stream: the tree branch runs on the context's
-    // high-priority stream, the per-key R/3 inversions on its low-priority
-    // stream, so R/3 blocks fill the SMs the narrow tree levels and the root
-    // inversion leave idle instead of delaying the tree.
+    // high-priority stream; with r3_overlap the per-key R/3 inversions run on
+    // its low-priority stream, so R/3 blocks fill the SMs the narrow tree
+    // levels and the root inversion leave idle; without, they run first on
+    // the tree stream.
     const cudaStream_t caller = st;
+    const bool overlap = ctx->r3_overlap != 0;
+    cudaStream_t r3s = overlap ? ctx->aux : ctx->tree;
     SNT_CUDA(cudaEventRecord(ctx->ev_fork, caller));
     SNT_CUDA(cudaStreamWaitEvent(ctx->tree, ctx->ev_fork, 0));
-    SNT_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    if (overlap) SNT_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
     st = ctx->tree;
     if (tm) SNT_CUDA(cudaEventRecord(ev[0], st));
     SNT_CUDA(launch_sample_f<P>(seed, first, Bi, leaves, sk, pi.sk_bytes, 2 * sb + pi.pk_bytes, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[1], st));
     const int n_inj = (ctx->inj_P == P) ? ctx->n_inj : 0;
-    if (tm) SNT_CUDA(cudaEventRecord(ev[2], ctx->aux));
+    if (tm) SNT_CUDA(cudaEventRecord(ev[2], r3s));
     SNT_CUDA(launch_r3_keygen<P>(seed, first, Bi, gbuf, sk, pi.sk_bytes, sb, ctx->d_inj_idx,
-                                 ctx->d_inj_g, n_inj, ctx->d_err, ctx->aux));
-    if (tm) SNT_CUDA(cudaEventRecord(ev[3], ctx->aux));
-    SNT_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
+                                 ctx->d_inj_g, n_inj, ctx->d_err, r3s, ctx->r3_lanes));
+    if (tm) SNT_CUDA(cudaEventRecord(ev[3], r3s));
+    if (overlap) SNT_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
     if (batched) {
         const int L = (int)t.n.size() - 1;
         for (int l = 1; l <= L; ++l)
             SNT_CUDA(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1],
-                                       nodes + (size_t)t.off[l] * pi.pad, st));
+                                       nodes + (size_t)t.off[l] * pi.pad, st, ctx->tree_split));
         if (tm) SNT_CUDA(cudaEventRecord(ev[4], st));
         int16_t *root = nodes + (size_t)t.off[L] * pi.pad;
         SNT_CUDA(launch_rq_inv_jump<P>(1, root, pi.pad, root, pi.pad, nullptr, ctx->d_err, ERR_ROOT,
@@ -120,7 +126,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         if (tm) SNT_CUDA(cudaEventRecord(ev[5], st));
         for (int l = L; l >= 1; --l)
             SNT_CUDA(launch_tree_down<P>(nodes + (size_t)t.off[l] * pi.pad,
-                                         nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1], st));
+                                         nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1], st,
+                                         ctx->tree_split));
         if (tm) SNT_CUDA(cudaEventRecord(ev[6], st));
     } else {
         SNT_CUDA(launch_rq_inv<P>(Bi, leaves, pi.pad, leaves, pi.pad, nullptr, ctx->d_err, ERR_ROOT,
@@ -131,7 +138,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
             SNT_CUDA(cudaEventRecord(ev[6], st));
         }
     }
-    SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    if (overlap) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     if (tm) SNT_CUDA(cudaEventRecord(ev[7], st));
     SNT_CUDA(launch_finalize<P>(Bi, gbuf, leaves, pk, pi.pk_bytes, sk, pi.sk_bytes, 2 * sb,
                                 pi.sched, st));
@@ -353,9 +360,9 @@ snt_status snt_r3_inv(snt_ctx *ctx, int P, size_t n, const int8_t *g_dev, int8_t
     DeviceGuard dg(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     switch (P) {
-        case 653: SNT_CUDA(launch_r3_inv<653>((int)n, g_dev, out_dev, ok_dev, st)); break;
-        case 761: SNT_CUDA(launch_r3_inv<761>((int)n, g_dev, out_dev, ok_dev, st)); break;
-        case 857: SNT_CUDA(launch_r3_inv<857>((int)n, g_dev, out_dev, ok_dev, st)); break;
+        case 653: SNT_CUDA(launch_r3_inv<653>((int)n, g_dev, out_dev, ok_dev, st, ctx->r3_lanes)); break;
+        case 761: SNT_CUDA(launch_r3_inv<761>((int)n, g_dev, out_dev, ok_dev, st, ctx->r3_lanes)); break;
+        case 857: SNT_CUDA(launch_r3_inv<857>((int)n, g_dev, out_dev, ok_dev, st, ctx->r3_lanes)); break;
         default: return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     }
     return SNT_OK;
@@ -379,6 +386,38 @@ snt_status snt_debug_inject_g(snt_ctx *ctx, int P, size_t n, const uint64_t *key
     ctx->n_inj = (int)n;
     ctx->inj_P = P;
     return SNT_OK;
+}
+
+snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
+    switch (option) {
+        case SNT_OPT_R3_LANES:
+            if (value != 4 && value != 8 && value != 32)
+                return set_error(SNT_EINVAL, "R/3 lanes per element must be 4, 8 or 32");
+            ctx->r3_lanes = value;
+            return SNT_OK;
+        case SNT_OPT_TREE_SPLIT:
+            if (value != 1 && value != 2 && value != 4 && value != 8)
+                return set_error(SNT_EINVAL, "tree split must be 1, 2, 4 or 8");
+            ctx->tree_split = value;
+            return SNT_OK;
+        case SNT_OPT_R3_OVERLAP:
+            if (value != 0 && value != 1) return set_error(SNT_EINVAL, "R/3 overlap is 0 or 1");
+            ctx->r3_overlap = value;
+            return SNT_OK;
+        default:
+            return set_error(SNT_EINVAL, "unknown option %d", option);
+    }
+}
+
+snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
+    if (!ctx || !value) return set_error(SNT_EINVAL, "null argument");
+    switch (option) {
+        case SNT_OPT_R3_LANES: *value = ctx->r3_lanes; return SNT_OK;
+        case SNT_OPT_TREE_SPLIT: *value = ctx->tree_split; return SNT_OK;
+        case SNT_OPT_R3_OVERLAP: *value = ctx->r3_overlap; return SNT_OK;
+        default: return set_error(SNT_EINVAL, "unknown option %d", option);
+    }
 }
 
 snt_status snt_ctx_set_timing(snt_ctx *ctx, int on) {

@@ -34,9 +34,9 @@ k_finalize(const int8_t *__restrict__ gbuf, const int16_t *__restrict__ ainv,
     __syncthreads();
     int acc[1][8];
     const int *const A1[1] = {As};
-    toeplitz_tile<P, 1>(A1, Es, acc);
+    toeplitz_tile<P, 1>(A1, Es, threadIdx.x, 0, Tp<P>::p8, acc);
     const int bl[1] = {(int)inv[P - 1]};
-    toeplitz_finish<P, 1>(A1, bl, acc);
+    toeplitz_finish<P, 1>(A1, bl, acc, threadIdx.x, true);
     const int j0 = 8 * threadIdx.x;
 #pragma unroll
     for (int t = 0; t < 8; ++t)
@@ -103,51 +103,55 @@ __constant__ uint64_t c_sha512_k[80] = {
 
 __device__ __forceinline__ uint64_t rotr(uint64_t x, int n) { return (x >> n) | (x << (64 - n)); }
 
-// One warp hashes 32 keys, one key per lane.  The 32 messages 0x04 | pk are
-// staged in shared memory by coalesced copies, each row `stride` bytes with
-// stride / 4 odd so that the 32 lanes' reads of the same offset fall in
-// distinct banks.  Message words are read as aligned 32-bit pairs; the
+// One warp hashes 32 keys, one key per lane.  The 32 public keys of a warp
+// are consecutive rows, i.e. one contiguous span, copied to shared memory
+// with 16-byte loads when the span is 16-byte aligned (byte loads otherwise).
+// Lane j then reads its message 0x04 | pk_j byte by byte from there; the
 // padding (0x80, zeros, 128-bit big-endian bit length) is generated.
 __global__ void __launch_bounds__(32)
 k_sha512_pk(int B, const uint8_t *__restrict__ pk, int pk_bytes, uint8_t *__restrict__ sk,
-            int sk_bytes, int hash_off, int stride) {
-    extern __shared__ __align__(16) uint8_t msg[];
+            int sk_bytes, int hash_off) {
+    extern __shared__ __align__(16) uint8_t blk[];
     const int lane = threadIdx.x;
     const int base = blockIdx.x * 32;
     const int nkeys = min(32, B - base);
-    const int len = pk_bytes + 1;
-    for (int j = 0; j < nkeys; ++j) {
-        const uint8_t *src = pk + (size_t)(base + j) * pk_bytes;
-        uint8_t *dst = msg + j * stride;
-        if (lane == 0) dst[0] = 4;
-        for (int b = lane; b < pk_bytes; b += 32) dst[1 + b] = src[b];
-        for (int b = len + lane; b < stride; b += 32) dst[b] = 0;
+    const int nbytes = nkeys * pk_bytes;
+    const uint8_t *src = pk + (size_t)base * pk_bytes;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int n16 = nbytes / 16;
+        const int4 *s4 = reinterpret_cast<const int4 *>(src);
+        int4 *d4 = reinterpret_cast<int4 *>(blk);
+#pragma unroll 4
+        for (int i = lane; i < n16; i += 32) d4[i] = s4[i];
+        done = n16 * 16;
     }
+    for (int i = done + lane; i < nbytes; i += 32) blk[i] = src[i];
     __syncwarp();
     if (lane >= nkeys) return;
-    const uint8_t *m = msg + lane * stride;
+    const uint8_t *row = blk + lane * pk_bytes;  // message byte pos (1 <= pos <= pk_bytes) = row[pos - 1]
+    const int len = pk_bytes + 1;
     const int nblk = (len + 1 + 16 + 127) / 128;
     const uint64_t bitlen = (uint64_t)len * 8u;
     uint64_t H[8] = {0x6a09e667f3bcc908ULL, 0xbb67ae8584caa73bULL, 0x3c6ef372fe94f82bULL,
                      0xa54ff53a5f1d36f1ULL, 0x510e527fade682d1ULL, 0x9b05688c2b3e6c1fULL,
                      0x1f83d9abfb41bd6bULL, 0x5be0cd19137e2179ULL};
-    for (int blk = 0; blk < nblk; ++blk) {
+    for (int b0 = 0; b0 < nblk; ++b0) {
         uint64_t W[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
-            const int pos = 128 * blk + 8 * t;
-            uint64_t v;
-            if (pos + 8 <= len) {
-                const uint32_t hi = *reinterpret_cast<const uint32_t *>(m + pos);
-                const uint32_t lo = *reinterpret_cast<const uint32_t *>(m + pos + 4);
-                v = ((uint64_t)__byte_perm(hi, 0, 0x0123) << 32) | __byte_perm(lo, 0, 0x0123);
+            const int pos = 128 * b0 + 8 * t;
+            uint64_t v = 0;
+            if (pos >= 1 && pos + 8 <= len) {
+#pragma unroll
+                for (int b = 0; b < 8; ++b) v = (v << 8) | row[pos + b - 1];
             } else {
-                v = 0;
 #pragma unroll
                 for (int b = 0; b < 8; ++b) {
                     const int q = pos + b;
                     uint32_t byte = 0;
-                    if (q < len) byte = m[q];
+                    if (q == 0) byte = 4u;
+                    else if (q < len) byte = row[q - 1];
                     else if (q == len) byte = 0x80u;
                     else if (q >= nblk * 128 - 8) byte = (uint32_t)(bitlen >> (8 * (nblk * 128 - 1 - q))) & 255u;
                     v = (v << 8) | byte;
@@ -192,10 +196,8 @@ cudaError_t launch_finalize(int B, const int8_t *gbuf, const int16_t *ainv, uint
 
 cudaError_t launch_sha512_pk(int B, const uint8_t *pk, int pk_bytes, uint8_t *sk, int sk_bytes,
                              int hash_off, cudaStream_t st) {
-    int stride = (pk_bytes + 1 + 3) / 4 * 4;
-    if (((stride / 4) & 1) == 0) stride += 4;
-    k_sha512_pk<<<(B + 31) / 32, 32, 32 * stride, st>>>(B, pk, pk_bytes, sk, sk_bytes, hash_off,
-                                                          stride);
+    const int smem = (32 * pk_bytes + 15) / 16 * 16;
+    k_sha512_pk<<<(B + 31) / 32, 32, smem, st>>>(B, pk, pk_bytes, sk, sk_bytes, hash_off);
     return cudaGetLastError();
 }
 

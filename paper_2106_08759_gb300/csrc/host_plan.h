@@ -13,6 +13,11 @@
 
 namespace snt {
 
+// Defaults of the tuning options (snt_ctx_set_option).
+constexpr int kDefaultR3Lanes = 8;     // lanes per element of the R/3 divstep kernel
+constexpr int kDefaultTreeSplit = 8;   // largest split of one product over thread groups
+constexpr int kDefaultR3Overlap = 1;   // R/3 on its own low-priority stream
+
 // Records a one-line error message (snt_last_error_string) and returns s.
 snt_status set_error(snt_status s, const char *fmt, ...);
 

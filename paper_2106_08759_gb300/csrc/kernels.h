@@ -26,13 +26,17 @@ cudaError_t launch_sample_f(uint64_t seed, uint64_t first, int B, int16_t *leave
 template <int P>
 cudaError_t launch_r3_keygen(uint64_t seed, uint64_t first, int B, int8_t *g_out, uint8_t *sk,
                              int sk_bytes, int sk_off, const uint64_t *inj_idx,
-                             const int8_t *inj_g, int n_inj, int *err, cudaStream_t st);
+                             const int8_t *inj_g, int n_inj, int *err, cudaStream_t st,
+                             int lanes);
 template <int P>
-cudaError_t launch_r3_inv(int n, const int8_t *g, int8_t *out, int32_t *ok, cudaStream_t st);
+cudaError_t launch_r3_inv(int n, const int8_t *g, int8_t *out, int32_t *ok, cudaStream_t st,
+                          int lanes);
 template <int P>
-cudaError_t launch_tree_up(const int16_t *lin, int n_in, int16_t *lout, cudaStream_t st);
+cudaError_t launch_tree_up(const int16_t *lin, int n_in, int16_t *lout, cudaStream_t st,
+                           int max_split);
 template <int P>
-cudaError_t launch_tree_down(const int16_t *lpar, int16_t *lch, int n_ch, cudaStream_t st);
+cudaError_t launch_tree_down(const int16_t *lpar, int16_t *lch, int n_ch, cudaStream_t st,
+                             int max_split);
 template <int P>
 cudaError_t launch_mul_batch(int n, const int16_t *a, const int16_t *b, int16_t *c,
                              cudaStream_t st);

@@ -67,16 +67,17 @@ snt_status run_static(const snt::ParamInfo &pi, uint64_t seed, uint64_t first, s
     SNT_CUDA_S(cudaMemsetAsync(err, 0, sizeof(int), st));
     SNT_CUDA_S(launch_sample_f<P>(seed, first, Bi, nodes, sk, pi.sk_bytes, 2 * sb + pi.pk_bytes, st));
     SNT_CUDA_S(launch_r3_keygen<P>(seed, first, Bi, gbuf, sk, pi.sk_bytes, sb, nullptr, nullptr, 0,
-                                   err, st));
+                                   err, st, kDefaultR3Lanes));
     const int L = (int)t.n.size() - 1;
     for (int l = 1; l <= L; ++l)
         SNT_CUDA_S(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1],
-                                     nodes + (size_t)t.off[l] * pi.pad, st));
+                                     nodes + (size_t)t.off[l] * pi.pad, st, kDefaultTreeSplit));
     int16_t *root = nodes + (size_t)t.off[L] * pi.pad;
     SNT_CUDA_S(launch_rq_inv_jump<P>(1, root, pi.pad, root, pi.pad, nullptr, err, ERR_ROOT, st));
     for (int l = L; l >= 1; --l)
         SNT_CUDA_S(launch_tree_down<P>(nodes + (size_t)t.off[l] * pi.pad,
-                                       nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1], st));
+                                       nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1], st,
+                                       kDefaultTreeSplit));
     SNT_CUDA_S(launch_finalize<P>(Bi, gbuf, nodes, pk, pi.pk_bytes, sk, pi.sk_bytes, 2 * sb,
                                   pi.sched, st));
     SNT_CUDA_S(launch_sha512_pk(Bi, pk, pi.pk_bytes, sk, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));

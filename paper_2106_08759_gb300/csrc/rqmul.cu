@@ -19,12 +19,17 @@
 
 namespace snt {
 
-template <int P>
-__global__ void __launch_bounds__(Tp<P>::NT)
+// Products per CTA are split K ways over the inner index (toeplitz_split):
+// narrow tree levels (few products) use K = 8 to cut the latency of each
+// product, wide levels K = 1 for throughput.
+template <int P, int K>
+__global__ void __launch_bounds__(Tp<P>::NT * K)
 k_tree_up(const int16_t *__restrict__ lin, int n_in, int16_t *__restrict__ lout) {
     using G = Geo<P>;
+    constexpr int NT = Tp<P>::NT;
     __shared__ __align__(16) int As[Tp<P>::p8];
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
+    __shared__ int part[K > 1 ? (K - 1) * Tp<P>::p8 : 1];
     const int j = blockIdx.x;
     const int16_t *a = lin + (size_t)(2 * j) * G::pad;
     int16_t *c = lout + (size_t)j * G::pad;
@@ -38,19 +43,23 @@ k_tree_up(const int16_t *__restrict__ lin, int n_in, int16_t *__restrict__ lout)
     __syncthreads();
     int acc[1][8];
     const int *const A1[1] = {As};
-    toeplitz_tile<P, 1>(A1, Es, acc);
+    toeplitz_split<P, 1, K>(A1, Es, part, acc);
+    const int tloc = threadIdx.x % NT;
+    const bool active = threadIdx.x < NT;
     const int bl[1] = {(int)b[P - 1]};
-    toeplitz_finish<P, 1>(A1, bl, acc);
-    store_tile<P>(c, acc[0], G::pad);
+    toeplitz_finish<P, 1>(A1, bl, acc, tloc, active);
+    if (active) store_tile<P>(c, acc[0], G::pad, tloc);
 }
 
-template <int P>
-__global__ void __launch_bounds__(Tp<P>::NT)
+template <int P, int K>
+__global__ void __launch_bounds__(Tp<P>::NT * K)
 k_tree_down(const int16_t *__restrict__ lpar, int16_t *__restrict__ lch, int n_ch) {
     using G = Geo<P>;
+    constexpr int NT = Tp<P>::NT;
     __shared__ __align__(16) int Xs[Tp<P>::p8];
     __shared__ __align__(16) int Ys[Tp<P>::p8];
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
+    __shared__ int part[K > 1 ? (K - 1) * Tp<P>::p8 : 1];
     const int j = blockIdx.x;
     const int16_t *T = lpar + (size_t)j * G::pad;
     int16_t *x = lch + (size_t)(2 * j) * G::pad;
@@ -65,12 +74,16 @@ k_tree_down(const int16_t *__restrict__ lpar, int16_t *__restrict__ lch, int n_c
     __syncthreads();  // both children are in shared memory before either is overwritten
     int acc[2][8];
     const int *const A2[2] = {Ys, Xs};
-    toeplitz_tile<P, 2>(A2, Es, acc);
+    toeplitz_split<P, 2, K>(A2, Es, part, acc);
+    const int tloc = threadIdx.x % NT;
+    const bool active = threadIdx.x < NT;
     const int tl = (int)T[P - 1];
     const int bl[2] = {tl, tl};
-    toeplitz_finish<P, 2>(A2, bl, acc);
-    store_tile<P>(x, acc[0], G::pad);  // 1/x = T * y
-    store_tile<P>(y, acc[1], G::pad);  // 1/y = T * x
+    toeplitz_finish<P, 2>(A2, bl, acc, tloc, active);
+    if (active) {
+        store_tile<P>(x, acc[0], G::pad, tloc);  // 1/x = T * y
+        store_tile<P>(y, acc[1], G::pad, tloc);  // 1/y = T * x
+    }
 }
 
 // c_e = a_e * b_e, n products, all operands stride p (microbenchmark layout).
@@ -88,26 +101,46 @@ k_mul_batch(int n, const int16_t *__restrict__ a, const int16_t *__restrict__ b,
     __syncthreads();
     int acc[1][8];
     const int *const A1[1] = {As};
-    toeplitz_tile<P, 1>(A1, Es, acc);
+    toeplitz_tile<P, 1>(A1, Es, threadIdx.x, 0, Tp<P>::p8, acc);
     const int bl[1] = {(int)be[P - 1]};
-    toeplitz_finish<P, 1>(A1, bl, acc);
+    toeplitz_finish<P, 1>(A1, bl, acc, threadIdx.x, true);
     const int j0 = 8 * threadIdx.x;
 #pragma unroll
     for (int t = 0; t < 8; ++t)
         if (j0 + t < P) c[(size_t)e * P + j0 + t] = (int16_t)acc[0][t];
 }
 
+// Split factor for a level of n products: enough threads to fill the GPU.
+inline int split_for(int n, int max_split) {
+    const int k = n <= 48 ? 8 : n <= 160 ? 4 : n <= 400 ? 2 : 1;
+    return k < max_split ? k : max_split;
+}
+
 template <int P>
-cudaError_t launch_tree_up(const int16_t *lin, int n_in, int16_t *lout, cudaStream_t st) {
+cudaError_t launch_tree_up(const int16_t *lin, int n_in, int16_t *lout, cudaStream_t st,
+                           int max_split) {
     const int n_out = (n_in + 1) / 2;
-    k_tree_up<P><<<n_out, Tp<P>::NT, 0, st>>>(lin, n_in, lout);
+    constexpr int NT = Tp<P>::NT;
+    switch (split_for(n_out, max_split)) {
+        case 8: k_tree_up<P, 8><<<n_out, NT * 8, 0, st>>>(lin, n_in, lout); break;
+        case 4: k_tree_up<P, 4><<<n_out, NT * 4, 0, st>>>(lin, n_in, lout); break;
+        case 2: k_tree_up<P, 2><<<n_out, NT * 2, 0, st>>>(lin, n_in, lout); break;
+        default: k_tree_up<P, 1><<<n_out, NT, 0, st>>>(lin, n_in, lout); break;
+    }
     return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t launch_tree_down(const int16_t *lpar, int16_t *lch, int n_ch, cudaStream_t st) {
+cudaError_t launch_tree_down(const int16_t *lpar, int16_t *lch, int n_ch, cudaStream_t st,
+                             int max_split) {
     const int n_par = (n_ch + 1) / 2;
-    k_tree_down<P><<<n_par, Tp<P>::NT, 0, st>>>(lpar, lch, n_ch);
+    constexpr int NT = Tp<P>::NT;
+    switch (split_for(n_par, max_split)) {
+        case 8: k_tree_down<P, 8><<<n_par, NT * 8, 0, st>>>(lpar, lch, n_ch); break;
+        case 4: k_tree_down<P, 4><<<n_par, NT * 4, 0, st>>>(lpar, lch, n_ch); break;
+        case 2: k_tree_down<P, 2><<<n_par, NT * 2, 0, st>>>(lpar, lch, n_ch); break;
+        default: k_tree_down<P, 1><<<n_par, NT, 0, st>>>(lpar, lch, n_ch); break;
+    }
     return cudaGetLastError();
 }
 
@@ -119,8 +152,8 @@ cudaError_t launch_mul_batch(int n, const int16_t *a, const int16_t *b, int16_t 
 }
 
 #define SNT_MUL_INST(P)                                                                        \
-    template cudaError_t launch_tree_up<P>(const int16_t *, int, int16_t *, cudaStream_t);     \
-    template cudaError_t launch_tree_down<P>(const int16_t *, int16_t *, int, cudaStream_t);   \
+    template cudaError_t launch_tree_up<P>(const int16_t *, int, int16_t *, cudaStream_t, int); \
+    template cudaError_t launch_tree_down<P>(const int16_t *, int16_t *, int, cudaStream_t, int); \
     template cudaError_t launch_mul_batch<P>(int, const int16_t *, const int16_t *, int16_t *, \
                                              cudaStream_t);
 SNT_MUL_INST(653)

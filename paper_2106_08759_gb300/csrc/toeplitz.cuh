@@ -49,13 +49,14 @@ __device__ __forceinline__ void fill_A(const T *__restrict__ a, int *As) {
     for (int i = threadIdx.x; i < Tp<P>::p8; i += blockDim.x) As[i] = (i < P) ? (int)a[i] : 0;
 }
 
-// acc[k][t] = sum_i A_k[i] E[j0 + t - i + p - 1] for NA operands sharing E,
-// reduced mod q every 256 terms; j0 = 8 * threadIdx.x.
+// acc[k][t] = sum_i A_k[i] E[j0 + t - i + p - 1] over i in [ib_lo, ib_hi)
+// (multiples of 8) for NA operands sharing E, j0 = 8 * tloc; reduced mod q
+// every 256 terms and at the end (centred).
 template <int P, int NA>
-__device__ __forceinline__ void toeplitz_tile(const int *const (&As)[NA], const int *Es,
-                                              int (&acc)[NA][8]) {
+__device__ __forceinline__ void toeplitz_tile(const int *const (&As)[NA], const int *Es, int tloc,
+                                              int ib_lo, int ib_hi, int (&acc)[NA][8]) {
     constexpr int Q = Geo<P>::q;
-    const int j0 = 8 * threadIdx.x;
+    const int j0 = 8 * tloc;
     const int base = Tp<P>::OFF + P - 9 + j0;  // window start for i-block 0
 #pragma unroll
     for (int k = 0; k < NA; ++k)
@@ -63,13 +64,13 @@ __device__ __forceinline__ void toeplitz_tile(const int *const (&As)[NA], const 
         for (int t = 0; t < 8; ++t) acc[k][t] = 0;
     int whi[8];
     {
-        const int4 h0 = *reinterpret_cast<const int4 *>(&Es[base + 8]);
-        const int4 h1 = *reinterpret_cast<const int4 *>(&Es[base + 12]);
+        const int4 h0 = *reinterpret_cast<const int4 *>(&Es[base - ib_lo + 8]);
+        const int4 h1 = *reinterpret_cast<const int4 *>(&Es[base - ib_lo + 12]);
         whi[0] = h0.x; whi[1] = h0.y; whi[2] = h0.z; whi[3] = h0.w;
         whi[4] = h1.x; whi[5] = h1.y; whi[6] = h1.z; whi[7] = h1.w;
     }
 #pragma unroll 2
-    for (int ib = 0; ib < Tp<P>::p8; ib += 8) {
+    for (int ib = ib_lo; ib < ib_hi; ib += 8) {
         int wlo[8];
         const int4 l0 = *reinterpret_cast<const int4 *>(&Es[base - ib]);
         const int4 l1 = *reinterpret_cast<const int4 *>(&Es[base - ib + 4]);
@@ -91,40 +92,79 @@ __device__ __forceinline__ void toeplitz_tile(const int *const (&As)[NA], const 
         }
 #pragma unroll
         for (int z = 0; z < 8; ++z) whi[z] = wlo[z];
-        if (((ib + 8) & 255) == 0) {
+        if (((ib + 8 - ib_lo) & 255) == 0) {
 #pragma unroll
             for (int k = 0; k < NA; ++k)
 #pragma unroll
                 for (int t = 0; t < 8; ++t) acc[k][t] = cmod<Q>(acc[k][t]);
         }
     }
+#pragma unroll
+    for (int k = 0; k < NA; ++k)
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc[k][t] = cmod<Q>(acc[k][t]);
+}
+
+// K-way split of the i-range: thread tid = grp * NT + tloc sums i-blocks
+// [grp * per, (grp + 1) * per); group 0 ends with the full centred sums.
+// Every thread of the CTA must call it (it contains barriers when K > 1).
+template <int P, int NA, int K>
+__device__ __forceinline__ void toeplitz_split(const int *const (&As)[NA], const int *Es,
+                                               int *part, int (&acc)[NA][8]) {
+    constexpr int NT = Tp<P>::NT, Q = Geo<P>::q;
+    constexpr int per = (NT + K - 1) / K;  // i-blocks of 8 per group
+    const int tloc = threadIdx.x % NT, grp = threadIdx.x / NT;
+    const int ib_lo = min(grp * per, NT) * 8, ib_hi = min((grp + 1) * per, NT) * 8;
+    toeplitz_tile<P, NA>(As, Es, tloc, ib_lo, ib_hi, acc);
+    if (K > 1) {
+        const int j0 = 8 * tloc;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            if (grp > 0)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) part[(grp - 1) * Tp<P>::p8 + j0 + t] = acc[k][t];
+            __syncthreads();
+            if (grp == 0) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    int sum = acc[k][t];
+                    for (int g = 0; g < K - 1; ++g) sum += part[g * Tp<P>::p8 + j0 + t];
+                    acc[k][t] = cmod<Q>(sum);
+                }
+            }
+            __syncthreads();
+        }
+    }
 }
 
 // Adds the [j >= 1] a_j b_{p-1} term, reduces, fixes output 0 and returns
-// centred values (zero for j >= p).  Output 0 needs a fix: the E table also
-// folds the x^(p-1) coefficient c_{p-1} = sum_{i+m=p-1} a_i b_m into row 0,
-// although x^(p-1) is not reduced.  The row-(p-1) result is exactly
+// centred values (zero for j >= p) in the threads with active = true (one
+// thread per 8 outputs, tloc = its tile).  Output 0 needs a fix: the E table
+// also folds the x^(p-1) coefficient c_{p-1} = sum_{i+m=p-1} a_i b_m into row
+// 0, although x^(p-1) is not reduced.  The row-(p-1) result is exactly
 // c_{p-1} + a_{p-1} b_{p-1}, so
 //     c_0 = (row 0) - (row p-1) + (a_0 + a_{p-1}) b_{p-1}.
 // Contains a __syncthreads(): every thread of the CTA must call it.
 template <int P, int NA>
 __device__ __forceinline__ void toeplitz_finish(const int *const (&As)[NA], const int (&blast)[NA],
-                                                int (&acc)[NA][8]) {
+                                                int (&acc)[NA][8], int tloc, bool active) {
     constexpr int Q = Geo<P>::q;
     __shared__ int last_row[NA];
-    const int j0 = 8 * threadIdx.x;
+    const int j0 = 8 * tloc;
+    if (active) {
 #pragma unroll
-    for (int k = 0; k < NA; ++k)
+        for (int k = 0; k < NA; ++k)
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int j = j0 + t;
-            int v = acc[k][t];
-            if (j >= 1 && j < P) v += As[k][j] * blast[k];
-            acc[k][t] = (j < P) ? cmod<Q>(v) : 0;
-            if (j == P - 1) last_row[k] = acc[k][t];
-        }
+            for (int t = 0; t < 8; ++t) {
+                const int j = j0 + t;
+                int v = acc[k][t];
+                if (j >= 1 && j < P) v += As[k][j] * blast[k];
+                acc[k][t] = (j < P) ? cmod<Q>(v) : 0;
+                if (j == P - 1) last_row[k] = acc[k][t];
+            }
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (active && tloc == 0) {
 #pragma unroll
         for (int k = 0; k < NA; ++k)
             acc[k][0] = cmod<Q>(acc[k][0] - last_row[k] + (As[k][0] + As[k][P - 1]) * blast[k]);
@@ -134,15 +174,16 @@ __device__ __forceinline__ void toeplitz_finish(const int *const (&As)[NA], cons
 // Stores 8 outputs (j0 .. j0+7) as int16; pads from p8 to `pad` are zeroed by
 // the threads that own the last tile.
 template <int P>
-__device__ __forceinline__ void store_tile(int16_t *__restrict__ c, const int (&v)[8], int pad) {
-    const int j0 = 8 * threadIdx.x;
+__device__ __forceinline__ void store_tile(int16_t *__restrict__ c, const int (&v)[8], int pad,
+                                           int tloc) {
+    const int j0 = 8 * tloc;
     int4 pk;
     pk.x = (v[0] & 0xffff) | (v[1] << 16);
     pk.y = (v[2] & 0xffff) | (v[3] << 16);
     pk.z = (v[4] & 0xffff) | (v[5] << 16);
     pk.w = (v[6] & 0xffff) | (v[7] << 16);
     *reinterpret_cast<int4 *>(&c[j0]) = pk;
-    if (threadIdx.x == blockDim.x - 1)
+    if (tloc == Tp<P>::NT - 1)
         for (int j = Tp<P>::p8; j < pad; ++j) c[j] = 0;
 }
 

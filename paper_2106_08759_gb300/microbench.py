@@ -1,0 +1,148 @@
+"""Kernel microbenchmark (sntrup761 building blocks) on one GPU.
+
+    python -m paper_2106_08759_gb300.microbench [--quick]
+
+Times each building block alone (CUDA events on the launching stream, L2
+flushed before every timed launch) on seeded synthetic inputs:
+  - R/q products, general x general and general x Short (2^20 each),
+  - R/3 inversions by bit-sliced divsteps (2^16),
+  - R/q inversions by per-step divsteps (2^10) and by jump divsteps (2^10,
+    and one element alone: the latency of the tree's root inversion),
+  - batch keygen phases at B = 4096 with the auxiliary-stream overlap.
+Prints one JSON line.  Inputs come from synth (numpy); outputs are not
+checked here (the parity tests do that).
+"""
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--quick", action="store_true", help="smaller counts")
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time the layout options of the R/3 kernel and of keygen")
+    args = ap.parse_args()
+
+    import numpy as np
+    import torch
+
+    import paper_2106_08759_gb300 as snt
+    from synth import rq_uniform, short_batch, ternary_batch
+
+    P, p = 761, 761
+    dev = torch.device("cuda", 0)
+    ctx = snt.Context(0, 512 << 20)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def timeit(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(args.reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        return best
+
+    def t(x, dt):
+        return torch.from_numpy(np.ascontiguousarray(x)).to(dtype=dt, device=dev)
+
+    out = {"p": p}
+    n = (1 << 16) if args.quick else (1 << 20)
+    A = t(rq_uniform(P, n, 1).ravel(), torch.int16)
+    Bm = t(rq_uniform(P, n, 2).ravel(), torch.int16)
+    S = t(short_batch(P, n, 3).ravel(), torch.int16)
+    C = torch.empty(n * p, dtype=torch.int16, device=dev)
+    ms = timeit(lambda: snt.snt_rq_mul(ctx, P, n, A, Bm, C))
+    out["rq_mul_gen"] = {"n": n, "ms": ms, "products_per_s": n / ms * 1e3,
+                         "gmac_per_s": n * p * p / ms / 1e6}
+    ms = timeit(lambda: snt.snt_rq_mul(ctx, P, n, A, S, C))
+    out["rq_mul_short"] = {"n": n, "ms": ms, "products_per_s": n / ms * 1e3}
+    del A, Bm, S, C
+
+    m = (1 << 12) if args.quick else (1 << 16)
+    G = t(ternary_batch(P, m, 5).ravel(), torch.int8)
+    O = torch.empty(m * p, dtype=torch.int8, device=dev)
+    OK = torch.empty(m, dtype=torch.int32, device=dev)
+    ms = timeit(lambda: snt.snt_r3_inv(ctx, P, m, G, O, OK))
+    out["r3_inv"] = {"n": m, "ms": ms, "inv_per_s": m / ms * 1e3}
+    G4 = G[: 4096 * p]
+    ms = timeit(lambda: snt.snt_r3_inv(ctx, P, 4096, G4, O, OK))
+    out["r3_inv_4096"] = {"n": 4096, "ms": ms}
+    if args.sweep:
+        default_lanes = ctx.get_option(snt.SNT_OPT_R3_LANES)
+        for lanes in (4, 8, 32):
+            ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
+            out["r3_inv_4096_lanes%d_ms" % lanes] = timeit(
+                lambda: snt.snt_r3_inv(ctx, P, 4096, G4, O, OK))
+            out["r3_inv_%d_lanes%d_ms" % (m, lanes)] = timeit(
+                lambda: snt.snt_r3_inv(ctx, P, m, G, O, OK))
+        ctx.set_option(snt.SNT_OPT_R3_LANES, default_lanes)
+
+    k = 1 << 10
+    X = t(rq_uniform(P, k, 6).ravel(), torch.int16)
+    XO = torch.empty(k * p, dtype=torch.int16, device=dev)
+    XK = torch.empty(k, dtype=torch.int32, device=dev)
+    ms = timeit(lambda: snt.snt_rq_inv(ctx, P, k, X, XO, XK))
+    out["rq_inv_perstep"] = {"n": k, "ms": ms, "inv_per_s": k / ms * 1e3}
+    ms = timeit(lambda: snt.snt_rq_inv_latency(ctx, P, k, X, XO, XK))
+    out["rq_inv_jump"] = {"n": k, "ms": ms, "inv_per_s": k / ms * 1e3}
+    ms = timeit(lambda: snt.snt_rq_inv_latency(ctx, P, 1, X, XO, XK))
+    out["rq_inv_jump_single_ms"] = ms
+    ms = timeit(lambda: snt.snt_rq_inv(ctx, P, 1, X, XO, XK))
+    out["rq_inv_perstep_single_ms"] = ms
+
+    Bk = 4096
+    pkb, skb, _, _ = snt.snt_param_sizes(P)
+    pk = torch.empty(Bk * pkb, dtype=torch.uint8, device=dev)
+    sk = torch.empty(Bk * skb, dtype=torch.uint8, device=dev)
+    ctx.set_timing(True)
+    snt.snt_batch_keygen(ctx, P, 1, 0, Bk, pk, sk)
+    ph = ctx.phase_times()
+    tot = 0.0
+    for i in range(args.reps):
+        flush.zero_()
+        snt.snt_batch_keygen(ctx, P, 1, (i + 1) * Bk, Bk, pk, sk)
+        ph = ctx.phase_times()
+        tot += ph["total"]
+    out["keygen_4096_phases_ms"] = ph
+    out["keygen_4096_ms"] = tot / args.reps
+    if args.sweep:
+        sweep = {}
+        for overlap in (0, 1):
+            for lanes in (4, 8, 32):
+                for split in (1, 8):
+                    ctx.set_option(snt.SNT_OPT_R3_OVERLAP, overlap)
+                    ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
+                    ctx.set_option(snt.SNT_OPT_TREE_SPLIT, split)
+                    snt.snt_batch_keygen(ctx, P, 1, 0, Bk, pk, sk)
+                    ctx.phase_times()
+                    tot = 0.0
+                    for i in range(args.reps):
+                        flush.zero_()
+                        snt.snt_batch_keygen(ctx, P, 1, (i + 1) * Bk, Bk, pk, sk)
+                        ph = ctx.phase_times()
+                        tot += ph["total"]
+                    key = "overlap%d_lanes%d_split%d" % (overlap, lanes, split)
+                    sweep[key] = {"ms": round(tot / args.reps, 4),
+                                  "phases": {k: round(v, 4) for k, v in ph.items()}}
+        out["keygen_4096_sweep"] = sweep
+    ctx.close()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -89,12 +89,13 @@ def _non_invertible(p, rng):
     return np.where(g == 2, -1, g)
 
 
+@pytest.mark.parametrize("lanes", [4, 8, 32])
 @pytest.mark.parametrize("P", [653, 761, 857])
-def test_r3_inv_matches_oracle(snt, ctx, P):
+def test_r3_inv_matches_oracle(snt, ctx, P, lanes):
     import torch
     p = P
     rng = np.random.default_rng(P + 2)
-    n = 20
+    n = 37  # ragged: not a multiple of the elements per CTA
     g = rng.integers(-1, 2, (n, p))
     g[0] = 0
     g[1] = 0; g[1, 0] = 1
@@ -102,7 +103,11 @@ def test_r3_inv_matches_oracle(snt, ctx, P):
     g[3] = 1
     out = torch.empty(n * p, dtype=torch.int8, device="cuda")
     ok = torch.empty(n, dtype=torch.int32, device="cuda")
-    snt.snt_r3_inv(ctx, P, n, _t(g.ravel(), torch.int8), out, ok)
+    ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
+    try:
+        snt.snt_r3_inv(ctx, P, n, _t(g.ravel(), torch.int8), out, ok)
+    finally:
+        ctx.set_option(snt.SNT_OPT_R3_LANES, 8)
     got = out.cpu().numpy().reshape(n, p)
     okh = ok.cpu().numpy()
     assert okh[2] == 0 and okh[0] == 0

@@ -56,6 +56,26 @@ def test_ragged_tree_shapes(snt, ctx, B):
     assert first_mismatch(sk, rsk) is None
 
 
+@pytest.mark.parametrize("opts", [(4, 8, 1), (8, 1, 0), (32, 2, 1), (4, 4, 0)])
+def test_tuning_options_do_not_change_keys(snt, ctx, opts):
+    # R/3 lanes per element, tree split, R/3 overlap: layouts only
+    lanes, split, overlap = opts
+    ref = gpu_keygen(snt, ctx, 761, 21, 300, 45)
+    ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
+    ctx.set_option(snt.SNT_OPT_TREE_SPLIT, split)
+    ctx.set_option(snt.SNT_OPT_R3_OVERLAP, overlap)
+    try:
+        got = gpu_keygen(snt, ctx, 761, 21, 300, 45)
+        got857 = gpu_keygen(snt, ctx, 857, 22, 0, 19)
+    finally:
+        ctx.set_option(snt.SNT_OPT_R3_LANES, 8)
+        ctx.set_option(snt.SNT_OPT_TREE_SPLIT, 8)
+        ctx.set_option(snt.SNT_OPT_R3_OVERLAP, 1)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    rpk, rsk = oracle.keygen_batch(857, 22, 0, 19)
+    assert first_mismatch(got857[0], rpk) is None and first_mismatch(got857[1], rsk) is None
+
+
 def test_split_batches_give_identical_bytes(snt, ctx):
     pk, sk = gpu_keygen(snt, ctx, 761, 9, 100, 37)
     pk1, sk1 = gpu_keygen(snt, ctx, 761, 9, 100, 20)
