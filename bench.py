@@ -180,6 +180,7 @@ def run_ours(args):
 
     lop3_peak, sms = snt.snt_measure_int_peak(local, 0)
     imad_peak, _ = snt.snt_measure_int_peak(local, 1)
+    tuned = ctx.autotune(P, B)  # kernel layouts for this GPU, before any timed step
 
     L = 0
     n = B
@@ -293,6 +294,7 @@ def run_ours(args):
                        "ms_per_step": round(pk_ms / pk_steps, 4),
                        "batched_speedup": round(value / perkey_rate, 3)},
         "phases_ms": {k: round(v, 4) for k, v in phase.items()},
+        "tuned": tuned,
         "int_peaks_tops": {"lop3": round(lop3_peak / 1e12, 3), "imad": round(imad_peak / 1e12, 3),
                            "sms": sms},
         "roofline": roofline,

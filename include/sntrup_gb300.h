@@ -167,13 +167,26 @@ typedef enum {
     /* largest number of thread groups one R/q product of a narrow tree level
      * is split over: 1, 2, 4 or 8 */
     SNT_OPT_TREE_SPLIT = 2,
-    /* 1: the per-key R/3 inversions run on a low-priority stream concurrent
-     * with the product tree; 0: they run first, on the tree's stream */
+    /* where the per-key R/3 inversions run: 0 first, on the tree's stream;
+     * 1 on a low-priority stream concurrent with the whole tree; 2 on the
+     * low-priority stream from the up-sweep's first narrow level (fewer than
+     * 256 products) up to the down-sweep's first wide level, so they fill the
+     * SMs the narrow levels and the root inversion leave idle */
     SNT_OPT_R3_OVERLAP = 3
 } snt_option;
 
 snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);
 snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
+
+/* Autotuner: times batch keygen of B keys of parameter set P under each
+ * combination of R/3 lanes (4, 8, 32), tree split (4, 8) and R/3 overlap
+ * (0, 1, 2) on this GPU (CUDA events, best of three after a warm-up) and
+ * keeps the fastest for every later keygen call of this context with the same
+ * P and ceil(log2 B); it overrides the snt_ctx_set_option values there.
+ * Synchronous; uses the context's scratch (B must fit the budget).  The chosen
+ * values are written to the optional out pointers. */
+snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *split_out,
+                        int *overlap_out);
 
 /* ---- Tracing ---- */
 

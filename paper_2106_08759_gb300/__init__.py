@@ -69,6 +69,8 @@ def load():
         "snt_debug_inject_g": [P, i32, sz, P, P],
         "snt_ctx_set_timing": [P, i32],
         "snt_ctx_set_option": [P, i32, i32],
+        "snt_autotune": [P, i32, sz, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_int)],
         "snt_ctx_get_option": [P, i32, ctypes.POINTER(ctypes.c_int)],
         "snt_ctx_phase_times": [P, P, i32],
         "snt_measure_int_peak": [i32, i32, ctypes.POINTER(ctypes.c_double),
@@ -156,6 +158,13 @@ class Context:
         v = ctypes.c_int()
         _check(load().snt_ctx_get_option(self.handle, option, ctypes.byref(v)))
         return v.value
+
+    def autotune(self, P, B):
+        """Pick the fastest kernel layouts for (P, B) on this GPU; returns them."""
+        la, sp, ov = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().snt_autotune(self.handle, P, B, ctypes.byref(la), ctypes.byref(sp),
+                                   ctypes.byref(ov)))
+        return {"r3_lanes": la.value, "tree_split": sp.value, "r3_overlap": ov.value}
 
     def set_timing(self, on=True):
         _check(load().snt_ctx_set_timing(self.handle, 1 if on else 0))

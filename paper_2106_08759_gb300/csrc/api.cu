@@ -72,13 +72,26 @@ struct snt_ctx {
     int inj_P = 0;
     cudaStream_t aux = nullptr;   // low priority: per-key R/3 inversions
     cudaStream_t tree = nullptr;  // high priority: sampling, product tree, h, hash
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr, ev_r3fork = nullptr;
     bool timing = false;
     cudaEvent_t ev_phase[kPhaseEvents] = {};
     int r3_lanes = kDefaultR3Lanes;
     int tree_split = kDefaultTreeSplit;
     int r3_overlap = kDefaultR3Overlap;
+    // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
+    struct Tuned { int lanes = 0, split = 0, overlap = 0; };
+    Tuned tuned[3][25];
+    cudaStream_t tune = nullptr;  // stream used while autotuning
 };
+
+namespace {
+int pidx(int P) { return P == 653 ? 0 : P == 761 ? 1 : 2; }
+int bbucket(size_t B) {
+    int b = 0;
+    while (((size_t)1 << b) < B && b < 24) ++b;
+    return b;
+}
+}  // namespace
 
 namespace {
 
@@ -93,41 +106,83 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     const int sb = pi.small_bytes;
     cudaEvent_t *ev = ctx->ev_phase;
     const bool tm = ctx->timing;
-    // fork from the caller's stream: the tree branch runs on the context's
-    // high-priority stream; with r3_overlap the per-key R/3 inversions run on
-    // its low-priority stream, so R/3 blocks fill the SMs the narrow tree
-    // levels and the root inversion leave idle; without, they run first on
-    // the tree stream.
+    // Fork from the caller's stream.  The tree branch runs on the context's
+    // high-priority stream.  The per-key R/3 inversions (independent of the
+    // tree until h) run
+    //   overlap 0: first, on the tree stream;
+    //   overlap 1: on the low-priority stream from the start, joined before h;
+    //   overlap 2: on the low-priority stream, forked when the up-sweep
+    //              reaches its narrow levels (fewer than kNarrow products) and
+    //              joined before the first wide down-sweep level, so they fill
+    //              the SMs that the narrow levels and the root inversion leave
+    //              idle without competing with the wide levels.
     const cudaStream_t caller = st;
-    const bool overlap = ctx->r3_overlap != 0;
-    cudaStream_t r3s = overlap ? ctx->aux : ctx->tree;
-    SNT_CUDA(cudaEventRecord(ctx->ev_fork, caller));
-    SNT_CUDA(cudaStreamWaitEvent(ctx->tree, ctx->ev_fork, 0));
-    if (overlap) SNT_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    int mode = ctx->r3_overlap, lanes = ctx->r3_lanes, split = ctx->tree_split;
+    const snt_ctx::Tuned &tu = ctx->tuned[pidx(P)][bbucket(B)];
+    if (tu.lanes) { mode = tu.overlap; lanes = tu.lanes; split = tu.split; }
     st = ctx->tree;
+    SNT_CUDA(cudaEventRecord(ctx->ev_fork, caller));
+    SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_fork, 0));
+    const int n_inj = (ctx->inj_P == P) ? ctx->n_inj : 0;
+    auto launch_r3 = [&](cudaStream_t r3s) -> snt_status {
+        if (tm) SNT_CUDA(cudaEventRecord(ev[2], r3s));
+        SNT_CUDA(launch_r3_keygen<P>(seed, first, Bi, gbuf, sk, pi.sk_bytes, sb, ctx->d_inj_idx,
+                                     ctx->d_inj_g, n_inj, ctx->d_err, r3s, lanes));
+        if (tm) SNT_CUDA(cudaEventRecord(ev[3], r3s));
+        return SNT_OK;
+    };
+    auto fork_r3 = [&]() -> snt_status {  // R/3 on the low-priority stream from here
+        SNT_CUDA(cudaEventRecord(ctx->ev_r3fork, st));
+        SNT_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_r3fork, 0));
+        const snt_status s3 = launch_r3(ctx->aux);
+        if (s3 != SNT_OK) return s3;
+        SNT_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
+        return SNT_OK;
+    };
+    bool forked = false, joined = false;
     if (tm) SNT_CUDA(cudaEventRecord(ev[0], st));
     SNT_CUDA(launch_sample_f<P>(seed, first, Bi, leaves, sk, pi.sk_bytes, 2 * sb + pi.pk_bytes, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[1], st));
-    const int n_inj = (ctx->inj_P == P) ? ctx->n_inj : 0;
-    if (tm) SNT_CUDA(cudaEventRecord(ev[2], r3s));
-    SNT_CUDA(launch_r3_keygen<P>(seed, first, Bi, gbuf, sk, pi.sk_bytes, sb, ctx->d_inj_idx,
-                                 ctx->d_inj_g, n_inj, ctx->d_err, r3s, ctx->r3_lanes));
-    if (tm) SNT_CUDA(cudaEventRecord(ev[3], r3s));
-    if (overlap) SNT_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
+    if (mode == 0) {
+        const snt_status s3 = launch_r3(st);
+        if (s3 != SNT_OK) return s3;
+        forked = joined = true;
+    } else if (mode == 1 || !batched) {
+        const snt_status s3 = fork_r3();
+        if (s3 != SNT_OK) return s3;
+        forked = true;
+    }
+    constexpr int kNarrow = 256;
     if (batched) {
         const int L = (int)t.n.size() - 1;
-        for (int l = 1; l <= L; ++l)
+        for (int l = 1; l <= L; ++l) {
+            if (!forked && t.n[l] < kNarrow) {
+                const snt_status s3 = fork_r3();
+                if (s3 != SNT_OK) return s3;
+                forked = true;
+            }
             SNT_CUDA(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1],
-                                       nodes + (size_t)t.off[l] * pi.pad, st, ctx->tree_split));
+                                       nodes + (size_t)t.off[l] * pi.pad, st, split));
+        }
+        if (!forked) {
+            const snt_status s3 = fork_r3();
+            if (s3 != SNT_OK) return s3;
+            forked = true;
+        }
         if (tm) SNT_CUDA(cudaEventRecord(ev[4], st));
         int16_t *root = nodes + (size_t)t.off[L] * pi.pad;
         SNT_CUDA(launch_rq_inv_jump<P>(1, root, pi.pad, root, pi.pad, nullptr, ctx->d_err, ERR_ROOT,
                                        st));
         if (tm) SNT_CUDA(cudaEventRecord(ev[5], st));
-        for (int l = L; l >= 1; --l)
+        for (int l = L; l >= 1; --l) {
+            if (mode == 2 && !joined && t.n[l] >= kNarrow) {
+                SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+                joined = true;
+            }
             SNT_CUDA(launch_tree_down<P>(nodes + (size_t)t.off[l] * pi.pad,
                                          nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1], st,
-                                         ctx->tree_split));
+                                         split));
+        }
         if (tm) SNT_CUDA(cudaEventRecord(ev[6], st));
     } else {
         SNT_CUDA(launch_rq_inv<P>(Bi, leaves, pi.pad, leaves, pi.pad, nullptr, ctx->d_err, ERR_ROOT,
@@ -138,7 +193,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
             SNT_CUDA(cudaEventRecord(ev[6], st));
         }
     }
-    if (overlap) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    if (!joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     if (tm) SNT_CUDA(cudaEventRecord(ev[7], st));
     SNT_CUDA(launch_finalize<P>(Bi, gbuf, leaves, pk, pi.pk_bytes, sk, pi.sk_bytes, 2 * sb,
                                 pi.sched, st));
@@ -221,7 +276,9 @@ snt_status snt_ctx_create(int device, size_t mem_budget, snt_ctx **out) {
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_low);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->tree, cudaStreamNonBlocking, prio_high);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->tune, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_r3fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     for (int i = 0; i < kPhaseEvents && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev_phase[i]);
@@ -251,7 +308,9 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
         if (ctx->ev_phase[i]) cudaEventDestroy(ctx->ev_phase[i]);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
+    if (ctx->ev_r3fork) cudaEventDestroy(ctx->ev_r3fork);
     if (ctx->tree) cudaStreamDestroy(ctx->tree);
+    if (ctx->tune) cudaStreamDestroy(ctx->tune);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     delete ctx;
@@ -402,7 +461,7 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             ctx->tree_split = value;
             return SNT_OK;
         case SNT_OPT_R3_OVERLAP:
-            if (value != 0 && value != 1) return set_error(SNT_EINVAL, "R/3 overlap is 0 or 1");
+            if (value < 0 || value > 2) return set_error(SNT_EINVAL, "R/3 overlap is 0, 1 or 2");
             ctx->r3_overlap = value;
             return SNT_OK;
         default:
@@ -418,6 +477,61 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
         case SNT_OPT_R3_OVERLAP: *value = ctx->r3_overlap; return SNT_OK;
         default: return set_error(SNT_EINVAL, "unknown option %d", option);
     }
+}
+
+snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *split_out,
+                        int *overlap_out) {
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
+    ParamInfo pi;
+    if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
+    if (B == 0 || B > kMaxB) return set_error(SNT_EINVAL, "batch size %zu out of range", B);
+    if (keygen_scratch(pi, B, true) > ctx->budget)
+        return set_error(SNT_ENOMEM, "batch of %zu keys exceeds the budget", B);
+    DeviceGuard dg(ctx->device);
+    // staging for the keys inside the arena (as for the host-buffer call)
+    const Tree t = make_tree(B);
+    const size_t o = align256(t.total * pi.pad * sizeof(int16_t)) + align256(B * pi.pad);
+    uint8_t *dpk = ctx->arena + o, *dsk = ctx->arena + o + align256(B * pi.pk_bytes);
+    snt_stream ts = reinterpret_cast<snt_stream>(ctx->tune);
+    cudaEvent_t e0, e1;
+    SNT_CUDA(cudaEventCreate(&e0));
+    SNT_CUDA(cudaEventCreate(&e1));
+    const snt_ctx::Tuned saved = ctx->tuned[pidx(P)][bbucket(B)];
+    snt_ctx::Tuned best;
+    float best_ms = 1e30f;
+    const int lanes_c[] = {4, 8, 32}, split_c[] = {4, 8}, overlap_c[] = {0, 1, 2};
+    snt_status st = SNT_OK;
+    for (int la : lanes_c)
+        for (int sp : split_c)
+            for (int ov : overlap_c) {
+                snt_ctx::Tuned cand;
+                cand.lanes = la; cand.split = sp; cand.overlap = ov;
+                ctx->tuned[pidx(P)][bbucket(B)] = cand;
+                float best_c = 1e30f;
+                for (int rep = 0; rep < 4 && st == SNT_OK; ++rep) {
+                    if (cudaEventRecord(e0, ctx->tune) != cudaSuccess) { st = SNT_ECUDA; break; }
+                    st = keygen_common(ctx, P, 0x5eed, (uint64_t)rep * B, B, dpk, dsk, ts, true, false);
+                    if (st != SNT_OK) break;
+                    if (cudaEventRecord(e1, ctx->tune) != cudaSuccess ||
+                        cudaEventSynchronize(e1) != cudaSuccess) { st = SNT_ECUDA; break; }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0 && ms < best_c) best_c = ms;  // first run warms up
+                }
+                if (st != SNT_OK) break;
+                if (best_c < best_ms) { best_ms = best_c; best = cand; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SNT_OK) {
+        ctx->tuned[pidx(P)][bbucket(B)] = saved;
+        return st;
+    }
+    ctx->tuned[pidx(P)][bbucket(B)] = best;
+    if (lanes_out) *lanes_out = best.lanes;
+    if (split_out) *split_out = best.split;
+    if (overlap_out) *overlap_out = best.overlap;
+    return snt_ctx_sync(ctx, ts);
 }
 
 snt_status snt_ctx_set_timing(snt_ctx *ctx, int on) {

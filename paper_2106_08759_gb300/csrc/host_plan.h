@@ -14,7 +14,7 @@
 namespace snt {
 
 // Defaults of the tuning options (snt_ctx_set_option).
-constexpr int kDefaultR3Lanes = 8;     // lanes per element of the R/3 divstep kernel
+constexpr int kDefaultR3Lanes = 4;     // lanes per element of the R/3 divstep kernel
 constexpr int kDefaultTreeSplit = 8;   // largest split of one product over thread groups
 constexpr int kDefaultR3Overlap = 1;   // R/3 on its own low-priority stream
 

@@ -51,6 +51,18 @@ __device__ __forceinline__ void f3_add(uint32_t am, uint32_t as, uint32_t bm, ui
     rs = (am & (as ^ bm)) | (~am & bs);
 }
 
+// (a, b) <- (b, a) if sw == 1, unchanged if sw == 0, with three IMADs.
+// neg1 holds 0xffffffff in a register the compiler cannot see through, so
+// the first product stays an IMAD too.
+__device__ __forceinline__ void cswap_fma(uint32_t &a, uint32_t &b, uint32_t sw, uint32_t neg1) {
+    uint32_t d, na, nb;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(neg1), "r"(b));     // b - a
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(na) : "r"(d), "r"(sw), "r"(a));      // a + d sw
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(nb) : "r"(d), "r"(0u - sw), "r"(b)); // b - d sw
+    a = na;
+    b = nb;
+}
+
 // 2p - 1 divsteps on this group's state.  In: planes of G (reversed g).
 // Out: planes of 1/g in reversed order (trit j is coefficient p-1-j of 1/g).
 // Returns true iff g is invertible.  All 32 lanes of the warp must call it.
@@ -75,6 +87,8 @@ __device__ __forceinline__ bool r3_divsteps(uint32_t (&gm)[R3Geo<P, LKT>::WL],
     }
     int delta = 1;
     uint32_t f0s = 0;  // sign bit of F(0); F(0) is never zero
+    uint32_t neg1;
+    asm volatile("mov.u32 %0, 0xffffffff;" : "=r"(neg1));
 #pragma unroll 1
     for (int step = 0; step < 2 * P - 1; ++step) {
         // V <- x V: carry the top trit of each lane into the next lane
@@ -92,15 +106,15 @@ __device__ __forceinline__ bool r3_divsteps(uint32_t (&gm)[R3Geo<P, LKT>::WL],
         const uint32_t g0 = __shfl_sync(FULL, (gm[0] & 1u) | ((gs[0] & 1u) << 1), 0, LK);
         const uint32_t g0m = g0 & 1u, g0s = g0 >> 1;
         const uint32_t sw = (uint32_t)(delta > 0) & g0m;
-        const uint32_t msk = 0u - sw;
+        // Conditional swaps as integer multiply-adds, a + (b - a) * sw with sw
+        // in {0, 1} (exact modulo 2^32): they run on the FMA pipe, which the
+        // bit operations of the F_3 arithmetic leave idle.
 #pragma unroll
         for (int w = 0; w < WL; ++w) {
-            const uint32_t nfm = (gm[w] & msk) | (fm[w] & ~msk), ngm = (fm[w] & msk) | (gm[w] & ~msk);
-            const uint32_t nfs = (gs[w] & msk) | (fs[w] & ~msk), ngs = (fs[w] & msk) | (gs[w] & ~msk);
-            const uint32_t nvm = (rm[w] & msk) | (vm[w] & ~msk), nrm = (vm[w] & msk) | (rm[w] & ~msk);
-            const uint32_t nvs = (rs[w] & msk) | (vs[w] & ~msk), nrs = (vs[w] & msk) | (rs[w] & ~msk);
-            fm[w] = nfm; gm[w] = ngm; fs[w] = nfs; gs[w] = ngs;
-            vm[w] = nvm; rm[w] = nrm; vs[w] = nvs; rs[w] = nrs;
+            cswap_fma(fm[w], gm[w], sw, neg1);
+            cswap_fma(fs[w], gs[w], sw, neg1);
+            cswap_fma(vm[w], rm[w], sw, neg1);
+            cswap_fma(vs[w], rs[w], sw, neg1);
         }
         const uint32_t nf0s = sw ? g0s : f0s;
         const uint32_t ng0s = sw ? f0s : g0s;  // G(0) stays nonzero iff it was

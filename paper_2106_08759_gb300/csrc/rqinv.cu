@@ -121,116 +121,239 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 // Jump divsteps (latency-optimised form for the single root inversion).
 //
 // The first m divsteps of (delta, F, G) depend only on delta and the low m
-// coefficients of F and G.  So warp 0 runs a chunk of m <= 31 steps on those
-// coefficients alone (one coefficient per lane, shuffles for the shifts and
-// for F(0), G(0)) and accumulates the chunk's transition matrix
+// coefficients of F and G.  A leader warp runs a chunk of m <= 31 steps on
+// those coefficients alone (one coefficient per lane, shuffles for the shifts
+// and G(0)) and accumulates the chunk's transition matrix
 //     x^m (F', G') = A (F, G),   A = [[u, v], [w, z]],  deg <= m,
 // built step by step as  row1 <- x * row1,  row2 <- F(0) row2 - G(0) row1
-// (rows exchanged first when the step swaps).  The whole CTA then applies A:
+// (rows exchanged first when the step swaps).  The other warps apply A:
 //     F' = (u F + v G) / x^m,   G' = (w F + z G) / x^m,
 //     V' = u V + (v / x) R,     R' = x w V + z R,
 // the last two because V is multiplied by x before each step's swap, which
-// conjugates A by diag(1, x).  2p - 1 steps take ceil((2p-1)/31) chunks and
-// as many barriers, instead of one barrier per step.  All values are kept
-// centred, so a 64-term application sum stays below 2^31.
+// conjugates A by diag(1, x).  The chunks are pipelined: while the appliers
+// apply chunk c, the leader computes the 32 low coefficients of F', G' itself
+// and runs the divsteps of chunk c + 1, so a chunk costs about the larger of
+// the two.  One barrier per chunk, ceil((2p-1)/31) chunks.
+//
+// Ranges: inside the leader's steps values are lazily reduced to [-q, 2q)
+// (G(0) = 0 mod q iff G(0) is -q, 0 or q); the matrix and the state are
+// centred between chunks, so a 64-term application sum stays below 2^31.
 // ---------------------------------------------------------------------------
 template <int P> struct JumpGeo {
-    static constexpr int M = 31;              // steps per chunk
-    static constexpr int OFF = 32;            // zero margin below index 0
-    static constexpr int LEN = OFF + P + 1 + 32;
+    static constexpr int M = 31;                        // steps per chunk
+    static constexpr int OFF = 32;                      // zero margin below index 0
+    static constexpr int TILES = (P + 1 + 7) / 8;       // 8 outputs per applier thread
+    static constexpr int NAPP = (TILES + 31) / 32 * 32; // applier threads
+    static constexpr int NT = 32 + NAPP;                // + the leader warp
+    static constexpr int LEN = OFF + 8 * TILES + 40;    // logical slots per polynomial
+    static constexpr int PLEN = LEN + LEN / 8 + 1;      // physical slots (one pad per 8)
 };
 
-template <int P, int NT>
-__global__ void __launch_bounds__(NT)
+// Physical slot of logical slot i: one padding word after every 8, so the
+// applier threads (8 consecutive outputs each) read banks 9 words apart,
+// i.e. 32 distinct banks per warp instead of 4.
+__device__ __forceinline__ int slot(int i) { return i + (i >> 3); }
+
+template <int Q> __device__ __forceinline__ bool is_zero_lazy(int x) {  // x in [-Q, 2Q)
+    return x == 0 || x == Q || x == -Q;
+}
+
+// The leader's chunk: m divsteps from (fl, gl) (lane i = coefficient i),
+// matrix returned centred in (u, v, w, z) (lane k = coefficient k).
+template <int Q>
+__device__ __forceinline__ void leader_chunk(int m, int &delta, int fl, int gl, int &u, int &v,
+                                             int &w, int &z) {
+    const int lane = threadIdx.x & 31;
+    u = (lane == 0); v = 0; w = 0; z = (lane == 0);
+    int f0 = __shfl_sync(0xffffffffu, fl, 0);
+    int g0 = __shfl_sync(0xffffffffu, gl, 0);
+    for (int s = 0; s < m; ++s) {
+        if (delta > 0 && !is_zero_lazy<Q>(g0)) {  // warp-uniform
+            int t = fl; fl = gl; gl = t;
+            t = u; u = w; w = t;
+            t = v; v = z; z = t;
+            t = f0; f0 = g0; g0 = t;
+            delta = -delta;
+        }
+        ++delta;
+        const int nw = lazy_red<Q>(f0 * w - g0 * u);
+        const int nz = lazy_red<Q>(f0 * z - g0 * v);
+        const int ng = lazy_red<Q>(f0 * gl - g0 * fl);
+        u = __shfl_up_sync(0xffffffffu, u, 1);
+        v = __shfl_up_sync(0xffffffffu, v, 1);
+        if (lane == 0) { u = 0; v = 0; }
+        w = nw;
+        z = nz;
+        // next G(0) is coefficient 1 of the updated G: broadcast it directly,
+        // off the path of the full shift
+        g0 = __shfl_sync(0xffffffffu, ng, 1);
+        gl = __shfl_down_sync(0xffffffffu, ng, 1);
+        if (lane == 31) gl = 0;
+    }
+    u = cmod<Q>(u); v = cmod<Q>(v); w = cmod<Q>(w); z = cmod<Q>(z);
+}
+
+template <int P>
+__global__ void __launch_bounds__(JumpGeo<P>::NT)
 k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_stride,
               int32_t *__restrict__ okv, int *__restrict__ err, int err_bit) {
     constexpr int Q = Geo<P>::q;
-    constexpr int LEN = JumpGeo<P>::LEN, OFF = JumpGeo<P>::OFF;
-    __shared__ int st[2][4][LEN];  // [buffer][F, G, V, R][index + OFF]
-    __shared__ int mat[4][33];     // u, v, w, z (coefficient 32 stays zero)
+    using JG = JumpGeo<P>;
+    constexpr int LEN = JG::LEN, OFF = JG::OFF, NT = JG::NT;
+    constexpr int NCH = (2 * P - 1 + JG::M - 1) / JG::M;
+    __shared__ int st[2][4][JG::PLEN];  // [buffer][F, G, V, R][slot(index + OFF)]
+    __shared__ int mat[2][4][34];       // [buffer][u, v, w, z][1 + coefficient], zero at 0 and 33
     __shared__ int s_ok;
     const int e = blockIdx.x;
     if (e >= n) return;
     const int tid = threadIdx.x, lane = tid & 31;
+    const bool leader = tid < 32;
     const int16_t *a = in + (size_t)e * in_stride;
-    for (int i = tid; i < 2 * 4 * LEN; i += NT) (&st[0][0][0])[i] = 0;
-    if (tid < 4) mat[tid][32] = 0;
+    for (int i = tid; i < 2 * 4 * JG::PLEN; i += NT) (&st[0][0][0])[i] = 0;
+    for (int i = tid; i < 2 * 4 * 34; i += NT) (&mat[0][0][0])[i] = 0;
     __syncthreads();
-    for (int i = tid; i < P; i += NT) st[0][1][OFF + i] = (int)a[P - 1 - i];
+    for (int i = tid; i < P; i += NT) st[0][1][slot(OFF + i)] = (int)a[P - 1 - i];
     if (tid == 0) {
-        st[0][0][OFF] = 1;
-        st[0][0][OFF + P - 1] = -1;
-        st[0][0][OFF + P] = -1;
-        st[0][3][OFF] = 1;
+        st[0][0][slot(OFF)] = 1;
+        st[0][0][slot(OFF + P - 1)] = -1;
+        st[0][0][slot(OFF + P)] = -1;
+        st[0][3][slot(OFF)] = 1;
     }
     __syncthreads();
-    int delta = 1;  // used by warp 0 only
+    int delta = 1;  // leader only
+    if (leader) {
+        int u, v, w, z;
+        leader_chunk<Q>(min(JG::M, 2 * P - 1), delta, st[0][0][slot(OFF + lane)],
+                        st[0][1][slot(OFF + lane)], u, v, w, z);
+        mat[0][0][1 + lane] = u; mat[0][1][1 + lane] = v;
+        mat[0][2][1 + lane] = w; mat[0][3][1 + lane] = z;
+    }
+    __syncthreads();
     int cur = 0;
-    for (int done = 0; done < 2 * P - 1; done += JumpGeo<P>::M) {
-        const int m = min(JumpGeo<P>::M, 2 * P - 1 - done);
-        if (tid < 32) {
-            int fl = st[cur][0][OFF + lane], gl = st[cur][1][OFF + lane];
-            int u = (lane == 0), v = 0, w = 0, z = (lane == 0);
-            for (int s = 0; s < m; ++s) {
-                int f0 = __shfl_sync(0xffffffffu, fl, 0);
-                int g0 = __shfl_sync(0xffffffffu, gl, 0);
-                if (delta > 0 && g0 != 0) {  // warp-uniform
-                    int t = fl; fl = gl; gl = t;
-                    t = u; u = w; w = t;
-                    t = v; v = z; z = t;
-                    t = f0; f0 = g0; g0 = t;
-                    delta = -delta;
-                }
-                ++delta;
-                const int nw = cmod<Q>(f0 * w - g0 * u);
-                const int nz = cmod<Q>(f0 * z - g0 * v);
-                u = __shfl_up_sync(0xffffffffu, u, 1);
-                v = __shfl_up_sync(0xffffffffu, v, 1);
-                if (lane == 0) { u = 0; v = 0; }
-                w = nw;
-                z = nz;
-                const int ng = cmod<Q>(f0 * gl - g0 * fl);
-                gl = __shfl_down_sync(0xffffffffu, ng, 1);
-                if (lane == 31) gl = 0;
-            }
-            mat[0][lane] = u;
-            mat[1][lane] = v;
-            mat[2][lane] = w;
-            mat[3][lane] = z;
-        }
-        __syncthreads();
+    for (int c = 0; c < NCH; ++c) {
+        const int m = min(JG::M, 2 * P - 1 - c * JG::M);
         const int *F = st[cur][0], *G = st[cur][1], *V = st[cur][2], *R = st[cur][3];
-        int *F2 = st[cur ^ 1][0], *G2 = st[cur ^ 1][1], *V2 = st[cur ^ 1][2], *R2 = st[cur ^ 1][3];
-        for (int i = tid; i <= P; i += NT) {
-            int af = 0, ag = 0, av = 0, ar = 0;
-            const int hi = OFF + i + m, lo = OFF + i;
+        const int(*A)[34] = mat[c & 1];
+        if (leader) {
+            if (c + 1 < NCH) {
+                // low 32 coefficients of F', G' (lane i), then chunk c + 1
+                int af = 0, ag = 0;
+                const int hi = OFF + lane + m;
 #pragma unroll 8
-            for (int k = 0; k < 32; ++k) {
-                const int uk = mat[0][k], vk = mat[1][k], wk = mat[2][k], zk = mat[3][k];
-                const int fv = F[hi - k], gv = G[hi - k];
-                af += uk * fv + vk * gv;
-                ag += wk * fv + zk * gv;
-                const int vv = V[lo - k], rv = R[lo - k];
-                const int vk1 = mat[1][k + 1], wkm = (k > 0) ? mat[2][k - 1] : 0;
-                av += uk * vv + vk1 * rv;
-                ar += wkm * vv + zk * rv;
+                for (int k = 0; k < 32; ++k) {
+                    const int fv = F[slot(hi - k)], gv = G[slot(hi - k)];
+                    af += A[0][1 + k] * fv + A[1][1 + k] * gv;
+                    ag += A[2][1 + k] * fv + A[3][1 + k] * gv;
+                }
+                const int m1 = min(JG::M, 2 * P - 1 - (c + 1) * JG::M);
+                int u, v, w, z;
+                leader_chunk<Q>(m1, delta, cmod<Q>(af), cmod<Q>(ag), u, v, w, z);
+                int(*An)[34] = mat[(c + 1) & 1];
+                An[0][1 + lane] = u; An[1][1 + lane] = v;
+                An[2][1 + lane] = w; An[3][1 + lane] = z;
+            } else if (lane == 0) {
+                s_ok = (delta == 0);
             }
-            F2[OFF + i] = cmod<Q>(af);
-            G2[OFF + i] = cmod<Q>(ag);
-            V2[OFF + i] = cmod<Q>(av);
-            R2[OFF + i] = cmod<Q>(ar);
+        } else {
+            const int tile = tid - 32;
+            if (tile < JG::TILES) {
+                const int i0 = 8 * tile;
+                int *F2 = st[cur ^ 1][0], *G2 = st[cur ^ 1][1], *V2 = st[cur ^ 1][2], *R2 = st[cur ^ 1][3];
+                // F' = (u F + v G) / x^m, G' = (w F + z G) / x^m : index i + m - k
+                {
+                    int aF[8], aG[8], fhi[8], ghi[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        aF[t] = 0; aG[t] = 0;
+                        fhi[t] = F[slot(OFF + i0 + m + t)];
+                        ghi[t] = G[slot(OFF + i0 + m + t)];
+                    }
+#pragma unroll 1
+                    for (int kb = 0; kb < 32; kb += 8) {
+                        const int b0 = OFF + i0 + m - kb;
+                        int flo[8], glo[8], uu[8], vv[8], ww[8], zz[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            flo[j] = F[slot(b0 - 8 + j)];
+                            glo[j] = G[slot(b0 - 8 + j)];
+                            uu[j] = A[0][1 + kb + j];
+                            vv[j] = A[1][1 + kb + j];
+                            ww[j] = A[2][1 + kb + j];
+                            zz[j] = A[3][1 + kb + j];
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk)
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) {
+                                const int d = t - kk;
+                                const int fv = d >= 0 ? fhi[d] : flo[8 + d];
+                                const int gv = d >= 0 ? ghi[d] : glo[8 + d];
+                                aF[t] += uu[kk] * fv + vv[kk] * gv;
+                                aG[t] += ww[kk] * fv + zz[kk] * gv;
+                            }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) { fhi[j] = flo[j]; ghi[j] = glo[j]; }
+                    }
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        if (i0 + t <= P) {
+                            F2[slot(OFF + i0 + t)] = cmod<Q>(aF[t]);
+                            G2[slot(OFF + i0 + t)] = cmod<Q>(aG[t]);
+                        }
+                }
+                // V' = u V + (v/x) R, R' = (x w) V + z R : index i - k
+                {
+                    int aV[8], aR[8], vhi[8], rhi[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        aV[t] = 0; aR[t] = 0;
+                        vhi[t] = V[slot(OFF + i0 + t)];
+                        rhi[t] = R[slot(OFF + i0 + t)];
+                    }
+#pragma unroll 1
+                    for (int kb = 0; kb < 32; kb += 8) {
+                        const int b0 = OFF + i0 - kb;
+                        int vlo[8], rlo[8], uu[8], vs[8], ws[8], zz[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            vlo[j] = V[slot(b0 - 8 + j)];
+                            rlo[j] = R[slot(b0 - 8 + j)];
+                            uu[j] = A[0][1 + kb + j];
+                            vs[j] = A[1][2 + kb + j];  // v_{k+1}
+                            ws[j] = A[2][kb + j];      // w_{k-1}
+                            zz[j] = A[3][1 + kb + j];
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk)
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) {
+                                const int d = t - kk;
+                                const int vv = d >= 0 ? vhi[d] : vlo[8 + d];
+                                const int rv = d >= 0 ? rhi[d] : rlo[8 + d];
+                                aV[t] += uu[kk] * vv + vs[kk] * rv;
+                                aR[t] += ws[kk] * vv + zz[kk] * rv;
+                            }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) { vhi[j] = vlo[j]; rhi[j] = rlo[j]; }
+                    }
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        if (i0 + t <= P) {
+                            V2[slot(OFF + i0 + t)] = cmod<Q>(aV[t]);
+                            R2[slot(OFF + i0 + t)] = cmod<Q>(aR[t]);
+                        }
+                }
+            }
         }
         __syncthreads();
         cur ^= 1;
     }
-    if (tid == 0) s_ok = (delta == 0);
-    __syncthreads();
     const bool ok = s_ok != 0;
-    const int f0 = freeze_lazy<Q>(st[cur][0][OFF]);
+    const int f0 = freeze_lazy<Q>(st[cur][0][slot(OFF)]);
     const int sc = ok ? inv_mod<Q>(f0) : 0;
     int16_t *o = out + (size_t)e * out_stride;
     for (int i = tid; i < P; i += NT) {
-        const int v = freeze_lazy<Q>(st[cur][2][OFF + P - 1 - i]);
+        const int v = freeze_lazy<Q>(st[cur][2][slot(OFF + P - 1 - i)]);
         o[i] = (int16_t)cmod<Q>(sc * v);
     }
     if (tid == 0) {
@@ -243,7 +366,8 @@ template <int P>
 cudaError_t launch_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
                                cudaStream_t st) {
-    k_rq_inv_jump<P, 512><<<n, 512, 0, st>>>(n, in, in_stride, out, out_stride, ok, err, err_bit);
+    k_rq_inv_jump<P><<<n, JumpGeo<P>::NT, 0, st>>>(n, in, in_stride, out, out_stride, ok, err,
+                                                   err_bit);
     return cudaGetLastError();
 }
 

@@ -6,73 +6,99 @@
 // stream 1; the first w have bit 0 cleared (low bits decode to -1 or +1),
 // the rest have low bits forced to 01 (decode to 0); the words are sorted as
 // unsigned integers and coefficient j is (word_j mod 4) - 1.  The sort is a
-// 1024-slot bitonic network in shared memory, padded with 0xFFFFFFFF
+// 1024-slot bitonic network, padded with 0xFFFFFFFF
 // (no real word can equal it: bit 0 or bit 1 is cleared).
 #include "common.cuh"
 #include "kernels.h"
 
 namespace snt {
 
+// One CTA of 256 threads per key; thread t holds elements 4t .. 4t+3 of the
+// 1024-slot network in registers.  Compare-exchange partners closer than 4
+// slots are in the same thread, closer than 128 in the same warp (shuffles),
+// farther ones in another warp (exchanged through shared memory, 6 of the 55
+// stages).
 template <int P>
 __global__ void __launch_bounds__(256)
 k_sample_f(uint64_t seed, uint64_t first, int B, int16_t *__restrict__ leaves,
            uint8_t *__restrict__ sk, int sk_bytes, int rho_off) {
     using G = Geo<P>;
-    __shared__ uint32_t s[1024];
+    __shared__ __align__(16) uint32_t xs[1024];
     const int key = blockIdx.x;
     if (key >= B) return;
     const uint64_t k = first + (uint64_t)key;
-    const int tid = threadIdx.x;
+    const int t = threadIdx.x;
 
     // words of stream 1, low bits forced; sentinels above p
-    for (int blk = tid; blk < 256; blk += blockDim.x) {
-        uint32_t r[4] = {0u, 0u, 0u, 0u};
-        if (4 * blk < G::p) rand_block(seed, k, STREAM_F, 0u, (uint32_t)blk, r);
+    uint32_t v[4] = {0u, 0u, 0u, 0u};
+    if (4 * t < G::p) rand_block(seed, k, STREAM_F, 0u, (uint32_t)t, v);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int idx = 4 * blk + j;
-            uint32_t v;
-            if (idx < G::w) v = r[j] & ~1u;
-            else if (idx < G::p) v = (r[j] & ~3u) | 1u;
-            else v = 0xFFFFFFFFu;
-            s[idx] = v;
-        }
+    for (int r = 0; r < 4; ++r) {
+        const int idx = 4 * t + r;
+        if (idx < G::w) v[r] = v[r] & ~1u;
+        else if (idx < G::p) v[r] = (v[r] & ~3u) | 1u;
+        else v[r] = 0xFFFFFFFFu;
     }
-    __syncthreads();
 
-    // ascending bitonic sort of 1024 words
+    // ascending bitonic sort of the 1024 slots
+#pragma unroll 1
     for (int size = 2; size <= 1024; size <<= 1) {
+#pragma unroll 1
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = tid; t < 512; t += blockDim.x) {
-                const int lo = 2 * t - (t & (stride - 1));
-                const int hi = lo + stride;
-                const bool asc = (lo & size) == 0;
-                const uint32_t a = s[lo], b = s[hi];
-                if ((a > b) == asc) { s[lo] = b; s[hi] = a; }
+            if (stride >= 4) {
+                uint32_t o[4];
+                if (stride >= 128) {
+                    *reinterpret_cast<uint4 *>(&xs[4 * t]) = make_uint4(v[0], v[1], v[2], v[3]);
+                    __syncthreads();
+                    const uint4 q = *reinterpret_cast<const uint4 *>(&xs[4 * (t ^ (stride >> 2))]);
+                    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+                    __syncthreads();
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) o[r] = __shfl_xor_sync(0xffffffffu, v[r], stride >> 2);
+                }
+                const int i = 4 * t;  // same relation for all four slots of this thread
+                const bool asc = (i & size) == 0;
+                const bool low = (i & stride) == 0;  // this slot is the lower one of its pair
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const uint32_t mn = min(v[r], o[r]), mx = max(v[r], o[r]);
+                    v[r] = (low == asc) ? mn : mx;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const bool asc = ((4 * t + r) & size) == 0;  // size 2 depends on r
+                    if ((r & stride) == 0) {
+                        const uint32_t a = v[r], b = v[r | stride];
+                        const bool sw = (a > b) == asc;
+                        v[r] = sw ? b : a;
+                        v[r | stride] = sw ? a : b;
+                    }
+                }
             }
-            __syncthreads();
         }
     }
 
     // leaves a = 3f (centred int16), zero padded to G::pad
     int16_t *leaf = leaves + (size_t)key * G::pad;
-    for (int j = tid; j < G::pad; j += blockDim.x)
-        leaf[j] = (int16_t)(j < G::p ? 3 * ((int)(s[j] & 3u) - 1) : 0);
-
-    // Small_encode(f): byte b packs coefficients 4b..4b+3 as (c + 1) in 2 bits
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int j = 4 * t + r;
+        if (j < G::pad) leaf[j] = (int16_t)(j < G::p ? 3 * ((int)(v[r] & 3u) - 1) : 0);
+    }
+    // Small_encode(f): byte t packs coefficients 4t..4t+3 as (c + 1) in 2 bits
     uint8_t *skk = sk + (size_t)key * sk_bytes;
-    for (int b = tid; b < G::small_bytes; b += blockDim.x) {
+    if (t < G::small_bytes) {
         uint32_t byte = 0;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int idx = 4 * b + t;
-            if (idx < G::p) byte |= (s[idx] & 3u) << (2 * t);
-        }
-        skk[b] = (uint8_t)byte;
+        for (int r = 0; r < 4; ++r)
+            if (4 * t + r < G::p) byte |= (v[r] & 3u) << (2 * r);
+        skk[t] = (uint8_t)byte;
     }
 
     // rho: small_bytes bytes of stream 2, little-endian within each word
-    for (int blk = tid; 16 * blk < G::small_bytes; blk += blockDim.x) {
+    for (int blk = t; 16 * blk < G::small_bytes; blk += blockDim.x) {
         uint32_t r[4];
         rand_block(seed, k, STREAM_RHO, 0u, (uint32_t)blk, r);
 #pragma unroll

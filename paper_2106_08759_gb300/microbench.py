@@ -122,9 +122,9 @@ def main():
     out["keygen_4096_ms"] = tot / args.reps
     if args.sweep:
         sweep = {}
-        for overlap in (0, 1):
-            for lanes in (4, 8, 32):
-                for split in (1, 8):
+        for overlap in (0, 1, 2):
+            for lanes in (4, 8):
+                for split in (4, 8):
                     ctx.set_option(snt.SNT_OPT_R3_OVERLAP, overlap)
                     ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
                     ctx.set_option(snt.SNT_OPT_TREE_SPLIT, split)

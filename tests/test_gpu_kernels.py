@@ -107,7 +107,7 @@ def test_r3_inv_matches_oracle(snt, ctx, P, lanes):
     try:
         snt.snt_r3_inv(ctx, P, n, _t(g.ravel(), torch.int8), out, ok)
     finally:
-        ctx.set_option(snt.SNT_OPT_R3_LANES, 8)
+        ctx.set_option(snt.SNT_OPT_R3_LANES, 4)
     got = out.cpu().numpy().reshape(n, p)
     okh = ok.cpu().numpy()
     assert okh[2] == 0 and okh[0] == 0

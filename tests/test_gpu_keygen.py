@@ -56,7 +56,7 @@ def test_ragged_tree_shapes(snt, ctx, B):
     assert first_mismatch(sk, rsk) is None
 
 
-@pytest.mark.parametrize("opts", [(4, 8, 1), (8, 1, 0), (32, 2, 1), (4, 4, 0)])
+@pytest.mark.parametrize("opts", [(4, 8, 1), (8, 1, 0), (32, 2, 2), (4, 4, 0), (8, 8, 2)])
 def test_tuning_options_do_not_change_keys(snt, ctx, opts):
     # R/3 lanes per element, tree split, R/3 overlap: layouts only
     lanes, split, overlap = opts
@@ -68,12 +68,21 @@ def test_tuning_options_do_not_change_keys(snt, ctx, opts):
         got = gpu_keygen(snt, ctx, 761, 21, 300, 45)
         got857 = gpu_keygen(snt, ctx, 857, 22, 0, 19)
     finally:
-        ctx.set_option(snt.SNT_OPT_R3_LANES, 8)
+        ctx.set_option(snt.SNT_OPT_R3_LANES, 4)
         ctx.set_option(snt.SNT_OPT_TREE_SPLIT, 8)
         ctx.set_option(snt.SNT_OPT_R3_OVERLAP, 1)
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
     rpk, rsk = oracle.keygen_batch(857, 22, 0, 19)
     assert first_mismatch(got857[0], rpk) is None and first_mismatch(got857[1], rsk) is None
+
+
+def test_autotuned_layouts_give_the_same_keys(snt):
+    with snt.Context(0, 64 << 20) as c:
+        choice = c.autotune(761, 48)
+        assert choice["r3_lanes"] in (4, 8, 32) and choice["r3_overlap"] in (0, 1, 2)
+        pk, sk = gpu_keygen(snt, c, 761, 31, 7, 48)
+    rpk, rsk = oracle.keygen_batch(761, 31, 7, 48)
+    assert first_mismatch(pk, rpk) is None and first_mismatch(sk, rsk) is None
 
 
 def test_split_batches_give_identical_bytes(snt, ctx):
