@@ -91,6 +91,20 @@ snt_status snt_keygen_perkey(snt_ctx *ctx, int P, uint64_t seed,
                              uint64_t first_key_index, size_t B,
                              uint8_t *pk_dev, uint8_t *sk_dev, snt_stream stream);
 
+/* Many batches in one launch (the ragged workload: uneven sizes, mixed
+ * parameter sets).  Batch i has parameter set P[i], B[i] keys with key indices
+ * first_idx[i] + j and seed seeds[i], written to pk_dev[i] / sk_dev[i] (device
+ * pointers, each B[i] * sizes of P[i]).  Every batch gets exactly the bytes
+ * snt_batch_keygen would give it alone: each batch keeps its own Montgomery
+ * product tree (Algorithm 1), while the batches of one parameter set share the
+ * launches, level by level.  The launch sequence of a plan (the list of
+ * (P[i], B[i])) is captured into a CUDA graph on first use and replayed while
+ * the plan repeats.  Asynchronous on `stream`; 1 <= n_batches <= 65536. */
+snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, const int *P,
+                                   const size_t *B, const uint64_t *seeds,
+                                   const uint64_t *first_idx, uint8_t *const *pk_dev,
+                                   uint8_t *const *sk_dev, snt_stream stream);
+
 /* Host-memory convenience form of snt_batch_keygen: generates on the device,
  * copies B * pk_bytes and B * sk_bytes into the caller's host buffers and
  * returns when they are complete (synchronous; includes snt_ctx_sync). */

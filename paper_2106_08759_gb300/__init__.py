@@ -62,6 +62,7 @@ def load():
         "snt_keygen_perkey": [P, i32, u64, u64, sz, P, P, P],
         "snt_batch_keygen_host": [P, i32, u64, u64, sz, P, P],
         "snt_batch_keygen_static": [i32, i32, u64, u64, sz, P, P, P],
+        "snt_batch_keygen_ragged": [P, sz, P, P, P, P, P, P, P],
         "snt_rq_mul": [P, i32, sz, P, P, P, P],
         "snt_rq_inv": [P, i32, sz, P, P, P, P],
         "snt_rq_inv_latency": [P, i32, sz, P, P, P, P],
@@ -196,6 +197,23 @@ def snt_keygen_perkey(ctx, P, seed, first_key_index, B, pk, sk, stream=None):
     _check(load().snt_keygen_perkey(ctx.handle, P, seed, first_key_index, B,
                                     _dptr(pk, torch.uint8), _dptr(sk, torch.uint8),
                                     _stream(stream)))
+
+
+def snt_batch_keygen_ragged(ctx, Ps, Bs, seeds, firsts, pks, sks, stream=None):
+    """Many batches (mixed sizes and parameter sets) in one graph launch.
+
+    pks / sks: lists of uint8 CUDA tensors, one per batch."""
+    import torch
+    n = len(Ps)
+    assert len(Bs) == n and len(seeds) == n and len(firsts) == n and len(pks) == n and len(sks) == n
+    P_arr = (ctypes.c_int * n)(*[int(x) for x in Ps])
+    B_arr = (ctypes.c_size_t * n)(*[int(x) for x in Bs])
+    S_arr = (ctypes.c_uint64 * n)(*[int(x) for x in seeds])
+    F_arr = (ctypes.c_uint64 * n)(*[int(x) for x in firsts])
+    PK = (ctypes.c_void_p * n)(*[_dptr(t, torch.uint8).value for t in pks])
+    SK = (ctypes.c_void_p * n)(*[_dptr(t, torch.uint8).value for t in sks])
+    _check(load().snt_batch_keygen_ragged(ctx.handle, n, P_arr, B_arr, S_arr, F_arr, PK, SK,
+                                          _stream(stream)))
 
 
 def snt_batch_keygen_static(device, P, seed, first_key_index, B, pk, sk, stream=None):

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "ctx.h"
 #include "host_plan.h"
 #include "kernels.h"
 #include "sntrup_gb300.h"
@@ -50,48 +51,8 @@ snt_status cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 
-constexpr int kMaxInject = 64;
-// Phase events of one keygen call (snt_ctx_set_timing): on the main stream
-// 0 start, 1 after sampling f, 4 after the up-sweep (or per-key R/q
-// inversions), 5 after the root, 6 after the down-sweep, 7 after the join,
-// 8 after h/encode, 9 after SHA-512; on the auxiliary stream 2 / 3 around the
-// R/3 kernel.
-constexpr int kPhaseEvents = 10;
-constexpr size_t kMaxB = (size_t)1 << 24;
-
 }  // namespace
 
-struct snt_ctx {
-    int device = 0;
-    size_t budget = 0;
-    uint8_t *arena = nullptr;
-    int *d_err = nullptr;
-    uint64_t *d_inj_idx = nullptr;
-    int8_t *d_inj_g = nullptr;
-    int n_inj = 0;
-    int inj_P = 0;
-    cudaStream_t aux = nullptr;   // low priority: per-key R/3 inversions
-    cudaStream_t tree = nullptr;  // high priority: sampling, product tree, h, hash
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr, ev_r3fork = nullptr;
-    bool timing = false;
-    cudaEvent_t ev_phase[kPhaseEvents] = {};
-    int r3_lanes = kDefaultR3Lanes;
-    int tree_split = kDefaultTreeSplit;
-    int r3_overlap = kDefaultR3Overlap;
-    // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
-    struct Tuned { int lanes = 0, split = 0, overlap = 0; };
-    Tuned tuned[3][25];
-    cudaStream_t tune = nullptr;  // stream used while autotuning
-};
-
-namespace {
-int pidx(int P) { return P == 653 ? 0 : P == 761 ? 1 : 2; }
-int bbucket(size_t B) {
-    int b = 0;
-    while (((size_t)1 << b) < B && b < 24) ++b;
-    return b;
-}
-}  // namespace
 
 namespace {
 
@@ -104,6 +65,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     int16_t *leaves = nodes;
     const int Bi = (int)B;
     const int sb = pi.small_bytes;
+    const KeyMap km = single_batch(seed, first, Bi, pk, sk);
     cudaEvent_t *ev = ctx->ev_phase;
     const bool tm = ctx->timing;
     // Fork from the caller's stream.  The tree branch runs on the context's
@@ -126,8 +88,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     const int n_inj = (ctx->inj_P == P) ? ctx->n_inj : 0;
     auto launch_r3 = [&](cudaStream_t r3s) -> snt_status {
         if (tm) SNT_CUDA(cudaEventRecord(ev[2], r3s));
-        SNT_CUDA(launch_r3_keygen<P>(seed, first, Bi, gbuf, sk, pi.sk_bytes, sb, ctx->d_inj_idx,
-                                     ctx->d_inj_g, n_inj, ctx->d_err, r3s, lanes));
+        SNT_CUDA(launch_r3_keygen<P>(km, Bi, gbuf, pi.sk_bytes, sb, ctx->d_inj_idx, ctx->d_inj_g,
+                                     n_inj, ctx->d_err, r3s, lanes));
         if (tm) SNT_CUDA(cudaEventRecord(ev[3], r3s));
         return SNT_OK;
     };
@@ -141,7 +103,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     };
     bool forked = false, joined = false;
     if (tm) SNT_CUDA(cudaEventRecord(ev[0], st));
-    SNT_CUDA(launch_sample_f<P>(seed, first, Bi, leaves, sk, pi.sk_bytes, 2 * sb + pi.pk_bytes, st));
+    SNT_CUDA(launch_sample_f<P>(km, Bi, leaves, pi.sk_bytes, 2 * sb + pi.pk_bytes, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[1], st));
     if (mode == 0) {
         const snt_status s3 = launch_r3(st);
@@ -161,8 +123,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                 if (s3 != SNT_OK) return s3;
                 forked = true;
             }
-            SNT_CUDA(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1],
-                                       nodes + (size_t)t.off[l] * pi.pad, st, split));
+            SNT_CUDA(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad, single_tree(t.n[l - 1]),
+                                       t.n[l], nodes + (size_t)t.off[l] * pi.pad, st, split));
         }
         if (!forked) {
             const snt_status s3 = fork_r3();
@@ -179,9 +141,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                 SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
                 joined = true;
             }
-            SNT_CUDA(launch_tree_down<P>(nodes + (size_t)t.off[l] * pi.pad,
-                                         nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1], st,
-                                         split));
+            SNT_CUDA(launch_tree_down<P>(nodes + (size_t)t.off[l] * pi.pad, single_tree(t.n[l - 1]),
+                                         t.n[l], nodes + (size_t)t.off[l - 1] * pi.pad, st, split));
         }
         if (tm) SNT_CUDA(cudaEventRecord(ev[6], st));
     } else {
@@ -195,10 +156,10 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     }
     if (!joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     if (tm) SNT_CUDA(cudaEventRecord(ev[7], st));
-    SNT_CUDA(launch_finalize<P>(Bi, gbuf, leaves, pk, pi.pk_bytes, sk, pi.sk_bytes, 2 * sb,
-                                pi.sched, st));
+    SNT_CUDA(launch_finalize<P>(km, Bi, gbuf, leaves, pi.pk_bytes, pi.sk_bytes, 2 * sb, pi.sched,
+                                st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[8], st));
-    SNT_CUDA(launch_sha512_pk(Bi, pk, pi.pk_bytes, sk, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
+    SNT_CUDA(launch_sha512_pk(km, Bi, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[9], st));
     // join back into the caller's stream
     SNT_CUDA(cudaEventRecord(ctx->ev_done, st));
@@ -309,6 +270,7 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
     if (ctx->ev_r3fork) cudaEventDestroy(ctx->ev_r3fork);
+    if (ctx->ragged.exec) cudaGraphExecDestroy(ctx->ragged.exec);
     if (ctx->tree) cudaStreamDestroy(ctx->tree);
     if (ctx->tune) cudaStreamDestroy(ctx->tune);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);

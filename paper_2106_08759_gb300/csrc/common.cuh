@@ -92,3 +92,28 @@ __device__ __forceinline__ void rand_block(uint64_t seed, uint64_t k, uint32_t s
 enum : uint32_t { STREAM_G = 0, STREAM_F = 1, STREAM_RHO = 2, STREAM_ENC = 3 };
 
 }  // namespace snt
+#include "kernels.h"
+namespace snt {
+
+// Batch of key j of a launch (binary search over the batch table).
+__device__ __forceinline__ BatchDesc key_batch(const KeyMap &km, int j) {
+    if (km.nb == 0) return km.one;
+    int lo = 0, hi = km.nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (km.tab[mid].key_base <= j) lo = mid; else hi = mid - 1;
+    }
+    return km.tab[lo];
+}
+
+// Batch owning node j of a forest level (pre: nb + 1 prefix sums).
+__device__ __forceinline__ int level_batch(const int *pre, int nb, int j) {
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace snt

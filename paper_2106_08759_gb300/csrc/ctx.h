@@ -1,0 +1,63 @@
+// ctx.h -- the library context (internal): scratch arena, streams, events,
+// device error word, tuning options and the ragged-launch graph cache.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "host_plan.h"
+
+namespace snt {
+inline constexpr int kMaxInject = 64;
+// Phase events of one keygen call (snt_ctx_set_timing): on the main stream
+// 0 start, 1 after sampling f, 4 after the up-sweep (or per-key R/q
+// inversions), 5 after the root, 6 after the down-sweep, 7 after the join,
+// 8 after h/encode, 9 after SHA-512; on the auxiliary stream 2 / 3 around the
+// R/3 kernel.
+inline constexpr int kPhaseEvents = 10;
+inline constexpr size_t kMaxB = (size_t)1 << 24;
+
+
+// Cached CUDA graph of one ragged launch plan (the list of (P, B) pairs).
+struct RaggedGraph {
+    std::vector<int> sig;            // P and B of every batch, in call order
+    cudaGraphExec_t exec = nullptr;
+    size_t table_off = 0, table_bytes = 0;  // device tables inside the arena
+};
+
+}  // namespace snt
+
+struct snt_ctx {
+    int device = 0;
+    size_t budget = 0;
+    uint8_t *arena = nullptr;
+    int *d_err = nullptr;
+    uint64_t *d_inj_idx = nullptr;
+    int8_t *d_inj_g = nullptr;
+    int n_inj = 0;
+    int inj_P = 0;
+    cudaStream_t aux = nullptr;   // low priority: per-key R/3 inversions
+    cudaStream_t tree = nullptr;  // high priority: sampling, product tree, h, hash
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr, ev_r3fork = nullptr;
+    bool timing = false;
+    cudaEvent_t ev_phase[snt::kPhaseEvents] = {};
+    int r3_lanes = snt::kDefaultR3Lanes;
+    int tree_split = snt::kDefaultTreeSplit;
+    int r3_overlap = snt::kDefaultR3Overlap;
+    // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
+    struct Tuned { int lanes = 0, split = 0, overlap = 0; };
+    Tuned tuned[3][25];
+    cudaStream_t tune = nullptr;  // stream used while autotuning
+    snt::RaggedGraph ragged;      // last ragged plan and its graph
+};
+
+
+namespace snt {
+inline int pidx(int P) { return P == 653 ? 0 : P == 761 ? 1 : 2; }
+inline int bbucket(size_t B) {
+    int b = 0;
+    while (((size_t)1 << b) < B && b < 24) ++b;
+    return b;
+}
+}  // namespace snt

@@ -18,9 +18,8 @@ namespace snt {
 
 template <int P>
 __global__ void __launch_bounds__(Tp<P>::NT)
-k_finalize(const int8_t *__restrict__ gbuf, const int16_t *__restrict__ ainv,
-           uint8_t *__restrict__ pk, int pk_bytes, uint8_t *__restrict__ sk, int sk_bytes,
-           int sk_pk_off, EncSched S) {
+k_finalize(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__restrict__ ainv,
+           int pk_bytes, int sk_bytes, int sk_pk_off, EncSched S) {
     using G = Geo<P>;
     __shared__ __align__(16) int As[Tp<P>::p8];
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
@@ -67,8 +66,9 @@ k_finalize(const int8_t *__restrict__ gbuf, const int16_t *__restrict__ ainv,
         for (int b = 0; b < S.efinal; ++b) { ob[S.foff + b] = (uint8_t)(r & 255u); r >>= 8; }
     }
     __syncthreads();
-    uint8_t *pkk = pk + (size_t)key * pk_bytes;
-    uint8_t *skk = sk + (size_t)key * sk_bytes + sk_pk_off;
+    const BatchDesc d = key_batch(km, key);
+    uint8_t *pkk = d.pk + (size_t)(key - d.key_base) * pk_bytes;
+    uint8_t *skk = d.sk + (size_t)(key - d.key_base) * sk_bytes + sk_pk_off;
     for (int b = threadIdx.x; b < pk_bytes; b += blockDim.x) {
         pkk[b] = ob[b];
         skk[b] = ob[b];
@@ -109,16 +109,22 @@ __device__ __forceinline__ uint64_t rotr(uint64_t x, int n) { return (x >> n) | 
 // Lane j then reads its message 0x04 | pk_j byte by byte from there; the
 // padding (0x80, zeros, 128-bit big-endian bit length) is generated.
 __global__ void __launch_bounds__(32)
-k_sha512_pk(int B, const uint8_t *__restrict__ pk, int pk_bytes, uint8_t *__restrict__ sk,
-            int sk_bytes, int hash_off) {
+k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
     extern __shared__ __align__(16) uint8_t blk[];
     const int lane = threadIdx.x;
     const int base = blockIdx.x * 32;
     const int nkeys = min(32, B - base);
     const int nbytes = nkeys * pk_bytes;
-    const uint8_t *src = pk + (size_t)base * pk_bytes;
-    int done = 0;
-    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    if (km.nb > 0) {  // keys from a batch table: copy row by row
+        for (int j = 0; j < nkeys; ++j) {
+            const BatchDesc d = key_batch(km, base + j);
+            const uint8_t *row = d.pk + (size_t)(base + j - d.key_base) * pk_bytes;
+            for (int b = lane; b < pk_bytes; b += 32) blk[j * pk_bytes + b] = row[b];
+        }
+    }
+    const uint8_t *src = km.one.pk + (size_t)base * pk_bytes;
+    int done = (km.nb > 0) ? nbytes : 0;
+    if (km.nb == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
         const int n16 = nbytes / 16;
         const int4 *s4 = reinterpret_cast<const int4 *>(src);
         int4 *d4 = reinterpret_cast<int4 *>(blk);
@@ -184,7 +190,8 @@ k_sha512_pk(int B, const uint8_t *__restrict__ pk, int pk_bytes, uint8_t *__rest
         H[0] += a; H[1] += b; H[2] += c; H[3] += d;
         H[4] += e; H[5] += f; H[6] += g; H[7] += h;
     }
-    uint8_t *out = sk + (size_t)(base + lane) * sk_bytes + hash_off;
+    const BatchDesc dk = key_batch(km, base + lane);
+    uint8_t *out = dk.sk + (size_t)(base + lane - dk.key_base) * sk_bytes + hash_off;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -192,24 +199,23 @@ k_sha512_pk(int B, const uint8_t *__restrict__ pk, int pk_bytes, uint8_t *__rest
 }
 
 template <int P>
-cudaError_t launch_finalize(int B, const int8_t *gbuf, const int16_t *ainv, uint8_t *pk,
-                            int pk_bytes, uint8_t *sk, int sk_bytes, int sk_pk_off,
-                            const EncSched &S, cudaStream_t st) {
-    k_finalize<P><<<B, Tp<P>::NT, 0, st>>>(gbuf, ainv, pk, pk_bytes, sk, sk_bytes, sk_pk_off, S);
+cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, const int16_t *ainv,
+                            int pk_bytes, int sk_bytes, int sk_pk_off, const EncSched &S,
+                            cudaStream_t st) {
+    k_finalize<P><<<nkeys, Tp<P>::NT, 0, st>>>(km, gbuf, ainv, pk_bytes, sk_bytes, sk_pk_off, S);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sha512_pk(int B, const uint8_t *pk, int pk_bytes, uint8_t *sk, int sk_bytes,
+cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
                              int hash_off, cudaStream_t st) {
     const int smem = (32 * pk_bytes + 15) / 16 * 16;
-    k_sha512_pk<<<(B + 31) / 32, 32, smem, st>>>(B, pk, pk_bytes, sk, sk_bytes, hash_off);
+    k_sha512_pk<<<(nkeys + 31) / 32, 32, smem, st>>>(km, nkeys, pk_bytes, sk_bytes, hash_off);
     return cudaGetLastError();
 }
 
 #define SNT_FIN_INST(P)                                                                       \
-    template cudaError_t launch_finalize<P>(int, const int8_t *, const int16_t *, uint8_t *, \
-                                            int, uint8_t *, int, int, const EncSched &,      \
-                                            cudaStream_t);
+    template cudaError_t launch_finalize<P>(const KeyMap &, int, const int8_t *, const int16_t *, \
+                                            int, int, int, const EncSched &, cudaStream_t);
 SNT_FIN_INST(653)
 SNT_FIN_INST(761)
 SNT_FIN_INST(857)

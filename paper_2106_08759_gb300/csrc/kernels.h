@@ -13,6 +13,32 @@ struct EncLevel {
     uint32_t mu, mlast;
     int eu, elast, boff;
 };
+// One batch of a keygen launch: key i of the batch has key index first + i
+// and randomness seed `seed`; its leaf / g rows are rows key_base + i of the
+// launch's arrays and its outputs go to pk + i * pk_bytes, sk + i * sk_bytes.
+struct BatchDesc {
+    uint64_t seed, first;
+    int key_base, nkeys;
+    uint8_t *pk, *sk;
+};
+
+// The keys of one launch: a single batch passed by value (nb == 0), or a
+// device table of nb >= 1 batches in increasing key_base order.
+struct KeyMap {
+    BatchDesc one;
+    const BatchDesc *tab;
+    int nb;
+};
+
+// Level of a product-tree forest: the nodes of every batch at this level are
+// contiguous, batch b owning nodes [pre_out[b], pre_out[b+1]) of the level and
+// its children [pre_in[b], pre_in[b+1]) of the level below.  nb == 0: one
+// tree, n_in children (the arrays are unused).
+struct LevelMap {
+    const int *pre_in, *pre_out;
+    int nb, n_in;
+};
+
 struct EncSched {
     int nlev;
     EncLevel lev[16];
@@ -20,38 +46,53 @@ struct EncSched {
     int total;         // encoded length
 };
 
+inline KeyMap single_batch(uint64_t seed, uint64_t first, int B, uint8_t *pk, uint8_t *sk) {
+    KeyMap km;
+    km.one.seed = seed; km.one.first = first; km.one.key_base = 0; km.one.nkeys = B;
+    km.one.pk = pk; km.one.sk = sk;
+    km.tab = nullptr;
+    km.nb = 0;
+    return km;
+}
+
+inline LevelMap single_tree(int n_in) {
+    LevelMap lm;
+    lm.pre_in = nullptr; lm.pre_out = nullptr; lm.nb = 0; lm.n_in = n_in;
+    return lm;
+}
+
 template <int P>
-cudaError_t launch_sample_f(uint64_t seed, uint64_t first, int B, int16_t *leaves, uint8_t *sk,
-                            int sk_bytes, int rho_off, cudaStream_t st);
+cudaError_t launch_sample_f(const KeyMap &km, int nkeys, int16_t *leaves, int sk_bytes,
+                            int rho_off, cudaStream_t st);
 template <int P>
-cudaError_t launch_r3_keygen(uint64_t seed, uint64_t first, int B, int8_t *g_out, uint8_t *sk,
-                             int sk_bytes, int sk_off, const uint64_t *inj_idx,
-                             const int8_t *inj_g, int n_inj, int *err, cudaStream_t st,
-                             int lanes);
+cudaError_t launch_r3_keygen(const KeyMap &km, int nkeys, int8_t *g_out, int sk_bytes,
+                             int sk_off, const uint64_t *inj_idx, const int8_t *inj_g, int n_inj,
+                             int *err, cudaStream_t st, int lanes);
 template <int P>
 cudaError_t launch_r3_inv(int n, const int8_t *g, int8_t *out, int32_t *ok, cudaStream_t st,
                           int lanes);
 template <int P>
-cudaError_t launch_tree_up(const int16_t *lin, int n_in, int16_t *lout, cudaStream_t st,
-                           int max_split);
+cudaError_t launch_tree_up(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
+                           cudaStream_t st, int max_split);
 template <int P>
-cudaError_t launch_tree_down(const int16_t *lpar, int16_t *lch, int n_ch, cudaStream_t st,
-                             int max_split);
+cudaError_t launch_tree_down(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t *lch,
+                             cudaStream_t st, int max_split);
 template <int P>
 cudaError_t launch_mul_batch(int n, const int16_t *a, const int16_t *b, int16_t *c,
                              cudaStream_t st);
 template <int P>
 cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out,
                           long out_stride, int32_t *ok, int *err, int err_bit, cudaStream_t st);
+// idx (optional): element e is row idx[e] of in / out instead of row e.
 template <int P>
 cudaError_t launch_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
-                               cudaStream_t st);
+                               cudaStream_t st, const int *idx = nullptr);
 template <int P>
-cudaError_t launch_finalize(int B, const int8_t *gbuf, const int16_t *ainv, uint8_t *pk,
-                            int pk_bytes, uint8_t *sk, int sk_bytes, int sk_pk_off,
-                            const EncSched &S, cudaStream_t st);
-cudaError_t launch_sha512_pk(int B, const uint8_t *pk, int pk_bytes, uint8_t *sk, int sk_bytes,
+cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, const int16_t *ainv,
+                            int pk_bytes, int sk_bytes, int sk_pk_off, const EncSched &S,
+                            cudaStream_t st);
+cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
                              int hash_off, cudaStream_t st);
 
 }  // namespace snt

@@ -65,22 +65,23 @@ snt_status run_static(const snt::ParamInfo &pi, uint64_t seed, uint64_t first, s
     int8_t *gbuf = reinterpret_cast<int8_t *>(scratch + align256(t.total * pi.pad * sizeof(int16_t)));
     const int Bi = (int)B, sb = pi.small_bytes;
     SNT_CUDA_S(cudaMemsetAsync(err, 0, sizeof(int), st));
-    SNT_CUDA_S(launch_sample_f<P>(seed, first, Bi, nodes, sk, pi.sk_bytes, 2 * sb + pi.pk_bytes, st));
-    SNT_CUDA_S(launch_r3_keygen<P>(seed, first, Bi, gbuf, sk, pi.sk_bytes, sb, nullptr, nullptr, 0,
-                                   err, st, kDefaultR3Lanes));
+    const KeyMap km = single_batch(seed, first, Bi, pk, sk);
+    SNT_CUDA_S(launch_sample_f<P>(km, Bi, nodes, pi.sk_bytes, 2 * sb + pi.pk_bytes, st));
+    SNT_CUDA_S(launch_r3_keygen<P>(km, Bi, gbuf, pi.sk_bytes, sb, nullptr, nullptr, 0, err, st,
+                                   kDefaultR3Lanes));
     const int L = (int)t.n.size() - 1;
     for (int l = 1; l <= L; ++l)
-        SNT_CUDA_S(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1],
-                                     nodes + (size_t)t.off[l] * pi.pad, st, kDefaultTreeSplit));
+        SNT_CUDA_S(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad, single_tree(t.n[l - 1]),
+                                     t.n[l], nodes + (size_t)t.off[l] * pi.pad, st, kDefaultTreeSplit));
     int16_t *root = nodes + (size_t)t.off[L] * pi.pad;
     SNT_CUDA_S(launch_rq_inv_jump<P>(1, root, pi.pad, root, pi.pad, nullptr, err, ERR_ROOT, st));
     for (int l = L; l >= 1; --l)
-        SNT_CUDA_S(launch_tree_down<P>(nodes + (size_t)t.off[l] * pi.pad,
-                                       nodes + (size_t)t.off[l - 1] * pi.pad, t.n[l - 1], st,
+        SNT_CUDA_S(launch_tree_down<P>(nodes + (size_t)t.off[l] * pi.pad, single_tree(t.n[l - 1]),
+                                       t.n[l], nodes + (size_t)t.off[l - 1] * pi.pad, st,
                                        kDefaultTreeSplit));
-    SNT_CUDA_S(launch_finalize<P>(Bi, gbuf, nodes, pk, pi.pk_bytes, sk, pi.sk_bytes, 2 * sb,
-                                  pi.sched, st));
-    SNT_CUDA_S(launch_sha512_pk(Bi, pk, pi.pk_bytes, sk, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
+    SNT_CUDA_S(launch_finalize<P>(km, Bi, gbuf, nodes, pi.pk_bytes, pi.sk_bytes, 2 * sb, pi.sched,
+                                  st));
+    SNT_CUDA_S(launch_sha512_pk(km, Bi, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     int herr = 0;
     SNT_CUDA_S(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SNT_CUDA_S(cudaStreamSynchronize(st));

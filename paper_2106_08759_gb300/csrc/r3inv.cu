@@ -196,8 +196,7 @@ __device__ __forceinline__ void reversed_to_smem(const uint32_t (&om)[R3Geo<P, L
 // ---------------------------------------------------------------------------
 template <int P, int LKT>
 __global__ void __launch_bounds__(32 * R3Geo<P, LKT>::WARPS)
-k_r3_keygen(uint64_t seed, uint64_t first, int B, int8_t *__restrict__ g_out,
-            uint8_t *__restrict__ sk, int sk_bytes, int sk_off,
+k_r3_keygen(KeyMap km, int B, int8_t *__restrict__ g_out, int sk_bytes, int sk_off,
             const uint64_t *__restrict__ inj_idx, const int8_t *__restrict__ inj_g,
             int n_inj, int *__restrict__ err) {
     using Gm = Geo<P>;
@@ -210,7 +209,9 @@ k_r3_keygen(uint64_t seed, uint64_t first, int B, int8_t *__restrict__ g_out,
     if (ebase >= B) return;                               // warp-uniform
     const int key = ebase + grp;
     const bool live = key < B;
-    const uint64_t k = first + (uint64_t)key;
+    const BatchDesc bd = key_batch(km, live ? key : ebase);
+    const uint64_t seed = bd.seed;
+    const uint64_t k = bd.first + (uint64_t)(key - bd.key_base);
     int8_t *gsm = smem[warp * EPW + grp];
 
     // optional injected attempt-0 draw (test hook)
@@ -274,7 +275,8 @@ k_r3_keygen(uint64_t seed, uint64_t first, int B, int8_t *__restrict__ g_out,
     for (int e = 0; e < EPW; ++e) {
         if (ebase + e >= B) break;
         const int8_t *src = smem[warp * EPW + e];
-        uint8_t *skk = sk + (size_t)(ebase + e) * sk_bytes + sk_off;
+        const BatchDesc be = key_batch(km, ebase + e);
+        uint8_t *skk = be.sk + (size_t)(ebase + e - be.key_base) * sk_bytes + sk_off;
         for (int b = lane; b < Gm::small_bytes; b += 32) {
             uint32_t byte = 0;
 #pragma unroll
@@ -323,24 +325,23 @@ k_r3_inv(int n, const int8_t *__restrict__ g, int8_t *__restrict__ out,
 }
 
 template <int P, int LK>
-cudaError_t launch_r3_keygen_lk(uint64_t seed, uint64_t first, int B, int8_t *g_out,
-                                uint8_t *sk, int sk_bytes, int sk_off, const uint64_t *inj_idx,
-                                const int8_t *inj_g, int n_inj, int *err, cudaStream_t st) {
+cudaError_t launch_r3_keygen_lk(const KeyMap &km, int B, int8_t *g_out, int sk_bytes, int sk_off,
+                                const uint64_t *inj_idx, const int8_t *inj_g, int n_inj, int *err,
+                                cudaStream_t st) {
     constexpr int EPB = R3Geo<P, LK>::EPB;
     k_r3_keygen<P, LK><<<(B + EPB - 1) / EPB, 32 * R3Geo<P, LK>::WARPS, 0, st>>>(
-        seed, first, B, g_out, sk, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err);
+        km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err);
     return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t launch_r3_keygen(uint64_t seed, uint64_t first, int B, int8_t *g_out,
-                             uint8_t *sk, int sk_bytes, int sk_off, const uint64_t *inj_idx,
-                             const int8_t *inj_g, int n_inj, int *err, cudaStream_t st,
-                             int lanes) {
+cudaError_t launch_r3_keygen(const KeyMap &km, int B, int8_t *g_out, int sk_bytes, int sk_off,
+                             const uint64_t *inj_idx, const int8_t *inj_g, int n_inj, int *err,
+                             cudaStream_t st, int lanes) {
     switch (lanes) {
-        case 4: return launch_r3_keygen_lk<P, 4>(seed, first, B, g_out, sk, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st);
-        case 8: return launch_r3_keygen_lk<P, 8>(seed, first, B, g_out, sk, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st);
-        default: return launch_r3_keygen_lk<P, 32>(seed, first, B, g_out, sk, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st);
+        case 4: return launch_r3_keygen_lk<P, 4>(km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st);
+        case 8: return launch_r3_keygen_lk<P, 8>(km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st);
+        default: return launch_r3_keygen_lk<P, 32>(km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st);
     }
 }
 
@@ -362,9 +363,9 @@ cudaError_t launch_r3_inv(int n, const int8_t *g, int8_t *out, int32_t *ok, cuda
 }
 
 #define SNT_R3_INST(P)                                                                      \
-    template cudaError_t launch_r3_keygen<P>(uint64_t, uint64_t, int, int8_t *, uint8_t *,  \
-                                             int, int, const uint64_t *, const int8_t *,    \
-                                             int, int *, cudaStream_t, int);                \
+    template cudaError_t launch_r3_keygen<P>(const KeyMap &, int, int8_t *, int, int,       \
+                                             const uint64_t *, const int8_t *, int, int *,  \
+                                             cudaStream_t, int);                            \
     template cudaError_t launch_r3_inv<P>(int, const int8_t *, int8_t *, int32_t *, cudaStream_t, int);
 SNT_R3_INST(653)
 SNT_R3_INST(761)

@@ -196,7 +196,7 @@ __device__ __forceinline__ void leader_chunk(int m, int &delta, int fl, int gl, 
 template <int P>
 __global__ void __launch_bounds__(JumpGeo<P>::NT)
 k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_stride,
-              int32_t *__restrict__ okv, int *__restrict__ err, int err_bit) {
+              int32_t *__restrict__ okv, int *__restrict__ err, int err_bit, const int *idx) {
     constexpr int Q = Geo<P>::q;
     using JG = JumpGeo<P>;
     constexpr int LEN = JG::LEN, OFF = JG::OFF, NT = JG::NT;
@@ -208,7 +208,8 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     if (e >= n) return;
     const int tid = threadIdx.x, lane = tid & 31;
     const bool leader = tid < 32;
-    const int16_t *a = in + (size_t)e * in_stride;
+    const int row = idx ? idx[e] : e;
+    const int16_t *a = in + (size_t)row * in_stride;
     for (int i = tid; i < 2 * 4 * JG::PLEN; i += NT) (&st[0][0][0])[i] = 0;
     for (int i = tid; i < 2 * 4 * 34; i += NT) (&mat[0][0][0])[i] = 0;
     __syncthreads();
@@ -351,7 +352,7 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     const bool ok = s_ok != 0;
     const int f0 = freeze_lazy<Q>(st[cur][0][slot(OFF)]);
     const int sc = ok ? inv_mod<Q>(f0) : 0;
-    int16_t *o = out + (size_t)e * out_stride;
+    int16_t *o = out + (size_t)row * out_stride;
     for (int i = tid; i < P; i += NT) {
         const int v = freeze_lazy<Q>(st[cur][2][slot(OFF + P - 1 - i)]);
         o[i] = (int16_t)cmod<Q>(sc * v);
@@ -365,9 +366,9 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
 template <int P>
 cudaError_t launch_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
-                               cudaStream_t st) {
+                               cudaStream_t st, const int *idx) {
     k_rq_inv_jump<P><<<n, JumpGeo<P>::NT, 0, st>>>(n, in, in_stride, out, out_stride, ok, err,
-                                                   err_bit);
+                                                   err_bit, idx);
     return cudaGetLastError();
 }
 
@@ -383,7 +384,7 @@ cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out
     template cudaError_t launch_rq_inv<P>(int, const int16_t *, long, int16_t *, long,     \
                                           int32_t *, int *, int, cudaStream_t);            \
     template cudaError_t launch_rq_inv_jump<P>(int, const int16_t *, long, int16_t *, long, \
-                                               int32_t *, int *, int, cudaStream_t);
+                                               int32_t *, int *, int, cudaStream_t, const int *);
 SNT_INV_INST(653)
 SNT_INV_INST(761)
 SNT_INV_INST(857)

@@ -24,16 +24,23 @@ namespace snt {
 // product, wide levels K = 1 for throughput.
 template <int P, int K>
 __global__ void __launch_bounds__(Tp<P>::NT * K)
-k_tree_up(const int16_t *__restrict__ lin, int n_in, int16_t *__restrict__ lout) {
+k_tree_up(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict__ lout) {
     using G = Geo<P>;
     constexpr int NT = Tp<P>::NT;
     __shared__ __align__(16) int As[Tp<P>::p8];
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
     __shared__ int part[K > 1 ? (K - 1) * Tp<P>::p8 : 1];
     const int j = blockIdx.x;
-    const int16_t *a = lin + (size_t)(2 * j) * G::pad;
+    int idx = j, base = 0, n_in = lm.n_in;  // this node's index in its tree, its children
+    if (lm.nb > 0) {
+        const int b = level_batch(lm.pre_out, lm.nb, j);
+        idx = j - lm.pre_out[b];
+        base = lm.pre_in[b];
+        n_in = lm.pre_in[b + 1] - base;
+    }
+    const int16_t *a = lin + (size_t)(base + 2 * idx) * G::pad;
     int16_t *c = lout + (size_t)j * G::pad;
-    if (2 * j + 1 >= n_in) {  // unpaired: move up unchanged
+    if (2 * idx + 1 >= n_in) {  // unpaired: move up unchanged
         for (int i = threadIdx.x; i < G::pad; i += blockDim.x) c[i] = a[i];
         return;
     }
@@ -53,7 +60,7 @@ k_tree_up(const int16_t *__restrict__ lin, int n_in, int16_t *__restrict__ lout)
 
 template <int P, int K>
 __global__ void __launch_bounds__(Tp<P>::NT * K)
-k_tree_down(const int16_t *__restrict__ lpar, int16_t *__restrict__ lch, int n_ch) {
+k_tree_down(const int16_t *__restrict__ lpar, LevelMap lm, int16_t *__restrict__ lch) {
     using G = Geo<P>;
     constexpr int NT = Tp<P>::NT;
     __shared__ __align__(16) int Xs[Tp<P>::p8];
@@ -61,9 +68,16 @@ k_tree_down(const int16_t *__restrict__ lpar, int16_t *__restrict__ lch, int n_c
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
     __shared__ int part[K > 1 ? (K - 1) * Tp<P>::p8 : 1];
     const int j = blockIdx.x;
+    int idx = j, base = 0, n_ch = lm.n_in;
+    if (lm.nb > 0) {
+        const int b = level_batch(lm.pre_out, lm.nb, j);
+        idx = j - lm.pre_out[b];
+        base = lm.pre_in[b];
+        n_ch = lm.pre_in[b + 1] - base;
+    }
     const int16_t *T = lpar + (size_t)j * G::pad;
-    int16_t *x = lch + (size_t)(2 * j) * G::pad;
-    if (2 * j + 1 >= n_ch) {  // unpaired child: its inverse is the parent's
+    int16_t *x = lch + (size_t)(base + 2 * idx) * G::pad;
+    if (2 * idx + 1 >= n_ch) {  // unpaired child: its inverse is the parent's
         for (int i = threadIdx.x; i < G::pad; i += blockDim.x) x[i] = T[i];
         return;
     }
@@ -117,29 +131,27 @@ inline int split_for(int n, int max_split) {
 }
 
 template <int P>
-cudaError_t launch_tree_up(const int16_t *lin, int n_in, int16_t *lout, cudaStream_t st,
-                           int max_split) {
-    const int n_out = (n_in + 1) / 2;
+cudaError_t launch_tree_up(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
+                           cudaStream_t st, int max_split) {
     constexpr int NT = Tp<P>::NT;
     switch (split_for(n_out, max_split)) {
-        case 8: k_tree_up<P, 8><<<n_out, NT * 8, 0, st>>>(lin, n_in, lout); break;
-        case 4: k_tree_up<P, 4><<<n_out, NT * 4, 0, st>>>(lin, n_in, lout); break;
-        case 2: k_tree_up<P, 2><<<n_out, NT * 2, 0, st>>>(lin, n_in, lout); break;
-        default: k_tree_up<P, 1><<<n_out, NT, 0, st>>>(lin, n_in, lout); break;
+        case 8: k_tree_up<P, 8><<<n_out, NT * 8, 0, st>>>(lin, lm, lout); break;
+        case 4: k_tree_up<P, 4><<<n_out, NT * 4, 0, st>>>(lin, lm, lout); break;
+        case 2: k_tree_up<P, 2><<<n_out, NT * 2, 0, st>>>(lin, lm, lout); break;
+        default: k_tree_up<P, 1><<<n_out, NT, 0, st>>>(lin, lm, lout); break;
     }
     return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t launch_tree_down(const int16_t *lpar, int16_t *lch, int n_ch, cudaStream_t st,
-                             int max_split) {
-    const int n_par = (n_ch + 1) / 2;
+cudaError_t launch_tree_down(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t *lch,
+                             cudaStream_t st, int max_split) {
     constexpr int NT = Tp<P>::NT;
     switch (split_for(n_par, max_split)) {
-        case 8: k_tree_down<P, 8><<<n_par, NT * 8, 0, st>>>(lpar, lch, n_ch); break;
-        case 4: k_tree_down<P, 4><<<n_par, NT * 4, 0, st>>>(lpar, lch, n_ch); break;
-        case 2: k_tree_down<P, 2><<<n_par, NT * 2, 0, st>>>(lpar, lch, n_ch); break;
-        default: k_tree_down<P, 1><<<n_par, NT, 0, st>>>(lpar, lch, n_ch); break;
+        case 8: k_tree_down<P, 8><<<n_par, NT * 8, 0, st>>>(lpar, lm, lch); break;
+        case 4: k_tree_down<P, 4><<<n_par, NT * 4, 0, st>>>(lpar, lm, lch); break;
+        case 2: k_tree_down<P, 2><<<n_par, NT * 2, 0, st>>>(lpar, lm, lch); break;
+        default: k_tree_down<P, 1><<<n_par, NT, 0, st>>>(lpar, lm, lch); break;
     }
     return cudaGetLastError();
 }
@@ -152,8 +164,10 @@ cudaError_t launch_mul_batch(int n, const int16_t *a, const int16_t *b, int16_t 
 }
 
 #define SNT_MUL_INST(P)                                                                        \
-    template cudaError_t launch_tree_up<P>(const int16_t *, int, int16_t *, cudaStream_t, int); \
-    template cudaError_t launch_tree_down<P>(const int16_t *, int16_t *, int, cudaStream_t, int); \
+    template cudaError_t launch_tree_up<P>(const int16_t *, const LevelMap &, int, int16_t *,  \
+                                           cudaStream_t, int);                                 \
+    template cudaError_t launch_tree_down<P>(const int16_t *, const LevelMap &, int, int16_t *,\
+                                             cudaStream_t, int);                               \
     template cudaError_t launch_mul_batch<P>(int, const int16_t *, const int16_t *, int16_t *, \
                                              cudaStream_t);
 SNT_MUL_INST(653)

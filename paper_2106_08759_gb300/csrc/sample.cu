@@ -20,13 +20,14 @@ namespace snt {
 // stages).
 template <int P>
 __global__ void __launch_bounds__(256)
-k_sample_f(uint64_t seed, uint64_t first, int B, int16_t *__restrict__ leaves,
-           uint8_t *__restrict__ sk, int sk_bytes, int rho_off) {
+k_sample_f(KeyMap km, int nkeys, int16_t *__restrict__ leaves, int sk_bytes, int rho_off) {
     using G = Geo<P>;
     __shared__ __align__(16) uint32_t xs[1024];
     const int key = blockIdx.x;
-    if (key >= B) return;
-    const uint64_t k = first + (uint64_t)key;
+    if (key >= nkeys) return;
+    const BatchDesc d = key_batch(km, key);
+    const uint64_t seed = d.seed;
+    const uint64_t k = d.first + (uint64_t)(key - d.key_base);
     const int t = threadIdx.x;
 
     // words of stream 1, low bits forced; sentinels above p
@@ -88,7 +89,7 @@ k_sample_f(uint64_t seed, uint64_t first, int B, int16_t *__restrict__ leaves,
         if (j < G::pad) leaf[j] = (int16_t)(j < G::p ? 3 * ((int)(v[r] & 3u) - 1) : 0);
     }
     // Small_encode(f): byte t packs coefficients 4t..4t+3 as (c + 1) in 2 bits
-    uint8_t *skk = sk + (size_t)key * sk_bytes;
+    uint8_t *skk = d.sk + (size_t)(key - d.key_base) * sk_bytes;
     if (t < G::small_bytes) {
         uint32_t byte = 0;
 #pragma unroll
@@ -110,14 +111,14 @@ k_sample_f(uint64_t seed, uint64_t first, int B, int16_t *__restrict__ leaves,
 }
 
 template <int P>
-cudaError_t launch_sample_f(uint64_t seed, uint64_t first, int B, int16_t *leaves,
-                            uint8_t *sk, int sk_bytes, int rho_off, cudaStream_t st) {
-    k_sample_f<P><<<B, 256, 0, st>>>(seed, first, B, leaves, sk, sk_bytes, rho_off);
+cudaError_t launch_sample_f(const KeyMap &km, int nkeys, int16_t *leaves, int sk_bytes,
+                            int rho_off, cudaStream_t st) {
+    k_sample_f<P><<<nkeys, 256, 0, st>>>(km, nkeys, leaves, sk_bytes, rho_off);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_sample_f<653>(uint64_t, uint64_t, int, int16_t *, uint8_t *, int, int, cudaStream_t);
-template cudaError_t launch_sample_f<761>(uint64_t, uint64_t, int, int16_t *, uint8_t *, int, int, cudaStream_t);
-template cudaError_t launch_sample_f<857>(uint64_t, uint64_t, int, int16_t *, uint8_t *, int, int, cudaStream_t);
+template cudaError_t launch_sample_f<653>(const KeyMap &, int, int16_t *, int, int, cudaStream_t);
+template cudaError_t launch_sample_f<761>(const KeyMap &, int, int16_t *, int, int, cudaStream_t);
+template cudaError_t launch_sample_f<857>(const KeyMap &, int, int16_t *, int, int, cudaStream_t);
 
 }  // namespace snt

@@ -141,6 +141,30 @@ def main():
                                   "phases": {k: round(v, 4) for k, v in ph.items()}}
         out["keygen_4096_sweep"] = sweep
     ctx.close()
+
+    # ragged workload: 256 batches, log-uniform sizes in [1, 2048], mixed
+    # parameter sets, one graph launch (timed after the graph is built)
+    from synth import ragged_batches
+    sizes, ps = ragged_batches(256, 2048, 42)
+    rctx = snt.Context(0, 1 << 30)
+    pks, sks = [], []
+    for P_, B_ in zip(ps, sizes):
+        pkb_, skb_, _, _ = snt.snt_param_sizes(int(P_))
+        pks.append(torch.empty(int(B_) * pkb_, dtype=torch.uint8, device=dev))
+        sks.append(torch.empty(int(B_) * skb_, dtype=torch.uint8, device=dev))
+    firsts = [int(x) for x in np.cumsum([0] + list(sizes[:-1]))]
+    it = [0]
+
+    def ragged():
+        it[0] += 1
+        snt.snt_batch_keygen_ragged(rctx, [int(x) for x in ps], [int(x) for x in sizes],
+                                    [it[0] * 1000 + i for i in range(256)], firsts, pks, sks)
+
+    ms = timeit(ragged)
+    nkeys = int(sizes.sum())
+    out["ragged_256"] = {"batches": 256, "keys": nkeys, "ms": ms, "keys_per_s": nkeys / ms * 1e3,
+                         "keys_by_p": {int(P_): int(sizes[ps == P_].sum()) for P_ in (653, 761, 857)}}
+    rctx.close()
     print(json.dumps(out))
 
 

@@ -1,0 +1,78 @@
+"""Ragged keygen (many batches, mixed sizes and parameter sets, one graph
+launch): every batch must equal snt_batch_keygen of that batch alone, which
+the other tests tie to the oracle; a few keys are also checked against the
+oracle directly."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def snt():
+    require_gpu()
+    import paper_2106_08759_gb300 as m
+    m.load()
+    return m
+
+
+def _run_ragged(snt, ctx, Ps, Bs, seeds, firsts):
+    import torch
+    pks, sks = [], []
+    for P, B in zip(Ps, Bs):
+        pkb, skb, _, _ = snt.snt_param_sizes(P)
+        pks.append(torch.full((B * pkb,), 0xAA, dtype=torch.uint8, device="cuda"))
+        sks.append(torch.full((B * skb,), 0xAA, dtype=torch.uint8, device="cuda"))
+    snt.snt_batch_keygen_ragged(ctx, Ps, Bs, seeds, firsts, pks, sks)
+    ctx.sync()
+    return [(pk.cpu().numpy().reshape(B, -1), sk.cpu().numpy().reshape(B, -1))
+            for pk, sk, B in zip(pks, sks, Bs)]
+
+
+def _single(snt, ctx, P, B, seed, first):
+    import torch
+    pkb, skb, _, _ = snt.snt_param_sizes(P)
+    pk = torch.empty(B * pkb, dtype=torch.uint8, device="cuda")
+    sk = torch.empty(B * skb, dtype=torch.uint8, device="cuda")
+    snt.snt_batch_keygen(ctx, P, seed, first, B, pk, sk)
+    ctx.sync()
+    return pk.cpu().numpy().reshape(B, -1), sk.cpu().numpy().reshape(B, -1)
+
+
+def test_ragged_small_mixed(snt):
+    Ps = [761, 653, 857, 761, 761, 653, 857]
+    Bs = [5, 1, 33, 2, 64, 17, 1]
+    firsts = [0, 10, 20, 100, 200, 300, 400]
+    with snt.Context(0, 128 << 20) as ctx:
+        for rnd, seeds in enumerate([[11, 12, 13, 14, 15, 16, 17], [21, 22, 23, 24, 25, 26, 27]]):
+            # the second round replays the cached graph with new seeds
+            got = _run_ragged(snt, ctx, Ps, Bs, seeds, firsts)
+            for (pk, sk), P, B, s, f in zip(got, Ps, Bs, seeds, firsts):
+                rpk, rsk = _single(snt, ctx, P, B, s, f)
+                assert np.array_equal(pk, rpk) and np.array_equal(sk, rsk), (rnd, P, B)
+        # oracle spot checks (second round's seeds)
+        for i in (1, 2, 6):
+            opk, osk, _ = oracle.keygen(Ps[i], seeds[i], firsts[i] + Bs[i] - 1)
+            assert np.array_equal(got[i][0][-1], opk) and np.array_equal(got[i][1][-1], osk)
+
+
+def test_ragged_full_workload_256_batches(snt):
+    """The ragged workload: 256 batches of log-uniform size in [1, 2048]
+    (seed 42), equal shares of sntrup653/761/857 after a seeded shuffle."""
+    from synth import ragged_batches
+    sizes, ps = ragged_batches(256, 2048, 42)
+    seeds = [1000 + i for i in range(256)]
+    firsts = list(np.cumsum([0] + list(sizes[:-1])))
+    with snt.Context(0, 1 << 30) as ctx:
+        got = _run_ragged(snt, ctx, list(ps), list(sizes), seeds, firsts)
+        for i in range(256):
+            rpk, rsk = _single(snt, ctx, int(ps[i]), int(sizes[i]), seeds[i], int(firsts[i]))
+            assert np.array_equal(got[i][0], rpk) and np.array_equal(got[i][1], rsk), i
+    rng = np.random.default_rng(3)
+    for i in rng.integers(0, 256, 6):
+        j = int(rng.integers(0, sizes[i]))
+        opk, osk, _ = oracle.keygen(int(ps[i]), seeds[i], int(firsts[i]) + j)
+        assert np.array_equal(got[i][0][j], opk) and np.array_equal(got[i][1][j], osk)
