@@ -64,6 +64,12 @@ def lib():
                 "orc_sizes": (None, [ctypes.c_int, i32, P, P, P]),
                 "orc_keygen": (ctypes.c_int, [ctypes.c_int, i32, ctypes.c_int, u64, u64,
                                               P, ctypes.c_int, P, P, P, P, P, P]),
+                "orc_sample_short_stream": (None, [ctypes.c_int, ctypes.c_int, u64, u64, u32, P]),
+                "orc_rounded_bytes": (sz, [ctypes.c_int, i32]),
+                "rounded_encode": (None, [ctypes.c_int, i32, P, P]),
+                "rounded_decode": (None, [ctypes.c_int, i32, P, P]),
+                "orc_encap": (None, [ctypes.c_int, i32, ctypes.c_int, P, u64, u64, P, P]),
+                "orc_decap": (ctypes.c_int, [ctypes.c_int, i32, ctypes.c_int, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -239,3 +245,50 @@ def keygen_batch(p, seed, first, B, g_inject=None):
         pks[i] = pk
         sks[i] = sk
     return pks, sks
+
+
+def ct_bytes(p):
+    _, q, _ = PARAMS[p]
+    return int(lib().orc_rounded_bytes(p, q)) + 32
+
+
+def sample_short_stream(p, w, seed, k, stream):
+    f = np.zeros(p, np.int8)
+    lib().orc_sample_short_stream(p, w, seed, k, stream, _ptr(f))
+    return f
+
+
+def encap(p, pk, seed, k):
+    """(ct, ss) for public key pk; r is Short from stream 3 of (seed, k)."""
+    _, q, w = PARAMS[p]
+    pk = np.ascontiguousarray(pk, dtype=np.uint8)
+    ct = np.zeros(ct_bytes(p), np.uint8)
+    ss = np.zeros(32, np.uint8)
+    lib().orc_encap(p, q, w, _ptr(pk), seed, k, _ptr(ct), _ptr(ss))
+    return ct, ss
+
+
+def decap(p, sk, ct):
+    """(ss, accepted) for secret key sk and ciphertext ct."""
+    _, q, w = PARAMS[p]
+    sk = np.ascontiguousarray(sk, dtype=np.uint8)
+    ct = np.ascontiguousarray(ct, dtype=np.uint8)
+    ss = np.zeros(32, np.uint8)
+    ok = lib().orc_decap(p, q, w, _ptr(sk), _ptr(ct), _ptr(ss))
+    return ss, bool(ok)
+
+
+def rounded_decode(p, data):
+    _, q, _ = PARAMS[p]
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    c = np.zeros(p, np.int32)
+    lib().rounded_decode(p, q, _ptr(data), _ptr(c))
+    return c
+
+
+def rounded_encode(p, c):
+    _, q, _ = PARAMS[p]
+    c = np.ascontiguousarray(c, dtype=np.int32)
+    out = np.zeros(ct_bytes(p) - 32, np.uint8)
+    lib().rounded_encode(p, q, _ptr(c), _ptr(out))
+    return out

@@ -112,10 +112,11 @@ static int cmp_u32(const void *x, const void *y)
  * at uniformly random positions (ties in the upper 30 bits are broken by the
  * numeric order, deterministically).
  */
-void orc_sample_short(int p, int w, uint64_t seed, uint64_t k, int8_t *f)
+void orc_sample_short_stream(int p, int w, uint64_t seed, uint64_t k, uint32_t stream,
+                             int8_t *f)
 {
     uint32_t *u = (uint32_t *)malloc(sizeof(uint32_t) * p);
-    orc_random_words(seed, k, 1, 0, p, u);
+    orc_random_words(seed, k, stream, 0, p, u);
     for (int i = 0; i < p; i++) {
         if (i < w) u[i] = u[i] & ~1u;
         else       u[i] = (u[i] & ~3u) | 1u;
@@ -123,6 +124,11 @@ void orc_sample_short(int p, int w, uint64_t seed, uint64_t k, int8_t *f)
     qsort(u, (size_t)p, sizeof(uint32_t), cmp_u32);
     for (int j = 0; j < p; j++) f[j] = (int8_t)((int)(u[j] & 3u) - 1);
     free(u);
+}
+
+void orc_sample_short(int p, int w, uint64_t seed, uint64_t k, int8_t *f)
+{
+    orc_sample_short_stream(p, w, seed, k, 1, f);
 }
 
 /* rho (part of the secret key, used for implicit rejection): nbytes bytes of
@@ -699,4 +705,148 @@ done:
     free(g); free(f); free(v); free(g32); free(v32); free(a32); free(ai32);
     free(h32); free(h);
     return attempts;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Encapsulation and decapsulation (the serving path).  The paper measures   */
+/* them (Table 1) and defers their definition to the NTRU Prime             */
+/* specification; reading (round-3 Streamlined NTRU Prime KEM):             */
+/*   Round(a): each coefficient to the nearest multiple of 3 (centred).      */
+/*   Rounded_encode: Encode of (c_i + (q-1)/2) / 3 with radix (q+2)/3.       */
+/*   Hash_prefix(b, x) = SHA-512(b | x)[0:32].                              */
+/*   Encap(pk; r Short from stream 3):                                      */
+/*     c = Round(h r), C = Rounded_encode(c), r_enc = Small_encode(r),       */
+/*     confirm = Hash_prefix(2, Hash_prefix(3, r_enc) | Hash_prefix(4, pk)), */
+/*     ct = C | confirm, ss = Hash_prefix(1, Hash_prefix(3, r_enc) | ct).    */
+/*   Decap(ct, sk):                                                         */
+/*     e = (3 f c mod q, centred) mod 3, r' = e v in R/3 (v = 1/g);           */
+/*     if weight(r') != w: r' = (1, ..., 1 (w times), 0, ..., 0);            */
+/*     re-encrypt r' to ct'; ss = Hash_prefix(1, Hash_prefix(3, r'_enc) | ct)*/
+/*     if ct' == ct, else Hash_prefix(0, Hash_prefix(3, rho) | ct).          */
+/* ------------------------------------------------------------------------ */
+static void hash_prefix(uint8_t b, const uint8_t *x, size_t len, uint8_t out[32])
+{
+    uint8_t *m = malloc(len + 1), d[64];
+    m[0] = b;
+    memcpy(m + 1, x, len);
+    orc_sha512(m, len + 1, d);
+    memcpy(out, d, 32);
+    free(m);
+}
+
+size_t orc_rounded_bytes(int p, int32_t q)
+{
+    uint64_t *R = calloc((size_t)p, 8), *M = malloc(8 * (size_t)p);
+    for (int i = 0; i < p; i++) M[i] = (uint64_t)((q + 2) / 3);
+    size_t len = enc_rec(NULL, R, M, (size_t)p);
+    free(R); free(M);
+    return len;
+}
+
+/* c: centred multiples of 3 */
+void rounded_encode(int p, int32_t q, const int32_t *c, uint8_t *out)
+{
+    uint64_t *R = malloc(8 * (size_t)p), *M = malloc(8 * (size_t)p);
+    for (int i = 0; i < p; i++) {
+        R[i] = (uint64_t)((c[i] + (q - 1) / 2) / 3);
+        M[i] = (uint64_t)((q + 2) / 3);
+    }
+    enc_rec(out, R, M, (size_t)p);
+    free(R); free(M);
+}
+
+void rounded_decode(int p, int32_t q, const uint8_t *in, int32_t *c)
+{
+    uint64_t *R = calloc((size_t)p, 8), *M = malloc(8 * (size_t)p);
+    for (int i = 0; i < p; i++) M[i] = (uint64_t)((q + 2) / 3);
+    dec_rec(in, R, M, (size_t)p);
+    for (int i = 0; i < p; i++) c[i] = (int32_t)(3 * (int64_t)R[i] - (q - 1) / 2);
+    free(R); free(M);
+}
+
+/* Round(h r) for the centred product */
+static void round3(int p, int32_t q, const int32_t *hr, int32_t *c)
+{
+    for (int i = 0; i < p; i++) c[i] = hr[i] - centred(hr[i], 3);
+    (void)q;
+}
+
+/* ct = Rounded_encode(Round(h r)) | confirm; returns via ct (length
+ * rounded_bytes + 32); h3_out = Hash_prefix(3, Small_encode(r)). */
+static void encrypt_confirm(int p, int32_t q, const int32_t *h, const int8_t *r,
+                            const uint8_t cache[32], uint8_t *ct, uint8_t h3_out[32])
+{
+    size_t rb = orc_rounded_bytes(p, q), sb = (size_t)(p + 3) / 4;
+    int32_t *r32 = malloc(4 * (size_t)p), *hr = malloc(4 * (size_t)p), *c = malloc(4 * (size_t)p);
+    for (int i = 0; i < p; i++) r32[i] = r[i];
+    orc_ring_mul(p, q, h, r32, hr);
+    round3(p, q, hr, c);
+    rounded_encode(p, q, c, ct);
+    uint8_t *renc = malloc(sb), buf[64];
+    orc_small_encode(p, r, renc);
+    hash_prefix(3, renc, sb, h3_out);
+    memcpy(buf, h3_out, 32);
+    memcpy(buf + 32, cache, 32);
+    hash_prefix(2, buf, 64, ct + rb);
+    free(r32); free(hr); free(c); free(renc);
+}
+
+/* Encapsulation for key index k of the request stream (r from stream 3). */
+void orc_encap(int p, int32_t q, int w, const uint8_t *pk, uint64_t seed, uint64_t k,
+               uint8_t *ct, uint8_t ss[32])
+{
+    size_t pkb = orc_rq_encoded_bytes(p, q), rb = orc_rounded_bytes(p, q);
+    int16_t *h16 = malloc(2 * (size_t)p);
+    int32_t *h = malloc(4 * (size_t)p);
+    int8_t *r = malloc((size_t)p);
+    orc_rq_decode(p, q, pk, h16);
+    for (int i = 0; i < p; i++) h[i] = h16[i];
+    orc_sample_short_stream(p, w, seed, k, 3, r);
+    uint8_t cache[32], h3[32];
+    hash_prefix(4, pk, pkb, cache);
+    encrypt_confirm(p, q, h, r, cache, ct, h3);
+    uint8_t *buf = malloc(32 + rb + 32);
+    memcpy(buf, h3, 32);
+    memcpy(buf + 32, ct, rb + 32);
+    hash_prefix(1, buf, 32 + rb + 32, ss);
+    free(buf); free(h16); free(h); free(r);
+}
+
+/* Decapsulation; returns 1 if the ciphertext was accepted (re-encryption
+ * matched), 0 if the implicit-rejection key was produced. */
+int orc_decap(int p, int32_t q, int w, const uint8_t *sk, const uint8_t *ct, uint8_t ss[32])
+{
+    size_t sb = (size_t)(p + 3) / 4, pkb = orc_rq_encoded_bytes(p, q), rb = orc_rounded_bytes(p, q);
+    const uint8_t *pk = sk + 2 * sb, *rho = sk + 2 * sb + pkb, *cache = sk + 3 * sb + pkb;
+    int8_t *f = malloc((size_t)p), *v = malloc((size_t)p), *rr = malloc((size_t)p);
+    int32_t *c = malloc(4 * (size_t)p), *f3 = malloc(4 * (size_t)p), *e = malloc(4 * (size_t)p),
+            *e3 = malloc(4 * (size_t)p), *v32 = malloc(4 * (size_t)p), *r32 = malloc(4 * (size_t)p),
+            *h = malloc(4 * (size_t)p);
+    int16_t *h16 = malloc(2 * (size_t)p);
+    orc_small_decode(p, sk, f);
+    orc_small_decode(p, sk + sb, v);
+    rounded_decode(p, q, ct, c);
+    for (int i = 0; i < p; i++) f3[i] = 3 * f[i];
+    orc_ring_mul(p, q, c, f3, e);                      /* 3 f c, centred */
+    for (int i = 0; i < p; i++) { e3[i] = centred(e[i], 3); v32[i] = v[i]; }
+    orc_ring_mul(p, 3, e3, v32, r32);                  /* r' = e v in R/3 */
+    int weight = 0;
+    for (int i = 0; i < p; i++) weight += (r32[i] != 0);
+    for (int i = 0; i < p; i++) rr[i] = (int8_t)(weight == w ? r32[i] : (i < w ? 1 : 0));
+    orc_rq_decode(p, q, pk, h16);
+    for (int i = 0; i < p; i++) h[i] = h16[i];
+    uint8_t *ct2 = malloc(rb + 32), h3[32];
+    encrypt_confirm(p, q, h, rr, cache, ct2, h3);
+    int ok = (memcmp(ct2, ct, rb + 32) == 0);
+    uint8_t *buf = malloc(32 + rb + 32);
+    if (ok) {
+        memcpy(buf, h3, 32);
+    } else {
+        hash_prefix(3, rho, sb, buf);
+    }
+    memcpy(buf + 32, ct, rb + 32);
+    hash_prefix(ok ? 1 : 0, buf, 32 + rb + 32, ss);
+    free(buf); free(ct2); free(f); free(v); free(rr); free(c); free(f3); free(e); free(e3);
+    free(v32); free(r32); free(h); free(h16);
+    return ok;
 }

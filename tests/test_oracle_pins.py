@@ -346,3 +346,58 @@ def test_keygen_resamples_non_invertible_g():
     assert np.array_equal(out["g"], oracle.sample_small(p, seed, k, 1))
     # f does not depend on how many g attempts were needed
     assert np.array_equal(out["f"], oracle.keygen(p, seed, k, intermediates=True)["f"])
+
+
+# ------------------------------------------------------------ encap / decap
+def test_ct_size_matches_table1():
+    # Table 1: sntrup761 public key + ciphertext = 2197 bytes
+    row = read_golden("table1_sizes.txt")[0]
+    pkb, _, _ = oracle.sizes(761)
+    assert pkb + oracle.ct_bytes(761) == int(row[1])
+
+
+@pytest.mark.parametrize("p", [653, 761, 857])
+def test_decap_of_encap_gives_the_session_key(p):
+    _, q, w = PARAMS[p]
+    for k in range(4):
+        pk, sk, _ = oracle.keygen(p, 77, k)
+        ct, ss = oracle.encap(p, pk, 123, k)
+        ss2, ok = oracle.decap(p, sk, ct)
+        assert ok and ss2.tobytes() == ss.tobytes()
+        # the ciphertext body is Round(h r): decode it and check it is a
+        # multiple of 3 in every coefficient, close to h r
+        r = oracle.sample_short_stream(p, w, 123, k, 3)
+        h = oracle.rq_decode(p, q, pk).astype(np.int64)
+        hr = oracle.ring_mul(p, q, h, r.astype(np.int64))
+        assert np.count_nonzero(r) == w
+        c = oracle.rounded_decode(p, ct[:-32]).astype(np.int64)
+        assert np.all(c % 3 == 0) and np.abs(c - hr).max() <= 1   # Round(h r)
+        assert np.array_equal(oracle.rounded_encode(p, c), ct[:-32])
+
+
+def test_session_key_definition_vs_hashlib():
+    p = 761
+    pkb, skb, sb = oracle.sizes(p)
+    pk, sk, _ = oracle.keygen(p, 5, 1)
+    ct, ss = oracle.encap(p, pk, 9, 2)
+    r = oracle.sample_short_stream(p, 286, 9, 2, 3)
+    renc = oracle.small_encode(p, r).tobytes()
+    h3 = hashlib.sha512(b"\x03" + renc).digest()[:32]
+    cache = hashlib.sha512(b"\x04" + pk.tobytes()).digest()[:32]
+    confirm = hashlib.sha512(b"\x02" + h3 + cache).digest()[:32]
+    assert ct.tobytes()[-32:] == confirm
+    assert ss.tobytes() == hashlib.sha512(b"\x01" + h3 + ct.tobytes()).digest()[:32]
+
+
+def test_tampered_ciphertext_gets_implicit_rejection():
+    p = 761
+    pkb, skb, sb = oracle.sizes(p)
+    pk, sk, _ = oracle.keygen(p, 5, 3)
+    ct, ss = oracle.encap(p, pk, 9, 4)
+    bad = ct.copy()
+    bad[10] ^= 1
+    ss2, ok = oracle.decap(p, sk, bad)
+    assert not ok and ss2.tobytes() != ss.tobytes()
+    rho = sk[2 * sb + pkb:3 * sb + pkb].tobytes()
+    h3r = hashlib.sha512(b"\x03" + rho).digest()[:32]
+    assert ss2.tobytes() == hashlib.sha512(b"\x00" + h3r + bad.tobytes()).digest()[:32]
