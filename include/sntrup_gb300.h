@@ -136,6 +136,28 @@ snt_status snt_batch_keygen_static(int device, int P, uint64_t seed,
                                    uint64_t first_key_index, size_t B,
                                    uint8_t *pk_dev, uint8_t *sk_dev, snt_stream stream);
 
+/* ---- Key encapsulation (the serving path) ----
+ * The paper measures encapsulation and decapsulation (Table 1: 46914 and 56241
+ * Haswell cycles for sntrup761) and takes their definition from the NTRU
+ * Prime specification.  Reading (round-3 Streamlined NTRU Prime KEM): the
+ * ciphertext is Rounded_encode(Round(h r)) | Hash_prefix(2, Hash_prefix(3,
+ * r_enc) | Hash_prefix(4, pk)) (1039 bytes for sntrup761, Table 1's 2197
+ * key + ciphertext bytes), the session key Hash_prefix(1, Hash_prefix(3, r_enc)
+ * | ct); decapsulation re-encrypts and falls back to Hash_prefix(0,
+ * Hash_prefix(3, rho) | ct) if the ciphertext does not match (implicit
+ * rejection).  One CTA per item, asynchronous on `stream`. */
+
+/* n encapsulations: item i uses pk_dev + i * pk_bytes and the Short r of
+ * stream 3 for (seed, first_idx + i); writes ct_dev + i * ct_bytes and
+ * ss_dev + i * 32. */
+snt_status snt_enc(snt_ctx *ctx, int P, size_t n, const uint8_t *pk_dev, uint64_t seed,
+                   uint64_t first_idx, uint8_t *ct_dev, uint8_t *ss_dev, snt_stream stream);
+
+/* n decapsulations: item i uses sk_dev + i * sk_bytes and ct_dev + i * ct_bytes,
+ * writes ss_dev + i * 32. */
+snt_status snt_dec(snt_ctx *ctx, int P, size_t n, const uint8_t *sk_dev, const uint8_t *ct_dev,
+                   uint8_t *ss_dev, snt_stream stream);
+
 /* ---- Building blocks (kernel microbenchmarks; same kernels as keygen) ---- */
 
 /* c_i = a_i * b_i in R/q for i < n.  a_dev, b_dev, c_dev: n * p int16

@@ -64,6 +64,8 @@ def load():
         "snt_batch_keygen_static": [i32, i32, u64, u64, sz, P, P, P],
         "snt_batch_keygen_ragged": [P, sz, P, P, P, P, P, P, P],
         "snt_rq_mul": [P, i32, sz, P, P, P, P],
+        "snt_enc": [P, i32, sz, P, u64, u64, P, P, P],
+        "snt_dec": [P, i32, sz, P, P, P, P],
         "snt_rq_inv": [P, i32, sz, P, P, P, P],
         "snt_rq_inv_latency": [P, i32, sz, P, P, P, P],
         "snt_r3_inv": [P, i32, sz, P, P, P, P],
@@ -240,6 +242,18 @@ def snt_batch_keygen_host(ctx, P, seed, first_key_index, B, pk_host=None, sk_hos
                                         pk_host.ctypes.data_as(ctypes.c_void_p),
                                         sk_host.ctypes.data_as(ctypes.c_void_p)))
     return pk_host, sk_host
+
+
+def snt_enc(ctx, P, n, pk, seed, first_idx, ct, ss, stream=None):
+    import torch
+    _check(load().snt_enc(ctx.handle, P, n, _dptr(pk, torch.uint8), seed, first_idx,
+                          _dptr(ct, torch.uint8), _dptr(ss, torch.uint8), _stream(stream)))
+
+
+def snt_dec(ctx, P, n, sk, ct, ss, stream=None):
+    import torch
+    _check(load().snt_dec(ctx.handle, P, n, _dptr(sk, torch.uint8), _dptr(ct, torch.uint8),
+                          _dptr(ss, torch.uint8), _stream(stream)))
 
 
 def snt_rq_mul(ctx, P, n, a, b, c, stream=None):

@@ -325,6 +325,45 @@ snt_status snt_batch_keygen_host(snt_ctx *ctx, int P, uint64_t seed, uint64_t fi
     return keygen_common(ctx, P, seed, first_key_index, B, pk_host, sk_host, nullptr, true, true);
 }
 
+snt_status snt_enc(snt_ctx *ctx, int P, size_t n, const uint8_t *pk_dev, uint64_t seed,
+                   uint64_t first_idx, uint8_t *ct_dev, uint8_t *ss_dev, snt_stream stream) {
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
+    ParamInfo pi;
+    if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
+    if (n == 0 || n > (size_t)INT32_MAX) return set_error(SNT_EINVAL, "count %zu out of range", n);
+    if (!pk_dev || !ct_dev || !ss_dev) return set_error(SNT_EINVAL, "null buffer");
+    DeviceGuard dg(ctx->device);
+    EncMap em;
+    em.tab = nullptr; em.pk = pk_dev; em.first = first_idx; em.seed = seed;
+    em.ct = ct_dev; em.ss = ss_dev;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (P) {
+        case 653: SNT_CUDA(launch_encap<653>(em, (int)n, pi.pk_bytes, pi.ct_bytes, pi.sched, pi.rsched, st)); break;
+        case 761: SNT_CUDA(launch_encap<761>(em, (int)n, pi.pk_bytes, pi.ct_bytes, pi.sched, pi.rsched, st)); break;
+        default:  SNT_CUDA(launch_encap<857>(em, (int)n, pi.pk_bytes, pi.ct_bytes, pi.sched, pi.rsched, st)); break;
+    }
+    return SNT_OK;
+}
+
+snt_status snt_dec(snt_ctx *ctx, int P, size_t n, const uint8_t *sk_dev, const uint8_t *ct_dev,
+                   uint8_t *ss_dev, snt_stream stream) {
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
+    ParamInfo pi;
+    if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
+    if (n == 0 || n > (size_t)INT32_MAX) return set_error(SNT_EINVAL, "count %zu out of range", n);
+    if (!sk_dev || !ct_dev || !ss_dev) return set_error(SNT_EINVAL, "null buffer");
+    DeviceGuard dg(ctx->device);
+    DecMap dm;
+    dm.tab = nullptr; dm.sk = sk_dev; dm.ct = ct_dev; dm.ss = ss_dev;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (P) {
+        case 653: SNT_CUDA(launch_decap<653>(dm, (int)n, pi.pk_bytes, pi.sk_bytes, pi.ct_bytes, pi.sched, pi.rsched, st)); break;
+        case 761: SNT_CUDA(launch_decap<761>(dm, (int)n, pi.pk_bytes, pi.sk_bytes, pi.ct_bytes, pi.sched, pi.rsched, st)); break;
+        default:  SNT_CUDA(launch_decap<857>(dm, (int)n, pi.pk_bytes, pi.sk_bytes, pi.ct_bytes, pi.sched, pi.rsched, st)); break;
+    }
+    return SNT_OK;
+}
+
 snt_status snt_rq_mul(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev, const int16_t *b_dev,
                       int16_t *c_dev, snt_stream stream) {
     if (!ctx) return set_error(SNT_EINVAL, "null context");

@@ -58,6 +58,7 @@ inline bool build_sched(int p, uint32_t m0, EncSched &S) {
     int e = 0;
     for (uint64_t m = ml; m > 1; m = (m + 255) >> 8) ++e;
     S.efinal = e;
+    S.mfinal = (uint32_t)ml;
     S.foff = off;
     S.total = off + e;
     return true;
@@ -66,7 +67,8 @@ inline bool build_sched(int p, uint32_t m0, EncSched &S) {
 struct ParamInfo {
     int P, p, q, w, pad;
     int small_bytes, pk_bytes, sk_bytes, ct_bytes;
-    EncSched sched;
+    EncSched sched;   // Rq_encode (radix q)
+    EncSched rsched;  // Rounded_encode (radix (q+2)/3)
 };
 
 inline bool param_info(int P, ParamInfo &pi) {
@@ -84,9 +86,8 @@ inline bool param_info(int P, ParamInfo &pi) {
     // sk = Small_encode(f) | Small_encode(1/g) | pk | rho | Hash_prefix(4, pk)
     pi.sk_bytes = 3 * pi.small_bytes + pi.pk_bytes + 32;
     // ct = Rounded encoding (radix (q+2)/3) | 32-byte confirmation hash
-    EncSched rs;
-    if (!build_sched(p, (uint32_t)((q + 2) / 3), rs)) return false;
-    pi.ct_bytes = rs.total + 32;
+    if (!build_sched(p, (uint32_t)((q + 2) / 3), pi.rsched)) return false;
+    pi.ct_bytes = pi.rsched.total + 32;
     return true;
 }
 

@@ -39,10 +39,35 @@ struct LevelMap {
     int nb, n_in;
 };
 
+// Items of an encapsulation / decapsulation launch: a device table of items
+// (tab != nullptr) or contiguous arrays (item i at base + i * size, key
+// index first + i for the encapsulation randomness).
+struct EncItem {
+    const uint8_t *pk;
+    uint64_t k;
+    uint8_t *ct, *ss;
+};
+struct EncMap {
+    const EncItem *tab;
+    const uint8_t *pk;
+    uint64_t first, seed;
+    uint8_t *ct, *ss;
+};
+struct DecItem {
+    const uint8_t *sk, *ct;
+    uint8_t *ss;
+};
+struct DecMap {
+    const DecItem *tab;
+    const uint8_t *sk, *ct;
+    uint8_t *ss;
+};
+
 struct EncSched {
     int nlev;
     EncLevel lev[16];
     int efinal, foff;  // bytes of the single remaining entry and their offset
+    uint32_t mfinal;   // radix of that entry
     int total;         // encoded length
 };
 
@@ -94,5 +119,11 @@ cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, con
                             cudaStream_t st);
 cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
                              int hash_off, cudaStream_t st);
+template <int P>
+cudaError_t launch_encap(const EncMap &em, int n, int pk_bytes, int ct_bytes, const EncSched &Spk,
+                         const EncSched &Sct, cudaStream_t st);
+template <int P>
+cudaError_t launch_decap(const DecMap &dm, int n, int pk_bytes, int sk_bytes, int ct_bytes,
+                         const EncSched &Spk, const EncSched &Sct, cudaStream_t st);
 
 }  // namespace snt

@@ -10,6 +10,7 @@
 // (no real word can equal it: bit 0 or bit 1 is cleared).
 #include "common.cuh"
 #include "kernels.h"
+#include "short.cuh"
 
 namespace snt {
 
@@ -30,56 +31,8 @@ k_sample_f(KeyMap km, int nkeys, int16_t *__restrict__ leaves, int sk_bytes, int
     const uint64_t k = d.first + (uint64_t)(key - d.key_base);
     const int t = threadIdx.x;
 
-    // words of stream 1, low bits forced; sentinels above p
-    uint32_t v[4] = {0u, 0u, 0u, 0u};
-    if (4 * t < G::p) rand_block(seed, k, STREAM_F, 0u, (uint32_t)t, v);
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int idx = 4 * t + r;
-        if (idx < G::w) v[r] = v[r] & ~1u;
-        else if (idx < G::p) v[r] = (v[r] & ~3u) | 1u;
-        else v[r] = 0xFFFFFFFFu;
-    }
-
-    // ascending bitonic sort of the 1024 slots
-#pragma unroll 1
-    for (int size = 2; size <= 1024; size <<= 1) {
-#pragma unroll 1
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride >= 4) {
-                uint32_t o[4];
-                if (stride >= 128) {
-                    *reinterpret_cast<uint4 *>(&xs[4 * t]) = make_uint4(v[0], v[1], v[2], v[3]);
-                    __syncthreads();
-                    const uint4 q = *reinterpret_cast<const uint4 *>(&xs[4 * (t ^ (stride >> 2))]);
-                    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
-                    __syncthreads();
-                } else {
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) o[r] = __shfl_xor_sync(0xffffffffu, v[r], stride >> 2);
-                }
-                const int i = 4 * t;  // same relation for all four slots of this thread
-                const bool asc = (i & size) == 0;
-                const bool low = (i & stride) == 0;  // this slot is the lower one of its pair
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const uint32_t mn = min(v[r], o[r]), mx = max(v[r], o[r]);
-                    v[r] = (low == asc) ? mn : mx;
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const bool asc = ((4 * t + r) & size) == 0;  // size 2 depends on r
-                    if ((r & stride) == 0) {
-                        const uint32_t a = v[r], b = v[r | stride];
-                        const bool sw = (a > b) == asc;
-                        v[r] = sw ? b : a;
-                        v[r | stride] = sw ? a : b;
-                    }
-                }
-            }
-        }
-    }
+    uint32_t v[4];
+    short_sorted_words<P>(seed, k, STREAM_F, v, xs);
 
     // leaves a = 3f (centred int16), zero padded to G::pad
     int16_t *leaf = leaves + (size_t)key * G::pad;

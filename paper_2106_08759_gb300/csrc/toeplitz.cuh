@@ -28,16 +28,16 @@ template <int P> struct Tp {
     static_assert((P & 3) == 1, "16-byte aligned windows need p = 1 mod 4");
 };
 
-// E table of b (centred int16, any stride) into shared memory.
-template <int P, typename T>
+// E table of b (centred, any stride) into shared memory; Q is the
+// coefficient modulus (q for R/q, 3 for R/3).
+template <int P, typename T, int Q = Geo<P>::q>
 __device__ __forceinline__ void fill_E(const T *__restrict__ b, int *Es) {
-    using G = Geo<P>;
     for (int idx = threadIdx.x; idx < Tp<P>::ESZ; idx += blockDim.x) {
         const int t = idx - Tp<P>::OFF;
         int e = 0;
         if (t >= 0 && t <= 2 * P - 2) {
             const int d = t - (P - 1);
-            e = (d >= 0) ? (int)b[d] : cmod<G::q>((int)b[P + d] + (int)b[P + d - 1]);
+            e = (d >= 0) ? (int)b[d] : cmod<Q>((int)b[P + d] + (int)b[P + d - 1]);
         }
         Es[idx] = e;
     }
@@ -52,10 +52,9 @@ __device__ __forceinline__ void fill_A(const T *__restrict__ a, int *As) {
 // acc[k][t] = sum_i A_k[i] E[j0 + t - i + p - 1] over i in [ib_lo, ib_hi)
 // (multiples of 8) for NA operands sharing E, j0 = 8 * tloc; reduced mod q
 // every 256 terms and at the end (centred).
-template <int P, int NA>
+template <int P, int NA, int Q = Geo<P>::q>
 __device__ __forceinline__ void toeplitz_tile(const int *const (&As)[NA], const int *Es, int tloc,
                                               int ib_lo, int ib_hi, int (&acc)[NA][8]) {
-    constexpr int Q = Geo<P>::q;
     const int j0 = 8 * tloc;
     const int base = Tp<P>::OFF + P - 9 + j0;  // window start for i-block 0
 #pragma unroll
@@ -108,19 +107,20 @@ __device__ __forceinline__ void toeplitz_tile(const int *const (&As)[NA], const 
 // K-way split of the i-range: thread tid = grp * NT + tloc sums i-blocks
 // [grp * per, (grp + 1) * per); group 0 ends with the full centred sums.
 // Every thread of the CTA must call it (it contains barriers when K > 1).
-template <int P, int NA, int K>
+// Threads beyond NT * K take no part (they only join the barriers).
+template <int P, int NA, int K, int Q = Geo<P>::q>
 __device__ __forceinline__ void toeplitz_split(const int *const (&As)[NA], const int *Es,
                                                int *part, int (&acc)[NA][8]) {
-    constexpr int NT = Tp<P>::NT, Q = Geo<P>::q;
+    constexpr int NT = Tp<P>::NT;
     constexpr int per = (NT + K - 1) / K;  // i-blocks of 8 per group
     const int tloc = threadIdx.x % NT, grp = threadIdx.x / NT;
     const int ib_lo = min(grp * per, NT) * 8, ib_hi = min((grp + 1) * per, NT) * 8;
-    toeplitz_tile<P, NA>(As, Es, tloc, ib_lo, ib_hi, acc);
+    toeplitz_tile<P, NA, Q>(As, Es, tloc, ib_lo, ib_hi, acc);
     if (K > 1) {
         const int j0 = 8 * tloc;
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
-            if (grp > 0)
+            if (grp > 0 && grp < K)
 #pragma unroll
                 for (int t = 0; t < 8; ++t) part[(grp - 1) * Tp<P>::p8 + j0 + t] = acc[k][t];
             __syncthreads();
@@ -145,10 +145,9 @@ __device__ __forceinline__ void toeplitz_split(const int *const (&As)[NA], const
 // c_{p-1} + a_{p-1} b_{p-1}, so
 //     c_0 = (row 0) - (row p-1) + (a_0 + a_{p-1}) b_{p-1}.
 // Contains a __syncthreads(): every thread of the CTA must call it.
-template <int P, int NA>
+template <int P, int NA, int Q = Geo<P>::q>
 __device__ __forceinline__ void toeplitz_finish(const int *const (&As)[NA], const int (&blast)[NA],
                                                 int (&acc)[NA][8], int tloc, bool active) {
-    constexpr int Q = Geo<P>::q;
     __shared__ int last_row[NA];
     const int j0 = 8 * tloc;
     if (active) {
