@@ -158,6 +158,64 @@ snt_status snt_enc(snt_ctx *ctx, int P, size_t n, const uint8_t *pk_dev, uint64_
 snt_status snt_dec(snt_ctx *ctx, int P, size_t n, const uint8_t *sk_dev, const uint8_t *ct_dev,
                    uint8_t *ss_dev, snt_stream stream);
 
+/* ---- Serving loop ----
+ * A device-resident pool of key pairs refilled by batch key generation (the
+ * pool of the paper's engNTRU batch_lib, Sec. 4.2), and a stream of
+ * handshakes served by continuous batching.  Encapsulation requests arrive as
+ * a Poisson process; every item takes a fresh pool key.  With probability
+ * dec_fraction a request is followed by a decapsulation request for the same
+ * items, arriving when the encapsulation completes; its session keys are
+ * checked against the encapsulation's.  Arrived requests wait in one FIFO per
+ * type and are admitted oldest first as launch slots, pool keys and the
+ * memory budget allow (an encapsulation whole, a decapsulation possibly over
+ * several launches); up to max_inflight launches run concurrently. */
+typedef struct {
+    int P;                   /* parameter set */
+    double rate;             /* requests per second, both types (encapsulations are
+                                Poisson at rate / (1 + dec_fraction)) */
+    double duration_s;       /* length of the arrival stream in seconds */
+    int max_items;           /* items per request: log-uniform in [1, max_items] */
+    double dec_fraction;     /* probability that an encapsulation request is followed
+                                by a decapsulation of its items, in [0, 1] */
+    size_t pool_keys;        /* key pool capacity (rounded to refill batches, >= 2 of them) */
+    size_t refill_batch;     /* keys per refill, in [max_items, 8192] */
+    size_t mem_budget;       /* device bytes for the pool and in-flight items */
+    int max_inflight;        /* concurrent launches */
+    int max_launch_items;    /* items per launch (>= max(64, max_items)) */
+    uint64_t seed;           /* keys, encapsulation randomness, arrival process */
+} snt_serve_config;
+
+typedef struct {
+    size_t requests, items_enc, items_dec, keys_generated;
+    size_t mismatches;       /* decapsulations whose key differed from the encapsulation's */
+    size_t memory_waits;     /* admissions deferred by the memory budget */
+    size_t max_queue;        /* longest request queue seen */
+    double wall_s, p50_ms, p99_ms, mean_ms, max_ms, items_per_s, requests_per_s;
+} snt_serve_stats;
+
+/* Optional record of the first `cap` encapsulation items served: key index
+ * k[i] of the encapsulation randomness (stream 3 of cfg->seed), the public
+ * key pk[i * pk_bytes ..], ciphertext ct[i * ct_bytes ..] and session key
+ * ss[i * 32 ..] (host buffers of the caller); count is set on return.  Lets a
+ * caller recompute those items alone and compare. */
+typedef struct {
+    size_t cap, count;
+    uint64_t *k;
+    uint8_t *pk, *ct, *ss;
+} snt_serve_audit;
+
+/* Runs the arrival stream in real time and returns latency statistics
+ * (arrival to completion of the launch holding the request's last item).  Synchronous.  If
+ * latency_ms is not NULL, the latency of request i (arrival order) is written
+ * to latency_ms[i] for i < latency_cap; audit may be NULL.  Uses the
+ * context's scratch for the refills and allocates the pool (within
+ * mem_budget) for the run.  Request order: encapsulation requests by arrival,
+ * each followed by its decapsulation request if it has one.  Returns
+ * SNT_ETIMEOUT if the requests have not all completed 20 s after the end of
+ * the arrival stream. */
+snt_status snt_serve_run(snt_ctx *ctx, const snt_serve_config *cfg, snt_serve_stats *out,
+                         double *latency_ms, size_t latency_cap, snt_serve_audit *audit);
+
 /* ---- Building blocks (kernel microbenchmarks; same kernels as keygen) ---- */
 
 /* c_i = a_i * b_i in R/q for i < n.  a_dev, b_dev, c_dev: n * p int16

@@ -32,6 +32,30 @@ STATUS = {0: "SNT_OK", -1: "SNT_EINVAL", -2: "SNT_ENOMEM", -3: "SNT_ECUDA",
           -4: "SNT_ETIMEOUT", -5: "SNT_EINTERNAL"}
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int), ("rate", ctypes.c_double), ("duration_s", ctypes.c_double),
+                ("max_items", ctypes.c_int), ("dec_fraction", ctypes.c_double),
+                ("pool_keys", ctypes.c_size_t), ("refill_batch", ctypes.c_size_t),
+                ("mem_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
+                ("max_launch_items", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_size_t), ("items_enc", ctypes.c_size_t),
+                ("items_dec", ctypes.c_size_t), ("keys_generated", ctypes.c_size_t),
+                ("mismatches", ctypes.c_size_t), ("memory_waits", ctypes.c_size_t),
+                ("max_queue", ctypes.c_size_t), ("wall_s", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("items_per_s", ctypes.c_double), ("requests_per_s", ctypes.c_double)]
+
+
+class ServeAudit(ctypes.Structure):
+    _fields_ = [("cap", ctypes.c_size_t), ("count", ctypes.c_size_t),
+                ("k", ctypes.POINTER(ctypes.c_uint64)), ("pk", ctypes.POINTER(ctypes.c_uint8)),
+                ("ct", ctypes.POINTER(ctypes.c_uint8)), ("ss", ctypes.POINTER(ctypes.c_uint8))]
+
+
 class SntError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status, msg))
@@ -65,6 +89,7 @@ def load():
         "snt_batch_keygen_ragged": [P, sz, P, P, P, P, P, P, P],
         "snt_rq_mul": [P, i32, sz, P, P, P, P],
         "snt_enc": [P, i32, sz, P, u64, u64, P, P, P],
+        "snt_serve_run": [P, P, P, P, sz, P],
         "snt_dec": [P, i32, sz, P, P, P, P],
         "snt_rq_inv": [P, i32, sz, P, P, P, P],
         "snt_rq_inv_latency": [P, i32, sz, P, P, P, P],
@@ -254,6 +279,41 @@ def snt_dec(ctx, P, n, sk, ct, ss, stream=None):
     import torch
     _check(load().snt_dec(ctx.handle, P, n, _dptr(sk, torch.uint8), _dptr(ct, torch.uint8),
                           _dptr(ss, torch.uint8), _stream(stream)))
+
+
+def snt_serve_run(ctx, P=761, rate=1e4, duration_s=1.0, max_items=64, dec_fraction=1.0,
+                  pool_keys=16384, refill_batch=8192, mem_budget=16 << 30, max_inflight=4,
+                  max_launch_items=4096, seed=1, audit=0):
+    """Serving loop (Poisson handshakes: encapsulation requests, each followed
+    with probability dec_fraction by the decapsulation of its items; continuous
+    batching; device key pool).  Returns (stats dict, per-request latencies in
+    ms, audit dict)."""
+    cfg = ServeConfig(P, rate, duration_s, max_items, dec_fraction, pool_keys, refill_batch,
+                      mem_budget, max_inflight, max_launch_items, seed)
+    st = ServeStats()
+    cap = int(rate * duration_s * 2) + 1024
+    lat = np.zeros(cap, np.float64)
+    pkb, _, ctb, _ = snt_param_sizes(P)
+    aud = None
+    bufs = None
+    if audit:
+        bufs = dict(k=np.zeros(audit, np.uint64), pk=np.zeros((audit, pkb), np.uint8),
+                    ct=np.zeros((audit, ctb), np.uint8), ss=np.zeros((audit, 32), np.uint8))
+        aud = ServeAudit(audit, 0,
+                         bufs["k"].ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                         bufs["pk"].ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                         bufs["ct"].ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                         bufs["ss"].ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    _check(load().snt_serve_run(ctx.handle, ctypes.byref(cfg), ctypes.byref(st),
+                                lat.ctypes.data_as(ctypes.c_void_p), cap,
+                                ctypes.byref(aud) if aud is not None else None))
+    stats = {name: getattr(st, name) for name, _ in ServeStats._fields_}
+    n = min(stats["requests"], cap)
+    audit_out = None
+    if aud is not None:
+        c = aud.count
+        audit_out = {key: v[:c] for key, v in bufs.items()}
+    return stats, lat[:n], audit_out
 
 
 def snt_rq_mul(ctx, P, n, a, b, c, stream=None):

@@ -58,7 +58,8 @@ namespace {
 
 template <int P>
 snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t first, size_t B,
-                      uint8_t *pk, uint8_t *sk, cudaStream_t st, bool batched, uint8_t *arena) {
+                      uint8_t *pk, uint8_t *sk, cudaStream_t st, bool batched, uint8_t *arena,
+                      bool inline_stream = false) {
     const Tree t = make_tree(B);
     int16_t *nodes = reinterpret_cast<int16_t *>(arena);
     int8_t *gbuf = reinterpret_cast<int8_t *>(arena + align256(t.total * pi.pad * sizeof(int16_t)));
@@ -82,9 +83,13 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     int mode = ctx->r3_overlap, lanes = ctx->r3_lanes, split = ctx->tree_split;
     const snt_ctx::Tuned &tu = ctx->tuned[pidx(P)][bbucket(B)];
     if (tu.lanes) { mode = tu.overlap; lanes = tu.lanes; split = tu.split; }
-    st = ctx->tree;
-    SNT_CUDA(cudaEventRecord(ctx->ev_fork, caller));
-    SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_fork, 0));
+    if (inline_stream) {
+        mode = 0;  // everything in order on the caller's stream
+    } else {
+        st = ctx->tree;
+        SNT_CUDA(cudaEventRecord(ctx->ev_fork, caller));
+        SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_fork, 0));
+    }
     const int n_inj = (ctx->inj_P == P) ? ctx->n_inj : 0;
     auto launch_r3 = [&](cudaStream_t r3s) -> snt_status {
         if (tm) SNT_CUDA(cudaEventRecord(ev[2], r3s));
@@ -161,9 +166,10 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     if (tm) SNT_CUDA(cudaEventRecord(ev[8], st));
     SNT_CUDA(launch_sha512_pk(km, Bi, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[9], st));
-    // join back into the caller's stream
-    SNT_CUDA(cudaEventRecord(ctx->ev_done, st));
-    SNT_CUDA(cudaStreamWaitEvent(caller, ctx->ev_done, 0));
+    if (!inline_stream) {  // join back into the caller's stream
+        SNT_CUDA(cudaEventRecord(ctx->ev_done, st));
+        SNT_CUDA(cudaStreamWaitEvent(caller, ctx->ev_done, 0));
+    }
     return SNT_OK;
 }
 
@@ -202,6 +208,19 @@ snt_status keygen_common(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, siz
 }
 
 }  // namespace
+
+snt_status snt::keygen_into(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, size_t B,
+                            uint8_t *pk, uint8_t *sk, cudaStream_t stream) {
+    ParamInfo pi;
+    if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
+    if (B == 0 || B > kMaxB) return set_error(SNT_EINVAL, "batch size %zu", B);
+    if (keygen_scratch(pi, B, false) > ctx->budget) return set_error(SNT_ENOMEM, "budget");
+    switch (P) {
+        case 653: return run_keygen<653>(ctx, pi, seed, first, B, pk, sk, stream, true, ctx->arena, true);
+        case 761: return run_keygen<761>(ctx, pi, seed, first, B, pk, sk, stream, true, ctx->arena, true);
+        default:  return run_keygen<857>(ctx, pi, seed, first, B, pk, sk, stream, true, ctx->arena, true);
+    }
+}
 
 extern "C" {
 

@@ -134,4 +134,9 @@ struct DeviceGuard {
     }
 };
 
+// Batch keygen of B keys into pk / sk entirely on `stream` (no fork onto
+// the context's own streams), for background refills of the serving pool.
+snt_status keygen_into(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, size_t B, uint8_t *pk,
+                       uint8_t *sk, cudaStream_t stream);
+
 }  // namespace snt

@@ -30,7 +30,7 @@ constexpr int KEM_THREADS = 256;
 constexpr int KEM_SPLIT = 2;  // products use 2 * p8/8 <= 256 threads
 
 template <int P>
-__global__ void __launch_bounds__(KEM_THREADS)
+__global__ void __launch_bounds__(KEM_THREADS, 4)
 k_encap(EncMap em, int n, int pk_bytes, int ct_bytes, EncSched Spk, EncSched Sct) {
     using G = Geo<P>;
     constexpr int NT = Tp<P>::NT, Q = G::q;
@@ -52,6 +52,7 @@ k_encap(EncMap em, int n, int pk_bytes, int ct_bytes, EncSched Spk, EncSched Sct
         item = em.tab[it];
     } else {
         item.pk = em.pk + (size_t)it * pk_bytes;
+        item.cache = nullptr;
         item.k = em.first + (uint64_t)it;
         item.ct = em.ct + (size_t)it * ct_bytes;
         item.ss = em.ss + (size_t)it * 32;
@@ -98,7 +99,12 @@ k_encap(EncMap em, int n, int pk_bytes, int ct_bytes, EncSched Spk, EncSched Sct
     __syncthreads();
     mixed_encode<G::pad>(R, Sct, ctb);
     const int rb = ct_bytes - 32;
-    if (tid == 0) sha512_prefixed(4, pkb, pk_bytes, nullptr, 0, hh[0]);
+    if (tid == 0) {
+        if (item.cache)
+            for (int b = 0; b < 32; ++b) hh[0][b] = item.cache[b];
+        else
+            sha512_prefixed(4, pkb, pk_bytes, nullptr, 0, hh[0]);
+    }
     if (tid == 32) sha512_prefixed(3, renc, G::small_bytes, nullptr, 0, hh[1]);
     __syncthreads();
     if (tid == 0) {
@@ -111,7 +117,7 @@ k_encap(EncMap em, int n, int pk_bytes, int ct_bytes, EncSched Spk, EncSched Sct
 }
 
 template <int P>
-__global__ void __launch_bounds__(KEM_THREADS)
+__global__ void __launch_bounds__(KEM_THREADS, 4)
 k_decap(DecMap dm, int n, int pk_bytes, int sk_bytes, int ct_bytes, EncSched Spk, EncSched Sct) {
     using G = Geo<P>;
     constexpr int NT = Tp<P>::NT, Q = G::q;

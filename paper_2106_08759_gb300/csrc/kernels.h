@@ -44,6 +44,7 @@ struct LevelMap {
 // index first + i for the encapsulation randomness).
 struct EncItem {
     const uint8_t *pk;
+    const uint8_t *cache;  // Hash_prefix(4, pk) if already known (the sk tail), else nullptr
     uint64_t k;
     uint8_t *ct, *ss;
 };
