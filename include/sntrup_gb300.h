@@ -266,7 +266,11 @@ typedef enum {
      * low-priority stream from the up-sweep's first narrow level (fewer than
      * 256 products) up to the down-sweep's first wide level, so they fill the
      * SMs the narrow levels and the root inversion leave idle */
-    SNT_OPT_R3_OVERLAP = 3
+    SNT_OPT_R3_OVERLAP = 3,
+    /* 1: each product of a tree level with at most 64 products is split by
+     * output segments over several CTAs (up to 12 SMs per product) instead of
+     * running on one SM; 0: one CTA per product on every level */
+    SNT_OPT_NARROW_SEG = 4
 } snt_option;
 
 snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);

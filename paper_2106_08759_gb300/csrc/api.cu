@@ -64,6 +64,11 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     int16_t *nodes = reinterpret_cast<int16_t *>(arena);
     int8_t *gbuf = reinterpret_cast<int8_t *>(arena + align256(t.total * pi.pad * sizeof(int16_t)));
     int16_t *leaves = nodes;
+    const int16_t *inv_leaves = leaves;  // 1/(3f) of every key, for h
+    // two ping-pong level buffers after the rest of the scratch
+    int16_t *pp[2];
+    pp[0] = reinterpret_cast<int16_t *>(arena + keygen_scratch(pi, B, false));
+    pp[1] = pp[0] + narrow_scratch(pi) / 2 / sizeof(int16_t);
     const int Bi = (int)B;
     const int sb = pi.small_bytes;
     const KeyMap km = single_batch(seed, first, Bi, pk, sk);
@@ -81,6 +86,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     //              idle without competing with the wide levels.
     const cudaStream_t caller = st;
     int mode = ctx->r3_overlap, lanes = ctx->r3_lanes, split = ctx->tree_split;
+    const bool narrow = ctx->narrow_seg != 0;
     const snt_ctx::Tuned &tu = ctx->tuned[pidx(P)][bbucket(B)];
     if (tu.lanes) { mode = tu.overlap; lanes = tu.lanes; split = tu.split; }
     if (inline_stream) {
@@ -128,8 +134,14 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                 if (s3 != SNT_OK) return s3;
                 forked = true;
             }
-            SNT_CUDA(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad, single_tree(t.n[l - 1]),
-                                       t.n[l], nodes + (size_t)t.off[l] * pi.pad, st, split));
+            if (narrow && t.n[l] <= kSegMaxNodes)
+                SNT_CUDA(launch_tree_up_seg<P>(nodes + (size_t)t.off[l - 1] * pi.pad,
+                                               single_tree(t.n[l - 1]), t.n[l],
+                                               nodes + (size_t)t.off[l] * pi.pad, st));
+            else
+                SNT_CUDA(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad,
+                                           single_tree(t.n[l - 1]), t.n[l],
+                                           nodes + (size_t)t.off[l] * pi.pad, st, split));
         }
         if (!forked) {
             const snt_status s3 = fork_r3();
@@ -141,14 +153,28 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         SNT_CUDA(launch_rq_inv_jump<P>(1, root, pi.pad, root, pi.pad, nullptr, ctx->d_err, ERR_ROOT,
                                        st));
         if (tm) SNT_CUDA(cudaEventRecord(ev[5], st));
+        // Inverses of level l live at par: in place over the level's
+        // products, or, after an output-split level, in one of the two
+        // ping-pong buffers (children of one split level at a time).
+        const int16_t *par = root;
+        int ping = 0;
         for (int l = L; l >= 1; --l) {
             if (mode == 2 && !joined && t.n[l] >= kNarrow) {
                 SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
                 joined = true;
             }
-            SNT_CUDA(launch_tree_down<P>(nodes + (size_t)t.off[l] * pi.pad, single_tree(t.n[l - 1]),
-                                         t.n[l], nodes + (size_t)t.off[l - 1] * pi.pad, st, split));
+            int16_t *lch = nodes + (size_t)t.off[l - 1] * pi.pad;
+            if (narrow && t.n[l] <= kSegMaxNodes) {
+                int16_t *out = pp[ping];
+                ping ^= 1;
+                SNT_CUDA(launch_tree_down_seg<P>(par, single_tree(t.n[l - 1]), t.n[l], lch, out, st));
+                par = out;
+            } else {
+                SNT_CUDA(launch_tree_down<P>(par, single_tree(t.n[l - 1]), t.n[l], lch, st, split));
+                par = lch;
+            }
         }
+        inv_leaves = par;
         if (tm) SNT_CUDA(cudaEventRecord(ev[6], st));
     } else {
         SNT_CUDA(launch_rq_inv<P>(Bi, leaves, pi.pad, leaves, pi.pad, nullptr, ctx->d_err, ERR_ROOT,
@@ -161,8 +187,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     }
     if (!joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     if (tm) SNT_CUDA(cudaEventRecord(ev[7], st));
-    SNT_CUDA(launch_finalize<P>(km, Bi, gbuf, leaves, pi.pk_bytes, pi.sk_bytes, 2 * sb, pi.sched,
-                                st));
+    SNT_CUDA(launch_finalize<P>(km, Bi, gbuf, inv_leaves, pi.pk_bytes, pi.sk_bytes, 2 * sb,
+                                pi.sched, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[8], st));
     SNT_CUDA(launch_sha512_pk(km, Bi, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[9], st));
@@ -181,7 +207,7 @@ snt_status keygen_common(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, siz
     if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     if (B == 0 || B > kMaxB) return set_error(SNT_EINVAL, "batch size %zu outside [1, %zu]", B, kMaxB);
     if (!pk || !sk) return set_error(SNT_EINVAL, "null output buffer");
-    const size_t need = keygen_scratch(pi, B, host_out);
+    const size_t need = keygen_arena(pi, B, host_out);
     if (need > ctx->budget)
         return set_error(SNT_ENOMEM, "batch of %zu keys needs %zu scratch bytes, budget %zu", B, need,
                     ctx->budget);
@@ -190,8 +216,7 @@ snt_status keygen_common(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, siz
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint8_t *dpk = pk, *dsk = sk;
     if (host_out) {
-        const Tree t = make_tree(B);
-        size_t o = align256(t.total * pi.pad * sizeof(int16_t)) + align256(B * pi.pad);
+        const size_t o = staging_offset(pi, B);
         dpk = ctx->arena + o;
         dsk = ctx->arena + o + align256(B * pi.pk_bytes);
     }
@@ -214,7 +239,7 @@ snt_status snt::keygen_into(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, 
     ParamInfo pi;
     if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     if (B == 0 || B > kMaxB) return set_error(SNT_EINVAL, "batch size %zu", B);
-    if (keygen_scratch(pi, B, false) > ctx->budget) return set_error(SNT_ENOMEM, "budget");
+    if (keygen_arena(pi, B, false) > ctx->budget) return set_error(SNT_ENOMEM, "budget");
     switch (P) {
         case 653: return run_keygen<653>(ctx, pi, seed, first, B, pk, sk, stream, true, ctx->arena, true);
         case 761: return run_keygen<761>(ctx, pi, seed, first, B, pk, sk, stream, true, ctx->arena, true);
@@ -305,7 +330,7 @@ snt_status snt_ctx_max_batch(snt_ctx *ctx, int P, size_t *max_B) {
     size_t lo = 0, hi = kMaxB;
     while (lo < hi) {
         const size_t mid = (lo + hi + 1) / 2;
-        if (keygen_scratch(pi, mid, true) <= ctx->budget) lo = mid; else hi = mid - 1;
+        if (keygen_arena(pi, mid, true) <= ctx->budget) lo = mid; else hi = mid - 1;
     }
     *max_B = lo;
     return SNT_OK;
@@ -484,6 +509,10 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             if (value < 0 || value > 2) return set_error(SNT_EINVAL, "R/3 overlap is 0, 1 or 2");
             ctx->r3_overlap = value;
             return SNT_OK;
+        case SNT_OPT_NARROW_SEG:
+            if (value != 0 && value != 1) return set_error(SNT_EINVAL, "narrow split is 0 or 1");
+            ctx->narrow_seg = value;
+            return SNT_OK;
         default:
             return set_error(SNT_EINVAL, "unknown option %d", option);
     }
@@ -495,6 +524,7 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
         case SNT_OPT_R3_LANES: *value = ctx->r3_lanes; return SNT_OK;
         case SNT_OPT_TREE_SPLIT: *value = ctx->tree_split; return SNT_OK;
         case SNT_OPT_R3_OVERLAP: *value = ctx->r3_overlap; return SNT_OK;
+        case SNT_OPT_NARROW_SEG: *value = ctx->narrow_seg; return SNT_OK;
         default: return set_error(SNT_EINVAL, "unknown option %d", option);
     }
 }
@@ -505,12 +535,11 @@ snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *spli
     ParamInfo pi;
     if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     if (B == 0 || B > kMaxB) return set_error(SNT_EINVAL, "batch size %zu out of range", B);
-    if (keygen_scratch(pi, B, true) > ctx->budget)
+    if (keygen_arena(pi, B, true) > ctx->budget)
         return set_error(SNT_ENOMEM, "batch of %zu keys exceeds the budget", B);
     DeviceGuard dg(ctx->device);
     // staging for the keys inside the arena (as for the host-buffer call)
-    const Tree t = make_tree(B);
-    const size_t o = align256(t.total * pi.pad * sizeof(int16_t)) + align256(B * pi.pad);
+    const size_t o = staging_offset(pi, B);
     uint8_t *dpk = ctx->arena + o, *dsk = ctx->arena + o + align256(B * pi.pk_bytes);
     snt_stream ts = reinterpret_cast<snt_stream>(ctx->tune);
     cudaEvent_t e0, e1;

@@ -45,6 +45,7 @@ struct snt_ctx {
     int r3_lanes = snt::kDefaultR3Lanes;
     int tree_split = snt::kDefaultTreeSplit;
     int r3_overlap = snt::kDefaultR3Overlap;
+    int narrow_seg = snt::kDefaultNarrowSeg;
     // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
     struct Tuned { int lanes = 0, split = 0, overlap = 0; };
     Tuned tuned[3][25];

@@ -17,6 +17,7 @@ namespace snt {
 constexpr int kDefaultR3Lanes = 4;     // lanes per element of the R/3 divstep kernel
 constexpr int kDefaultTreeSplit = 8;   // largest split of one product over thread groups
 constexpr int kDefaultR3Overlap = 1;   // R/3 on its own low-priority stream
+constexpr int kDefaultNarrowSeg = 1;   // output-split narrow tree levels
 
 // Records a one-line error message (snt_last_error_string) and returns s.
 snt_status set_error(snt_status s, const char *fmt, ...);
@@ -121,6 +122,21 @@ inline size_t keygen_scratch(const ParamInfo &pi, size_t B, bool host_out) {
     size_t bytes = align256(t.total * pi.pad * sizeof(int16_t)) + align256(B * pi.pad);
     if (host_out) bytes += align256(B * pi.pk_bytes) + align256(B * pi.sk_bytes);
     return bytes;
+}
+
+// Arena bytes of a keygen call through a context: the scratch above plus two
+// ping-pong level buffers for the output-split narrow levels of the
+// down-sweep (at most 2 * kSegMaxNodes children per level), placed after it.
+inline size_t narrow_scratch(const ParamInfo &pi) {
+    return 2 * align256((size_t)2 * kSegMaxNodes * pi.pad * sizeof(int16_t));
+}
+inline size_t keygen_arena(const ParamInfo &pi, size_t B, bool host_out) {
+    return keygen_scratch(pi, B, host_out) + narrow_scratch(pi);
+}
+// Arena layout of a context keygen call: tree nodes, g rows, the ping-pong
+// buffers, then (host-buffer calls) the pk and sk staging at this offset.
+inline size_t staging_offset(const ParamInfo &pi, size_t B) {
+    return keygen_scratch(pi, B, false) + narrow_scratch(pi);
 }
 
 struct DeviceGuard {

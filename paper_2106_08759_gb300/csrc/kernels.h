@@ -103,6 +103,16 @@ cudaError_t launch_tree_up(const int16_t *lin, const LevelMap &lm, int n_out, in
 template <int P>
 cudaError_t launch_tree_down(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t *lch,
                              cudaStream_t st, int max_split);
+// Output-split narrow levels (at most kSegMaxNodes products per launch): the
+// up-sweep as launch_tree_up; the down-sweep writes the children's inverses
+// to lout (indexed like lch) instead of over the children.
+constexpr int kSegMaxNodes = 64;
+template <int P>
+cudaError_t launch_tree_up_seg(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
+                               cudaStream_t st);
+template <int P>
+cudaError_t launch_tree_down_seg(const int16_t *lpar, const LevelMap &lm, int n_par,
+                                 const int16_t *lch, int16_t *lout, cudaStream_t st);
 template <int P>
 cudaError_t launch_mul_batch(int n, const int16_t *a, const int16_t *b, int16_t *c,
                              cudaStream_t st);

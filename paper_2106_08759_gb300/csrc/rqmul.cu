@@ -100,6 +100,134 @@ k_tree_down(const int16_t *__restrict__ lpar, LevelMap lm, int16_t *__restrict__
     }
 }
 
+// Output-split forms of both sweeps for the narrow levels (toeplitz_seg):
+// grid (nodes, S).  The down-sweep writes the children's inverses to a
+// separate level buffer `lout` (same node indexing as lch), since the other
+// segments of the same product still read the children.
+template <int P, int S, int K>
+__global__ void __launch_bounds__(SegGeo<P, S>::TS * K)
+k_tree_up_seg(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict__ lout) {
+    using G = Geo<P>;
+    __shared__ __align__(16) int As[Tp<P>::p8];
+    __shared__ __align__(16) int Es[Tp<P>::ESZ];
+    __shared__ int part[K > 1 ? (K - 1) * SegGeo<P, S>::TS * 8 : 1];
+    const int j = blockIdx.x, seg = blockIdx.y;
+    int idx = j, base = 0, n_in = lm.n_in;
+    if (lm.nb > 0) {
+        const int b = level_batch(lm.pre_out, lm.nb, j);
+        idx = j - lm.pre_out[b];
+        base = lm.pre_in[b];
+        n_in = lm.pre_in[b + 1] - base;
+    }
+    const int16_t *a = lin + (size_t)(base + 2 * idx) * G::pad;
+    int16_t *c = lout + (size_t)j * G::pad;
+    if (2 * idx + 1 >= n_in) {  // unpaired: move up unchanged (segment 0 copies)
+        if (seg == 0)
+            for (int i = threadIdx.x; i < G::pad; i += blockDim.x) c[i] = a[i];
+        return;
+    }
+    const int16_t *b = a + G::pad;
+    fill_A<P>(a, As);
+    fill_E<P>(b, Es);
+    __syncthreads();
+    int acc[1][8], tloc;
+    bool active;
+    const int *const A1[1] = {As};
+    const int bl[1] = {(int)b[P - 1]};
+    toeplitz_seg<P, 1, S, K>(A1, Es, bl, part, seg, acc, tloc, active);
+    if (active) store_tile<P>(c, acc[0], G::pad, tloc);
+}
+
+template <int P, int S, int K>
+__global__ void __launch_bounds__(SegGeo<P, S>::TS * K)
+k_tree_down_seg(const int16_t *__restrict__ lpar, LevelMap lm, const int16_t *__restrict__ lch,
+                int16_t *__restrict__ lout) {
+    using G = Geo<P>;
+    __shared__ __align__(16) int Xs[Tp<P>::p8];
+    __shared__ __align__(16) int Ys[Tp<P>::p8];
+    __shared__ __align__(16) int Es[Tp<P>::ESZ];
+    __shared__ int part[K > 1 ? (K - 1) * SegGeo<P, S>::TS * 8 : 1];
+    const int j = blockIdx.x, seg = blockIdx.y;
+    int idx = j, base = 0, n_ch = lm.n_in;
+    if (lm.nb > 0) {
+        const int b = level_batch(lm.pre_out, lm.nb, j);
+        idx = j - lm.pre_out[b];
+        base = lm.pre_in[b];
+        n_ch = lm.pre_in[b + 1] - base;
+    }
+    const int16_t *T = lpar + (size_t)j * G::pad;
+    const int16_t *x = lch + (size_t)(base + 2 * idx) * G::pad;
+    int16_t *ox = lout + (size_t)(base + 2 * idx) * G::pad;
+    if (2 * idx + 1 >= n_ch) {  // unpaired child: its inverse is the parent's
+        if (seg == 0)
+            for (int i = threadIdx.x; i < G::pad; i += blockDim.x) ox[i] = T[i];
+        return;
+    }
+    const int16_t *y = x + G::pad;
+    int16_t *oy = ox + G::pad;
+    fill_A<P>(x, Xs);
+    fill_A<P>(y, Ys);
+    fill_E<P>(T, Es);
+    __syncthreads();
+    int acc[2][8], tloc;
+    bool active;
+    const int *const A2[2] = {Ys, Xs};
+    const int tl = (int)T[P - 1];
+    const int bl[2] = {tl, tl};
+    toeplitz_seg<P, 2, S, K>(A2, Es, bl, part, seg, acc, tloc, active);
+    if (active) {
+        store_tile<P>(ox, acc[0], G::pad, tloc);  // 1/x = T * y
+        store_tile<P>(oy, acc[1], G::pad, tloc);  // 1/y = T * x
+    }
+}
+
+// Output split of a narrow level of n products: (S, K), S = 1 for a level
+// wide enough to fill the GPU with one CTA per product.
+inline void seg_plan(int n, int &S, int &K) {
+    S = 1; K = 1;
+    if (n <= 8)       { S = 12; K = 16; }
+    else if (n <= 16) { S = 8;  K = 16; }
+    else if (n <= 32) { S = 4;  K = 8; }
+    else if (n <= kSegMaxNodes) { S = 2; K = 4; }
+}
+
+template <int P>
+cudaError_t launch_tree_up_seg(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
+                               cudaStream_t st) {
+    int S, K;
+    seg_plan(n_out, S, K);
+#define SNT_UP_SEG(SS, KK) \
+    k_tree_up_seg<P, SS, KK><<<dim3(n_out, SS), SegGeo<P, SS>::TS * KK, 0, st>>>(lin, lm, lout)
+    switch (S) {
+        case 12: SNT_UP_SEG(12, 16); break;
+        case 8: SNT_UP_SEG(8, 16); break;
+        case 4: SNT_UP_SEG(4, 8); break;
+        case 2: SNT_UP_SEG(2, 4); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef SNT_UP_SEG
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_tree_down_seg(const int16_t *lpar, const LevelMap &lm, int n_par,
+                                 const int16_t *lch, int16_t *lout, cudaStream_t st) {
+    int S, K;
+    seg_plan(n_par, S, K);
+#define SNT_DOWN_SEG(SS, KK)                                                              \
+    k_tree_down_seg<P, SS, KK><<<dim3(n_par, SS), SegGeo<P, SS>::TS * KK, 0, st>>>(lpar, lm, \
+                                                                                  lch, lout)
+    switch (S) {
+        case 12: SNT_DOWN_SEG(12, 16); break;
+        case 8: SNT_DOWN_SEG(8, 16); break;
+        case 4: SNT_DOWN_SEG(4, 8); break;
+        case 2: SNT_DOWN_SEG(2, 4); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef SNT_DOWN_SEG
+    return cudaGetLastError();
+}
+
 // c_e = a_e * b_e, n products, all operands stride p (microbenchmark layout).
 template <int P>
 __global__ void __launch_bounds__(Tp<P>::NT)
@@ -169,7 +297,11 @@ cudaError_t launch_mul_batch(int n, const int16_t *a, const int16_t *b, int16_t 
     template cudaError_t launch_tree_down<P>(const int16_t *, const LevelMap &, int, int16_t *,\
                                              cudaStream_t, int);                               \
     template cudaError_t launch_mul_batch<P>(int, const int16_t *, const int16_t *, int16_t *, \
-                                             cudaStream_t);
+                                             cudaStream_t);                                    \
+    template cudaError_t launch_tree_up_seg<P>(const int16_t *, const LevelMap &, int,         \
+                                               int16_t *, cudaStream_t);                       \
+    template cudaError_t launch_tree_down_seg<P>(const int16_t *, const LevelMap &, int,       \
+                                                 const int16_t *, int16_t *, cudaStream_t);
 SNT_MUL_INST(653)
 SNT_MUL_INST(761)
 SNT_MUL_INST(857)

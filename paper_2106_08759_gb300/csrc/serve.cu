@@ -126,7 +126,7 @@ extern "C" snt_status snt_serve_run(snt_ctx *ctx, const snt_serve_config *cfg,
     const size_t need = pool_bytes + (size_t)S * launch_bytes;
     if (need > cfg->mem_budget)
         return set_error(SNT_ENOMEM, "serving state needs %zu bytes, budget %zu", need, cfg->mem_budget);
-    if (keygen_scratch(pi, (size_t)chunk, false) > ctx->budget)
+    if (keygen_arena(pi, (size_t)chunk, false) > ctx->budget)
         return set_error(SNT_ENOMEM, "refill batch of %d keys exceeds the context budget", chunk);
 
     DeviceGuard dg(ctx->device);

@@ -170,6 +170,88 @@ __device__ __forceinline__ void toeplitz_finish(const int *const (&As)[NA], cons
     }
 }
 
+// Output-split form, for the narrow tree levels whose few products would
+// each keep one SM busy for the whole level: the NT output tiles are cut into
+// S segments of TS tiles, each segment is one CTA (so a product spreads over
+// S SMs), and each CTA splits the i-range over K thread groups (TS * K
+// threads).  No barrier is needed between CTAs: every segment reads all of A
+// and E and writes only its own outputs.  The output-0 fix needs row p - 1,
+// which lives in the last segment, so segment 0 recomputes that one row as a
+// dot product (warp 0).
+template <int P, int S> struct SegGeo {
+    static constexpr int NT = Tp<P>::NT;
+    static constexpr int TS = (NT + S - 1) / S;  // tiles per segment
+};
+
+// Finished, centred outputs of tile tloc = seg * TS + (thread % TS) for the
+// threads that return active = true (group 0, tloc < NT); the a_j b_{p-1}
+// term and the output-0 fix are included, outputs j >= p are zero.  Every
+// thread of the CTA must call it (it contains barriers).
+template <int P, int NA, int S, int K, int Q = Geo<P>::q>
+__device__ __forceinline__ void toeplitz_seg(const int *const (&As)[NA], const int *Es,
+                                             const int (&blast)[NA], int *part, int seg,
+                                             int (&acc)[NA][8], int &tloc, bool &active) {
+    constexpr int NT = Tp<P>::NT, TS = SegGeo<P, S>::TS;
+    constexpr int per = (NT + K - 1) / K;  // i-blocks of 8 per group
+    __shared__ int last_row[NA];
+    const int tl = threadIdx.x % TS, grp = threadIdx.x / TS;
+    tloc = seg * TS + tl;
+    const bool tile = tloc < NT && grp < K;
+    if (tile) {
+        const int ib_lo = min(grp * per, NT) * 8, ib_hi = min((grp + 1) * per, NT) * 8;
+        toeplitz_tile<P, NA, Q>(As, Es, tloc, ib_lo, ib_hi, acc);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NA; ++k)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc[k][t] = 0;
+    }
+    if (seg == 0 && threadIdx.x < 32) {
+        // row p-1: sum_i A_i E[2p - 2 - i]; at most ceil(p/32) <= 27 terms of
+        // <= (q-1)^2/4 per lane before the reduction, below 2^31
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            int r = 0;
+            for (int i = threadIdx.x; i < P; i += 32) r += As[k][i] * Es[Tp<P>::OFF + 2 * P - 2 - i];
+            r = cmod<Q>(r);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+            if (threadIdx.x == 0) last_row[k] = cmod<Q>(r + As[k][P - 1] * blast[k]);
+        }
+    }
+    const int j0 = 8 * tloc;
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+        if (K > 1 && tile && grp > 0)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) part[((grp - 1) * TS + tl) * 8 + t] = acc[k][t];
+        __syncthreads();
+        if (K > 1 && tile && grp == 0)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                int sum = acc[k][t];
+                for (int g = 0; g < K - 1; ++g) sum += part[(g * TS + tl) * 8 + t];
+                acc[k][t] = cmod<Q>(sum);
+            }
+        __syncthreads();
+    }
+    active = tile && grp == 0;
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int j = j0 + t;
+                int v = acc[k][t];
+                if (j >= 1 && j < P) v += As[k][j] * blast[k];
+                acc[k][t] = (j < P) ? cmod<Q>(v) : 0;
+            }
+            if (tloc == 0)
+                acc[k][0] = cmod<Q>(acc[k][0] - last_row[k] + (As[k][0] + As[k][P - 1]) * blast[k]);
+        }
+    }
+}
+
 // Stores 8 outputs (j0 .. j0+7) as int16; pads from p8 to `pad` are zeroed by
 // the threads that own the last tile.
 template <int P>

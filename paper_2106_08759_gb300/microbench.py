@@ -1,6 +1,6 @@
 """Kernel microbenchmark (sntrup761 building blocks) on one GPU.
 
-    python -m paper_2106_08759_gb300.microbench [--quick]
+    python -m paper_2106_08759_gb300.microbench [--quick] [--sweep] [--keygen-only B]
 
 Times each building block alone (CUDA events on the launching stream, L2
 flushed before every timed launch) on seeded synthetic inputs:
@@ -28,6 +28,9 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--sweep", action="store_true",
                     help="also time the layout options of the R/3 kernel and of keygen")
+    ap.add_argument("--keygen-only", type=int, default=0, metavar="B",
+                    help="only run batch keygen of B keys --reps times with the default "
+                         "options (a small, fixed target for a profiler)")
     args = ap.parse_args()
 
     import numpy as np
@@ -59,6 +62,20 @@ def main():
 
     def t(x, dt):
         return torch.from_numpy(np.ascontiguousarray(x)).to(dtype=dt, device=dev)
+
+    if args.keygen_only:
+        B = args.keygen_only
+        pkb, skb, _, _ = snt.snt_param_sizes(P)
+        pk = torch.empty(B * pkb, dtype=torch.uint8, device=dev)
+        sk = torch.empty(B * skb, dtype=torch.uint8, device=dev)
+        for i in range(args.reps):
+            flush.zero_()
+            snt.snt_batch_keygen(ctx, P, 1, i * B, B, pk, sk, st)
+        torch.cuda.synchronize()
+        ctx.sync()
+        print(json.dumps({"keygen_only": B, "reps": args.reps}))
+        ctx.close()
+        return
 
     out = {"p": p}
     n = (1 << 16) if args.quick else (1 << 20)
@@ -122,23 +139,25 @@ def main():
     out["keygen_4096_ms"] = tot / args.reps
     if args.sweep:
         sweep = {}
-        for overlap in (0, 1, 2):
-            for lanes in (4, 8):
-                for split in (4, 8):
-                    ctx.set_option(snt.SNT_OPT_R3_OVERLAP, overlap)
-                    ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
-                    ctx.set_option(snt.SNT_OPT_TREE_SPLIT, split)
-                    snt.snt_batch_keygen(ctx, P, 1, 0, Bk, pk, sk)
-                    ctx.phase_times()
-                    tot = 0.0
-                    for i in range(args.reps):
-                        flush.zero_()
-                        snt.snt_batch_keygen(ctx, P, 1, (i + 1) * Bk, Bk, pk, sk)
-                        ph = ctx.phase_times()
-                        tot += ph["total"]
-                    key = "overlap%d_lanes%d_split%d" % (overlap, lanes, split)
-                    sweep[key] = {"ms": round(tot / args.reps, 4),
-                                  "phases": {k: round(v, 4) for k, v in ph.items()}}
+        for narrow in (0, 1):
+            for overlap in (0, 1, 2):
+                for lanes in (4, 8):
+                    for split in (4, 8):
+                        ctx.set_option(snt.SNT_OPT_NARROW_SEG, narrow)
+                        ctx.set_option(snt.SNT_OPT_R3_OVERLAP, overlap)
+                        ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
+                        ctx.set_option(snt.SNT_OPT_TREE_SPLIT, split)
+                        snt.snt_batch_keygen(ctx, P, 1, 0, Bk, pk, sk)
+                        ctx.phase_times()
+                        tot = 0.0
+                        for i in range(args.reps):
+                            flush.zero_()
+                            snt.snt_batch_keygen(ctx, P, 1, (i + 1) * Bk, Bk, pk, sk)
+                            ph = ctx.phase_times()
+                            tot += ph["total"]
+                        key = "narrow%d_overlap%d_lanes%d_split%d" % (narrow, overlap, lanes, split)
+                        sweep[key] = {"ms": round(tot / args.reps, 4),
+                                      "phases": {k: round(v, 4) for k, v in ph.items()}}
         out["keygen_4096_sweep"] = sweep
     ctx.close()
 

@@ -76,6 +76,28 @@ def test_tuning_options_do_not_change_keys(snt, ctx, opts):
     assert first_mismatch(got857[0], rpk) is None and first_mismatch(got857[1], rsk) is None
 
 
+@pytest.mark.parametrize("B", [2, 3, 9, 17, 33, 65, 130, 257])
+def test_output_split_narrow_levels_give_the_same_keys(snt, ctx, B):
+    # narrow tree levels split by output segments over several CTAs (up and
+    # down, with the ping-pong inverse buffers) against one CTA per product;
+    # B spans every segment plan and unpaired nodes at several levels
+    ctx.set_option(snt.SNT_OPT_NARROW_SEG, 0)
+    try:
+        ref = gpu_keygen(snt, ctx, 761, 77, 1000, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_NARROW_SEG, 1)
+    got = gpu_keygen(snt, ctx, 761, 77, 1000, B)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+@pytest.mark.parametrize("P,B", [(653, 9), (857, 33)])
+def test_output_split_narrow_levels_vs_oracle(snt, ctx, P, B):
+    assert ctx.get_option(snt.SNT_OPT_NARROW_SEG) == 1
+    pk, sk = gpu_keygen(snt, ctx, P, 78, 3, B)
+    rpk, rsk = oracle.keygen_batch(P, 78, 3, B)
+    assert first_mismatch(pk, rpk) is None and first_mismatch(sk, rsk) is None
+
+
 def test_autotuned_layouts_give_the_same_keys(snt):
     with snt.Context(0, 64 << 20) as c:
         choice = c.autotune(761, 48)
