@@ -306,7 +306,11 @@ snt_status snt_ctx_phase_times(snt_ctx *ctx, float *ms, int n);
 
 /* Measures the device's integer-pipe throughput with a register-resident
  * stream of independent instructions: kind 0 = LOP3 (3-input logic, the
- * bit-sliced R/3 work), kind 1 = IMAD (32-bit multiply-add, the R/q products).
+ * bit-sliced R/3 work), kind 1 = IMAD (32-bit multiply-add, the R/q
+ * products), kind 2 = DP4A (4-way 8-bit dot product with 32-bit accumulate),
+ * kind 3 = IMAD and LOP3 alternating (both pipes' combined issue rate),
+ * kind 4 = PRMT (byte permute), kind 5 = SHF (funnel shift), kind 6 = DP4A
+ * and PRMT alternating.
  * Writes instructions per second (summed over all SMs) to *ops_per_s and the
  * SM count to *sms.  Synchronous; uses no scratch. */
 snt_status snt_measure_int_peak(int device, int kind, double *ops_per_s, int *sms);

@@ -342,7 +342,8 @@ def snt_r3_inv(ctx, P, n, g, out, ok, stream=None):
 
 
 def snt_measure_int_peak(device=0, kind=0):
-    """(instructions/s, SM count) of the LOP3 (kind 0) or IMAD (kind 1) stream."""
+    """(instructions/s, SM count) of an instruction stream: 0 LOP3, 1 IMAD,
+    2 DP4A, 3 IMAD+LOP3, 4 PRMT, 5 SHF, 6 DP4A+PRMT."""
     v = ctypes.c_double()
     n = ctypes.c_int()
     _check(load().snt_measure_int_peak(device, kind, ctypes.byref(v), ctypes.byref(n)))

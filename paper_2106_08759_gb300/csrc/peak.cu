@@ -1,6 +1,7 @@
 // peak.cu -- integer-pipe throughput microbenchmark used as the denominator
 // of the ALU roofline (LOP3 for the bit-sliced R/3 divsteps, IMAD for the R/q
-// products).  Eight independent register chains per thread, inline PTX so
+// products), plus DP4A (four 8-bit products per instruction), PRMT and funnel
+// shifts (byte windows), and two mixes (whether two pipes issue side by side).  Eight independent register chains per thread, inline PTX so
 // every counted operation is exactly one instruction, grid = 8 CTAs of 256
 // threads per SM.
 #include <cstdio>
@@ -26,6 +27,51 @@ __global__ void __launch_bounds__(256) k_int_peak(int iters, unsigned seed, unsi
                 asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a5) : "r"(b), "r"(c));
                 asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a6) : "r"(b), "r"(c));
                 asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a7) : "r"(b), "r"(c));
+            } else if (KIND == 2) {
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a0) : "r"(b), "r"(c));
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a1) : "r"(b), "r"(c));
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a2) : "r"(b), "r"(c));
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a3) : "r"(b), "r"(c));
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a4) : "r"(b), "r"(c));
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a5) : "r"(b), "r"(c));
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a6) : "r"(b), "r"(c));
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a7) : "r"(b), "r"(c));
+            } else if (KIND == 3) {
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a0) : "r"(b), "r"(c));
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a1) : "r"(b), "r"(c));
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a2) : "r"(b), "r"(c));
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a3) : "r"(b), "r"(c));
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a4) : "r"(b), "r"(c));
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a5) : "r"(b), "r"(c));
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a6) : "r"(b), "r"(c));
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a7) : "r"(b), "r"(c));
+            } else if (KIND == 4) {
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a0) : "r"(b));
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a1) : "r"(b));
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a2) : "r"(b));
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a3) : "r"(b));
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a4) : "r"(b));
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a5) : "r"(b));
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a6) : "r"(b));
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a7) : "r"(b));
+            } else if (KIND == 5) {
+                asm volatile("shf.r.wrap.b32 %0, %0, %1, %2;" : "+r"(a0) : "r"(b), "r"(c));
+                asm volatile("shf.r.wrap.b32 %0, %0, %1, %2;" : "+r"(a1) : "r"(b), "r"(c));
+                asm volatile("shf.r.wrap.b32 %0, %0, %1, %2;" : "+r"(a2) : "r"(b), "r"(c));
+                asm volatile("shf.r.wrap.b32 %0, %0, %1, %2;" : "+r"(a3) : "r"(b), "r"(c));
+                asm volatile("shf.r.wrap.b32 %0, %0, %1, %2;" : "+r"(a4) : "r"(b), "r"(c));
+                asm volatile("shf.r.wrap.b32 %0, %0, %1, %2;" : "+r"(a5) : "r"(b), "r"(c));
+                asm volatile("shf.r.wrap.b32 %0, %0, %1, %2;" : "+r"(a6) : "r"(b), "r"(c));
+                asm volatile("shf.r.wrap.b32 %0, %0, %1, %2;" : "+r"(a7) : "r"(b), "r"(c));
+            } else if (KIND == 6) {
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a0) : "r"(b), "r"(c));
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a1) : "r"(b));
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a2) : "r"(b), "r"(c));
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a3) : "r"(b));
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a4) : "r"(b), "r"(c));
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a5) : "r"(b));
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(a6) : "r"(b), "r"(c));
+                asm volatile("prmt.b32 %0, %0, %1, 0x3214;" : "+r"(a7) : "r"(b));
             } else {
                 asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a0) : "r"(b), "r"(c));
                 asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a1) : "r"(b), "r"(c));
@@ -45,7 +91,7 @@ __global__ void __launch_bounds__(256) k_int_peak(int iters, unsigned seed, unsi
 }  // namespace
 
 extern "C" snt_status snt_measure_int_peak(int device, int kind, double *ops_per_s, int *sms) {
-    if (!ops_per_s || (kind != 0 && kind != 1)) return SNT_EINVAL;
+    if (!ops_per_s || kind < 0 || kind > 6) return SNT_EINVAL;
     int prev = 0;
     if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return SNT_ECUDA;
     cudaDeviceProp prop;
@@ -59,8 +105,15 @@ extern "C" snt_status snt_measure_int_peak(int device, int kind, double *ops_per
     float best = 1e30f;
     for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
         cudaEventRecord(t0);
-        if (kind == 0) k_int_peak<0><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink);
-        else k_int_peak<1><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink);
+        switch (kind) {
+            case 0: k_int_peak<0><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
+            case 1: k_int_peak<1><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
+            case 2: k_int_peak<2><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
+            case 3: k_int_peak<3><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
+            case 4: k_int_peak<4><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
+            case 5: k_int_peak<5><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
+            default: k_int_peak<6><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
+        }
         cudaEventRecord(t1);
         e = cudaEventSynchronize(t1);
         float ms = 0;
