@@ -270,7 +270,14 @@ typedef enum {
     /* 1: each product of a tree level with at most 64 products is split by
      * output segments over several CTAs (up to 12 SMs per product) instead of
      * running on one SM; 0: one CTA per product on every level */
-    SNT_OPT_NARROW_SEG = 4
+    SNT_OPT_NARROW_SEG = 4,
+    /* engine of the R/q products (tree, h excluded, snt_rq_mul): 0 CUDA-core
+     * Toeplitz products on the IMAD pipe; 1 the same Toeplitz products on
+     * the tensor cores (warp MMA on exact 6-bit f16 limbs, f32 accumulate) */
+    SNT_OPT_RQ_ENGINE = 5,
+    /* tensor-core engine: MMA tiles (128 outputs each) per warp, 1, 2 or 3;
+     * a product's tiles are spread over the warps of one CTA */
+    SNT_OPT_MMA_TILES = 6
 } snt_option;
 
 snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);
@@ -310,7 +317,9 @@ snt_status snt_ctx_phase_times(snt_ctx *ctx, float *ms, int n);
  * products), kind 2 = DP4A (4-way 8-bit dot product with 32-bit accumulate),
  * kind 3 = IMAD and LOP3 alternating (both pipes' combined issue rate),
  * kind 4 = PRMT (byte permute), kind 5 = SHF (funnel shift), kind 6 = DP4A
- * and PRMT alternating.
+ * and PRMT alternating; kinds 7 and 8 are warp-level tensor MMA streams
+ * (m16n8k16 f16 -> f32 and m16n8k32 s8 -> s32) and report multiply-adds
+ * per second instead of instructions.
  * Writes instructions per second (summed over all SMs) to *ops_per_s and the
  * SM count to *sms.  Synchronous; uses no scratch. */
 snt_status snt_measure_int_peak(int device, int kind, double *ops_per_s, int *sms);

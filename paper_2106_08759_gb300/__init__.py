@@ -22,6 +22,7 @@ PARAMS = {653: (653, 4621, 288), 761: (761, 4591, 286), 857: (857, 5167, 322)}
 
 # tuning options (snt_option)
 SNT_OPT_R3_LANES, SNT_OPT_TREE_SPLIT, SNT_OPT_R3_OVERLAP, SNT_OPT_NARROW_SEG = 1, 2, 3, 4
+SNT_OPT_RQ_ENGINE, SNT_OPT_MMA_TILES = 5, 6
 
 # phase names of snt_ctx_phase_times (SNT_NPHASES entries)
 PHASES = ("sample_f", "r3_inv", "tree_up", "root_inv", "tree_down", "h_encode", "sha512",
@@ -343,7 +344,8 @@ def snt_r3_inv(ctx, P, n, g, out, ok, stream=None):
 
 def snt_measure_int_peak(device=0, kind=0):
     """(instructions/s, SM count) of an instruction stream: 0 LOP3, 1 IMAD,
-    2 DP4A, 3 IMAD+LOP3, 4 PRMT, 5 SHF, 6 DP4A+PRMT."""
+    2 DP4A, 3 IMAD+LOP3, 4 PRMT, 5 SHF, 6 DP4A+PRMT; 7 and 8 are warp MMA
+    streams (f16 m16n8k16, s8 m16n8k32) in multiply-adds per second."""
     v = ctypes.c_double()
     n = ctypes.c_int()
     _check(load().snt_measure_int_peak(device, kind, ctypes.byref(v), ctypes.byref(n)))

@@ -87,6 +87,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     const cudaStream_t caller = st;
     int mode = ctx->r3_overlap, lanes = ctx->r3_lanes, split = ctx->tree_split;
     const bool narrow = ctx->narrow_seg != 0;
+    const bool mma = ctx->rq_engine != 0;
+    const int mma_tiles = ctx->mma_tiles;
     const snt_ctx::Tuned &tu = ctx->tuned[pidx(P)][bbucket(B)];
     if (tu.lanes) { mode = tu.overlap; lanes = tu.lanes; split = tu.split; }
     if (inline_stream) {
@@ -134,7 +136,12 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                 if (s3 != SNT_OK) return s3;
                 forked = true;
             }
-            if (narrow && t.n[l] <= kSegMaxNodes)
+            if (mma)
+                SNT_CUDA(launch_tree_up_mma<P>(nodes + (size_t)t.off[l - 1] * pi.pad,
+                                               single_tree(t.n[l - 1]), t.n[l],
+                                               nodes + (size_t)t.off[l] * pi.pad, st, mma_tiles,
+                                               l == 1));
+            else if (narrow && t.n[l] <= kSegMaxNodes)
                 SNT_CUDA(launch_tree_up_seg<P>(nodes + (size_t)t.off[l - 1] * pi.pad,
                                                single_tree(t.n[l - 1]), t.n[l],
                                                nodes + (size_t)t.off[l] * pi.pad, st));
@@ -164,7 +171,11 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                 joined = true;
             }
             int16_t *lch = nodes + (size_t)t.off[l - 1] * pi.pad;
-            if (narrow && t.n[l] <= kSegMaxNodes) {
+            if (mma) {  // in place on every level
+                SNT_CUDA(launch_tree_down_mma<P>(par, single_tree(t.n[l - 1]), t.n[l], lch, st,
+                                                 mma_tiles, l == 1));
+                par = lch;
+            } else if (narrow && t.n[l] <= kSegMaxNodes) {
                 int16_t *out = pp[ping];
                 ping ^= 1;
                 SNT_CUDA(launch_tree_down_seg<P>(par, single_tree(t.n[l - 1]), t.n[l], lch, out, st));
@@ -415,10 +426,14 @@ snt_status snt_rq_mul(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev, const
     if (!a_dev || !b_dev || !c_dev) return set_error(SNT_EINVAL, "null buffer");
     DeviceGuard dg(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const bool mma = ctx->rq_engine != 0;
     switch (P) {
-        case 653: SNT_CUDA(launch_mul_batch<653>((int)n, a_dev, b_dev, c_dev, st)); break;
-        case 761: SNT_CUDA(launch_mul_batch<761>((int)n, a_dev, b_dev, c_dev, st)); break;
-        case 857: SNT_CUDA(launch_mul_batch<857>((int)n, a_dev, b_dev, c_dev, st)); break;
+        case 653: SNT_CUDA(mma ? launch_mul_batch_mma<653>((int)n, a_dev, b_dev, c_dev, st)
+                               : launch_mul_batch<653>((int)n, a_dev, b_dev, c_dev, st)); break;
+        case 761: SNT_CUDA(mma ? launch_mul_batch_mma<761>((int)n, a_dev, b_dev, c_dev, st)
+                               : launch_mul_batch<761>((int)n, a_dev, b_dev, c_dev, st)); break;
+        case 857: SNT_CUDA(mma ? launch_mul_batch_mma<857>((int)n, a_dev, b_dev, c_dev, st)
+                               : launch_mul_batch<857>((int)n, a_dev, b_dev, c_dev, st)); break;
         default: return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     }
     return SNT_OK;
@@ -513,6 +528,14 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             if (value != 0 && value != 1) return set_error(SNT_EINVAL, "narrow split is 0 or 1");
             ctx->narrow_seg = value;
             return SNT_OK;
+        case SNT_OPT_RQ_ENGINE:
+            if (value != 0 && value != 1) return set_error(SNT_EINVAL, "R/q engine is 0 or 1");
+            ctx->rq_engine = value;
+            return SNT_OK;
+        case SNT_OPT_MMA_TILES:
+            if (value < 1 || value > 3) return set_error(SNT_EINVAL, "MMA tiles per warp is 1, 2 or 3");
+            ctx->mma_tiles = value;
+            return SNT_OK;
         default:
             return set_error(SNT_EINVAL, "unknown option %d", option);
     }
@@ -525,6 +548,8 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
         case SNT_OPT_TREE_SPLIT: *value = ctx->tree_split; return SNT_OK;
         case SNT_OPT_R3_OVERLAP: *value = ctx->r3_overlap; return SNT_OK;
         case SNT_OPT_NARROW_SEG: *value = ctx->narrow_seg; return SNT_OK;
+        case SNT_OPT_RQ_ENGINE: *value = ctx->rq_engine; return SNT_OK;
+        case SNT_OPT_MMA_TILES: *value = ctx->mma_tiles; return SNT_OK;
         default: return set_error(SNT_EINVAL, "unknown option %d", option);
     }
 }

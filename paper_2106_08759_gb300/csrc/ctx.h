@@ -46,6 +46,8 @@ struct snt_ctx {
     int tree_split = snt::kDefaultTreeSplit;
     int r3_overlap = snt::kDefaultR3Overlap;
     int narrow_seg = snt::kDefaultNarrowSeg;
+    int rq_engine = snt::kDefaultRqEngine;
+    int mma_tiles = snt::kDefaultMmaTiles;
     // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
     struct Tuned { int lanes = 0, split = 0, overlap = 0; };
     Tuned tuned[3][25];

@@ -18,6 +18,8 @@ constexpr int kDefaultR3Lanes = 4;     // lanes per element of the R/3 divstep k
 constexpr int kDefaultTreeSplit = 8;   // largest split of one product over thread groups
 constexpr int kDefaultR3Overlap = 1;   // R/3 on its own low-priority stream
 constexpr int kDefaultNarrowSeg = 1;   // output-split narrow tree levels
+constexpr int kDefaultRqEngine = 1;    // R/q products on the tensor cores
+constexpr int kDefaultMmaTiles = 1;    // MMA tiles per warp
 
 // Records a one-line error message (snt_last_error_string) and returns s.
 snt_status set_error(snt_status s, const char *fmt, ...);

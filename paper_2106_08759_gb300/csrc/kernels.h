@@ -116,6 +116,20 @@ cudaError_t launch_tree_down_seg(const int16_t *lpar, const LevelMap &lm, int n_
 template <int P>
 cudaError_t launch_mul_batch(int n, const int16_t *a, const int16_t *b, int16_t *c,
                              cudaStream_t st);
+// Tensor-core engine (rqmma.cu): same products and bytes; one CTA per
+// product (per parent in the down-sweep), `tiles` MMA tiles per warp.  The
+// down-sweep overwrites the children in place.
+// `leaves`: the level's inputs (up) or children (down) are the leaves 3f,
+// whose small coefficients need fewer limb products.
+template <int P>
+cudaError_t launch_tree_up_mma(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
+                               cudaStream_t st, int tiles, bool leaves);
+template <int P>
+cudaError_t launch_tree_down_mma(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t *lch,
+                                 cudaStream_t st, int tiles, bool leaves);
+template <int P>
+cudaError_t launch_mul_batch_mma(int n, const int16_t *a, const int16_t *b, int16_t *c,
+                                 cudaStream_t st);
 template <int P>
 cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out,
                           long out_stride, int32_t *ok, int *err, int err_bit, cudaStream_t st);

@@ -88,10 +88,44 @@ __global__ void __launch_bounds__(256) k_int_peak(int iters, unsigned seed, unsi
     if (x == 0x12345678u) sink[0] = x;  // keeps the chains live
 }
 
+// Legacy warp-level tensor MMA streams (four independent accumulator sets
+// per warp): KIND 7 = m16n8k16 f16 x f16 -> f32, KIND 8 = m16n8k32 s8 x s8
+// -> s32.  Counted in multiply-adds (2048 resp. 4096 per instruction).
+template <int KIND>
+__global__ void __launch_bounds__(256) k_mma_peak(int iters, unsigned seed, unsigned *sink) {
+    const unsigned a0 = seed ^ threadIdx.x, a1 = a0 * 3u, a2 = a0 * 5u, a3 = a0 * 7u;
+    const unsigned b0 = a0 * 11u, b1 = a0 * 13u;
+    unsigned d[4][4] = {};
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (KIND == 7)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+                        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                        : "+r"(d[s][0]), "+r"(d[s][1]), "+r"(d[s][2]), "+r"(d[s][3])
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+                else
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 "
+                        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                        : "+r"(d[s][0]), "+r"(d[s][1]), "+r"(d[s][2]), "+r"(d[s][3])
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+            }
+        }
+    }
+    unsigned x = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) x ^= d[s][0] ^ d[s][1] ^ d[s][2] ^ d[s][3];
+    if (x == 0x12345678u) sink[0] = x;
+}
+
 }  // namespace
 
 extern "C" snt_status snt_measure_int_peak(int device, int kind, double *ops_per_s, int *sms) {
-    if (!ops_per_s || kind < 0 || kind > 6) return SNT_EINVAL;
+    if (!ops_per_s || kind < 0 || kind > 8) return SNT_EINVAL;
     int prev = 0;
     if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return SNT_ECUDA;
     cudaDeviceProp prop;
@@ -112,7 +146,9 @@ extern "C" snt_status snt_measure_int_peak(int device, int kind, double *ops_per
             case 3: k_int_peak<3><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
             case 4: k_int_peak<4><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
             case 5: k_int_peak<5><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
-            default: k_int_peak<6><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
+            case 6: k_int_peak<6><<<blocks, threads>>>(iters, 0x9e3779b9u + rep, sink); break;
+            case 7: k_mma_peak<7><<<blocks, threads>>>(iters / 8, 0x9e3779b9u + rep, sink); break;
+            default: k_mma_peak<8><<<blocks, threads>>>(iters / 8, 0x9e3779b9u + rep, sink); break;
         }
         cudaEventRecord(t1);
         e = cudaEventSynchronize(t1);
@@ -121,7 +157,9 @@ extern "C" snt_status snt_measure_int_peak(int device, int kind, double *ops_per
         if (rep > 0 && ms < best) best = ms;  // first launch is warm-up
     }
     if (e == cudaSuccess) {
-        const double ops = (double)blocks * threads * iters * 16.0 * 8.0;
+        double ops = (double)blocks * threads * iters * 16.0 * 8.0;
+        if (kind >= 7)  // multiply-adds: per warp, (iters / 8) * 16 instructions
+            ops = (double)blocks * (threads / 32) * (iters / 8) * 16.0 * (kind == 7 ? 2048.0 : 4096.0);
         *ops_per_s = ops / (best * 1e-3);
         if (sms) *sms = prop.multiProcessorCount;
     }

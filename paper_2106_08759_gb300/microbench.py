@@ -88,6 +88,13 @@ def main():
                          "gmac_per_s": n * p * p / ms / 1e6}
     ms = timeit(lambda: snt.snt_rq_mul(ctx, P, n, A, S, C))
     out["rq_mul_short"] = {"n": n, "ms": ms, "products_per_s": n / ms * 1e3}
+    eng = ctx.get_option(snt.SNT_OPT_RQ_ENGINE)
+    for e in (0, 1):
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, e)
+        ms = timeit(lambda: snt.snt_rq_mul(ctx, P, n, A, Bm, C))
+        out["rq_mul_gen_engine%d" % e] = {"n": n, "ms": ms, "products_per_s": n / ms * 1e3,
+                                          "gmac_per_s": n * p * p / ms / 1e6}
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, eng)
     del A, Bm, S, C
 
     m = (1 << 12) if args.quick else (1 << 16)
@@ -139,6 +146,26 @@ def main():
     out["keygen_4096_ms"] = tot / args.reps
     if args.sweep:
         sweep = {}
+        def run_keygen_avg():
+            snt.snt_batch_keygen(ctx, P, 1, 0, Bk, pk, sk)
+            ctx.phase_times()
+            tot = 0.0
+            for i in range(args.reps):
+                flush.zero_()
+                snt.snt_batch_keygen(ctx, P, 1, (i + 1) * Bk, Bk, pk, sk)
+                ph = ctx.phase_times()
+                tot += ph["total"]
+            return {"ms": round(tot / args.reps, 4), "phases": {k: round(v, 4) for k, v in ph.items()}}
+        ctx.set_option(snt.SNT_OPT_R3_LANES, 4)
+        ctx.set_option(snt.SNT_OPT_TREE_SPLIT, 8)
+        for overlap in (0, 1, 2):
+            ctx.set_option(snt.SNT_OPT_R3_OVERLAP, overlap)
+            for tiles in (1, 2, 3):
+                ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
+                ctx.set_option(snt.SNT_OPT_MMA_TILES, tiles)
+                sweep["mma_tiles%d_overlap%d" % (tiles, overlap)] = run_keygen_avg()
+        ctx.set_option(snt.SNT_OPT_MMA_TILES, 1)
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 0)
         for narrow in (0, 1):
             for overlap in (0, 1, 2):
                 for lanes in (4, 8):
@@ -158,6 +185,7 @@ def main():
                         key = "narrow%d_overlap%d_lanes%d_split%d" % (narrow, overlap, lanes, split)
                         sweep[key] = {"ms": round(tot / args.reps, 4),
                                       "phases": {k: round(v, 4) for k, v in ph.items()}}
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
         out["keygen_4096_sweep"] = sweep
     ctx.close()
 

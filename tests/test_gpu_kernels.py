@@ -42,15 +42,22 @@ def _rq_cases(p, q, rng, n):
     return a, b
 
 
+@pytest.mark.parametrize("engine", [0, 1])
 @pytest.mark.parametrize("P", [653, 761, 857])
-def test_rq_mul_matches_oracle(snt, ctx, P):
+def test_rq_mul_matches_oracle(snt, ctx, P, engine):
+    # engine 0: CUDA-core Toeplitz products; 1: the same products as warp MMAs
+    # on exact f16 limbs (extreme operands exercise the limb and sum bounds)
     import torch
     p, q, _ = oracle.PARAMS[P]
     rng = np.random.default_rng(P)
-    n = 40
+    n = 41  # ragged last CTA of the 4-products-per-CTA tensor-core kernel
     a, b = _rq_cases(p, q, rng, n)
     c = torch.empty(n * p, dtype=torch.int16, device="cuda")
-    snt.snt_rq_mul(ctx, P, n, _t(a.ravel(), torch.int16), _t(b.ravel(), torch.int16), c)
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, engine)
+    try:
+        snt.snt_rq_mul(ctx, P, n, _t(a.ravel(), torch.int16), _t(b.ravel(), torch.int16), c)
+    finally:
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
     got = c.cpu().numpy().reshape(n, p)
     for i in range(n):
         assert np.array_equal(got[i], oracle.ring_mul(p, q, a[i], b[i])), i

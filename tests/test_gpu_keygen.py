@@ -78,22 +78,47 @@ def test_tuning_options_do_not_change_keys(snt, ctx, opts):
 
 @pytest.mark.parametrize("B", [2, 3, 9, 17, 33, 65, 130, 257])
 def test_output_split_narrow_levels_give_the_same_keys(snt, ctx, B):
-    # narrow tree levels split by output segments over several CTAs (up and
-    # down, with the ping-pong inverse buffers) against one CTA per product;
-    # B spans every segment plan and unpaired nodes at several levels
+    # CUDA-core engine: narrow tree levels split by output segments over
+    # several CTAs (up and down, with the ping-pong inverse buffers) against
+    # one CTA per product; B spans every segment plan and unpaired nodes
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 0)
     ctx.set_option(snt.SNT_OPT_NARROW_SEG, 0)
     try:
         ref = gpu_keygen(snt, ctx, 761, 77, 1000, B)
+        ctx.set_option(snt.SNT_OPT_NARROW_SEG, 1)
+        got = gpu_keygen(snt, ctx, 761, 77, 1000, B)
     finally:
         ctx.set_option(snt.SNT_OPT_NARROW_SEG, 1)
-    got = gpu_keygen(snt, ctx, 761, 77, 1000, B)
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+@pytest.mark.parametrize("tiles", [1, 2, 3])
+@pytest.mark.parametrize("P,B", [(761, 300), (653, 77), (857, 130)])
+def test_tensor_core_engine_gives_the_same_keys(snt, ctx, P, B, tiles):
+    # tree products as warp MMAs on exact f16 limbs, 1, 2 or 3 tiles of 128
+    # outputs per warp (ragged last warp for 653 and 857)
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 0)
+    try:
+        ref = gpu_keygen(snt, ctx, P, 5, 40, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
+    ctx.set_option(snt.SNT_OPT_MMA_TILES, tiles)
+    try:
+        got = gpu_keygen(snt, ctx, P, 5, 40, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_MMA_TILES, 1)
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
 
 
 @pytest.mark.parametrize("P,B", [(653, 9), (857, 33)])
 def test_output_split_narrow_levels_vs_oracle(snt, ctx, P, B):
     assert ctx.get_option(snt.SNT_OPT_NARROW_SEG) == 1
-    pk, sk = gpu_keygen(snt, ctx, P, 78, 3, B)
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 0)
+    try:
+        pk, sk = gpu_keygen(snt, ctx, P, 78, 3, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
     rpk, rsk = oracle.keygen_batch(P, 78, 3, B)
     assert first_mismatch(pk, rpk) is None and first_mismatch(sk, rsk) is None
 
