@@ -6,8 +6,10 @@ One step = one snt_batch_keygen call: B fresh key pairs from a 64-bit seed
 inversion, h, Rq_encode, sk assembly and SHA-512), all on the device.  The
 line also reports the per-key GPU path (snt_keygen_perkey) on the same
 workload, the end-to-end rate through the host-buffer call, the ALU roofline
-of the dominant kernel against measured integer-pipe peaks, and the CPU
-oracle timed on the host cores.
+of the dominant kernel against measured integer-pipe peaks, the CPU oracle
+timed on the host cores, and the serving loop (p50/p99 latency and
+throughput of encapsulation/decapsulation handshakes over the device key
+pool at 10^4, 10^5 and 10^6 requests/s).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -32,9 +34,21 @@ WORDS = (P + 1 + 31) // 32
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 LAUNCHES_FIXED = 5           # sample_f, r3, root, finalize, sha512 (+ 2 per tree level)
 
-# DRAM traffic per launch of the dominant kernel from the committed ncu
-# capture (profiles/); None until a capture of the current kernel exists.
-NCU_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per call of a phase's kernel at B = 4096, from
+# the committed ncu captures (profiles/), keyed by kernel instantiation; a
+# kernel is absent until a capture of its current code exists.
+NCU_TRAFFIC_BYTES = {"k_r3_keygen<761, 4>": 32512}
+
+
+def kernel_of(phase, tuned):
+    """Kernel instantiation that runs a phase under the tuned layouts."""
+    if phase == "r3_inv":
+        return "k_r3_keygen<761, %d>" % tuned.get("r3_lanes", 4)
+    mma = tuned.get("rq_engine") == 1
+    return {"tree_up": "k_tree_up_mma" if mma else "k_tree_up",
+            "tree_down": "k_tree_down_mma" if mma else "k_tree_down",
+            "h_encode": "k_finalize_mma<761>" if mma else "k_finalize<761>",
+            "root_inv": "k_rq_inv_jump<761>"}[phase]
 
 
 def parse():
@@ -47,6 +61,9 @@ def parse():
     ap.add_argument("--seed", type=lambda s: int(s, 0), default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--perkey-steps", type=int, default=None)
+    ap.add_argument("--serve-rates", default="1e4,1e5,1e6",
+                    help="request rates of the serving runs (empty: none)")
+    ap.add_argument("--serve-duration", type=float, default=0.5)
     return ap.parse_args()
 
 
@@ -125,6 +142,15 @@ class ClockSampler:
 
 
 # --------------------------------------------------------- algorithmic ops
+def _measured_peaks():
+    """The measured peaks of this GPU pool, if the file is present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def ops_per_call(B, p=P):
     """Algorithmic integer operations of each phase for one call of B keys.
 
@@ -146,6 +172,8 @@ def ops_per_call(B, p=P):
 
 PIPE_OF = {"r3_inv": "lop3", "tree_up": "imad", "tree_down": "imad", "h_encode": "imad",
            "root_inv": "imad"}
+# with the tensor-core engine the products are f16 MMAs
+TENSOR_PHASES = ("tree_up", "tree_down", "h_encode")
 
 
 # ------------------------------------------------------------------ our arm
@@ -180,6 +208,8 @@ def run_ours(args):
 
     lop3_peak, sms = snt.snt_measure_int_peak(local, 0)
     imad_peak, _ = snt.snt_measure_int_peak(local, 1)
+    mma_peak, _ = snt.snt_measure_int_peak(local, 7)  # warp-MMA f16 multiply-adds per second
+    peaks = _measured_peaks()
     tuned = ctx.autotune(P, B)  # kernel layouts for this GPU, before any timed step
 
     L = 0
@@ -254,24 +284,60 @@ def run_ours(args):
         e2e_s = float(t.item())
     e2e_rate = world * B * e2e_steps / e2e_s
 
-    # roofline of the dominant kernel (largest phase time), ALU bound
+    # roofline of the dominant kernel (largest phase time): an integer-pipe
+    # bound for the R/3 divsteps and the CUDA-core products, the tensor bound
+    # for the products on the tensor cores
     ops = ops_per_call(B)
     kernels = {k: phase.get(k, 0.0) for k in ops}
     dom = max(kernels, key=kernels.get)
     dom_ms = kernels[dom]
-    achieved = ops[dom] / (dom_ms * 1e-3) / 1e12
-    peak = (lop3_peak if PIPE_OF[dom] == "lop3" else imad_peak) / 1e12
     launches_of = {"r3_inv": 1, "tree_up": L, "tree_down": L, "h_encode": 1, "root_inv": 1}
-    roofline = {
-        "bound": "alu", "kernel": dom, "pipe": PIPE_OF[dom],
-        "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-        "frac": round(achieved / peak, 4),
-        "peak_source": "measured on this GPU by snt_measure_int_peak (%s stream, %d SMs)"
-                       % (PIPE_OF[dom].upper(), sms),
-        "ops_per_call": ops[dom], "launches_per_call": launches_of[dom],
-        "ms_per_call": round(dom_ms, 4),
-        "traffic": NCU_TRAFFIC_BYTES,
-    }
+    if tuned.get("rq_engine") == 1 and dom in TENSOR_PHASES:
+        achieved = 2.0 * ops[dom] / (dom_ms * 1e-3) / 1e12  # TFLOP/s of the p^2 products
+        peak = peaks.get("bf16_tflops") or 1900.0
+        roofline = {
+            "bound": "tensor", "kernel": kernel_of(dom, tuned), "phase": dom, "pipe": "tensor (mma.sync f16, f32 accumulate)",
+            "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4),
+            "peak_source": ("of measured: dense bf16 GEMM burst in MEASURED_PEAKS.json (f16 has "
+                            "the same nominal rate)" if peaks.get("bf16_tflops") else
+                            "of fallback: 1.9 PFLOP/s bf16 burst"),
+            "warp_mma_f16_peak_tflops": round(2.0 * mma_peak / 1e12, 1),
+            "flops_per_call": 2 * ops[dom], "launches_per_call": launches_of[dom],
+            "ms_per_call": round(dom_ms, 4),
+            "traffic": NCU_TRAFFIC_BYTES.get(kernel_of(dom, tuned)),
+        }
+    else:
+        achieved = ops[dom] / (dom_ms * 1e-3) / 1e12
+        peak = (lop3_peak if PIPE_OF[dom] == "lop3" else imad_peak) / 1e12
+        roofline = {
+            "bound": "alu", "kernel": kernel_of(dom, tuned), "phase": dom, "pipe": PIPE_OF[dom],
+            "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
+            "frac": round(achieved / peak, 4),
+            "peak_source": "measured on this GPU by snt_measure_int_peak (%s stream, %d SMs)"
+                           % (PIPE_OF[dom].upper(), sms),
+            "ops_per_call": ops[dom], "launches_per_call": launches_of[dom],
+            "ms_per_call": round(dom_ms, 4),
+            "traffic": NCU_TRAFFIC_BYTES.get(kernel_of(dom, tuned)),
+        }
+
+    # serving loop: Poisson handshakes (encapsulation, then decapsulation of
+    # the same items), log-uniform sizes in [1, 64], key pool refilled in
+    # batches of 8192, 16 GiB device budget; latency from arrival to completion
+    serve = []
+    for r in [float(x) for x in args.serve_rates.split(",") if x.strip()]:
+        st, _, _ = snt.snt_serve_run(ctx, P=P, rate=r, duration_s=args.serve_duration,
+                                     max_items=64, dec_fraction=1.0, pool_keys=16384,
+                                     refill_batch=8192, mem_budget=16 << 30, max_inflight=4,
+                                     max_launch_items=4096, seed=args.seed + 17)
+        serve.append({"rate": r, "requests": st["requests"],
+                      "p50_ms": round(st["p50_ms"], 4), "p99_ms": round(st["p99_ms"], 4),
+                      "max_ms": round(st["max_ms"], 3),
+                      "served_requests_per_s": round(st["requests_per_s"], 1),
+                      "items_per_s": round(st["items_per_s"], 1),
+                      "items_enc": st["items_enc"], "items_dec": st["items_dec"],
+                      "keys_generated": st["keys_generated"], "mismatches": st["mismatches"],
+                      "max_queue": st["max_queue"], "wall_s": round(st["wall_s"], 3)})
 
     cpu = None
     if do_cpu:
@@ -296,6 +362,7 @@ def run_ours(args):
         "phases_ms": {k: round(v, 4) for k, v in phase.items()},
         "tuned": tuned,
         "int_peaks_tops": {"lop3": round(lop3_peak / 1e12, 3), "imad": round(imad_peak / 1e12, 3),
+                           "warp_mma_f16_macs": round(mma_peak / 1e12, 3),
                            "sms": sms},
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -303,6 +370,12 @@ def run_ours(args):
                 "d2h_bytes_per_step": B * (pkb + skb)},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
+        "serve": {"workload": "sntrup761 handshakes for %.2f s per rate: Poisson encapsulation "
+                              "requests of log-uniform size in [1, 64], each followed by the "
+                              "decapsulation of its items; 16384-key device pool refilled by "
+                              "8192-key batch keygen; 16 GiB budget; 4 launch streams"
+                              % args.serve_duration,
+                  "runs": serve},
         "paper_context": "156317 Haswell cycles/key at n=32 (E3-1275 v3, 3.5 GHz: ~22.4k keys/s/core)",
     }
     ctx.close()

@@ -284,12 +284,16 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);
 snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
 
 /* Autotuner: times batch keygen of B keys of parameter set P under each
- * combination of R/3 lanes (4, 8, 32), tree split (4, 8) and R/3 overlap
- * (0, 1, 2) on this GPU (CUDA events, best of three after a warm-up) and
+ * combination of R/3 lanes (4, 8, 32), R/3 overlap (0, 1, 2) and R/q engine
+ * (tensor cores with 1 or 2 MMA tiles per warp, or CUDA cores with tree
+ * split 4 or 8) on this GPU (CUDA events, best of three after a warm-up) and
  * keeps the fastest for every later keygen call of this context with the same
  * P and ceil(log2 B); it overrides the snt_ctx_set_option values there.
- * Synchronous; uses the context's scratch (B must fit the budget).  The chosen
- * values are written to the optional out pointers. */
+ * Synchronous; uses the context's scratch (B must fit the budget).
+ * choice (optional, 5 ints): lanes, split, overlap, engine, tiles. */
+snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice);
+
+/* snt_autotune_ex returning lanes, split and overlap only. */
 snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *split_out,
                         int *overlap_out);
 

@@ -100,6 +100,7 @@ def load():
         "snt_ctx_set_option": [P, i32, i32],
         "snt_autotune": [P, i32, sz, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                          ctypes.POINTER(ctypes.c_int)],
+        "snt_autotune_ex": [P, i32, sz, ctypes.POINTER(ctypes.c_int)],
         "snt_ctx_get_option": [P, i32, ctypes.POINTER(ctypes.c_int)],
         "snt_ctx_phase_times": [P, P, i32],
         "snt_measure_int_peak": [i32, i32, ctypes.POINTER(ctypes.c_double),
@@ -190,10 +191,10 @@ class Context:
 
     def autotune(self, P, B):
         """Pick the fastest kernel layouts for (P, B) on this GPU; returns them."""
-        la, sp, ov = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(load().snt_autotune(self.handle, P, B, ctypes.byref(la), ctypes.byref(sp),
-                                   ctypes.byref(ov)))
-        return {"r3_lanes": la.value, "tree_split": sp.value, "r3_overlap": ov.value}
+        c = (ctypes.c_int * 5)()
+        _check(load().snt_autotune_ex(self.handle, P, B, c))
+        return {"r3_lanes": c[0], "tree_split": c[1], "r3_overlap": c[2], "rq_engine": c[3],
+                "mma_tiles": c[4]}
 
     def set_timing(self, on=True):
         _check(load().snt_ctx_set_timing(self.handle, 1 if on else 0))

@@ -87,10 +87,13 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     const cudaStream_t caller = st;
     int mode = ctx->r3_overlap, lanes = ctx->r3_lanes, split = ctx->tree_split;
     const bool narrow = ctx->narrow_seg != 0;
-    const bool mma = ctx->rq_engine != 0;
-    const int mma_tiles = ctx->mma_tiles;
+    bool mma = ctx->rq_engine != 0;
+    int mma_tiles = ctx->mma_tiles;
     const snt_ctx::Tuned &tu = ctx->tuned[pidx(P)][bbucket(B)];
-    if (tu.lanes) { mode = tu.overlap; lanes = tu.lanes; split = tu.split; }
+    if (tu.lanes) {
+        mode = tu.overlap; lanes = tu.lanes; split = tu.split;
+        mma = tu.engine != 0; mma_tiles = tu.tiles;
+    }
     if (inline_stream) {
         mode = 0;  // everything in order on the caller's stream
     } else {
@@ -199,7 +202,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     if (!joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     if (tm) SNT_CUDA(cudaEventRecord(ev[7], st));
     SNT_CUDA(launch_finalize<P>(km, Bi, gbuf, inv_leaves, pi.pk_bytes, pi.sk_bytes, 2 * sb,
-                                pi.sched, st));
+                                pi.sched, st, mma));
     if (tm) SNT_CUDA(cudaEventRecord(ev[8], st));
     SNT_CUDA(launch_sha512_pk(km, Bi, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[9], st));
@@ -554,8 +557,7 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
     }
 }
 
-snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *split_out,
-                        int *overlap_out) {
+snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
     if (!ctx) return set_error(SNT_EINVAL, "null context");
     ParamInfo pi;
     if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
@@ -571,30 +573,41 @@ snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *spli
     SNT_CUDA(cudaEventCreate(&e0));
     SNT_CUDA(cudaEventCreate(&e1));
     const snt_ctx::Tuned saved = ctx->tuned[pidx(P)][bbucket(B)];
+    // candidates: R/3 lanes x overlap x (tensor-core engine with 1 or 2 tiles
+    // per warp, or CUDA-core engine with tree split 4 or 8)
+    std::vector<snt_ctx::Tuned> cands;
+    for (int la : {4, 8, 32})
+        for (int ov : {0, 1, 2}) {
+            for (int ti : {1, 2}) {
+                snt_ctx::Tuned c;
+                c.lanes = la; c.overlap = ov; c.engine = 1; c.tiles = ti; c.split = ctx->tree_split;
+                cands.push_back(c);
+            }
+            for (int sp : {4, 8}) {
+                snt_ctx::Tuned c;
+                c.lanes = la; c.overlap = ov; c.engine = 0; c.tiles = 1; c.split = sp;
+                cands.push_back(c);
+            }
+        }
     snt_ctx::Tuned best;
     float best_ms = 1e30f;
-    const int lanes_c[] = {4, 8, 32}, split_c[] = {4, 8}, overlap_c[] = {0, 1, 2};
     snt_status st = SNT_OK;
-    for (int la : lanes_c)
-        for (int sp : split_c)
-            for (int ov : overlap_c) {
-                snt_ctx::Tuned cand;
-                cand.lanes = la; cand.split = sp; cand.overlap = ov;
-                ctx->tuned[pidx(P)][bbucket(B)] = cand;
-                float best_c = 1e30f;
-                for (int rep = 0; rep < 4 && st == SNT_OK; ++rep) {
-                    if (cudaEventRecord(e0, ctx->tune) != cudaSuccess) { st = SNT_ECUDA; break; }
-                    st = keygen_common(ctx, P, 0x5eed, (uint64_t)rep * B, B, dpk, dsk, ts, true, false);
-                    if (st != SNT_OK) break;
-                    if (cudaEventRecord(e1, ctx->tune) != cudaSuccess ||
-                        cudaEventSynchronize(e1) != cudaSuccess) { st = SNT_ECUDA; break; }
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep > 0 && ms < best_c) best_c = ms;  // first run warms up
-                }
-                if (st != SNT_OK) break;
-                if (best_c < best_ms) { best_ms = best_c; best = cand; }
-            }
+    for (const snt_ctx::Tuned &cand : cands) {
+        ctx->tuned[pidx(P)][bbucket(B)] = cand;
+        float best_c = 1e30f;
+        for (int rep = 0; rep < 4 && st == SNT_OK; ++rep) {
+            if (cudaEventRecord(e0, ctx->tune) != cudaSuccess) { st = SNT_ECUDA; break; }
+            st = keygen_common(ctx, P, 0x5eed, (uint64_t)rep * B, B, dpk, dsk, ts, true, false);
+            if (st != SNT_OK) break;
+            if (cudaEventRecord(e1, ctx->tune) != cudaSuccess ||
+                cudaEventSynchronize(e1) != cudaSuccess) { st = SNT_ECUDA; break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best_c) best_c = ms;  // first run warms up
+        }
+        if (st != SNT_OK) break;
+        if (best_c < best_ms) { best_ms = best_c; best = cand; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != SNT_OK) {
@@ -602,10 +615,25 @@ snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *spli
         return st;
     }
     ctx->tuned[pidx(P)][bbucket(B)] = best;
-    if (lanes_out) *lanes_out = best.lanes;
-    if (split_out) *split_out = best.split;
-    if (overlap_out) *overlap_out = best.overlap;
+    if (choice) {
+        choice[0] = best.lanes;
+        choice[1] = best.split;
+        choice[2] = best.overlap;
+        choice[3] = best.engine;
+        choice[4] = best.tiles;
+    }
     return snt_ctx_sync(ctx, ts);
+}
+
+snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *split_out,
+                        int *overlap_out) {
+    int c[5] = {0, 0, 0, 0, 0};
+    const snt_status st = snt_autotune_ex(ctx, P, B, c);
+    if (st != SNT_OK) return st;
+    if (lanes_out) *lanes_out = c[0];
+    if (split_out) *split_out = c[1];
+    if (overlap_out) *overlap_out = c[2];
+    return SNT_OK;
 }
 
 snt_status snt_ctx_set_timing(snt_ctx *ctx, int on) {

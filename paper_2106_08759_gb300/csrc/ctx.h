@@ -49,7 +49,7 @@ struct snt_ctx {
     int rq_engine = snt::kDefaultRqEngine;
     int mma_tiles = snt::kDefaultMmaTiles;
     // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
-    struct Tuned { int lanes = 0, split = 0, overlap = 0; };
+    struct Tuned { int lanes = 0, split = 0, overlap = 0, engine = 0, tiles = 1; };
     Tuned tuned[3][25];
     cudaStream_t tune = nullptr;  // stream used while autotuning
     snt::RaggedGraph ragged;      // last ragged plan and its graph

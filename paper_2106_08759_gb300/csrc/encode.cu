@@ -15,6 +15,7 @@
 #include "toeplitz.cuh"
 #include "sha512.cuh"
 #include "mixed.cuh"
+#include "mma_mul.cuh"
 
 namespace snt {
 
@@ -49,6 +50,53 @@ k_finalize(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__restrict
     uint8_t *pkk = d.pk + (size_t)(key - d.key_base) * pk_bytes;
     uint8_t *skk = d.sk + (size_t)(key - d.key_base) * sk_bytes + sk_pk_off;
     for (int b = threadIdx.x; b < pk_bytes; b += blockDim.x) {
+        pkk[b] = ob[b];
+        skk[b] = ob[b];
+    }
+}
+
+// The same with h on the tensor cores (mma_mul.cuh): E from (3f)^-1, the
+// vector side g (small, MODE_SA), one warp per MMA tile; the encoding
+// buffers reuse the E table's shared memory once the products are done.
+template <int P>
+__global__ void __launch_bounds__(32 * MmaGeo<P, 1>::NW)
+k_finalize_mma(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__restrict__ ainv,
+               int pk_bytes, int sk_bytes, int sk_pk_off, EncSched S) {
+    using G = Geo<P>;
+    using M = MmaGeo<P, 1>;
+    static_assert(2 * G::pad * sizeof(uint32_t) + 1344 <= sizeof(MmaE<P, 1>), "encode buffers");
+    extern __shared__ __align__(16) uint8_t sm[];
+    MmaE<P, 1> &E = *reinterpret_cast<MmaE<P, 1> *>(sm);
+    MmaA<P, 1> &A = *reinterpret_cast<MmaA<P, 1> *>(sm + sizeof(MmaE<P, 1>));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nth = blockDim.x;
+    const int key = blockIdx.x;
+    const int8_t *g = gbuf + (size_t)key * G::pad;
+    const int16_t *inv = ainv + (size_t)key * G::pad;
+    mma_fill_a<P, 1, MODE_SA>(g, A, threadIdx.x, nth);
+    mma_fill_b<P, 1>(inv, E, threadIdx.x, nth);
+    __syncthreads();
+    mma_fill_pe<P, 1, MODE_GEN>(E, threadIdx.x, nth);
+    __syncthreads();
+    float acc[1][1][3][4];
+    const MmaA<P, 1> *const As[1] = {&A};
+    mma_tiles<P, 1, 1, MODE_SA>(E, As, warp, lane, acc);
+    const int bl = (int)E.b[M::p - 1];
+    __syncthreads();
+    mma_stage<P, 1, 1, MODE_SA>(A, warp, lane, 0, acc);
+    __syncthreads();
+    uint32_t(*Rb)[G::pad] = reinterpret_cast<uint32_t(*)[G::pad]>(sm);  // over E
+    uint8_t *ob = sm + 2 * G::pad * sizeof(uint32_t);
+    for (int j = threadIdx.x; j < P; j += nth) {
+        int v = (j == 0) ? A.u.stage[0] - A.u.stage[P - 1] + (int)A.a[0] * bl
+                         : A.u.stage[j] + (int)A.a[j] * bl;
+        Rb[0][j] = (uint32_t)(cmod<G::q>(v) + G::half);
+    }
+    __syncthreads();
+    mixed_encode<G::pad>(Rb, S, ob);
+    const BatchDesc d = key_batch(km, key);
+    uint8_t *pkk = d.pk + (size_t)(key - d.key_base) * pk_bytes;
+    uint8_t *skk = d.sk + (size_t)(key - d.key_base) * sk_bytes + sk_pk_off;
+    for (int b = threadIdx.x; b < pk_bytes; b += nth) {
         pkk[b] = ob[b];
         skk[b] = ob[b];
     }
@@ -159,8 +207,19 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
 template <int P>
 cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, const int16_t *ainv,
                             int pk_bytes, int sk_bytes, int sk_pk_off, const EncSched &S,
-                            cudaStream_t st) {
-    k_finalize<P><<<nkeys, Tp<P>::NT, 0, st>>>(km, gbuf, ainv, pk_bytes, sk_bytes, sk_pk_off, S);
+                            cudaStream_t st, bool mma) {
+    if (mma) {
+        const size_t sm = sizeof(MmaE<P, 1>) + sizeof(MmaA<P, 1>);
+        if (sm > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(
+                k_finalize_mma<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+        }
+        k_finalize_mma<P><<<nkeys, 32 * MmaGeo<P, 1>::NW, sm, st>>>(km, gbuf, ainv, pk_bytes,
+                                                                    sk_bytes, sk_pk_off, S);
+    } else {
+        k_finalize<P><<<nkeys, Tp<P>::NT, 0, st>>>(km, gbuf, ainv, pk_bytes, sk_bytes, sk_pk_off, S);
+    }
     return cudaGetLastError();
 }
 
@@ -173,7 +232,7 @@ cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_b
 
 #define SNT_FIN_INST(P)                                                                       \
     template cudaError_t launch_finalize<P>(const KeyMap &, int, const int8_t *, const int16_t *, \
-                                            int, int, int, const EncSched &, cudaStream_t);
+                                            int, int, int, const EncSched &, cudaStream_t, bool);
 SNT_FIN_INST(653)
 SNT_FIN_INST(761)
 SNT_FIN_INST(857)

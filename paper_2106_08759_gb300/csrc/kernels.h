@@ -138,10 +138,11 @@ template <int P>
 cudaError_t launch_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
                                cudaStream_t st, const int *idx = nullptr);
+// h = g * (3f)^-1, Rq_encode(h) into pk and sk; mma: h on the tensor cores.
 template <int P>
 cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, const int16_t *ainv,
                             int pk_bytes, int sk_bytes, int sk_pk_off, const EncSched &S,
-                            cudaStream_t st);
+                            cudaStream_t st, bool mma = false);
 cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
                              int hash_off, cudaStream_t st);
 template <int P>

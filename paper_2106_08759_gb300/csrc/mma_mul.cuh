@@ -120,10 +120,10 @@ template <int P> __device__ __forceinline__ int mma_E(const int16_t *b, int t) {
     return v;
 }
 
-// Vector side: a (global, centred int16, first p entries) into shared
-// memory, threads tid = 0 .. nth-1 of the group.
-template <int P, int NT, int MODE = MODE_GEN>
-__device__ __forceinline__ void mma_fill_a(const int16_t *__restrict__ a, MmaA<P, NT> &s, int tid,
+// Vector side: a (global, centred int16 or int8, first p entries) into
+// shared memory, threads tid = 0 .. nth-1 of the group.
+template <int P, int NT, int MODE = MODE_GEN, typename T = int16_t>
+__device__ __forceinline__ void mma_fill_a(const T *__restrict__ a, MmaA<P, NT> &s, int tid,
                                            int nth) {
     using M = MmaGeo<P, NT>;
     for (int r = tid; r < M::VBN; r += nth) {  // record (block I, tig)

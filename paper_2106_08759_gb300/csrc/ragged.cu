@@ -85,7 +85,7 @@ void plan_group(Group &g, const size_t *B) {
 template <int P>
 snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStream_t st,
                         cudaStream_t aux, cudaEvent_t ev_fork, cudaEvent_t ev_join, int lanes,
-                        int split) {
+                        int split, bool mma, int tiles) {
     const ParamInfo &pi = g.pi;
     const int nb = (int)g.batch.size();
     int16_t *nodes = reinterpret_cast<int16_t *>(ctx->arena + g.off_nodes);
@@ -110,8 +110,13 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
         lm.nb = nb;
         lm.n_in = 0;
         const int n_out = g.pre[l][nb];
-        SNT_CUDA_R(launch_tree_up<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lm, n_out,
-                                     nodes + (size_t)g.lev_off[l] * pi.pad, st, split));
+        if (mma)
+            SNT_CUDA_R(launch_tree_up_mma<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lm, n_out,
+                                             nodes + (size_t)g.lev_off[l] * pi.pad, st, tiles,
+                                             l == 1));
+        else
+            SNT_CUDA_R(launch_tree_up<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lm, n_out,
+                                         nodes + (size_t)g.lev_off[l] * pi.pad, st, split));
     }
     SNT_CUDA_R(launch_rq_inv_jump<P>(nb, nodes, pi.pad, nodes, pi.pad, nullptr, ctx->d_err,
                                      ERR_ROOT, st, roots));
@@ -122,12 +127,17 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
         lm.nb = nb;
         lm.n_in = 0;
         const int n_par = g.pre[l][nb];
-        SNT_CUDA_R(launch_tree_down<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lm, n_par,
-                                       nodes + (size_t)g.lev_off[l - 1] * pi.pad, st, split));
+        if (mma)
+            SNT_CUDA_R(launch_tree_down_mma<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lm, n_par,
+                                               nodes + (size_t)g.lev_off[l - 1] * pi.pad, st,
+                                               tiles, l == 1));
+        else
+            SNT_CUDA_R(launch_tree_down<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lm, n_par,
+                                           nodes + (size_t)g.lev_off[l - 1] * pi.pad, st, split));
     }
     SNT_CUDA_R(cudaStreamWaitEvent(st, ev_join, 0));
     SNT_CUDA_R(launch_finalize<P>(km, g.nkeys, gbuf, nodes, pi.pk_bytes, pi.sk_bytes, 2 * sb,
-                                  pi.sched, st));
+                                  pi.sched, st, mma));
     SNT_CUDA_R(launch_sha512_pk(km, g.nkeys, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     return SNT_OK;
 }
@@ -220,7 +230,12 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         sig.push_back((int)B[i]);
     }
     RaggedGraph &rg = ctx->ragged;
-    const int lanes = ctx->r3_lanes, split = ctx->tree_split;
+    const int lanes = ctx->r3_lanes, split = ctx->tree_split, tiles = ctx->mma_tiles;
+    const bool mma = ctx->rq_engine != 0;
+    // the cached graph holds the kernel layouts: they are part of its key
+    sig.push_back(lanes);
+    sig.push_back(split);
+    sig.push_back(mma ? tiles : 0);
     if (!(rg.exec && rg.sig == sig && rg.table_off == table_off)) {
         if (rg.exec) cudaGraphExecDestroy(rg.exec);
         rg.exec = nullptr;
@@ -233,9 +248,9 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
             const Group &g = groups[j];
             if (g.batch.empty()) continue;
             switch (g.P) {
-                case 653: s = launch_group<653>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split); break;
-                case 761: s = launch_group<761>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split); break;
-                default: s = launch_group<857>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split); break;
+                case 653: s = launch_group<653>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles); break;
+                case 761: s = launch_group<761>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles); break;
+                default: s = launch_group<857>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles); break;
             }
         }
         cudaGraph_t graph = nullptr;
