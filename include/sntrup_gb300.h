@@ -277,7 +277,10 @@ typedef enum {
     SNT_OPT_RQ_ENGINE = 5,
     /* tensor-core engine: MMA tiles (128 outputs each) per warp, 1, 2 or 3;
      * a product's tiles are spread over the warps of one CTA */
-    SNT_OPT_MMA_TILES = 6
+    SNT_OPT_MMA_TILES = 6,
+    /* elements each lane group of the R/3 kernel runs at once, 1 or 2 (two
+     * independent divstep chains per lane, sharing the shuffles) */
+    SNT_OPT_R3_KPT = 7
 } snt_option;
 
 snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);
@@ -289,8 +292,9 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
  * split 4 or 8) on this GPU (CUDA events, best of three after a warm-up) and
  * keeps the fastest for every later keygen call of this context with the same
  * P and ceil(log2 B); it overrides the snt_ctx_set_option values there.
- * Synchronous; uses the context's scratch (B must fit the budget).
- * choice (optional, 5 ints): lanes, split, overlap, engine, tiles. */
+ * Synchronous; uses the context's scratch (B must fit the budget).  The R/3
+ * kernel's elements per lane group (1, 2) are searched too.
+ * choice (optional, 6 ints): lanes, split, overlap, engine, tiles, kpt. */
 snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice);
 
 /* snt_autotune_ex returning lanes, split and overlap only. */
@@ -299,12 +303,14 @@ snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *spli
 
 /* ---- Tracing ---- */
 
-/* Phases reported by snt_ctx_phase_times, in this order: sampling of f and the
- * leaves 3f; sampling of g with its R/3 inversion (auxiliary stream); tree
- * up-sweep (per-key path: all per-key R/q inversions); root inversion;
- * down-sweep; h = g/(3f) with Rq_encode; SHA-512 of the public keys; whole
- * call (main stream, start to end). */
-#define SNT_NPHASES 8
+/* Phases reported by snt_ctx_phase_times, in this order: sampling of f, the
+ * leaves 3f and g's first draw; the R/3 inversions with any further draws of
+ * g (auxiliary stream); tree up-sweep (per-key path: all per-key R/q
+ * inversions); root inversion; down-sweep; h = g/(3f) with Rq_encode; SHA-512
+ * of the public keys; whole call (main stream, start to end); the wait for
+ * the R/3 inversions at the end of the call with the fix-up of resampled
+ * keys. */
+#define SNT_NPHASES 9
 
 /* Turn per-phase CUDA events on (on != 0) or off for later keygen calls. */
 snt_status snt_ctx_set_timing(snt_ctx *ctx, int on);

@@ -69,30 +69,35 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     int16_t *pp[2];
     pp[0] = reinterpret_cast<int16_t *>(arena + keygen_scratch(pi, B, false));
     pp[1] = pp[0] + narrow_scratch(pi) / 2 / sizeof(int16_t);
+    // resampling list of the deferred R/3 kernel
+    int *fix_count = reinterpret_cast<int *>(arena + fix_offset(pi, B));
+    int *fix_keys = fix_count + 1;
+    int8_t *gfix = reinterpret_cast<int8_t *>(arena + fix_offset(pi, B) + fix_list_bytes(B));
     const int Bi = (int)B;
     const int sb = pi.small_bytes;
     const KeyMap km = single_batch(seed, first, Bi, pk, sk);
     cudaEvent_t *ev = ctx->ev_phase;
     const bool tm = ctx->timing;
     // Fork from the caller's stream.  The tree branch runs on the context's
-    // high-priority stream.  The per-key R/3 inversions (independent of the
-    // tree until h) run
+    // high-priority stream.  g's first draw is sampled with f, so h needs no
+    // R/3 result: the per-key R/3 inversions only write 1/g into sk and list
+    // the (rare) keys whose g needed another draw; they run
     //   overlap 0: first, on the tree stream;
-    //   overlap 1: on the low-priority stream from the start, joined before h;
-    //   overlap 2: on the low-priority stream, forked when the up-sweep
-    //              reaches its narrow levels (fewer than kNarrow products) and
-    //              joined before the first wide down-sweep level, so they fill
-    //              the SMs that the narrow levels and the root inversion leave
-    //              idle without competing with the wide levels.
+    //   overlap 1: on the low-priority stream from the start;
+    //   overlap 2: on the low-priority stream from the up-sweep's first narrow
+    //              level (fewer than kNarrow products), so they fill the SMs
+    //              that the narrow levels and the root inversion leave idle;
+    // and are joined at the end of the call, before the fix-up of the listed
+    // keys (h, pk and the pk hash again with the final g).
     const cudaStream_t caller = st;
     int mode = ctx->r3_overlap, lanes = ctx->r3_lanes, split = ctx->tree_split;
     const bool narrow = ctx->narrow_seg != 0;
     bool mma = ctx->rq_engine != 0;
-    int mma_tiles = ctx->mma_tiles;
+    int mma_tiles = ctx->mma_tiles, kpt = ctx->r3_kpt;
     const snt_ctx::Tuned &tu = ctx->tuned[pidx(P)][bbucket(B)];
     if (tu.lanes) {
         mode = tu.overlap; lanes = tu.lanes; split = tu.split;
-        mma = tu.engine != 0; mma_tiles = tu.tiles;
+        mma = tu.engine != 0; mma_tiles = tu.tiles; kpt = tu.kpt;
     }
     if (inline_stream) {
         mode = 0;  // everything in order on the caller's stream
@@ -105,7 +110,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     auto launch_r3 = [&](cudaStream_t r3s) -> snt_status {
         if (tm) SNT_CUDA(cudaEventRecord(ev[2], r3s));
         SNT_CUDA(launch_r3_keygen<P>(km, Bi, gbuf, pi.sk_bytes, sb, ctx->d_inj_idx, ctx->d_inj_g,
-                                     n_inj, ctx->d_err, r3s, lanes));
+                                     n_inj, ctx->d_err, r3s, lanes, kpt, gfix, fix_count,
+                                     fix_keys));
         if (tm) SNT_CUDA(cudaEventRecord(ev[3], r3s));
         return SNT_OK;
     };
@@ -119,7 +125,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     };
     bool forked = false, joined = false;
     if (tm) SNT_CUDA(cudaEventRecord(ev[0], st));
-    SNT_CUDA(launch_sample_f<P>(km, Bi, leaves, pi.sk_bytes, 2 * sb + pi.pk_bytes, st));
+    SNT_CUDA(launch_sample_f<P>(km, Bi, leaves, pi.sk_bytes, 2 * sb + pi.pk_bytes, st, gbuf,
+                                ctx->d_inj_idx, ctx->d_inj_g, n_inj, fix_count));
     if (tm) SNT_CUDA(cudaEventRecord(ev[1], st));
     if (mode == 0) {
         const snt_status s3 = launch_r3(st);
@@ -169,10 +176,6 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         const int16_t *par = root;
         int ping = 0;
         for (int l = L; l >= 1; --l) {
-            if (mode == 2 && !joined && t.n[l] >= kNarrow) {
-                SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
-                joined = true;
-            }
             int16_t *lch = nodes + (size_t)t.off[l - 1] * pi.pad;
             if (mma) {  // in place on every level
                 SNT_CUDA(launch_tree_down_mma<P>(par, single_tree(t.n[l - 1]), t.n[l], lch, st,
@@ -199,13 +202,16 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
             SNT_CUDA(cudaEventRecord(ev[6], st));
         }
     }
-    if (!joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     if (tm) SNT_CUDA(cudaEventRecord(ev[7], st));
     SNT_CUDA(launch_finalize<P>(km, Bi, gbuf, inv_leaves, pi.pk_bytes, pi.sk_bytes, 2 * sb,
                                 pi.sched, st, mma));
     if (tm) SNT_CUDA(cudaEventRecord(ev[8], st));
     SNT_CUDA(launch_sha512_pk(km, Bi, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[9], st));
+    if (!joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    SNT_CUDA(launch_fixup<P>(km, fix_count, fix_keys, gfix, inv_leaves, pi.pk_bytes, pi.sk_bytes,
+                             2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st));
+    if (tm) SNT_CUDA(cudaEventRecord(ev[10], st));
     if (!inline_stream) {  // join back into the caller's stream
         SNT_CUDA(cudaEventRecord(ctx->ev_done, st));
         SNT_CUDA(cudaStreamWaitEvent(caller, ctx->ev_done, 0));
@@ -482,9 +488,9 @@ snt_status snt_r3_inv(snt_ctx *ctx, int P, size_t n, const int8_t *g_dev, int8_t
     DeviceGuard dg(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     switch (P) {
-        case 653: SNT_CUDA(launch_r3_inv<653>((int)n, g_dev, out_dev, ok_dev, st, ctx->r3_lanes)); break;
-        case 761: SNT_CUDA(launch_r3_inv<761>((int)n, g_dev, out_dev, ok_dev, st, ctx->r3_lanes)); break;
-        case 857: SNT_CUDA(launch_r3_inv<857>((int)n, g_dev, out_dev, ok_dev, st, ctx->r3_lanes)); break;
+        case 653: SNT_CUDA(launch_r3_inv<653>((int)n, g_dev, out_dev, ok_dev, st, ctx->r3_lanes, ctx->r3_kpt)); break;
+        case 761: SNT_CUDA(launch_r3_inv<761>((int)n, g_dev, out_dev, ok_dev, st, ctx->r3_lanes, ctx->r3_kpt)); break;
+        case 857: SNT_CUDA(launch_r3_inv<857>((int)n, g_dev, out_dev, ok_dev, st, ctx->r3_lanes, ctx->r3_kpt)); break;
         default: return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     }
     return SNT_OK;
@@ -539,6 +545,10 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             if (value < 1 || value > 3) return set_error(SNT_EINVAL, "MMA tiles per warp is 1, 2 or 3");
             ctx->mma_tiles = value;
             return SNT_OK;
+        case SNT_OPT_R3_KPT:
+            if (value != 1 && value != 2) return set_error(SNT_EINVAL, "R/3 elements per lane group is 1 or 2");
+            ctx->r3_kpt = value;
+            return SNT_OK;
         default:
             return set_error(SNT_EINVAL, "unknown option %d", option);
     }
@@ -553,6 +563,7 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
         case SNT_OPT_NARROW_SEG: *value = ctx->narrow_seg; return SNT_OK;
         case SNT_OPT_RQ_ENGINE: *value = ctx->rq_engine; return SNT_OK;
         case SNT_OPT_MMA_TILES: *value = ctx->mma_tiles; return SNT_OK;
+        case SNT_OPT_R3_KPT: *value = ctx->r3_kpt; return SNT_OK;
         default: return set_error(SNT_EINVAL, "unknown option %d", option);
     }
 }
@@ -577,16 +588,19 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
     // per warp, or CUDA-core engine with tree split 4 or 8)
     std::vector<snt_ctx::Tuned> cands;
     for (int la : {4, 8, 32})
-        for (int ov : {0, 1, 2}) {
-            for (int ti : {1, 2}) {
-                snt_ctx::Tuned c;
-                c.lanes = la; c.overlap = ov; c.engine = 1; c.tiles = ti; c.split = ctx->tree_split;
-                cands.push_back(c);
-            }
-            for (int sp : {4, 8}) {
-                snt_ctx::Tuned c;
-                c.lanes = la; c.overlap = ov; c.engine = 0; c.tiles = 1; c.split = sp;
-                cands.push_back(c);
+        for (int kp : {1}) {  // two elements per lane group measured slower at every size
+            for (int ov : {0, 1, 2}) {
+                for (int ti : {1, 2}) {
+                    snt_ctx::Tuned c;
+                    c.lanes = la; c.kpt = kp; c.overlap = ov; c.engine = 1; c.tiles = ti;
+                    c.split = ctx->tree_split;
+                    cands.push_back(c);
+                }
+                for (int sp : {4, 8}) {
+                    snt_ctx::Tuned c;
+                    c.lanes = la; c.kpt = kp; c.overlap = ov; c.engine = 0; c.tiles = 1; c.split = sp;
+                    cands.push_back(c);
+                }
             }
         }
     snt_ctx::Tuned best;
@@ -621,13 +635,14 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
         choice[2] = best.overlap;
         choice[3] = best.engine;
         choice[4] = best.tiles;
+        choice[5] = best.kpt;
     }
     return snt_ctx_sync(ctx, ts);
 }
 
 snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *split_out,
                         int *overlap_out) {
-    int c[5] = {0, 0, 0, 0, 0};
+    int c[6] = {0, 0, 0, 0, 0, 0};
     const snt_status st = snt_autotune_ex(ctx, P, B, c);
     if (st != SNT_OK) return st;
     if (lanes_out) *lanes_out = c[0];
@@ -647,9 +662,10 @@ snt_status snt_ctx_phase_times(snt_ctx *ctx, float *ms, int n) {
     if (!ctx->timing) return set_error(SNT_EINVAL, "phase timing is off");
     DeviceGuard dg(ctx->device);
     cudaEvent_t *ev = ctx->ev_phase;
-    SNT_CUDA(cudaEventSynchronize(ev[9]));
+    SNT_CUDA(cudaEventSynchronize(ev[10]));
     SNT_CUDA(cudaEventSynchronize(ev[3]));
-    const int pairs[SNT_NPHASES][2] = {{0, 1}, {2, 3}, {1, 4}, {4, 5}, {5, 6}, {7, 8}, {8, 9}, {0, 9}};
+    const int pairs[SNT_NPHASES][2] = {{0, 1}, {2, 3}, {1, 4}, {4, 5}, {5, 6},
+                                       {7, 8}, {8, 9}, {0, 10}, {9, 10}};
     for (int i = 0; i < SNT_NPHASES; ++i)
         SNT_CUDA(cudaEventElapsedTime(&ms[i], ev[pairs[i][0]], ev[pairs[i][1]]));
     return SNT_OK;

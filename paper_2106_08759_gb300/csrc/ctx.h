@@ -15,7 +15,7 @@ inline constexpr int kMaxInject = 64;
 // inversions), 5 after the root, 6 after the down-sweep, 7 after the join,
 // 8 after h/encode, 9 after SHA-512; on the auxiliary stream 2 / 3 around the
 // R/3 kernel.
-inline constexpr int kPhaseEvents = 10;
+inline constexpr int kPhaseEvents = 11;
 inline constexpr size_t kMaxB = (size_t)1 << 24;
 
 
@@ -48,8 +48,9 @@ struct snt_ctx {
     int narrow_seg = snt::kDefaultNarrowSeg;
     int rq_engine = snt::kDefaultRqEngine;
     int mma_tiles = snt::kDefaultMmaTiles;
+    int r3_kpt = snt::kDefaultR3Kpt;
     // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
-    struct Tuned { int lanes = 0, split = 0, overlap = 0, engine = 0, tiles = 1; };
+    struct Tuned { int lanes = 0, split = 0, overlap = 0, engine = 0, tiles = 1, kpt = 1; };
     Tuned tuned[3][25];
     cudaStream_t tune = nullptr;  // stream used while autotuning
     snt::RaggedGraph ragged;      // last ragged plan and its graph

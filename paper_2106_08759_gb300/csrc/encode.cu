@@ -102,6 +102,50 @@ k_finalize_mma(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__rest
     }
 }
 
+// Fix-up of the keys whose g needed another attempt (deferred R/3 kernel):
+// h = g * (3f)^-1 with the final g, Rq_encode into pk and sk, and the hash
+// of the new pk into sk.  Runs after the h, hash and R/3 kernels of the call;
+// CTAs take list entries in turn, so an empty list costs one read.
+template <int P>
+__global__ void __launch_bounds__(Tp<P>::NT)
+k_fixup(KeyMap km, const int *__restrict__ fix_count, const int *__restrict__ fix_keys,
+        const int8_t *__restrict__ gfix, const int16_t *__restrict__ ainv, int pk_bytes,
+        int sk_bytes, int sk_pk_off, int hash_off, EncSched S) {
+    using G = Geo<P>;
+    __shared__ __align__(16) int As[Tp<P>::p8];
+    __shared__ __align__(16) int Es[Tp<P>::ESZ];
+    __shared__ uint32_t Rb[2][G::pad];
+    __shared__ uint8_t ob[1344];
+    const int n = *fix_count;
+    for (int f = blockIdx.x; f < n; f += gridDim.x) {
+        const int key = fix_keys[f];
+        const int16_t *inv = ainv + (size_t)key * G::pad;
+        __syncthreads();  // shared buffers free from the previous entry
+        fill_A<P>(gfix + (size_t)f * G::pad, As);
+        fill_E<P>(inv, Es);
+        __syncthreads();
+        int acc[1][8];
+        const int *const A1[1] = {As};
+        toeplitz_tile<P, 1>(A1, Es, threadIdx.x, 0, Tp<P>::p8, acc);
+        const int bl[1] = {(int)inv[P - 1]};
+        toeplitz_finish<P, 1>(A1, bl, acc, threadIdx.x, true);
+        const int j0 = 8 * threadIdx.x;
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (j0 + t < P) Rb[0][j0 + t] = (uint32_t)(acc[0][t] + G::half);
+        __syncthreads();
+        mixed_encode<G::pad>(Rb, S, ob);
+        const BatchDesc d = key_batch(km, key);
+        uint8_t *pkk = d.pk + (size_t)(key - d.key_base) * pk_bytes;
+        uint8_t *skk = d.sk + (size_t)(key - d.key_base) * sk_bytes;
+        for (int b = threadIdx.x; b < pk_bytes; b += blockDim.x) {
+            pkk[b] = ob[b];
+            skk[sk_pk_off + b] = ob[b];
+        }
+        if (threadIdx.x == 0) sha512_prefixed(4, ob, pk_bytes, nullptr, 0, skk + hash_off);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // SHA-512 (FIPS 180-4) of 0x04 | pk, first 32 bytes into the secret key
 // (Hash_prefix(4, pk) of the NTRU Prime secret key).  One thread per key.
@@ -223,6 +267,15 @@ cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, con
     return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_keys,
+                         const int8_t *gfix, const int16_t *ainv, int pk_bytes, int sk_bytes,
+                         int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st) {
+    k_fixup<P><<<8, Tp<P>::NT, 0, st>>>(km, fix_count, fix_keys, gfix, ainv, pk_bytes, sk_bytes,
+                                        sk_pk_off, hash_off, S);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
                              int hash_off, cudaStream_t st) {
     const int smem = (32 * pk_bytes + 15) / 16 * 16;
@@ -232,7 +285,10 @@ cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_b
 
 #define SNT_FIN_INST(P)                                                                       \
     template cudaError_t launch_finalize<P>(const KeyMap &, int, const int8_t *, const int16_t *, \
-                                            int, int, int, const EncSched &, cudaStream_t, bool);
+                                            int, int, int, const EncSched &, cudaStream_t, bool); \
+    template cudaError_t launch_fixup<P>(const KeyMap &, const int *, const int *, const int8_t *, \
+                                         const int16_t *, int, int, int, int, const EncSched &,   \
+                                         cudaStream_t);
 SNT_FIN_INST(653)
 SNT_FIN_INST(761)
 SNT_FIN_INST(857)

@@ -20,6 +20,7 @@ constexpr int kDefaultR3Overlap = 1;   // R/3 on its own low-priority stream
 constexpr int kDefaultNarrowSeg = 1;   // output-split narrow tree levels
 constexpr int kDefaultRqEngine = 1;    // R/q products on the tensor cores
 constexpr int kDefaultMmaTiles = 1;    // MMA tiles per warp
+constexpr int kDefaultR3Kpt = 1;       // R/3 elements per lane group
 
 // Records a one-line error message (snt_last_error_string) and returns s.
 snt_status set_error(snt_status s, const char *fmt, ...);
@@ -132,13 +133,23 @@ inline size_t keygen_scratch(const ParamInfo &pi, size_t B, bool host_out) {
 inline size_t narrow_scratch(const ParamInfo &pi) {
     return 2 * align256((size_t)2 * kSegMaxNodes * pi.pad * sizeof(int16_t));
 }
+// ... then the resampling list of the deferred R/3 kernel: a count, B key
+// indices and B rows of g (int8, stride pad).
+inline size_t fix_list_bytes(size_t B) { return align256(sizeof(int) * (1 + B)); }
+inline size_t fix_scratch(const ParamInfo &pi, size_t B) {
+    return fix_list_bytes(B) + align256(B * pi.pad);
+}
 inline size_t keygen_arena(const ParamInfo &pi, size_t B, bool host_out) {
-    return keygen_scratch(pi, B, host_out) + narrow_scratch(pi);
+    return keygen_scratch(pi, B, host_out) + narrow_scratch(pi) + fix_scratch(pi, B);
 }
 // Arena layout of a context keygen call: tree nodes, g rows, the ping-pong
-// buffers, then (host-buffer calls) the pk and sk staging at this offset.
-inline size_t staging_offset(const ParamInfo &pi, size_t B) {
+// buffers, the resampling list, then (host-buffer calls) the pk and sk
+// staging at this offset.
+inline size_t fix_offset(const ParamInfo &pi, size_t B) {
     return keygen_scratch(pi, B, false) + narrow_scratch(pi);
+}
+inline size_t staging_offset(const ParamInfo &pi, size_t B) {
+    return fix_offset(pi, B) + fix_scratch(pi, B);
 }
 
 struct DeviceGuard {

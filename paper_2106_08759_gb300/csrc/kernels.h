@@ -87,16 +87,24 @@ inline LevelMap single_tree(int n_in) {
     return lm;
 }
 
+// g_out (optional): also g's attempt-0 draw per key (int8, stride pad), with
+// the injected test draws, and *fix_count = 0 (the resampling list).
 template <int P>
 cudaError_t launch_sample_f(const KeyMap &km, int nkeys, int16_t *leaves, int sk_bytes,
-                            int rho_off, cudaStream_t st);
+                            int rho_off, cudaStream_t st, int8_t *g_out = nullptr,
+                            const uint64_t *inj_idx = nullptr, const int8_t *inj_g = nullptr,
+                            int n_inj = 0, int *fix_count = nullptr);
+// gfix != null: deferred form (attempt 0 read from g_out, g_out untouched,
+// resampled keys appended to fix_keys / gfix rows, *fix_count of them).
 template <int P>
 cudaError_t launch_r3_keygen(const KeyMap &km, int nkeys, int8_t *g_out, int sk_bytes,
                              int sk_off, const uint64_t *inj_idx, const int8_t *inj_g, int n_inj,
-                             int *err, cudaStream_t st, int lanes);
+                             int *err, cudaStream_t st, int lanes, int kpt = 1,
+                             int8_t *gfix = nullptr, int *fix_count = nullptr,
+                             int *fix_keys = nullptr);
 template <int P>
 cudaError_t launch_r3_inv(int n, const int8_t *g, int8_t *out, int32_t *ok, cudaStream_t st,
-                          int lanes);
+                          int lanes, int kpt = 1);
 template <int P>
 cudaError_t launch_tree_up(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
                            cudaStream_t st, int max_split);
@@ -138,6 +146,11 @@ template <int P>
 cudaError_t launch_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
                                cudaStream_t st, const int *idx = nullptr);
+// Keys on the resampling list: h with the final g, pk, sk's copy and hash.
+template <int P>
+cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_keys,
+                         const int8_t *gfix, const int16_t *ainv, int pk_bytes, int sk_bytes,
+                         int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st);
 // h = g * (3f)^-1, Rq_encode(h) into pk and sk; mma: h on the tensor cores.
 template <int P>
 cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, const int16_t *ainv,

@@ -22,8 +22,10 @@
 // per 32 trits.  One-trit shifts are funnel shifts inside a lane plus one
 // shuffle (two packed carry bits) across the lanes of the group.  Per-step
 // control (G(0), F(0), delta, the swap) is uniform within a group and
-// branch-free.  32 / LK elements share a warp, so every shuffle and control
-// instruction serves all of them.
+// branch-free.  32 / LK element groups share a warp, and each group may run
+// KPT elements at once (their words interleaved in the same registers' step
+// loop, their shuffled bits packed into the same shuffles), so every shuffle
+// serves 32 KPT / LK elements and each lane has KPT independent chains.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -31,13 +33,16 @@ namespace snt {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-template <int P, int LK_> struct R3Geo {
+template <int P, int LK_, int KPT_ = 1> struct R3Geo {
     static constexpr int WORDS = (P + 1 + 31) / 32;      // 21 / 24 / 27
     static constexpr int LK = LK_;                        // lanes per element: 4, 8 or 32
+    static constexpr int KPT = KPT_;                      // elements per lane group: 1 or 2
     static constexpr int WL = (WORDS + LK - 1) / LK;      // words per lane
-    static constexpr int EPW = 32 / LK;                   // elements per warp
-    static constexpr int WARPS = 4;                       // warps per CTA
+    static constexpr int GPW = 32 / LK;                   // lane groups per warp
+    static constexpr int EPW = GPW * KPT;                 // elements per warp
+    static constexpr int WARPS = 4 / KPT;                 // warps per CTA
     static constexpr int EPB = EPW * WARPS;               // elements per CTA
+    static constexpr int ROW = Geo<P>::pad;               // shared bytes per element
 };
 
 // (am, as) + (bm, bs) in F_3 on 32 trits at once (s is don't-care where m = 0):
@@ -63,17 +68,18 @@ __device__ __forceinline__ void cswap_fma(uint32_t &a, uint32_t &b, uint32_t sw,
     b = nb;
 }
 
-// 2p - 1 divsteps on this group's state.  In: planes of G (reversed g).
+// 2p - 1 divsteps on this group's KPT states.  In: planes of G (reversed g).
 // Out: planes of 1/g in reversed order (trit j is coefficient p-1-j of 1/g).
-// Returns true iff g is invertible.  All 32 lanes of the warp must call it.
-template <int P, int LKT>
-__device__ __forceinline__ bool r3_divsteps(uint32_t (&gm)[R3Geo<P, LKT>::WL],
-                                            uint32_t (&gs)[R3Geo<P, LKT>::WL],
-                                            uint32_t (&vm)[R3Geo<P, LKT>::WL],
-                                            uint32_t (&vs)[R3Geo<P, LKT>::WL]) {
+// good[k] = g_k invertible.  All 32 lanes of the warp must call it.
+template <int P, int LKT, int KPT>
+__device__ __forceinline__ void r3_divsteps(uint32_t (&gm)[KPT][R3Geo<P, LKT>::WL],
+                                            uint32_t (&gs)[KPT][R3Geo<P, LKT>::WL],
+                                            uint32_t (&vm)[KPT][R3Geo<P, LKT>::WL],
+                                            uint32_t (&vs)[KPT][R3Geo<P, LKT>::WL],
+                                            bool (&good)[KPT]) {
     constexpr int WL = R3Geo<P, LKT>::WL, LK = LKT;
     const int sub = threadIdx.x & (LK - 1);
-    uint32_t fm[WL], fs[WL], rm[WL], rs[WL];
+    uint32_t fm[KPT][WL], fs[KPT][WL], rm[KPT][WL], rs[KPT][WL];
 #pragma unroll
     for (int w = 0; w < WL; ++w) {
         const int t0 = 32 * (WL * sub + w);  // first trit of this word
@@ -81,67 +87,91 @@ __device__ __forceinline__ bool r3_divsteps(uint32_t (&gm)[R3Geo<P, LKT>::WL],
         if (t0 == 0) m |= 1u;
         if (P - 1 >= t0 && P - 1 < t0 + 32) { m |= 1u << (P - 1 - t0); s |= 1u << (P - 1 - t0); }
         if (P >= t0 && P < t0 + 32) { m |= 1u << (P - t0); s |= 1u << (P - t0); }
-        fm[w] = m; fs[w] = s;
-        vm[w] = 0; vs[w] = 0;
-        rm[w] = (t0 == 0) ? 1u : 0u; rs[w] = 0;
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+            fm[k][w] = m; fs[k][w] = s;
+            vm[k][w] = 0; vs[k][w] = 0;
+            rm[k][w] = (t0 == 0) ? 1u : 0u; rs[k][w] = 0;
+        }
     }
-    int delta = 1;
-    uint32_t f0s = 0;  // sign bit of F(0); F(0) is never zero
+    int delta[KPT];
+    uint32_t f0s[KPT];  // sign bit of F(0); F(0) is never zero
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) { delta[k] = 1; f0s[k] = 0; }
     uint32_t neg1;
     asm volatile("mov.u32 %0, 0xffffffff;" : "=r"(neg1));
 #pragma unroll 1
     for (int step = 0; step < 2 * P - 1; ++step) {
-        // V <- x V: carry the top trit of each lane into the next lane
-        uint32_t cv = (vm[WL - 1] >> 31) | ((vs[WL - 1] >> 30) & 2u);
+        // V <- x V: carry the top trit of each lane into the next lane (two
+        // bits per element, all elements in one shuffle)
+        uint32_t cv = 0;
+#pragma unroll
+        for (int k = 0; k < KPT; ++k)
+            cv |= ((vm[k][WL - 1] >> 31) | ((vs[k][WL - 1] >> 30) & 2u)) << (2 * k);
         cv = __shfl_up_sync(FULL, cv, 1, LK);
         if (sub == 0) cv = 0;
+        // G(0) of every element, uniform within the group
+        uint32_t g0 = 0;
 #pragma unroll
-        for (int w = WL - 1; w > 0; --w) {
-            vm[w] = __funnelshift_l(vm[w - 1], vm[w], 1);
-            vs[w] = __funnelshift_l(vs[w - 1], vs[w], 1);
-        }
-        vm[0] = (vm[0] << 1) | (cv & 1u);
-        vs[0] = (vs[0] << 1) | (cv >> 1);
-        // G(0), uniform within the group
-        const uint32_t g0 = __shfl_sync(FULL, (gm[0] & 1u) | ((gs[0] & 1u) << 1), 0, LK);
-        const uint32_t g0m = g0 & 1u, g0s = g0 >> 1;
-        const uint32_t sw = (uint32_t)(delta > 0) & g0m;
-        // Conditional swaps as integer multiply-adds, a + (b - a) * sw with sw
-        // in {0, 1} (exact modulo 2^32): they run on the FMA pipe, which the
-        // bit operations of the F_3 arithmetic leave idle.
+        for (int k = 0; k < KPT; ++k) g0 |= ((gm[k][0] & 1u) | ((gs[k][0] & 1u) << 1)) << (2 * k);
+        g0 = __shfl_sync(FULL, g0, 0, LK);
 #pragma unroll
-        for (int w = 0; w < WL; ++w) {
-            cswap_fma(fm[w], gm[w], sw, neg1);
-            cswap_fma(fs[w], gs[w], sw, neg1);
-            cswap_fma(vm[w], rm[w], sw, neg1);
-            cswap_fma(vs[w], rs[w], sw, neg1);
-        }
-        const uint32_t nf0s = sw ? g0s : f0s;
-        const uint32_t ng0s = sw ? f0s : g0s;  // G(0) stays nonzero iff it was
-        f0s = nf0s;
-        delta = (sw ? -delta : delta) + 1;
-        // c = -G(0) F(0) (= -G(0)/F(0) in F_3)
-        const uint32_t cm = 0u - g0m;
-        const uint32_t cs = 0u - ((ng0s ^ f0s ^ 1u) & 1u);
+        for (int k = 0; k < KPT; ++k) {
 #pragma unroll
-        for (int w = 0; w < WL; ++w) {
-            f3_add(gm[w], gs[w], fm[w] & cm, fs[w] ^ cs, gm[w], gs[w]);
-            f3_add(rm[w], rs[w], vm[w] & cm, vs[w] ^ cs, rm[w], rs[w]);
+            for (int w = WL - 1; w > 0; --w) {
+                vm[k][w] = __funnelshift_l(vm[k][w - 1], vm[k][w], 1);
+                vs[k][w] = __funnelshift_l(vs[k][w - 1], vs[k][w], 1);
+            }
+            vm[k][0] = (vm[k][0] << 1) | ((cv >> (2 * k)) & 1u);
+            vs[k][0] = (vs[k][0] << 1) | ((cv >> (2 * k + 1)) & 1u);
+            const uint32_t g0m = (g0 >> (2 * k)) & 1u, g0s = (g0 >> (2 * k + 1)) & 1u;
+            const uint32_t sw = (uint32_t)(delta[k] > 0) & g0m;
+            // Conditional swaps as integer multiply-adds, a + (b - a) * sw with
+            // sw in {0, 1} (exact modulo 2^32): they run on the FMA pipe, which
+            // the bit operations of the F_3 arithmetic leave idle.
+#pragma unroll
+            for (int w = 0; w < WL; ++w) {
+                cswap_fma(fm[k][w], gm[k][w], sw, neg1);
+                cswap_fma(fs[k][w], gs[k][w], sw, neg1);
+                cswap_fma(vm[k][w], rm[k][w], sw, neg1);
+                cswap_fma(vs[k][w], rs[k][w], sw, neg1);
+            }
+            const uint32_t nf0s = sw ? g0s : f0s[k];
+            const uint32_t ng0s = sw ? f0s[k] : g0s;  // G(0) stays nonzero iff it was
+            f0s[k] = nf0s;
+            delta[k] = (sw ? -delta[k] : delta[k]) + 1;
+            // c = -G(0) F(0) (= -G(0)/F(0) in F_3)
+            const uint32_t cm = 0u - g0m;
+            const uint32_t cs = 0u - ((ng0s ^ f0s[k] ^ 1u) & 1u);
+#pragma unroll
+            for (int w = 0; w < WL; ++w) {
+                f3_add(gm[k][w], gs[k][w], fm[k][w] & cm, fs[k][w] ^ cs, gm[k][w], gs[k][w]);
+                f3_add(rm[k][w], rs[k][w], vm[k][w] & cm, vs[k][w] ^ cs, rm[k][w], rs[k][w]);
+            }
         }
         // G <- G / x (trit 0 is zero now): bring in bit 0 of the next lane
-        uint32_t cg = __shfl_down_sync(FULL, (gm[0] & 1u) | ((gs[0] & 1u) << 1), 1, LK);
+        uint32_t cg = 0;
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) cg |= ((gm[k][0] & 1u) | ((gs[k][0] & 1u) << 1)) << (2 * k);
+        cg = __shfl_down_sync(FULL, cg, 1, LK);
         if (sub == LK - 1) cg = 0;
 #pragma unroll
-        for (int w = 0; w < WL - 1; ++w) {
-            gm[w] = __funnelshift_r(gm[w], gm[w + 1], 1);
-            gs[w] = __funnelshift_r(gs[w], gs[w + 1], 1);
+        for (int k = 0; k < KPT; ++k) {
+#pragma unroll
+            for (int w = 0; w < WL - 1; ++w) {
+                gm[k][w] = __funnelshift_r(gm[k][w], gm[k][w + 1], 1);
+                gs[k][w] = __funnelshift_r(gs[k][w], gs[k][w + 1], 1);
+            }
+            gm[k][WL - 1] = __funnelshift_r(gm[k][WL - 1], cg >> (2 * k), 1);
+            gs[k][WL - 1] = __funnelshift_r(gs[k][WL - 1], cg >> (2 * k + 1), 1);
         }
-        gm[WL - 1] = __funnelshift_r(gm[WL - 1], cg, 1);
-        gs[WL - 1] = __funnelshift_r(gs[WL - 1], cg >> 1, 1);
     }
 #pragma unroll
-    for (int w = 0; w < WL; ++w) vs[w] ^= 0u - f0s;
-    return delta == 0;
+    for (int k = 0; k < KPT; ++k) {
+#pragma unroll
+        for (int w = 0; w < WL; ++w) vs[k][w] ^= 0u - f0s[k];
+        good[k] = delta[k] == 0;
+    }
 }
 
 // This lane's planes of G (trit t = g[p-1-t]) from int8 coefficients g[0..p)
@@ -193,83 +223,136 @@ __device__ __forceinline__ void reversed_to_smem(const uint32_t (&om)[R3Geo<P, L
 // into the secret key at sk_off.  A warp keeps retrying while any of its
 // elements still needs an invertible g (each retry costs the warp a full
 // divstep run; a random g fails with probability about 3^-19).
+//
+// Deferred form (gfix != null): attempt 0 of g is already in g_out (written
+// by the sampling kernel, read by the h kernel while this one runs), so it
+// is read from there and g_out is left untouched; a key that needs another
+// attempt is appended to the resampling list (fix_keys[i], its final g in
+// row i of gfix) for the fix-up kernel that runs after both.
 // ---------------------------------------------------------------------------
-template <int P, int LKT>
-__global__ void __launch_bounds__(32 * R3Geo<P, LKT>::WARPS)
+template <int P, int LKT, int KPT>
+__global__ void __launch_bounds__(32 * R3Geo<P, LKT, KPT>::WARPS)
 k_r3_keygen(KeyMap km, int B, int8_t *__restrict__ g_out, int sk_bytes, int sk_off,
             const uint64_t *__restrict__ inj_idx, const int8_t *__restrict__ inj_g,
-            int n_inj, int *__restrict__ err) {
+            int n_inj, int *__restrict__ err, int8_t *__restrict__ gfix,
+            int *__restrict__ fix_count, int *__restrict__ fix_keys) {
     using Gm = Geo<P>;
-    using RG = R3Geo<P, LKT>;
-    constexpr int WL = RG::WL, LK = RG::LK, EPW = RG::EPW;
-    __shared__ int8_t smem[RG::EPB][1024];
+    using RG = R3Geo<P, LKT, KPT>;
+    constexpr int WL = RG::WL, LK = RG::LK, EPW = RG::EPW, GPW = RG::GPW;
+    __shared__ __align__(16) int8_t smem[RG::EPB][RG::ROW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = lane & (LK - 1), grp = lane / LK;
     const int ebase = blockIdx.x * RG::EPB + warp * EPW;  // first element of this warp
     if (ebase >= B) return;                               // warp-uniform
-    const int key = ebase + grp;
-    const bool live = key < B;
-    const BatchDesc bd = key_batch(km, live ? key : ebase);
-    const uint64_t seed = bd.seed;
-    const uint64_t k = bd.first + (uint64_t)(key - bd.key_base);
-    int8_t *gsm = smem[warp * EPW + grp];
-
-    // optional injected attempt-0 draw (test hook)
-    int inj = -1;
-    if (live)
-        for (int j = sub; j < n_inj; j += LK)
-            if (inj_idx[j] == k) inj = j;
-    for (int off = LK / 2; off > 0; off >>= 1) inj = max(inj, __shfl_xor_sync(FULL, inj, off, LK));
-
-    bool ok = !live;
-    uint32_t om[WL], os[WL];
+    // this group's elements: warp slots grp + k GPW
+    const bool deferred = gfix != nullptr;
+    bool ok[KPT], first_ok[KPT];
+    uint64_t seed[KPT], kidx[KPT];
+    int inj[KPT];
+    int8_t *gsm[KPT];
 #pragma unroll
-    for (int w = 0; w < WL; ++w) { om[w] = 0; os[w] = 0; }
+    for (int k = 0; k < KPT; ++k) {
+        const int e = ebase + grp + k * GPW;
+        const bool live = e < B;
+        const BatchDesc bd = key_batch(km, live ? e : ebase);
+        seed[k] = bd.seed;
+        kidx[k] = bd.first + (uint64_t)((live ? e : ebase) - bd.key_base);
+        gsm[k] = smem[warp * EPW + grp + k * GPW];
+        ok[k] = !live;
+        first_ok[k] = true;
+        // optional injected attempt-0 draw (test hook)
+        int j0 = -1;
+        if (live)
+            for (int j = sub; j < n_inj; j += LK)
+                if (inj_idx[j] == kidx[k]) j0 = j;
+        for (int off = LK / 2; off > 0; off >>= 1) j0 = max(j0, __shfl_xor_sync(FULL, j0, off, LK));
+        inj[k] = j0;
+    }
+    uint32_t om[KPT][WL], os[KPT][WL];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int w = 0; w < WL; ++w) { om[k][w] = 0; os[k][w] = 0; }
     for (int att = 0; att < kMaxGAttempts; ++att) {
-        if (__all_sync(FULL, ok)) break;
-        if (!ok) {
-            if (att == 0 && inj >= 0) {
-                for (int i = sub; i < P; i += LK) gsm[i] = inj_g[(size_t)inj * Gm::p + i];
+        bool all_ok = true;
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) all_ok = all_ok && ok[k];
+        if (__all_sync(FULL, all_ok)) break;
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+            if (ok[k]) continue;
+            if (att == 0 && deferred) {
+                const int8_t *g0 = g_out + (size_t)(ebase + grp + k * GPW) * Gm::pad;
+                for (int i = sub; i < P; i += LK) gsm[k][i] = g0[i];
+            } else if (att == 0 && inj[k] >= 0) {
+                for (int i = sub; i < P; i += LK) gsm[k][i] = inj_g[(size_t)inj[k] * Gm::p + i];
             } else {
                 // g_i = floor(3 (u_i mod 2^30) / 2^30) - 1 for word u_i of stream 0
                 for (int blk = sub; 4 * blk < P; blk += LK) {
                     uint32_t r[4];
-                    rand_block(seed, k, STREAM_G, (uint32_t)att, (uint32_t)blk, r);
+                    rand_block(seed[k], kidx[k], STREAM_G, (uint32_t)att, (uint32_t)blk, r);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const int i = 4 * blk + j;
                         if (i < P)
-                            gsm[i] = (int8_t)((int)(((unsigned long long)(r[j] & 0x3fffffffu) * 3u) >> 30) - 1);
+                            gsm[k][i] = (int8_t)((int)(((unsigned long long)(r[j] & 0x3fffffffu) * 3u) >> 30) - 1);
                     }
                 }
             }
         }
         __syncwarp();
-        uint32_t gm[WL], gs[WL], vm[WL], vs[WL];
-        planes_from_reversed<P, LKT>(gsm, gm, gs);
-        const bool good = r3_divsteps<P, LKT>(gm, gs, vm, vs);
-        if (!ok && good) {
+        uint32_t gm[KPT][WL], gs[KPT][WL], vm[KPT][WL], vs[KPT][WL];
 #pragma unroll
-            for (int w = 0; w < WL; ++w) { om[w] = vm[w]; os[w] = vs[w]; }
+        for (int k = 0; k < KPT; ++k) planes_from_reversed<P, LKT>(gsm[k], gm[k], gs[k]);
+        bool good[KPT];
+        r3_divsteps<P, LKT, KPT>(gm, gs, vm, vs, good);
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+            if (!ok[k] && good[k]) {
+#pragma unroll
+                for (int w = 0; w < WL; ++w) { om[k][w] = vm[k][w]; os[k][w] = vs[k][w]; }
+            }
+            if (att == 0) first_ok[k] = ok[k] || good[k];
+            ok[k] = ok[k] || good[k];
         }
-        ok = ok || good;
         __syncwarp();
     }
-    if (live && !ok) {
-        if (sub == 0) atomicOr(err, ERR_RESAMPLE);
 #pragma unroll
-        for (int w = 0; w < WL; ++w) { om[w] = 0; os[w] = 0; }
-    }
-    // g (natural order) for h = g * (3f)^-1: the warp writes its rows together
+    for (int k = 0; k < KPT; ++k)
+        if (!ok[k]) {  // (dead slots start ok)
+            if (sub == 0) atomicOr(err, ERR_RESAMPLE);
+#pragma unroll
+            for (int w = 0; w < WL; ++w) { om[k][w] = 0; os[k][w] = 0; }
+        }
     __syncwarp();
-    for (int e = 0; e < EPW; ++e) {
-        if (ebase + e >= B) break;
-        const int8_t *src = smem[warp * EPW + e];
-        int8_t *gk = g_out + (size_t)(ebase + e) * Gm::pad;
-        for (int i = lane; i < Gm::pad; i += 32) gk[i] = (i < P) ? src[i] : (int8_t)0;
+    if (deferred) {
+        // resampled keys: final g to the resampling list (one slot per key)
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+            const int e = ebase + grp + k * GPW;
+            int slot = 0;
+            const bool fix = e < B && ok[k] && !first_ok[k];
+            if (fix && sub == 0) {
+                slot = atomicAdd(fix_count, 1);
+                fix_keys[slot] = e;
+            }
+            slot = __shfl_sync(FULL, slot, 0, LK);
+            if (fix)
+                for (int i = sub; i < Gm::pad; i += LK)
+                    gfix[(size_t)slot * Gm::pad + i] = (i < P) ? gsm[k][i] : (int8_t)0;
+        }
+    } else {
+        // g (natural order) for h = g * (3f)^-1: the warp writes its rows together
+        for (int e = 0; e < EPW; ++e) {
+            if (ebase + e >= B) break;
+            const int8_t *src = smem[warp * EPW + e];
+            int8_t *gk = g_out + (size_t)(ebase + e) * Gm::pad;
+            for (int i = lane; i < Gm::pad; i += 32) gk[i] = (i < P) ? src[i] : (int8_t)0;
+        }
     }
     __syncwarp();
-    reversed_to_smem<P, LKT>(om, os, gsm);
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) reversed_to_smem<P, LKT>(om[k], os[k], gsm[k]);
     __syncwarp();
     // Small_encode(1/g)
     for (int e = 0; e < EPW; ++e) {
@@ -293,80 +376,112 @@ k_r3_keygen(KeyMap km, int B, int8_t *__restrict__ g_out, int sk_bytes, int sk_o
 // Batch form for the kernel microbenchmark: out_i = 1/g_i, ok_i.
 // g, out: n x p int8 (stride p).
 // ---------------------------------------------------------------------------
-template <int P, int LKT>
-__global__ void __launch_bounds__(32 * R3Geo<P, LKT>::WARPS)
+template <int P, int LKT, int KPT>
+__global__ void __launch_bounds__(32 * R3Geo<P, LKT, KPT>::WARPS)
 k_r3_inv(int n, const int8_t *__restrict__ g, int8_t *__restrict__ out,
          int32_t *__restrict__ okv) {
-    using RG = R3Geo<P, LKT>;
-    constexpr int WL = RG::WL, LK = RG::LK, EPW = RG::EPW;
-    __shared__ int8_t smem[RG::EPB][1024];
+    using RG = R3Geo<P, LKT, KPT>;
+    constexpr int WL = RG::WL, LK = RG::LK, EPW = RG::EPW, GPW = RG::GPW;
+    __shared__ __align__(16) int8_t smem[RG::EPB][RG::ROW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = lane & (LK - 1), grp = lane / LK;
     const int ebase = blockIdx.x * RG::EPB + warp * EPW;
     if (ebase >= n) return;
-    const int e = ebase + grp;
-    const bool live = e < n;
-    int8_t *gsm = smem[warp * EPW + grp];
-    for (int i = sub; i < P; i += LK) gsm[i] = live ? g[(size_t)e * P + i] : (int8_t)0;
-    __syncwarp();
-    uint32_t gm[WL], gs[WL], vm[WL], vs[WL];
-    planes_from_reversed<P, LKT>(gsm, gm, gs);
-    const bool ok = r3_divsteps<P, LKT>(gm, gs, vm, vs);
-    if (!ok)
+    uint32_t gm[KPT][WL], gs[KPT][WL], vm[KPT][WL], vs[KPT][WL];
+    int8_t *gsm[KPT];
 #pragma unroll
-        for (int w = 0; w < WL; ++w) { vm[w] = 0; vs[w] = 0; }
+    for (int k = 0; k < KPT; ++k) {
+        const int e = ebase + grp + k * GPW;
+        gsm[k] = smem[warp * EPW + grp + k * GPW];
+        for (int i = sub; i < P; i += LK) gsm[k][i] = (e < n) ? g[(size_t)e * P + i] : (int8_t)0;
+    }
     __syncwarp();
-    reversed_to_smem<P, LKT>(vm, vs, gsm);
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) planes_from_reversed<P, LKT>(gsm[k], gm[k], gs[k]);
+    bool ok[KPT];
+    r3_divsteps<P, LKT, KPT>(gm, gs, vm, vs, ok);
+#pragma unroll
+    for (int k = 0; k < KPT; ++k)
+        if (!ok[k])
+#pragma unroll
+            for (int w = 0; w < WL; ++w) { vm[k][w] = 0; vs[k][w] = 0; }
     __syncwarp();
-    if (live) {
-        for (int i = sub; i < P; i += LK) out[(size_t)e * P + i] = gsm[i];
-        if (sub == 0) okv[e] = ok ? 1 : 0;
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) reversed_to_smem<P, LKT>(vm[k], vs[k], gsm[k]);
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+        const int e = ebase + grp + k * GPW;
+        if (e < n) {
+            for (int i = sub; i < P; i += LK) out[(size_t)e * P + i] = gsm[k][i];
+            if (sub == 0) okv[e] = ok[k] ? 1 : 0;
+        }
     }
 }
 
-template <int P, int LK>
+template <int P, int LK, int KPT>
 cudaError_t launch_r3_keygen_lk(const KeyMap &km, int B, int8_t *g_out, int sk_bytes, int sk_off,
                                 const uint64_t *inj_idx, const int8_t *inj_g, int n_inj, int *err,
-                                cudaStream_t st) {
-    constexpr int EPB = R3Geo<P, LK>::EPB;
-    k_r3_keygen<P, LK><<<(B + EPB - 1) / EPB, 32 * R3Geo<P, LK>::WARPS, 0, st>>>(
-        km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err);
+                                cudaStream_t st, int8_t *gfix, int *fix_count, int *fix_keys) {
+    using RG = R3Geo<P, LK, KPT>;
+    k_r3_keygen<P, LK, KPT><<<(B + RG::EPB - 1) / RG::EPB, 32 * RG::WARPS, 0, st>>>(
+        km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, gfix, fix_count, fix_keys);
     return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t launch_r3_keygen(const KeyMap &km, int B, int8_t *g_out, int sk_bytes, int sk_off,
                              const uint64_t *inj_idx, const int8_t *inj_g, int n_inj, int *err,
-                             cudaStream_t st, int lanes) {
-    switch (lanes) {
-        case 4: return launch_r3_keygen_lk<P, 4>(km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st);
-        case 8: return launch_r3_keygen_lk<P, 8>(km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st);
-        default: return launch_r3_keygen_lk<P, 32>(km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st);
+                             cudaStream_t st, int lanes, int kpt, int8_t *gfix, int *fix_count,
+                             int *fix_keys) {
+#define SNT_R3K(LK, KP)                                                                     \
+    launch_r3_keygen_lk<P, LK, KP>(km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st, \
+                                   gfix, fix_count, fix_keys)
+    if (kpt == 2) {
+        switch (lanes) {
+            case 4: return SNT_R3K(4, 2);
+            case 8: return SNT_R3K(8, 2);
+            default: return SNT_R3K(32, 2);
+        }
     }
+    switch (lanes) {
+        case 4: return SNT_R3K(4, 1);
+        case 8: return SNT_R3K(8, 1);
+        default: return SNT_R3K(32, 1);
+    }
+#undef SNT_R3K
 }
 
-template <int P, int LK>
+template <int P, int LK, int KPT>
 cudaError_t launch_r3_inv_lk(int n, const int8_t *g, int8_t *out, int32_t *ok, cudaStream_t st) {
-    constexpr int EPB = R3Geo<P, LK>::EPB;
-    k_r3_inv<P, LK><<<(n + EPB - 1) / EPB, 32 * R3Geo<P, LK>::WARPS, 0, st>>>(n, g, out, ok);
+    using RG = R3Geo<P, LK, KPT>;
+    k_r3_inv<P, LK, KPT><<<(n + RG::EPB - 1) / RG::EPB, 32 * RG::WARPS, 0, st>>>(n, g, out, ok);
     return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t launch_r3_inv(int n, const int8_t *g, int8_t *out, int32_t *ok, cudaStream_t st,
-                          int lanes) {
+                          int lanes, int kpt) {
+    if (kpt == 2) {
+        switch (lanes) {
+            case 4: return launch_r3_inv_lk<P, 4, 2>(n, g, out, ok, st);
+            case 8: return launch_r3_inv_lk<P, 8, 2>(n, g, out, ok, st);
+            default: return launch_r3_inv_lk<P, 32, 2>(n, g, out, ok, st);
+        }
+    }
     switch (lanes) {
-        case 4: return launch_r3_inv_lk<P, 4>(n, g, out, ok, st);
-        case 8: return launch_r3_inv_lk<P, 8>(n, g, out, ok, st);
-        default: return launch_r3_inv_lk<P, 32>(n, g, out, ok, st);
+        case 4: return launch_r3_inv_lk<P, 4, 1>(n, g, out, ok, st);
+        case 8: return launch_r3_inv_lk<P, 8, 1>(n, g, out, ok, st);
+        default: return launch_r3_inv_lk<P, 32, 1>(n, g, out, ok, st);
     }
 }
 
 #define SNT_R3_INST(P)                                                                      \
     template cudaError_t launch_r3_keygen<P>(const KeyMap &, int, int8_t *, int, int,       \
                                              const uint64_t *, const int8_t *, int, int *,  \
-                                             cudaStream_t, int);                            \
-    template cudaError_t launch_r3_inv<P>(int, const int8_t *, int8_t *, int32_t *, cudaStream_t, int);
+                                             cudaStream_t, int, int, int8_t *, int *, int *); \
+    template cudaError_t launch_r3_inv<P>(int, const int8_t *, int8_t *, int32_t *, cudaStream_t, int, \
+                                          int);
 SNT_R3_INST(653)
 SNT_R3_INST(761)
 SNT_R3_INST(857)

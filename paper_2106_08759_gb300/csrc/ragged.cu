@@ -40,8 +40,9 @@ struct Group {
     std::vector<int> lev_off;             // first node of each level (nodes)
     std::vector<int> root_row;            // node row of each batch's root
     size_t nodes = 0;                     // node rows in the forest
-    // arena offsets (bytes)
-    size_t off_nodes = 0, off_g = 0;
+    // arena offsets (bytes): tree nodes, g rows, resampling list (count and
+    // keys, then final g rows) of the deferred R/3 kernel
+    size_t off_nodes = 0, off_g = 0, off_fix = 0, off_gfix = 0;
     // table offsets (bytes, from the start of the uploaded table block)
     size_t t_desc = 0, t_pre = 0, t_root = 0;
 };
@@ -85,11 +86,14 @@ void plan_group(Group &g, const size_t *B) {
 template <int P>
 snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStream_t st,
                         cudaStream_t aux, cudaEvent_t ev_fork, cudaEvent_t ev_join, int lanes,
-                        int split, bool mma, int tiles) {
+                        int split, bool mma, int tiles, int kpt) {
     const ParamInfo &pi = g.pi;
     const int nb = (int)g.batch.size();
     int16_t *nodes = reinterpret_cast<int16_t *>(ctx->arena + g.off_nodes);
     int8_t *gbuf = reinterpret_cast<int8_t *>(ctx->arena + g.off_g);
+    int *fix_count = reinterpret_cast<int *>(ctx->arena + g.off_fix);
+    int *fix_keys = fix_count + 1;
+    int8_t *gfix = reinterpret_cast<int8_t *>(ctx->arena + g.off_gfix);
     KeyMap km;
     std::memset(&km, 0, sizeof(km));
     km.tab = reinterpret_cast<const BatchDesc *>(tables + g.t_desc);
@@ -97,11 +101,14 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
     const int *pre = reinterpret_cast<const int *>(tables + g.t_pre);  // [level][nb + 1]
     const int *roots = reinterpret_cast<const int *>(tables + g.t_root);
     const int sb = pi.small_bytes;
-    SNT_CUDA_R(launch_sample_f<P>(km, g.nkeys, nodes, pi.sk_bytes, 2 * sb + pi.pk_bytes, st));
+    // g's first draw with f; the R/3 inversions run beside the whole forest
+    // and are joined at the end, before the fix-up of resampled keys
+    SNT_CUDA_R(launch_sample_f<P>(km, g.nkeys, nodes, pi.sk_bytes, 2 * sb + pi.pk_bytes, st, gbuf,
+                                  nullptr, nullptr, 0, fix_count));
     SNT_CUDA_R(cudaEventRecord(ev_fork, st));
     SNT_CUDA_R(cudaStreamWaitEvent(aux, ev_fork, 0));
     SNT_CUDA_R(launch_r3_keygen<P>(km, g.nkeys, gbuf, pi.sk_bytes, sb, nullptr, nullptr, 0,
-                                   ctx->d_err, aux, lanes));
+                                   ctx->d_err, aux, lanes, kpt, gfix, fix_count, fix_keys));
     SNT_CUDA_R(cudaEventRecord(ev_join, aux));
     for (int l = 1; l <= g.L; ++l) {
         LevelMap lm;
@@ -135,10 +142,12 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
             SNT_CUDA_R(launch_tree_down<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lm, n_par,
                                            nodes + (size_t)g.lev_off[l - 1] * pi.pad, st, split));
     }
-    SNT_CUDA_R(cudaStreamWaitEvent(st, ev_join, 0));
     SNT_CUDA_R(launch_finalize<P>(km, g.nkeys, gbuf, nodes, pi.pk_bytes, pi.sk_bytes, 2 * sb,
                                   pi.sched, st, mma));
     SNT_CUDA_R(launch_sha512_pk(km, g.nkeys, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
+    SNT_CUDA_R(cudaStreamWaitEvent(st, ev_join, 0));
+    SNT_CUDA_R(launch_fixup<P>(km, fix_count, fix_keys, gfix, nodes, pi.pk_bytes, pi.sk_bytes,
+                               2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st));
     return SNT_OK;
 }
 
@@ -179,6 +188,10 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         g.off_nodes = arena_off;
         arena_off += align_up(g.nodes * g.pi.pad * sizeof(int16_t), 256);
         g.off_g = arena_off;
+        arena_off += align_up((size_t)g.nkeys * g.pi.pad, 256);
+        g.off_fix = arena_off;
+        arena_off += align_up(sizeof(int) * (1 + (size_t)g.nkeys), 256);
+        g.off_gfix = arena_off;
         arena_off += align_up((size_t)g.nkeys * g.pi.pad, 256);
         const size_t nb = g.batch.size();
         g.t_desc = tbytes;
@@ -231,11 +244,13 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
     }
     RaggedGraph &rg = ctx->ragged;
     const int lanes = ctx->r3_lanes, split = ctx->tree_split, tiles = ctx->mma_tiles;
+    const int kpt = ctx->r3_kpt;
     const bool mma = ctx->rq_engine != 0;
     // the cached graph holds the kernel layouts: they are part of its key
     sig.push_back(lanes);
     sig.push_back(split);
     sig.push_back(mma ? tiles : 0);
+    sig.push_back(kpt);
     if (!(rg.exec && rg.sig == sig && rg.table_off == table_off)) {
         if (rg.exec) cudaGraphExecDestroy(rg.exec);
         rg.exec = nullptr;
@@ -248,9 +263,9 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
             const Group &g = groups[j];
             if (g.batch.empty()) continue;
             switch (g.P) {
-                case 653: s = launch_group<653>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles); break;
-                case 761: s = launch_group<761>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles); break;
-                default: s = launch_group<857>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles); break;
+                case 653: s = launch_group<653>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles, kpt); break;
+                case 761: s = launch_group<761>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles, kpt); break;
+                default: s = launch_group<857>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles, kpt); break;
             }
         }
         cudaGraph_t graph = nullptr;

@@ -1,5 +1,5 @@
-// sample.cu -- Short f sampling, the product-tree leaves 3f, Small_encode(f)
-// and rho, one CTA per key.
+// sample.cu -- Short f sampling, the product-tree leaves 3f, Small_encode(f),
+// rho and (optionally) the first draw of g, one CTA per key.
 //
 // Sec. 3.1 KeyGen step 3 / Algorithm 1 line "f <- Short": f has exactly w
 // nonzero coefficients, each +-1.  Reading of the uniform draw: p words of
@@ -19,9 +19,15 @@ namespace snt {
 // slots are in the same thread, closer than 128 in the same warp (shuffles),
 // farther ones in another warp (exchanged through shared memory, 6 of the 55
 // stages).
+// With g_out: also g's attempt-0 draw (the R/3 kernel's formula, stream 0,
+// or the injected test draw) as int8 rows of stride pad, so that h can be
+// formed before the R/3 inversions finish; and the resampling list's count
+// is reset for this call.
 template <int P>
 __global__ void __launch_bounds__(256)
-k_sample_f(KeyMap km, int nkeys, int16_t *__restrict__ leaves, int sk_bytes, int rho_off) {
+k_sample_f(KeyMap km, int nkeys, int16_t *__restrict__ leaves, int sk_bytes, int rho_off,
+           int8_t *__restrict__ g_out, const uint64_t *__restrict__ inj_idx,
+           const int8_t *__restrict__ inj_g, int n_inj, int *__restrict__ fix_count) {
     using G = Geo<P>;
     __shared__ __align__(16) uint32_t xs[1024];
     const int key = blockIdx.x;
@@ -51,6 +57,35 @@ k_sample_f(KeyMap km, int nkeys, int16_t *__restrict__ leaves, int sk_bytes, int
         skk[t] = (uint8_t)byte;
     }
 
+    if (g_out) {
+        __shared__ int inj;
+        if (t == 0) {
+            inj = -1;
+            for (int j = 0; j < n_inj; ++j)
+                if (inj_idx[j] == k) inj = j;
+            if (key == 0) *fix_count = 0;
+        }
+        __syncthreads();
+        int8_t *grow = g_out + (size_t)key * G::pad;
+        if (inj >= 0) {
+            for (int i = t; i < G::pad; i += blockDim.x)
+                grow[i] = (i < G::p) ? inj_g[(size_t)inj * G::p + i] : (int8_t)0;
+        } else {
+            // g_i = floor(3 (u_i mod 2^30) / 2^30) - 1 for word u_i of stream 0, attempt 0
+            for (int blk = t; 4 * blk < G::pad; blk += blockDim.x) {
+                uint32_t r[4];
+                rand_block(seed, k, STREAM_G, 0u, (uint32_t)blk, r);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = 4 * blk + j;
+                    grow[i] = (i < G::p)
+                        ? (int8_t)((int)(((unsigned long long)(r[j] & 0x3fffffffu) * 3u) >> 30) - 1)
+                        : (int8_t)0;
+                }
+            }
+        }
+    }
+
     // rho: small_bytes bytes of stream 2, little-endian within each word
     for (int blk = t; 16 * blk < G::small_bytes; blk += blockDim.x) {
         uint32_t r[4];
@@ -65,13 +100,20 @@ k_sample_f(KeyMap km, int nkeys, int16_t *__restrict__ leaves, int sk_bytes, int
 
 template <int P>
 cudaError_t launch_sample_f(const KeyMap &km, int nkeys, int16_t *leaves, int sk_bytes,
-                            int rho_off, cudaStream_t st) {
-    k_sample_f<P><<<nkeys, 256, 0, st>>>(km, nkeys, leaves, sk_bytes, rho_off);
+                            int rho_off, cudaStream_t st, int8_t *g_out,
+                            const uint64_t *inj_idx, const int8_t *inj_g, int n_inj,
+                            int *fix_count) {
+    k_sample_f<P><<<nkeys, 256, 0, st>>>(km, nkeys, leaves, sk_bytes, rho_off, g_out, inj_idx,
+                                         inj_g, n_inj, fix_count);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_sample_f<653>(const KeyMap &, int, int16_t *, int, int, cudaStream_t);
-template cudaError_t launch_sample_f<761>(const KeyMap &, int, int16_t *, int, int, cudaStream_t);
-template cudaError_t launch_sample_f<857>(const KeyMap &, int, int16_t *, int, int, cudaStream_t);
+#define SNT_SAMPLE_INST(P)                                                                  \
+    template cudaError_t launch_sample_f<P>(const KeyMap &, int, int16_t *, int, int,       \
+                                            cudaStream_t, int8_t *, const uint64_t *,       \
+                                            const int8_t *, int, int *);
+SNT_SAMPLE_INST(653)
+SNT_SAMPLE_INST(761)
+SNT_SAMPLE_INST(857)
 
 }  // namespace snt

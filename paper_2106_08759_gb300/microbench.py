@@ -109,12 +109,15 @@ def main():
     if args.sweep:
         default_lanes = ctx.get_option(snt.SNT_OPT_R3_LANES)
         for lanes in (4, 8, 32):
-            ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
-            out["r3_inv_4096_lanes%d_ms" % lanes] = timeit(
-                lambda: snt.snt_r3_inv(ctx, P, 4096, G4, O, OK))
-            out["r3_inv_%d_lanes%d_ms" % (m, lanes)] = timeit(
-                lambda: snt.snt_r3_inv(ctx, P, m, G, O, OK))
+            for kpt in (1, 2):
+                ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
+                ctx.set_option(snt.SNT_OPT_R3_KPT, kpt)
+                out["r3_inv_4096_lanes%d_kpt%d_ms" % (lanes, kpt)] = timeit(
+                    lambda: snt.snt_r3_inv(ctx, P, 4096, G4, O, OK))
+                out["r3_inv_%d_lanes%d_kpt%d_ms" % (m, lanes, kpt)] = timeit(
+                    lambda: snt.snt_r3_inv(ctx, P, m, G, O, OK))
         ctx.set_option(snt.SNT_OPT_R3_LANES, default_lanes)
+        ctx.set_option(snt.SNT_OPT_R3_KPT, 1)
 
     k = 1 << 10
     X = t(rq_uniform(P, k, 6).ravel(), torch.int16)
@@ -160,11 +163,17 @@ def main():
         ctx.set_option(snt.SNT_OPT_TREE_SPLIT, 8)
         for overlap in (0, 1, 2):
             ctx.set_option(snt.SNT_OPT_R3_OVERLAP, overlap)
-            for tiles in (1, 2, 3):
-                ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
-                ctx.set_option(snt.SNT_OPT_MMA_TILES, tiles)
-                sweep["mma_tiles%d_overlap%d" % (tiles, overlap)] = run_keygen_avg()
+            for tiles in (1, 2):
+                for lanes, kpt in ((4, 1), (4, 2), (8, 1), (8, 2)):
+                    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
+                    ctx.set_option(snt.SNT_OPT_MMA_TILES, tiles)
+                    ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
+                    ctx.set_option(snt.SNT_OPT_R3_KPT, kpt)
+                    sweep["mma_tiles%d_overlap%d_lanes%d_kpt%d" % (tiles, overlap, lanes, kpt)] = \
+                        run_keygen_avg()
         ctx.set_option(snt.SNT_OPT_MMA_TILES, 1)
+        ctx.set_option(snt.SNT_OPT_R3_LANES, 4)
+        ctx.set_option(snt.SNT_OPT_R3_KPT, 1)
         ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 0)
         for narrow in (0, 1):
             for overlap in (0, 1, 2):

@@ -96,9 +96,9 @@ def _non_invertible(p, rng):
     return np.where(g == 2, -1, g)
 
 
-@pytest.mark.parametrize("lanes", [4, 8, 32])
+@pytest.mark.parametrize("lanes,kpt", [(4, 1), (8, 1), (32, 1), (4, 2), (8, 2), (32, 2)])
 @pytest.mark.parametrize("P", [653, 761, 857])
-def test_r3_inv_matches_oracle(snt, ctx, P, lanes):
+def test_r3_inv_matches_oracle(snt, ctx, P, lanes, kpt):
     import torch
     p = P
     rng = np.random.default_rng(P + 2)
@@ -111,10 +111,12 @@ def test_r3_inv_matches_oracle(snt, ctx, P, lanes):
     out = torch.empty(n * p, dtype=torch.int8, device="cuda")
     ok = torch.empty(n, dtype=torch.int32, device="cuda")
     ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
+    ctx.set_option(snt.SNT_OPT_R3_KPT, kpt)  # 2: two elements per lane group, interleaved
     try:
         snt.snt_r3_inv(ctx, P, n, _t(g.ravel(), torch.int8), out, ok)
     finally:
         ctx.set_option(snt.SNT_OPT_R3_LANES, 4)
+        ctx.set_option(snt.SNT_OPT_R3_KPT, 1)
     got = out.cpu().numpy().reshape(n, p)
     okh = ok.cpu().numpy()
     assert okh[2] == 0 and okh[0] == 0

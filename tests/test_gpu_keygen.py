@@ -93,6 +93,28 @@ def test_output_split_narrow_levels_give_the_same_keys(snt, ctx, B):
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
 
 
+@pytest.mark.parametrize("lanes,kpt", [(4, 2), (8, 2), (32, 2)])
+def test_r3_two_elements_per_lane_group_give_the_same_keys(snt, ctx, lanes, kpt):
+    # R/3 kernel with two interleaved elements per lane group (ragged B, an
+    # injected zero divisor that forces a second attempt for one element of
+    # a pair while the other is done)
+    bad = _non_invertible_g()
+    ref = gpu_keygen(snt, ctx, 761, 12, 100, 45)
+    ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
+    ctx.set_option(snt.SNT_OPT_R3_KPT, kpt)
+    try:
+        got = gpu_keygen(snt, ctx, 761, 12, 100, 45)
+        snt.snt_debug_inject_g(ctx, 761, [107], np.stack([bad]))
+        inj = gpu_keygen(snt, ctx, 761, 12, 100, 45)
+    finally:
+        snt.snt_debug_inject_g(ctx, 761, [], np.zeros((0, 761), np.int8))
+        ctx.set_option(snt.SNT_OPT_R3_LANES, 4)
+        ctx.set_option(snt.SNT_OPT_R3_KPT, 1)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    rpk, rsk = oracle.keygen_batch(761, 12, 100, 45, g_inject={7: bad})
+    assert first_mismatch(inj[0], rpk) is None and first_mismatch(inj[1], rsk) is None
+
+
 @pytest.mark.parametrize("tiles", [1, 2, 3])
 @pytest.mark.parametrize("P,B", [(761, 300), (653, 77), (857, 130)])
 def test_tensor_core_engine_gives_the_same_keys(snt, ctx, P, B, tiles):
