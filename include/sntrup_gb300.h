@@ -280,7 +280,26 @@ typedef enum {
     SNT_OPT_MMA_TILES = 6,
     /* elements each lane group of the R/3 kernel runs at once, 1 or 2 (two
      * independent divstep chains per lane, sharing the shuffles) */
-    SNT_OPT_R3_KPT = 7
+    SNT_OPT_R3_KPT = 7,
+    /* tensor-core engine: at most this many warps share one tile's sum on
+     * narrow tree levels (1, 2 or 4; 2 from 256 products down, 4 from 64) */
+    SNT_OPT_MMA_KSPLIT = 8,
+    /* Montgomery's trick over a forest: at most this many equal subtrees
+     * (powers of two, 1 .. 1024), each with its own root inversion, all roots
+     * inverted in one launch; the tree's narrowest, latency-bound levels are
+     * traded for parallel root inversions.  The count used is the largest
+     * power of two not above the value that divides B (same bytes for any
+     * choice: inverses are unique). */
+    SNT_OPT_ROOTS = 9,
+    /* R/3 inverses of g: 0 per key by bit-sliced divsteps (which also decide
+     * invertibility); 1 the paper's batch path (Sec. 3.1.1): every g is
+     * tested invertible by its remainders modulo the irreducible factors of
+     * x^p - x - 1 over F_3 (and redrawn until it is), then all are inverted
+     * with Montgomery's trick in R/3 (tensor-core product forest, one
+     * jump-divstep inversion per subtree); 2 the same forest on the first
+     * draws at once, invertibility read off each subtree's root (a product
+     * is invertible iff every factor is), a failed subtree redone per key */
+    SNT_OPT_R3_MODE = 10
 } snt_option;
 
 snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);
@@ -294,7 +313,11 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
  * P and ceil(log2 B); it overrides the snt_ctx_set_option values there.
  * Synchronous; uses the context's scratch (B must fit the budget).  The R/3
  * kernel's elements per lane group (1, 2) are searched too.
- * choice (optional, 6 ints): lanes, split, overlap, engine, tiles, kpt. */
+ * Forests of 1, 4, 16 or 64 subtrees (SNT_OPT_ROOTS) are searched with the
+ * tensor-core engine.
+ * The R/3 mode (per key or batch) is searched too.
+ * choice (optional, 8 ints): lanes, split, overlap, engine, tiles, kpt, roots,
+ * r3 mode. */
 snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice);
 
 /* snt_autotune_ex returning lanes, split and overlap only. */

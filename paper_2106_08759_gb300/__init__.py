@@ -22,7 +22,8 @@ PARAMS = {653: (653, 4621, 288), 761: (761, 4591, 286), 857: (857, 5167, 322)}
 
 # tuning options (snt_option)
 SNT_OPT_R3_LANES, SNT_OPT_TREE_SPLIT, SNT_OPT_R3_OVERLAP, SNT_OPT_NARROW_SEG = 1, 2, 3, 4
-SNT_OPT_RQ_ENGINE, SNT_OPT_MMA_TILES, SNT_OPT_R3_KPT = 5, 6, 7
+SNT_OPT_RQ_ENGINE, SNT_OPT_MMA_TILES, SNT_OPT_R3_KPT, SNT_OPT_MMA_KSPLIT = 5, 6, 7, 8
+SNT_OPT_ROOTS, SNT_OPT_R3_MODE = 9, 10
 
 # phase names of snt_ctx_phase_times (SNT_NPHASES entries)
 PHASES = ("sample_f", "r3_inv", "tree_up", "root_inv", "tree_down", "h_encode", "sha512",
@@ -191,10 +192,10 @@ class Context:
 
     def autotune(self, P, B):
         """Pick the fastest kernel layouts for (P, B) on this GPU; returns them."""
-        c = (ctypes.c_int * 6)()
+        c = (ctypes.c_int * 8)()
         _check(load().snt_autotune_ex(self.handle, P, B, c))
         return {"r3_lanes": c[0], "tree_split": c[1], "r3_overlap": c[2], "rq_engine": c[3],
-                "mma_tiles": c[4], "r3_kpt": c[5]}
+                "mma_tiles": c[4], "r3_kpt": c[5], "roots": c[6], "r3_mode": c[7]}
 
     def set_timing(self, on=True):
         _check(load().snt_ctx_set_timing(self.handle, 1 if on else 0))

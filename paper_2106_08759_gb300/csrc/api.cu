@@ -60,9 +60,9 @@ template <int P>
 snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t first, size_t B,
                       uint8_t *pk, uint8_t *sk, cudaStream_t st, bool batched, uint8_t *arena,
                       bool inline_stream = false) {
-    const Tree t = make_tree(B);
+    const Tree tb = make_tree(B);  // the scratch layout (any forest of B fits its rows)
     int16_t *nodes = reinterpret_cast<int16_t *>(arena);
-    int8_t *gbuf = reinterpret_cast<int8_t *>(arena + align256(t.total * pi.pad * sizeof(int16_t)));
+    int8_t *gbuf = reinterpret_cast<int8_t *>(arena + align256(tb.total * pi.pad * sizeof(int16_t)));
     int16_t *leaves = nodes;
     const int16_t *inv_leaves = leaves;  // 1/(3f) of every key, for h
     // two ping-pong level buffers after the rest of the scratch
@@ -93,12 +93,30 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     int mode = ctx->r3_overlap, lanes = ctx->r3_lanes, split = ctx->tree_split;
     const bool narrow = ctx->narrow_seg != 0;
     bool mma = ctx->rq_engine != 0;
-    int mma_tiles = ctx->mma_tiles, kpt = ctx->r3_kpt;
+    int mma_tiles = ctx->mma_tiles, kpt = ctx->r3_kpt, roots = ctx->roots, r3mode = ctx->r3_mode;
     const snt_ctx::Tuned &tu = ctx->tuned[pidx(P)][bbucket(B)];
     if (tu.lanes) {
         mode = tu.overlap; lanes = tu.lanes; split = tu.split;
-        mma = tu.engine != 0; mma_tiles = tu.tiles; kpt = tu.kpt;
+        mma = tu.engine != 0; mma_tiles = tu.tiles; kpt = tu.kpt; roots = tu.roots;
+        r3mode = tu.r3mode;
     }
+    // R/3 batch inversion (the per-key path keeps per-key divsteps):
+    //   mode 1 (Sec. 3.1.1): isInvertible per key (redrawing g until it is),
+    //          then one Montgomery forest in R/3; h waits for the final g's;
+    //   mode 2: the forest on the first draws right away; a subtree whose
+    //          root does not invert (some g in it is a zero divisor, about
+    //          3^-19 per key) goes to the deferred per-key kernel, which redraws
+    //          and lists those keys for the fix-up.
+    const bool r3chk = batched && r3mode == 1, r3opt = batched && r3mode == 2;
+    const bool r3tree = r3chk || r3opt;
+    R3Factors fac;
+    if (r3chk) {
+        const snt_status sf = r3_factors_for(ctx, P, fac);
+        if (sf != SNT_OK) return sf;
+    }
+    int16_t *nodes3 = reinterpret_cast<int16_t *>(arena + r3_offset(pi, B));
+    int32_t *r3ok = reinterpret_cast<int32_t *>(arena + r3_offset(pi, B) + r3_scratch(pi, B) -
+                                                kR3OkBytes);
     if (inline_stream) {
         mode = 0;  // everything in order on the caller's stream
     } else {
@@ -109,9 +127,41 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     const int n_inj = (ctx->inj_P == P) ? ctx->n_inj : 0;
     auto launch_r3 = [&](cudaStream_t r3s) -> snt_status {
         if (tm) SNT_CUDA(cudaEventRecord(ev[2], r3s));
-        SNT_CUDA(launch_r3_keygen<P>(km, Bi, gbuf, pi.sk_bytes, sb, ctx->d_inj_idx, ctx->d_inj_g,
-                                     n_inj, ctx->d_err, r3s, lanes, kpt, gfix, fix_count,
-                                     fix_keys));
+        if (r3tree) {
+            if (r3chk) {
+                // every g checked (and redrawn) first: h may use gbuf after this
+                SNT_CUDA(launch_r3_check<P>(km, Bi, gbuf, nodes3, fac, ctx->d_err, r3s));
+                SNT_CUDA(cudaEventRecord(ctx->ev_gready, r3s));
+            }
+            const Forest f3 = make_forest(B, roots);
+            const int sub3 = (int)(B / f3.K);
+            const Tree &t3 = f3.t;
+            const int L3 = (int)t3.n.size() - 1;
+            for (int l = 1; l <= L3; ++l)
+                SNT_CUDA(launch_tree_up_mma3<P>(nodes3 + (size_t)t3.off[l - 1] * pi.pad,
+                                                equal_subtrees(f3.sub[l - 1], f3.sub[l]), t3.n[l],
+                                                nodes3 + (size_t)t3.off[l] * pi.pad, r3s,
+                                                ctx->mma_ksplit));
+            int16_t *root3 = nodes3 + (size_t)t3.off[L3] * pi.pad;
+            SNT_CUDA(launch_r3_inv_jump<P>(f3.K, root3, pi.pad, root3, pi.pad,
+                                           r3opt ? r3ok : nullptr, r3opt ? nullptr : ctx->d_err,
+                                           ERR_ROOT, r3s));
+            for (int l = L3; l >= 1; --l)
+                SNT_CUDA(launch_tree_down_mma3<P>(nodes3 + (size_t)t3.off[l] * pi.pad,
+                                                  equal_subtrees(f3.sub[l - 1], f3.sub[l]),
+                                                  t3.n[l], nodes3 + (size_t)t3.off[l - 1] * pi.pad,
+                                                  r3s, ctx->mma_ksplit));
+            SNT_CUDA(launch_r3_encode_v<P>(km, Bi, nodes3, pi.sk_bytes, sb, r3s,
+                                           r3opt ? r3ok : nullptr, sub3));
+            if (r3opt)  // subtrees whose root did not invert: per key, with redraws
+                SNT_CUDA(launch_r3_keygen<P>(km, Bi, gbuf, pi.sk_bytes, sb, ctx->d_inj_idx,
+                                             ctx->d_inj_g, n_inj, ctx->d_err, r3s, lanes, kpt,
+                                             gfix, fix_count, fix_keys, r3ok, sub3));
+        } else {
+            SNT_CUDA(launch_r3_keygen<P>(km, Bi, gbuf, pi.sk_bytes, sb, ctx->d_inj_idx,
+                                         ctx->d_inj_g, n_inj, ctx->d_err, r3s, lanes, kpt, gfix,
+                                         fix_count, fix_keys));
+        }
         if (tm) SNT_CUDA(cudaEventRecord(ev[3], r3s));
         return SNT_OK;
     };
@@ -126,7 +176,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     bool forked = false, joined = false;
     if (tm) SNT_CUDA(cudaEventRecord(ev[0], st));
     SNT_CUDA(launch_sample_f<P>(km, Bi, leaves, pi.sk_bytes, 2 * sb + pi.pk_bytes, st, gbuf,
-                                ctx->d_inj_idx, ctx->d_inj_g, n_inj, fix_count));
+                                ctx->d_inj_idx, ctx->d_inj_g, n_inj, fix_count,
+                                r3opt ? nodes3 : nullptr));
     if (tm) SNT_CUDA(cudaEventRecord(ev[1], st));
     if (mode == 0) {
         const snt_status s3 = launch_r3(st);
@@ -139,6 +190,11 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     }
     constexpr int kNarrow = 256;
     if (batched) {
+        // K equal subtrees (K = 1: one tree); level l of subtree b is the
+        // contiguous block of fo.sub[l] rows at t.off[l] + b * fo.sub[l]
+        const Forest fo = make_forest(B, roots);
+        const Tree &t = fo.t;
+        auto lmap = [&](int l) { return equal_subtrees(fo.sub[l - 1], fo.sub[l]); };
         const int L = (int)t.n.size() - 1;
         for (int l = 1; l <= L; ++l) {
             if (!forked && t.n[l] < kNarrow) {
@@ -148,16 +204,16 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
             }
             if (mma)
                 SNT_CUDA(launch_tree_up_mma<P>(nodes + (size_t)t.off[l - 1] * pi.pad,
-                                               single_tree(t.n[l - 1]), t.n[l],
+                                               lmap(l), t.n[l],
                                                nodes + (size_t)t.off[l] * pi.pad, st, mma_tiles,
-                                               l == 1));
+                                               l == 1, ctx->mma_ksplit));
             else if (narrow && t.n[l] <= kSegMaxNodes)
                 SNT_CUDA(launch_tree_up_seg<P>(nodes + (size_t)t.off[l - 1] * pi.pad,
-                                               single_tree(t.n[l - 1]), t.n[l],
+                                               lmap(l), t.n[l],
                                                nodes + (size_t)t.off[l] * pi.pad, st));
             else
                 SNT_CUDA(launch_tree_up<P>(nodes + (size_t)t.off[l - 1] * pi.pad,
-                                           single_tree(t.n[l - 1]), t.n[l],
+                                           lmap(l), t.n[l],
                                            nodes + (size_t)t.off[l] * pi.pad, st, split));
         }
         if (!forked) {
@@ -167,8 +223,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         }
         if (tm) SNT_CUDA(cudaEventRecord(ev[4], st));
         int16_t *root = nodes + (size_t)t.off[L] * pi.pad;
-        SNT_CUDA(launch_rq_inv_jump<P>(1, root, pi.pad, root, pi.pad, nullptr, ctx->d_err, ERR_ROOT,
-                                       st));
+        SNT_CUDA(launch_rq_inv_jump<P>(fo.K, root, pi.pad, root, pi.pad, nullptr, ctx->d_err,
+                                       ERR_ROOT, st));
         if (tm) SNT_CUDA(cudaEventRecord(ev[5], st));
         // Inverses of level l live at par: in place over the level's
         // products, or, after an output-split level, in one of the two
@@ -178,16 +234,16 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         for (int l = L; l >= 1; --l) {
             int16_t *lch = nodes + (size_t)t.off[l - 1] * pi.pad;
             if (mma) {  // in place on every level
-                SNT_CUDA(launch_tree_down_mma<P>(par, single_tree(t.n[l - 1]), t.n[l], lch, st,
-                                                 mma_tiles, l == 1));
+                SNT_CUDA(launch_tree_down_mma<P>(par, lmap(l), t.n[l], lch, st,
+                                                 mma_tiles, l == 1, ctx->mma_ksplit));
                 par = lch;
             } else if (narrow && t.n[l] <= kSegMaxNodes) {
                 int16_t *out = pp[ping];
                 ping ^= 1;
-                SNT_CUDA(launch_tree_down_seg<P>(par, single_tree(t.n[l - 1]), t.n[l], lch, out, st));
+                SNT_CUDA(launch_tree_down_seg<P>(par, lmap(l), t.n[l], lch, out, st));
                 par = out;
             } else {
-                SNT_CUDA(launch_tree_down<P>(par, single_tree(t.n[l - 1]), t.n[l], lch, st, split));
+                SNT_CUDA(launch_tree_down<P>(par, lmap(l), t.n[l], lch, st, split));
                 par = lch;
             }
         }
@@ -202,6 +258,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
             SNT_CUDA(cudaEventRecord(ev[6], st));
         }
     }
+    if (r3chk && !joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_gready, 0));  // final g's
     if (tm) SNT_CUDA(cudaEventRecord(ev[7], st));
     SNT_CUDA(launch_finalize<P>(km, Bi, gbuf, inv_leaves, pi.pk_bytes, pi.sk_bytes, 2 * sb,
                                 pi.sched, st, mma));
@@ -209,8 +266,9 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     SNT_CUDA(launch_sha512_pk(km, Bi, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[9], st));
     if (!joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
-    SNT_CUDA(launch_fixup<P>(km, fix_count, fix_keys, gfix, inv_leaves, pi.pk_bytes, pi.sk_bytes,
-                             2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st));
+    if (!r3chk)  // keys whose g was redrawn by the deferred per-key R/3 kernel
+        SNT_CUDA(launch_fixup<P>(km, fix_count, fix_keys, gfix, inv_leaves, pi.pk_bytes,
+                                 pi.sk_bytes, 2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[10], st));
     if (!inline_stream) {  // join back into the caller's stream
         SNT_CUDA(cudaEventRecord(ctx->ev_done, st));
@@ -304,6 +362,7 @@ snt_status snt_ctx_create(int device, size_t mem_budget, snt_ctx **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->tune, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_r3fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_gready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     for (int i = 0; i < kPhaseEvents && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev_phase[i]);
@@ -334,6 +393,9 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
     if (ctx->ev_r3fork) cudaEventDestroy(ctx->ev_r3fork);
+    if (ctx->ev_gready) cudaEventDestroy(ctx->ev_gready);
+    for (uint32_t *f : ctx->d_r3fac)
+        if (f) cudaFree(f);
     if (ctx->ragged.exec) cudaGraphExecDestroy(ctx->ragged.exec);
     if (ctx->tree) cudaStreamDestroy(ctx->tree);
     if (ctx->tune) cudaStreamDestroy(ctx->tune);
@@ -549,6 +611,19 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             if (value != 1 && value != 2) return set_error(SNT_EINVAL, "R/3 elements per lane group is 1 or 2");
             ctx->r3_kpt = value;
             return SNT_OK;
+        case SNT_OPT_MMA_KSPLIT:
+            if (value != 1 && value != 2 && value != 4) return set_error(SNT_EINVAL, "K-split is 1, 2 or 4");
+            ctx->mma_ksplit = value;
+            return SNT_OK;
+        case SNT_OPT_ROOTS:
+            if (value < 1 || value > 1024 || (value & (value - 1)))
+                return set_error(SNT_EINVAL, "roots per batch is a power of two in [1, 1024]");
+            ctx->roots = value;
+            return SNT_OK;
+        case SNT_OPT_R3_MODE:
+            if (value < 0 || value > 2) return set_error(SNT_EINVAL, "R/3 mode is 0, 1 or 2");
+            ctx->r3_mode = value;
+            return SNT_OK;
         default:
             return set_error(SNT_EINVAL, "unknown option %d", option);
     }
@@ -564,6 +639,9 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
         case SNT_OPT_RQ_ENGINE: *value = ctx->rq_engine; return SNT_OK;
         case SNT_OPT_MMA_TILES: *value = ctx->mma_tiles; return SNT_OK;
         case SNT_OPT_R3_KPT: *value = ctx->r3_kpt; return SNT_OK;
+        case SNT_OPT_MMA_KSPLIT: *value = ctx->mma_ksplit; return SNT_OK;
+        case SNT_OPT_ROOTS: *value = ctx->roots; return SNT_OK;
+        case SNT_OPT_R3_MODE: *value = ctx->r3_mode; return SNT_OK;
         default: return set_error(SNT_EINVAL, "unknown option %d", option);
     }
 }
@@ -590,12 +668,16 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
     for (int la : {4, 8, 32})
         for (int kp : {1}) {  // two elements per lane group measured slower at every size
             for (int ov : {0, 1, 2}) {
-                for (int ti : {1, 2}) {
-                    snt_ctx::Tuned c;
-                    c.lanes = la; c.kpt = kp; c.overlap = ov; c.engine = 1; c.tiles = ti;
-                    c.split = ctx->tree_split;
-                    cands.push_back(c);
-                }
+                for (int ti : {1, 2})
+                    for (int rt : {1, 4, 16, 64})
+                        for (int r3m : {0, 1, 2}) {
+                            if (rt > 1 && (la == 32 || ti == 2)) continue;
+                            if (r3m == 1 && (la != 4 || ti == 2)) continue;  // lanes: per-key only
+                            snt_ctx::Tuned c;
+                            c.lanes = la; c.kpt = kp; c.overlap = ov; c.engine = 1; c.tiles = ti;
+                            c.roots = rt; c.r3mode = r3m; c.split = ctx->tree_split;
+                            cands.push_back(c);
+                        }
                 for (int sp : {4, 8}) {
                     snt_ctx::Tuned c;
                     c.lanes = la; c.kpt = kp; c.overlap = ov; c.engine = 0; c.tiles = 1; c.split = sp;
@@ -636,13 +718,15 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
         choice[3] = best.engine;
         choice[4] = best.tiles;
         choice[5] = best.kpt;
+        choice[6] = best.roots;
+        choice[7] = best.r3mode;
     }
     return snt_ctx_sync(ctx, ts);
 }
 
 snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *split_out,
                         int *overlap_out) {
-    int c[6] = {0, 0, 0, 0, 0, 0};
+    int c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const snt_status st = snt_autotune_ex(ctx, P, B, c);
     if (st != SNT_OK) return st;
     if (lanes_out) *lanes_out = c[0];

@@ -116,4 +116,21 @@ __device__ __forceinline__ int level_batch(const int *pre, int nb, int j) {
     return lo;
 }
 
+// Node j of a level: its index in its own tree (idx), the first child row of
+// that tree in the input level (base) and the tree's input count (n_in).
+__device__ __forceinline__ void lm_node(const LevelMap &lm, int j, int &idx, int &base,
+                                        int &n_in) {
+    idx = j; base = 0; n_in = lm.n_in;
+    if (lm.nb > 0) {
+        const int b = level_batch(lm.pre_out, lm.nb, j);
+        idx = j - lm.pre_out[b];
+        base = lm.pre_in[b];
+        n_in = lm.pre_in[b + 1] - base;
+    } else if (lm.sub_out > 0) {
+        const int b = j / lm.sub_out;
+        idx = j - b * lm.sub_out;
+        base = b * lm.n_in;
+    }
+}
+
 }  // namespace snt

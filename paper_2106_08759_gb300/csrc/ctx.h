@@ -40,6 +40,8 @@ struct snt_ctx {
     cudaStream_t aux = nullptr;   // low priority: per-key R/3 inversions
     cudaStream_t tree = nullptr;  // high priority: sampling, product tree, h, hash
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr, ev_r3fork = nullptr;
+    cudaEvent_t ev_gready = nullptr;       // R/3 batch path: every g final
+    uint32_t *d_r3fac[3] = {nullptr, nullptr, nullptr};  // F_3 factors per parameter set
     bool timing = false;
     cudaEvent_t ev_phase[snt::kPhaseEvents] = {};
     int r3_lanes = snt::kDefaultR3Lanes;
@@ -49,8 +51,13 @@ struct snt_ctx {
     int rq_engine = snt::kDefaultRqEngine;
     int mma_tiles = snt::kDefaultMmaTiles;
     int r3_kpt = snt::kDefaultR3Kpt;
+    int mma_ksplit = snt::kDefaultMmaKsplit;
+    int roots = snt::kDefaultRoots;
+    int r3_mode = snt::kDefaultR3Mode;
     // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
-    struct Tuned { int lanes = 0, split = 0, overlap = 0, engine = 0, tiles = 1, kpt = 1; };
+    struct Tuned {
+        int lanes = 0, split = 0, overlap = 0, engine = 0, tiles = 1, kpt = 1, roots = 1, r3mode = 0;
+    };
     Tuned tuned[3][25];
     cudaStream_t tune = nullptr;  // stream used while autotuning
     snt::RaggedGraph ragged;      // last ragged plan and its graph
@@ -64,4 +71,7 @@ inline int bbucket(size_t B) {
     while (((size_t)1 << b) < B && b < 24) ++b;
     return b;
 }
+// Device copy of the F_3 factors of x^P - x - 1 for the R/3 batch path
+// (computed on the host on first use; r3batch.cu).
+snt_status r3_factors_for(snt_ctx *ctx, int P, R3Factors &out);
 }  // namespace snt

@@ -21,6 +21,9 @@ constexpr int kDefaultNarrowSeg = 1;   // output-split narrow tree levels
 constexpr int kDefaultRqEngine = 1;    // R/q products on the tensor cores
 constexpr int kDefaultMmaTiles = 1;    // MMA tiles per warp
 constexpr int kDefaultR3Kpt = 1;       // R/3 elements per lane group
+constexpr int kDefaultMmaKsplit = 4;   // K-split of narrow tensor-core levels
+constexpr int kDefaultRoots = 1;       // subtrees (root inversions) per batch
+constexpr int kDefaultR3Mode = 0;      // 0 per-key R/3 divsteps, 1 R/3 batch inversion
 
 // Records a one-line error message (snt_last_error_string) and returns s.
 snt_status set_error(snt_status s, const char *fmt, ...);
@@ -118,6 +121,37 @@ inline Tree make_tree(size_t B) {
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// A batch as K equal subtrees side by side (Montgomery's trick per subtree,
+// K root inversions in one launch): K is the largest power of two <= k_req
+// that divides B and whose forest fits the single tree's node rows.  n[l]
+// and off[l] count the whole level; sub[l] nodes of it belong to each
+// subtree.  K = 1 is the single tree.
+struct Forest {
+    int K = 1;
+    Tree t;
+    std::vector<int> sub;
+};
+
+inline Forest make_forest(size_t B, int k_req) {
+    const size_t single = make_tree(B).total;
+    int K = 1;
+    while (2 * K <= k_req && B % (size_t)(2 * K) == 0 &&
+           (size_t)(2 * K) * make_tree(B / (2 * K)).total <= single)
+        K *= 2;
+    Forest f;
+    f.K = K;
+    const Tree s = make_tree(B / K);
+    size_t off = 0;
+    for (size_t l = 0; l < s.n.size(); ++l) {
+        f.sub.push_back(s.n[l]);
+        f.t.n.push_back(K * s.n[l]);
+        f.t.off.push_back((int)off);
+        off += (size_t)K * s.n[l];
+    }
+    f.t.total = off;
+    return f;
+}
+
 // Scratch bytes for one keygen call: every tree node (int16, stride pad) and
 // g (int8, stride pad) for each key; host_out adds device staging for pk/sk.
 inline size_t keygen_scratch(const ParamInfo &pi, size_t B, bool host_out) {
@@ -139,8 +173,15 @@ inline size_t fix_list_bytes(size_t B) { return align256(sizeof(int) * (1 + B));
 inline size_t fix_scratch(const ParamInfo &pi, size_t B) {
     return fix_list_bytes(B) + align256(B * pi.pad);
 }
+// ... then the R/3 batch inversion's tree (int16 rows, like the R/q tree)
+// and its subtree roots' invertibility flags.
+constexpr size_t kR3OkBytes = 4 * 1024;
+inline size_t r3_scratch(const ParamInfo &pi, size_t B) {
+    return align256(make_tree(B).total * pi.pad * sizeof(int16_t)) + kR3OkBytes;
+}
 inline size_t keygen_arena(const ParamInfo &pi, size_t B, bool host_out) {
-    return keygen_scratch(pi, B, host_out) + narrow_scratch(pi) + fix_scratch(pi, B);
+    return keygen_scratch(pi, B, host_out) + narrow_scratch(pi) + fix_scratch(pi, B) +
+           r3_scratch(pi, B);
 }
 // Arena layout of a context keygen call: tree nodes, g rows, the ping-pong
 // buffers, the resampling list, then (host-buffer calls) the pk and sk
@@ -148,8 +189,11 @@ inline size_t keygen_arena(const ParamInfo &pi, size_t B, bool host_out) {
 inline size_t fix_offset(const ParamInfo &pi, size_t B) {
     return keygen_scratch(pi, B, false) + narrow_scratch(pi);
 }
-inline size_t staging_offset(const ParamInfo &pi, size_t B) {
+inline size_t r3_offset(const ParamInfo &pi, size_t B) {
     return fix_offset(pi, B) + fix_scratch(pi, B);
+}
+inline size_t staging_offset(const ParamInfo &pi, size_t B) {
+    return r3_offset(pi, B) + r3_scratch(pi, B);
 }
 
 struct DeviceGuard {

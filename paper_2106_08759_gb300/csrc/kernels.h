@@ -34,9 +34,24 @@ struct KeyMap {
 // contiguous, batch b owning nodes [pre_out[b], pre_out[b+1]) of the level and
 // its children [pre_in[b], pre_in[b+1]) of the level below.  nb == 0: one
 // tree, n_in children (the arrays are unused).
+// Irreducible factors of x^p - x - 1 over F_3 for the invertibility test:
+// factor i has degree deg[i] and `words` 32-coefficient words per bit plane
+// (m: nonzero, then s: coefficient -1) at w + off[i].
+constexpr int kMaxR3Factors = 8;
+struct R3Factors {
+    int n = 0, total_words = 0;
+    int deg[kMaxR3Factors] = {}, words[kMaxR3Factors] = {}, off[kMaxR3Factors] = {};
+    const uint32_t *w = nullptr;
+};
+
+// Nodes of one tree level.  nb > 0: a forest of batches with per-level node
+// prefix sums (pre_in / pre_out, nb + 1 entries each).  Otherwise equal
+// subtrees side by side: sub_out nodes of this level per subtree, each with
+// n_in children (sub_out = 0 or the whole level: a single tree).
 struct LevelMap {
-    const int *pre_in, *pre_out;
-    int nb, n_in;
+    const int *pre_in = nullptr, *pre_out = nullptr;
+    int nb = 0, n_in = 0;
+    int sub_out = 0;
 };
 
 // Items of an encapsulation / decapsulation launch: a device table of items
@@ -83,25 +98,36 @@ inline KeyMap single_batch(uint64_t seed, uint64_t first, int B, uint8_t *pk, ui
 
 inline LevelMap single_tree(int n_in) {
     LevelMap lm;
-    lm.pre_in = nullptr; lm.pre_out = nullptr; lm.nb = 0; lm.n_in = n_in;
+    lm.pre_in = nullptr; lm.pre_out = nullptr; lm.nb = 0; lm.n_in = n_in; lm.sub_out = 0;
+    return lm;
+}
+// Level of a forest of equal subtrees: n_in children and sub_out nodes each.
+inline LevelMap equal_subtrees(int n_in, int sub_out) {
+    LevelMap lm = single_tree(n_in);
+    lm.sub_out = sub_out;
     return lm;
 }
 
 // g_out (optional): also g's attempt-0 draw per key (int8, stride pad), with
-// the injected test draws, and *fix_count = 0 (the resampling list).
+// the injected test draws, and *fix_count = 0 (the resampling list);
+// g16_out (optional): the same draw as int16 rows (leaves of the R/3 forest).
 template <int P>
 cudaError_t launch_sample_f(const KeyMap &km, int nkeys, int16_t *leaves, int sk_bytes,
                             int rho_off, cudaStream_t st, int8_t *g_out = nullptr,
                             const uint64_t *inj_idx = nullptr, const int8_t *inj_g = nullptr,
-                            int n_inj = 0, int *fix_count = nullptr);
+                            int n_inj = 0, int *fix_count = nullptr,
+                            int16_t *g16_out = nullptr);
 // gfix != null: deferred form (attempt 0 read from g_out, g_out untouched,
 // resampled keys appended to fix_keys / gfix rows, *fix_count of them).
+// sub_ok != null: fall-back form, only warps holding a key of a subtree
+// (sub_size keys each) whose flag is 0 do any work.
 template <int P>
 cudaError_t launch_r3_keygen(const KeyMap &km, int nkeys, int8_t *g_out, int sk_bytes,
                              int sk_off, const uint64_t *inj_idx, const int8_t *inj_g, int n_inj,
                              int *err, cudaStream_t st, int lanes, int kpt = 1,
                              int8_t *gfix = nullptr, int *fix_count = nullptr,
-                             int *fix_keys = nullptr);
+                             int *fix_keys = nullptr, const int *sub_ok = nullptr,
+                             int sub_size = 0);
 template <int P>
 cudaError_t launch_r3_inv(int n, const int8_t *g, int8_t *out, int32_t *ok, cudaStream_t st,
                           int lanes, int kpt = 1);
@@ -128,13 +154,21 @@ cudaError_t launch_mul_batch(int n, const int16_t *a, const int16_t *b, int16_t 
 // product (per parent in the down-sweep), `tiles` MMA tiles per warp.  The
 // down-sweep overwrites the children in place.
 // `leaves`: the level's inputs (up) or children (down) are the leaves 3f,
-// whose small coefficients need fewer limb products.
+// whose small coefficients need fewer limb products.  Levels of at most 256
+// (64) products split each product's sum over 2 (4) warps, up to kmax.
 template <int P>
 cudaError_t launch_tree_up_mma(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
-                               cudaStream_t st, int tiles, bool leaves);
+                               cudaStream_t st, int tiles, bool leaves, int kmax = 4);
 template <int P>
 cudaError_t launch_tree_down_mma(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t *lch,
-                                 cudaStream_t st, int tiles, bool leaves);
+                                 cudaStream_t st, int tiles, bool leaves, int kmax = 4);
+// R/3 trees for the batch inversion of the g's (coefficients mod 3).
+template <int P>
+cudaError_t launch_tree_up_mma3(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
+                                cudaStream_t st, int kmax);
+template <int P>
+cudaError_t launch_tree_down_mma3(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t *lch,
+                                  cudaStream_t st, int kmax);
 template <int P>
 cudaError_t launch_mul_batch_mma(int n, const int16_t *a, const int16_t *b, int16_t *c,
                                  cudaStream_t st);
@@ -146,6 +180,23 @@ template <int P>
 cudaError_t launch_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
                                cudaStream_t st, const int *idx = nullptr);
+// R/3 batch path (r3batch.cu): invertibility test and resampling of g (warp
+// per key; final g into the R/3 leaves, int16, and over a resampled gbuf
+// row), and Small_encode(1/g) into sk from the inverted leaves.
+template <int P>
+cudaError_t launch_r3_check(const KeyMap &km, int B, int8_t *gbuf, int16_t *leaves3,
+                            const R3Factors &fac, int *err, cudaStream_t st);
+template <int P>
+cudaError_t launch_r3_encode_v(const KeyMap &km, int B, const int16_t *v3, int sk_bytes,
+                               int sk_off, cudaStream_t st, const int *sub_ok = nullptr,
+                               int sub_size = 0);
+// Jump-divstep inversions in R/3 (entries mod 3, centred int16 rows); ok
+// (optional) receives 1 per invertible element; err (optional) gets err_bit
+// for a non-invertible one.
+template <int P>
+cudaError_t launch_r3_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
+                               long out_stride, int32_t *ok, int *err, int err_bit,
+                               cudaStream_t st);
 // Keys on the resampling list: h with the final g, pk, sk's copy and hash.
 template <int P>
 cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_keys,

@@ -109,9 +109,10 @@ __device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1
 }
 
 // E table value t in [0, 2p - 2], zero elsewhere; b centred in shared memory
-// (so a folded sum b_{t+1} + b_t needs at most one correction by q).
-template <int P> __device__ __forceinline__ int mma_E(const int16_t *b, int t) {
-    constexpr int p = Prm<P>::p, q = Prm<P>::q, h = (q - 1) / 2;
+// (so a folded sum b_{t+1} + b_t needs at most one correction by q).  Q is
+// the coefficient modulus: q for R/q, 3 for R/3.
+template <int P, int Q = Prm<P>::q> __device__ __forceinline__ int mma_E(const int16_t *b, int t) {
+    constexpr int p = Prm<P>::p, q = Q, h = (q - 1) / 2;
     if (t < 0 || t > 2 * p - 2) return 0;
     if (t >= p - 1) return b[t - p + 1];
     int v = (int)b[t + 1] + (int)b[t];
@@ -159,12 +160,12 @@ __device__ __forceinline__ void mma_fill_b(const int16_t *__restrict__ b, MmaE<P
 }
 
 // E side, step 2 (after a barrier): the limb pair table.
-template <int P, int NT, int MODE = MODE_GEN>
+template <int P, int NT, int MODE = MODE_GEN, int Q = Prm<P>::q>
 __device__ __forceinline__ void mma_fill_pe(MmaE<P, NT> &s, int tid, int nth) {
     using M = MmaGeo<P, NT>;
     for (int w = tid; w < M::PWN; w += nth) {
         const int x = w + M::XLO;
-        const int e0 = mma_E<P>(s.b, x), e1 = mma_E<P>(s.b, x - 1);
+        const int e0 = mma_E<P, Q>(s.b, x), e1 = mma_E<P, Q>(s.b, x - 1);
         if (MODE == MODE_SAE) {  // small E: the value is its own l limb
             s.t.pl[w] = h2_small(e0, e1);
             continue;
@@ -180,9 +181,12 @@ __device__ __forceinline__ void mma_fill_pe(MmaE<P, NT> &s, int tid, int nth) {
 // accumulates the limb sums of every (tile, product): P_hh, P_ll, P_ss
 // (MODE_GEN), P_1, P_2 (MODE_SA) or P (MODE_SAE).  A2 of step D + 1 is A1 of
 // step D (x advances by 16), so two table loads per step suffice.
+// ks / nks: this warp's share of the D range when a tile's sum is split over
+// nks warps (contiguous parts, reduced by mma_ksplit_reduce).
 template <int P, int NT, int NPR, int MODE = MODE_GEN>
 __device__ __forceinline__ void mma_tiles(const MmaE<P, NT> &E, const MmaA<P, NT> *const (&A)[NPR],
-                                          int T0, int lane, float (&acc)[NT][NPR][3][4]) {
+                                          int T0, int lane, float (&acc)[NT][NPR][3][4],
+                                          int ks = 0, int nks = 1) {
     using M = MmaGeo<P, NT>;
     const int g = lane >> 2, tig = lane & 3;
 #pragma unroll
@@ -193,8 +197,11 @@ __device__ __forceinline__ void mma_tiles(const MmaE<P, NT> &E, const MmaA<P, NT
             for (int m = 0; m < 3; ++m)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[tt][pr][m][c] = 0.f;
-    const int dlo = 8 * T0 - (M::NBLK - 1);
-    const int dhi = 8 * (T0 + NT - 1) + 7;
+    const int dall = 8 * T0 - (M::NBLK - 1);          // first D of the tiles
+    const int dn = 8 * (NT - 1) + 7 + M::NBLK;        // D values of the tiles
+    const int part = (dn + nks - 1) / nks;
+    const int dlo = dall + ks * part;
+    const int dhi = min(dall + dn, dlo + part) - 1;
     const int x0 = 16 * dlo + g - 2 * tig + M::p - 1 - M::XLO;  // table index at D = dlo
     int rec = 4 * (8 * T0 + g - dlo + M::PADB) + tig;            // B record of tile T0
     if (MODE == MODE_SAE) {
@@ -239,13 +246,35 @@ __device__ __forceinline__ void mma_tiles(const MmaE<P, NT> &E, const MmaA<P, NT
     }
 }
 
+// Sum of a K-split: warps with ks > 0 store their partial sums in red
+// (floats, (nks - 1) x nw x 32 lanes x NT*NPR*12, nw = warps per part), warps
+// with ks = 0 add them (exact: every partial sum is an integer below 2^24).
+// Contains a barrier: every thread of the CTA must call it.
+template <int NT, int NPR>
+__device__ __forceinline__ void mma_ksplit_reduce(float (&acc)[NT][NPR][3][4], float *red, int ks,
+                                                  int nks, int tw, int nw, int lane) {
+    constexpr int NV = NT * NPR * 12;
+    float *flat = &acc[0][0][0][0];
+    if (ks > 0) {
+        float *dst = red + ((size_t)((ks - 1) * nw + tw) * 32 + lane) * NV;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dst[v] = flat[v];
+    }
+    __syncthreads();
+    if (ks == 0)
+        for (int k = 1; k < nks; ++k) {
+            const float *src = red + ((size_t)((k - 1) * nw + tw) * 32 + lane) * NV;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) flat[v] += src[v];
+        }
+}
+
 // Row sums of tiles [T0, T0 + NT) of product pr into A.u.stage (centred).
 // The caller must have synchronised every warp reading A.u.v since the loop.
-template <int P, int NT, int NPR, int MODE = MODE_GEN>
+template <int P, int NT, int NPR, int MODE = MODE_GEN, int Q = Prm<P>::q>
 __device__ __forceinline__ void mma_stage(MmaA<P, NT> &A, int T0, int lane, int pr,
                                           const float (&acc)[NT][NPR][3][4]) {
     using M = MmaGeo<P, NT>;
-    constexpr int Q = M::q;
     const int g = lane >> 2, tig = lane & 3;
 #pragma unroll
     for (int tt = 0; tt < NT; ++tt)
@@ -267,11 +296,10 @@ __device__ __forceinline__ void mma_stage(MmaA<P, NT> &A, int T0, int lane, int 
 
 // Final outputs c_0 .. c_{nout-1} (centred int16, zero beyond p) from the
 // staged rows, by threads tid = 0 .. nth-1.
-template <int P, int NT>
+template <int P, int NT, int Q = Prm<P>::q>
 __device__ __forceinline__ void mma_finish(const MmaA<P, NT> &A, int blast,
                                            int16_t *__restrict__ c, int nout, int tid, int nth) {
     using M = MmaGeo<P, NT>;
-    constexpr int Q = M::q;
     for (int j = tid; j < nout; j += nth) {
         int v = 0;
         if (j == 0) v = cmod<Q>(A.u.stage[0] - A.u.stage[M::p - 1] + (int)A.a[0] * blast);

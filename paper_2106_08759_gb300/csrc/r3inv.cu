@@ -235,7 +235,8 @@ __global__ void __launch_bounds__(32 * R3Geo<P, LKT, KPT>::WARPS)
 k_r3_keygen(KeyMap km, int B, int8_t *__restrict__ g_out, int sk_bytes, int sk_off,
             const uint64_t *__restrict__ inj_idx, const int8_t *__restrict__ inj_g,
             int n_inj, int *__restrict__ err, int8_t *__restrict__ gfix,
-            int *__restrict__ fix_count, int *__restrict__ fix_keys) {
+            int *__restrict__ fix_count, int *__restrict__ fix_keys,
+            const int *__restrict__ sub_ok, int sub_size) {
     using Gm = Geo<P>;
     using RG = R3Geo<P, LKT, KPT>;
     constexpr int WL = RG::WL, LK = RG::LK, EPW = RG::EPW, GPW = RG::GPW;
@@ -244,6 +245,11 @@ k_r3_keygen(KeyMap km, int B, int8_t *__restrict__ g_out, int sk_bytes, int sk_o
     const int sub = lane & (LK - 1), grp = lane / LK;
     const int ebase = blockIdx.x * RG::EPB + warp * EPW;  // first element of this warp
     if (ebase >= B) return;                               // warp-uniform
+    if (sub_ok) {  // fall-back form: only warps with a key in a failed subtree
+        bool all_ok = true;
+        for (int e = ebase; e < min(ebase + EPW, B); ++e) all_ok = all_ok && sub_ok[e / sub_size] != 0;
+        if (all_ok) return;
+    }
     // this group's elements: warp slots grp + k GPW
     const bool deferred = gfix != nullptr;
     bool ok[KPT], first_ok[KPT];
@@ -422,10 +428,12 @@ k_r3_inv(int n, const int8_t *__restrict__ g, int8_t *__restrict__ out,
 template <int P, int LK, int KPT>
 cudaError_t launch_r3_keygen_lk(const KeyMap &km, int B, int8_t *g_out, int sk_bytes, int sk_off,
                                 const uint64_t *inj_idx, const int8_t *inj_g, int n_inj, int *err,
-                                cudaStream_t st, int8_t *gfix, int *fix_count, int *fix_keys) {
+                                cudaStream_t st, int8_t *gfix, int *fix_count, int *fix_keys,
+                                const int *sub_ok, int sub_size) {
     using RG = R3Geo<P, LK, KPT>;
     k_r3_keygen<P, LK, KPT><<<(B + RG::EPB - 1) / RG::EPB, 32 * RG::WARPS, 0, st>>>(
-        km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, gfix, fix_count, fix_keys);
+        km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, gfix, fix_count, fix_keys,
+        sub_ok, sub_size);
     return cudaGetLastError();
 }
 
@@ -433,10 +441,10 @@ template <int P>
 cudaError_t launch_r3_keygen(const KeyMap &km, int B, int8_t *g_out, int sk_bytes, int sk_off,
                              const uint64_t *inj_idx, const int8_t *inj_g, int n_inj, int *err,
                              cudaStream_t st, int lanes, int kpt, int8_t *gfix, int *fix_count,
-                             int *fix_keys) {
+                             int *fix_keys, const int *sub_ok, int sub_size) {
 #define SNT_R3K(LK, KP)                                                                     \
     launch_r3_keygen_lk<P, LK, KP>(km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st, \
-                                   gfix, fix_count, fix_keys)
+                                   gfix, fix_count, fix_keys, sub_ok, sub_size)
     if (kpt == 2) {
         switch (lanes) {
             case 4: return SNT_R3K(4, 2);
@@ -479,7 +487,8 @@ cudaError_t launch_r3_inv(int n, const int8_t *g, int8_t *out, int32_t *ok, cuda
 #define SNT_R3_INST(P)                                                                      \
     template cudaError_t launch_r3_keygen<P>(const KeyMap &, int, int8_t *, int, int,       \
                                              const uint64_t *, const int8_t *, int, int *,  \
-                                             cudaStream_t, int, int, int8_t *, int *, int *); \
+                                             cudaStream_t, int, int, int8_t *, int *, int *, \
+                                             const int *, int);                              \
     template cudaError_t launch_r3_inv<P>(int, const int8_t *, int8_t *, int32_t *, cudaStream_t, int, \
                                           int);
 SNT_R3_INST(653)

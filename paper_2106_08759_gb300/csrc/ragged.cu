@@ -120,7 +120,7 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
         if (mma)
             SNT_CUDA_R(launch_tree_up_mma<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lm, n_out,
                                              nodes + (size_t)g.lev_off[l] * pi.pad, st, tiles,
-                                             l == 1));
+                                             l == 1, ctx->mma_ksplit));
         else
             SNT_CUDA_R(launch_tree_up<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lm, n_out,
                                          nodes + (size_t)g.lev_off[l] * pi.pad, st, split));
@@ -137,7 +137,7 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
         if (mma)
             SNT_CUDA_R(launch_tree_down_mma<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lm, n_par,
                                                nodes + (size_t)g.lev_off[l - 1] * pi.pad, st,
-                                               tiles, l == 1));
+                                               tiles, l == 1, ctx->mma_ksplit));
         else
             SNT_CUDA_R(launch_tree_down<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lm, n_par,
                                            nodes + (size_t)g.lev_off[l - 1] * pi.pad, st, split));
@@ -251,6 +251,7 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
     sig.push_back(split);
     sig.push_back(mma ? tiles : 0);
     sig.push_back(kpt);
+    sig.push_back(ctx->mma_ksplit);
     if (!(rg.exec && rg.sig == sig && rg.table_off == table_off)) {
         if (rg.exec) cudaGraphExecDestroy(rg.exec);
         rg.exec = nullptr;

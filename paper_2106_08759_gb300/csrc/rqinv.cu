@@ -193,11 +193,12 @@ __device__ __forceinline__ void leader_chunk(int m, int &delta, int fl, int gl, 
     u = cmod<Q>(u); v = cmod<Q>(v); w = cmod<Q>(w); z = cmod<Q>(z);
 }
 
-template <int P>
+// Q: the coefficient modulus (q: R/q; 3: R/3, for the root inversions of
+// the R/3 batch inversion).
+template <int P, int Q = Geo<P>::q>
 __global__ void __launch_bounds__(JumpGeo<P>::NT)
 k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_stride,
               int32_t *__restrict__ okv, int *__restrict__ err, int err_bit, const int *idx) {
-    constexpr int Q = Geo<P>::q;
     using JG = JumpGeo<P>;
     constexpr int LEN = JG::LEN, OFF = JG::OFF, NT = JG::NT;
     constexpr int NCH = (2 * P - 1 + JG::M - 1) / JG::M;
@@ -373,6 +374,15 @@ cudaError_t launch_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t
 }
 
 template <int P>
+cudaError_t launch_r3_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
+                               long out_stride, int32_t *ok, int *err, int err_bit,
+                               cudaStream_t st) {
+    k_rq_inv_jump<P, 3><<<n, JumpGeo<P>::NT, 0, st>>>(n, in, in_stride, out, out_stride, ok, err,
+                                                      err_bit, nullptr);
+    return cudaGetLastError();
+}
+
+template <int P>
 cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out,
                           long out_stride, int32_t *ok, int *err, int err_bit, cudaStream_t st) {
     constexpr int NT = inv_threads<P>();
@@ -384,7 +394,9 @@ cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out
     template cudaError_t launch_rq_inv<P>(int, const int16_t *, long, int16_t *, long,     \
                                           int32_t *, int *, int, cudaStream_t);            \
     template cudaError_t launch_rq_inv_jump<P>(int, const int16_t *, long, int16_t *, long, \
-                                               int32_t *, int *, int, cudaStream_t, const int *);
+                                               int32_t *, int *, int, cudaStream_t, const int *); \
+    template cudaError_t launch_r3_inv_jump<P>(int, const int16_t *, long, int16_t *, long, \
+                                               int32_t *, int *, int, cudaStream_t);
 SNT_INV_INST(653)
 SNT_INV_INST(761)
 SNT_INV_INST(857)

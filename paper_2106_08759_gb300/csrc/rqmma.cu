@@ -6,6 +6,9 @@
 // (down-sweep, sharing the parent's E table) with NW warps of NT tiles each.
 // In the down-sweep the children are overwritten in place: every read of
 // them happens before the CTA's first barrier and only this CTA touches them.
+// On narrow levels (few products: latency, not throughput) each tile's sum
+// is also split over KS warps along D (K-split), cutting the serial MMA
+// chain of a product KS-fold.
 #include <cuda_fp16.h>
 
 #include "kernels.h"
@@ -20,31 +23,23 @@ template <typename K> cudaError_t allow_smem(K kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Node mapping of a level (single tree or forest), as in rqmul.cu.
-__device__ __forceinline__ void node_of(const LevelMap &lm, int j, int &idx, int &base, int &n_in) {
-    idx = j; base = 0; n_in = lm.n_in;
-    if (lm.nb > 0) {
-        const int b = level_batch(lm.pre_out, lm.nb, j);
-        idx = j - lm.pre_out[b];
-        base = lm.pre_in[b];
-        n_in = lm.pre_in[b + 1] - base;
-    }
-}
 
 }  // namespace
 
-template <int P, int NT, int MODE>
-__global__ void __launch_bounds__(32 * MmaGeo<P, NT>::NW)
+template <int P, int NT, int MODE, int KS, int Q = Prm<P>::q>
+__global__ void __launch_bounds__(32 * MmaGeo<P, NT>::NW * KS)
 k_tree_up_mma(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict__ lout) {
     using G = Geo<P>;
     using M = MmaGeo<P, NT>;
     extern __shared__ __align__(16) uint8_t sm[];
     MmaE<P, NT> &E = *reinterpret_cast<MmaE<P, NT> *>(sm);
     MmaA<P, NT> &A = *reinterpret_cast<MmaA<P, NT> *>(sm + sizeof(MmaE<P, NT>));
+    float *red = reinterpret_cast<float *>(sm + sizeof(MmaE<P, NT>) + sizeof(MmaA<P, NT>));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nth = blockDim.x;
+    const int tw = warp % M::NW, ks = warp / M::NW;  // tile group, K-split part
     const int j = blockIdx.x;
     int idx, base, n_in;
-    node_of(lm, j, idx, base, n_in);
+    lm_node(lm, j, idx, base, n_in);
     const int16_t *a = lin + (size_t)(base + 2 * idx) * G::pad;
     int16_t *c = lout + (size_t)j * G::pad;
     if (2 * idx + 1 >= n_in) {  // unpaired: move up unchanged (uniform over the CTA)
@@ -54,29 +49,32 @@ k_tree_up_mma(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict_
     mma_fill_a<P, NT, MODE>(a, A, threadIdx.x, nth);
     mma_fill_b<P, NT>(a + G::pad, E, threadIdx.x, nth);
     __syncthreads();
-    mma_fill_pe<P, NT, MODE>(E, threadIdx.x, nth);
+    mma_fill_pe<P, NT, MODE, Q>(E, threadIdx.x, nth);
     __syncthreads();
     float acc[NT][1][3][4];
     const MmaA<P, NT> *const As[1] = {&A};
-    mma_tiles<P, NT, 1, MODE>(E, As, warp * NT, lane, acc);
+    mma_tiles<P, NT, 1, MODE>(E, As, tw * NT, lane, acc, ks, KS);
+    if (KS > 1) mma_ksplit_reduce<NT, 1>(acc, red, ks, KS, tw, M::NW, lane);
     __syncthreads();
-    mma_stage<P, NT, 1, MODE>(A, warp * NT, lane, 0, acc);
+    if (ks == 0) mma_stage<P, NT, 1, MODE, Q>(A, tw * NT, lane, 0, acc);
     __syncthreads();
-    mma_finish<P, NT>(A, (int)E.b[M::p - 1], c, G::pad, threadIdx.x, nth);
+    mma_finish<P, NT, Q>(A, (int)E.b[M::p - 1], c, G::pad, threadIdx.x, nth);
 }
 
-template <int P, int NT, int MODE>
-__global__ void __launch_bounds__(32 * MmaGeo<P, NT>::NW)
+template <int P, int NT, int MODE, int KS, int Q = Prm<P>::q>
+__global__ void __launch_bounds__(32 * MmaGeo<P, NT>::NW * KS)
 k_tree_down_mma(const int16_t *__restrict__ lpar, LevelMap lm, int16_t *__restrict__ lch) {
     using G = Geo<P>;
     using M = MmaGeo<P, NT>;
     extern __shared__ __align__(16) uint8_t sm[];
     MmaE<P, NT> &E = *reinterpret_cast<MmaE<P, NT> *>(sm);
     MmaA<P, NT> *A = reinterpret_cast<MmaA<P, NT> *>(sm + sizeof(MmaE<P, NT>));
+    float *red = reinterpret_cast<float *>(sm + sizeof(MmaE<P, NT>) + 2 * sizeof(MmaA<P, NT>));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nth = blockDim.x;
+    const int tw = warp % M::NW, ks = warp / M::NW;  // tile group, K-split part
     const int j = blockIdx.x;
     int idx, base, n_ch;
-    node_of(lm, j, idx, base, n_ch);
+    lm_node(lm, j, idx, base, n_ch);
     const int16_t *T = lpar + (size_t)j * G::pad;
     int16_t *x = lch + (size_t)(base + 2 * idx) * G::pad;
     int16_t *y = x + G::pad;
@@ -88,18 +86,22 @@ k_tree_down_mma(const int16_t *__restrict__ lpar, LevelMap lm, int16_t *__restri
     mma_fill_a<P, NT, MODE>(x, A[1], threadIdx.x, nth);  // 1/y = T * x
     mma_fill_b<P, NT>(T, E, threadIdx.x, nth);
     __syncthreads();  // both children are in shared memory before either is overwritten
-    mma_fill_pe<P, NT, MODE_GEN>(E, threadIdx.x, nth);  // T is never small
+    // the parent T is small only in R/3 (MODE_SAE), never in R/q
+    mma_fill_pe<P, NT, MODE == MODE_SAE ? MODE_SAE : MODE_GEN, Q>(E, threadIdx.x, nth);
     __syncthreads();
     float acc[NT][2][3][4];
     const MmaA<P, NT> *const As[2] = {&A[0], &A[1]};
-    mma_tiles<P, NT, 2, MODE>(E, As, warp * NT, lane, acc);
+    mma_tiles<P, NT, 2, MODE>(E, As, tw * NT, lane, acc, ks, KS);
+    if (KS > 1) mma_ksplit_reduce<NT, 2>(acc, red, ks, KS, tw, M::NW, lane);
     __syncthreads();
-    mma_stage<P, NT, 2, MODE>(A[0], warp * NT, lane, 0, acc);
-    mma_stage<P, NT, 2, MODE>(A[1], warp * NT, lane, 1, acc);
+    if (ks == 0) {
+        mma_stage<P, NT, 2, MODE, Q>(A[0], tw * NT, lane, 0, acc);
+        mma_stage<P, NT, 2, MODE, Q>(A[1], tw * NT, lane, 1, acc);
+    }
     __syncthreads();
     const int tl = (int)E.b[M::p - 1];
-    mma_finish<P, NT>(A[0], tl, x, G::pad, threadIdx.x, nth);
-    mma_finish<P, NT>(A[1], tl, y, G::pad, threadIdx.x, nth);
+    mma_finish<P, NT, Q>(A[0], tl, x, G::pad, threadIdx.x, nth);
+    mma_finish<P, NT, Q>(A[1], tl, y, G::pad, threadIdx.x, nth);
 }
 
 // c_e = a_e * b_e, n products, all operands stride p (microbenchmark layout).
@@ -128,27 +130,43 @@ k_mul_batch_mma(const int16_t *__restrict__ a, const int16_t *__restrict__ b,
 }
 
 namespace {
-template <int P, int NT, int MODE>
+template <int P, int NT, int MODE, int KS = 1, int Q = Prm<P>::q>
 cudaError_t up_nt(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout, cudaStream_t st) {
-    const size_t sm = sizeof(MmaE<P, NT>) + sizeof(MmaA<P, NT>);
-    cudaError_t e = allow_smem(k_tree_up_mma<P, NT, MODE>, sm);
+    using M = MmaGeo<P, NT>;
+    const size_t sm = sizeof(MmaE<P, NT>) + sizeof(MmaA<P, NT>) +
+                      (size_t)(KS - 1) * M::NW * 32 * NT * 12 * sizeof(float);
+    cudaError_t e = allow_smem(k_tree_up_mma<P, NT, MODE, KS, Q>, sm);
     if (e != cudaSuccess) return e;
-    k_tree_up_mma<P, NT, MODE><<<n_out, 32 * MmaGeo<P, NT>::NW, sm, st>>>(lin, lm, lout);
+    k_tree_up_mma<P, NT, MODE, KS, Q><<<n_out, 32 * M::NW * KS, sm, st>>>(lin, lm, lout);
     return cudaGetLastError();
 }
-template <int P, int NT, int MODE>
+template <int P, int NT, int MODE, int KS = 1, int Q = Prm<P>::q>
 cudaError_t down_nt(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t *lch, cudaStream_t st) {
-    const size_t sm = sizeof(MmaE<P, NT>) + 2 * sizeof(MmaA<P, NT>);
-    cudaError_t e = allow_smem(k_tree_down_mma<P, NT, MODE>, sm);
+    using M = MmaGeo<P, NT>;
+    const size_t sm = sizeof(MmaE<P, NT>) + 2 * sizeof(MmaA<P, NT>) +
+                      (size_t)(KS - 1) * M::NW * 32 * NT * 2 * 12 * sizeof(float);
+    cudaError_t e = allow_smem(k_tree_down_mma<P, NT, MODE, KS, Q>, sm);
     if (e != cudaSuccess) return e;
-    k_tree_down_mma<P, NT, MODE><<<n_par, 32 * MmaGeo<P, NT>::NW, sm, st>>>(lpar, lm, lch);
+    k_tree_down_mma<P, NT, MODE, KS, Q><<<n_par, 32 * M::NW * KS, sm, st>>>(lpar, lm, lch);
     return cudaGetLastError();
+}
+// K-split of a level of n products (at most kmax): latency-bound levels only.
+inline int ksplit_for(int n, int kmax) {
+    const int k = n <= 64 ? 4 : n <= 256 ? 2 : 1;
+    return k < kmax ? k : (kmax >= 4 ? 4 : kmax >= 2 ? 2 : 1);
 }
 }  // namespace
 
 template <int P>
 cudaError_t launch_tree_up_mma(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
-                               cudaStream_t st, int tiles, bool leaves) {
+                               cudaStream_t st, int tiles, bool leaves, int kmax) {
+    switch (ksplit_for(n_out, kmax)) {  // narrow level: one tile per warp, K-split
+        case 4: return leaves ? up_nt<P, 1, MODE_SAE, 4>(lin, lm, n_out, lout, st)
+                              : up_nt<P, 1, MODE_GEN, 4>(lin, lm, n_out, lout, st);
+        case 2: return leaves ? up_nt<P, 1, MODE_SAE, 2>(lin, lm, n_out, lout, st)
+                              : up_nt<P, 1, MODE_GEN, 2>(lin, lm, n_out, lout, st);
+        default: break;
+    }
     if (leaves) {  // leaf x leaf: both operands 3f, one MMA per tile
         switch (tiles) {
             case 2: return up_nt<P, 2, MODE_SAE>(lin, lm, n_out, lout, st);
@@ -165,7 +183,14 @@ cudaError_t launch_tree_up_mma(const int16_t *lin, const LevelMap &lm, int n_out
 
 template <int P>
 cudaError_t launch_tree_down_mma(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t *lch,
-                                 cudaStream_t st, int tiles, bool leaves) {
+                                 cudaStream_t st, int tiles, bool leaves, int kmax) {
+    switch (ksplit_for(n_par, kmax)) {  // narrow level: one tile per warp, K-split
+        case 4: return leaves ? down_nt<P, 1, MODE_SA, 4>(lpar, lm, n_par, lch, st)
+                              : down_nt<P, 1, MODE_GEN, 4>(lpar, lm, n_par, lch, st);
+        case 2: return leaves ? down_nt<P, 1, MODE_SA, 2>(lpar, lm, n_par, lch, st)
+                              : down_nt<P, 1, MODE_GEN, 2>(lpar, lm, n_par, lch, st);
+        default: break;
+    }
     if (leaves) {  // parent inverse x leaf 3f: two MMAs per tile
         switch (tiles) {
             case 2: return down_nt<P, 2, MODE_SA>(lpar, lm, n_par, lch, st);
@@ -177,6 +202,27 @@ cudaError_t launch_tree_down_mma(const int16_t *lpar, const LevelMap &lm, int n_
         case 2: return down_nt<P, 2, MODE_GEN>(lpar, lm, n_par, lch, st);
         case 3: return down_nt<P, 3, MODE_GEN>(lpar, lm, n_par, lch, st);
         default: return down_nt<P, 1, MODE_GEN>(lpar, lm, n_par, lch, st);
+    }
+}
+
+// The same trees in R/3 (coefficients mod 3, all operands small: one MMA
+// per tile on every level), for the batch inversion of the g's.
+template <int P>
+cudaError_t launch_tree_up_mma3(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
+                                cudaStream_t st, int kmax) {
+    switch (ksplit_for(n_out, kmax)) {
+        case 4: return up_nt<P, 1, MODE_SAE, 4, 3>(lin, lm, n_out, lout, st);
+        case 2: return up_nt<P, 1, MODE_SAE, 2, 3>(lin, lm, n_out, lout, st);
+        default: return up_nt<P, 1, MODE_SAE, 1, 3>(lin, lm, n_out, lout, st);
+    }
+}
+template <int P>
+cudaError_t launch_tree_down_mma3(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t *lch,
+                                  cudaStream_t st, int kmax) {
+    switch (ksplit_for(n_par, kmax)) {
+        case 4: return down_nt<P, 1, MODE_SAE, 4, 3>(lpar, lm, n_par, lch, st);
+        case 2: return down_nt<P, 1, MODE_SAE, 2, 3>(lpar, lm, n_par, lch, st);
+        default: return down_nt<P, 1, MODE_SAE, 1, 3>(lpar, lm, n_par, lch, st);
     }
 }
 
@@ -193,11 +239,15 @@ cudaError_t launch_mul_batch_mma(int n, const int16_t *a, const int16_t *b, int1
 
 #define SNT_MMA_INST(P)                                                                         \
     template cudaError_t launch_tree_up_mma<P>(const int16_t *, const LevelMap &, int, int16_t *, \
-                                               cudaStream_t, int, bool);                        \
+                                               cudaStream_t, int, bool, int);                   \
     template cudaError_t launch_tree_down_mma<P>(const int16_t *, const LevelMap &, int,        \
-                                                 int16_t *, cudaStream_t, int, bool);           \
+                                                 int16_t *, cudaStream_t, int, bool, int);      \
     template cudaError_t launch_mul_batch_mma<P>(int, const int16_t *, const int16_t *,         \
-                                                 int16_t *, cudaStream_t);
+                                                 int16_t *, cudaStream_t);                      \
+    template cudaError_t launch_tree_up_mma3<P>(const int16_t *, const LevelMap &, int,         \
+                                                int16_t *, cudaStream_t, int);                  \
+    template cudaError_t launch_tree_down_mma3<P>(const int16_t *, const LevelMap &, int,       \
+                                                  int16_t *, cudaStream_t, int);
 SNT_MMA_INST(653)
 SNT_MMA_INST(761)
 SNT_MMA_INST(857)

@@ -31,13 +31,8 @@ k_tree_up(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict__ lo
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
     __shared__ int part[K > 1 ? (K - 1) * Tp<P>::p8 : 1];
     const int j = blockIdx.x;
-    int idx = j, base = 0, n_in = lm.n_in;  // this node's index in its tree, its children
-    if (lm.nb > 0) {
-        const int b = level_batch(lm.pre_out, lm.nb, j);
-        idx = j - lm.pre_out[b];
-        base = lm.pre_in[b];
-        n_in = lm.pre_in[b + 1] - base;
-    }
+    int idx, base, n_in;  // this node's index in its tree, its children
+    lm_node(lm, j, idx, base, n_in);
     const int16_t *a = lin + (size_t)(base + 2 * idx) * G::pad;
     int16_t *c = lout + (size_t)j * G::pad;
     if (2 * idx + 1 >= n_in) {  // unpaired: move up unchanged
@@ -68,13 +63,8 @@ k_tree_down(const int16_t *__restrict__ lpar, LevelMap lm, int16_t *__restrict__
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
     __shared__ int part[K > 1 ? (K - 1) * Tp<P>::p8 : 1];
     const int j = blockIdx.x;
-    int idx = j, base = 0, n_ch = lm.n_in;
-    if (lm.nb > 0) {
-        const int b = level_batch(lm.pre_out, lm.nb, j);
-        idx = j - lm.pre_out[b];
-        base = lm.pre_in[b];
-        n_ch = lm.pre_in[b + 1] - base;
-    }
+    int idx, base, n_ch;
+    lm_node(lm, j, idx, base, n_ch);
     const int16_t *T = lpar + (size_t)j * G::pad;
     int16_t *x = lch + (size_t)(base + 2 * idx) * G::pad;
     if (2 * idx + 1 >= n_ch) {  // unpaired child: its inverse is the parent's
@@ -112,13 +102,8 @@ k_tree_up_seg(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict_
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
     __shared__ int part[K > 1 ? (K - 1) * SegGeo<P, S>::TS * 8 : 1];
     const int j = blockIdx.x, seg = blockIdx.y;
-    int idx = j, base = 0, n_in = lm.n_in;
-    if (lm.nb > 0) {
-        const int b = level_batch(lm.pre_out, lm.nb, j);
-        idx = j - lm.pre_out[b];
-        base = lm.pre_in[b];
-        n_in = lm.pre_in[b + 1] - base;
-    }
+    int idx, base, n_in;
+    lm_node(lm, j, idx, base, n_in);
     const int16_t *a = lin + (size_t)(base + 2 * idx) * G::pad;
     int16_t *c = lout + (size_t)j * G::pad;
     if (2 * idx + 1 >= n_in) {  // unpaired: move up unchanged (segment 0 copies)
@@ -148,13 +133,8 @@ k_tree_down_seg(const int16_t *__restrict__ lpar, LevelMap lm, const int16_t *__
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
     __shared__ int part[K > 1 ? (K - 1) * SegGeo<P, S>::TS * 8 : 1];
     const int j = blockIdx.x, seg = blockIdx.y;
-    int idx = j, base = 0, n_ch = lm.n_in;
-    if (lm.nb > 0) {
-        const int b = level_batch(lm.pre_out, lm.nb, j);
-        idx = j - lm.pre_out[b];
-        base = lm.pre_in[b];
-        n_ch = lm.pre_in[b + 1] - base;
-    }
+    int idx, base, n_ch;
+    lm_node(lm, j, idx, base, n_ch);
     const int16_t *T = lpar + (size_t)j * G::pad;
     const int16_t *x = lch + (size_t)(base + 2 * idx) * G::pad;
     int16_t *ox = lout + (size_t)(base + 2 * idx) * G::pad;

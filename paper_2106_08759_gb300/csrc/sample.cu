@@ -27,7 +27,8 @@ template <int P>
 __global__ void __launch_bounds__(256)
 k_sample_f(KeyMap km, int nkeys, int16_t *__restrict__ leaves, int sk_bytes, int rho_off,
            int8_t *__restrict__ g_out, const uint64_t *__restrict__ inj_idx,
-           const int8_t *__restrict__ inj_g, int n_inj, int *__restrict__ fix_count) {
+           const int8_t *__restrict__ inj_g, int n_inj, int *__restrict__ fix_count,
+           int16_t *__restrict__ g16_out) {
     using G = Geo<P>;
     __shared__ __align__(16) uint32_t xs[1024];
     const int key = blockIdx.x;
@@ -67,9 +68,13 @@ k_sample_f(KeyMap km, int nkeys, int16_t *__restrict__ leaves, int sk_bytes, int
         }
         __syncthreads();
         int8_t *grow = g_out + (size_t)key * G::pad;
+        int16_t *g16 = g16_out ? g16_out + (size_t)key * G::pad : nullptr;
         if (inj >= 0) {
-            for (int i = t; i < G::pad; i += blockDim.x)
-                grow[i] = (i < G::p) ? inj_g[(size_t)inj * G::p + i] : (int8_t)0;
+            for (int i = t; i < G::pad; i += blockDim.x) {
+                const int8_t c = (i < G::p) ? inj_g[(size_t)inj * G::p + i] : (int8_t)0;
+                grow[i] = c;
+                if (g16) g16[i] = c;
+            }
         } else {
             // g_i = floor(3 (u_i mod 2^30) / 2^30) - 1 for word u_i of stream 0, attempt 0
             for (int blk = t; 4 * blk < G::pad; blk += blockDim.x) {
@@ -78,9 +83,11 @@ k_sample_f(KeyMap km, int nkeys, int16_t *__restrict__ leaves, int sk_bytes, int
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int i = 4 * blk + j;
-                    grow[i] = (i < G::p)
+                    const int8_t c = (i < G::p)
                         ? (int8_t)((int)(((unsigned long long)(r[j] & 0x3fffffffu) * 3u) >> 30) - 1)
                         : (int8_t)0;
+                    grow[i] = c;
+                    if (g16) g16[i] = c;
                 }
             }
         }
@@ -102,16 +109,16 @@ template <int P>
 cudaError_t launch_sample_f(const KeyMap &km, int nkeys, int16_t *leaves, int sk_bytes,
                             int rho_off, cudaStream_t st, int8_t *g_out,
                             const uint64_t *inj_idx, const int8_t *inj_g, int n_inj,
-                            int *fix_count) {
+                            int *fix_count, int16_t *g16_out) {
     k_sample_f<P><<<nkeys, 256, 0, st>>>(km, nkeys, leaves, sk_bytes, rho_off, g_out, inj_idx,
-                                         inj_g, n_inj, fix_count);
+                                         inj_g, n_inj, fix_count, g16_out);
     return cudaGetLastError();
 }
 
 #define SNT_SAMPLE_INST(P)                                                                  \
     template cudaError_t launch_sample_f<P>(const KeyMap &, int, int16_t *, int, int,       \
                                             cudaStream_t, int8_t *, const uint64_t *,       \
-                                            const int8_t *, int, int *);
+                                            const int8_t *, int, int *, int16_t *);
 SNT_SAMPLE_INST(653)
 SNT_SAMPLE_INST(761)
 SNT_SAMPLE_INST(857)

@@ -31,6 +31,8 @@ def main():
     ap.add_argument("--keygen-only", type=int, default=0, metavar="B",
                     help="only run batch keygen of B keys --reps times with the default "
                          "options (a small, fixed target for a profiler)")
+    ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
+                    help="context option for --keygen-only, e.g. R3_MODE=1 (SNT_OPT_ prefix implied)")
     args = ap.parse_args()
 
     import numpy as np
@@ -64,6 +66,9 @@ def main():
         return torch.from_numpy(np.ascontiguousarray(x)).to(dtype=dt, device=dev)
 
     if args.keygen_only:
+        for o in args.opt:
+            name, val = o.split("=")
+            ctx.set_option(getattr(snt, "SNT_OPT_" + name), int(val))
         B = args.keygen_only
         pkb, skb, _, _ = snt.snt_param_sizes(P)
         pk = torch.empty(B * pkb, dtype=torch.uint8, device=dev)
@@ -163,17 +168,15 @@ def main():
         ctx.set_option(snt.SNT_OPT_TREE_SPLIT, 8)
         for overlap in (0, 1, 2):
             ctx.set_option(snt.SNT_OPT_R3_OVERLAP, overlap)
-            for tiles in (1, 2):
-                for lanes, kpt in ((4, 1), (4, 2), (8, 1), (8, 2)):
+            for roots in (1, 4, 16, 64):
+                for r3mode in (0, 1, 2):
                     ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
-                    ctx.set_option(snt.SNT_OPT_MMA_TILES, tiles)
-                    ctx.set_option(snt.SNT_OPT_R3_LANES, lanes)
-                    ctx.set_option(snt.SNT_OPT_R3_KPT, kpt)
-                    sweep["mma_tiles%d_overlap%d_lanes%d_kpt%d" % (tiles, overlap, lanes, kpt)] = \
+                    ctx.set_option(snt.SNT_OPT_ROOTS, roots)
+                    ctx.set_option(snt.SNT_OPT_R3_MODE, r3mode)
+                    sweep["mma_roots%d_overlap%d_r3mode%d" % (roots, overlap, r3mode)] = \
                         run_keygen_avg()
-        ctx.set_option(snt.SNT_OPT_MMA_TILES, 1)
-        ctx.set_option(snt.SNT_OPT_R3_LANES, 4)
-        ctx.set_option(snt.SNT_OPT_R3_KPT, 1)
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+        ctx.set_option(snt.SNT_OPT_R3_MODE, 0)
         ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 0)
         for narrow in (0, 1):
             for overlap in (0, 1, 2):

@@ -133,6 +133,112 @@ def test_tensor_core_engine_gives_the_same_keys(snt, ctx, P, B, tiles):
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
 
 
+@pytest.mark.parametrize("engine", [1, 0])
+@pytest.mark.parametrize("roots,B", [(2, 96), (32, 96), (1024, 96), (4, 300), (8, 7), (64, 4096)])
+def test_forest_of_subtrees_gives_the_same_keys(snt, ctx, engine, roots, B):
+    # Montgomery's trick over K equal subtrees with K root inversions in one
+    # launch (K = the largest power of two <= roots dividing B: 300 -> 4,
+    # 7 -> 1); inverses are unique, so the bytes equal the single tree's
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, engine)
+    try:
+        ref = gpu_keygen(snt, ctx, 761, 8, 500, B)
+        ctx.set_option(snt.SNT_OPT_ROOTS, roots)
+        got = gpu_keygen(snt, ctx, 761, 8, 500, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    if B <= 96:
+        rpk, rsk = oracle.keygen_batch(761, 8, 500, B)
+        assert first_mismatch(got[0], rpk) is None and first_mismatch(got[1], rsk) is None
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("roots", [1, 16])
+@pytest.mark.parametrize("P,B", [(761, 64), (653, 45), (857, 33), (761, 2)])
+def test_r3_batch_inversion_matches_oracle(snt, ctx, P, B, roots, mode):
+    # mode 1: isInvertible by remainders modulo the F_3 factors, then
+    # Montgomery's trick in R/3 (tensor-core forest, jump-divstep roots mod 3);
+    # mode 2: the forest on the first draws, invertibility from the roots
+    ctx.set_option(snt.SNT_OPT_R3_MODE, mode)
+    ctx.set_option(snt.SNT_OPT_ROOTS, roots)
+    try:
+        pk, sk = gpu_keygen(snt, ctx, P, 21, 9, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_R3_MODE, 0)
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+    rpk, rsk = oracle.keygen_batch(P, 21, 9, B)
+    assert first_mismatch(pk, rpk) is None and first_mismatch(sk, rsk) is None
+
+
+def _zero_divisors(p, rng):
+    """g = f_i * r for every irreducible factor f_i of x^p - x - 1 over F_3."""
+    out = []
+    for d, _, poly in oracle.ddf(p, 3):
+        f = np.asarray(poly[: d + 1]) % 3
+        r = rng.integers(0, 3, p - d)
+        g = np.convolve(f, r)[:p] % 3
+        out.append(np.where(g == 2, -1, g).astype(np.int8))
+    return out
+
+
+@pytest.mark.parametrize("mode,roots", [(1, 1), (2, 1), (2, 8)])
+@pytest.mark.parametrize("P", [653, 761, 857])
+def test_r3_batch_redraws_every_kind_of_zero_divisor(snt, ctx, P, mode, roots):
+    # one injected non-invertible first draw per factor of x^p - x - 1: the
+    # remainder test (mode 1) or the failing subtree root (mode 2, then the
+    # per-key fall-back and the fix-up of h, pk and its hash) must reject each,
+    # and the redraw must match the oracle
+    p = oracle.PARAMS[P][0]
+    bads = _zero_divisors(p, np.random.default_rng(P))
+    B = 40
+    offs = [3 + 5 * i for i in range(len(bads))]
+    snt.snt_debug_inject_g(ctx, P, [200 + o for o in offs], np.stack(bads))
+    ctx.set_option(snt.SNT_OPT_R3_MODE, mode)
+    ctx.set_option(snt.SNT_OPT_ROOTS, roots)
+    try:
+        pk, sk = gpu_keygen(snt, ctx, P, 4, 200, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_R3_MODE, 0)
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+        snt.snt_debug_inject_g(ctx, P, [], np.zeros((0, p), np.int8))
+    rpk, rsk = oracle.keygen_batch(P, 4, 200, B, g_inject=dict(zip(offs, bads)))
+    assert first_mismatch(pk, rpk) is None and first_mismatch(sk, rsk) is None
+    for o, g in zip(offs, bads):  # each was really redrawn
+        assert oracle.keygen(P, 4, 200 + o, g_attempt0=g)[2] >= 2
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_r3_batch_equals_per_key_at_b4096(snt, ctx, mode):
+    ref = gpu_keygen(snt, ctx, 761, 33, 0, 4096)
+    ctx.set_option(snt.SNT_OPT_R3_MODE, mode)
+    ctx.set_option(snt.SNT_OPT_ROOTS, 64)
+    try:
+        got = gpu_keygen(snt, ctx, 761, 33, 0, 4096)
+    finally:
+        ctx.set_option(snt.SNT_OPT_R3_MODE, 0)
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+@pytest.mark.parametrize("ksplit", [1, 2, 4])
+@pytest.mark.parametrize("P,B", [(761, 600), (653, 5), (857, 200)])
+def test_tensor_core_ksplit_gives_the_same_keys(snt, ctx, P, B, ksplit):
+    # narrow levels with each tile's sum split over 1, 2 or 4 warps; B = 5
+    # and 200 make the leaf levels narrow too (the small-operand forms)
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 0)
+    try:
+        ref = gpu_keygen(snt, ctx, P, 6, 77, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
+    ctx.set_option(snt.SNT_OPT_MMA_KSPLIT, ksplit)
+    try:
+        got = gpu_keygen(snt, ctx, P, 6, 77, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_MMA_KSPLIT, 4)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
 @pytest.mark.parametrize("P,B", [(653, 9), (857, 33)])
 def test_output_split_narrow_levels_vs_oracle(snt, ctx, P, B):
     assert ctx.get_option(snt.SNT_OPT_NARROW_SEG) == 1
