@@ -32,7 +32,21 @@ METRIC = "sntrup761 keygens/s on 1 GB300, batched vs per-key GPU path; p50/p99 s
 P, Q, W = 761, 4591, 286
 WORDS = (P + 1 + 31) // 32
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
-LAUNCHES_FIXED = 5           # sample_f, r3, root, finalize, sha512 (+ 2 per tree level)
+def launches_per_call(B, tuned):
+    """Library kernel launches of one batch keygen call under the tuned layouts.
+
+    R/q: sampling, up-sweep (one per level), roots, down-sweep, h, SHA-512;
+    R/3 per key: its kernel and the fix-up; R/3 check-first batch: the check,
+    its forest (2 per level + roots) and the encoding; R/3 first-draw batch:
+    the forest, the encoding, the fall-back kernel and the fix-up."""
+    K = forest_roots(B, tuned.get("roots", 1))
+    L, n = 0, B // K
+    while n > 1:
+        n = (n + 1) // 2
+        L += 1
+    rq = 1 + L + 1 + L + 1 + 1
+    r3 = {0: 2, 1: 1 + 2 * L + 1 + 1, 2: 2 * L + 1 + 1 + 1 + 1}[tuned.get("r3_mode", 0)]
+    return rq + r3
 
 # DRAM bytes (read + write) per call of a phase's kernel at B = 4096, from
 # the committed ncu captures (profiles/), keyed by kernel instantiation; a
@@ -43,12 +57,51 @@ NCU_TRAFFIC_BYTES = {"k_r3_keygen<761, 4>": 32512}
 def kernel_of(phase, tuned):
     """Kernel instantiation that runs a phase under the tuned layouts."""
     if phase == "r3_inv":
-        return "k_r3_keygen<761, %d>" % tuned.get("r3_lanes", 4)
+        if tuned.get("r3_mode", 0) == 0:
+            return "k_r3_keygen<761, %d>" % tuned.get("r3_lanes", 4)
+        return "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>"
     mma = tuned.get("rq_engine") == 1
     return {"tree_up": "k_tree_up_mma" if mma else "k_tree_up",
             "tree_down": "k_tree_down_mma" if mma else "k_tree_down",
             "h_encode": "k_finalize_mma<761>" if mma else "k_finalize<761>",
-            "root_inv": "k_rq_inv_jump<761>"}[phase]
+            "root_inv": "k_rq_inv_jump<761, 4591>"}[phase]
+
+
+# ---- replicas (N > 1): one process per GPU, independent batches ----------------
+def replica_key_base(rank):
+    """First key index of a rank: disjoint 2^40-key ranges, so replicas never
+    generate the same key (key i of a call uses (seed, first + i) only)."""
+    return rank << 40
+
+
+def max_over_ranks(x, dist, device):
+    """Max of a per-rank number over all ranks (the job's wall time)."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, B, steps, seconds):
+    """Keys of all ranks per second of the slowest rank."""
+    return world * B * steps / seconds
+
+
+def tree_nodes(n):
+    t = 0
+    while True:
+        t += n
+        if n == 1:
+            return t
+        n = (n + 1) // 2
+
+
+def forest_roots(B, roots):
+    """Subtrees the library uses for a batch (its forest rule)."""
+    k = 1
+    while 2 * k <= roots and B % (2 * k) == 0 and 2 * k * tree_nodes(B // (2 * k)) <= tree_nodes(B):
+        k *= 2
+    return k
 
 
 def parse():
@@ -151,22 +204,25 @@ def _measured_peaks():
         return {}
 
 
-def ops_per_call(B, p=P):
-    """Algorithmic integer operations of each phase for one call of B keys.
+def ops_per_call(B, K=1, r3_mode=0, p=P):
+    """Algorithmic integer operations of each phase for one call of B keys in
+    K subtrees.
 
-    R/q products count p^2 multiply-adds (the Toeplitz/schoolbook form every
-    product kernel computes); the R/3 divsteps count 6 word operations per
+    Products count p^2 multiply-adds (the Toeplitz/schoolbook form every
+    product kernel computes; a forest of K subtrees has B - K products up and
+    2(B - K) down); the per-key R/3 divsteps count 6 word operations per
     32-trit word for each of the two polynomial updates per step (bit-sliced
-    F_3 multiply-add); the root inversion counts 2 multiply-reduce updates of
-    p + 1 coefficients per step."""
+    F_3 multiply-add), the R/3 batch paths their 3(B - K) products mod 3; a
+    root inversion counts 2 multiply-reduce updates of p + 1 coefficients per
+    step."""
     steps = 2 * p - 1
     mac = p * p
     return {
-        "r3_inv": B * steps * 2 * WORDS * 6,
-        "tree_up": (B - 1) * mac,
-        "tree_down": 2 * (B - 1) * mac,
+        "r3_inv": B * steps * 2 * WORDS * 6 if r3_mode == 0 else 3 * (B - K) * mac,
+        "tree_up": (B - K) * mac,
+        "tree_down": 2 * (B - K) * mac,
         "h_encode": B * mac,
-        "root_inv": steps * 2 * (p + 1),
+        "root_inv": K * steps * 2 * (p + 1),
     }
 
 
@@ -204,7 +260,7 @@ def run_ours(args):
     sk = torch.empty(B * skb, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    base = (rank << 40)
+    base = replica_key_base(rank)
 
     lop3_peak, sms = snt.snt_measure_int_peak(local, 0)
     imad_peak, _ = snt.snt_measure_int_peak(local, 1)
@@ -212,12 +268,7 @@ def run_ours(args):
     peaks = _measured_peaks()
     tuned = ctx.autotune(P, B)  # kernel layouts for this GPU, before any timed step
 
-    L = 0
-    n = B
-    while n > 1:
-        n = (n + 1) // 2
-        L += 1
-    launches_per_step = LAUNCHES_FIXED + 2 * L
+    launches_per_step = launches_per_call(B, tuned)
 
     def timed(fn, steps, warmup, phases=False):
         ctx.set_timing(phases)
@@ -242,9 +293,7 @@ def run_ours(args):
         ctx.sync()
         total_ms = sum(a.elapsed_time(b) for a, b in evs)
         if dist:
-            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+            total_ms = max_over_ranks(total_ms, dist, dev)
         return total_ms, {k: v / steps for k, v in acc.items()}
 
     def batched(first):
@@ -257,11 +306,11 @@ def run_ours(args):
         total_ms, phase = timed(batched, args.steps, max(3, args.warmup), phases=True)
     clocks = clk.summary()
     ms_per_step = total_ms / args.steps
-    value = world * B * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(world, B, args.steps, total_ms * 1e-3)
 
     pk_steps = args.perkey_steps or max(3, args.steps // 10)
     pk_ms, _ = timed(perkey, pk_steps, 3)
-    perkey_rate = world * B * pk_steps / (pk_ms * 1e-3)
+    perkey_rate = whole_job_rate(world, B, pk_steps, pk_ms * 1e-3)
 
     # end to end through the host-buffer entry point (device->host copy of
     # every key pair inside the timed region; the only inputs are the seed and
@@ -279,47 +328,64 @@ def run_ours(args):
         snt.snt_batch_keygen_host(ctx, P, args.seed, base + (3 * 10**9) + i * B, B, hpk, hsk)
     e2e_s = time.perf_counter() - t0
     if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_rate = world * B * e2e_steps / e2e_s
+        e2e_s = max_over_ranks(e2e_s, dist, dev)
+    e2e_rate = whole_job_rate(world, B, e2e_steps, e2e_s)
 
-    # roofline of the dominant kernel (largest phase time): an integer-pipe
-    # bound for the R/3 divsteps and the CUDA-core products, the tensor bound
-    # for the products on the tensor cores
-    ops = ops_per_call(B)
-    kernels = {k: phase.get(k, 0.0) for k in ops}
-    dom = max(kernels, key=kernels.get)
-    dom_ms = kernels[dom]
-    launches_of = {"r3_inv": 1, "tree_up": L, "tree_down": L, "h_encode": 1, "root_inv": 1}
-    if tuned.get("rq_engine") == 1 and dom in TENSOR_PHASES:
-        achieved = 2.0 * ops[dom] / (dom_ms * 1e-3) / 1e12  # TFLOP/s of the p^2 products
-        peak = peaks.get("bf16_tflops") or 1900.0
-        roofline = {
-            "bound": "tensor", "kernel": kernel_of(dom, tuned), "phase": dom, "pipe": "tensor (mma.sync f16, f32 accumulate)",
-            "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4),
-            "peak_source": ("of measured: dense bf16 GEMM burst in MEASURED_PEAKS.json (f16 has "
-                            "the same nominal rate)" if peaks.get("bf16_tflops") else
-                            "of fallback: 1.9 PFLOP/s bf16 burst"),
-            "warp_mma_f16_peak_tflops": round(2.0 * mma_peak / 1e12, 1),
-            "flops_per_call": 2 * ops[dom], "launches_per_call": launches_of[dom],
-            "ms_per_call": round(dom_ms, 4),
-            "traffic": NCU_TRAFFIC_BYTES.get(kernel_of(dom, tuned)),
-        }
-    else:
-        achieved = ops[dom] / (dom_ms * 1e-3) / 1e12
-        peak = (lop3_peak if PIPE_OF[dom] == "lop3" else imad_peak) / 1e12
-        roofline = {
-            "bound": "alu", "kernel": kernel_of(dom, tuned), "phase": dom, "pipe": PIPE_OF[dom],
+    # roofline of every counted phase (phase time from the library's events,
+    # algorithmic work per call): the integer-pipe bound for the divsteps and
+    # the CUDA-core products, the tensor bound for products on the tensor
+    # cores.  "roofline" is the longest phase on the critical path; the R/3
+    # phase runs beside the tree (auxiliary stream) unless its overlap is 0.
+    K = forest_roots(B, tuned.get("roots", 1))
+    r3m = tuned.get("r3_mode", 0)
+    ops = ops_per_call(B, K, r3m)
+    Lk = 0
+    n = B // K
+    while n > 1:
+        n = (n + 1) // 2
+        Lk += 1
+    launches_of = {"r3_inv": 1 if r3m == 0 else 2 * Lk + 3, "tree_up": Lk, "tree_down": Lk,
+                   "h_encode": 1, "root_inv": 1}
+    tensor_phases = TENSOR_PHASES + (("r3_inv",) if r3m else ())
+
+    def roofline_of(ph):
+        ms = phase.get(ph, 0.0)
+        if ms <= 0:
+            return None
+        if tuned.get("rq_engine") == 1 and ph in tensor_phases:
+            achieved = 2.0 * ops[ph] / (ms * 1e-3) / 1e12  # TFLOP/s of the p^2 products
+            peak = peaks.get("bf16_tflops") or 1900.0
+            return {
+                "bound": "tensor", "kernel": kernel_of(ph, tuned), "phase": ph,
+                "pipe": "tensor (mma.sync f16, f32 accumulate)",
+                "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4),
+                "peak_source": ("of measured: dense bf16 GEMM burst in MEASURED_PEAKS.json (f16 "
+                                "has the same nominal rate)" if peaks.get("bf16_tflops") else
+                                "of fallback: 1.9 PFLOP/s bf16 burst"),
+                "warp_mma_f16_peak_tflops": round(2.0 * mma_peak / 1e12, 1),
+                "flops_per_call": 2 * ops[ph], "launches_per_call": launches_of[ph],
+                "ms_per_call": round(ms, 4),
+                "traffic": NCU_TRAFFIC_BYTES.get(kernel_of(ph, tuned)),
+            }
+        achieved = ops[ph] / (ms * 1e-3) / 1e12
+        peak = (lop3_peak if PIPE_OF[ph] == "lop3" else imad_peak) / 1e12
+        return {
+            "bound": "alu", "kernel": kernel_of(ph, tuned), "phase": ph, "pipe": PIPE_OF[ph],
             "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
             "frac": round(achieved / peak, 4),
             "peak_source": "measured on this GPU by snt_measure_int_peak (%s stream, %d SMs)"
-                           % (PIPE_OF[dom].upper(), sms),
-            "ops_per_call": ops[dom], "launches_per_call": launches_of[dom],
-            "ms_per_call": round(dom_ms, 4),
-            "traffic": NCU_TRAFFIC_BYTES.get(kernel_of(dom, tuned)),
+                           % (PIPE_OF[ph].upper(), sms),
+            "ops_per_call": ops[ph], "launches_per_call": launches_of[ph],
+            "ms_per_call": round(ms, 4),
+            "traffic": NCU_TRAFFIC_BYTES.get(kernel_of(ph, tuned)),
         }
+
+    phase_roofline = {ph: roofline_of(ph) for ph in ops}
+    critical = [ph for ph in ops if ph != "r3_inv" or tuned.get("r3_overlap", 1) == 0]
+    dom = max(critical, key=lambda ph: phase.get(ph, 0.0))
+    roofline = dict(phase_roofline[dom])
+    roofline["roots"] = K
 
     # serving loop: Poisson handshakes (encapsulation, then decapsulation of
     # the same items), log-uniform sizes in [1, 64], key pool refilled in
@@ -365,6 +431,7 @@ def run_ours(args):
                            "warp_mma_f16_macs": round(mma_peak / 1e12, 3),
                            "sms": sms},
         "roofline": roofline,
+        "phase_roofline": phase_roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_rate, 1), "unit": "keys/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": B * (pkb + skb)},
