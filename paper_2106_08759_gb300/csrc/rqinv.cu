@@ -135,6 +135,21 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 // and runs the divsteps of chunk c + 1, so a chunk costs about the larger of
 // the two.  One barrier per chunk, ceil((2p-1)/31) chunks.
 //
+// Live extents.  A chunk's matrix entries have degree at most m, so F', G'
+// are zero wherever F and G are (index i of F' reads F at i + m - k, k <= m),
+// and V', R' reach at most m + 1 past V and R.  The block keeps the extent
+// of each state (one past the highest nonzero coefficient of F or G, and of
+// V or R, found by the appliers as they write) and computes only the live
+// outputs, zeroing what the older state left above them in the target
+// buffer.  F, G shrink while V, R grow, their extents summing to about
+// p + 2, so a chunk applies the matrix to about p + 34 coefficients rather
+// than to four full-length polynomials.  The live outputs are cut into
+// items of NOUT consecutive coefficients of one pair ((F', G') or (V', R')),
+// one item per applier thread in one code path for both pairs, so that a
+// warp holding items of both pairs does not diverge.  Applier warps avoid
+// the warp ids that share the leader's scheduler (warp w issues on
+// scheduler w % 4), so the leader's serial chain keeps a scheduler to itself.
+//
 // Ranges: inside the leader's steps values are lazily reduced to [-q, 2q)
 // (G(0) = 0 mod q iff G(0) is -q, 0 or q); the matrix and the state are
 // centred between chunks, so a 64-term application sum stays below 2^31.
@@ -142,17 +157,15 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 template <int P> struct JumpGeo {
     static constexpr int M = 31;                        // steps per chunk
     static constexpr int OFF = 32;                      // zero margin below index 0
-    static constexpr int TILES = (P + 1 + 7) / 8;       // 8 outputs per applier thread
-    static constexpr int NAPP = (TILES + 31) / 32 * 32; // applier threads
-    static constexpr int NT = 32 + NAPP;                // + the leader warp
-    static constexpr int LEN = OFF + 8 * TILES + 40;    // logical slots per polynomial
-    static constexpr int PLEN = LEN + LEN / 8 + 1;      // physical slots (one pad per 8)
+    static constexpr int NWA = 6;                       // applier warps (ids 1-3, 5-7)
+    static constexpr int NA = 32 * NWA;                 // applier threads
+    // outputs per item: the fewest that keep the items of the widest chunk
+    // (about p + 34 outputs, plus rounding of both pairs) within NA
+    static constexpr int NOUT = (P + 34 + 3) / 4 + 2 <= NA ? 4 : 5;
+    static constexpr int NW = 8;                        // leader, 6 appliers, 1 idle
+    static constexpr int NT = 32 * NW;
+    static constexpr int LEN = OFF + P + 1 + NOUT + 40; // slots per polynomial
 };
-
-// Physical slot of logical slot i: one padding word after every 8, so the
-// applier threads (8 consecutive outputs each) read banks 9 words apart,
-// i.e. 32 distinct banks per warp instead of 4.
-__device__ __forceinline__ int slot(int i) { return i + (i >> 3); }
 
 template <int Q> __device__ __forceinline__ bool is_zero_lazy(int x) {  // x in [-Q, 2Q)
     return x == 0 || x == Q || x == -Q;
@@ -160,35 +173,46 @@ template <int Q> __device__ __forceinline__ bool is_zero_lazy(int x) {  // x in 
 
 // The leader's chunk: m divsteps from (fl, gl) (lane i = coefficient i),
 // matrix returned centred in (u, v, w, z) (lane k = coefficient k).
+//
+// Each step forms the new G row as f0 g - g0 f from the values before the
+// swap. When the step swaps, that is minus the divstep's new G (Section 3's
+// divstep sends (f, g) to (g, (g0 f - f0 g)/x)), so a row of the returned
+// matrix may differ from the divstep matrix's row by a sign. Nothing
+// downstream depends on that sign: the swap test looks only at delta and
+// whether g0 is zero, F and V (G and R) are always updated by the same row,
+// and the inverse is V / F(0) at the end. Dropping the sign takes the swap
+// off the step's dependency chain, which is then the product, the
+// reduction and one shuffle.
+//
+// Lane 31 of G after the shift keeps its own value instead of the unknown
+// coefficient 32: step s reads only coefficient 0, which depends on
+// coefficients 0..s of the chunk's input, so the error never reaches it
+// within 31 steps. The matrix entries have degree at most s at step s, so
+// lane 31 of u and v is zero before every shift and a rotation by one lane
+// is the multiplication by x.
 template <int Q>
 __device__ __forceinline__ void leader_chunk(int m, int &delta, int fl, int gl, int &u, int &v,
                                              int &w, int &z) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, from = (lane + 31) & 31;
     u = (lane == 0); v = 0; w = 0; z = (lane == 0);
     int f0 = __shfl_sync(0xffffffffu, fl, 0);
     int g0 = __shfl_sync(0xffffffffu, gl, 0);
     for (int s = 0; s < m; ++s) {
-        if (delta > 0 && !is_zero_lazy<Q>(g0)) {  // warp-uniform
-            int t = fl; fl = gl; gl = t;
-            t = u; u = w; w = t;
-            t = v; v = z; z = t;
-            t = f0; f0 = g0; g0 = t;
-            delta = -delta;
-        }
-        ++delta;
+        const int ng = lazy_red<Q>(f0 * gl - g0 * fl);
         const int nw = lazy_red<Q>(f0 * w - g0 * u);
         const int nz = lazy_red<Q>(f0 * z - g0 * v);
-        const int ng = lazy_red<Q>(f0 * gl - g0 * fl);
-        u = __shfl_up_sync(0xffffffffu, u, 1);
-        v = __shfl_up_sync(0xffffffffu, v, 1);
-        if (lane == 0) { u = 0; v = 0; }
+        const bool sw = (delta > 0) & !is_zero_lazy<Q>(g0);  // warp-uniform
+        delta = (sw ? -delta : delta) + 1;
+        fl = sw ? gl : fl;
+        f0 = sw ? g0 : f0;
+        u = __shfl_sync(0xffffffffu, sw ? w : u, from);
+        v = __shfl_sync(0xffffffffu, sw ? z : v, from);
         w = nw;
         z = nz;
-        // next G(0) is coefficient 1 of the updated G: broadcast it directly,
+        // next G(0) is coefficient 1 of the new G: broadcast it directly,
         // off the path of the full shift
         g0 = __shfl_sync(0xffffffffu, ng, 1);
         gl = __shfl_down_sync(0xffffffffu, ng, 1);
-        if (lane == 31) gl = 0;
     }
     u = cmod<Q>(u); v = cmod<Q>(v); w = cmod<Q>(w); z = cmod<Q>(z);
 }
@@ -200,10 +224,13 @@ __global__ void __launch_bounds__(JumpGeo<P>::NT)
 k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_stride,
               int32_t *__restrict__ okv, int *__restrict__ err, int err_bit, const int *idx) {
     using JG = JumpGeo<P>;
-    constexpr int LEN = JG::LEN, OFF = JG::OFF, NT = JG::NT;
+    constexpr int LEN = JG::LEN, OFF = JG::OFF, NT = JG::NT, NOUT = JG::NOUT;
     constexpr int NCH = (2 * P - 1 + JG::M - 1) / JG::M;
-    __shared__ int st[2][4][JG::PLEN];  // [buffer][F, G, V, R][slot(index + OFF)]
+    __shared__ int st[2][4][LEN];       // [buffer][F, G, V, R][index + OFF]
     __shared__ int mat[2][4][34];       // [buffer][u, v, w, z][1 + coefficient], zero at 0 and 33
+    // extents of the state after chunk c - 1 in ext[c % 4]: [0] F, G and
+    // [1] V, R (one past the highest nonzero coefficient)
+    __shared__ int ext[4][2];
     __shared__ int s_ok;
     const int e = blockIdx.x;
     if (e >= n) return;
@@ -211,22 +238,25 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     const bool leader = tid < 32;
     const int row = idx ? idx[e] : e;
     const int16_t *a = in + (size_t)row * in_stride;
-    for (int i = tid; i < 2 * 4 * JG::PLEN; i += NT) (&st[0][0][0])[i] = 0;
+    for (int i = tid; i < 2 * 4 * LEN; i += NT) (&st[0][0][0])[i] = 0;
     for (int i = tid; i < 2 * 4 * 34; i += NT) (&mat[0][0][0])[i] = 0;
+    if (tid < 8) (&ext[0][0])[tid] = 0;
     __syncthreads();
-    for (int i = tid; i < P; i += NT) st[0][1][slot(OFF + i)] = (int)a[P - 1 - i];
+    for (int i = tid; i < P; i += NT) st[0][1][OFF + i] = (int)a[P - 1 - i];
     if (tid == 0) {
-        st[0][0][slot(OFF)] = 1;
-        st[0][0][slot(OFF + P - 1)] = -1;
-        st[0][0][slot(OFF + P)] = -1;
-        st[0][3][slot(OFF)] = 1;
+        st[0][0][OFF] = 1;
+        st[0][0][OFF + P - 1] = -1;
+        st[0][0][OFF + P] = -1;
+        st[0][3][OFF] = 1;
+        ext[0][0] = P + 1;
+        ext[0][1] = 1;
     }
     __syncthreads();
     int delta = 1;  // leader only
     if (leader) {
         int u, v, w, z;
-        leader_chunk<Q>(min(JG::M, 2 * P - 1), delta, st[0][0][slot(OFF + lane)],
-                        st[0][1][slot(OFF + lane)], u, v, w, z);
+        leader_chunk<Q>(min(JG::M, 2 * P - 1), delta, st[0][0][OFF + lane], st[0][1][OFF + lane],
+                        u, v, w, z);
         mat[0][0][1 + lane] = u; mat[0][1][1 + lane] = v;
         mat[0][2][1 + lane] = w; mat[0][3][1 + lane] = z;
     }
@@ -234,16 +264,16 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     int cur = 0;
     for (int c = 0; c < NCH; ++c) {
         const int m = min(JG::M, 2 * P - 1 - c * JG::M);
-        const int *F = st[cur][0], *G = st[cur][1], *V = st[cur][2], *R = st[cur][3];
         const int(*A)[34] = mat[c & 1];
         if (leader) {
             if (c + 1 < NCH) {
                 // low 32 coefficients of F', G' (lane i), then chunk c + 1
+                const int *F = st[cur][0], *G = st[cur][1];
                 int af = 0, ag = 0;
                 const int hi = OFF + lane + m;
 #pragma unroll 8
                 for (int k = 0; k < 32; ++k) {
-                    const int fv = F[slot(hi - k)], gv = G[slot(hi - k)];
+                    const int fv = F[hi - k], gv = G[hi - k];
                     af += A[0][1 + k] * fv + A[1][1 + k] * gv;
                     ag += A[2][1 + k] * fv + A[3][1 + k] * gv;
                 }
@@ -256,106 +286,84 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
             } else if (lane == 0) {
                 s_ok = (delta == 0);
             }
-        } else {
-            const int tile = tid - 32;
-            if (tile < JG::TILES) {
-                const int i0 = 8 * tile;
-                int *F2 = st[cur ^ 1][0], *G2 = st[cur ^ 1][1], *V2 = st[cur ^ 1][2], *R2 = st[cur ^ 1][3];
-                // F' = (u F + v G) / x^m, G' = (w F + z G) / x^m : index i + m - k
-                {
-                    int aF[8], aG[8], fhi[8], ghi[8];
+        } else if ((tid >> 5) & 3) {
+            const int w = tid >> 5, ai = w - 1 - (w - 1) / 4;
+            const int at = 32 * ai + lane;
+            // live ranges of the outputs and what the target buffer held
+            const int rfg = ext[c & 3][0], rvr = min(ext[c & 3][1] + m + 1, P + 1);
+            const int ofg = ext[(c + 3) & 3][0], ovr = ext[(c + 3) & 3][1];
+            int *T = &st[cur ^ 1][0][0];
+            for (int i = rfg + at; i < ofg; i += JG::NA) { T[OFF + i] = 0; T[LEN + OFF + i] = 0; }
+            for (int i = rvr + at; i < ovr; i += JG::NA) {
+                T[2 * LEN + OFF + i] = 0; T[3 * LEN + OFF + i] = 0;
+            }
+            if (at == 0) { ext[(c + 2) & 3][0] = 0; ext[(c + 2) & 3][1] = 0; }
+            const int nfg = (rfg + NOUT - 1) / NOUT, nit = nfg + (rvr + NOUT - 1) / NOUT;
+            int top_fg = 0, top_vr = 0;
+            for (int it = at; it < nit; it += JG::NA) {
+                // pair 0: F' = (u F + v G) / x^m, G' = (w F + z G) / x^m, inputs at i + m - k
+                // pair 1: V' = u V + (v/x) R, R' = (x w) V + z R, inputs at i - k
+                const int pr = it >= nfg;
+                const int i0 = NOUT * (pr ? it - nfg : it), r = pr ? rvr : rfg;
+                const int *X = st[cur][2 * pr], *Y = st[cur][2 * pr + 1];
+                const int *a0 = &A[0][1], *a1 = &A[1][1 + pr], *a2 = &A[2][1 - pr], *a3 = &A[3][1];
+                const int b = OFF + i0 + (pr ? 0 : m);
+                int o1[NOUT], o2[NOUT], xh[NOUT], yh[NOUT];
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        aF[t] = 0; aG[t] = 0;
-                        fhi[t] = F[slot(OFF + i0 + m + t)];
-                        ghi[t] = G[slot(OFF + i0 + m + t)];
-                    }
-#pragma unroll 1
-                    for (int kb = 0; kb < 32; kb += 8) {
-                        const int b0 = OFF + i0 + m - kb;
-                        int flo[8], glo[8], uu[8], vv[8], ww[8], zz[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            flo[j] = F[slot(b0 - 8 + j)];
-                            glo[j] = G[slot(b0 - 8 + j)];
-                            uu[j] = A[0][1 + kb + j];
-                            vv[j] = A[1][1 + kb + j];
-                            ww[j] = A[2][1 + kb + j];
-                            zz[j] = A[3][1 + kb + j];
-                        }
-#pragma unroll
-                        for (int kk = 0; kk < 8; ++kk)
-#pragma unroll
-                            for (int t = 0; t < 8; ++t) {
-                                const int d = t - kk;
-                                const int fv = d >= 0 ? fhi[d] : flo[8 + d];
-                                const int gv = d >= 0 ? ghi[d] : glo[8 + d];
-                                aF[t] += uu[kk] * fv + vv[kk] * gv;
-                                aG[t] += ww[kk] * fv + zz[kk] * gv;
-                            }
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) { fhi[j] = flo[j]; ghi[j] = glo[j]; }
-                    }
-#pragma unroll
-                    for (int t = 0; t < 8; ++t)
-                        if (i0 + t <= P) {
-                            F2[slot(OFF + i0 + t)] = cmod<Q>(aF[t]);
-                            G2[slot(OFF + i0 + t)] = cmod<Q>(aG[t]);
-                        }
+                for (int t = 0; t < NOUT; ++t) {
+                    o1[t] = 0; o2[t] = 0;
+                    xh[t] = X[b + t]; yh[t] = Y[b + t];
                 }
-                // V' = u V + (v/x) R, R' = (x w) V + z R : index i - k
-                {
-                    int aV[8], aR[8], vhi[8], rhi[8];
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        aV[t] = 0; aR[t] = 0;
-                        vhi[t] = V[slot(OFF + i0 + t)];
-                        rhi[t] = R[slot(OFF + i0 + t)];
-                    }
 #pragma unroll 1
-                    for (int kb = 0; kb < 32; kb += 8) {
-                        const int b0 = OFF + i0 - kb;
-                        int vlo[8], rlo[8], uu[8], vs[8], ws[8], zz[8];
+                for (int kb = 0; kb < 32; kb += 8) {
+                    int xl[8], yl[8], c0[8], c1[8], c2[8], c3[8];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            vlo[j] = V[slot(b0 - 8 + j)];
-                            rlo[j] = R[slot(b0 - 8 + j)];
-                            uu[j] = A[0][1 + kb + j];
-                            vs[j] = A[1][2 + kb + j];  // v_{k+1}
-                            ws[j] = A[2][kb + j];      // w_{k-1}
-                            zz[j] = A[3][1 + kb + j];
-                        }
-#pragma unroll
-                        for (int kk = 0; kk < 8; ++kk)
-#pragma unroll
-                            for (int t = 0; t < 8; ++t) {
-                                const int d = t - kk;
-                                const int vv = d >= 0 ? vhi[d] : vlo[8 + d];
-                                const int rv = d >= 0 ? rhi[d] : rlo[8 + d];
-                                aV[t] += uu[kk] * vv + vs[kk] * rv;
-                                aR[t] += ws[kk] * vv + zz[kk] * rv;
-                            }
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) { vhi[j] = vlo[j]; rhi[j] = rlo[j]; }
+                    for (int j = 0; j < 8; ++j) {
+                        xl[j] = X[b - kb - 8 + j]; yl[j] = Y[b - kb - 8 + j];
+                        c0[j] = a0[kb + j]; c1[j] = a1[kb + j];
+                        c2[j] = a2[kb + j]; c3[j] = a3[kb + j];
                     }
 #pragma unroll
-                    for (int t = 0; t < 8; ++t)
-                        if (i0 + t <= P) {
-                            V2[slot(OFF + i0 + t)] = cmod<Q>(aV[t]);
-                            R2[slot(OFF + i0 + t)] = cmod<Q>(aR[t]);
+                    for (int kk = 0; kk < 8; ++kk)
+#pragma unroll
+                        for (int t = 0; t < NOUT; ++t) {
+                            const int d = t - kk;
+                            const int xv = d >= 0 ? xh[d] : xl[8 + d];
+                            const int yv = d >= 0 ? yh[d] : yl[8 + d];
+                            o1[t] += c0[kk] * xv + c1[kk] * yv;
+                            o2[t] += c2[kk] * xv + c3[kk] * yv;
                         }
+#pragma unroll
+                    for (int t = 0; t < NOUT; ++t) { xh[t] = xl[t]; yh[t] = yl[t]; }
                 }
+                int *X2 = st[cur ^ 1][2 * pr], *Y2 = st[cur ^ 1][2 * pr + 1];
+                int top = 0;
+#pragma unroll
+                for (int t = 0; t < NOUT; ++t)
+                    if (i0 + t < r) {
+                        const int v1 = cmod<Q>(o1[t]), v2 = cmod<Q>(o2[t]);
+                        X2[OFF + i0 + t] = v1;
+                        Y2[OFF + i0 + t] = v2;
+                        if (v1 | v2) top = i0 + t + 1;
+                    }
+                if (pr) top_vr = max(top_vr, top); else top_fg = max(top_fg, top);
+            }
+            top_fg = __reduce_max_sync(0xffffffffu, top_fg);
+            top_vr = __reduce_max_sync(0xffffffffu, top_vr);
+            if (lane == 0) {
+                atomicMax(&ext[(c + 1) & 3][0], top_fg);
+                atomicMax(&ext[(c + 1) & 3][1], top_vr);
             }
         }
         __syncthreads();
         cur ^= 1;
     }
     const bool ok = s_ok != 0;
-    const int f0 = freeze_lazy<Q>(st[cur][0][slot(OFF)]);
+    const int f0 = freeze_lazy<Q>(st[cur][0][OFF]);
     const int sc = ok ? inv_mod<Q>(f0) : 0;
     int16_t *o = out + (size_t)row * out_stride;
     for (int i = tid; i < P; i += NT) {
-        const int v = freeze_lazy<Q>(st[cur][2][slot(OFF + P - 1 - i)]);
+        const int v = freeze_lazy<Q>(st[cur][2][OFF + P - 1 - i]);
         o[i] = (int16_t)cmod<Q>(sc * v);
     }
     if (tid == 0) {
