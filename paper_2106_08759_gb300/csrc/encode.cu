@@ -215,30 +215,7 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
             }
             W[t] = v;
         }
-        uint64_t a = H[0], b = H[1], c = H[2], d = H[3], e = H[4], f = H[5], g = H[6], h = H[7];
-        // 80 rounds as 5 passes of a 16-round body: W indices stay static
-        // (registers) while the code stays small enough for the i-cache.
-#pragma unroll 1
-        for (int r = 0; r < 80; r += 16) {
-#pragma unroll
-            for (int tt = 0; tt < 16; ++tt) {
-                if (r > 0) {
-                    const uint64_t w15 = W[(tt + 1) & 15], w2 = W[(tt + 14) & 15];
-                    const uint64_t s0 = rotr(w15, 1) ^ rotr(w15, 8) ^ (w15 >> 7);
-                    const uint64_t s1 = rotr(w2, 19) ^ rotr(w2, 61) ^ (w2 >> 6);
-                    W[tt] += s0 + W[(tt + 9) & 15] + s1;
-                }
-                const uint64_t S1 = rotr(e, 14) ^ rotr(e, 18) ^ rotr(e, 41);
-                const uint64_t ch = (e & f) ^ (~e & g);
-                const uint64_t T1 = h + S1 + ch + c_sha512_k[r + tt] + W[tt];
-                const uint64_t S0 = rotr(a, 28) ^ rotr(a, 34) ^ rotr(a, 39);
-                const uint64_t mj = (a & b) ^ (a & c) ^ (b & c);
-                h = g; g = f; f = e; e = d + T1;
-                d = c; c = b; b = a; a = T1 + S0 + mj;
-            }
-        }
-        H[0] += a; H[1] += b; H[2] += c; H[3] += d;
-        H[4] += e; H[5] += f; H[6] += g; H[7] += h;
+        sha512_block(H, W);
     }
     const BatchDesc dk = key_batch(km, base + lane);
     uint8_t *out = dk.sk + (size_t)(base + lane - dk.key_base) * sk_bytes + hash_off;

@@ -21,20 +21,24 @@
 // 2tig + 1), (g + 8, same cols), (g, 2tig + 8, 2tig + 9), (g + 8, 2tig + 8,
 // 2tig + 9).  In T_D these are (E[x], E[x-1]), (E[x+8], E[x+7]),
 // (E[x-8], E[x-9]) and (E[x], E[x-1]) again, x = 16D + g - 2 tig + p - 1:
-// a table PE[x] holding the pair (E[x], E[x-1]) of each limb gives one
-// 128-bit shared load per register position, and no Toeplitz block is
+// a table PE[x] holding the pair (E[x], E[x-1]) of both limbs gives one
+// 64-bit shared load per register position, and no Toeplitz block is
 // materialised.  The B fragment of a block of a (pairs 2tig, 2tig + 1 and
-// 2tig + 8, 2tig + 9) is likewise one 128-bit plus one 64-bit load.
+// 2tig + 8, 2tig + 9) of both limbs is likewise one 128-bit load.
 //
 // Exactness.  fp16 holds integers up to 2048 exactly; centred residues reach
 // (q - 1) / 2 = 2583, so both operands are split into limbs
 //     x = 64 h + l,  h = floor((x + 32) / 64) in [-41, 41], l in [-32, 31],
-// and three limb products are accumulated (Karatsuba): P_hh = sum h h',
-// P_ll = sum l l', P_ss = sum (h + l)(h' + l').  Every product and every
-// partial sum is an integer below 16 * 73 * 73 * 54 < 2^24 in magnitude, so
-// the f32 accumulation is exact in any order; then
-//     row = 4096 P_hh + 64 (P_ss - P_hh - P_ll) + P_ll
-// is formed from the residues of the three sums mod q.
+// and the limb products are accumulated in three sums: P_hh = sum h h',
+// P_x = sum (h l' + l h') and P_ll = sum l l'.  Each is an integer below
+// 2 * 768 * 41 * 32 < 2^24 in magnitude, so the f32 accumulation is exact in
+// any order; then
+//     row = 4096 P_hh + 64 P_x + P_ll
+// is formed from the residues of the three sums mod q.  Four MMAs per step
+// rather than the three of Karatsuba's (h + l)(h' + l'): the loop is bound by
+// shared-memory wavefronts, and dropping the h + l limb from both tables
+// takes a step from 20 wavefronts and 12 tensor-pipe cycles (two products
+// per CTA) to 12 wavefronts and 16 cycles.
 //
 // Small operands.  A leaf of the tree is 3f with coefficients in {-3, 0, 3}:
 // its high limb is zero.  MODE_SA (vector side small) needs only
@@ -62,23 +66,20 @@ template <int P, int NT> struct MmaGeo {
     static constexpr int VBN = (NBLK + 2 * PADB) * 4;  // B records (block, tig)
 };
 
-// E side of one product: per x the pairs (E[x], E[x-1]) of the h, l and
-// h + l limbs (f16x2 words; .w unused), and the operand E is built from.
+// E side of one product: per x the pairs (E[x], E[x-1]) of the h and l
+// limbs (f16x2 words), and the operand E is built from.
 template <int P, int NT> struct MmaE {
     union {
-        uint4 pe[MmaGeo<P, NT>::PWN];
+        uint2 pe[MmaGeo<P, NT>::PWN];
         uint32_t pl[MmaGeo<P, NT>::PWN];  // MODE_SAE: the l pairs only
     } t;
     int16_t b[MmaGeo<P, NT>::AN];
 };
 // Vector side of one product: per (block, tig) the B words (h01, h89, l01,
-// l89) and (s01, s89), then (after the MMA loop) the staged row sums.
+// l89), then (after the MMA loop) the staged row sums.
 template <int P, int NT> struct MmaA {
     union {
-        struct {
-            uint4 hl[MmaGeo<P, NT>::VBN];
-            uint2 s[MmaGeo<P, NT>::VBN];
-        } v;
+        uint4 hl[MmaGeo<P, NT>::VBN];
         uint2 sl[MmaGeo<P, NT>::VBN];  // MODE_SA / MODE_SAE: the l words (l01, l89)
         int stage[MmaGeo<P, NT>::AN];
     } u;
@@ -145,9 +146,8 @@ __device__ __forceinline__ void mma_fill_a(const T *__restrict__ a, MmaA<P, NT> 
         int h[4], l[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) limbs64(v[u], h[u], l[u]);
-        s.u.v.hl[r] = make_uint4(h2_small(h[0], h[1]), h2_small(h[2], h[3]), h2_small(l[0], l[1]),
-                                 h2_small(l[2], l[3]));
-        s.u.v.s[r] = make_uint2(h2_small(h[0] + l[0], h[1] + l[1]), h2_small(h[2] + l[2], h[3] + l[3]));
+        s.u.hl[r] = make_uint4(h2_small(h[0], h[1]), h2_small(h[2], h[3]), h2_small(l[0], l[1]),
+                               h2_small(l[2], l[3]));
     }
 }
 
@@ -173,12 +173,12 @@ __device__ __forceinline__ void mma_fill_pe(MmaE<P, NT> &s, int tid, int nth) {
         int h0, l0, h1, l1;
         limbs64(e0, h0, l0);
         limbs64(e1, h1, l1);
-        s.t.pe[w] = make_uint4(h2_small(h0, h1), h2_small(l0, l1), h2_small(h0 + l0, h1 + l1), 0u);
+        s.t.pe[w] = make_uint2(h2_small(h0, h1), h2_small(l0, l1));
     }
 }
 
 // Tiles [T0, T0 + NT) of NPR products sharing one E side, by one warp:
-// accumulates the limb sums of every (tile, product): P_hh, P_ll, P_ss
+// accumulates the limb sums of every (tile, product): P_hh, P_x, P_ll
 // (MODE_GEN), P_1, P_2 (MODE_SA) or P (MODE_SAE).  A2 of step D + 1 is A1 of
 // step D (x advances by 16), so two table loads per step suffice.
 // ks / nks: this warp's share of the D range when a tile's sum is split over
@@ -221,11 +221,11 @@ __device__ __forceinline__ void mma_tiles(const MmaE<P, NT> &E, const MmaA<P, NT
         }
         return;
     }
-    const uint4 *pe = E.t.pe + x0;
-    uint4 A2 = pe[-8];
+    const uint2 *pe = E.t.pe + x0;
+    uint2 A2 = pe[-8];
 #pragma unroll 2
     for (int D = dlo; D <= dhi; ++D, pe += 16, rec -= 4) {
-        const uint4 A0 = pe[0], A1 = pe[8];
+        const uint2 A0 = pe[0], A1 = pe[8];
 #pragma unroll
         for (int tt = 0; tt < NT; ++tt)
 #pragma unroll
@@ -235,11 +235,11 @@ __device__ __forceinline__ void mma_tiles(const MmaE<P, NT> &E, const MmaA<P, NT
                     mma16816(acc[tt][pr][0], A0.x, A1.x, A2.x, A0.x, b.x, b.y);
                     mma16816(acc[tt][pr][1], A0.y, A1.y, A2.y, A0.y, b.x, b.y);
                 } else {
-                    const uint4 bhl = A[pr]->u.v.hl[rec + 32 * tt];
-                    const uint2 bs = A[pr]->u.v.s[rec + 32 * tt];
-                    mma16816(acc[tt][pr][0], A0.x, A1.x, A2.x, A0.x, bhl.x, bhl.y);
-                    mma16816(acc[tt][pr][1], A0.y, A1.y, A2.y, A0.y, bhl.z, bhl.w);
-                    mma16816(acc[tt][pr][2], A0.z, A1.z, A2.z, A0.z, bs.x, bs.y);
+                    const uint4 b = A[pr]->u.hl[rec + 32 * tt];
+                    mma16816(acc[tt][pr][0], A0.x, A1.x, A2.x, A0.x, b.x, b.y);  // h h'
+                    mma16816(acc[tt][pr][1], A0.x, A1.x, A2.x, A0.x, b.z, b.w);  // h l'
+                    mma16816(acc[tt][pr][1], A0.y, A1.y, A2.y, A0.y, b.x, b.y);  // l h'
+                    mma16816(acc[tt][pr][2], A0.y, A1.y, A2.y, A0.y, b.z, b.w);  // l l'
                 }
             }
         A2 = A1;
@@ -270,7 +270,7 @@ __device__ __forceinline__ void mma_ksplit_reduce(float (&acc)[NT][NPR][3][4], f
 }
 
 // Row sums of tiles [T0, T0 + NT) of product pr into A.u.stage (centred).
-// The caller must have synchronised every warp reading A.u.v since the loop.
+// The caller must have synchronised every warp reading A.u.hl since the loop.
 template <int P, int NT, int NPR, int MODE = MODE_GEN, int Q = Prm<P>::q>
 __device__ __forceinline__ void mma_stage(MmaA<P, NT> &A, int T0, int lane, int pr,
                                           const float (&acc)[NT][NPR][3][4]) {
@@ -287,7 +287,7 @@ __device__ __forceinline__ void mma_stage(MmaA<P, NT> &A, int T0, int lane, int 
             const int p1 = __float2int_rn(acc[tt][pr][1][c]);
             const int p2 = __float2int_rn(acc[tt][pr][2][c]);
             int v;
-            if (MODE == MODE_GEN) v = 4096 * cmod<Q>(p0) + 64 * cmod<Q>(p2 - p0 - p1) + cmod<Q>(p1);
+            if (MODE == MODE_GEN) v = 4096 * cmod<Q>(p0) + 64 * cmod<Q>(p1) + cmod<Q>(p2);
             else if (MODE == MODE_SA) v = 64 * p0 + p1;  // |P_1| <= 123 * 16 * NBLK, |P_2| < 2^24
             else v = p0;
             A.u.stage[j] = cmod<Q>(v);

@@ -198,23 +198,45 @@ __device__ __forceinline__ void leader_chunk(int m, int &delta, int fl, int gl, 
     int f0 = __shfl_sync(0xffffffffu, fl, 0);
     int g0 = __shfl_sync(0xffffffffu, gl, 0);
     for (int s = 0; s < m; ++s) {
+        // the chain: new G, then its shift and its coefficient 0 (read
+        // straight from lane 1) issued first; the rest of the step runs in
+        // the shuffles' shadow
         const int ng = lazy_red<Q>(f0 * gl - g0 * fl);
+        const int g0n = __shfl_sync(0xffffffffu, ng, 1);
+        const int gln = __shfl_down_sync(0xffffffffu, ng, 1);
         const int nw = lazy_red<Q>(f0 * w - g0 * u);
         const int nz = lazy_red<Q>(f0 * z - g0 * v);
         const bool sw = (delta > 0) & !is_zero_lazy<Q>(g0);  // warp-uniform
         delta = (sw ? -delta : delta) + 1;
         fl = sw ? gl : fl;
         f0 = sw ? g0 : f0;
-        u = __shfl_sync(0xffffffffu, sw ? w : u, from);
-        v = __shfl_sync(0xffffffffu, sw ? z : v, from);
+        // u, v (lazy, inside int16) shifted together as one packed word
+        const int uv = __shfl_sync(0xffffffffu, __byte_perm(sw ? w : u, sw ? z : v, 0x5410), from);
+        u = (uv << 16) >> 16;
+        v = uv >> 16;
         w = nw;
         z = nz;
-        // next G(0) is coefficient 1 of the new G: broadcast it directly,
-        // off the path of the full shift
-        g0 = __shfl_sync(0xffffffffu, ng, 1);
-        gl = __shfl_down_sync(0xffffffffu, ng, 1);
+        g0 = g0n;
+        gl = gln;
     }
     u = cmod<Q>(u); v = cmod<Q>(v); w = cmod<Q>(w); z = cmod<Q>(z);
+}
+
+// Eight consecutive matrix coefficients from a 16-byte aligned address.
+__device__ __forceinline__ void load8(int (&c)[8], const int *p) {
+    const int4 a = reinterpret_cast<const int4 *>(p)[0], b = reinterpret_cast<const int4 *>(p)[1];
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+}
+
+// Lane k's coefficients of the chunk matrix into the six rows: coefficient k
+// of u, v, w, z at 4 + k, v_k at 4 + (k - 1) of the v_{k+1} row and w_k at
+// 4 + (k + 1) of the w_{k-1} row. The slots those rows leave unwritten (v_32
+// and w_{-1}) stay zero from the block's start.
+__device__ __forceinline__ void put_matrix(int (*An)[40], int lane, int u, int v, int w, int z) {
+    An[0][4 + lane] = u; An[1][4 + lane] = v;
+    An[2][4 + lane] = w; An[3][4 + lane] = z;
+    An[4][3 + lane] = v; An[5][5 + lane] = w;
 }
 
 // Q: the coefficient modulus (q: R/q; 3: R/3, for the root inversions of
@@ -227,7 +249,10 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     constexpr int LEN = JG::LEN, OFF = JG::OFF, NT = JG::NT, NOUT = JG::NOUT;
     constexpr int NCH = (2 * P - 1 + JG::M - 1) / JG::M;
     __shared__ int st[2][4][LEN];       // [buffer][F, G, V, R][index + OFF]
-    __shared__ int mat[2][4][34];       // [buffer][u, v, w, z][1 + coefficient], zero at 0 and 33
+    // chunk matrix [buffer][row][4 + k]: rows u, v, w, z and the shifted
+    // rows v_{k+1}, w_{k-1} used by (V', R'); 16-byte rows for vector loads,
+    // zero outside k = 0..31
+    __shared__ __align__(16) int mat[2][6][40];
     // extents of the state after chunk c - 1 in ext[c % 4]: [0] F, G and
     // [1] V, R (one past the highest nonzero coefficient)
     __shared__ int ext[4][2];
@@ -239,7 +264,7 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     const int row = idx ? idx[e] : e;
     const int16_t *a = in + (size_t)row * in_stride;
     for (int i = tid; i < 2 * 4 * LEN; i += NT) (&st[0][0][0])[i] = 0;
-    for (int i = tid; i < 2 * 4 * 34; i += NT) (&mat[0][0][0])[i] = 0;
+    for (int i = tid; i < 2 * 6 * 40; i += NT) (&mat[0][0][0])[i] = 0;
     if (tid < 8) (&ext[0][0])[tid] = 0;
     __syncthreads();
     for (int i = tid; i < P; i += NT) st[0][1][OFF + i] = (int)a[P - 1 - i];
@@ -257,32 +282,36 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
         int u, v, w, z;
         leader_chunk<Q>(min(JG::M, 2 * P - 1), delta, st[0][0][OFF + lane], st[0][1][OFF + lane],
                         u, v, w, z);
-        mat[0][0][1 + lane] = u; mat[0][1][1 + lane] = v;
-        mat[0][2][1 + lane] = w; mat[0][3][1 + lane] = z;
+        put_matrix(mat[0], lane, u, v, w, z);
     }
     __syncthreads();
     int cur = 0;
     for (int c = 0; c < NCH; ++c) {
         const int m = min(JG::M, 2 * P - 1 - c * JG::M);
-        const int(*A)[34] = mat[c & 1];
+        const int(*A)[40] = mat[c & 1];
         if (leader) {
             if (c + 1 < NCH) {
                 // low 32 coefficients of F', G' (lane i), then chunk c + 1
                 const int *F = st[cur][0], *G = st[cur][1];
-                int af = 0, ag = 0;
+                int af[2] = {0, 0}, ag[2] = {0, 0};
                 const int hi = OFF + lane + m;
-#pragma unroll 8
-                for (int k = 0; k < 32; ++k) {
-                    const int fv = F[hi - k], gv = G[hi - k];
-                    af += A[0][1 + k] * fv + A[1][1 + k] * gv;
-                    ag += A[2][1 + k] * fv + A[3][1 + k] * gv;
+#pragma unroll
+                for (int kb = 0; kb < 32; kb += 8) {
+                    int c0[8], c1[8], c2[8], c3[8];
+                    load8(c0, &A[0][4 + kb]); load8(c1, &A[1][4 + kb]);
+                    load8(c2, &A[2][4 + kb]); load8(c3, &A[3][4 + kb]);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int fv = F[hi - kb - j], gv = G[hi - kb - j];
+                        af[j & 1] += c0[j] * fv + c1[j] * gv;
+                        ag[j & 1] += c2[j] * fv + c3[j] * gv;
+                    }
                 }
                 const int m1 = min(JG::M, 2 * P - 1 - (c + 1) * JG::M);
                 int u, v, w, z;
-                leader_chunk<Q>(m1, delta, cmod<Q>(af), cmod<Q>(ag), u, v, w, z);
-                int(*An)[34] = mat[(c + 1) & 1];
-                An[0][1 + lane] = u; An[1][1 + lane] = v;
-                An[2][1 + lane] = w; An[3][1 + lane] = z;
+                leader_chunk<Q>(m1, delta, cmod<Q>(af[0] + af[1]), cmod<Q>(ag[0] + ag[1]), u, v, w,
+                                z);
+                put_matrix(mat[(c + 1) & 1], lane, u, v, w, z);
             } else if (lane == 0) {
                 s_ok = (delta == 0);
             }
@@ -306,7 +335,8 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
                 const int pr = it >= nfg;
                 const int i0 = NOUT * (pr ? it - nfg : it), r = pr ? rvr : rfg;
                 const int *X = st[cur][2 * pr], *Y = st[cur][2 * pr + 1];
-                const int *a0 = &A[0][1], *a1 = &A[1][1 + pr], *a2 = &A[2][1 - pr], *a3 = &A[3][1];
+                const int *a0 = &A[0][4], *a1 = &A[pr ? 4 : 1][4], *a2 = &A[pr ? 5 : 2][4],
+                          *a3 = &A[3][4];
                 const int b = OFF + i0 + (pr ? 0 : m);
                 int o1[NOUT], o2[NOUT], xh[NOUT], yh[NOUT];
 #pragma unroll
@@ -318,11 +348,8 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
                 for (int kb = 0; kb < 32; kb += 8) {
                     int xl[8], yl[8], c0[8], c1[8], c2[8], c3[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        xl[j] = X[b - kb - 8 + j]; yl[j] = Y[b - kb - 8 + j];
-                        c0[j] = a0[kb + j]; c1[j] = a1[kb + j];
-                        c2[j] = a2[kb + j]; c3[j] = a3[kb + j];
-                    }
+                    for (int j = 0; j < 8; ++j) { xl[j] = X[b - kb - 8 + j]; yl[j] = Y[b - kb - 8 + j]; }
+                    load8(c0, a0 + kb); load8(c1, a1 + kb); load8(c2, a2 + kb); load8(c3, a3 + kb);
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk)
 #pragma unroll

@@ -31,6 +31,11 @@ static __constant__ uint64_t c_sha512_k[80] = {
 __device__ __forceinline__ uint64_t rotr(uint64_t x, int n) { return (x >> n) | (x << (64 - n)); }
 
 // One 128-byte block: W[16] holds the big-endian message words on entry.
+//
+// The round is arranged for a short dependency chain: h + K_t + W_t and
+// d + h + K_t + W_t do not depend on the previous round's new e and a, so
+// they are formed early and the new e is one three-input add after Sigma1(e)
+// and Ch; the new a adds Sigma0(a) + Maj to the same partial sum.
 __device__ __forceinline__ void sha512_block(uint64_t (&H)[8], uint64_t (&W)[16]) {
     uint64_t a = H[0], b = H[1], c = H[2], d = H[3], e = H[4], f = H[5], g = H[6], h = H[7];
 #pragma unroll 1
@@ -43,13 +48,15 @@ __device__ __forceinline__ void sha512_block(uint64_t (&H)[8], uint64_t (&W)[16]
                 const uint64_t s1 = rotr(w2, 19) ^ rotr(w2, 61) ^ (w2 >> 6);
                 W[tt] += s0 + W[(tt + 9) & 15] + s1;
             }
+            const uint64_t hkw = h + (c_sha512_k[r + tt] + W[tt]);
+            const uint64_t dhkw = d + hkw;
             const uint64_t S1 = rotr(e, 14) ^ rotr(e, 18) ^ rotr(e, 41);
             const uint64_t ch = (e & f) ^ (~e & g);
-            const uint64_t T1 = h + S1 + ch + c_sha512_k[r + tt] + W[tt];
             const uint64_t S0 = rotr(a, 28) ^ rotr(a, 34) ^ rotr(a, 39);
             const uint64_t mj = (a & b) ^ (a & c) ^ (b & c);
-            h = g; g = f; f = e; e = d + T1;
-            d = c; c = b; b = a; a = T1 + S0 + mj;
+            const uint64_t t1 = hkw + S1 + ch;
+            h = g; g = f; f = e; e = dhkw + S1 + ch;
+            d = c; c = b; b = a; a = t1 + (S0 + mj);
         }
     }
     H[0] += a; H[1] += b; H[2] += c; H[3] += d;
