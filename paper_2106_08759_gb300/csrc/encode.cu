@@ -87,8 +87,8 @@ k_finalize_mma(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__rest
     uint32_t(*Rb)[G::pad] = reinterpret_cast<uint32_t(*)[G::pad]>(sm);  // over E
     uint8_t *ob = sm + 2 * G::pad * sizeof(uint32_t);
     for (int j = threadIdx.x; j < P; j += nth) {
-        int v = (j == 0) ? A.u.stage[0] - A.u.stage[P - 1] + (int)A.a[0] * bl
-                         : A.u.stage[j] + (int)A.a[j] * bl;
+        int v = (j == 0) ? A.u.stage[0] - A.u.stage[stage_slot(P - 1)] + (int)A.a[0] * bl
+                         : A.u.stage[stage_slot(j)] + (int)A.a[j] * bl;
         Rb[0][j] = (uint32_t)(cmod<G::q>(v) + G::half);
     }
     __syncthreads();

@@ -81,10 +81,14 @@ template <int P, int NT> struct MmaA {
     union {
         uint4 hl[MmaGeo<P, NT>::VBN];
         uint2 sl[MmaGeo<P, NT>::VBN];  // MODE_SA / MODE_SAE: the l words (l01, l89)
-        int stage[MmaGeo<P, NT>::AN];
+        int stage[MmaGeo<P, NT>::AN + MmaGeo<P, NT>::AN / 4];  // at stage_slot(j)
     } u;
     int16_t a[MmaGeo<P, NT>::AN];
 };
+
+// Slot of row sum j in the staging array: 8 padding words after every 32,
+// so the four lanes of a fragment column (rows 32 apart) hit distinct banks.
+__device__ __forceinline__ int stage_slot(int j) { return j + 8 * (j >> 5); }
 
 __device__ __forceinline__ void limbs64(int x, int &h, int &l) {
     h = (x + 32) >> 6;
@@ -159,21 +163,25 @@ __device__ __forceinline__ void mma_fill_b(const int16_t *__restrict__ b, MmaE<P
     for (int k = tid; k < M::AN; k += nth) s.b[k] = k < M::p ? b[k] : 0;
 }
 
-// E side, step 2 (after a barrier): the limb pair table.
+// E side, step 2 (after a barrier): the limb pair table, two neighbouring
+// entries per thread (three E values, one 16-byte store).
 template <int P, int NT, int MODE = MODE_GEN, int Q = Prm<P>::q>
 __device__ __forceinline__ void mma_fill_pe(MmaE<P, NT> &s, int tid, int nth) {
     using M = MmaGeo<P, NT>;
-    for (int w = tid; w < M::PWN; w += nth) {
+    static_assert(M::PWN % 2 == 0, "pair table of even length");
+    for (int w = 2 * tid; w < M::PWN; w += 2 * nth) {
         const int x = w + M::XLO;
-        const int e0 = mma_E<P, Q>(s.b, x), e1 = mma_E<P, Q>(s.b, x - 1);
+        const int em = mma_E<P, Q>(s.b, x - 1), e0 = mma_E<P, Q>(s.b, x), e1 = mma_E<P, Q>(s.b, x + 1);
         if (MODE == MODE_SAE) {  // small E: the value is its own l limb
-            s.t.pl[w] = h2_small(e0, e1);
+            *reinterpret_cast<uint2 *>(&s.t.pl[w]) = make_uint2(h2_small(e0, em), h2_small(e1, e0));
             continue;
         }
-        int h0, l0, h1, l1;
+        int hm, lm, h0, l0, h1, l1;
+        limbs64(em, hm, lm);
         limbs64(e0, h0, l0);
         limbs64(e1, h1, l1);
-        s.t.pe[w] = make_uint2(h2_small(h0, h1), h2_small(l0, l1));
+        *reinterpret_cast<uint4 *>(&s.t.pe[w]) =
+            make_uint4(h2_small(h0, hm), h2_small(l0, lm), h2_small(h1, h0), h2_small(l1, l0));
     }
 }
 
@@ -290,22 +298,35 @@ __device__ __forceinline__ void mma_stage(MmaA<P, NT> &A, int T0, int lane, int 
             if (MODE == MODE_GEN) v = 4096 * cmod<Q>(p0) + 64 * cmod<Q>(p1) + cmod<Q>(p2);
             else if (MODE == MODE_SA) v = 64 * p0 + p1;  // |P_1| <= 123 * 16 * NBLK, |P_2| < 2^24
             else v = p0;
-            A.u.stage[j] = cmod<Q>(v);
+            A.u.stage[stage_slot(j)] = cmod<Q>(v);
         }
 }
 
 // Final outputs c_0 .. c_{nout-1} (centred int16, zero beyond p) from the
-// staged rows, by threads tid = 0 .. nth-1.
+// staged rows, by threads tid = 0 .. nth-1; two outputs per thread when c is
+// 4-byte aligned and nout even.
 template <int P, int NT, int Q = Prm<P>::q>
 __device__ __forceinline__ void mma_finish(const MmaA<P, NT> &A, int blast,
                                            int16_t *__restrict__ c, int nout, int tid, int nth) {
     using M = MmaGeo<P, NT>;
-    for (int j = tid; j < nout; j += nth) {
-        int v = 0;
-        if (j == 0) v = cmod<Q>(A.u.stage[0] - A.u.stage[M::p - 1] + (int)A.a[0] * blast);
-        else if (j < M::p) v = cmod<Q>(A.u.stage[j] + (int)A.a[j] * blast);
-        c[j] = (int16_t)v;
+    auto out = [&](int j, int r) -> int {
+        if (j >= M::p) return 0;
+        if (j == 0) r -= A.u.stage[stage_slot(M::p - 1)];
+        return cmod<Q>(r + (int)A.a[j] * blast);
+    };
+    if (((reinterpret_cast<uintptr_t>(c) & 3) == 0) && (nout % 2 == 0)) {
+        for (int j = 2 * tid; j < nout; j += 2 * nth) {
+            int v0 = 0, v1 = 0;
+            if (j < M::AN) {
+                const int2 r = *reinterpret_cast<const int2 *>(&A.u.stage[stage_slot(j)]);
+                v0 = out(j, r.x);
+                v1 = out(j + 1, r.y);
+            }
+            *reinterpret_cast<uint32_t *>(c + j) = (uint32_t)(uint16_t)v0 | ((uint32_t)v1 << 16);
+        }
+        return;
     }
+    for (int j = tid; j < nout; j += nth) c[j] = (int16_t)(j < M::AN ? out(j, A.u.stage[stage_slot(j)]) : 0);
 }
 
 }  // namespace snt
