@@ -13,6 +13,8 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "toeplitz.cuh"
+#include <atomic>
+
 #include "sha512.cuh"
 #include "mixed.cuh"
 #include "mma_mul.cuh"
@@ -148,20 +150,39 @@ k_fixup(KeyMap km, const int *__restrict__ fix_count, const int *__restrict__ fi
 
 // ---------------------------------------------------------------------------
 // SHA-512 (FIPS 180-4) of 0x04 | pk, first 32 bytes into the secret key
-// (Hash_prefix(4, pk) of the NTRU Prime secret key).  One thread per key.
+// (Hash_prefix(4, pk) of the NTRU Prime secret key).
 // ---------------------------------------------------------------------------
 
 
 
-// One warp hashes 32 keys, one key per lane.  The 32 public keys of a warp
-// are consecutive rows, i.e. one contiguous span, copied to shared memory
-// with 16-byte loads when the span is 16-byte aligned (byte loads otherwise).
-// Lane j then reads its message 0x04 | pk_j byte by byte from there; the
-// padding (0x80, zeros, 128-bit big-endian bit length) is generated.
-__global__ void __launch_bounds__(32)
+// Named barriers between the two warps of the pk-hash kernel.
+__device__ __forceinline__ void nbar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Two warps hash 32 keys, one key per lane.  The 32 public keys are
+// consecutive rows, i.e. one contiguous span, copied to shared memory with
+// 16-byte loads when the span is 16-byte aligned (byte loads otherwise).
+//
+// A block's 80 rounds form one serial chain per key, and a single warp runs
+// the whole compression at about three cycles per instruction, so the work
+// is split by dependency: warp 1 (producer) reads the message 0x04 | pk_j of
+// its lane byte by byte (the padding 0x80, zeros and 128-bit big-endian bit
+// length generated), expands the schedule and writes W_t + K_t for the 80
+// rounds into one of two table slots; warp 0 (consumer) runs the rounds from
+// the table.  Named barriers 1, 2 mark slot 0, 1 full, 3, 4 mark it free
+// again; each is used in a fixed order by both warps, once per block.
+constexpr int kShaWkBytes = 2 * 80 * 32 * 8;
+
+__global__ void __launch_bounds__(64)
 k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
-    extern __shared__ __align__(16) uint8_t blk[];
-    const int lane = threadIdx.x;
+    extern __shared__ __align__(16) uint8_t sm[];
+    uint64_t(*wk)[80][32] = reinterpret_cast<uint64_t(*)[80][32]>(sm);  // [slot][round][key]
+    uint8_t *blk = sm + kShaWkBytes;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int base = blockIdx.x * 32;
     const int nkeys = min(32, B - base);
     const int nbytes = nkeys * pk_bytes;
@@ -169,7 +190,7 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
         for (int j = 0; j < nkeys; ++j) {
             const BatchDesc d = key_batch(km, base + j);
             const uint8_t *row = d.pk + (size_t)(base + j - d.key_base) * pk_bytes;
-            for (int b = lane; b < pk_bytes; b += 32) blk[j * pk_bytes + b] = row[b];
+            for (int b = tid; b < pk_bytes; b += 64) blk[j * pk_bytes + b] = row[b];
         }
     }
     const uint8_t *src = km.one.pk + (size_t)base * pk_bytes;
@@ -179,44 +200,69 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
         const int4 *s4 = reinterpret_cast<const int4 *>(src);
         int4 *d4 = reinterpret_cast<int4 *>(blk);
 #pragma unroll 4
-        for (int i = lane; i < n16; i += 32) d4[i] = s4[i];
+        for (int i = tid; i < n16; i += 64) d4[i] = s4[i];
         done = n16 * 16;
     }
-    for (int i = done + lane; i < nbytes; i += 32) blk[i] = src[i];
-    __syncwarp();
-    if (lane >= nkeys) return;
-    const uint8_t *row = blk + lane * pk_bytes;  // message byte pos (1 <= pos <= pk_bytes) = row[pos - 1]
+    for (int i = done + tid; i < nbytes; i += 64) blk[i] = src[i];
+    __syncthreads();
     const int len = pk_bytes + 1;
     const int nblk = (len + 1 + 16 + 127) / 128;
-    const uint64_t bitlen = (uint64_t)len * 8u;
+    if (warp == 1) {
+        // lanes past the last key repeat it; their digests are not stored
+        const uint8_t *row = blk + min(lane, nkeys - 1) * pk_bytes;  // byte pos (1..pk_bytes) at row[pos - 1]
+        const uint64_t bitlen = (uint64_t)len * 8u;
+        for (int b0 = 0; b0 < nblk; ++b0) {
+            const int slot = b0 & 1;
+            if (b0 >= 2) nbar_sync(3 + slot, 64);
+            uint64_t W[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int pos = 128 * b0 + 8 * t;
+                uint64_t v = 0;
+                if (pos >= 1 && pos + 8 <= len) {
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) v = (v << 8) | row[pos + b - 1];
+                } else {
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        const int q = pos + b;
+                        uint32_t byte = 0;
+                        if (q == 0) byte = 4u;
+                        else if (q < len) byte = row[q - 1];
+                        else if (q == len) byte = 0x80u;
+                        else if (q >= nblk * 128 - 8) byte = (uint32_t)(bitlen >> (8 * (nblk * 128 - 1 - q))) & 255u;
+                        v = (v << 8) | byte;
+                    }
+                }
+                W[t] = v;
+            }
+#pragma unroll 1
+            for (int r = 0; r < 80; r += 16) {
+#pragma unroll
+                for (int tt = 0; tt < 16; ++tt) {
+                    if (r > 0) {
+                        const uint64_t w15 = W[(tt + 1) & 15], w2 = W[(tt + 14) & 15];
+                        const uint64_t s0 = rotr(w15, 1) ^ rotr(w15, 8) ^ (w15 >> 7);
+                        const uint64_t s1 = rotr(w2, 19) ^ rotr(w2, 61) ^ (w2 >> 6);
+                        W[tt] += s0 + W[(tt + 9) & 15] + s1;
+                    }
+                    wk[slot][r + tt][lane] = W[tt] + c_sha512_k[r + tt];
+                }
+            }
+            nbar_arrive(1 + slot, 64);
+        }
+        return;
+    }
     uint64_t H[8] = {0x6a09e667f3bcc908ULL, 0xbb67ae8584caa73bULL, 0x3c6ef372fe94f82bULL,
                      0xa54ff53a5f1d36f1ULL, 0x510e527fade682d1ULL, 0x9b05688c2b3e6c1fULL,
                      0x1f83d9abfb41bd6bULL, 0x5be0cd19137e2179ULL};
     for (int b0 = 0; b0 < nblk; ++b0) {
-        uint64_t W[16];
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            const int pos = 128 * b0 + 8 * t;
-            uint64_t v = 0;
-            if (pos >= 1 && pos + 8 <= len) {
-#pragma unroll
-                for (int b = 0; b < 8; ++b) v = (v << 8) | row[pos + b - 1];
-            } else {
-#pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    const int q = pos + b;
-                    uint32_t byte = 0;
-                    if (q == 0) byte = 4u;
-                    else if (q < len) byte = row[q - 1];
-                    else if (q == len) byte = 0x80u;
-                    else if (q >= nblk * 128 - 8) byte = (uint32_t)(bitlen >> (8 * (nblk * 128 - 1 - q))) & 255u;
-                    v = (v << 8) | byte;
-                }
-            }
-            W[t] = v;
-        }
-        sha512_block(H, W);
+        const int slot = b0 & 1;
+        nbar_sync(1 + slot, 64);
+        sha512_rounds_wk(H, wk[slot], lane);
+        if (b0 + 2 < nblk) nbar_arrive(3 + slot, 64);
     }
+    if (lane >= nkeys) return;
     const BatchDesc dk = key_batch(km, base + lane);
     uint8_t *out = dk.sk + (size_t)(base + lane - dk.key_base) * sk_bytes + hash_off;
 #pragma unroll
@@ -255,8 +301,21 @@ cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_
 
 cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
                              int hash_off, cudaStream_t st) {
-    const int smem = (32 * pk_bytes + 15) / 16 * 16;
-    k_sha512_pk<<<(nkeys + 31) / 32, 32, smem, st>>>(km, nkeys, pk_bytes, sk_bytes, hash_off);
+    const int smem = kShaWkBytes + (32 * pk_bytes + 15) / 16 * 16;
+    // the opt-in above 48 KB, once per device at the largest size any
+    // parameter set needs (host state, not stream work)
+    static std::atomic<uint64_t> opted{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (!(opted.load() & (1ull << (dev & 63)))) {
+        e = cudaFuncSetAttribute(k_sha512_pk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kShaWkBytes + 32 * 1344);
+        if (e != cudaSuccess) return e;
+        opted.fetch_or(1ull << (dev & 63));
+    }
+    if (smem > kShaWkBytes + 32 * 1344) return cudaErrorInvalidValue;
+    k_sha512_pk<<<(nkeys + 31) / 32, 64, smem, st>>>(km, nkeys, pk_bytes, sk_bytes, hash_off);
     return cudaGetLastError();
 }
 

@@ -63,6 +63,30 @@ __device__ __forceinline__ void sha512_block(uint64_t (&H)[8], uint64_t (&W)[16]
     H[4] += e; H[5] += f; H[6] += g; H[7] += h;
 }
 
+// The 80 rounds of one block with W_t + K_t given per round (wk[t][lane]):
+// the same round as sha512_block, the schedule computed elsewhere.
+__device__ __forceinline__ void sha512_rounds_wk(uint64_t (&H)[8], const uint64_t (*wk)[32],
+                                                 int lane) {
+    uint64_t a = H[0], b = H[1], c = H[2], d = H[3], e = H[4], f = H[5], g = H[6], h = H[7];
+#pragma unroll 1
+    for (int r = 0; r < 80; r += 16) {
+#pragma unroll
+        for (int tt = 0; tt < 16; ++tt) {
+            const uint64_t hkw = h + wk[r + tt][lane];
+            const uint64_t dhkw = d + hkw;
+            const uint64_t S1 = rotr(e, 14) ^ rotr(e, 18) ^ rotr(e, 41);
+            const uint64_t ch = (e & f) ^ (~e & g);
+            const uint64_t S0 = rotr(a, 28) ^ rotr(a, 34) ^ rotr(a, 39);
+            const uint64_t mj = (a & b) ^ (a & c) ^ (b & c);
+            const uint64_t t1 = hkw + S1 + ch;
+            h = g; g = f; f = e; e = dhkw + S1 + ch;
+            d = c; c = b; b = a; a = t1 + (S0 + mj);
+        }
+    }
+    H[0] += a; H[1] += b; H[2] += c; H[3] += d;
+    H[4] += e; H[5] += f; H[6] += g; H[7] += h;
+}
+
 // First 32 bytes of SHA-512(prefix | s1[0..l1) | s2[0..l2)), by one thread
 // (the Hash_prefix of the NTRU Prime KEM).  s1 / s2 may be in any memory.
 static __device__ __noinline__ void sha512_prefixed(uint8_t prefix, const uint8_t *s1, int l1,
