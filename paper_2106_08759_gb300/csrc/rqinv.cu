@@ -23,6 +23,7 @@
 // base uncovers were never written.  One barrier per step.
 #include "common.cuh"
 #include "kernels.h"
+#include "mma_mul.cuh"
 
 namespace snt {
 
@@ -143,12 +144,30 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 // outputs, zeroing what the older state left above them in the target
 // buffer.  F, G shrink while V, R grow, their extents summing to about
 // p + 2, so a chunk applies the matrix to about p + 34 coefficients rather
-// than to four full-length polynomials.  The live outputs are cut into
-// items of NOUT consecutive coefficients of one pair ((F', G') or (V', R')),
-// one item per applier thread in one code path for both pairs, so that a
-// warp holding items of both pairs does not diverge.  Applier warps avoid
-// the warp ids that share the leader's scheduler (warp w issues on
-// scheduler w % 4), so the leader's serial chain keeps a scheduler to itself.
+// than to four full-length polynomials.  Applier warps avoid the warp ids
+// that share the leader's scheduler (warp w issues on scheduler w % 4), so
+// the leader's serial chain keeps a scheduler to itself.
+//
+// The application on the tensor cores.  Each output of a pair is a sum of
+// two Toeplitz products with the chunk matrix: with T_e[i][j] = e[i - j + o],
+//     F' = T_u F + T_v G,  G' = T_w F + T_z G   (o = m for all four),
+//     V' = T_u V + T_v R,  R' = T_w V + T_z R   (o = 0, +1, -1, 0),
+// the form of the tensor-core R/q product (mma_mul.cuh): for 16-coefficient
+// blocks the block (I, J) of T_e depends only on D = I - J, so an m16n8k16
+// MMA takes A from a pair table of e ((e[x], e[x-1]) per x, built by the
+// applier warps from the matrix at the start of the chunk) and as B eight
+// 16-coefficient blocks of the state (read as int pairs, split into 6-bit
+// limbs in f16).  The state is kept in that form: each coefficient is one
+// word holding its h and l limbs as two f16 values, written once by the
+// application that produces it, so a B fragment is two 8-byte loads and four
+// byte permutes; the leader reads an int copy of the low 64 coefficients of
+// F and G, and the inverse is read back from V's limbs at the end.  An item
+// is one 128-output tile of one pair (at most eight per chunk, one per applier
+// warp, three applier warps per scheduler): D runs over
+// the 3 or 4 values where some T_e block is nonzero, three limb products per
+// operand pair (Karatsuba: h h', l l', (h + l)(h' + l'); one, l l', when every
+// value is in {-1, 0, 1}); a sum has at most 64 terms, so every limb sum is
+// exact in f32 and 4096 P_hh + 64 P_x + P_ll stays below 2^31.
 //
 // Ranges: inside the leader's steps values are lazily reduced to [-q, 2q)
 // (G(0) = 0 mod q iff G(0) is -q, 0 or q); the matrix and the state are
@@ -157,14 +176,14 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 template <int P> struct JumpGeo {
     static constexpr int M = 31;                        // steps per chunk
     static constexpr int OFF = 32;                      // zero margin below index 0
-    static constexpr int NWA = 6;                       // applier warps (ids 1-3, 5-7)
+    static constexpr int NWA = 9;                       // applier warps (ids 1-3, 5-7, 9-11)
     static constexpr int NA = 32 * NWA;                 // applier threads
-    // outputs per item: the fewest that keep the items of the widest chunk
-    // (about p + 34 outputs, plus rounding of both pairs) within NA
-    static constexpr int NOUT = (P + 34 + 3) / 4 + 2 <= NA ? 4 : 5;
-    static constexpr int NW = 8;                        // leader, 6 appliers, 1 idle
+    static constexpr int NW = 12;                       // leader, 9 appliers, 2 idle
     static constexpr int NT = 32 * NW;
-    static constexpr int LEN = OFF + P + 1 + NOUT + 40; // slots per polynomial
+    // a tile reads blocks up to two past its last output block (D >= -2)
+    static constexpr int LEN = (OFF + P + 160 + 31) / 32 * 32;  // slots per polynomial
+    static constexpr int PTX = 112;                     // pair-table entries per matrix entry
+    static constexpr int PT0 = 48;                      // table index of coefficient 0
 };
 
 template <int Q> __device__ __forceinline__ bool is_zero_lazy(int x) {  // x in [-Q, 2Q)
@@ -191,33 +210,44 @@ template <int Q> __device__ __forceinline__ bool is_zero_lazy(int x) {  // x in 
 // lane 31 of u and v is zero before every shift and a rotation by one lane
 // is the multiplication by x.
 template <int Q>
+__device__ __forceinline__ void leader_step(int from, int &delta, int &f0, int &g0, int &fl, int &gl,
+                                            int &u, int &v, int &w, int &z) {
+    // the chain: new G, then its shift and its coefficient 0 (read straight
+    // from lane 1) issued first; the rest of the step runs in the shuffles'
+    // shadow
+    const int ng = lazy_red<Q>(f0 * gl - g0 * fl);
+    const int g0n = __shfl_sync(0xffffffffu, ng, 1);
+    const int gln = __shfl_down_sync(0xffffffffu, ng, 1);
+    const int nw = lazy_red<Q>(f0 * w - g0 * u);
+    const int nz = lazy_red<Q>(f0 * z - g0 * v);
+    const bool sw = (delta > 0) & !is_zero_lazy<Q>(g0);  // warp-uniform
+    delta = (sw ? -delta : delta) + 1;
+    fl = sw ? gl : fl;
+    f0 = sw ? g0 : f0;
+    // u, v (lazy, inside int16) shifted together as one packed word
+    const int uv = __shfl_sync(0xffffffffu, __byte_perm(sw ? w : u, sw ? z : v, 0x5410), from);
+    u = (uv << 16) >> 16;
+    v = uv >> 16;
+    w = nw;
+    z = nz;
+    g0 = g0n;
+    gl = gln;
+}
+
+// A full chunk (M steps) is unrolled so consecutive steps interleave; the
+// last, shorter chunk runs the same step in a loop.
+template <int Q, int M>
 __device__ __forceinline__ void leader_chunk(int m, int &delta, int fl, int gl, int &u, int &v,
                                              int &w, int &z) {
     const int lane = threadIdx.x & 31, from = (lane + 31) & 31;
     u = (lane == 0); v = 0; w = 0; z = (lane == 0);
     int f0 = __shfl_sync(0xffffffffu, fl, 0);
     int g0 = __shfl_sync(0xffffffffu, gl, 0);
-    for (int s = 0; s < m; ++s) {
-        // the chain: new G, then its shift and its coefficient 0 (read
-        // straight from lane 1) issued first; the rest of the step runs in
-        // the shuffles' shadow
-        const int ng = lazy_red<Q>(f0 * gl - g0 * fl);
-        const int g0n = __shfl_sync(0xffffffffu, ng, 1);
-        const int gln = __shfl_down_sync(0xffffffffu, ng, 1);
-        const int nw = lazy_red<Q>(f0 * w - g0 * u);
-        const int nz = lazy_red<Q>(f0 * z - g0 * v);
-        const bool sw = (delta > 0) & !is_zero_lazy<Q>(g0);  // warp-uniform
-        delta = (sw ? -delta : delta) + 1;
-        fl = sw ? gl : fl;
-        f0 = sw ? g0 : f0;
-        // u, v (lazy, inside int16) shifted together as one packed word
-        const int uv = __shfl_sync(0xffffffffu, __byte_perm(sw ? w : u, sw ? z : v, 0x5410), from);
-        u = (uv << 16) >> 16;
-        v = uv >> 16;
-        w = nw;
-        z = nz;
-        g0 = g0n;
-        gl = gln;
+    if (m == M) {
+#pragma unroll
+        for (int s = 0; s < M; ++s) leader_step<Q>(from, delta, f0, g0, fl, gl, u, v, w, z);
+    } else {
+        for (int s = 0; s < m; ++s) leader_step<Q>(from, delta, f0, g0, fl, gl, u, v, w, z);
     }
     u = cmod<Q>(u); v = cmod<Q>(v); w = cmod<Q>(w); z = cmod<Q>(z);
 }
@@ -229,30 +259,90 @@ __device__ __forceinline__ void load8(int (&c)[8], const int *p) {
     c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
 }
 
-// Lane k's coefficients of the chunk matrix into the six rows: coefficient k
-// of u, v, w, z at 4 + k, v_k at 4 + (k - 1) of the v_{k+1} row and w_k at
-// 4 + (k + 1) of the w_{k-1} row. The slots those rows leave unwritten (v_32
-// and w_{-1}) stay zero from the block's start.
+// Lane k's coefficients of the chunk matrix: coefficient k of u, v, w, z at
+// 4 + k of its row (zero outside k = 0..31 from the block's start).
 __device__ __forceinline__ void put_matrix(int (*An)[40], int lane, int u, int v, int w, int z) {
     An[0][4 + lane] = u; An[1][4 + lane] = v;
     An[2][4 + lane] = w; An[3][4 + lane] = z;
-    An[4][3 + lane] = v; An[5][5 + lane] = w;
+}
+
+// Shared-memory slot of state word j: bit 3 flipped by bit 5, so the B
+// fragment loads of a half-warp (four blocks 16 words apart) hit 32 distinct
+// banks and the application's stores (rows 32 words apart) at most two
+// lanes per bank; pairs (2k, 2k + 1) stay adjacent.
+__device__ __forceinline__ int ssl(int j) { return j ^ (((j >> 5) & 1) << 3); }
+
+// A coefficient as one state word: its limbs h (low half) and l (high half)
+// as f16.
+__device__ __forceinline__ uint32_t limb_word(int x) {
+    int h, l;
+    limbs64(x, h, l);
+    return h2_small(h, l);
+}
+__device__ __forceinline__ int word_value(uint32_t w) {
+    const __half2 v = *reinterpret_cast<const __half2 *>(&w);
+    return 64 * __half2int_rn(__low2half(v)) + __half2int_rn(__high2half(v));
+}
+
+// The B fragment words (h01, h89, l01, l89, s01, s89; s = h + l) of a block
+// of state words: j is the word of coefficient 2 tig of the block (even).
+__device__ __forceinline__ uint32_t hadd2_u(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+template <bool SMALL>
+__device__ __forceinline__ void jump_frag_b(const uint32_t *X, int j, uint32_t (&b)[6]) {
+    const uint2 lo = *reinterpret_cast<const uint2 *>(X + ssl(j));
+    const uint2 hi = *reinterpret_cast<const uint2 *>(X + ssl(j + 8));
+    b[2] = __byte_perm(lo.x, lo.y, 0x7632);
+    b[3] = __byte_perm(hi.x, hi.y, 0x7632);
+    if (!SMALL) {
+        b[0] = __byte_perm(lo.x, lo.y, 0x5410);
+        b[1] = __byte_perm(hi.x, hi.y, 0x5410);
+        b[4] = hadd2_u(b[0], b[2]);
+        b[5] = hadd2_u(b[1], b[3]);
+    }
+}
+
+// acc[0..2] += the Karatsuba limb products h h', l l' and (h + l)(h' + l')
+// of A (pair-table words at x, x + 8, x - 8) and the B words b (h01, h89,
+// l01, l89, s01, s89); the sums are formed in f16, exact for these small
+// integers.  Only l l' when SMALL.
+template <bool SMALL>
+__device__ __forceinline__ void jump_mma(float (&acc)[SMALL ? 1 : 3][4], const uint2 *pt, int x,
+                                         const uint32_t (&b)[6]) {
+    const uint2 a0 = pt[x], a1 = pt[x + 8], a2 = pt[x - 8];
+    if (SMALL) {
+        mma16816(acc[0], a0.y, a1.y, a2.y, a0.y, b[2], b[3]);
+    } else {
+        const uint32_t s0 = hadd2_u(a0.x, a0.y), s1 = hadd2_u(a1.x, a1.y), s2 = hadd2_u(a2.x, a2.y);
+        mma16816(acc[0], a0.x, a1.x, a2.x, a0.x, b[0], b[1]);
+        mma16816(acc[1], a0.y, a1.y, a2.y, a0.y, b[2], b[3]);
+        mma16816(acc[2], s0, s1, s2, s0, b[4], b[5]);
+    }
 }
 
 // Q: the coefficient modulus (q: R/q; 3: R/3, for the root inversions of
 // the R/3 batch inversion).
 template <int P, int Q = Geo<P>::q>
-__global__ void __launch_bounds__(JumpGeo<P>::NT)
+__global__ void __launch_bounds__(JumpGeo<P>::NT, 1)
 k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_stride,
               int32_t *__restrict__ okv, int *__restrict__ err, int err_bit, const int *idx) {
     using JG = JumpGeo<P>;
-    constexpr int LEN = JG::LEN, OFF = JG::OFF, NT = JG::NT, NOUT = JG::NOUT;
+    constexpr int LEN = JG::LEN, OFF = JG::OFF, NT = JG::NT;
+    constexpr bool SMALL = Q < 64;  // every value in {-1, 0, 1}: the l limbs only
     constexpr int NCH = (2 * P - 1 + JG::M - 1) / JG::M;
-    __shared__ int st[2][4][LEN];       // [buffer][F, G, V, R][index + OFF]
-    // chunk matrix [buffer][row][4 + k]: rows u, v, w, z and the shifted
-    // rows v_{k+1}, w_{k-1} used by (V', R'); 16-byte rows for vector loads,
-    // zero outside k = 0..31
-    __shared__ __align__(16) int mat[2][6][40];
+    // state words (limbs as f16 pairs) [buffer][F, G, V, R][index + OFF], and
+    // int copies of F, G at indices -32 .. 63 for the leader's prologue
+    __shared__ __align__(16) uint32_t st[2][4][LEN];
+    __shared__ int lowfg[2][2][96];
+    // chunk matrix [buffer][u, v, w, z][4 + k], 16-byte rows for vector
+    // loads, zero outside k = 0..31
+    __shared__ __align__(16) int mat[2][4][40];
+    // limb pair tables of u, v, w, z for the appliers: entry PT0 + x holds
+    // (h, l) of (e[x], e[x-1]) as f16x2 words, zero outside x = 0..32
+    __shared__ __align__(16) uint2 pt[4][JG::PTX];
     // extents of the state after chunk c - 1 in ext[c % 4]: [0] F, G and
     // [1] V, R (one past the highest nonzero coefficient)
     __shared__ int ext[4][2];
@@ -263,16 +353,23 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     const bool leader = tid < 32;
     const int row = idx ? idx[e] : e;
     const int16_t *a = in + (size_t)row * in_stride;
-    for (int i = tid; i < 2 * 4 * LEN; i += NT) (&st[0][0][0])[i] = 0;
-    for (int i = tid; i < 2 * 6 * 40; i += NT) (&mat[0][0][0])[i] = 0;
+    for (int i = tid; i < 2 * 4 * LEN; i += NT) (&st[0][0][0])[i] = 0u;  // f16 zeros
+    for (int i = tid; i < 2 * 2 * 96; i += NT) (&lowfg[0][0][0])[i] = 0;
+    for (int i = tid; i < 2 * 4 * 40; i += NT) (&mat[0][0][0])[i] = 0;
+    for (int i = tid; i < 4 * JG::PTX; i += NT) (&pt[0][0])[i] = make_uint2(0u, 0u);
     if (tid < 8) (&ext[0][0])[tid] = 0;
     __syncthreads();
-    for (int i = tid; i < P; i += NT) st[0][1][OFF + i] = (int)a[P - 1 - i];
+    for (int i = tid; i < P; i += NT) {
+        const int g = (int)a[P - 1 - i];
+        st[0][1][ssl(OFF + i)] = limb_word(g);
+        if (i < 64) lowfg[0][1][32 + i] = g;
+    }
     if (tid == 0) {
-        st[0][0][OFF] = 1;
-        st[0][0][OFF + P - 1] = -1;
-        st[0][0][OFF + P] = -1;
-        st[0][3][OFF] = 1;
+        st[0][0][ssl(OFF)] = limb_word(1);
+        st[0][0][ssl(OFF + P - 1)] = limb_word(-1);
+        st[0][0][ssl(OFF + P)] = limb_word(-1);
+        st[0][3][ssl(OFF)] = limb_word(1);
+        lowfg[0][0][32] = 1;
         ext[0][0] = P + 1;
         ext[0][1] = 1;
     }
@@ -280,8 +377,8 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     int delta = 1;  // leader only
     if (leader) {
         int u, v, w, z;
-        leader_chunk<Q>(min(JG::M, 2 * P - 1), delta, st[0][0][OFF + lane], st[0][1][OFF + lane],
-                        u, v, w, z);
+        leader_chunk<Q, JG::M>(min(JG::M, 2 * P - 1), delta, lowfg[0][0][32 + lane],
+                               lowfg[0][1][32 + lane], u, v, w, z);
         put_matrix(mat[0], lane, u, v, w, z);
     }
     __syncthreads();
@@ -292,9 +389,9 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
         if (leader) {
             if (c + 1 < NCH) {
                 // low 32 coefficients of F', G' (lane i), then chunk c + 1
-                const int *F = st[cur][0], *G = st[cur][1];
+                const int *F = lowfg[cur][0], *G = lowfg[cur][1];
                 int af[2] = {0, 0}, ag[2] = {0, 0};
-                const int hi = OFF + lane + m;
+                const int hi = 32 + lane + m;
 #pragma unroll
                 for (int kb = 0; kb < 32; kb += 8) {
                     int c0[8], c1[8], c2[8], c3[8];
@@ -309,7 +406,7 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
                 }
                 const int m1 = min(JG::M, 2 * P - 1 - (c + 1) * JG::M);
                 int u, v, w, z;
-                leader_chunk<Q>(m1, delta, cmod<Q>(af[0] + af[1]), cmod<Q>(ag[0] + ag[1]), u, v, w,
+                leader_chunk<Q, JG::M>(m1, delta, cmod<Q>(af[0] + af[1]), cmod<Q>(ag[0] + ag[1]), u, v, w,
                                 z);
                 put_matrix(mat[(c + 1) & 1], lane, u, v, w, z);
             } else if (lane == 0) {
@@ -321,58 +418,85 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
             // live ranges of the outputs and what the target buffer held
             const int rfg = ext[c & 3][0], rvr = min(ext[c & 3][1] + m + 1, P + 1);
             const int ofg = ext[(c + 3) & 3][0], ovr = ext[(c + 3) & 3][1];
-            int *T = &st[cur ^ 1][0][0];
-            for (int i = rfg + at; i < ofg; i += JG::NA) { T[OFF + i] = 0; T[LEN + OFF + i] = 0; }
+            uint32_t *T = &st[cur ^ 1][0][0];
+            for (int i = rfg + at; i < ofg; i += JG::NA) {
+                T[ssl(OFF + i)] = 0u; T[LEN + ssl(OFF + i)] = 0u;
+                if (i < 64) { lowfg[cur ^ 1][0][32 + i] = 0; lowfg[cur ^ 1][1][32 + i] = 0; }
+            }
             for (int i = rvr + at; i < ovr; i += JG::NA) {
-                T[2 * LEN + OFF + i] = 0; T[3 * LEN + OFF + i] = 0;
+                T[2 * LEN + ssl(OFF + i)] = 0u; T[3 * LEN + ssl(OFF + i)] = 0u;
             }
             if (at == 0) { ext[(c + 2) & 3][0] = 0; ext[(c + 2) & 3][1] = 0; }
-            const int nfg = (rfg + NOUT - 1) / NOUT, nit = nfg + (rvr + NOUT - 1) / NOUT;
+            // pair tables of this chunk's matrix, then the appliers' barrier
+            if (at < 4 * 33) {
+                const int en = at / 33, k = at % 33;
+                const int e0 = A[en][4 + k], e1 = A[en][3 + k];  // e[k], e[k-1]; zero at 32 and -1
+                int h0, l0, h1, l1;
+                limbs64(e0, h0, l0);
+                limbs64(e1, h1, l1);
+                pt[en][JG::PT0 + k] = make_uint2(h2_small(h0, h1), h2_small(l0, l1));
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(JG::NA) : "memory");
+            const int g = lane >> 2, tig = lane & 3;
+            const int nfg = (rfg + 127) / 128, nit = nfg + (rvr + 127) / 128;
             int top_fg = 0, top_vr = 0;
-            for (int it = at; it < nit; it += JG::NA) {
-                // pair 0: F' = (u F + v G) / x^m, G' = (w F + z G) / x^m, inputs at i + m - k
-                // pair 1: V' = u V + (v/x) R, R' = (x w) V + z R, inputs at i - k
+            for (int it = ai; it < nit; it += JG::NWA) {  // one tile of one pair per warp
                 const int pr = it >= nfg;
-                const int i0 = NOUT * (pr ? it - nfg : it), r = pr ? rvr : rfg;
-                const int *X = st[cur][2 * pr], *Y = st[cur][2 * pr + 1];
-                const int *a0 = &A[0][4], *a1 = &A[pr ? 4 : 1][4], *a2 = &A[pr ? 5 : 2][4],
-                          *a3 = &A[3][4];
-                const int b = OFF + i0 + (pr ? 0 : m);
-                int o1[NOUT], o2[NOUT], xh[NOUT], yh[NOUT];
+                const int T0 = pr ? it - nfg : it, r = pr ? rvr : rfg;
+                const uint32_t *X = st[cur][2 * pr], *Y = st[cur][2 * pr + 1];
+                // offsets o of T_u, T_v, T_w, T_z and the D range where some
+                // block is nonzero: 0 <= 16 D + (row - col) + o <= 31
+                const int ou = pr ? 0 : m, ov = pr ? 1 : m, ow = pr ? -1 : m;
+                const int dlo = pr ? -1 : -((15 + m) >> 4), dhi = pr ? 2 : (46 - m) >> 4;
+                constexpr int NL = SMALL ? 1 : 3;  // limb products h h', l l', s s'
+                float acc[2][NL][4];                // [output][limb product]
 #pragma unroll
-                for (int t = 0; t < NOUT; ++t) {
-                    o1[t] = 0; o2[t] = 0;
-                    xh[t] = X[b + t]; yh[t] = Y[b + t];
+                for (int o = 0; o < 2; ++o)
+#pragma unroll
+                    for (int t = 0; t < NL; ++t)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[o][t][q] = 0.f;
+#pragma unroll
+                for (int dd = 0; dd < 4; ++dd) {  // at most four D values
+                    const int D = dlo + dd;
+                    if (D > dhi) break;
+                    const int jb = OFF + 16 * (8 * T0 + g - D) + 2 * tig;  // input block I - D
+                    uint32_t bx[6], by[6];
+                    jump_frag_b<SMALL>(X, jb, bx);
+                    jump_frag_b<SMALL>(Y, jb, by);
+                    const int x = JG::PT0 + 16 * D + g - 2 * tig;
+                    // X terms of both outputs first, so the two MMAs that
+                    // meet in one accumulator are apart
+                    jump_mma<SMALL>(acc[0], pt[0], x + ou, bx);
+                    jump_mma<SMALL>(acc[1], pt[2], x + ow, bx);
+                    jump_mma<SMALL>(acc[0], pt[1], x + ov, by);
+                    jump_mma<SMALL>(acc[1], pt[3], x + ou, by);
                 }
-#pragma unroll 1
-                for (int kb = 0; kb < 32; kb += 8) {
-                    int xl[8], yl[8], c0[8], c1[8], c2[8], c3[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) { xl[j] = X[b - kb - 8 + j]; yl[j] = Y[b - kb - 8 + j]; }
-                    load8(c0, a0 + kb); load8(c1, a1 + kb); load8(c2, a2 + kb); load8(c3, a3 + kb);
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk)
-#pragma unroll
-                        for (int t = 0; t < NOUT; ++t) {
-                            const int d = t - kk;
-                            const int xv = d >= 0 ? xh[d] : xl[8 + d];
-                            const int yv = d >= 0 ? yh[d] : yl[8 + d];
-                            o1[t] += c0[kk] * xv + c1[kk] * yv;
-                            o2[t] += c2[kk] * xv + c3[kk] * yv;
-                        }
-#pragma unroll
-                    for (int t = 0; t < NOUT; ++t) { xh[t] = xl[t]; yh[t] = yl[t]; }
-                }
-                int *X2 = st[cur ^ 1][2 * pr], *Y2 = st[cur ^ 1][2 * pr + 1];
+                uint32_t *X2 = st[cur ^ 1][2 * pr], *Y2 = st[cur ^ 1][2 * pr + 1];
                 int top = 0;
 #pragma unroll
-                for (int t = 0; t < NOUT; ++t)
-                    if (i0 + t < r) {
-                        const int v1 = cmod<Q>(o1[t]), v2 = cmod<Q>(o2[t]);
-                        X2[OFF + i0 + t] = v1;
-                        Y2[OFF + i0 + t] = v2;
-                        if (v1 | v2) top = i0 + t + 1;
+                for (int q = 0; q < 4; ++q) {
+                    const int i = 16 * (8 * T0 + 2 * tig + (q & 1)) + g + 8 * (q >> 1);
+                    if (i < r) {
+                        int v[2];
+#pragma unroll
+                        for (int o = 0; o < 2; ++o) {
+                            // integer-valued sums below 2^24: the f32 arithmetic is exact
+                            if (SMALL) {
+                                v[o] = cmod<Q>(__float2int_rn(acc[o][0][q]));
+                            } else {
+                                // P_x = P_ss - P_hh - P_ll; |64 P_x + P_ll| < 2^24
+                                const float phh = acc[o][0][q], pll = acc[o][1][q];
+                                const int t = __float2int_rn(fmaf(64.f, acc[o][2][q] - phh - pll, pll));
+                                v[o] = cmod<Q>(4096 * __float2int_rn(phh) + t);
+                            }
+                        }
+                        X2[ssl(OFF + i)] = limb_word(v[0]);
+                        Y2[ssl(OFF + i)] = limb_word(v[1]);
+                        if (!pr && i < 64) { lowfg[cur ^ 1][0][32 + i] = v[0]; lowfg[cur ^ 1][1][32 + i] = v[1]; }
+                        if (v[0] | v[1]) top = max(top, i + 1);
                     }
+                }
                 if (pr) top_vr = max(top_vr, top); else top_fg = max(top_fg, top);
             }
             top_fg = __reduce_max_sync(0xffffffffu, top_fg);
@@ -386,11 +510,11 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
         cur ^= 1;
     }
     const bool ok = s_ok != 0;
-    const int f0 = freeze_lazy<Q>(st[cur][0][OFF]);
+    const int f0 = freeze_lazy<Q>(lowfg[cur][0][32]);
     const int sc = ok ? inv_mod<Q>(f0) : 0;
     int16_t *o = out + (size_t)row * out_stride;
     for (int i = tid; i < P; i += NT) {
-        const int v = freeze_lazy<Q>(st[cur][2][OFF + P - 1 - i]);
+        const int v = freeze_lazy<Q>(word_value(st[cur][2][ssl(OFF + P - 1 - i)]));
         o[i] = (int16_t)cmod<Q>(sc * v);
     }
     if (tid == 0) {
