@@ -48,10 +48,18 @@ def launches_per_call(B, tuned):
     r3 = {0: 2, 1: 1 + 2 * L + 1 + 1, 2: 2 * L + 1 + 1 + 1 + 1}[tuned.get("r3_mode", 0)]
     return rq + r3
 
-# DRAM bytes (read + write) per call of a phase's kernel at B = 4096, from
-# the committed ncu captures (profiles/), keyed by kernel instantiation; a
-# kernel is absent until a capture of its current code exists.
-NCU_TRAFFIC_BYTES = {"k_r3_keygen<761, 4>": 32512}
+# DRAM bytes (read + write) per call of a phase's kernels at B = 4096 under
+# the tuned layouts (64 roots, R/3 forest), summed over the phase's launches
+# of one call, from the committed ncu capture
+# (profiles/launches_keygen_b4096_sntrup761.md), keyed by kernel; a kernel is
+# absent until a capture of its current code exists.  Writes stay in L2.
+NCU_TRAFFIC_BYTES = {
+    "k_tree_up_mma": 12530000,
+    "k_tree_down_mma": 18790000,
+    "k_rq_inv_jump<761, 4591>": 164096,
+    "k_finalize_mma<761>": 9460000,
+    "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 37770000,
+}
 
 
 def kernel_of(phase, tuned):
