@@ -75,4 +75,76 @@ __device__ __forceinline__ void short_sorted_words(uint64_t seed, uint64_t k, ui
 
 }
 
+// One compare-exchange stage inside a lane: slots r and r | S (r & S == 0)
+// of v, ascending when SIZE > 0 and (r & SIZE) == 0 (the direction of small
+// bitonic blocks is fixed by the slot) or, when SIZE == 0, when asc.
+template <int S, int SIZE>
+__device__ __forceinline__ void bitonic_lane_stage(uint32_t (&v)[32], bool asc) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+        if ((r & S) == 0) {
+            const bool a = SIZE ? ((r & SIZE) == 0) : asc;
+            const uint32_t x = v[r], y = v[r | S];
+            const uint32_t mn = min(x, y), mx = max(x, y);
+            v[r] = a ? mn : mx;
+            v[r | S] = a ? mx : mn;
+        }
+}
+
+// The same Short draw by one warp: lane L holds slots 32L .. 32L+31 of the
+// 1024-slot network in registers, so partners closer than 32 slots are in
+// the same lane (compare-exchanges, their direction a constant for blocks
+// up to 16 slots) and the rest one lane-xor shuffle away; no shared memory
+// and no barrier.  On return lane L holds sorted slots 32L .. 32L+31.
+template <int P>
+__device__ __forceinline__ void short_sorted_warp(uint64_t seed, uint64_t k, uint32_t stream,
+                                                  uint32_t (&v)[32]) {
+    using G = Geo<P>;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        uint32_t r[4] = {0u, 0u, 0u, 0u};
+        const int blk = 8 * lane + b;
+        if (4 * blk < G::p) rand_block(seed, k, stream, 0u, (uint32_t)blk, r);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int idx = 4 * blk + j;
+            uint32_t x = r[j];
+            if (idx < G::w) x &= ~1u;
+            else if (idx < G::p) x = (x & ~3u) | 1u;
+            else x = 0xFFFFFFFFu;
+            v[4 * b + j] = x;
+        }
+    }
+    bitonic_lane_stage<1, 2>(v, true);
+    bitonic_lane_stage<2, 4>(v, true);
+    bitonic_lane_stage<1, 4>(v, true);
+    bitonic_lane_stage<4, 8>(v, true);
+    bitonic_lane_stage<2, 8>(v, true);
+    bitonic_lane_stage<1, 8>(v, true);
+    bitonic_lane_stage<8, 16>(v, true);
+    bitonic_lane_stage<4, 16>(v, true);
+    bitonic_lane_stage<2, 16>(v, true);
+    bitonic_lane_stage<1, 16>(v, true);
+#pragma unroll 1
+    for (int size = 32; size <= 1024; size <<= 1) {
+        const bool asc = ((32 * lane) & size) == 0;
+#pragma unroll 1
+        for (int stride = size >> 1; stride >= 32; stride >>= 1) {
+            const int m = stride >> 5;
+            const bool keep_min = ((lane & m) == 0) == asc;  // lower slot of an ascending pair
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const uint32_t o = __shfl_xor_sync(0xffffffffu, v[r], m);
+                v[r] = keep_min ? min(v[r], o) : max(v[r], o);
+            }
+        }
+        bitonic_lane_stage<16, 0>(v, asc);
+        bitonic_lane_stage<8, 0>(v, asc);
+        bitonic_lane_stage<4, 0>(v, asc);
+        bitonic_lane_stage<2, 0>(v, asc);
+        bitonic_lane_stage<1, 0>(v, asc);
+    }
+}
+
 }  // namespace snt
