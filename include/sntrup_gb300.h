@@ -299,7 +299,15 @@ typedef enum {
      * jump-divstep inversion per subtree); 2 the same forest on the first
      * draws at once, invertibility read off each subtree's root (a product
      * is invertible iff every factor is), a failed subtree redone per key */
-    SNT_OPT_R3_MODE = 10
+    SNT_OPT_R3_MODE = 10,
+    /* 1 (default): the tensor-core batch path forms h from the inverses of
+     * the tree's level-1 nodes, h_L = 3 inv(P) (g_L f_R) for P = (3f_L)(3f_R),
+     * instead of inverting every leaf and then multiplying by g (one small
+     * and one half-cost product per key instead of two general ones; p = 653
+     * and 761 only: for 857 the limb sums could reach 2^24 and the option is
+     * ignored); 0: the leaf level of the down-sweep, then h = g (3f)^-1.
+     * Same bytes either way. */
+    SNT_OPT_FUSE_LEAF = 11
 } snt_option;
 
 snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);

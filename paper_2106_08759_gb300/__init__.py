@@ -23,7 +23,7 @@ PARAMS = {653: (653, 4621, 288), 761: (761, 4591, 286), 857: (857, 5167, 322)}
 # tuning options (snt_option)
 SNT_OPT_R3_LANES, SNT_OPT_TREE_SPLIT, SNT_OPT_R3_OVERLAP, SNT_OPT_NARROW_SEG = 1, 2, 3, 4
 SNT_OPT_RQ_ENGINE, SNT_OPT_MMA_TILES, SNT_OPT_R3_KPT, SNT_OPT_MMA_KSPLIT = 5, 6, 7, 8
-SNT_OPT_ROOTS, SNT_OPT_R3_MODE = 9, 10
+SNT_OPT_ROOTS, SNT_OPT_R3_MODE, SNT_OPT_FUSE_LEAF = 9, 10, 11
 
 # phase names of snt_ctx_phase_times (SNT_NPHASES entries)
 PHASES = ("sample_f", "r3_inv", "tree_up", "root_inv", "tree_down", "h_encode", "sha512",

@@ -64,7 +64,10 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     int16_t *nodes = reinterpret_cast<int16_t *>(arena);
     int8_t *gbuf = reinterpret_cast<int8_t *>(arena + align256(tb.total * pi.pad * sizeof(int16_t)));
     int16_t *leaves = nodes;
-    const int16_t *inv_leaves = leaves;  // 1/(3f) of every key, for h
+    const int16_t *inv_leaves = leaves;  // 1/(3f) of every key, for h (level-1 inverses if fused)
+    bool fuse = false;                   // h from the level-1 inverses (k_finalize_pair)
+    int n1 = 0;
+    LevelMap lm1;
     // two ping-pong level buffers after the rest of the scratch
     int16_t *pp[2];
     pp[0] = reinterpret_cast<int16_t *>(arena + keygen_scratch(pi, B, false));
@@ -231,7 +234,10 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         // ping-pong buffers (children of one split level at a time).
         const int16_t *par = root;
         int ping = 0;
-        for (int l = L; l >= 1; --l) {
+        // fused leaf level: stop at the level-1 inverses, h is formed from them
+        fuse = mma && ctx->fuse_leaf && FuseLeaf<P>::ok && L >= 1;
+        if (fuse) { n1 = t.n[1]; lm1 = lmap(1); }
+        for (int l = L; l >= (fuse ? 2 : 1); --l) {
             int16_t *lch = nodes + (size_t)t.off[l - 1] * pi.pad;
             if (mma) {  // in place on every level
                 SNT_CUDA(launch_tree_down_mma<P>(par, lmap(l), t.n[l], lch, st,
@@ -260,15 +266,20 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     }
     if (r3chk && !joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_gready, 0));  // final g's
     if (tm) SNT_CUDA(cudaEventRecord(ev[7], st));
-    SNT_CUDA(launch_finalize<P>(km, Bi, gbuf, inv_leaves, pi.pk_bytes, pi.sk_bytes, 2 * sb,
-                                pi.sched, st, mma));
+    if (fuse)
+        SNT_CUDA(launch_finalize_pair<P>(km, n1, gbuf, leaves, inv_leaves, lm1, pi.pk_bytes,
+                                         pi.sk_bytes, 2 * sb, pi.sched, st));
+    else
+        SNT_CUDA(launch_finalize<P>(km, Bi, gbuf, inv_leaves, pi.pk_bytes, pi.sk_bytes, 2 * sb,
+                                    pi.sched, st, mma));
     if (tm) SNT_CUDA(cudaEventRecord(ev[8], st));
     SNT_CUDA(launch_sha512_pk(km, Bi, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     if (tm) SNT_CUDA(cudaEventRecord(ev[9], st));
     if (!joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     if (!r3chk)  // keys whose g was redrawn by the deferred per-key R/3 kernel
         SNT_CUDA(launch_fixup<P>(km, fix_count, fix_keys, gfix, inv_leaves, pi.pk_bytes,
-                                 pi.sk_bytes, 2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st));
+                                 pi.sk_bytes, 2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st,
+                                 fuse ? leaves : nullptr, lm1));
     if (tm) SNT_CUDA(cudaEventRecord(ev[10], st));
     if (!inline_stream) {  // join back into the caller's stream
         SNT_CUDA(cudaEventRecord(ctx->ev_done, st));
@@ -624,6 +635,10 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             if (value < 0 || value > 2) return set_error(SNT_EINVAL, "R/3 mode is 0, 1 or 2");
             ctx->r3_mode = value;
             return SNT_OK;
+        case SNT_OPT_FUSE_LEAF:
+            if (value < 0 || value > 1) return set_error(SNT_EINVAL, "fuse-leaf is 0 or 1");
+            ctx->fuse_leaf = value;
+            return SNT_OK;
         default:
             return set_error(SNT_EINVAL, "unknown option %d", option);
     }
@@ -642,6 +657,7 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
         case SNT_OPT_MMA_KSPLIT: *value = ctx->mma_ksplit; return SNT_OK;
         case SNT_OPT_ROOTS: *value = ctx->roots; return SNT_OK;
         case SNT_OPT_R3_MODE: *value = ctx->r3_mode; return SNT_OK;
+        case SNT_OPT_FUSE_LEAF: *value = ctx->fuse_leaf; return SNT_OK;
         default: return set_error(SNT_EINVAL, "unknown option %d", option);
     }
 }

@@ -16,6 +16,16 @@ template <> struct Prm<653> { static constexpr int p = 653, q = 4621, w = 288; }
 template <> struct Prm<761> { static constexpr int p = 761, q = 4591, w = 286; };
 template <> struct Prm<857> { static constexpr int p = 857, q = 5167, w = 322; };
 
+// Whether h can be formed from the inverses of the level-1 nodes (the leaf
+// level of the down-sweep skipped): h_L = 3 inv(P) (g_L f_R) with
+// |g_L f_R| <= 2w taken as one f16 limb against inv(P)'s 6-bit limbs needs
+// every limb sum, at most p * h_max * 2w, below 2^24 (h_max the high limb of
+// a centred residue).
+template <int P> struct FuseLeaf {
+    static constexpr long long hmax = ((Prm<P>::q - 1) / 2 + 32) / 64;
+    static constexpr bool ok = (long long)Prm<P>::p * hmax * 2 * Prm<P>::w < (1LL << 24);
+};
+
 // Geometry of one polynomial in device memory.
 //   words: 32-trit words holding the p + 1 trits a divstep state needs
 //   pad:   coefficient stride of every stored polynomial (words * 32), so

@@ -54,6 +54,7 @@ struct snt_ctx {
     int mma_ksplit = snt::kDefaultMmaKsplit;
     int roots = snt::kDefaultRoots;
     int r3_mode = snt::kDefaultR3Mode;
+    int fuse_leaf = 1;  // h from the level-1 inverses (where FuseLeaf<P>::ok)
     // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
     struct Tuned {
         int lanes = 0, split = 0, overlap = 0, engine = 0, tiles = 1, kpt = 1, roots = 1, r3mode = 0;

@@ -104,25 +104,200 @@ k_finalize_mma(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__rest
     }
 }
 
+// h for the two keys under a level-1 node j of the product forest, whose
+// inverse inv(P_j) the down-sweep leaves at its row (the leaf level of the
+// down-sweep is not run).  With P_j = (3 f_L)(3 f_R),
+//     1/(3 f_L) = inv(P_j) 3 f_R,   so   h_L = g_L / (3 f_L) = 3 inv(P_j) (g_L f_R),
+// and likewise for R (Sec. 2.2's Montgomery trick, the last level folded into
+// h).  s_L = g_L f_R has both operands small (one MMA per step); each output
+// coefficient of a product mod x^p - x - 1 is d_j + d_{p+j} + d_{p+j-1} with
+// the first two over disjoint parts of f's support, so |s_L| <= 2w and s_L
+// goes into the second product as one f16 limb: two MMAs per step against
+// inv(P_j)'s pair table, which is built once for both keys (FuseLeaf<P>
+// checks that the limb sums stay below 2^24).  An unpaired leaf (a subtree of
+// odd size) is its own level-1 node: h = g inv(node) directly.
+template <int P>
+__global__ void __launch_bounds__(32 * MmaGeo<P, 1>::NW)
+k_finalize_pair(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__restrict__ leaves,
+                const int16_t *__restrict__ inv1, LevelMap lm1, int pk_bytes, int sk_bytes,
+                int sk_pk_off, EncSched S) {
+    using G = Geo<P>;
+    using M = MmaGeo<P, 1>;
+    static_assert(FuseLeaf<P>::ok, "limb sums of the fused leaf level exceed 2^24");
+    static_assert(2 * G::pad * sizeof(uint32_t) + 1344 <= sizeof(MmaE<P, 1>), "encode buffers");
+    extern __shared__ __align__(16) uint8_t sm[];
+    MmaE<P, 1> &E = *reinterpret_cast<MmaE<P, 1> *>(sm);
+    MmaA<P, 1> *A = reinterpret_cast<MmaA<P, 1> *>(sm + sizeof(MmaE<P, 1>));
+    int16_t(*sv)[G::pad] =
+        reinterpret_cast<int16_t(*)[G::pad]>(sm + sizeof(MmaE<P, 1>) + 2 * sizeof(MmaA<P, 1>));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nth = blockDim.x, tid = threadIdx.x;
+    const int j = blockIdx.x;
+    int idx, base, n_in;
+    lm_node(lm1, j, idx, base, n_in);
+    const int kl = base + 2 * idx;  // leaf rows are key indices
+    const bool paired = 2 * idx + 1 < n_in;
+    const int16_t *ip = inv1 + (size_t)j * G::pad;
+    if (paired) {
+        for (int side = 0; side < 2; ++side) {  // s = g_kg f_kf
+            const int kg = kl + side, kf = kl + 1 - side;
+            mma_fill_a<P, 1, MODE_SAE>(gbuf + (size_t)kg * G::pad, A[0], tid, nth);
+            const int16_t *fr = leaves + (size_t)kf * G::pad;  // 3f
+            for (int k = tid; k < M::AN; k += nth) E.b[k] = k < M::p ? (int16_t)(fr[k] / 3) : 0;
+            __syncthreads();
+            mma_fill_pe<P, 1, MODE_SAE>(E, tid, nth);
+            __syncthreads();
+            float acc[1][1][3][4];
+            const MmaA<P, 1> *const As[1] = {&A[0]};
+            mma_tiles<P, 1, 1, MODE_SAE>(E, As, warp, lane, acc);
+            __syncthreads();
+            mma_stage<P, 1, 1, MODE_SAE>(A[0], warp, lane, 0, acc);
+            __syncthreads();
+            const int bl = (int)E.b[M::p - 1];
+            for (int k = tid; k < G::pad; k += nth) {  // |s| <= 2w: exact, no reduction
+                int v = 0;
+                if (k == 0) v = A[0].u.stage[0] - A[0].u.stage[stage_slot(M::p - 1)] + (int)A[0].a[0] * bl;
+                else if (k < M::p) v = A[0].u.stage[stage_slot(k)] + (int)A[0].a[k] * bl;
+                sv[side][k] = (int16_t)v;
+            }
+            __syncthreads();
+        }
+        // h' = inv(P_j) s for both keys, one pair table of inv(P_j)
+        mma_fill_b<P, 1>(ip, E, tid, nth);
+        mma_fill_a_wide<P, 1>(sv[0], A[0], tid, nth);
+        mma_fill_a_wide<P, 1>(sv[1], A[1], tid, nth);
+        __syncthreads();
+        mma_fill_pe<P, 1, MODE_GEN>(E, tid, nth);
+        __syncthreads();
+        float acc[1][2][3][4];
+        const MmaA<P, 1> *const As[2] = {&A[0], &A[1]};
+        mma_tiles<P, 1, 2, MODE_SA>(E, As, warp, lane, acc);
+        const int bl = (int)E.b[M::p - 1];
+        __syncthreads();
+        mma_stage<P, 1, 2, MODE_SA>(A[0], warp, lane, 0, acc);
+        mma_stage<P, 1, 2, MODE_SA>(A[1], warp, lane, 1, acc);
+        __syncthreads();
+        // h for both keys: key L's encode buffers over E, key R's over the
+        // vector records (written after every read of A, through registers)
+        uint32_t(*Rb0)[G::pad] = reinterpret_cast<uint32_t(*)[G::pad]>(sm);
+        uint8_t *ob0 = sm + 2 * G::pad * sizeof(uint32_t);
+        uint32_t(*Rb1)[G::pad] = reinterpret_cast<uint32_t(*)[G::pad]>(sm + sizeof(MmaE<P, 1>));
+        uint8_t *ob1 = sm + sizeof(MmaE<P, 1>) + 2 * G::pad * sizeof(uint32_t);
+        static_assert(2 * G::pad * sizeof(uint32_t) + 1344 <= 2 * sizeof(MmaA<P, 1>) + 2 * G::pad * sizeof(int16_t),
+                      "second encode buffer");
+        constexpr int KPT = (P + 32 * MmaGeo<P, 1>::NW - 1) / (32 * MmaGeo<P, 1>::NW);
+        uint32_t hr[KPT];
+#pragma unroll
+        for (int u = 0; u < KPT; ++u) {
+            const int k = tid + u * nth;
+            if (k < P) {
+                int vl = (k == 0) ? A[0].u.stage[0] - A[0].u.stage[stage_slot(P - 1)] + (int)A[0].a[0] * bl
+                                  : A[0].u.stage[stage_slot(k)] + (int)A[0].a[k] * bl;
+                int vr = (k == 0) ? A[1].u.stage[0] - A[1].u.stage[stage_slot(P - 1)] + (int)A[1].a[0] * bl
+                                  : A[1].u.stage[stage_slot(k)] + (int)A[1].a[k] * bl;
+                Rb0[0][k] = (uint32_t)(cmod<G::q>(3 * cmod<G::q>(vl)) + G::half);
+                hr[u] = (uint32_t)(cmod<G::q>(3 * cmod<G::q>(vr)) + G::half);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < KPT; ++u) {
+            const int k = tid + u * nth;
+            if (k < P) Rb1[0][k] = hr[u];
+        }
+        __syncthreads();
+        mixed_encode2<G::pad>(Rb0, Rb1, S, ob0, ob1);
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int key = kl + side;
+            const uint8_t *ob = side ? ob1 : ob0;
+            const BatchDesc d = key_batch(km, key);
+            uint8_t *pkk = d.pk + (size_t)(key - d.key_base) * pk_bytes;
+            uint8_t *skk = d.sk + (size_t)(key - d.key_base) * sk_bytes + sk_pk_off;
+            for (int b = tid; b < pk_bytes; b += nth) {
+                pkk[b] = ob[b];
+                skk[b] = ob[b];
+            }
+        }
+        return;
+    }
+    // unpaired leaf: h = g * inv(node), as k_finalize_mma
+    mma_fill_a<P, 1, MODE_SA>(gbuf + (size_t)kl * G::pad, A[0], tid, nth);
+    mma_fill_b<P, 1>(ip, E, tid, nth);
+    __syncthreads();
+    mma_fill_pe<P, 1, MODE_GEN>(E, tid, nth);
+    __syncthreads();
+    float acc[1][1][3][4];
+    const MmaA<P, 1> *const As[1] = {&A[0]};
+    mma_tiles<P, 1, 1, MODE_SA>(E, As, warp, lane, acc);
+    const int bl = (int)E.b[M::p - 1];
+    __syncthreads();
+    mma_stage<P, 1, 1, MODE_SA>(A[0], warp, lane, 0, acc);
+    __syncthreads();
+    uint32_t(*Rb)[G::pad] = reinterpret_cast<uint32_t(*)[G::pad]>(sm);
+    uint8_t *ob = sm + 2 * G::pad * sizeof(uint32_t);
+    for (int k = tid; k < P; k += nth) {
+        int v = (k == 0) ? A[0].u.stage[0] - A[0].u.stage[stage_slot(P - 1)] + (int)A[0].a[0] * bl
+                         : A[0].u.stage[stage_slot(k)] + (int)A[0].a[k] * bl;
+        Rb[0][k] = (uint32_t)(cmod<G::q>(v) + G::half);
+    }
+    __syncthreads();
+    mixed_encode<G::pad>(Rb, S, ob);
+    const BatchDesc d = key_batch(km, kl);
+    uint8_t *pkk = d.pk + (size_t)(kl - d.key_base) * pk_bytes;
+    uint8_t *skk = d.sk + (size_t)(kl - d.key_base) * sk_bytes + sk_pk_off;
+    for (int b = tid; b < pk_bytes; b += nth) {
+        pkk[b] = ob[b];
+        skk[b] = ob[b];
+    }
+}
+
 // Fix-up of the keys whose g needed another attempt (deferred R/3 kernel):
 // h = g * (3f)^-1 with the final g, Rq_encode into pk and sk, and the hash
 // of the new pk into sk.  Runs after the h, hash and R/3 kernels of the call;
-// CTAs take list entries in turn, so an empty list costs one read.
+// CTAs take list entries in turn, so an empty list costs one read.  With
+// leaves (the fused leaf level), ainv holds the level-1 inverses and
+// (3f)^-1 = inv(node) * (3f of the sibling leaf) is formed here first.
 template <int P>
 __global__ void __launch_bounds__(Tp<P>::NT)
 k_fixup(KeyMap km, const int *__restrict__ fix_count, const int *__restrict__ fix_keys,
         const int8_t *__restrict__ gfix, const int16_t *__restrict__ ainv, int pk_bytes,
-        int sk_bytes, int sk_pk_off, int hash_off, EncSched S) {
+        int sk_bytes, int sk_pk_off, int hash_off, EncSched S,
+        const int16_t *__restrict__ leaves, LevelMap lm1) {
     using G = Geo<P>;
     __shared__ __align__(16) int As[Tp<P>::p8];
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
     __shared__ uint32_t Rb[2][G::pad];
     __shared__ uint8_t ob[1344];
+    __shared__ __align__(16) int16_t ik[G::pad];
     const int n = *fix_count;
     for (int f = blockIdx.x; f < n; f += gridDim.x) {
         const int key = fix_keys[f];
         const int16_t *inv = ainv + (size_t)key * G::pad;
         __syncthreads();  // shared buffers free from the previous entry
+        if (leaves) {
+            // leaf row key: subtree b, index i; level-1 node b * sub_out + i / 2
+            const int b = key / lm1.n_in, i = key - b * lm1.n_in;
+            const int16_t *node = ainv + (size_t)(b * lm1.sub_out + i / 2) * G::pad;
+            const int sib = i ^ 1;
+            if (sib < lm1.n_in) {
+                fill_A<P>(leaves + (size_t)(b * lm1.n_in + sib) * G::pad, As);
+                fill_E<P>(node, Es);
+                __syncthreads();
+                int acc[1][8];
+                const int *const A1[1] = {As};
+                toeplitz_tile<P, 1>(A1, Es, threadIdx.x, 0, Tp<P>::p8, acc);
+                const int bl[1] = {(int)node[P - 1]};
+                toeplitz_finish<P, 1>(A1, bl, acc, threadIdx.x, true);
+                const int j0 = 8 * threadIdx.x;
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (j0 + t < G::pad) ik[j0 + t] = (int16_t)(j0 + t < P ? acc[0][t] : 0);
+                inv = ik;
+            } else {
+                inv = node;  // unpaired: the node is the leaf
+            }
+            __syncthreads();
+        }
         fill_A<P>(gfix + (size_t)f * G::pad, As);
         fill_E<P>(inv, Es);
         __syncthreads();
@@ -293,10 +468,31 @@ cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, con
 template <int P>
 cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_keys,
                          const int8_t *gfix, const int16_t *ainv, int pk_bytes, int sk_bytes,
-                         int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st) {
+                         int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st,
+                         const int16_t *leaves, LevelMap lm1) {
     k_fixup<P><<<8, Tp<P>::NT, 0, st>>>(km, fix_count, fix_keys, gfix, ainv, pk_bytes, sk_bytes,
-                                        sk_pk_off, hash_off, S);
+                                        sk_pk_off, hash_off, S, leaves, lm1);
     return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_finalize_pair(const KeyMap &km, int n1, const int8_t *gbuf,
+                                 const int16_t *leaves, const int16_t *inv1, LevelMap lm1,
+                                 int pk_bytes, int sk_bytes, int sk_pk_off, const EncSched &S,
+                                 cudaStream_t st) {
+    if constexpr (!FuseLeaf<P>::ok) {
+        return cudaErrorNotSupported;
+    } else {
+        const size_t sm = sizeof(MmaE<P, 1>) + 2 * sizeof(MmaA<P, 1>) + 2 * Geo<P>::pad * sizeof(int16_t);
+        if (sm > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(
+                k_finalize_pair<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+        }
+        k_finalize_pair<P><<<n1, 32 * MmaGeo<P, 1>::NW, sm, st>>>(km, gbuf, leaves, inv1, lm1,
+                                                                  pk_bytes, sk_bytes, sk_pk_off, S);
+        return cudaGetLastError();
+    }
 }
 
 cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
@@ -324,7 +520,10 @@ cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_b
                                             int, int, int, const EncSched &, cudaStream_t, bool); \
     template cudaError_t launch_fixup<P>(const KeyMap &, const int *, const int *, const int8_t *, \
                                          const int16_t *, int, int, int, int, const EncSched &,   \
-                                         cudaStream_t);
+                                         cudaStream_t, const int16_t *, LevelMap);                \
+    template cudaError_t launch_finalize_pair<P>(const KeyMap &, int, const int8_t *,            \
+                                                 const int16_t *, const int16_t *, LevelMap, int, \
+                                                 int, int, const EncSched &, cudaStream_t);
 SNT_FIN_INST(653)
 SNT_FIN_INST(761)
 SNT_FIN_INST(857)

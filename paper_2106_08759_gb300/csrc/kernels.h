@@ -201,7 +201,13 @@ cudaError_t launch_r3_inv_jump(int n, const int16_t *in, long in_stride, int16_t
 template <int P>
 cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_keys,
                          const int8_t *gfix, const int16_t *ainv, int pk_bytes, int sk_bytes,
-                         int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st);
+                         int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st,
+                         const int16_t *leaves = nullptr, LevelMap lm1 = LevelMap{});
+template <int P>
+cudaError_t launch_finalize_pair(const KeyMap &km, int n1, const int8_t *gbuf,
+                                 const int16_t *leaves, const int16_t *inv1, LevelMap lm1,
+                                 int pk_bytes, int sk_bytes, int sk_pk_off, const EncSched &S,
+                                 cudaStream_t st);
 // h = g * (3f)^-1, Rq_encode(h) into pk and sk; mma: h on the tensor cores.
 template <int P>
 cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, const int16_t *ainv,

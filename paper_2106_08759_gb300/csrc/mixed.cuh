@@ -37,6 +37,42 @@ __device__ __forceinline__ void mixed_encode(uint32_t (*R)[PAD], const EncSched 
     __syncthreads();
 }
 
+// Two value arrays at once (R0 -> ob0, R1 -> ob1), half of the threads on
+// each, one barrier per level.  Contains barriers (all threads call it).
+template <int PAD>
+__device__ __forceinline__ void mixed_encode2(uint32_t (*R0)[PAD], uint32_t (*R1)[PAD],
+                                              const EncSched &S, uint8_t *ob0, uint8_t *ob1) {
+    const int half = blockDim.x / 2;
+    const bool second = (int)threadIdx.x >= half;
+    const int t = second ? threadIdx.x - half : threadIdx.x;
+    uint32_t(*R)[PAD] = second ? R1 : R0;
+    uint8_t *ob = second ? ob1 : ob0;
+    int cur = 0;
+    for (int l = 0; l < S.nlev; ++l) {
+        const EncLevel L = S.lev[l];
+        const uint32_t *rin = R[cur];
+        uint32_t *rout = R[cur ^ 1];
+        for (int i = t; 2 * i < L.n; i += half) {
+            if (2 * i + 1 < L.n) {
+                uint32_t r = rin[2 * i] + L.mu * rin[2 * i + 1];
+                const int e = (2 * i + 1 == L.n - 1) ? L.elast : L.eu;
+                const int off = L.boff + i * L.eu;
+                for (int b = 0; b < e; ++b) { ob[off + b] = (uint8_t)(r & 255u); r >>= 8; }
+                rout[i] = r;
+            } else {
+                rout[i] = rin[2 * i];
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    if (t == 0) {
+        uint32_t r = R[cur][0];
+        for (int b = 0; b < S.efinal; ++b) { ob[S.foff + b] = (uint8_t)(r & 255u); r >>= 8; }
+    }
+    __syncthreads();
+}
+
 // bytes -> values (the inverse, reducing every value modulo its radix as the
 // format's decoder does, so any byte string decodes to in-range values).
 // Returns the buffer index holding R[0..p).  Contains barriers.

@@ -143,15 +143,42 @@ __device__ __forceinline__ void mma_fill_a(const T *__restrict__ a, MmaA<P, NT> 
                 s.a[k] = (int16_t)v[u];
             }
         }
-        if (MODE != MODE_GEN) {  // small coefficients: the value is its own l limb
+        if constexpr (MODE != MODE_GEN) {  // small coefficients: the value is its own l limb
             s.u.sl[r] = make_uint2(h2_small(v[0], v[1]), h2_small(v[2], v[3]));
-            continue;
-        }
-        int h[4], l[4];
+        } else {
+            int h[4], l[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) limbs64(v[u], h[u], l[u]);
-        s.u.hl[r] = make_uint4(h2_small(h[0], h[1]), h2_small(h[2], h[3]), h2_small(l[0], l[1]),
-                               h2_small(l[2], l[3]));
+            for (int u = 0; u < 4; ++u) limbs64(v[u], h[u], l[u]);
+            s.u.hl[r] = make_uint4(h2_small(h[0], h[1]), h2_small(h[2], h[3]), h2_small(l[0], l[1]),
+                                   h2_small(l[2], l[3]));
+        }
+    }
+}
+
+// f16x2 of two integers |lo|, |hi| <= 2048 (exact conversions).
+__device__ __forceinline__ uint32_t h2_int(int lo, int hi) {
+    const __half2 h = __halves2half2(__int2half_rn(lo), __int2half_rn(hi));
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// Vector side with one limb of magnitude up to 2048 (a product of two small
+// elements), from int16 in any memory: the MODE_SA records with the value
+// itself in the l slot.
+template <int P, int NT>
+__device__ __forceinline__ void mma_fill_a_wide(const int16_t *a, MmaA<P, NT> &s, int tid, int nth) {
+    using M = MmaGeo<P, NT>;
+    for (int r = tid; r < M::VBN; r += nth) {
+        const int I = r / 4 - M::PADB, tig = r & 3;
+        int v[4] = {0, 0, 0, 0};
+        if (I >= 0 && I < M::NBLK) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = 16 * I + 2 * tig + (u & 1) + 8 * (u >> 1);
+                v[u] = k < M::p ? (int)a[k] : 0;
+                s.a[k] = (int16_t)v[u];
+            }
+        }
+        s.u.sl[r] = make_uint2(h2_int(v[0], v[1]), h2_int(v[2], v[3]));
     }
 }
 

@@ -324,3 +324,26 @@ def test_host_buffer_entry_point(snt, ctx):
     pk, sk = snt.snt_batch_keygen_host(ctx, 761, SEED, 3, 6)
     rpk, rsk = oracle.keygen_batch(761, SEED, 3, 6)
     assert np.array_equal(pk, rpk) and np.array_equal(sk, rsk)
+
+
+@pytest.mark.parametrize("P,roots,B", [(761, 1, 1), (761, 1, 2), (761, 1, 3), (653, 1, 7),
+                                       (761, 32, 96), (761, 4, 300), (653, 8, 40),
+                                       (761, 64, 4096), (857, 1, 9)])
+def test_fused_leaf_level_gives_the_same_keys(snt, ctx, P, roots, B):
+    # h = 3 inv(P) (g_L f_R) from the level-1 inverses (the leaf level of the
+    # down-sweep skipped) against the leaf level plus h = g (3f)^-1: the same
+    # bytes; B = 2 has the root as its level-1 node, B = 3 and the 32-root
+    # forest of 3-key subtrees have unpaired leaves, 857 keeps the leaf level
+    ctx.set_option(snt.SNT_OPT_ROOTS, roots)
+    try:
+        ctx.set_option(snt.SNT_OPT_FUSE_LEAF, 0)
+        ref = gpu_keygen(snt, ctx, P, 12, 70, B)
+        ctx.set_option(snt.SNT_OPT_FUSE_LEAF, 1)
+        got = gpu_keygen(snt, ctx, P, 12, 70, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_FUSE_LEAF, 1)
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    if B <= 96:
+        rpk, rsk = oracle.keygen_batch(P, 12, 70, B)
+        assert first_mismatch(got[0], rpk) is None and first_mismatch(got[1], rsk) is None
