@@ -32,19 +32,28 @@ METRIC = "sntrup761 keygens/s on 1 GB300, batched vs per-key GPU path; p50/p99 s
 P, Q, W = 761, 4591, 286
 WORDS = (P + 1 + 31) // 32
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+def fused_leaf(tuned, p=None):
+    """Whether the library forms h from the level-1 inverses (its default on
+    the tensor-core engine for p = 653, 761: the leaf level of the down-sweep
+    folded into the h kernel)."""
+    return tuned.get("rq_engine") == 1 and (p or P) in (653, 761)
+
+
 def launches_per_call(B, tuned):
     """Library kernel launches of one batch keygen call under the tuned layouts.
 
-    R/q: sampling, up-sweep (one per level), roots, down-sweep, h, SHA-512;
-    R/3 per key: its kernel and the fix-up; R/3 check-first batch: the check,
-    its forest (2 per level + roots) and the encoding; R/3 first-draw batch:
-    the forest, the encoding, the fall-back kernel and the fix-up."""
+    R/q: sampling, up-sweep (one per level), roots, down-sweep (without its
+    leaf level when fused), h, SHA-512; R/3 per key: its kernel and the
+    fix-up; R/3 check-first batch: the check, its forest (2 per level + roots)
+    and the encoding; R/3 first-draw batch: the forest, the encoding, the
+    fall-back kernel and the fix-up."""
     K = forest_roots(B, tuned.get("roots", 1))
     L, n = 0, B // K
     while n > 1:
         n = (n + 1) // 2
         L += 1
-    rq = 1 + L + 1 + L + 1 + 1
+    down = L - 1 if (fused_leaf(tuned) and L >= 1) else L
+    rq = 1 + L + 1 + down + 1 + 1
     r3 = {0: 2, 1: 1 + 2 * L + 1 + 1, 2: 2 * L + 1 + 1 + 1 + 1}[tuned.get("r3_mode", 0)]
     return rq + r3
 
@@ -54,11 +63,11 @@ def launches_per_call(B, tuned):
 # (profiles/launches_keygen_b4096_sntrup761.md), keyed by kernel; a kernel is
 # absent until a capture of its current code exists.  Writes stay in L2.
 NCU_TRAFFIC_BYTES = {
-    "k_tree_up_mma": 12530000,
-    "k_tree_down_mma": 18790000,
-    "k_rq_inv_jump<761, 4591>": 164096,
-    "k_finalize_mma<761>": 9460000,
-    "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 37770000,
+    "k_tree_up_mma": 12524032,
+    "k_tree_down_mma": 9325056,
+    "k_rq_inv_jump<761, 4591>": 165120,
+    "k_finalize_pair<761>": 12644352,
+    "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 37801728,
 }
 
 
@@ -71,7 +80,8 @@ def kernel_of(phase, tuned):
     mma = tuned.get("rq_engine") == 1
     return {"tree_up": "k_tree_up_mma" if mma else "k_tree_up",
             "tree_down": "k_tree_down_mma" if mma else "k_tree_down",
-            "h_encode": "k_finalize_mma<761>" if mma else "k_finalize<761>",
+            "h_encode": ("k_finalize_pair<761>" if fused_leaf(tuned) else "k_finalize_mma<761>")
+                        if mma else "k_finalize<761>",
             "root_inv": "k_rq_inv_jump<761, 4591>"}[phase]
 
 
@@ -212,24 +222,36 @@ def _measured_peaks():
         return {}
 
 
-def ops_per_call(B, K=1, r3_mode=0, p=P):
+def ops_per_call(B, K=1, r3_mode=0, p=P, fused=False):
     """Algorithmic integer operations of each phase for one call of B keys in
     K subtrees.
 
     Products count p^2 multiply-adds (the Toeplitz/schoolbook form every
     product kernel computes; a forest of K subtrees has B - K products up and
-    2(B - K) down); the per-key R/3 divsteps count 6 word operations per
-    32-trit word for each of the two polynomial updates per step (bit-sliced
-    F_3 multiply-add), the R/3 batch paths their 3(B - K) products mod 3; a
-    root inversion counts 2 multiply-reduce updates of p + 1 coefficients per
-    step."""
+    2(B - K) down, h one per key); with the fused leaf level the down-sweep
+    stops at level 1 (2 products per pair above it) and h costs, per leaf
+    pair, g_L f_R, g_R f_L and inv(P) s for both keys (an unpaired leaf one);
+    the per-key R/3 divsteps count 6 word operations per 32-trit word for each
+    of the two polynomial updates per step (bit-sliced F_3 multiply-add), the
+    R/3 batch paths their 3(B - K) products mod 3; a root inversion counts 2
+    multiply-reduce updates of p + 1 coefficients per step."""
     steps = 2 * p - 1
     mac = p * p
+    n0 = B // K
+    pairs, n = [], n0
+    while n > 1:
+        pairs.append(n // 2)
+        n = (n + 1) // 2
+    if fused and pairs:
+        down = 2 * (n0 - 1 - pairs[0]) * K
+        h = (4 * pairs[0] + (n0 - 2 * pairs[0])) * K
+    else:
+        down, h = 2 * (B - K), B
     return {
         "r3_inv": B * steps * 2 * WORDS * 6 if r3_mode == 0 else 3 * (B - K) * mac,
         "tree_up": (B - K) * mac,
-        "tree_down": 2 * (B - K) * mac,
-        "h_encode": B * mac,
+        "tree_down": down * mac,
+        "h_encode": h * mac,
         "root_inv": K * steps * 2 * (p + 1),
     }
 
@@ -346,13 +368,15 @@ def run_ours(args):
     # phase runs beside the tree (auxiliary stream) unless its overlap is 0.
     K = forest_roots(B, tuned.get("roots", 1))
     r3m = tuned.get("r3_mode", 0)
-    ops = ops_per_call(B, K, r3m)
+    fused = fused_leaf(tuned)
+    ops = ops_per_call(B, K, r3m, fused=fused)
     Lk = 0
     n = B // K
     while n > 1:
         n = (n + 1) // 2
         Lk += 1
-    launches_of = {"r3_inv": 1 if r3m == 0 else 2 * Lk + 3, "tree_up": Lk, "tree_down": Lk,
+    launches_of = {"r3_inv": 1 if r3m == 0 else 2 * Lk + 3, "tree_up": Lk,
+                   "tree_down": Lk - 1 if (fused and Lk >= 1) else Lk,
                    "h_encode": 1, "root_inv": 1}
     tensor_phases = TENSOR_PHASES + (("r3_inv",) if r3m else ())
 

@@ -316,8 +316,12 @@ snt_status keygen_common(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, siz
         default:  s = run_keygen<857>(ctx, pi, seed, first, B, dpk, dsk, st, batched, ctx->arena); break;
     }
     if (s != SNT_OK || !host_out) return s;
+    // the two copies on two streams (two copy engines at once); snt_ctx_sync
+    // waits for both
+    SNT_CUDA(cudaEventRecord(ctx->ev_fork, st));
+    SNT_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
     SNT_CUDA(cudaMemcpyAsync(pk, dpk, B * pi.pk_bytes, cudaMemcpyDeviceToHost, st));
-    SNT_CUDA(cudaMemcpyAsync(sk, dsk, B * pi.sk_bytes, cudaMemcpyDeviceToHost, st));
+    SNT_CUDA(cudaMemcpyAsync(sk, dsk, B * pi.sk_bytes, cudaMemcpyDeviceToHost, ctx->aux));
     return snt_ctx_sync(ctx, stream);
 }
 
