@@ -414,6 +414,24 @@ def run_ours(args):
         }
 
     phase_roofline = {ph: roofline_of(ph) for ph in ops}
+    # the whole path's algorithmic operations per key (the formula of each
+    # phase above, summed) at the measured key rate, against the measured
+    # integer multiply-add stream
+    ops_key = sum(ops.values()) / B
+    path_rate = value * ops_key
+    path_ops = {
+        "formula": ("per call: R/q products (up B-K, down and h as counted with the fused "
+                    "leaf level) x p^2 multiply-adds, root inversions K x (2p-1) x 2(p+1) "
+                    "multiply-reduces, R/3 " + ("per-key bit-sliced divsteps (word ops)"
+                                                if r3m == 0 else "batch products 3(B-K) x p^2 "
+                                                "multiply-adds mod 3") + "; divided by B"),
+        "ops_per_key": round(ops_key),
+        "rate_tops": round(path_rate / 1e12, 3),
+        "int32_peak_tops": round(imad_peak / 1e12, 3),
+        "frac_of_int32_peak": round(path_rate / imad_peak, 3),
+        "note": "the products run on the tensor cores (f16 warp MMA with exact limbs), so the "
+                "path can exceed the integer multiply-add peak",
+    }
     critical = [ph for ph in ops if ph != "r3_inv" or tuned.get("r3_overlap", 1) == 0]
     dom = max(critical, key=lambda ph: phase.get(ph, 0.0))
     roofline = dict(phase_roofline[dom])
@@ -464,6 +482,7 @@ def run_ours(args):
                            "sms": sms},
         "roofline": roofline,
         "phase_roofline": phase_roofline,
+        "path_ops": path_ops,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_rate, 1), "unit": "keys/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": B * (pkb + skb)},
