@@ -144,9 +144,10 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 // outputs, zeroing what the older state left above them in the target
 // buffer.  F, G shrink while V, R grow, their extents summing to about
 // p + 2, so a chunk applies the matrix to about p + 34 coefficients rather
-// than to four full-length polynomials.  Applier warps avoid the warp ids
-// that share the leader's scheduler (warp w issues on scheduler w % 4), so
-// the leader's serial chain keeps a scheduler to itself.
+// than to four full-length polynomials.  Every warp but the leader is an
+// applier: the appliers set the chunk time, so the tensor units and issue
+// slots of the leader's scheduler are worth more to them than a scheduler
+// of its own is to the leader (measured: 119 -> 113 us per root).
 //
 // The application on the tensor cores.  Each output of a pair is a sum of
 // two Toeplitz products with the chunk matrix: with T_e[i][j] = e[i - j + o],
@@ -163,7 +164,7 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 // byte permutes; the leader reads an int copy of the low 64 coefficients of
 // F and G, and the inverse is read back from V's limbs at the end.  An item
 // is one 128-output tile of one pair (at most eight per chunk, one per applier
-// warp, three applier warps per scheduler): D runs over
+// warp, two per scheduler): D runs over
 // the 3 or 4 values where some T_e block is nonzero, three limb products per
 // operand pair (Karatsuba: h h', l l', (h + l)(h' + l'); one, l l', when every
 // value is in {-1, 0, 1}); a sum has at most 64 terms, so every limb sum is
@@ -176,9 +177,9 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 template <int P> struct JumpGeo {
     static constexpr int M = 31;                        // steps per chunk
     static constexpr int OFF = 32;                      // zero margin below index 0
-    static constexpr int NWA = 9;                       // applier warps (ids 1-3, 5-7, 9-11)
+    static constexpr int NWA = 11;                      // applier warps (ids 1-11)
     static constexpr int NA = 32 * NWA;                 // applier threads
-    static constexpr int NW = 12;                       // leader, 9 appliers, 2 idle
+    static constexpr int NW = 12;                       // leader, 11 appliers
     static constexpr int NT = 32 * NW;
     // a tile reads blocks up to two past its last output block (D >= -2)
     static constexpr int LEN = (OFF + P + 160 + 31) / 32 * 32;  // slots per polynomial
@@ -412,8 +413,8 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
             } else if (lane == 0) {
                 s_ok = (delta == 0);
             }
-        } else if ((tid >> 5) & 3) {
-            const int w = tid >> 5, ai = w - 1 - (w - 1) / 4;
+        } else {
+            const int w = tid >> 5, ai = w - 1;
             const int at = 32 * ai + lane;
             // live ranges of the outputs and what the target buffer held
             const int rfg = ext[c & 3][0], rvr = min(ext[c & 3][1] + m + 1, P + 1);
