@@ -174,12 +174,17 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 // (G(0) = 0 mod q iff G(0) is -q, 0 or q); the matrix and the state are
 // centred between chunks, so a 64-term application sum stays below 2^31.
 // ---------------------------------------------------------------------------
-template <int P> struct JumpGeo {
+template <int P, int Q = Geo<P>::q> struct JumpGeo {
     static constexpr int M = 31;                        // steps per chunk
     static constexpr int OFF = 32;                      // zero margin below index 0
-    static constexpr int NWA = 11;                      // applier warps (ids 1-11)
+    // applier warps: in R/q every warp but the leader (ids 1-11); in R/3 an
+    // operand pair is one MMA, and six appliers on the three schedulers that
+    // are not the leader's (ids 1-3, 5-7; warp 4 idle) keep up with the leader
+    // while leaving its scheduler, and SM resources, to others
+    static constexpr bool SPARE = Q < 64;
+    static constexpr int NWA = SPARE ? 6 : 11;
     static constexpr int NA = 32 * NWA;                 // applier threads
-    static constexpr int NW = 12;                       // leader, 11 appliers
+    static constexpr int NW = SPARE ? 8 : 12;           // leader, appliers, idle
     static constexpr int NT = 32 * NW;
     // a tile reads blocks up to two past its last output block (D >= -2)
     static constexpr int LEN = (OFF + P + 160 + 31) / 32 * 32;  // slots per polynomial
@@ -327,10 +332,10 @@ __device__ __forceinline__ void jump_mma(float (&acc)[SMALL ? 1 : 3][4], const u
 // Q: the coefficient modulus (q: R/q; 3: R/3, for the root inversions of
 // the R/3 batch inversion).
 template <int P, int Q = Geo<P>::q>
-__global__ void __launch_bounds__(JumpGeo<P>::NT, 1)
+__global__ void __launch_bounds__(JumpGeo<P, Q>::NT, 1)
 k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_stride,
               int32_t *__restrict__ okv, int *__restrict__ err, int err_bit, const int *idx) {
-    using JG = JumpGeo<P>;
+    using JG = JumpGeo<P, Q>;
     constexpr int LEN = JG::LEN, OFF = JG::OFF, NT = JG::NT;
     constexpr bool SMALL = Q < 64;  // every value in {-1, 0, 1}: the l limbs only
     constexpr int NCH = (2 * P - 1 + JG::M - 1) / JG::M;
@@ -413,8 +418,8 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
             } else if (lane == 0) {
                 s_ok = (delta == 0);
             }
-        } else {
-            const int w = tid >> 5, ai = w - 1;
+        } else if (!JG::SPARE || ((tid >> 5) & 3)) {
+            const int w = tid >> 5, ai = JG::SPARE ? w - 1 - (w - 1) / 4 : w - 1;
             const int at = 32 * ai + lane;
             // live ranges of the outputs and what the target buffer held
             const int rfg = ext[c & 3][0], rvr = min(ext[c & 3][1] + m + 1, P + 1);
@@ -429,8 +434,8 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
             }
             if (at == 0) { ext[(c + 2) & 3][0] = 0; ext[(c + 2) & 3][1] = 0; }
             // pair tables of this chunk's matrix, then the appliers' barrier
-            if (at < 4 * 33) {
-                const int en = at / 33, k = at % 33;
+            for (int pe = at; pe < 4 * 33; pe += JG::NA) {
+                const int en = pe / 33, k = pe % 33;
                 const int e0 = A[en][4 + k], e1 = A[en][3 + k];  // e[k], e[k-1]; zero at 32 and -1
                 int h0, l0, h1, l1;
                 limbs64(e0, h0, l0);
@@ -537,7 +542,7 @@ template <int P>
 cudaError_t launch_r3_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
                                cudaStream_t st) {
-    k_rq_inv_jump<P, 3><<<n, JumpGeo<P>::NT, 0, st>>>(n, in, in_stride, out, out_stride, ok, err,
+    k_rq_inv_jump<P, 3><<<n, JumpGeo<P, 3>::NT, 0, st>>>(n, in, in_stride, out, out_stride, ok, err,
                                                       err_bit, nullptr);
     return cudaGetLastError();
 }
