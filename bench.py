@@ -63,11 +63,11 @@ def launches_per_call(B, tuned):
 # (profiles/launches_keygen_b4096_sntrup761.md), keyed by kernel; a kernel is
 # absent until a capture of its current code exists.  Writes stay in L2.
 NCU_TRAFFIC_BYTES = {
-    "k_tree_up_mma": 12522752,
+    "k_tree_up_mma": 12521984,
     "k_tree_down_mma": 9325056,
-    "k_rq_inv_jump<761, 4591>": 165120,
-    "k_finalize_pair<761>": 12658176,
-    "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 37793024,
+    "k_rq_inv_jump<761, 4591>": 166400,
+    "k_finalize_pair<761>": 12645888,
+    "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 37782016,
 }
 
 
