@@ -43,7 +43,8 @@ def launches_per_call(B, tuned):
     """Library kernel launches of one batch keygen call under the tuned layouts.
 
     R/q: sampling, up-sweep (one per level), roots, down-sweep (without its
-    leaf level when fused), h, SHA-512; R/3 per key: its kernel and the
+    leaf level when fused), h, SHA-512, and with the fused leaf level (unless
+    g is redrawn before h) the leaf-pair products s on the side stream; R/3 per key: its kernel and the
     fix-up; R/3 check-first batch: the check, its forest (2 per level + roots)
     and the encoding; R/3 first-draw batch: the forest, the encoding, the
     fall-back kernel and the fix-up."""
@@ -52,8 +53,10 @@ def launches_per_call(B, tuned):
     while n > 1:
         n = (n + 1) // 2
         L += 1
-    down = L - 1 if (fused_leaf(tuned) and L >= 1) else L
-    rq = 1 + L + 1 + down + 1 + 1
+    fused = fused_leaf(tuned) and L >= 1
+    down = L - 1 if fused else L
+    side = 1 if (fused and tuned.get("r3_mode", 0) != 1) else 0  # leaf-pair products s
+    rq = 1 + L + 1 + down + 1 + 1 + side
     r3 = {0: 2, 1: 1 + 2 * L + 1 + 1, 2: 2 * L + 1 + 1 + 1 + 1}[tuned.get("r3_mode", 0)]
     return rq + r3
 
@@ -66,7 +69,6 @@ NCU_TRAFFIC_BYTES = {
     "k_tree_up_mma": 12521984,
     "k_tree_down_mma": 9325056,
     "k_rq_inv_jump<761, 4591>": 166400,
-    "k_finalize_pair<761>": 12645888,
     "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 37782016,
 }
 
@@ -222,7 +224,7 @@ def _measured_peaks():
         return {}
 
 
-def ops_per_call(B, K=1, r3_mode=0, p=P, fused=False):
+def ops_per_call(B, K=1, r3_mode=0, p=P, fused=False, s_side=False):
     """Algorithmic integer operations of each phase for one call of B keys in
     K subtrees.
 
@@ -230,7 +232,9 @@ def ops_per_call(B, K=1, r3_mode=0, p=P, fused=False):
     product kernel computes; a forest of K subtrees has B - K products up and
     2(B - K) down, h one per key); with the fused leaf level the down-sweep
     stops at level 1 (2 products per pair above it) and h costs, per leaf
-    pair, g_L f_R, g_R f_L and inv(P) s for both keys (an unpaired leaf one);
+    pair, g_L f_R, g_R f_L and inv(P) s for both keys (an unpaired leaf one),
+    of which the two s products are counted as "leaf_s" when they run on the
+    side stream beside the root inversions (no phase time of their own);
     the per-key R/3 divsteps count 6 word operations per 32-trit word for each
     of the two polynomial updates per step (bit-sliced F_3 multiply-add), the
     R/3 batch paths their 3(B - K) products mod 3; a root inversion counts 2
@@ -242,18 +246,25 @@ def ops_per_call(B, K=1, r3_mode=0, p=P, fused=False):
     while n > 1:
         pairs.append(n // 2)
         n = (n + 1) // 2
+    side = 0
     if fused and pairs:
         down = 2 * (n0 - 1 - pairs[0]) * K
         h = (4 * pairs[0] + (n0 - 2 * pairs[0])) * K
+        if s_side:
+            side = 2 * pairs[0] * K
+            h -= side
     else:
         down, h = 2 * (B - K), B
-    return {
+    ops = {
         "r3_inv": B * steps * 2 * WORDS * 6 if r3_mode == 0 else 3 * (B - K) * mac,
         "tree_up": (B - K) * mac,
         "tree_down": down * mac,
         "h_encode": h * mac,
         "root_inv": K * steps * 2 * (p + 1),
     }
+    if side:
+        ops["leaf_s"] = side * mac
+    return ops
 
 
 PIPE_OF = {"r3_inv": "lop3", "tree_up": "imad", "tree_down": "imad", "h_encode": "imad",
@@ -369,7 +380,7 @@ def run_ours(args):
     K = forest_roots(B, tuned.get("roots", 1))
     r3m = tuned.get("r3_mode", 0)
     fused = fused_leaf(tuned)
-    ops = ops_per_call(B, K, r3m, fused=fused)
+    ops = ops_per_call(B, K, r3m, fused=fused, s_side=fused and r3m != 1)
     Lk = 0
     n = B // K
     while n > 1:
@@ -377,7 +388,7 @@ def run_ours(args):
         Lk += 1
     launches_of = {"r3_inv": 1 if r3m == 0 else 2 * Lk + 3, "tree_up": Lk,
                    "tree_down": Lk - 1 if (fused and Lk >= 1) else Lk,
-                   "h_encode": 1, "root_inv": 1}
+                   "h_encode": 1, "root_inv": 1, "leaf_s": 1}
     tensor_phases = TENSOR_PHASES + (("r3_inv",) if r3m else ())
 
     def roofline_of(ph):
@@ -413,7 +424,7 @@ def run_ours(args):
             "traffic": NCU_TRAFFIC_BYTES.get(kernel_of(ph, tuned)),
         }
 
-    phase_roofline = {ph: roofline_of(ph) for ph in ops}
+    phase_roofline = {ph: roofline_of(ph) for ph in ops if ph in phase}
     # the whole path's algorithmic operations per key (the formula of each
     # phase above, summed) at the measured key rate, against the measured
     # integer multiply-add stream

@@ -177,6 +177,17 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         return SNT_OK;
     };
     bool forked = false, joined = false;
+    // fused leaf level (h from the level-1 inverses): its leaf-pair products
+    // s = g_L f_R need only the draws, so they run on a side stream beside
+    // the root inversions; with R/3 mode 1 (g redrawn before h) or a single
+    // stream the h kernel forms them itself
+    if (batched) {
+        const Forest f1 = make_forest(B, roots);
+        fuse = mma && ctx->fuse_leaf && FuseLeaf<P>::ok && f1.t.n.size() >= 2;
+        if (fuse) { n1 = f1.t.n[1]; lm1 = equal_subtrees(f1.sub[0], f1.sub[1]); }
+    }
+    const bool s_ahead = fuse && !inline_stream && !r3chk;
+    int16_t *sbuf = reinterpret_cast<int16_t *>(arena + s_offset(pi, B));
     if (tm) SNT_CUDA(cudaEventRecord(ev[0], st));
     SNT_CUDA(launch_sample_f<P>(km, Bi, leaves, pi.sk_bytes, 2 * sb + pi.pk_bytes, st, gbuf,
                                 ctx->d_inj_idx, ctx->d_inj_g, n_inj, fix_count,
@@ -225,6 +236,12 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
             forked = true;
         }
         if (tm) SNT_CUDA(cudaEventRecord(ev[4], st));
+        if (s_ahead) {  // the K root inversions leave most SMs free
+            SNT_CUDA(cudaEventRecord(ctx->ev_sfork, st));
+            SNT_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_sfork, 0));
+            SNT_CUDA(launch_leaf_s<P>(n1, gbuf, leaves, lm1, sbuf, ctx->side));
+            SNT_CUDA(cudaEventRecord(ctx->ev_sready, ctx->side));
+        }
         int16_t *root = nodes + (size_t)t.off[L] * pi.pad;
         SNT_CUDA(launch_rq_inv_jump<P>(fo.K, root, pi.pad, root, pi.pad, nullptr, ctx->d_err,
                                        ERR_ROOT, st));
@@ -235,8 +252,6 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         const int16_t *par = root;
         int ping = 0;
         // fused leaf level: stop at the level-1 inverses, h is formed from them
-        fuse = mma && ctx->fuse_leaf && FuseLeaf<P>::ok && L >= 1;
-        if (fuse) { n1 = t.n[1]; lm1 = lmap(1); }
         for (int l = L; l >= (fuse ? 2 : 1); --l) {
             int16_t *lch = nodes + (size_t)t.off[l - 1] * pi.pad;
             if (mma) {  // in place on every level
@@ -266,9 +281,12 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     }
     if (r3chk && !joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_gready, 0));  // final g's
     if (tm) SNT_CUDA(cudaEventRecord(ev[7], st));
-    if (fuse)
+    if (fuse) {
+        if (s_ahead) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_sready, 0));
         SNT_CUDA(launch_finalize_pair<P>(km, n1, gbuf, leaves, inv_leaves, lm1, pi.pk_bytes,
-                                         pi.sk_bytes, 2 * sb, pi.sched, st));
+                                         pi.sk_bytes, 2 * sb, pi.sched, st,
+                                         s_ahead ? sbuf : nullptr));
+    }
     else
         SNT_CUDA(launch_finalize<P>(km, Bi, gbuf, inv_leaves, pi.pk_bytes, pi.sk_bytes, 2 * sb,
                                     pi.sched, st, mma));
@@ -375,9 +393,12 @@ snt_status snt_ctx_create(int device, size_t mem_budget, snt_ctx **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_low);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->tree, cudaStreamNonBlocking, prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->tune, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_low);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_r3fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_gready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sfork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     for (int i = 0; i < kPhaseEvents && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev_phase[i]);
@@ -394,6 +415,7 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     DeviceGuard dg(ctx->device);
     if (ctx->aux) cudaStreamSynchronize(ctx->aux);
     if (ctx->tree) cudaStreamSynchronize(ctx->tree);
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
     cudaDeviceSynchronize();
     if (ctx->arena) {
         cudaMemset(ctx->arena, 0, ctx->budget);  // secret-bearing scratch
@@ -409,11 +431,14 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
     if (ctx->ev_r3fork) cudaEventDestroy(ctx->ev_r3fork);
     if (ctx->ev_gready) cudaEventDestroy(ctx->ev_gready);
+    if (ctx->ev_sfork) cudaEventDestroy(ctx->ev_sfork);
+    if (ctx->ev_sready) cudaEventDestroy(ctx->ev_sready);
     for (uint32_t *f : ctx->d_r3fac)
         if (f) cudaFree(f);
     if (ctx->ragged.exec) cudaGraphExecDestroy(ctx->ragged.exec);
     if (ctx->tree) cudaStreamDestroy(ctx->tree);
     if (ctx->tune) cudaStreamDestroy(ctx->tune);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     delete ctx;
@@ -439,6 +464,7 @@ snt_status snt_ctx_sync(snt_ctx *ctx, snt_stream stream) {
     SNT_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
     SNT_CUDA(cudaStreamSynchronize(ctx->aux));
     SNT_CUDA(cudaStreamSynchronize(ctx->tree));
+    SNT_CUDA(cudaStreamSynchronize(ctx->side));
     int err = 0;
     SNT_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {

@@ -41,6 +41,8 @@ struct snt_ctx {
     cudaStream_t tree = nullptr;  // high priority: sampling, product tree, h, hash
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr, ev_r3fork = nullptr;
     cudaEvent_t ev_gready = nullptr;       // R/3 batch path: every g final
+    cudaStream_t side = nullptr;  // low priority: leaf-pair products s beside the root inversions
+    cudaEvent_t ev_sfork = nullptr, ev_sready = nullptr;  // fork to / join from the side stream
     uint32_t *d_r3fac[3] = {nullptr, nullptr, nullptr};  // F_3 factors per parameter set
     bool timing = false;
     cudaEvent_t ev_phase[snt::kPhaseEvents] = {};

@@ -104,6 +104,59 @@ k_finalize_mma(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__rest
     }
 }
 
+// s = g f for one key of a leaf pair: g's draw (int8 row) against f = (3f)/3
+// of the other leaf, both small (one MMA per step); |s| <= 2w, so the row is
+// exact without reduction.  Written to sv (any memory, pad entries) by the
+// whole CTA; contains barriers.
+template <int P>
+__device__ __forceinline__ void leaf_pair_s(const int8_t *g, const int16_t *f3, MmaE<P, 1> &E,
+                                            MmaA<P, 1> &A, int16_t *sv, int warp, int lane,
+                                            int tid, int nth) {
+    using G = Geo<P>;
+    using M = MmaGeo<P, 1>;
+    mma_fill_a<P, 1, MODE_SAE>(g, A, tid, nth);
+    for (int k = tid; k < M::AN; k += nth) E.b[k] = k < M::p ? (int16_t)(f3[k] / 3) : 0;
+    __syncthreads();
+    mma_fill_pe<P, 1, MODE_SAE>(E, tid, nth);
+    __syncthreads();
+    float acc[1][1][3][4];
+    const MmaA<P, 1> *const As[1] = {&A};
+    mma_tiles<P, 1, 1, MODE_SAE>(E, As, warp, lane, acc);
+    __syncthreads();
+    mma_stage<P, 1, 1, MODE_SAE>(A, warp, lane, 0, acc);
+    __syncthreads();
+    const int bl = (int)E.b[M::p - 1];
+    for (int k = tid; k < G::pad; k += nth) {
+        int v = 0;
+        if (k == 0) v = A.u.stage[0] - A.u.stage[stage_slot(M::p - 1)] + (int)A.a[0] * bl;
+        else if (k < M::p) v = A.u.stage[stage_slot(k)] + (int)A.a[k] * bl;
+        sv[k] = (int16_t)v;
+    }
+    __syncthreads();
+}
+
+// The leaf-pair products of every level-1 node into rows of sbuf (by key),
+// ahead of the down-sweep (they need only g's draws and the leaves).
+template <int P>
+__global__ void __launch_bounds__(32 * MmaGeo<P, 1>::NW)
+k_leaf_s(const int8_t *__restrict__ gbuf, const int16_t *__restrict__ leaves, LevelMap lm1,
+         int16_t *__restrict__ sbuf) {
+    using G = Geo<P>;
+    extern __shared__ __align__(16) uint8_t sm[];
+    MmaE<P, 1> &E = *reinterpret_cast<MmaE<P, 1> *>(sm);
+    MmaA<P, 1> &A = *reinterpret_cast<MmaA<P, 1> *>(sm + sizeof(MmaE<P, 1>));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nth = blockDim.x, tid = threadIdx.x;
+    int idx, base, n_in;
+    lm_node(lm1, blockIdx.x, idx, base, n_in);
+    if (2 * idx + 1 >= n_in) return;  // unpaired leaf: h = g inv(node) needs no s
+    const int kl = base + 2 * idx;
+    for (int side = 0; side < 2; ++side) {
+        const int kg = kl + side, kf = kl + 1 - side;
+        leaf_pair_s<P>(gbuf + (size_t)kg * G::pad, leaves + (size_t)kf * G::pad, E, A,
+                       sbuf + (size_t)kg * G::pad, warp, lane, tid, nth);
+    }
+}
+
 // h for the two keys under a level-1 node j of the product forest, whose
 // inverse inv(P_j) the down-sweep leaves at its row (the leaf level of the
 // down-sweep is not run).  With P_j = (3 f_L)(3 f_R),
@@ -120,7 +173,7 @@ template <int P>
 __global__ void __launch_bounds__(32 * MmaGeo<P, 1>::NW)
 k_finalize_pair(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__restrict__ leaves,
                 const int16_t *__restrict__ inv1, LevelMap lm1, int pk_bytes, int sk_bytes,
-                int sk_pk_off, EncSched S) {
+                int sk_pk_off, EncSched S, const int16_t *__restrict__ sbuf) {
     using G = Geo<P>;
     using M = MmaGeo<P, 1>;
     static_assert(FuseLeaf<P>::ok, "limb sums of the fused leaf level exceed 2^24");
@@ -138,33 +191,20 @@ k_finalize_pair(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__res
     const bool paired = 2 * idx + 1 < n_in;
     const int16_t *ip = inv1 + (size_t)j * G::pad;
     if (paired) {
-        for (int side = 0; side < 2; ++side) {  // s = g_kg f_kf
-            const int kg = kl + side, kf = kl + 1 - side;
-            mma_fill_a<P, 1, MODE_SAE>(gbuf + (size_t)kg * G::pad, A[0], tid, nth);
-            const int16_t *fr = leaves + (size_t)kf * G::pad;  // 3f
-            for (int k = tid; k < M::AN; k += nth) E.b[k] = k < M::p ? (int16_t)(fr[k] / 3) : 0;
-            __syncthreads();
-            mma_fill_pe<P, 1, MODE_SAE>(E, tid, nth);
-            __syncthreads();
-            float acc[1][1][3][4];
-            const MmaA<P, 1> *const As[1] = {&A[0]};
-            mma_tiles<P, 1, 1, MODE_SAE>(E, As, warp, lane, acc);
-            __syncthreads();
-            mma_stage<P, 1, 1, MODE_SAE>(A[0], warp, lane, 0, acc);
-            __syncthreads();
-            const int bl = (int)E.b[M::p - 1];
-            for (int k = tid; k < G::pad; k += nth) {  // |s| <= 2w: exact, no reduction
-                int v = 0;
-                if (k == 0) v = A[0].u.stage[0] - A[0].u.stage[stage_slot(M::p - 1)] + (int)A[0].a[0] * bl;
-                else if (k < M::p) v = A[0].u.stage[stage_slot(k)] + (int)A[0].a[k] * bl;
-                sv[side][k] = (int16_t)v;
-            }
-            __syncthreads();
+        const int16_t *s0 = sv[0], *s1 = sv[1];
+        if (sbuf) {  // formed ahead by k_leaf_s
+            s0 = sbuf + (size_t)kl * G::pad;
+            s1 = sbuf + (size_t)(kl + 1) * G::pad;
+        } else {
+            for (int side = 0; side < 2; ++side)  // s = g_kg f_kf
+                leaf_pair_s<P>(gbuf + (size_t)(kl + side) * G::pad,
+                               leaves + (size_t)(kl + 1 - side) * G::pad, E, A[0], sv[side], warp,
+                               lane, tid, nth);
         }
         // h' = inv(P_j) s for both keys, one pair table of inv(P_j)
         mma_fill_b<P, 1>(ip, E, tid, nth);
-        mma_fill_a_wide<P, 1>(sv[0], A[0], tid, nth);
-        mma_fill_a_wide<P, 1>(sv[1], A[1], tid, nth);
+        mma_fill_a_wide<P, 1>(s0, A[0], tid, nth);
+        mma_fill_a_wide<P, 1>(s1, A[1], tid, nth);
         __syncthreads();
         mma_fill_pe<P, 1, MODE_GEN>(E, tid, nth);
         __syncthreads();
@@ -479,7 +519,7 @@ template <int P>
 cudaError_t launch_finalize_pair(const KeyMap &km, int n1, const int8_t *gbuf,
                                  const int16_t *leaves, const int16_t *inv1, LevelMap lm1,
                                  int pk_bytes, int sk_bytes, int sk_pk_off, const EncSched &S,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const int16_t *sbuf) {
     if constexpr (!FuseLeaf<P>::ok) {
         return cudaErrorNotSupported;
     } else {
@@ -490,7 +530,20 @@ cudaError_t launch_finalize_pair(const KeyMap &km, int n1, const int8_t *gbuf,
             if (e != cudaSuccess) return e;
         }
         k_finalize_pair<P><<<n1, 32 * MmaGeo<P, 1>::NW, sm, st>>>(km, gbuf, leaves, inv1, lm1,
-                                                                  pk_bytes, sk_bytes, sk_pk_off, S);
+                                                                  pk_bytes, sk_bytes, sk_pk_off, S,
+                                                                  sbuf);
+        return cudaGetLastError();
+    }
+}
+
+template <int P>
+cudaError_t launch_leaf_s(int n1, const int8_t *gbuf, const int16_t *leaves, LevelMap lm1,
+                          int16_t *sbuf, cudaStream_t st) {
+    if constexpr (!FuseLeaf<P>::ok) {
+        return cudaErrorNotSupported;
+    } else {
+        const size_t sm = sizeof(MmaE<P, 1>) + sizeof(MmaA<P, 1>);
+        k_leaf_s<P><<<n1, 32 * MmaGeo<P, 1>::NW, sm, st>>>(gbuf, leaves, lm1, sbuf);
         return cudaGetLastError();
     }
 }
@@ -523,7 +576,10 @@ cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_b
                                          cudaStream_t, const int16_t *, LevelMap);                \
     template cudaError_t launch_finalize_pair<P>(const KeyMap &, int, const int8_t *,            \
                                                  const int16_t *, const int16_t *, LevelMap, int, \
-                                                 int, int, const EncSched &, cudaStream_t);
+                                                 int, int, const EncSched &, cudaStream_t,        \
+                                                 const int16_t *);                                \
+    template cudaError_t launch_leaf_s<P>(int, const int8_t *, const int16_t *, LevelMap,        \
+                                          int16_t *, cudaStream_t);
 SNT_FIN_INST(653)
 SNT_FIN_INST(761)
 SNT_FIN_INST(857)

@@ -179,9 +179,14 @@ constexpr size_t kR3OkBytes = 4 * 1024;
 inline size_t r3_scratch(const ParamInfo &pi, size_t B) {
     return align256(make_tree(B).total * pi.pad * sizeof(int16_t)) + kR3OkBytes;
 }
+// ... then the leaf-pair products s = g_L f_R, g_R f_L of the fused leaf
+// level (int16 rows, stride pad, one per key).
+inline size_t s_scratch(const ParamInfo &pi, size_t B) {
+    return align256(B * pi.pad * sizeof(int16_t));
+}
 inline size_t keygen_arena(const ParamInfo &pi, size_t B, bool host_out) {
     return keygen_scratch(pi, B, host_out) + narrow_scratch(pi) + fix_scratch(pi, B) +
-           r3_scratch(pi, B);
+           r3_scratch(pi, B) + s_scratch(pi, B);
 }
 // Arena layout of a context keygen call: tree nodes, g rows, the ping-pong
 // buffers, the resampling list, then (host-buffer calls) the pk and sk
@@ -192,8 +197,11 @@ inline size_t fix_offset(const ParamInfo &pi, size_t B) {
 inline size_t r3_offset(const ParamInfo &pi, size_t B) {
     return fix_offset(pi, B) + fix_scratch(pi, B);
 }
-inline size_t staging_offset(const ParamInfo &pi, size_t B) {
+inline size_t s_offset(const ParamInfo &pi, size_t B) {
     return r3_offset(pi, B) + r3_scratch(pi, B);
+}
+inline size_t staging_offset(const ParamInfo &pi, size_t B) {
+    return s_offset(pi, B) + s_scratch(pi, B);
 }
 
 struct DeviceGuard {

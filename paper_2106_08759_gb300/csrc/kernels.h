@@ -203,11 +203,17 @@ cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_
                          const int8_t *gfix, const int16_t *ainv, int pk_bytes, int sk_bytes,
                          int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st,
                          const int16_t *leaves = nullptr, LevelMap lm1 = LevelMap{});
+// sbuf (optional): the leaf-pair products s of launch_leaf_s, else formed here.
 template <int P>
 cudaError_t launch_finalize_pair(const KeyMap &km, int n1, const int8_t *gbuf,
                                  const int16_t *leaves, const int16_t *inv1, LevelMap lm1,
                                  int pk_bytes, int sk_bytes, int sk_pk_off, const EncSched &S,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const int16_t *sbuf = nullptr);
+// s_L = g_L f_R and s_R = g_R f_L of every leaf pair (rows of sbuf by key),
+// ahead of the down-sweep; needs only g's draws and the leaves.
+template <int P>
+cudaError_t launch_leaf_s(int n1, const int8_t *gbuf, const int16_t *leaves, LevelMap lm1,
+                          int16_t *sbuf, cudaStream_t st);
 // h = g * (3f)^-1, Rq_encode(h) into pk and sk; mma: h on the tensor cores.
 template <int P>
 cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, const int16_t *ainv,
