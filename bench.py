@@ -66,10 +66,11 @@ def launches_per_call(B, tuned):
 # (profiles/launches_keygen_b4096_sntrup761.md), keyed by kernel; a kernel is
 # absent until a capture of its current code exists.  Writes stay in L2.
 NCU_TRAFFIC_BYTES = {
-    "k_tree_up_mma": 12521984,
-    "k_tree_down_mma": 9325056,
-    "k_rq_inv_jump<761, 4591>": 166400,
-    "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 37782016,
+    "k_tree_up_mma": 12532992,
+    "k_tree_down_mma": 9324544,
+    "k_rq_inv_jump<761, 4591>": 165632,
+    "k_finalize_pair<761>": 9501440,
+    "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 37790976,
 }
 
 
