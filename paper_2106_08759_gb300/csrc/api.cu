@@ -86,8 +86,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     // R/3 result: the per-key R/3 inversions only write 1/g into sk and list
     // the (rare) keys whose g needed another draw; they run
     //   overlap 0: first, on the tree stream;
-    //   overlap 1: on the low-priority stream from the start;
-    //   overlap 2: on the low-priority stream from the up-sweep's first narrow
+    //   overlap 1: on the auxiliary (middle-priority) stream from the start;
+    //   overlap 2: on the auxiliary stream from the up-sweep's first narrow
     //              level (fewer than kNarrow products), so they fill the SMs
     //              that the narrow levels and the root inversion leave idle;
     // and are joined at the end of the call, before the fix-up of the listed
@@ -168,7 +168,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         if (tm) SNT_CUDA(cudaEventRecord(ev[3], r3s));
         return SNT_OK;
     };
-    auto fork_r3 = [&]() -> snt_status {  // R/3 on the low-priority stream from here
+    auto fork_r3 = [&]() -> snt_status {  // R/3 on the auxiliary stream from here
         SNT_CUDA(cudaEventRecord(ctx->ev_r3fork, st));
         SNT_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_r3fork, 0));
         const snt_status s3 = launch_r3(ctx->aux);
@@ -390,7 +390,10 @@ snt_status snt_ctx_create(int device, size_t mem_budget, snt_ctx **out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->d_inj_g, kMaxInject * 1024);
     int prio_low = 0, prio_high = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_low);
+    // tree first, then the R/3 work, then the leaf-pair products (which
+    // have the most slack before h needs them)
+    const int prio_mid = (prio_low + prio_high) / 2;
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_mid);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->tree, cudaStreamNonBlocking, prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->tune, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_low);
