@@ -262,7 +262,7 @@ typedef enum {
      * is split over: 1, 2, 4 or 8 */
     SNT_OPT_TREE_SPLIT = 2,
     /* where the per-key R/3 inversions run: 0 first, on the tree's stream;
-     * 1 on a lower-priority stream concurrent with the whole tree; 2 on that
+     * 1 on a second stream concurrent with the whole tree; 2 on that
      * stream from the up-sweep's first narrow level (fewer than
      * 256 products) up to the down-sweep's first wide level, so they fill the
      * SMs the narrow levels and the root inversion leave idle */

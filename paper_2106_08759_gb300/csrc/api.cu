@@ -86,7 +86,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     // R/3 result: the per-key R/3 inversions only write 1/g into sk and list
     // the (rare) keys whose g needed another draw; they run
     //   overlap 0: first, on the tree stream;
-    //   overlap 1: on the auxiliary (middle-priority) stream from the start;
+    //   overlap 1: on the auxiliary stream from the start;
     //   overlap 2: on the auxiliary stream from the up-sweep's first narrow
     //              level (fewer than kNarrow products), so they fill the SMs
     //              that the narrow levels and the root inversion leave idle;
@@ -390,10 +390,10 @@ snt_status snt_ctx_create(int device, size_t mem_budget, snt_ctx **out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->d_inj_g, kMaxInject * 1024);
     int prio_low = 0, prio_high = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
-    // tree first, then the R/3 work, then the leaf-pair products (which
-    // have the most slack before h needs them)
-    const int prio_mid = (prio_low + prio_high) / 2;
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_mid);
+    // the tree and the R/3 work first (measured: the R/3 branch below the
+    // tree in priority ends after it and the call waits), then the
+    // leaf-pair products, which have the most slack before h needs them
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->tree, cudaStreamNonBlocking, prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->tune, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_low);

@@ -37,7 +37,7 @@ struct snt_ctx {
     int8_t *d_inj_g = nullptr;
     int n_inj = 0;
     int inj_P = 0;
-    cudaStream_t aux = nullptr;   // middle priority: the R/3 inversions
+    cudaStream_t aux = nullptr;   // high priority: the R/3 inversions
     cudaStream_t tree = nullptr;  // high priority: sampling, product tree, h, hash
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr, ev_r3fork = nullptr;
     cudaEvent_t ev_gready = nullptr;       // R/3 batch path: every g final

@@ -16,7 +16,7 @@ namespace snt {
 // Defaults of the tuning options (snt_ctx_set_option).
 constexpr int kDefaultR3Lanes = 4;     // lanes per element of the R/3 divstep kernel
 constexpr int kDefaultTreeSplit = 8;   // largest split of one product over thread groups
-constexpr int kDefaultR3Overlap = 1;   // R/3 on its own lower-priority stream
+constexpr int kDefaultR3Overlap = 1;   // R/3 on its own stream beside the tree
 constexpr int kDefaultNarrowSeg = 1;   // output-split narrow tree levels
 constexpr int kDefaultRqEngine = 1;    // R/q products on the tensor cores
 constexpr int kDefaultMmaTiles = 1;    // MMA tiles per warp
