@@ -80,7 +80,10 @@ snt_status snt_ctx_sync(snt_ctx *ctx, snt_stream stream);
  * Writes B public keys (pk_dev, B * pk_bytes, key-major, contiguous) and B
  * secret keys (sk_dev, B * sk_bytes).  Key i uses key index
  * first_key_index + i.  1 <= B <= snt_ctx_max_batch(P).  Outputs are
- * byte-identical to snt_keygen_perkey and to any split of the batch. */
+ * byte-identical to snt_keygen_perkey and to any split of the batch.  The
+ * work forks from `stream` onto the context's own streams (the product tree,
+ * the R/3 inversions, the leaf-pair products of h) and joins back into
+ * `stream`, so work ordered after the call on `stream` sees every key. */
 snt_status snt_batch_keygen(snt_ctx *ctx, int P, uint64_t seed,
                             uint64_t first_key_index, size_t B,
                             uint8_t *pk_dev, uint8_t *sk_dev, snt_stream stream);
