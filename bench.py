@@ -62,9 +62,9 @@ def launches_per_call(B, tuned):
 
 # DRAM bytes (read + write) per call of a phase's kernels at B = 4096 under
 # the tuned layouts (64 roots, R/3 forest), summed over the phase's launches
-# of one call, from the committed ncu capture
-# (profiles/launches_keygen_b4096_sntrup761.md), keyed by kernel; a kernel is
-# absent until a capture of its current code exists.  Writes stay in L2.
+# of one call, from the committed ncu launch-list capture of one keygen call,
+# keyed by kernel; a kernel is absent until a capture of its current code
+# exists.  Writes stay in L2.
 NCU_TRAFFIC_BYTES = {
     "k_tree_up_mma": 12532992,
     "k_tree_down_mma": 9324544,
@@ -138,6 +138,8 @@ def parse():
     ap.add_argument("--serve-rates", default="1e4,1e5,1e6",
                     help="request rates of the serving runs (empty: none)")
     ap.add_argument("--serve-duration", type=float, default=0.5)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the B=32, ragged and building-block measurements")
     return ap.parse_args()
 
 
@@ -272,6 +274,137 @@ PIPE_OF = {"r3_inv": "lop3", "tree_up": "imad", "tree_down": "imad", "h_encode":
            "root_inv": "imad"}
 # with the tensor-core engine the products are f16 MMAs
 TENSOR_PHASES = ("tree_up", "tree_down", "h_encode")
+
+
+# ----------------------------------------------- the other configurations
+def micro_inputs(torch, n, seed, dev, short=False):
+    """n seeded synthetic sntrup761 operands on the device: R/q elements
+    uniform in [-(q-1)/2, (q-1)/2], or Short rows (w positions uniform among
+    p, random signs), generated in chunks by a seeded torch generator (the
+    same distributions as the test inputs)."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    h = (Q - 1) // 2
+    out = torch.empty((n, P), dtype=torch.int16, device=dev)
+    step = 1 << 16
+    for i in range(0, n, step):
+        m = min(step, n - i)
+        if short:
+            pos = torch.rand((m, P), generator=g, device=dev).topk(W, dim=1).indices
+            sgn = torch.randint(0, 2, (m, W), generator=g, device=dev, dtype=torch.int16) * 2 - 1
+            blk = torch.zeros((m, P), dtype=torch.int16, device=dev)
+            blk.scatter_(1, pos, sgn)
+            out[i:i + m] = blk
+        else:
+            out[i:i + m] = torch.randint(-h, h + 1, (m, P), generator=g, device=dev,
+                                         dtype=torch.int16)
+    return out
+
+
+def event_ms(torch, stream, flush, fn, reps):
+    """Median device time of fn over reps launches (CUDA events on the
+    launching stream, L2 flushed before each), after one warm-up."""
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def measure_b32(snt, torch, dev, stream, flush, seed, steps):
+    """Configuration 1: B = 32 keys per call (the paper's BatchKeyGen size),
+    batched and per key, autotuned for (761, 32)."""
+    B = 32
+    pkb, skb, _, _ = snt.snt_param_sizes(P)
+    out = {}
+    with snt.Context(dev.index or 0, 64 << 20) as c:
+        tuned = c.autotune(P, B)
+        pk = torch.empty(B * pkb, dtype=torch.uint8, device=dev)
+        sk = torch.empty(B * skb, dtype=torch.uint8, device=dev)
+        it = [0]
+
+        def call(fn):
+            def f():
+                it[0] += 1
+                fn(c, P, seed, (7 << 40) + it[0] * B, B, pk, sk, stream)
+            return f
+        for name, fn in (("batched", snt.snt_batch_keygen), ("perkey", snt.snt_keygen_perkey)):
+            ms = event_ms(torch, stream, flush, call(fn), steps)
+            out[name] = {"keys_per_s": round(B / ms * 1e3, 1), "ms_per_call": round(ms, 4)}
+        c.sync()
+    out["roots"] = tuned["roots"]
+    out["r3_mode"] = tuned["r3_mode"]
+    return out
+
+
+def measure_ragged(snt, torch, np, dev, stream, flush, reps):
+    """Configuration 3: 256 batches, sizes floor(exp(U[0, ln 2048])), a
+    shuffled equal mix of sntrup653/761/857 (seed 42), one graph launch."""
+    from synth import ragged_batches
+    sizes, ps = ragged_batches(256, 2048, 42)
+    pks, sks = [], []
+    for P_, B_ in zip(ps, sizes):
+        pkb_, skb_, _, _ = snt.snt_param_sizes(int(P_))
+        pks.append(torch.empty(int(B_) * pkb_, dtype=torch.uint8, device=dev))
+        sks.append(torch.empty(int(B_) * skb_, dtype=torch.uint8, device=dev))
+    firsts = [int(x) for x in np.cumsum([0] + list(sizes[:-1]))]
+    it = [0]
+    with snt.Context(dev.index or 0, 1 << 30) as c:
+        def ragged():
+            it[0] += 1
+            snt.snt_batch_keygen_ragged(c, [int(x) for x in ps], [int(x) for x in sizes],
+                                        [it[0] * 1000 + i for i in range(256)], firsts, pks,
+                                        sks, stream)
+        ms = event_ms(torch, stream, flush, ragged, reps)
+        c.sync()
+    nkeys = int(sizes.sum())
+    return {"batches": 256, "keys": nkeys, "ms_per_launch": round(ms, 4),
+            "keys_per_s": round(nkeys / ms * 1e3, 1),
+            "keys_by_p": {str(x): int(sizes[ps == x].sum()) for x in (653, 761, 857)}}
+
+
+def measure_micro(snt, torch, ctx, dev, stream, flush, reps):
+    """Configuration 4 (p = 761): 2^20 general x general and 2^20 general x
+    Short R/q products, 2^16 R/3 inversions, 2^10 R/q inversions (jump
+    divsteps and the step-at-a-time kernel)."""
+    n = 1 << 20
+    a = micro_inputs(torch, n, 1, dev)
+    b = micro_inputs(torch, n, 2, dev)
+    s = micro_inputs(torch, n, 3, dev, short=True)
+    c = torch.empty_like(a)
+    out = {}
+    ms = event_ms(torch, stream, flush, lambda: snt.snt_rq_mul(ctx, P, n, a, b, c, stream), reps)
+    out["rq_mul_general"] = {"n": n, "ms": round(ms, 3), "products_per_s": round(n / ms * 1e3),
+                             "gop_per_s": round(2 * n * P * P / ms / 1e6, 1)}
+    ms = event_ms(torch, stream, flush, lambda: snt.snt_rq_mul(ctx, P, n, a, s, c, stream), reps)
+    out["rq_mul_short"] = {"n": n, "ms": round(ms, 3), "products_per_s": round(n / ms * 1e3),
+                           "gop_per_s": round(n * P * W / ms / 1e6, 1)}
+    del a, b, s, c
+    m = 1 << 16
+    g = torch.randint(-1, 2, (m, P), generator=torch.Generator(device=dev).manual_seed(5),
+                      device=dev, dtype=torch.int8)
+    o = torch.empty_like(g)
+    ok = torch.empty(m, dtype=torch.int32, device=dev)
+    ms = event_ms(torch, stream, flush, lambda: snt.snt_r3_inv(ctx, P, m, g, o, ok, stream), reps)
+    out["r3_inv"] = {"n": m, "ms": round(ms, 3), "inv_per_s": round(m / ms * 1e3)}
+    k = 1 << 10
+    x = micro_inputs(torch, k, 6, dev)
+    xo = torch.empty_like(x)
+    xk = torch.empty(k, dtype=torch.int32, device=dev)
+    ms = event_ms(torch, stream, flush,
+                  lambda: snt.snt_rq_inv_latency(ctx, P, k, x, xo, xk, stream), reps)
+    out["rq_inv_jump"] = {"n": k, "ms": round(ms, 3), "inv_per_s": round(k / ms * 1e3)}
+    ms = event_ms(torch, stream, flush, lambda: snt.snt_rq_inv(ctx, P, k, x, xo, xk, stream), reps)
+    out["rq_inv_step"] = {"n": k, "ms": round(ms, 3), "inv_per_s": round(k / ms * 1e3)}
+    out["ops"] = "general: 2 p^2 per product (multiply-adds); Short: p w add/sub per product"
+    return out
 
 
 # ------------------------------------------------------------------ our arm
@@ -467,6 +600,12 @@ def run_ours(args):
                       "keys_generated": st["keys_generated"], "mismatches": st["mismatches"],
                       "max_queue": st["max_queue"], "wall_s": round(st["wall_s"], 3)})
 
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra["b32"] = measure_b32(snt, torch, dev, stream, flush, args.seed, 50)
+        extra["ragged"] = measure_ragged(snt, torch, np, dev, stream, flush, 5)
+        extra["micro"] = measure_micro(snt, torch, ctx, dev, stream, flush, 3)
+
     cpu = None
     if do_cpu:
         rate, nkeys = oracle_rate(pool, cores, args.seed, 5 * 10**9, 24)
@@ -484,30 +623,32 @@ def run_ours(args):
                                "(seed %d), fresh key indices every step" % (B, args.seed),
                    "p": P, "q": Q, "w": W, "B": B, "parallelism": "replicas" if world > 1 else "1gpu",
                    "l2": "flushed between steps (256 MiB write)"},
-        "perkey_gpu": {"value": round(perkey_rate, 1), "unit": "keys/s",
-                       "ms_per_step": round(pk_ms / pk_steps, 4),
-                       "batched_speedup": round(value / perkey_rate, 3)},
-        "phases_ms": {k: round(v, 4) for k, v in phase.items()},
-        "tuned": tuned,
-        "int_peaks_tops": {"lop3": round(lop3_peak / 1e12, 3), "imad": round(imad_peak / 1e12, 3),
-                           "warp_mma_f16_macs": round(mma_peak / 1e12, 3),
-                           "sms": sms},
         "roofline": roofline,
-        "phase_roofline": phase_roofline,
-        "path_ops": path_ops,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_rate, 1), "unit": "keys/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": B * (pkb + skb)},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
+        "int_peaks_tops": {"lop3": round(lop3_peak / 1e12, 3), "imad": round(imad_peak / 1e12, 3),
+                           "warp_mma_f16_macs": round(mma_peak / 1e12, 3),
+                           "sms": sms},
+        "phase_roofline": phase_roofline,
+        "path_ops": path_ops,
+        "paper_context": "156317 Haswell cycles/key at n=32 (E3-1275 v3, 3.5 GHz: ~22.4k keys/s/core)",
         "serve": {"workload": "sntrup761 handshakes for %.2f s per rate: Poisson encapsulation "
                               "requests of log-uniform size in [1, 64], each followed by the "
                               "decapsulation of its items; 16384-key device pool refilled by "
                               "8192-key batch keygen; 16 GiB budget; 4 launch streams"
                               % args.serve_duration,
                   "runs": serve},
-        "paper_context": "156317 Haswell cycles/key at n=32 (E3-1275 v3, 3.5 GHz: ~22.4k keys/s/core)",
+        # last, so that a reader of the line's tail sees them
+        "perkey_gpu": {"value": round(perkey_rate, 1), "unit": "keys/s",
+                       "ms_per_step": round(pk_ms / pk_steps, 4),
+                       "batched_speedup": round(value / perkey_rate, 3)},
     }
+    line.update(extra)
+    line["phases_ms"] = {k: round(v, 4) for k, v in phase.items()}
+    line["tuned"] = tuned
     ctx.close()
     if dist:
         dist.destroy_process_group()

@@ -89,7 +89,9 @@ snt_status snt_batch_keygen(snt_ctx *ctx, int P, uint64_t seed,
                             uint8_t *pk_dev, uint8_t *sk_dev, snt_stream stream);
 
 /* Same outputs as snt_batch_keygen, computed without batching the R/q
- * inversion: every key inverts its own 3f by divsteps (Sec. 3.1 KeyGen). */
+ * inversion: every key inverts its own 3f by divsteps (Sec. 3.1 KeyGen), by
+ * default jump divsteps in one CTA per key (SNT_OPT_PERKEY_INV), and its own
+ * 1/g in R/3 by bit-sliced divsteps.  The GPU baseline of the batched path. */
 snt_status snt_keygen_perkey(snt_ctx *ctx, int P, uint64_t seed,
                              uint64_t first_key_index, size_t B,
                              uint8_t *pk_dev, uint8_t *sk_dev, snt_stream stream);
@@ -127,7 +129,9 @@ snt_status snt_batch_keygen_host(snt_ctx *ctx, int P, uint64_t seed,
  *   - Writes the same bytes as snt_batch_keygen (same pk/sk layout).
  *   - The first call on a device looks up the scratch array's device address
  *     (cudaGetSymbolAddress, with that device current) and caches it; make
- *     that first call before any stream capture on the device.
+ *     that first call before any stream capture on the device.  The cached
+ *     address lives as long as the device's primary context: do not call
+ *     cudaDeviceReset on a device while this library stays loaded.
  *   - Every call uses the same scratch, which keeps the previous call's data:
  *     calls whose GPU work overlaps (different streams, threads or processes
  *     sharing the library instance without ordering) race and corrupt each
@@ -310,7 +314,13 @@ typedef enum {
      * and 761 only: for 857 the limb sums could reach 2^24 and the option is
      * ignored); 0: the leaf level of the down-sweep, then h = g (3f)^-1.
      * Same bytes either way. */
-    SNT_OPT_FUSE_LEAF = 11
+    SNT_OPT_FUSE_LEAF = 11,
+    /* R/q inversions of snt_keygen_perkey (one per key): 1 (default) jump
+     * divsteps, the kernel of the tree's root inversions (chunks of 31 steps
+     * on the low coefficients, the chunk's transition matrix applied to the
+     * whole state on the tensor cores); 0 the step-at-a-time kernel (one
+     * divstep of the whole state per CTA barrier).  Same bytes either way. */
+    SNT_OPT_PERKEY_INV = 12
 } snt_option;
 
 snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);

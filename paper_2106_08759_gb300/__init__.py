@@ -23,7 +23,7 @@ PARAMS = {653: (653, 4621, 288), 761: (761, 4591, 286), 857: (857, 5167, 322)}
 # tuning options (snt_option)
 SNT_OPT_R3_LANES, SNT_OPT_TREE_SPLIT, SNT_OPT_R3_OVERLAP, SNT_OPT_NARROW_SEG = 1, 2, 3, 4
 SNT_OPT_RQ_ENGINE, SNT_OPT_MMA_TILES, SNT_OPT_R3_KPT, SNT_OPT_MMA_KSPLIT = 5, 6, 7, 8
-SNT_OPT_ROOTS, SNT_OPT_R3_MODE, SNT_OPT_FUSE_LEAF = 9, 10, 11
+SNT_OPT_ROOTS, SNT_OPT_R3_MODE, SNT_OPT_FUSE_LEAF, SNT_OPT_PERKEY_INV = 9, 10, 11, 12
 
 # phase names of snt_ctx_phase_times (SNT_NPHASES entries)
 PHASES = ("sample_f", "r3_inv", "tree_up", "root_inv", "tree_down", "h_encode", "sha512",
@@ -215,8 +215,22 @@ def snt_ctx_sync(ctx, stream=None):
     ctx.sync(stream)
 
 
+def _check_room(P, B, pk, sk):
+    """Raise ValueError if pk / sk cannot hold B keys of parameter set P (the
+    kernels write B * pk_bytes and B * sk_bytes).  An unknown P or B = 0 is
+    left to the C call, which rejects it with SNT_EINVAL."""
+    if P not in PARAMS or B <= 0:
+        return
+    pkb, skb, _, _ = snt_param_sizes(P)
+    for t, need, name in ((pk, B * pkb, "pk"), (sk, B * skb, "sk")):
+        if t is not None and t.numel() * t.element_size() < need:
+            raise ValueError("%s holds %d bytes, %d keys of sntrup%d need %d"
+                             % (name, t.numel() * t.element_size(), B, P, need))
+
+
 def snt_batch_keygen(ctx, P, seed, first_key_index, B, pk, sk, stream=None):
     import torch
+    _check_room(P, B, pk, sk)
     _check(load().snt_batch_keygen(ctx.handle, P, seed, first_key_index, B,
                                    _dptr(pk, torch.uint8), _dptr(sk, torch.uint8),
                                    _stream(stream)))
@@ -224,6 +238,7 @@ def snt_batch_keygen(ctx, P, seed, first_key_index, B, pk, sk, stream=None):
 
 def snt_keygen_perkey(ctx, P, seed, first_key_index, B, pk, sk, stream=None):
     import torch
+    _check_room(P, B, pk, sk)
     _check(load().snt_keygen_perkey(ctx.handle, P, seed, first_key_index, B,
                                     _dptr(pk, torch.uint8), _dptr(sk, torch.uint8),
                                     _stream(stream)))
@@ -252,6 +267,7 @@ def snt_batch_keygen_static(device, P, seed, first_key_index, B, pk, sk, stream=
     For callers that cannot allocate device memory; returns when the keys are
     written.  See include/sntrup_gb300.h for the sharing rules."""
     import torch
+    _check_room(P, B, pk, sk)
     _check(load().snt_batch_keygen_static(device, P, seed, first_key_index, B,
                                           _dptr(pk, torch.uint8), _dptr(sk, torch.uint8),
                                           _stream(stream)))

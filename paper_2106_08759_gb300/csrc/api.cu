@@ -271,8 +271,14 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         inv_leaves = par;
         if (tm) SNT_CUDA(cudaEventRecord(ev[6], st));
     } else {
-        SNT_CUDA(launch_rq_inv<P>(Bi, leaves, pi.pad, leaves, pi.pad, nullptr, ctx->d_err, ERR_ROOT,
-                                  st));
+        // per key (Sec. 3.1 KeyGen step 4): jump divsteps (one CTA per key,
+        // the same kernel as the tree's roots) or the step-at-a-time kernel
+        if (ctx->perkey_inv)
+            SNT_CUDA(launch_rq_inv_jump<P>(Bi, leaves, pi.pad, leaves, pi.pad, nullptr, ctx->d_err,
+                                           ERR_ROOT, st));
+        else
+            SNT_CUDA(launch_rq_inv<P>(Bi, leaves, pi.pad, leaves, pi.pad, nullptr, ctx->d_err,
+                                      ERR_ROOT, st));
         if (tm) {
             SNT_CUDA(cudaEventRecord(ev[4], st));
             SNT_CUDA(cudaEventRecord(ev[5], st));
@@ -672,6 +678,10 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             if (value < 0 || value > 1) return set_error(SNT_EINVAL, "fuse-leaf is 0 or 1");
             ctx->fuse_leaf = value;
             return SNT_OK;
+        case SNT_OPT_PERKEY_INV:
+            if (value < 0 || value > 1) return set_error(SNT_EINVAL, "per-key inversion is 0 or 1");
+            ctx->perkey_inv = value;
+            return SNT_OK;
         default:
             return set_error(SNT_EINVAL, "unknown option %d", option);
     }
@@ -691,6 +701,7 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
         case SNT_OPT_ROOTS: *value = ctx->roots; return SNT_OK;
         case SNT_OPT_R3_MODE: *value = ctx->r3_mode; return SNT_OK;
         case SNT_OPT_FUSE_LEAF: *value = ctx->fuse_leaf; return SNT_OK;
+        case SNT_OPT_PERKEY_INV: *value = ctx->perkey_inv; return SNT_OK;
         default: return set_error(SNT_EINVAL, "unknown option %d", option);
     }
 }

@@ -57,6 +57,7 @@ struct snt_ctx {
     int roots = snt::kDefaultRoots;
     int r3_mode = snt::kDefaultR3Mode;
     int fuse_leaf = 1;  // h from the level-1 inverses (where FuseLeaf<P>::ok)
+    int perkey_inv = 1; // per-key path: 1 jump divsteps, 0 one divstep per barrier
     // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
     struct Tuned {
         int lanes = 0, split = 0, overlap = 0, engine = 0, tiles = 1, kpt = 1, roots = 1, r3mode = 0;

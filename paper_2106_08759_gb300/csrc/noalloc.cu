@@ -12,7 +12,9 @@
 // Host code must not pass the array's name to a kernel: on the host that
 // name is only a stand-in, not a device address.  The first call on a device
 // looks up the array's device address with cudaGetSymbolAddress (with that
-// device current) and caches it; later calls reuse the cached address.
+// device current) and caches it; later calls reuse the cached address, which
+// stays valid while the device's primary context lives (a cudaDeviceReset
+// while the library is loaded is not supported).
 #include <mutex>
 
 #include "host_plan.h"

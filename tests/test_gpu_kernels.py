@@ -126,17 +126,27 @@ def test_r3_inv_matches_oracle(snt, ctx, P, lanes, kpt):
         assert np.array_equal(got[i], ref), i
 
 
-def test_microbench_sizes_sampled(snt, ctx):
-    """Kernel microbenchmark workload at full size, sampled against the oracle:
-    2^20 general x general and 2^20 general x Short products, 2^16 R/3 and
-    2^10 R/q inversions (p = 761)."""
+@pytest.fixture(scope="module")
+def pool():
+    from oracle_pool import OraclePool
+    p = OraclePool()
+    yield p
+    p.close()
+
+
+def test_microbench_products_vs_oracle(snt, ctx, pool):
+    """Kernel microbenchmark workload at full size (p = 761): 2^20 general x
+    general and 2^20 general x Short products, 4096 sampled products of each
+    kind (the first, the last and the boundaries of the 4-products-per-CTA
+    groups among them) checked against the oracle's schoolbook product."""
     import torch
     p, q, w = oracle.PARAMS[761]
-    from synth import rq_uniform, short_batch, ternary_batch
+    from synth import rq_uniform, short_batch
     n = 1 << 20
     a = rq_uniform(761, n, seed=1)
     b = rq_uniform(761, n, seed=2)
     s = short_batch(761, n, seed=3)
+    assert (np.count_nonzero(s, axis=1) == w).all()
     da, db, ds = _t(a.ravel(), torch.int16), _t(b.ravel(), torch.int16), _t(s.ravel(), torch.int16)
     c = torch.empty(n * p, dtype=torch.int16, device="cuda")
     c2 = torch.empty(n * p, dtype=torch.int16, device="cuda")
@@ -144,13 +154,23 @@ def test_microbench_sizes_sampled(snt, ctx):
     snt.snt_rq_mul(ctx, 761, n, da, ds, c2)
     torch.cuda.synchronize()
     rng = np.random.default_rng(4)
-    idx = rng.integers(0, n, 64)
-    got = c.view(n, p)[torch.from_numpy(idx).cuda()].cpu().numpy()
-    got2 = c2.view(n, p)[torch.from_numpy(idx).cuda()].cpu().numpy()
-    for k, i in enumerate(idx):
-        assert np.array_equal(got[k], oracle.ring_mul(p, q, a[i], b[i]))
-        assert np.array_equal(got2[k], oracle.ring_mul(p, q, a[i], s[i]))
-    del c, c2, da, db, ds
+    idx = np.unique(np.concatenate([[0, 1, 2, 3, 4, n - 5, n - 4, n - 1],
+                                    rng.choice(n, 4096, replace=False)]))
+    assert idx.size >= 4096
+    ti = torch.from_numpy(idx).cuda()
+    got = c.view(n, p)[ti].cpu().numpy()
+    got2 = c2.view(n, p)[ti].cpu().numpy()
+    assert pool.bad_products(p, q, a[idx], b[idx], got) == []
+    assert pool.bad_products(p, q, a[idx], s[idx], got2) == []
+
+
+def test_microbench_all_r3_inversions(snt, ctx, pool):
+    """All 2^16 R/3 inversions of the microbenchmark workload: every output
+    with its flag set satisfies g * v = 1 in R/3 (the inverse is unique, so
+    this pins v), every flagged failure is a zero divisor per the oracle."""
+    import torch
+    from synth import ternary_batch
+    p = 761
     m = 1 << 16
     g = ternary_batch(761, m, seed=5)
     out = torch.empty(m * p, dtype=torch.int8, device="cuda")
@@ -158,15 +178,24 @@ def test_microbench_sizes_sampled(snt, ctx):
     snt.snt_r3_inv(ctx, 761, m, _t(g.ravel(), torch.int8), out, ok)
     outh = out.cpu().numpy().reshape(m, p)
     okh = ok.cpu().numpy()
-    for i in rng.integers(0, m, 48):
-        rok, ref = oracle.ring_inv(p, 3, g[i])
-        assert bool(okh[i]) == rok and np.array_equal(outh[i], ref)
+    assert pool.bad_identities(p, 3, g, outh, okh) == []
+
+
+@pytest.mark.parametrize("latency", [False, True])
+def test_microbench_all_rq_inversions(snt, ctx, pool, latency):
+    """All 2^10 R/q inversions of the microbenchmark workload, by the
+    step-at-a-time kernel and by jump divsteps, equal to the oracle's
+    extended-Euclid inverses."""
+    import torch
+    from synth import rq_uniform
+    p, q, _ = oracle.PARAMS[761]
     k = 1 << 10
     x = rq_uniform(761, k, seed=6)
     out = torch.empty(k * p, dtype=torch.int16, device="cuda")
     ok = torch.empty(k, dtype=torch.int32, device="cuda")
-    snt.snt_rq_inv(ctx, 761, k, _t(x.ravel(), torch.int16), out, ok)
+    fn = snt.snt_rq_inv_latency if latency else snt.snt_rq_inv
+    fn(ctx, 761, k, _t(x.ravel(), torch.int16), out, ok)
     outh = out.cpu().numpy().reshape(k, p)
-    assert ok.cpu().numpy().all()
-    for i in rng.integers(0, k, 24):
-        assert np.array_equal(outh[i], oracle.ring_inv(p, q, x[i])[1])
+    okh = ok.cpu().numpy()
+    assert okh.all()
+    assert pool.bad_inverses(p, q, x, outh, okh) == []

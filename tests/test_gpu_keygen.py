@@ -30,10 +30,15 @@ def ctx(snt):
     c.close()
 
 
-@pytest.mark.parametrize("perkey", [False, True])
-def test_b32_every_key_matches_oracle(snt, ctx, perkey):
-    # 32 keys of sntrup761 from a fixed 64-bit seed, key indices 0..31
-    pk, sk = gpu_keygen(snt, ctx, 761, SEED, 0, 32, perkey=perkey)
+@pytest.mark.parametrize("path", ["batched", "perkey_jump", "perkey_step"])
+def test_b32_every_key_matches_oracle(snt, ctx, path):
+    # 32 keys of sntrup761 from a fixed 64-bit seed, key indices 0..31; the
+    # per-key path with either R/q inversion kernel
+    ctx.set_option(snt.SNT_OPT_PERKEY_INV, 0 if path == "perkey_step" else 1)
+    try:
+        pk, sk = gpu_keygen(snt, ctx, 761, SEED, 0, 32, perkey=path != "batched")
+    finally:
+        ctx.set_option(snt.SNT_OPT_PERKEY_INV, 1)
     rpk, rsk = oracle.keygen_batch(761, SEED, 0, 32)
     assert first_mismatch(pk, rpk) is None
     assert first_mismatch(sk, rsk) is None
@@ -313,9 +318,12 @@ def test_invalid_arguments(snt, ctx):
         snt.snt_batch_keygen(ctx, 760, 0, 0, 1, pk, pk)
     assert e.value.status == -1
     small = snt.Context(0, 1 << 20)
+    big = torch.empty(4096 * 1763, dtype=torch.uint8, device="cuda")
     with pytest.raises(snt.SntError) as e:
-        snt.snt_batch_keygen(small, 761, 0, 0, 4096, pk, pk)
+        snt.snt_batch_keygen(small, 761, 0, 0, 4096, big, big)
     assert e.value.status == -2
+    with pytest.raises(ValueError):  # the binding checks the output room
+        snt.snt_batch_keygen(ctx, 761, 0, 0, 2, pk, pk)
     assert small.max_batch(761) >= 1
     small.close()
 
@@ -347,3 +355,41 @@ def test_fused_leaf_level_gives_the_same_keys(snt, ctx, P, roots, B):
     if B <= 96:
         rpk, rsk = oracle.keygen_batch(P, 12, 70, B)
         assert first_mismatch(got[0], rpk) is None and first_mismatch(got[1], rsk) is None
+
+
+@pytest.fixture(scope="module")
+def pool():
+    from oracle_pool import OraclePool
+    p = OraclePool()
+    yield p
+    p.close()
+
+
+def test_benchmarked_layout_b4096_vs_perkey_and_oracle(snt, pool):
+    """The configuration the benchmark times: a 256 MiB context autotuned for
+    (761, 4096), seed 1, B = 4096.  All keys equal the per-key path's (both
+    R/q inversion kernels), and at least 256 keys equal the oracle's: the
+    first and last key, both ends of every subtree of the tuned forest and
+    random ones."""
+    B, seed = 4096, 1
+    with snt.Context(0, 256 << 20) as c:
+        tuned = c.autotune(761, B)
+        pk, sk = gpu_keygen(snt, c, 761, seed, 0, B)
+        pk2, sk2 = gpu_keygen(snt, c, 761, seed, 0, B, perkey=True)
+        c.set_option(snt.SNT_OPT_PERKEY_INV, 0)
+        pk3, sk3 = gpu_keygen(snt, c, 761, seed, 0, B, perkey=True)
+    assert first_mismatch(pk, pk2) is None and first_mismatch(sk, sk2) is None
+    assert first_mismatch(pk, pk3) is None and first_mismatch(sk, sk3) is None
+    # forest rule of the library: for B = 4096 every power of two up to 256
+    # divides B and fits the node rows, so K = the tuned root count
+    K = tuned["roots"]
+    assert K in (1, 4, 16, 64, 128, 256)
+    sub = B // K
+    ends = [x for j in range(K) for x in (j * sub, j * sub + sub - 1)]
+    rng = np.random.default_rng(3)
+    idx = set(ends) | {0, B - 1}
+    while len(idx) < 256 + len(ends) // 2:
+        idx.add(int(rng.integers(0, B)))
+    idx = np.array(sorted(idx))
+    assert idx.size >= 256
+    assert pool.bad_keys(761, seed, idx, pk[idx], sk[idx]) == []

@@ -40,6 +40,55 @@ def test_random_words_counter_layout():
         assert w[i] == blk[i % 4]
 
 
+def _philox_words(seed, k, stream, attempt, n):
+    """n words of the randomness reading, built here from single Philox
+    blocks (pinned by the known answers above): word j is lane j mod 4 of the
+    block with counter ((stream << 16) | (j / 4), attempt, k mod 2^32, k >> 32)."""
+    key = [seed & 0xffffffff, seed >> 32]
+    return [int(oracle.philox4x32_10([(stream << 16) | (j // 4), attempt, k & 0xffffffff, k >> 32],
+                                     key)[j % 4]) for j in range(n)]
+
+
+@pytest.mark.parametrize("p", [653, 761, 857])
+def test_rho_is_stream_2_little_endian(p):
+    # rho (the implicit-rejection part of sk): byte j is byte j mod 4 of word
+    # j / 4 of stream 2, least significant byte first; pinned against Philox
+    # blocks and an explicit byte split, and in the oracle's own keys
+    sb = (p + 3) // 4
+    pkb, _, _ = oracle.sizes(p)
+    for seed, k in [(0x0123456789ABCDEF, 0), (1, (3 << 32) | 77), (0xFFFFFFFFFFFFFFFF, 4095)]:
+        words = _philox_words(seed, k, 2, 0, (sb + 3) // 4)
+        want = b"".join(w.to_bytes(4, "little") for w in words)[:sb]
+        assert oracle.rho(sb, seed, k).tobytes() == want
+        if k < 5000:
+            _, sk, _ = oracle.keygen(p, seed, k)
+            assert sk[2 * sb + pkb:3 * sb + pkb].tobytes() == want
+
+
+@pytest.mark.parametrize("p", [653, 761, 857])
+def test_small_g_is_scaled_stream_0_words(p):
+    # g coefficient i at attempt a: floor(3 (u mod 2^30) / 2^30) - 1 for word
+    # i of stream 0, attempt a (integer arithmetic in Python)
+    for seed, k, a in [(99, 3, 0), (5, 1 << 33, 2)]:
+        words = _philox_words(seed, k, 0, a, p)
+        want = [((u & (2**30 - 1)) * 3 >> 30) - 1 for u in words]
+        assert oracle.sample_small(p, seed, k, a).tolist() == want
+
+
+@pytest.mark.parametrize("p", [653, 761, 857])
+def test_short_f_is_sorted_forced_stream_1_words(p):
+    # Short f: p words of stream 1, the first w with bit 0 cleared (low bits
+    # 00 or 10: coefficient -1 or +1), the rest with low bits 01 (zero),
+    # sorted as unsigned integers (Python's sort), coefficient = low 2 bits - 1
+    w = PARAMS[p][2]
+    for seed, k in [(99, 3), (0xDEADBEEF, 1 << 40)]:
+        words = _philox_words(seed, k, 1, 0, p)
+        forced = [u & ~1 & 0xffffffff if i < w else (u & ~3 & 0xffffffff) | 1
+                  for i, u in enumerate(words)]
+        want = [(u & 3) - 1 for u in sorted(forced)]
+        assert oracle.sample_short(p, w, seed, k).tolist() == want
+
+
 # ------------------------------------------------------------------ sampling
 @pytest.mark.parametrize("p", [653, 761, 857])
 def test_short_and_small_invariants(p):
