@@ -357,6 +357,9 @@ def measure_ragged(snt, torch, np, dev, stream, flush, reps):
     firsts = [int(x) for x in np.cumsum([0] + list(sizes[:-1]))]
     it = [0]
     with snt.Context(dev.index or 0, 1 << 30) as c:
+        # layouts per (p, bucket of the largest batch), as a user would tune
+        tuned = {str(x): c.autotune(x, 2048) for x in (653, 761, 857)}
+
         def ragged():
             it[0] += 1
             snt.snt_batch_keygen_ragged(c, [int(x) for x in ps], [int(x) for x in sizes],
@@ -367,7 +370,8 @@ def measure_ragged(snt, torch, np, dev, stream, flush, reps):
     nkeys = int(sizes.sum())
     return {"batches": 256, "keys": nkeys, "ms_per_launch": round(ms, 4),
             "keys_per_s": round(nkeys / ms * 1e3, 1),
-            "keys_by_p": {str(x): int(sizes[ps == x].sum()) for x in (653, 761, 857)}}
+            "keys_by_p": {str(x): int(sizes[ps == x].sum()) for x in (653, 761, 857)},
+            "r3_batched": {k: v["r3_mode"] != 0 for k, v in tuned.items()}}
 
 
 def measure_micro(snt, torch, ctx, dev, stream, flush, reps):

@@ -102,9 +102,14 @@ snt_status snt_keygen_perkey(snt_ctx *ctx, int P, uint64_t seed,
  * pointers, each B[i] * sizes of P[i]).  Every batch gets exactly the bytes
  * snt_batch_keygen would give it alone: each batch keeps its own Montgomery
  * product tree (Algorithm 1), while the batches of one parameter set share the
- * launches, level by level.  The launch sequence of a plan (the list of
- * (P[i], B[i])) is captured into a CUDA graph on first use and replayed while
- * the plan repeats.  Asynchronous on `stream`; 1 <= n_batches <= 65536. */
+ * launches, level by level, and the three parameter sets run side by side on
+ * streams of the context.  The R/3 inverses are per key (SNT_OPT_R3_MODE 0)
+ * or batched after the invertibility test of Sec. 3.1.1 (modes 1 and 2).  A
+ * parameter set takes the layouts snt_autotune_ex chose on this context for
+ * (P, the ceil(log2) bucket of its largest batch), else the context's
+ * options.  The launch sequence of a plan (the list of (P[i], B[i]) and the
+ * layouts) is captured into a CUDA graph on first use and replayed while the
+ * plan repeats.  Asynchronous on `stream`; 1 <= n_batches <= 65536. */
 snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, const int *P,
                                    const size_t *B, const uint64_t *seeds,
                                    const uint64_t *first_idx, uint8_t *const *pk_dev,

@@ -445,6 +445,12 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     for (uint32_t *f : ctx->d_r3fac)
         if (f) cudaFree(f);
     if (ctx->ragged.exec) cudaGraphExecDestroy(ctx->ragged.exec);
+    for (int j = 0; j < 3; ++j) {
+        if (ctx->rg_main[j]) cudaStreamDestroy(ctx->rg_main[j]);
+        if (ctx->rg_aux[j]) cudaStreamDestroy(ctx->rg_aux[j]);
+        for (cudaEvent_t e : ctx->rg_ev[j])
+            if (e) cudaEventDestroy(e);
+    }
     if (ctx->tree) cudaStreamDestroy(ctx->tree);
     if (ctx->tune) cudaStreamDestroy(ctx->tune);
     if (ctx->side) cudaStreamDestroy(ctx->side);

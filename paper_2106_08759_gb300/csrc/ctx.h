@@ -65,6 +65,11 @@ struct snt_ctx {
     Tuned tuned[3][25];
     cudaStream_t tune = nullptr;  // stream used while autotuning
     snt::RaggedGraph ragged;      // last ragged plan and its graph
+    // ragged launches: per parameter set a main and an R/3 stream and their
+    // fork / g-ready / join / done events (created on first use)
+    bool rg_ready = false;
+    cudaStream_t rg_main[3] = {}, rg_aux[3] = {};
+    cudaEvent_t rg_ev[3][5] = {};
 };
 
 

@@ -196,7 +196,7 @@ cudaError_t launch_r3_encode_v(const KeyMap &km, int B, const int16_t *v3, int s
 template <int P>
 cudaError_t launch_r3_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
-                               cudaStream_t st);
+                               cudaStream_t st, const int *idx = nullptr);
 // Keys on the resampling list: h with the final g, pk, sk's copy and hash.
 template <int P>
 cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_keys,

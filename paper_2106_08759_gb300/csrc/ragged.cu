@@ -7,12 +7,19 @@
 // parameter set form a forest that is processed level by level: one launch
 // per tree level covers the nodes of every batch at that level (CTA -> batch
 // by a binary search over per-level prefix sums), one launch inverts every
-// batch's root, and the per-key kernels (sampling, R/3 inversion, h and
-// Rq_encode, SHA-512) run once over all keys of the parameter set, looking up
-// each key's batch in a device table.  The sequence of launches for a plan
-// (the list of (p, B) pairs) is captured once into a CUDA graph and replayed;
-// per-call data (seeds, key indices, output pointers) lives in device tables
-// uploaded before each replay.
+// batch's root, and the per-key kernels (sampling, h and Rq_encode, SHA-512)
+// run once over all keys of the parameter set, looking up each key's batch in
+// a device table.  The inverses of g in R/3 are either per key (divsteps, on
+// a second stream beside the R/q forest, redrawn keys fixed up at the end) or
+// batched as in Sec. 3.1.1: every g tested invertible by its remainders modulo
+// the F_3 factors of x^p - x - 1 (and redrawn until it is), then one R/3
+// forest with the same shape as the R/q forest.  The three parameter sets run
+// on their own pairs of streams, side by side.  Each parameter set takes the
+// layouts the autotuner chose for (p, the bucket of its largest batch) on this
+// context, else the context's options.  The sequence of launches for a plan
+// (the list of (p, B) pairs and the layouts) is captured once into a CUDA graph
+// and replayed; per-call data (seeds, key indices, output pointers) lives in
+// device tables uploaded before each replay.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -41,8 +48,12 @@ struct Group {
     std::vector<int> root_row;            // node row of each batch's root
     size_t nodes = 0;                     // node rows in the forest
     // arena offsets (bytes): tree nodes, g rows, resampling list (count and
-    // keys, then final g rows) of the deferred R/3 kernel
-    size_t off_nodes = 0, off_g = 0, off_fix = 0, off_gfix = 0;
+    // keys, then final g rows) of the deferred R/3 kernel, R/3 forest nodes
+    size_t off_nodes = 0, off_g = 0, off_fix = 0, off_gfix = 0, off_nodes3 = 0;
+    // kernel layouts of this parameter set
+    int lanes = 4, split = 8, tiles = 1, kpt = 1, ksplit = 4;
+    bool mma = true, r3batch = false;
+    R3Factors fac;
     // table offsets (bytes, from the start of the uploaded table block)
     size_t t_desc = 0, t_pre = 0, t_root = 0;
 };
@@ -85,11 +96,12 @@ void plan_group(Group &g, const size_t *B) {
 
 template <int P>
 snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStream_t st,
-                        cudaStream_t aux, cudaEvent_t ev_fork, cudaEvent_t ev_join, int lanes,
-                        int split, bool mma, int tiles, int kpt) {
+                        cudaStream_t aux, cudaEvent_t ev_fork, cudaEvent_t ev_gready,
+                        cudaEvent_t ev_join) {
     const ParamInfo &pi = g.pi;
     const int nb = (int)g.batch.size();
     int16_t *nodes = reinterpret_cast<int16_t *>(ctx->arena + g.off_nodes);
+    int16_t *nodes3 = reinterpret_cast<int16_t *>(ctx->arena + g.off_nodes3);
     int8_t *gbuf = reinterpret_cast<int8_t *>(ctx->arena + g.off_g);
     int *fix_count = reinterpret_cast<int *>(ctx->arena + g.off_fix);
     int *fix_keys = fix_count + 1;
@@ -101,53 +113,89 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
     const int *pre = reinterpret_cast<const int *>(tables + g.t_pre);  // [level][nb + 1]
     const int *roots = reinterpret_cast<const int *>(tables + g.t_root);
     const int sb = pi.small_bytes;
-    // g's first draw with f; the R/3 inversions run beside the whole forest
-    // and are joined at the end, before the fix-up of resampled keys
+    auto lmap = [&](int l) {
+        LevelMap lm;
+        lm.pre_in = pre + (size_t)(l - 1) * (nb + 1);
+        lm.pre_out = pre + (size_t)l * (nb + 1);
+        lm.nb = nb;
+        lm.n_in = 0;
+        return lm;
+    };
+    // g's first draw with f; the R/3 work runs on the auxiliary stream beside
+    // the R/q forest and is joined at the end
     SNT_CUDA_R(launch_sample_f<P>(km, g.nkeys, nodes, pi.sk_bytes, 2 * sb + pi.pk_bytes, st, gbuf,
                                   nullptr, nullptr, 0, fix_count));
     SNT_CUDA_R(cudaEventRecord(ev_fork, st));
     SNT_CUDA_R(cudaStreamWaitEvent(aux, ev_fork, 0));
-    SNT_CUDA_R(launch_r3_keygen<P>(km, g.nkeys, gbuf, pi.sk_bytes, sb, nullptr, nullptr, 0,
-                                   ctx->d_err, aux, lanes, kpt, gfix, fix_count, fix_keys));
+    if (g.r3batch) {
+        // Sec. 3.1.1: isInvertible (remainders modulo the F_3 factors) with
+        // redraws, final g into the R/3 leaves; then Montgomery's trick in R/3
+        // over the same forest shape, one jump-divstep root per batch
+        SNT_CUDA_R(launch_r3_check<P>(km, g.nkeys, gbuf, nodes3, g.fac, ctx->d_err, aux));
+        SNT_CUDA_R(cudaEventRecord(ev_gready, aux));
+        for (int l = 1; l <= g.L; ++l)
+            SNT_CUDA_R(launch_tree_up_mma3<P>(nodes3 + (size_t)g.lev_off[l - 1] * pi.pad, lmap(l),
+                                              g.pre[l][nb], nodes3 + (size_t)g.lev_off[l] * pi.pad,
+                                              aux, g.ksplit));
+        SNT_CUDA_R(launch_r3_inv_jump<P>(nb, nodes3, pi.pad, nodes3, pi.pad, nullptr, ctx->d_err,
+                                         ERR_ROOT, aux, roots));
+        for (int l = g.L; l >= 1; --l)
+            SNT_CUDA_R(launch_tree_down_mma3<P>(nodes3 + (size_t)g.lev_off[l] * pi.pad, lmap(l),
+                                                g.pre[l][nb],
+                                                nodes3 + (size_t)g.lev_off[l - 1] * pi.pad, aux,
+                                                g.ksplit));
+        SNT_CUDA_R(launch_r3_encode_v<P>(km, g.nkeys, nodes3, pi.sk_bytes, sb, aux));
+    } else {
+        SNT_CUDA_R(launch_r3_keygen<P>(km, g.nkeys, gbuf, pi.sk_bytes, sb, nullptr, nullptr, 0,
+                                       ctx->d_err, aux, g.lanes, g.kpt, gfix, fix_count, fix_keys));
+    }
     SNT_CUDA_R(cudaEventRecord(ev_join, aux));
     for (int l = 1; l <= g.L; ++l) {
-        LevelMap lm;
-        lm.pre_in = pre + (size_t)(l - 1) * (nb + 1);
-        lm.pre_out = pre + (size_t)l * (nb + 1);
-        lm.nb = nb;
-        lm.n_in = 0;
         const int n_out = g.pre[l][nb];
-        if (mma)
-            SNT_CUDA_R(launch_tree_up_mma<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lm, n_out,
-                                             nodes + (size_t)g.lev_off[l] * pi.pad, st, tiles,
-                                             l == 1, ctx->mma_ksplit));
+        if (g.mma)
+            SNT_CUDA_R(launch_tree_up_mma<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lmap(l),
+                                             n_out, nodes + (size_t)g.lev_off[l] * pi.pad, st,
+                                             g.tiles, l == 1, g.ksplit));
         else
-            SNT_CUDA_R(launch_tree_up<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lm, n_out,
-                                         nodes + (size_t)g.lev_off[l] * pi.pad, st, split));
+            SNT_CUDA_R(launch_tree_up<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lmap(l), n_out,
+                                         nodes + (size_t)g.lev_off[l] * pi.pad, st, g.split));
     }
     SNT_CUDA_R(launch_rq_inv_jump<P>(nb, nodes, pi.pad, nodes, pi.pad, nullptr, ctx->d_err,
                                      ERR_ROOT, st, roots));
     for (int l = g.L; l >= 1; --l) {
-        LevelMap lm;
-        lm.pre_in = pre + (size_t)(l - 1) * (nb + 1);
-        lm.pre_out = pre + (size_t)l * (nb + 1);
-        lm.nb = nb;
-        lm.n_in = 0;
         const int n_par = g.pre[l][nb];
-        if (mma)
-            SNT_CUDA_R(launch_tree_down_mma<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lm, n_par,
-                                               nodes + (size_t)g.lev_off[l - 1] * pi.pad, st,
-                                               tiles, l == 1, ctx->mma_ksplit));
+        if (g.mma)
+            SNT_CUDA_R(launch_tree_down_mma<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lmap(l),
+                                               n_par, nodes + (size_t)g.lev_off[l - 1] * pi.pad,
+                                               st, g.tiles, l == 1, g.ksplit));
         else
-            SNT_CUDA_R(launch_tree_down<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lm, n_par,
-                                           nodes + (size_t)g.lev_off[l - 1] * pi.pad, st, split));
+            SNT_CUDA_R(launch_tree_down<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lmap(l), n_par,
+                                           nodes + (size_t)g.lev_off[l - 1] * pi.pad, st, g.split));
     }
+    if (g.r3batch) SNT_CUDA_R(cudaStreamWaitEvent(st, ev_gready, 0));  // h needs the final g
     SNT_CUDA_R(launch_finalize<P>(km, g.nkeys, gbuf, nodes, pi.pk_bytes, pi.sk_bytes, 2 * sb,
-                                  pi.sched, st, mma));
+                                  pi.sched, st, g.mma));
     SNT_CUDA_R(launch_sha512_pk(km, g.nkeys, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     SNT_CUDA_R(cudaStreamWaitEvent(st, ev_join, 0));
-    SNT_CUDA_R(launch_fixup<P>(km, fix_count, fix_keys, gfix, nodes, pi.pk_bytes, pi.sk_bytes,
-                               2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st));
+    if (!g.r3batch)  // keys whose g the per-key R/3 kernel redrew: h, pk, hash again
+        SNT_CUDA_R(launch_fixup<P>(km, fix_count, fix_keys, gfix, nodes, pi.pk_bytes, pi.sk_bytes,
+                                   2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st));
+    return SNT_OK;
+}
+
+// Streams and events of the three parameter sets' branches (created on the
+// first ragged call, kept for the context's life).
+snt_status ensure_ragged_streams(snt_ctx *ctx) {
+    if (ctx->rg_ready) return SNT_OK;
+    int lo = 0, hi = 0;
+    SNT_CUDA_R(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    for (int j = 0; j < 3; ++j) {
+        SNT_CUDA_R(cudaStreamCreateWithPriority(&ctx->rg_main[j], cudaStreamNonBlocking, hi));
+        SNT_CUDA_R(cudaStreamCreateWithPriority(&ctx->rg_aux[j], cudaStreamNonBlocking, hi));
+        for (int e = 0; e < 5; ++e)
+            SNT_CUDA_R(cudaEventCreateWithFlags(&ctx->rg_ev[j][e], cudaEventDisableTiming));
+    }
+    ctx->rg_ready = true;
     return SNT_OK;
 }
 
@@ -193,6 +241,24 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         arena_off += align_up(sizeof(int) * (1 + (size_t)g.nkeys), 256);
         g.off_gfix = arena_off;
         arena_off += align_up((size_t)g.nkeys * g.pi.pad, 256);
+        // layouts: the autotuner's choice for (p, the largest batch's bucket)
+        // if it ran on this context, else the context's options
+        size_t bmax = 0;
+        for (int bi : g.batch) bmax = std::max(bmax, B[bi]);
+        const snt_ctx::Tuned &tu = ctx->tuned[pidx(g.P)][bbucket(bmax)];
+        g.lanes = ctx->r3_lanes; g.split = ctx->tree_split; g.tiles = ctx->mma_tiles;
+        g.kpt = ctx->r3_kpt; g.mma = ctx->rq_engine != 0; g.r3batch = ctx->r3_mode != 0;
+        g.ksplit = ctx->mma_ksplit;
+        if (tu.lanes) {
+            g.lanes = tu.lanes; g.split = tu.split; g.tiles = tu.tiles; g.kpt = tu.kpt;
+            g.mma = tu.engine != 0; g.r3batch = tu.r3mode != 0;
+        }
+        if (g.r3batch) {
+            const snt_status sf = r3_factors_for(ctx, g.P, g.fac);
+            if (sf != SNT_OK) return sf;
+            g.off_nodes3 = arena_off;
+            arena_off += align_up(g.nodes * g.pi.pad * sizeof(int16_t), 256);
+        }
         const size_t nb = g.batch.size();
         g.t_desc = tbytes;
         tbytes += align_up(nb * sizeof(BatchDesc), 16);
@@ -243,37 +309,53 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         sig.push_back((int)B[i]);
     }
     RaggedGraph &rg = ctx->ragged;
-    const int lanes = ctx->r3_lanes, split = ctx->tree_split, tiles = ctx->mma_tiles;
-    const int kpt = ctx->r3_kpt;
-    const bool mma = ctx->rq_engine != 0;
     // the cached graph holds the kernel layouts: they are part of its key
-    sig.push_back(lanes);
-    sig.push_back(split);
-    sig.push_back(mma ? tiles : 0);
-    sig.push_back(kpt);
-    sig.push_back(ctx->mma_ksplit);
+    for (int j = 0; j < 3; ++j) {
+        const Group &g = groups[j];
+        if (g.batch.empty()) continue;
+        sig.push_back(g.lanes);
+        sig.push_back(g.split);
+        sig.push_back(g.mma ? g.tiles : 0);
+        sig.push_back(g.kpt);
+        sig.push_back(g.ksplit);
+        sig.push_back(g.r3batch ? 1 : 0);
+    }
     if (!(rg.exec && rg.sig == sig && rg.table_off == table_off)) {
         if (rg.exec) cudaGraphExecDestroy(rg.exec);
         rg.exec = nullptr;
         rg.sig.clear();
-        // capture the launches of every group on the tree stream (R/3 forks
-        // to the auxiliary stream inside the capture)
+        const snt_status ss = ensure_ragged_streams(ctx);
+        if (ss != SNT_OK) return ss;
+        // capture from the tree stream: each parameter set forks onto its
+        // own pair of streams (its R/3 work onto the second) and joins back
         SNT_CUDA_R(cudaStreamBeginCapture(ctx->tree, cudaStreamCaptureModeThreadLocal));
         snt_status s = SNT_OK;
-        for (int j = 0; j < 3 && s == SNT_OK; ++j) {
+        cudaError_t ef = cudaEventRecord(ctx->ev_fork, ctx->tree);
+        for (int j = 0; j < 3 && s == SNT_OK && ef == cudaSuccess; ++j) {
             const Group &g = groups[j];
             if (g.batch.empty()) continue;
+            cudaStream_t gs = ctx->rg_main[j], ga = ctx->rg_aux[j];
+            cudaEvent_t *ev = ctx->rg_ev[j];
+            ef = cudaStreamWaitEvent(gs, ctx->ev_fork, 0);
+            if (ef != cudaSuccess) break;
             switch (g.P) {
-                case 653: s = launch_group<653>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles, kpt); break;
-                case 761: s = launch_group<761>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles, kpt); break;
-                default: s = launch_group<857>(ctx, g, tables, ctx->tree, ctx->aux, ctx->ev_fork, ctx->ev_join, lanes, split, mma, tiles, kpt); break;
+                case 653: s = launch_group<653>(ctx, g, tables, gs, ga, ev[0], ev[1], ev[2]); break;
+                case 761: s = launch_group<761>(ctx, g, tables, gs, ga, ev[0], ev[1], ev[2]); break;
+                default: s = launch_group<857>(ctx, g, tables, gs, ga, ev[0], ev[1], ev[2]); break;
             }
+            if (s != SNT_OK) break;
+            ef = cudaEventRecord(ev[3], gs);
+            if (ef == cudaSuccess) ef = cudaStreamWaitEvent(ctx->tree, ev[3], 0);
         }
         cudaGraph_t graph = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(ctx->tree, &graph);
         if (s != SNT_OK) {
             if (graph) cudaGraphDestroy(graph);
             return s;
+        }
+        if (ef != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return set_error(SNT_ECUDA, "graph capture fork/join: %s", cudaGetErrorString(ef));
         }
         if (ec != cudaSuccess) return set_error(SNT_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
         const cudaError_t ei = cudaGraphInstantiate(&rg.exec, graph, 0);

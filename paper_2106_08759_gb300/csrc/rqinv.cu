@@ -541,9 +541,9 @@ cudaError_t launch_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t
 template <int P>
 cudaError_t launch_r3_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
-                               cudaStream_t st) {
+                               cudaStream_t st, const int *idx) {
     k_rq_inv_jump<P, 3><<<n, JumpGeo<P, 3>::NT, 0, st>>>(n, in, in_stride, out, out_stride, ok, err,
-                                                      err_bit, nullptr);
+                                                      err_bit, idx);
     return cudaGetLastError();
 }
 
@@ -561,7 +561,7 @@ cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out
     template cudaError_t launch_rq_inv_jump<P>(int, const int16_t *, long, int16_t *, long, \
                                                int32_t *, int *, int, cudaStream_t, const int *); \
     template cudaError_t launch_r3_inv_jump<P>(int, const int16_t *, long, int16_t *, long, \
-                                               int32_t *, int *, int, cudaStream_t);
+                                               int32_t *, int *, int, cudaStream_t, const int *);
 SNT_INV_INST(653)
 SNT_INV_INST(761)
 SNT_INV_INST(857)

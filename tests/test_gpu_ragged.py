@@ -42,11 +42,14 @@ def _single(snt, ctx, P, B, seed, first):
     return pk.cpu().numpy().reshape(B, -1), sk.cpu().numpy().reshape(B, -1)
 
 
-def test_ragged_small_mixed(snt):
+@pytest.mark.parametrize("r3_mode", [0, 1])
+def test_ragged_small_mixed(snt, r3_mode):
+    # R/3 per key (0) or batched after the invertibility test (1)
     Ps = [761, 653, 857, 761, 761, 653, 857]
     Bs = [5, 1, 33, 2, 64, 17, 1]
     firsts = [0, 10, 20, 100, 200, 300, 400]
     with snt.Context(0, 128 << 20) as ctx:
+        ctx.set_option(snt.SNT_OPT_R3_MODE, r3_mode)
         for rnd, seeds in enumerate([[11, 12, 13, 14, 15, 16, 17], [21, 22, 23, 24, 25, 26, 27]]):
             # the second round replays the cached graph with new seeds
             got = _run_ragged(snt, ctx, Ps, Bs, seeds, firsts)
@@ -59,14 +62,20 @@ def test_ragged_small_mixed(snt):
             assert np.array_equal(got[i][0][-1], opk) and np.array_equal(got[i][1][-1], osk)
 
 
-def test_ragged_full_workload_256_batches(snt):
+@pytest.mark.parametrize("layout", ["options", "autotuned"])
+def test_ragged_full_workload_256_batches(snt, layout):
     """The ragged workload: 256 batches of log-uniform size in [1, 2048]
-    (seed 42), equal shares of sntrup653/761/857 after a seeded shuffle."""
+    (seed 42), equal shares of sntrup653/761/857 after a seeded shuffle; with
+    the context's default options, and with the layouts the autotuner picks
+    for (p, 2048), the configuration the benchmark times."""
     from synth import ragged_batches
     sizes, ps = ragged_batches(256, 2048, 42)
     seeds = [1000 + i for i in range(256)]
     firsts = list(np.cumsum([0] + list(sizes[:-1])))
     with snt.Context(0, 1 << 30) as ctx:
+        if layout == "autotuned":
+            for P in (653, 761, 857):
+                ctx.autotune(P, 2048)
         got = _run_ragged(snt, ctx, list(ps), list(sizes), seeds, firsts)
         for i in range(256):
             rpk, rsk = _single(snt, ctx, int(ps[i]), int(sizes[i]), seeds[i], int(firsts[i]))
