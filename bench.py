@@ -390,6 +390,17 @@ def measure_micro(snt, torch, ctx, dev, stream, flush, reps):
     ms = event_ms(torch, stream, flush, lambda: snt.snt_rq_mul(ctx, P, n, a, s, c, stream), reps)
     out["rq_mul_short"] = {"n": n, "ms": round(ms, 3), "products_per_s": round(n / ms * 1e3),
                            "gop_per_s": round(n * P * W / ms / 1e6, 1)}
+    # the same general products on each engine: 0 CUDA-core Toeplitz (IMAD),
+    # 1 tensor-core Toeplitz (f16 limbs), 2 the transform multiplier (IMAD)
+    eng = ctx.get_option(snt.SNT_OPT_RQ_ENGINE)
+    by_engine = {}
+    for e in (0, 1, 2):
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, e)
+        ms = event_ms(torch, stream, flush, lambda: snt.snt_rq_mul(ctx, P, n, a, b, c, stream),
+                      reps)
+        by_engine[str(e)] = round(n / ms * 1e3)
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, eng)
+    out["rq_mul_general_products_per_s_by_engine"] = by_engine
     del a, b, s, c
     m = 1 << 16
     g = torch.randint(-1, 2, (m, P), generator=torch.Generator(device=dev).manual_seed(5),

@@ -285,7 +285,12 @@ typedef enum {
     SNT_OPT_NARROW_SEG = 4,
     /* engine of the R/q products (tree, h excluded, snt_rq_mul): 0 CUDA-core
      * Toeplitz products on the IMAD pipe; 1 the same Toeplitz products on
-     * the tensor cores (warp MMA on exact 6-bit f16 limbs, f32 accumulate) */
+     * the tensor cores (warp MMA on exact 6-bit f16 limbs, f32 accumulate);
+     * 2 the paper's multiplier (Sec. 3.3) on the CUDA cores: truncated
+     * transforms over K = (Z/q)[x]/(x^64 + 1) whose twiddles are powers of x
+     * (shifts and negations), 48 pointwise products in K for p <= 768 (64 for
+     * sntrup857) on the IMAD pipe, for the tree's general x general levels
+     * (its leaf levels and h stay on the tensor cores) and snt_rq_mul */
     SNT_OPT_RQ_ENGINE = 5,
     /* tensor-core engine: MMA tiles (128 outputs each) per warp, 1, 2 or 3;
      * a product's tiles are spread over the warps of one CTA */
@@ -331,17 +336,18 @@ typedef enum {
 snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);
 snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
 
-/* Autotuner: times batch keygen of B keys of parameter set P under each
- * combination of R/3 lanes (4, 8, 32), R/3 overlap (0, 1, 2) and R/q engine
- * (tensor cores with 1 or 2 MMA tiles per warp, or CUDA cores with tree
- * split 4 or 8) on this GPU (CUDA events, best of three after a warm-up) and
- * keeps the fastest for every later keygen call of this context with the same
- * P and ceil(log2 B); it overrides the snt_ctx_set_option values there.
- * Synchronous; uses the context's scratch (B must fit the budget).  The R/3
- * kernel's elements per lane group (1, 2) are searched too.
- * Forests of 1, 4, 16 or 64 subtrees (SNT_OPT_ROOTS) are searched with the
- * tensor-core engine.
- * The R/3 mode (per key or batch) is searched too.
+/* Autotuner: times batch keygen of B keys of parameter set P on this GPU
+ * (CUDA events, best of three after a warm-up) under each candidate layout
+ * and keeps the fastest for every later keygen call of this context with the
+ * same P and ceil(log2 B) (and for the ragged call's parameter sets whose
+ * largest batch falls in that bucket); it overrides the snt_ctx_set_option
+ * values there.  Candidates: R/3 lanes (4, 8, 32) x R/3 overlap (0, 1, 2) x
+ * { tensor-core engine with 1 or 2 MMA tiles per warp, forests of 1, 4, 16,
+ * 64, 128 or 256 subtrees (SNT_OPT_ROOTS) and R/3 mode 0, 1 or 2; CUDA-core
+ * Toeplitz engine with tree split 4 or 8; transform multiplier (engine 2)
+ * with forests of 1, 16, 64 or 128 subtrees and R/3 mode 0 or 2 } (some
+ * combinations pruned; one R/3 element per lane group).  Synchronous; uses
+ * the context's scratch (B must fit the budget).
  * choice (optional, 8 ints): lanes, split, overlap, engine, tiles, kpt, roots,
  * r3 mode. */
 snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice);

@@ -95,14 +95,17 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     const cudaStream_t caller = st;
     int mode = ctx->r3_overlap, lanes = ctx->r3_lanes, split = ctx->tree_split;
     const bool narrow = ctx->narrow_seg != 0;
-    bool mma = ctx->rq_engine != 0;
+    int engine = ctx->rq_engine;
     int mma_tiles = ctx->mma_tiles, kpt = ctx->r3_kpt, roots = ctx->roots, r3mode = ctx->r3_mode;
     const snt_ctx::Tuned &tu = ctx->tuned[pidx(P)][bbucket(B)];
     if (tu.lanes) {
         mode = tu.overlap; lanes = tu.lanes; split = tu.split;
-        mma = tu.engine != 0; mma_tiles = tu.tiles; kpt = tu.kpt; roots = tu.roots;
+        engine = tu.engine; mma_tiles = tu.tiles; kpt = tu.kpt; roots = tu.roots;
         r3mode = tu.r3mode;
     }
+    // engine 2: the general x general levels by the transform multiplier,
+    // the small-operand levels (leaves) and h on the tensor cores
+    const bool mma = engine != 0, ntt = engine == 2;
     // R/3 batch inversion (the per-key path keeps per-key divsteps):
     //   mode 1 (Sec. 3.1.1): isInvertible per key (redrawing g until it is),
     //          then one Montgomery forest in R/3; h waits for the final g's;
@@ -216,7 +219,10 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                 if (s3 != SNT_OK) return s3;
                 forked = true;
             }
-            if (mma)
+            if (ntt && l > 1)
+                SNT_CUDA(launch_tree_up_ntt<P>(nodes + (size_t)t.off[l - 1] * pi.pad, lmap(l),
+                                               t.n[l], nodes + (size_t)t.off[l] * pi.pad, st));
+            else if (mma)
                 SNT_CUDA(launch_tree_up_mma<P>(nodes + (size_t)t.off[l - 1] * pi.pad,
                                                lmap(l), t.n[l],
                                                nodes + (size_t)t.off[l] * pi.pad, st, mma_tiles,
@@ -254,7 +260,10 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         // fused leaf level: stop at the level-1 inverses, h is formed from them
         for (int l = L; l >= (fuse ? 2 : 1); --l) {
             int16_t *lch = nodes + (size_t)t.off[l - 1] * pi.pad;
-            if (mma) {  // in place on every level
+            if (ntt && l > 1) {  // in place
+                SNT_CUDA(launch_tree_down_ntt<P>(par, lmap(l), t.n[l], lch, st));
+                par = lch;
+            } else if (mma) {  // in place on every level
                 SNT_CUDA(launch_tree_down_mma<P>(par, lmap(l), t.n[l], lch, st,
                                                  mma_tiles, l == 1, ctx->mma_ksplit));
                 par = lch;
@@ -553,14 +562,17 @@ snt_status snt_rq_mul(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev, const
     if (!a_dev || !b_dev || !c_dev) return set_error(SNT_EINVAL, "null buffer");
     DeviceGuard dg(ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const bool mma = ctx->rq_engine != 0;
+    const int eng = ctx->rq_engine;
     switch (P) {
-        case 653: SNT_CUDA(mma ? launch_mul_batch_mma<653>((int)n, a_dev, b_dev, c_dev, st)
-                               : launch_mul_batch<653>((int)n, a_dev, b_dev, c_dev, st)); break;
-        case 761: SNT_CUDA(mma ? launch_mul_batch_mma<761>((int)n, a_dev, b_dev, c_dev, st)
-                               : launch_mul_batch<761>((int)n, a_dev, b_dev, c_dev, st)); break;
-        case 857: SNT_CUDA(mma ? launch_mul_batch_mma<857>((int)n, a_dev, b_dev, c_dev, st)
-                               : launch_mul_batch<857>((int)n, a_dev, b_dev, c_dev, st)); break;
+        case 653: SNT_CUDA(eng == 2 ? launch_mul_batch_ntt<653>((int)n, a_dev, b_dev, c_dev, st)
+                           : eng == 1 ? launch_mul_batch_mma<653>((int)n, a_dev, b_dev, c_dev, st)
+                                      : launch_mul_batch<653>((int)n, a_dev, b_dev, c_dev, st)); break;
+        case 761: SNT_CUDA(eng == 2 ? launch_mul_batch_ntt<761>((int)n, a_dev, b_dev, c_dev, st)
+                           : eng == 1 ? launch_mul_batch_mma<761>((int)n, a_dev, b_dev, c_dev, st)
+                                      : launch_mul_batch<761>((int)n, a_dev, b_dev, c_dev, st)); break;
+        case 857: SNT_CUDA(eng == 2 ? launch_mul_batch_ntt<857>((int)n, a_dev, b_dev, c_dev, st)
+                           : eng == 1 ? launch_mul_batch_mma<857>((int)n, a_dev, b_dev, c_dev, st)
+                                      : launch_mul_batch<857>((int)n, a_dev, b_dev, c_dev, st)); break;
         default: return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     }
     return SNT_OK;
@@ -656,7 +668,7 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             ctx->narrow_seg = value;
             return SNT_OK;
         case SNT_OPT_RQ_ENGINE:
-            if (value != 0 && value != 1) return set_error(SNT_EINVAL, "R/q engine is 0 or 1");
+            if (value < 0 || value > 2) return set_error(SNT_EINVAL, "R/q engine is 0, 1 or 2");
             ctx->rq_engine = value;
             return SNT_OK;
         case SNT_OPT_MMA_TILES:
@@ -749,6 +761,15 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
                     c.lanes = la; c.kpt = kp; c.overlap = ov; c.engine = 0; c.tiles = 1; c.split = sp;
                     cands.push_back(c);
                 }
+                // the transform multiplier on the general levels
+                if (la != 32)
+                    for (int rt : {1, 16, 64, 128})
+                        for (int r3m : {0, 2}) {
+                            snt_ctx::Tuned c;
+                            c.lanes = la; c.kpt = kp; c.overlap = ov; c.engine = 2; c.tiles = 1;
+                            c.roots = rt; c.r3mode = r3m; c.split = ctx->tree_split;
+                            cands.push_back(c);
+                        }
             }
         }
     snt_ctx::Tuned best;

@@ -172,6 +172,18 @@ cudaError_t launch_tree_down_mma3(const int16_t *lpar, const LevelMap &lm, int n
 template <int P>
 cudaError_t launch_mul_batch_mma(int n, const int16_t *a, const int16_t *b, int16_t *c,
                                  cudaStream_t st);
+// R/q products by the paper's multiplier (Sec. 3.3): truncated transforms
+// over K = (Z/q)[x]/(x^64 + 1) with x as the root of unity, pointwise products
+// in K on the IMAD pipe (rqntt.cu).  Same layouts as the other engines.
+template <int P>
+cudaError_t launch_mul_batch_ntt(int n, const int16_t *a, const int16_t *b, int16_t *c,
+                                 cudaStream_t st);
+template <int P>
+cudaError_t launch_tree_up_ntt(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
+                               cudaStream_t st);
+template <int P>
+cudaError_t launch_tree_down_ntt(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t *lch,
+                                 cudaStream_t st);
 template <int P>
 cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out,
                           long out_stride, int32_t *ok, int *err, int err_bit, cudaStream_t st);

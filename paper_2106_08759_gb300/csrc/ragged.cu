@@ -52,7 +52,7 @@ struct Group {
     size_t off_nodes = 0, off_g = 0, off_fix = 0, off_gfix = 0, off_nodes3 = 0;
     // kernel layouts of this parameter set
     int lanes = 4, split = 8, tiles = 1, kpt = 1, ksplit = 4;
-    bool mma = true, r3batch = false;
+    bool mma = true, ntt = false, r3batch = false;
     R3Factors fac;
     // table offsets (bytes, from the start of the uploaded table block)
     size_t t_desc = 0, t_pre = 0, t_root = 0;
@@ -152,7 +152,10 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
     SNT_CUDA_R(cudaEventRecord(ev_join, aux));
     for (int l = 1; l <= g.L; ++l) {
         const int n_out = g.pre[l][nb];
-        if (g.mma)
+        if (g.ntt && l > 1)
+            SNT_CUDA_R(launch_tree_up_ntt<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lmap(l),
+                                             n_out, nodes + (size_t)g.lev_off[l] * pi.pad, st));
+        else if (g.mma)
             SNT_CUDA_R(launch_tree_up_mma<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lmap(l),
                                              n_out, nodes + (size_t)g.lev_off[l] * pi.pad, st,
                                              g.tiles, l == 1, g.ksplit));
@@ -164,7 +167,10 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
                                      ERR_ROOT, st, roots));
     for (int l = g.L; l >= 1; --l) {
         const int n_par = g.pre[l][nb];
-        if (g.mma)
+        if (g.ntt && l > 1)
+            SNT_CUDA_R(launch_tree_down_ntt<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lmap(l),
+                                               n_par, nodes + (size_t)g.lev_off[l - 1] * pi.pad, st));
+        else if (g.mma)
             SNT_CUDA_R(launch_tree_down_mma<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lmap(l),
                                                n_par, nodes + (size_t)g.lev_off[l - 1] * pi.pad,
                                                st, g.tiles, l == 1, g.ksplit));
@@ -247,11 +253,12 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         for (int bi : g.batch) bmax = std::max(bmax, B[bi]);
         const snt_ctx::Tuned &tu = ctx->tuned[pidx(g.P)][bbucket(bmax)];
         g.lanes = ctx->r3_lanes; g.split = ctx->tree_split; g.tiles = ctx->mma_tiles;
-        g.kpt = ctx->r3_kpt; g.mma = ctx->rq_engine != 0; g.r3batch = ctx->r3_mode != 0;
+        g.kpt = ctx->r3_kpt; g.mma = ctx->rq_engine != 0; g.ntt = ctx->rq_engine == 2;
+        g.r3batch = ctx->r3_mode != 0;
         g.ksplit = ctx->mma_ksplit;
         if (tu.lanes) {
             g.lanes = tu.lanes; g.split = tu.split; g.tiles = tu.tiles; g.kpt = tu.kpt;
-            g.mma = tu.engine != 0; g.r3batch = tu.r3mode != 0;
+            g.mma = tu.engine != 0; g.ntt = tu.engine == 2; g.r3batch = tu.r3mode != 0;
         }
         if (g.r3batch) {
             const snt_status sf = r3_factors_for(ctx, g.P, g.fac);
@@ -316,6 +323,7 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         sig.push_back(g.lanes);
         sig.push_back(g.split);
         sig.push_back(g.mma ? g.tiles : 0);
+        sig.push_back(g.ntt ? 1 : 0);
         sig.push_back(g.kpt);
         sig.push_back(g.ksplit);
         sig.push_back(g.r3batch ? 1 : 0);

@@ -120,6 +120,24 @@ def test_r3_two_elements_per_lane_group_give_the_same_keys(snt, ctx, lanes, kpt)
     assert first_mismatch(inj[0], rpk) is None and first_mismatch(inj[1], rsk) is None
 
 
+@pytest.mark.parametrize("P,B", [(761, 300), (653, 77), (857, 130), (761, 2), (761, 5)])
+def test_transform_engine_gives_the_same_keys(snt, ctx, P, B):
+    # general x general tree levels by the transform multiplier (engine 2)
+    # against the CUDA-core Toeplitz engine; B = 2 and 5 have few or no
+    # general levels (the leaf levels stay on the tensor cores)
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 0)
+    try:
+        ref = gpu_keygen(snt, ctx, P, 5, 40, B)
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 2)
+        got = gpu_keygen(snt, ctx, P, 5, 40, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    if B <= 5:
+        rpk, rsk = oracle.keygen_batch(P, 5, 40, B)
+        assert first_mismatch(got[0], rpk) is None and first_mismatch(got[1], rsk) is None
+
+
 @pytest.mark.parametrize("tiles", [1, 2, 3])
 @pytest.mark.parametrize("P,B", [(761, 300), (653, 77), (857, 130)])
 def test_tensor_core_engine_gives_the_same_keys(snt, ctx, P, B, tiles):
@@ -138,7 +156,7 @@ def test_tensor_core_engine_gives_the_same_keys(snt, ctx, P, B, tiles):
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
 
 
-@pytest.mark.parametrize("engine", [1, 0])
+@pytest.mark.parametrize("engine", [1, 0, 2])
 @pytest.mark.parametrize("roots,B", [(2, 96), (32, 96), (1024, 96), (4, 300), (8, 7), (64, 4096)])
 def test_forest_of_subtrees_gives_the_same_keys(snt, ctx, engine, roots, B):
     # Montgomery's trick over K equal subtrees with K root inversions in one
