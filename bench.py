@@ -613,7 +613,10 @@ def run_ours(args):
                       "items_per_s": round(st["items_per_s"], 1),
                       "items_enc": st["items_enc"], "items_dec": st["items_dec"],
                       "keys_generated": st["keys_generated"], "mismatches": st["mismatches"],
-                      "max_queue": st["max_queue"], "wall_s": round(st["wall_s"], 3)})
+                      "max_queue": st["max_queue"], "wall_s": round(st["wall_s"], 3),
+                      # items of the requests that arrived, per second of the arrival window
+                      "offered_items_per_s": round((st["items_enc"] + st["items_dec"])
+                                                   / args.serve_duration, 1)})
 
     extra = {}
     if not args.no_extra and rank == 0:
@@ -655,7 +658,12 @@ def run_ours(args):
                               "decapsulation of its items; 16384-key device pool refilled by "
                               "8192-key batch keygen; 16 GiB budget; 4 launch streams"
                               % args.serve_duration,
-                  "runs": serve},
+                  "runs": serve,
+                  # the loop's saturation throughput: the served rate of the
+                  # most loaded run whose offered load exceeded what it served
+                  "capacity_items_per_s": max([r["items_per_s"] for r in serve
+                                               if r["offered_items_per_s"] > 1.2 * r["items_per_s"]]
+                                              or [None])},
         # last, so that a reader of the line's tail sees them
         "perkey_gpu": {"value": round(perkey_rate, 1), "unit": "keys/s",
                        "ms_per_step": round(pk_ms / pk_steps, 4),

@@ -330,7 +330,14 @@ typedef enum {
      * on the low coefficients, the chunk's transition matrix applied to the
      * whole state on the tensor cores); 0 the step-at-a-time kernel (one
      * divstep of the whole state per CTA barrier).  Same bytes either way. */
-    SNT_OPT_PERKEY_INV = 12
+    SNT_OPT_PERKEY_INV = 12,
+    /* 1 (default), 2 or 4: batch keygen splits its forest's subtrees into
+     * that many groups of consecutive keys and runs each group from its
+     * up-sweep to its pk hash on a stream of its own, so that one group's
+     * latency-bound root inversions overlap another group's wide tree levels
+     * (tensor-core or transform engine; ignored unless the forest's subtree
+     * count is a multiple of it).  Same products, same bytes. */
+    SNT_OPT_PARTS = 13
 } snt_option;
 
 snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);
@@ -345,12 +352,18 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
  * { tensor-core engine with 1 or 2 MMA tiles per warp, forests of 1, 4, 16,
  * 64, 128 or 256 subtrees (SNT_OPT_ROOTS) and R/3 mode 0, 1 or 2; CUDA-core
  * Toeplitz engine with tree split 4 or 8; transform multiplier (engine 2)
- * with forests of 1, 16, 64 or 128 subtrees and R/3 mode 0 or 2 } (some
- * combinations pruned; one R/3 element per lane group).  Synchronous; uses
- * the context's scratch (B must fit the budget).
+ * with forests of 1, 16, 64 or 128 subtrees and R/3 mode 0 or 2; the
+ * tensor-core engine in 2 or 4 pipelined parts (SNT_OPT_PARTS) with forests
+ * of 16 .. 256 } (some combinations pruned; one R/3 element per lane group).
+ * Synchronous; uses the context's scratch (B must fit the budget).
  * choice (optional, 8 ints): lanes, split, overlap, engine, tiles, kpt, roots,
  * r3 mode. */
 snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice);
+
+/* The layouts the autotuner kept for (P, ceil(log2 B)) on this context:
+ * out[0 .. min(n, 9)) = lanes, split, overlap, engine, tiles, kpt, roots,
+ * r3 mode, parts (all zero if it has not run for that bucket). */
+snt_status snt_ctx_tuned(snt_ctx *ctx, int P, size_t B, int *out, int n);
 
 /* snt_autotune_ex returning lanes, split and overlap only. */
 snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *split_out,
@@ -388,6 +401,17 @@ snt_status snt_ctx_phase_times(snt_ctx *ctx, float *ms, int n);
  * Writes instructions per second (summed over all SMs) to *ops_per_s and the
  * SM count to *sms.  Synchronous; uses no scratch. */
 snt_status snt_measure_int_peak(int device, int kind, double *ops_per_s, int *sms);
+
+/* Measures the 5th-generation tensor-core MMA (tcgen05.mma kind::f16: f16
+ * operands from shared memory, f32 accumulator in tensor memory) at M = 128,
+ * K = 16 and N = n (16, 32, 64, 128 or 256): one CTA per SM issuing
+ * back-to-back MMAs into one accumulator, the result checked against its
+ * closed form.  Writes multiply-adds per second (all SMs) to *macs_per_s and
+ * the SM count to *sms.  The rate at small N bounds what a tcgen05 form of
+ * the R/q Toeplitz products could reach (no calls of key generation use
+ * it).  Returns SNT_EINTERNAL if the accumulator is wrong, SNT_ETIMEOUT if
+ * the MMAs did not complete in about two seconds.  Synchronous. */
+snt_status snt_measure_tc05(int device, int n, double *macs_per_s, int *sms);
 
 /* One-line description of the last error on this host thread. */
 const char *snt_last_error_string(void);

@@ -24,6 +24,7 @@ PARAMS = {653: (653, 4621, 288), 761: (761, 4591, 286), 857: (857, 5167, 322)}
 SNT_OPT_R3_LANES, SNT_OPT_TREE_SPLIT, SNT_OPT_R3_OVERLAP, SNT_OPT_NARROW_SEG = 1, 2, 3, 4
 SNT_OPT_RQ_ENGINE, SNT_OPT_MMA_TILES, SNT_OPT_R3_KPT, SNT_OPT_MMA_KSPLIT = 5, 6, 7, 8
 SNT_OPT_ROOTS, SNT_OPT_R3_MODE, SNT_OPT_FUSE_LEAF, SNT_OPT_PERKEY_INV = 9, 10, 11, 12
+SNT_OPT_PARTS = 13
 
 # phase names of snt_ctx_phase_times (SNT_NPHASES entries)
 PHASES = ("sample_f", "r3_inv", "tree_up", "root_inv", "tree_down", "h_encode", "sha512",
@@ -102,10 +103,13 @@ def load():
         "snt_autotune": [P, i32, sz, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                          ctypes.POINTER(ctypes.c_int)],
         "snt_autotune_ex": [P, i32, sz, ctypes.POINTER(ctypes.c_int)],
+        "snt_ctx_tuned": [P, i32, sz, ctypes.POINTER(ctypes.c_int), i32],
         "snt_ctx_get_option": [P, i32, ctypes.POINTER(ctypes.c_int)],
         "snt_ctx_phase_times": [P, P, i32],
         "snt_measure_int_peak": [i32, i32, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int)],
+        "snt_measure_tc05": [i32, i32, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -194,8 +198,15 @@ class Context:
         """Pick the fastest kernel layouts for (P, B) on this GPU; returns them."""
         c = (ctypes.c_int * 8)()
         _check(load().snt_autotune_ex(self.handle, P, B, c))
+        return self.tuned(P, B)
+
+    def tuned(self, P, B):
+        """The layouts the autotuner kept for (P, B) on this context."""
+        c = (ctypes.c_int * 9)()
+        _check(load().snt_ctx_tuned(self.handle, P, B, c, 9))
         return {"r3_lanes": c[0], "tree_split": c[1], "r3_overlap": c[2], "rq_engine": c[3],
-                "mma_tiles": c[4], "r3_kpt": c[5], "roots": c[6], "r3_mode": c[7]}
+                "mma_tiles": c[4], "r3_kpt": c[5], "roots": c[6], "r3_mode": c[7],
+                "parts": c[8]}
 
     def set_timing(self, on=True):
         _check(load().snt_ctx_set_timing(self.handle, 1 if on else 0))
@@ -368,6 +379,15 @@ def snt_measure_int_peak(device=0, kind=0):
     n = ctypes.c_int()
     _check(load().snt_measure_int_peak(device, kind, ctypes.byref(v), ctypes.byref(n)))
     return v.value, n.value
+
+
+def snt_measure_tc05(device=0, n=16):
+    """(multiply-adds/s, SM count) of back-to-back tcgen05.mma kind::f16 at
+    M = 128, K = 16, N = n, operands in shared memory (result checked)."""
+    v = ctypes.c_double()
+    k = ctypes.c_int()
+    _check(load().snt_measure_tc05(device, n, ctypes.byref(v), ctypes.byref(k)))
+    return v.value, k.value
 
 
 def snt_debug_inject_g(ctx, P, key_indices, gs):

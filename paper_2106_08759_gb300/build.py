@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libsntrup_gb300.so")
 
-SOURCES = ["api.cu", "sample.cu", "r3inv.cu", "rqmul.cu", "rqinv.cu", "encode.cu", "peak.cu", "noalloc.cu", "ragged.cu", "kem.cu", "serve.cu", "rqmma.cu", "r3batch.cu", "rqntt.cu"]
+SOURCES = ["api.cu", "sample.cu", "r3inv.cu", "rqmul.cu", "rqinv.cu", "encode.cu", "peak.cu", "noalloc.cu", "ragged.cu", "kem.cu", "serve.cu", "rqmma.cu", "r3batch.cu", "rqntt.cu", "tc05.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -97,11 +97,12 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     const bool narrow = ctx->narrow_seg != 0;
     int engine = ctx->rq_engine;
     int mma_tiles = ctx->mma_tiles, kpt = ctx->r3_kpt, roots = ctx->roots, r3mode = ctx->r3_mode;
+    int parts = ctx->parts;
     const snt_ctx::Tuned &tu = ctx->tuned[pidx(P)][bbucket(B)];
     if (tu.lanes) {
         mode = tu.overlap; lanes = tu.lanes; split = tu.split;
         engine = tu.engine; mma_tiles = tu.tiles; kpt = tu.kpt; roots = tu.roots;
-        r3mode = tu.r3mode;
+        r3mode = tu.r3mode; parts = tu.parts;
     }
     // engine 2: the general x general levels by the transform multiplier,
     // the small-operand levels (leaves) and h on the tensor cores
@@ -213,6 +214,101 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         const Tree &t = fo.t;
         auto lmap = [&](int l) { return equal_subtrees(fo.sub[l - 1], fo.sub[l]); };
         const int L = (int)t.n.size() - 1;
+        // Pipelined parts: the subtrees split into nparts groups of
+        // consecutive keys, each run from its up-sweep to its pk hash on a
+        // stream of its own, so that one group's latency-bound root
+        // inversions overlap another group's wide levels (the same products
+        // and inversions, the same bytes).
+        const int nparts = (mma && !inline_stream && parts > 1 && fo.K % parts == 0) ? parts : 1;
+        if (nparts > 1) {
+            const int KP = fo.K / nparts, BP = Bi / nparts;
+            cudaStream_t ps[kMaxParts] = {st, ctx->part[0], ctx->part[1], ctx->part[2]};
+            SNT_CUDA(cudaEventRecord(ctx->ev_pfork, st));
+            for (int q = 1; q < nparts; ++q) SNT_CUDA(cudaStreamWaitEvent(ps[q], ctx->ev_pfork, 0));
+            auto rows = [&](int l, int q) { return (size_t)t.off[l] + (size_t)q * KP * fo.sub[l]; };
+            for (int q = 0; q < nparts; ++q) {
+                const cudaStream_t sq = ps[q];
+                for (int l = 1; l <= L; ++l) {
+                    if (q == 0 && !forked && t.n[l] < kNarrow) {
+                        const snt_status s3 = fork_r3();
+                        if (s3 != SNT_OK) return s3;
+                        forked = true;
+                    }
+                    const int nq = KP * fo.sub[l];
+                    if (ntt && l > 1)
+                        SNT_CUDA(launch_tree_up_ntt<P>(nodes + rows(l - 1, q) * pi.pad, lmap(l), nq,
+                                                       nodes + rows(l, q) * pi.pad, sq));
+                    else
+                        SNT_CUDA(launch_tree_up_mma<P>(nodes + rows(l - 1, q) * pi.pad, lmap(l), nq,
+                                                       nodes + rows(l, q) * pi.pad, sq, mma_tiles,
+                                                       l == 1, ctx->mma_ksplit));
+                }
+                if (q == 0 && !forked) {
+                    const snt_status s3 = fork_r3();
+                    if (s3 != SNT_OK) return s3;
+                    forked = true;
+                }
+                if (tm && q == 0) SNT_CUDA(cudaEventRecord(ev[4], sq));
+                const size_t kq = (size_t)q * BP;  // first key row of the part
+                if (s_ahead) {
+                    SNT_CUDA(cudaEventRecord(ctx->ev_psfork[q], sq));
+                    SNT_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_psfork[q], 0));
+                    SNT_CUDA(launch_leaf_s<P>(KP * fo.sub[1], gbuf + kq * pi.pad,
+                                              leaves + kq * pi.pad, lm1, sbuf + kq * pi.pad,
+                                              ctx->side));
+                    SNT_CUDA(cudaEventRecord(ctx->ev_psready[q], ctx->side));
+                }
+                int16_t *rootq = nodes + rows(L, q) * pi.pad;
+                SNT_CUDA(launch_rq_inv_jump<P>(KP, rootq, pi.pad, rootq, pi.pad, nullptr,
+                                               ctx->d_err, ERR_ROOT, sq));
+                if (tm && q == 0) SNT_CUDA(cudaEventRecord(ev[5], sq));
+                for (int l = L; l >= (fuse ? 2 : 1); --l) {
+                    const int nq = KP * fo.sub[l];
+                    if (ntt && l > 1)
+                        SNT_CUDA(launch_tree_down_ntt<P>(nodes + rows(l, q) * pi.pad, lmap(l), nq,
+                                                         nodes + rows(l - 1, q) * pi.pad, sq));
+                    else
+                        SNT_CUDA(launch_tree_down_mma<P>(nodes + rows(l, q) * pi.pad, lmap(l), nq,
+                                                         nodes + rows(l - 1, q) * pi.pad, sq,
+                                                         mma_tiles, l == 1, ctx->mma_ksplit));
+                }
+                if (tm && q == 0) SNT_CUDA(cudaEventRecord(ev[6], sq));
+                if (r3chk && !joined) SNT_CUDA(cudaStreamWaitEvent(sq, ctx->ev_gready, 0));
+                if (tm && q == 0) SNT_CUDA(cudaEventRecord(ev[7], sq));
+                const KeyMap kmq = single_batch(seed, first + kq, BP, pk + kq * pi.pk_bytes,
+                                                sk + kq * pi.sk_bytes);
+                if (fuse) {
+                    if (s_ahead) SNT_CUDA(cudaStreamWaitEvent(sq, ctx->ev_psready[q], 0));
+                    SNT_CUDA(launch_finalize_pair<P>(kmq, KP * fo.sub[1], gbuf + kq * pi.pad,
+                                                     leaves + kq * pi.pad,
+                                                     nodes + rows(1, q) * pi.pad, lm1, pi.pk_bytes,
+                                                     pi.sk_bytes, 2 * sb, pi.sched, sq,
+                                                     s_ahead ? sbuf + kq * pi.pad : nullptr));
+                } else {
+                    SNT_CUDA(launch_finalize<P>(kmq, BP, gbuf + kq * pi.pad, nodes + kq * pi.pad,
+                                                pi.pk_bytes, pi.sk_bytes, 2 * sb, pi.sched, sq,
+                                                mma));
+                }
+                if (tm && q == 0) SNT_CUDA(cudaEventRecord(ev[8], sq));
+                SNT_CUDA(launch_sha512_pk(kmq, BP, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes,
+                                          sq));
+                if (tm && q == 0) SNT_CUDA(cudaEventRecord(ev[9], sq));
+                if (q > 0) {
+                    SNT_CUDA(cudaEventRecord(ctx->ev_pdone[q], sq));
+                    SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_pdone[q], 0));
+                }
+            }
+            inv_leaves = nodes + (size_t)t.off[fuse ? 1 : 0] * pi.pad;
+            if (!joined) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+            if (!r3chk)  // keys whose g was redrawn by the deferred per-key R/3 kernel
+                SNT_CUDA(launch_fixup<P>(km, fix_count, fix_keys, gfix, inv_leaves, pi.pk_bytes,
+                                         pi.sk_bytes, 2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st,
+                                         fuse ? leaves : nullptr, lm1));
+            if (tm) SNT_CUDA(cudaEventRecord(ev[10], st));
+            SNT_CUDA(cudaEventRecord(ctx->ev_done, st));
+            SNT_CUDA(cudaStreamWaitEvent(caller, ctx->ev_done, 0));
+            return SNT_OK;
+        }
         for (int l = 1; l <= L; ++l) {
             if (!forked && t.n[l] < kNarrow) {
                 const snt_status s3 = fork_r3();
@@ -412,6 +508,16 @@ snt_status snt_ctx_create(int device, size_t mem_budget, snt_ctx **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->tree, cudaStreamNonBlocking, prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->tune, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_low);
+    // pipelined parts after the first, each a step below the one before
+    for (int q = 0; q < kMaxParts - 1 && e == cudaSuccess; ++q)
+        e = cudaStreamCreateWithPriority(&c->part[q], cudaStreamNonBlocking,
+                                         prio_high + (q + 1 <= prio_low - prio_high ? q + 1 : prio_low - prio_high));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_pfork, cudaEventDisableTiming);
+    for (int q = 0; q < kMaxParts && e == cudaSuccess; ++q) {
+        e = cudaEventCreateWithFlags(&c->ev_pdone[q], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_psfork[q], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_psready[q], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_r3fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_gready, cudaEventDisableTiming);
@@ -434,6 +540,8 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     if (ctx->aux) cudaStreamSynchronize(ctx->aux);
     if (ctx->tree) cudaStreamSynchronize(ctx->tree);
     if (ctx->side) cudaStreamSynchronize(ctx->side);
+    for (cudaStream_t q : ctx->part)
+        if (q) cudaStreamSynchronize(q);
     cudaDeviceSynchronize();
     if (ctx->arena) {
         cudaMemset(ctx->arena, 0, ctx->budget);  // secret-bearing scratch
@@ -465,6 +573,14 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    for (cudaStream_t q : ctx->part)
+        if (q) cudaStreamDestroy(q);
+    if (ctx->ev_pfork) cudaEventDestroy(ctx->ev_pfork);
+    for (int q = 0; q < kMaxParts; ++q) {
+        if (ctx->ev_pdone[q]) cudaEventDestroy(ctx->ev_pdone[q]);
+        if (ctx->ev_psfork[q]) cudaEventDestroy(ctx->ev_psfork[q]);
+        if (ctx->ev_psready[q]) cudaEventDestroy(ctx->ev_psready[q]);
+    }
     delete ctx;
     return SNT_OK;
 }
@@ -489,6 +605,7 @@ snt_status snt_ctx_sync(snt_ctx *ctx, snt_stream stream) {
     SNT_CUDA(cudaStreamSynchronize(ctx->aux));
     SNT_CUDA(cudaStreamSynchronize(ctx->tree));
     SNT_CUDA(cudaStreamSynchronize(ctx->side));
+    for (cudaStream_t q : ctx->part) SNT_CUDA(cudaStreamSynchronize(q));
     int err = 0;
     SNT_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
@@ -700,6 +817,11 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             if (value < 0 || value > 1) return set_error(SNT_EINVAL, "per-key inversion is 0 or 1");
             ctx->perkey_inv = value;
             return SNT_OK;
+        case SNT_OPT_PARTS:
+            if (value != 1 && value != 2 && value != 4)
+                return set_error(SNT_EINVAL, "pipelined parts is 1, 2 or 4");
+            ctx->parts = value;
+            return SNT_OK;
         default:
             return set_error(SNT_EINVAL, "unknown option %d", option);
     }
@@ -720,6 +842,7 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
         case SNT_OPT_R3_MODE: *value = ctx->r3_mode; return SNT_OK;
         case SNT_OPT_FUSE_LEAF: *value = ctx->fuse_leaf; return SNT_OK;
         case SNT_OPT_PERKEY_INV: *value = ctx->perkey_inv; return SNT_OK;
+        case SNT_OPT_PARTS: *value = ctx->parts; return SNT_OK;
         default: return set_error(SNT_EINVAL, "unknown option %d", option);
     }
 }
@@ -761,6 +884,17 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
                     c.lanes = la; c.kpt = kp; c.overlap = ov; c.engine = 0; c.tiles = 1; c.split = sp;
                     cands.push_back(c);
                 }
+                // pipelined parts (tensor-core engine, forests of 16 .. 256)
+                if (la != 32)
+                    for (int pa : {2, 4})
+                        for (int rt : {16, 64, 128, 256})
+                            for (int r3m : {0, 2}) {
+                                snt_ctx::Tuned c;
+                                c.lanes = la; c.kpt = kp; c.overlap = ov; c.engine = 1; c.tiles = 1;
+                                c.roots = rt; c.r3mode = r3m; c.split = ctx->tree_split;
+                                c.parts = pa;
+                                cands.push_back(c);
+                            }
                 // the transform multiplier on the general levels
                 if (la != 32)
                     for (int rt : {1, 16, 64, 128})
@@ -809,6 +943,18 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
         choice[7] = best.r3mode;
     }
     return snt_ctx_sync(ctx, ts);
+}
+
+snt_status snt_ctx_tuned(snt_ctx *ctx, int P, size_t B, int *out, int n) {
+    if (!ctx || !out || n < 0) return set_error(SNT_EINVAL, "null argument");
+    ParamInfo pi;
+    if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
+    if (B == 0 || B > kMaxB) return set_error(SNT_EINVAL, "batch size %zu out of range", B);
+    const snt_ctx::Tuned &t = ctx->tuned[pidx(P)][bbucket(B)];
+    const int v[9] = {t.lanes, t.split, t.overlap, t.engine, t.tiles, t.kpt, t.roots, t.r3mode,
+                      t.parts};
+    for (int i = 0; i < n && i < 9; ++i) out[i] = v[i];
+    return SNT_OK;
 }
 
 snt_status snt_autotune(snt_ctx *ctx, int P, size_t B, int *lanes_out, int *split_out,

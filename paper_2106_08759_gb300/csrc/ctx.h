@@ -17,6 +17,7 @@ inline constexpr int kMaxInject = 64;
 // R/3 kernel.
 inline constexpr int kPhaseEvents = 11;
 inline constexpr size_t kMaxB = (size_t)1 << 24;
+inline constexpr int kMaxParts = 4;  // pipelined parts of one batch keygen call
 
 
 // Cached CUDA graph of one ragged launch plan (the list of (P, B) pairs).
@@ -58,9 +59,14 @@ struct snt_ctx {
     int r3_mode = snt::kDefaultR3Mode;
     int fuse_leaf = 1;  // h from the level-1 inverses (where FuseLeaf<P>::ok)
     int perkey_inv = 1; // per-key path: 1 jump divsteps, 0 one divstep per barrier
+    int parts = 1;      // pipelined parts of a batch keygen call (SNT_OPT_PARTS)
+    cudaStream_t part[snt::kMaxParts - 1] = {};  // streams of parts 1 .. kMaxParts-1
+    cudaEvent_t ev_pfork = nullptr, ev_pdone[snt::kMaxParts] = {};
+    cudaEvent_t ev_psfork[snt::kMaxParts] = {}, ev_psready[snt::kMaxParts] = {};
     // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
     struct Tuned {
         int lanes = 0, split = 0, overlap = 0, engine = 0, tiles = 1, kpt = 1, roots = 1, r3mode = 0;
+        int parts = 1;
     };
     Tuned tuned[3][25];
     cudaStream_t tune = nullptr;  // stream used while autotuning

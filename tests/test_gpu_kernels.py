@@ -213,3 +213,11 @@ def test_microbench_all_rq_inversions(snt, ctx, pool, latency):
     okh = ok.cpu().numpy()
     assert okh.all()
     assert pool.bad_inverses(p, q, x, outh, okh) == []
+
+
+@pytest.mark.parametrize("n", [16, 64, 256])
+def test_tcgen05_measurement_checks_its_accumulator(snt, n):
+    # the tcgen05.mma rate measurement (engine choice; not on the keygen path)
+    # verifies D = A B^T against its closed form before reporting a rate
+    rate, sms = snt.snt_measure_tc05(0, n)
+    assert rate > 0 and sms > 0

@@ -411,3 +411,52 @@ def test_benchmarked_layout_b4096_vs_perkey_and_oracle(snt, pool):
     idx = np.array(sorted(idx))
     assert idx.size >= 256
     assert pool.bad_keys(761, seed, idx, pk[idx], sk[idx]) == []
+
+
+@pytest.mark.parametrize("parts,roots,B,engine,r3mode,fuse", [
+    (2, 64, 4096, 1, 2, 1), (4, 64, 4096, 1, 2, 1), (4, 128, 4096, 1, 0, 1),
+    (2, 16, 96, 1, 0, 1), (4, 32, 96, 1, 1, 1), (4, 8, 96, 1, 2, 0), (2, 8, 96, 2, 0, 1),
+    (2, 2, 6, 1, 0, 1), (4, 3, 96, 1, 0, 1)])
+def test_pipelined_parts_give_the_same_keys(snt, ctx, parts, roots, B, engine, r3mode, fuse):
+    # the forest's subtrees split into groups of consecutive keys on their own
+    # streams (96 keys in 32 subtrees: 3-key subtrees with unpaired leaves);
+    # (4, 3, 96): the forest has 2 subtrees, not a multiple of 4, so the call
+    # runs in one part
+    ctx.set_option(snt.SNT_OPT_ROOTS, roots)
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, engine)
+    ctx.set_option(snt.SNT_OPT_R3_MODE, r3mode)
+    ctx.set_option(snt.SNT_OPT_FUSE_LEAF, fuse)
+    try:
+        ref = gpu_keygen(snt, ctx, 761, 14, 90, B)
+        ctx.set_option(snt.SNT_OPT_PARTS, parts)
+        got = gpu_keygen(snt, ctx, 761, 14, 90, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_PARTS, 1)
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
+        ctx.set_option(snt.SNT_OPT_R3_MODE, 0)
+        ctx.set_option(snt.SNT_OPT_FUSE_LEAF, 1)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    if B <= 96:
+        rpk, rsk = oracle.keygen_batch(761, 14, 90, B)
+        assert first_mismatch(got[0], rpk) is None and first_mismatch(got[1], rsk) is None
+
+
+def test_pipelined_parts_redraw_injected_zero_divisors(snt, ctx):
+    # keys of both parts whose first g is a zero divisor: the per-key R/3
+    # fall-back and the fix-up run after the parts join
+    bads = _zero_divisors(761, np.random.default_rng(9))
+    offs = [5, 60]
+    snt.snt_debug_inject_g(ctx, 761, [300 + o for o in offs], np.stack(bads[:2]))
+    ctx.set_option(snt.SNT_OPT_ROOTS, 8)
+    ctx.set_option(snt.SNT_OPT_PARTS, 2)
+    ctx.set_option(snt.SNT_OPT_R3_MODE, 2)
+    try:
+        pk, sk = gpu_keygen(snt, ctx, 761, 4, 300, 96)
+    finally:
+        ctx.set_option(snt.SNT_OPT_PARTS, 1)
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+        ctx.set_option(snt.SNT_OPT_R3_MODE, 0)
+        snt.snt_debug_inject_g(ctx, 761, [], np.zeros((0, 761), np.int8))
+    rpk, rsk = oracle.keygen_batch(761, 4, 300, 96, g_inject=dict(zip(offs, bads[:2])))
+    assert first_mismatch(pk, rpk) is None and first_mismatch(sk, rsk) is None
