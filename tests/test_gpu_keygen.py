@@ -416,11 +416,11 @@ def test_benchmarked_layout_b4096_vs_perkey_and_oracle(snt, pool):
 @pytest.mark.parametrize("parts,roots,B,engine,r3mode,fuse", [
     (2, 64, 4096, 1, 2, 1), (4, 64, 4096, 1, 2, 1), (4, 128, 4096, 1, 0, 1),
     (2, 16, 96, 1, 0, 1), (4, 32, 96, 1, 1, 1), (4, 8, 96, 1, 2, 0), (2, 8, 96, 2, 0, 1),
-    (2, 2, 6, 1, 0, 1), (4, 3, 96, 1, 0, 1)])
+    (2, 2, 6, 1, 0, 1), (4, 2, 96, 1, 0, 1)])
 def test_pipelined_parts_give_the_same_keys(snt, ctx, parts, roots, B, engine, r3mode, fuse):
     # the forest's subtrees split into groups of consecutive keys on their own
     # streams (96 keys in 32 subtrees: 3-key subtrees with unpaired leaves);
-    # (4, 3, 96): the forest has 2 subtrees, not a multiple of 4, so the call
+    # (4, 2, 96): the forest has 2 subtrees, not a multiple of 4, so the call
     # runs in one part
     ctx.set_option(snt.SNT_OPT_ROOTS, roots)
     ctx.set_option(snt.SNT_OPT_RQ_ENGINE, engine)
