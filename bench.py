@@ -419,6 +419,25 @@ def measure_micro(snt, torch, ctx, dev, stream, flush, reps):
     ms = event_ms(torch, stream, flush, lambda: snt.snt_rq_inv(ctx, P, k, x, xo, xk, stream), reps)
     out["rq_inv_step"] = {"n": k, "ms": round(ms, 3), "inv_per_s": round(k / ms * 1e3)}
     out["ops"] = "general: 2 p^2 per product (multiply-adds); Short: p w add/sub per product"
+    # the serving path's kernels alone: 65536 encapsulations and decapsulations
+    # (one CTA per item) on keys from batch keygen
+    nk = 1 << 16
+    pkb, skb, ctb, _ = snt.snt_param_sizes(P)
+    kpk = torch.empty(nk * pkb, dtype=torch.uint8, device=dev)
+    ksk = torch.empty(nk * skb, dtype=torch.uint8, device=dev)
+    for i in range(0, nk, 4096):
+        snt.snt_batch_keygen(ctx, P, 77, i, 4096, kpk[i * pkb:(i + 4096) * pkb],
+                             ksk[i * skb:(i + 4096) * skb], stream)
+    ct = torch.empty(nk * ctb, dtype=torch.uint8, device=dev)
+    ss = torch.empty(nk * 32, dtype=torch.uint8, device=dev)
+    ss2 = torch.empty(nk * 32, dtype=torch.uint8, device=dev)
+    ms_e = event_ms(torch, stream, flush, lambda: snt.snt_enc(ctx, P, nk, kpk, 5, 0, ct, ss, stream),
+                    reps)
+    ms_d = event_ms(torch, stream, flush, lambda: snt.snt_dec(ctx, P, nk, ksk, ct, ss2, stream),
+                    reps)
+    ctx.sync()
+    out["kem"] = {"n": nk, "enc_per_s": round(nk / ms_e * 1e3), "dec_per_s": round(nk / ms_d * 1e3),
+                  "dec_matches_enc": bool(torch.equal(ss, ss2))}
     return out
 
 

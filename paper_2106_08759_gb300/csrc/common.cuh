@@ -116,6 +116,22 @@ __device__ __forceinline__ BatchDesc key_batch(const KeyMap &km, int j) {
     return km.tab[lo];
 }
 
+// Index in the batch table of the batch of key j (0 for a single batch).
+__device__ __forceinline__ int key_batch_index(const KeyMap &km, int j) {
+    int lo = 0, hi = km.nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (km.tab[mid].key_base <= j) lo = mid; else hi = mid - 1;
+    }
+    return km.nb > 0 ? lo : 0;
+}
+
+// Flag index of key j's subtree: sub_size keys per subtree, or (sub_size 0)
+// one subtree per batch of the table.
+__device__ __forceinline__ int key_subtree(const KeyMap &km, int j, int sub_size) {
+    return sub_size > 0 ? j / sub_size : key_batch_index(km, j);
+}
+
 // Batch owning node j of a forest level (pre: nb + 1 prefix sums).
 __device__ __forceinline__ int level_batch(const int *pre, int nb, int j) {
     int lo = 0, hi = nb - 1;

@@ -315,12 +315,25 @@ k_fixup(KeyMap km, const int *__restrict__ fix_count, const int *__restrict__ fi
         const int16_t *inv = ainv + (size_t)key * G::pad;
         __syncthreads();  // shared buffers free from the previous entry
         if (leaves) {
-            // leaf row key: subtree b, index i; level-1 node b * sub_out + i / 2
-            const int b = key / lm1.n_in, i = key - b * lm1.n_in;
-            const int16_t *node = ainv + (size_t)(b * lm1.sub_out + i / 2) * G::pad;
+            // leaf row key: tree b, index i in it; level-1 node (first node
+            // of b) + i / 2; equal subtrees or (nb > 0) a forest of batches
+            int b, i, first_leaf, n_leaf, first_node;
+            if (lm1.nb > 0) {
+                b = level_batch(lm1.pre_in, lm1.nb, key);
+                first_leaf = lm1.pre_in[b];
+                n_leaf = lm1.pre_in[b + 1] - first_leaf;
+                first_node = lm1.pre_out[b];
+            } else {
+                b = key / lm1.n_in;
+                first_leaf = b * lm1.n_in;
+                n_leaf = lm1.n_in;
+                first_node = b * lm1.sub_out;
+            }
+            i = key - first_leaf;
+            const int16_t *node = ainv + (size_t)(first_node + i / 2) * G::pad;
             const int sib = i ^ 1;
-            if (sib < lm1.n_in) {
-                fill_A<P>(leaves + (size_t)(b * lm1.n_in + sib) * G::pad, As);
+            if (sib < n_leaf) {
+                fill_A<P>(leaves + (size_t)(first_leaf + sib) * G::pad, As);
                 fill_E<P>(node, Es);
                 __syncthreads();
                 int acc[1][8];

@@ -289,7 +289,8 @@ k_r3_check(KeyMap km, int B, int8_t *__restrict__ gbuf, int16_t *__restrict__ le
 }
 
 // Small_encode(1/g) into the secret key from the inverted R/3 leaves (keys of
-// subtrees whose root did not invert, sub_ok[key / sub_size] == 0, skipped).
+// subtrees whose root did not invert skipped: sub_ok[key / sub_size] == 0, or
+// with sub_size 0 the flag of the key's batch).
 template <int P>
 __global__ void __launch_bounds__(256)
 k_r3_encode_v(KeyMap km, int B, const int16_t *__restrict__ v3, int sk_bytes, int sk_off,
@@ -298,7 +299,7 @@ k_r3_encode_v(KeyMap km, int B, const int16_t *__restrict__ v3, int sk_bytes, in
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int key = idx / G::small_bytes, b = idx % G::small_bytes;
     if (key >= B) return;
-    if (sub_ok && !sub_ok[key / sub_size]) return;
+    if (sub_ok && !sub_ok[key_subtree(km, key, sub_size)]) return;
     const int16_t *v = v3 + (size_t)key * G::pad;
     uint32_t byte = 0;
 #pragma unroll

@@ -247,7 +247,8 @@ k_r3_keygen(KeyMap km, int B, int8_t *__restrict__ g_out, int sk_bytes, int sk_o
     if (ebase >= B) return;                               // warp-uniform
     if (sub_ok) {  // fall-back form: only warps with a key in a failed subtree
         bool all_ok = true;
-        for (int e = ebase; e < min(ebase + EPW, B); ++e) all_ok = all_ok && sub_ok[e / sub_size] != 0;
+        for (int e = ebase; e < min(ebase + EPW, B); ++e)
+            all_ok = all_ok && sub_ok[key_subtree(km, e, sub_size)] != 0;
         if (all_ok) return;
     }
     // this group's elements: warp slots grp + k GPW

@@ -52,7 +52,10 @@ struct Group {
     size_t off_nodes = 0, off_g = 0, off_fix = 0, off_gfix = 0, off_nodes3 = 0;
     // kernel layouts of this parameter set
     int lanes = 4, split = 8, tiles = 1, kpt = 1, ksplit = 4;
-    bool mma = true, ntt = false, r3batch = false;
+    // r3batch: R/3 inverses by the batch forest; r3first: on the first draws
+    // (invertibility from each batch's root, a failed batch redone per key)
+    bool mma = true, ntt = false, r3batch = false, r3first = false, fuse = false;
+    size_t off_r3ok = 0;  // one root flag per batch (r3first)
     R3Factors fac;
     // table offsets (bytes, from the start of the uploaded table block)
     size_t t_desc = 0, t_pre = 0, t_root = 0;
@@ -60,9 +63,13 @@ struct Group {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-void plan_group(Group &g, const size_t *B) {
+// Level structure of the batches of one parameter set.  min_levels = 1 (the
+// fused leaf level) gives a one-key batch a level-1 node too (its leaf moved
+// up unchanged), so that every batch's keys sit under level-1 nodes.  A
+// batch's root is its node on the last level where it has one.
+void plan_group(Group &g, const size_t *B, int min_levels) {
     const int nb = (int)g.batch.size();
-    std::vector<int> n(nb);
+    std::vector<int> n(nb), next(nb);
     for (int i = 0; i < nb; ++i) {
         n[i] = (int)B[g.batch[i]];
         g.nkeys += n[i];
@@ -76,21 +83,17 @@ void plan_group(Group &g, const size_t *B) {
         for (int i = 0; i < nb; ++i) pre[i + 1] = pre[i] + n[i];
         g.pre.push_back(pre);
         g.lev_off.push_back((int)off);
-        for (int i = 0; i < nb; ++i)
-            if (n[i] == 1 && (l == 0 || g.pre[l - 1][i + 1] - g.pre[l - 1][i] > 1))
-                g.root_row[i] = (int)off + pre[i];  // the level where batch i reaches one node
-        off += pre[nb];
         bool more = false;
         for (int i = 0; i < nb; ++i) {
-            n[i] = (n[i] > 1) ? (n[i] + 1) / 2 : 0;
-            more = more || n[i] > 0;
+            next[i] = n[i] > 1 ? (n[i] + 1) / 2 : (n[i] == 1 && l + 1 <= min_levels ? 1 : 0);
+            if (n[i] == 1 && next[i] == 0) g.root_row[i] = (int)off + pre[i];
+            more = more || next[i] > 0;
         }
+        off += pre[nb];
+        n = next;
         if (!more) break;
         g.L = l + 1;
     }
-    // a batch of one key has its root at level 0
-    for (int i = 0; i < nb; ++i)
-        if (B[g.batch[i]] == 1) g.root_row[i] = g.pre[0][i];
     g.nodes = off;
 }
 
@@ -106,6 +109,7 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
     int *fix_count = reinterpret_cast<int *>(ctx->arena + g.off_fix);
     int *fix_keys = fix_count + 1;
     int8_t *gfix = reinterpret_cast<int8_t *>(ctx->arena + g.off_gfix);
+    int *r3ok = reinterpret_cast<int *>(ctx->arena + g.off_r3ok);
     KeyMap km;
     std::memset(&km, 0, sizeof(km));
     km.tab = reinterpret_cast<const BatchDesc *>(tables + g.t_desc);
@@ -123,31 +127,46 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
     };
     // g's first draw with f; the R/3 work runs on the auxiliary stream beside
     // the R/q forest and is joined at the end
+    // (r3first: g's first draws also go to the R/3 leaves, as int16)
+    // the test hook's injected first draws (snt_debug_inject_g): by key index
+    const int n_inj = (ctx->inj_P == P) ? ctx->n_inj : 0;
     SNT_CUDA_R(launch_sample_f<P>(km, g.nkeys, nodes, pi.sk_bytes, 2 * sb + pi.pk_bytes, st, gbuf,
-                                  nullptr, nullptr, 0, fix_count));
+                                  ctx->d_inj_idx, ctx->d_inj_g, n_inj, fix_count,
+                                  g.r3first ? nodes3 : nullptr));
     SNT_CUDA_R(cudaEventRecord(ev_fork, st));
     SNT_CUDA_R(cudaStreamWaitEvent(aux, ev_fork, 0));
     if (g.r3batch) {
         // Sec. 3.1.1: isInvertible (remainders modulo the F_3 factors) with
-        // redraws, final g into the R/3 leaves; then Montgomery's trick in R/3
-        // over the same forest shape, one jump-divstep root per batch
-        SNT_CUDA_R(launch_r3_check<P>(km, g.nkeys, gbuf, nodes3, g.fac, ctx->d_err, aux));
-        SNT_CUDA_R(cudaEventRecord(ev_gready, aux));
+        // redraws, final g into the R/3 leaves, then Montgomery's trick in R/3
+        // over the same forest shape, one jump-divstep root per batch; or
+        // (r3first) the forest on the first draws, a batch whose root does
+        // not invert (some g in it is a zero divisor) redone per key below
+        if (!g.r3first) {
+            SNT_CUDA_R(launch_r3_check<P>(km, g.nkeys, gbuf, nodes3, g.fac, ctx->d_err, aux));
+            SNT_CUDA_R(cudaEventRecord(ev_gready, aux));
+        }
         for (int l = 1; l <= g.L; ++l)
             SNT_CUDA_R(launch_tree_up_mma3<P>(nodes3 + (size_t)g.lev_off[l - 1] * pi.pad, lmap(l),
                                               g.pre[l][nb], nodes3 + (size_t)g.lev_off[l] * pi.pad,
                                               aux, g.ksplit));
-        SNT_CUDA_R(launch_r3_inv_jump<P>(nb, nodes3, pi.pad, nodes3, pi.pad, nullptr, ctx->d_err,
-                                         ERR_ROOT, aux, roots));
+        SNT_CUDA_R(launch_r3_inv_jump<P>(nb, nodes3, pi.pad, nodes3, pi.pad,
+                                         g.r3first ? r3ok : nullptr,
+                                         g.r3first ? nullptr : ctx->d_err, ERR_ROOT, aux, roots));
         for (int l = g.L; l >= 1; --l)
             SNT_CUDA_R(launch_tree_down_mma3<P>(nodes3 + (size_t)g.lev_off[l] * pi.pad, lmap(l),
                                                 g.pre[l][nb],
                                                 nodes3 + (size_t)g.lev_off[l - 1] * pi.pad, aux,
                                                 g.ksplit));
-        SNT_CUDA_R(launch_r3_encode_v<P>(km, g.nkeys, nodes3, pi.sk_bytes, sb, aux));
+        SNT_CUDA_R(launch_r3_encode_v<P>(km, g.nkeys, nodes3, pi.sk_bytes, sb, aux,
+                                         g.r3first ? r3ok : nullptr, 0));
+        if (g.r3first)  // batches whose root did not invert: per key, with redraws
+            SNT_CUDA_R(launch_r3_keygen<P>(km, g.nkeys, gbuf, pi.sk_bytes, sb, ctx->d_inj_idx,
+                                           ctx->d_inj_g, n_inj, ctx->d_err, aux, g.lanes, g.kpt,
+                                           gfix, fix_count, fix_keys, r3ok, 0));
     } else {
-        SNT_CUDA_R(launch_r3_keygen<P>(km, g.nkeys, gbuf, pi.sk_bytes, sb, nullptr, nullptr, 0,
-                                       ctx->d_err, aux, g.lanes, g.kpt, gfix, fix_count, fix_keys));
+        SNT_CUDA_R(launch_r3_keygen<P>(km, g.nkeys, gbuf, pi.sk_bytes, sb, ctx->d_inj_idx,
+                                       ctx->d_inj_g, n_inj, ctx->d_err, aux, g.lanes, g.kpt, gfix,
+                                       fix_count, fix_keys));
     }
     SNT_CUDA_R(cudaEventRecord(ev_join, aux));
     for (int l = 1; l <= g.L; ++l) {
@@ -165,7 +184,7 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
     }
     SNT_CUDA_R(launch_rq_inv_jump<P>(nb, nodes, pi.pad, nodes, pi.pad, nullptr, ctx->d_err,
                                      ERR_ROOT, st, roots));
-    for (int l = g.L; l >= 1; --l) {
+    for (int l = g.L; l >= (g.fuse ? 2 : 1); --l) {
         const int n_par = g.pre[l][nb];
         if (g.ntt && l > 1)
             SNT_CUDA_R(launch_tree_down_ntt<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lmap(l),
@@ -178,14 +197,23 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
             SNT_CUDA_R(launch_tree_down<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lmap(l), n_par,
                                            nodes + (size_t)g.lev_off[l - 1] * pi.pad, st, g.split));
     }
-    if (g.r3batch) SNT_CUDA_R(cudaStreamWaitEvent(st, ev_gready, 0));  // h needs the final g
-    SNT_CUDA_R(launch_finalize<P>(km, g.nkeys, gbuf, nodes, pi.pk_bytes, pi.sk_bytes, 2 * sb,
-                                  pi.sched, st, g.mma));
+    if (g.r3batch && !g.r3first)  // h needs the final g
+        SNT_CUDA_R(cudaStreamWaitEvent(st, ev_gready, 0));
+    if (g.fuse)
+        SNT_CUDA_R(launch_finalize_pair<P>(km, g.pre[1][nb], gbuf, nodes,
+                                           nodes + (size_t)g.lev_off[1] * pi.pad, lmap(1),
+                                           pi.pk_bytes, pi.sk_bytes, 2 * sb, pi.sched, st,
+                                           nullptr));
+    else
+        SNT_CUDA_R(launch_finalize<P>(km, g.nkeys, gbuf, nodes, pi.pk_bytes, pi.sk_bytes, 2 * sb,
+                                      pi.sched, st, g.mma));
     SNT_CUDA_R(launch_sha512_pk(km, g.nkeys, pi.pk_bytes, pi.sk_bytes, 3 * sb + pi.pk_bytes, st));
     SNT_CUDA_R(cudaStreamWaitEvent(st, ev_join, 0));
-    if (!g.r3batch)  // keys whose g the per-key R/3 kernel redrew: h, pk, hash again
-        SNT_CUDA_R(launch_fixup<P>(km, fix_count, fix_keys, gfix, nodes, pi.pk_bytes, pi.sk_bytes,
-                                   2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st));
+    if (!g.r3batch || g.r3first)  // keys whose g a per-key R/3 kernel redrew: h, pk, hash again
+        SNT_CUDA_R(launch_fixup<P>(km, fix_count, fix_keys, gfix,
+                                   g.fuse ? nodes + (size_t)g.lev_off[1] * pi.pad : nodes,
+                                   pi.pk_bytes, pi.sk_bytes, 2 * sb, 3 * sb + pi.pk_bytes, pi.sched,
+                                   st, g.fuse ? nodes : nullptr, lmap(1)));
     return SNT_OK;
 }
 
@@ -238,15 +266,6 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         if (g.batch.empty()) continue;
         g.P = Ps[j];
         param_info(g.P, g.pi);
-        plan_group(g, B);
-        g.off_nodes = arena_off;
-        arena_off += align_up(g.nodes * g.pi.pad * sizeof(int16_t), 256);
-        g.off_g = arena_off;
-        arena_off += align_up((size_t)g.nkeys * g.pi.pad, 256);
-        g.off_fix = arena_off;
-        arena_off += align_up(sizeof(int) * (1 + (size_t)g.nkeys), 256);
-        g.off_gfix = arena_off;
-        arena_off += align_up((size_t)g.nkeys * g.pi.pad, 256);
         // layouts: the autotuner's choice for (p, the largest batch's bucket)
         // if it ran on this context, else the context's options
         size_t bmax = 0;
@@ -255,16 +274,36 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         g.lanes = ctx->r3_lanes; g.split = ctx->tree_split; g.tiles = ctx->mma_tiles;
         g.kpt = ctx->r3_kpt; g.mma = ctx->rq_engine != 0; g.ntt = ctx->rq_engine == 2;
         g.r3batch = ctx->r3_mode != 0;
+        g.r3first = ctx->r3_mode == 2;
         g.ksplit = ctx->mma_ksplit;
         if (tu.lanes) {
             g.lanes = tu.lanes; g.split = tu.split; g.tiles = tu.tiles; g.kpt = tu.kpt;
             g.mma = tu.engine != 0; g.ntt = tu.engine == 2; g.r3batch = tu.r3mode != 0;
+            g.r3first = tu.r3mode == 2;
         }
+        // h from the level-1 inverses (the down-sweep's leaf level folded
+        // into h, as in the single-batch call) needs the tensor-core h kernel
+        const bool fuse_ok = g.P == 653 ? FuseLeaf<653>::ok : g.P == 761 ? FuseLeaf<761>::ok
+                                                                         : FuseLeaf<857>::ok;
+        g.fuse = g.mma && ctx->fuse_leaf && fuse_ok;
+        plan_group(g, B, g.fuse ? 1 : 0);
+        g.off_nodes = arena_off;
+        arena_off += align_up(g.nodes * g.pi.pad * sizeof(int16_t), 256);
+        g.off_g = arena_off;
+        arena_off += align_up((size_t)g.nkeys * g.pi.pad, 256);
+        g.off_fix = arena_off;
+        arena_off += align_up(sizeof(int) * (1 + (size_t)g.nkeys), 256);
+        g.off_gfix = arena_off;
+        arena_off += align_up((size_t)g.nkeys * g.pi.pad, 256);
         if (g.r3batch) {
-            const snt_status sf = r3_factors_for(ctx, g.P, g.fac);
-            if (sf != SNT_OK) return sf;
+            if (!g.r3first) {
+                const snt_status sf = r3_factors_for(ctx, g.P, g.fac);
+                if (sf != SNT_OK) return sf;
+            }
             g.off_nodes3 = arena_off;
             arena_off += align_up(g.nodes * g.pi.pad * sizeof(int16_t), 256);
+            g.off_r3ok = arena_off;
+            arena_off += align_up(g.batch.size() * sizeof(int), 256);
         }
         const size_t nb = g.batch.size();
         g.t_desc = tbytes;
@@ -326,7 +365,9 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         sig.push_back(g.ntt ? 1 : 0);
         sig.push_back(g.kpt);
         sig.push_back(g.ksplit);
-        sig.push_back(g.r3batch ? 1 : 0);
+        sig.push_back(g.r3batch ? (g.r3first ? 2 : 1) : 0);
+        sig.push_back(g.fuse ? 1 : 0);
+        sig.push_back(ctx->inj_P == g.P ? ctx->n_inj : 0);
     }
     if (!(rg.exec && rg.sig == sig && rg.table_off == table_off)) {
         if (rg.exec) cudaGraphExecDestroy(rg.exec);

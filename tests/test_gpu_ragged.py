@@ -42,9 +42,10 @@ def _single(snt, ctx, P, B, seed, first):
     return pk.cpu().numpy().reshape(B, -1), sk.cpu().numpy().reshape(B, -1)
 
 
-@pytest.mark.parametrize("r3_mode", [0, 1])
+@pytest.mark.parametrize("r3_mode", [0, 1, 2])
 def test_ragged_small_mixed(snt, r3_mode):
-    # R/3 per key (0) or batched after the invertibility test (1)
+    # R/3 per key (0), batched after the invertibility test (1), or batched on
+    # the first draws with the per-batch fall-back (2)
     Ps = [761, 653, 857, 761, 761, 653, 857]
     Bs = [5, 1, 33, 2, 64, 17, 1]
     firsts = [0, 10, 20, 100, 200, 300, 400]
@@ -85,3 +86,31 @@ def test_ragged_full_workload_256_batches(snt, layout):
         j = int(rng.integers(0, sizes[i]))
         opk, osk, _ = oracle.keygen(int(ps[i]), seeds[i], int(firsts[i]) + j)
         assert np.array_equal(got[i][0][j], opk) and np.array_equal(got[i][1][j], osk)
+
+
+@pytest.mark.parametrize("r3_mode", [0, 1, 2])
+def test_ragged_redraws_injected_zero_divisors(snt, r3_mode):
+    # first draws of g that are zero divisors in R/3 (one per irreducible
+    # factor of x^761 - x - 1 over F_3) in two batches: the invertibility test
+    # (mode 1), the failing batch roots with the per-key fall-back and the
+    # fix-up of h, pk and its hash (mode 2), or the per-key kernel (mode 0)
+    # must redraw them exactly as the oracle does
+    rng = np.random.default_rng(11)
+    bads = []
+    for d, _, poly in oracle.ddf(761, 3):
+        f = np.asarray(poly[: d + 1]) % 3
+        g = np.convolve(f, rng.integers(0, 3, 761 - d))[:761] % 3
+        bads.append(np.where(g == 2, -1, g).astype(np.int8))
+    Ps = [761, 653, 761, 857, 761]
+    Bs = [40, 7, 1, 9, 33]
+    firsts = [0, 1000, 2000, 3000, 4000]
+    seeds = [5, 6, 7, 8, 9]
+    keys = [3, 2000, 4031]  # batch 0 key 3, the one-key batch, batch 4 key 31
+    with snt.Context(0, 128 << 20) as ctx:
+        snt.snt_debug_inject_g(ctx, 761, keys, np.stack(bads))
+        ctx.set_option(snt.SNT_OPT_R3_MODE, r3_mode)
+        got = _run_ragged(snt, ctx, Ps, Bs, seeds, firsts)
+    for (pk, sk), P, B, s, f in zip(got, Ps, Bs, seeds, firsts):
+        inj = {k - f: b for k, b in zip(keys, bads) if P == 761 and f <= k < f + B}
+        rpk, rsk = oracle.keygen_batch(P, s, f, B, g_inject=inj)
+        assert np.array_equal(pk, rpk) and np.array_equal(sk, rsk), (P, B)
