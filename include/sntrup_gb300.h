@@ -157,7 +157,9 @@ snt_status snt_batch_keygen_static(int device, int P, uint64_t seed,
  * key + ciphertext bytes), the session key Hash_prefix(1, Hash_prefix(3, r_enc)
  * | ct); decapsulation re-encrypts and falls back to Hash_prefix(0,
  * Hash_prefix(3, rho) | ct) if the ciphertext does not match (implicit
- * rejection).  One CTA per item, asynchronous on `stream`. */
+ * rejection).  A CTA runs the ring arithmetic of up to 32 items in turn and
+ * one of its warps hashes them, a lane per item (one item per CTA for small
+ * counts).  Asynchronous on `stream`. */
 
 /* n encapsulations: item i uses pk_dev + i * pk_bytes and the Short r of
  * stream 3 for (seed, first_idx + i); writes ct_dev + i * ct_bytes and

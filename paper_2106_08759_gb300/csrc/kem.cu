@@ -1,5 +1,6 @@
 // kem.cu -- encapsulation and decapsulation of Streamlined NTRU Prime on the
-// device, one CTA of 256 threads per item (the serving path).
+// device (the serving path): a CTA of 256 threads runs the ring arithmetic of
+// up to 32 items in turn, then one warp hashes them, a lane per item.
 //
 // The paper measures these operations (Table 1) and relies on the NTRU Prime
 // specification for their definition; reading (round-3 KEM):
@@ -29,24 +30,18 @@ namespace snt {
 constexpr int KEM_THREADS = 256;
 constexpr int KEM_SPLIT = 2;  // products use 2 * p8/8 <= 256 threads
 
-template <int P>
-__global__ void __launch_bounds__(KEM_THREADS, 4)
-k_encap(EncMap em, int n, int pk_bytes, int ct_bytes, EncSched Spk, EncSched Sct) {
-    using G = Geo<P>;
-    constexpr int NT = Tp<P>::NT, Q = G::q;
-    __shared__ __align__(16) uint8_t pkb[1344];
-    __shared__ __align__(16) uint8_t ctb[1216];
-    __shared__ __align__(16) int As[Tp<P>::p8];
-    __shared__ __align__(16) int Es[Tp<P>::ESZ];
-    __shared__ int part[(KEM_SPLIT - 1) * Tp<P>::p8];
-    __shared__ uint32_t R[2][G::pad];
-    __shared__ __align__(16) uint32_t xs[1024];
-    __shared__ int hs[G::pad];
-    __shared__ uint8_t renc[G::small_bytes];
-    __shared__ uint8_t hh[3][32];  // Hash_prefix(4, pk), Hash_prefix(3, r_enc), ss
-    const int it = blockIdx.x;
-    if (it >= n) return;
-    const int tid = threadIdx.x;
+// Items per CTA: a CTA runs the arithmetic of its items one after another
+// with all its threads, then warp 0 computes their hashes, one lane per item
+// (SHA-512 is a serial chain per message, so a lone thread per item would
+// leave the CTA waiting; 32 lanes hash 32 items for the instructions of one).
+// Small launches keep one item per CTA for latency.
+constexpr int KEM_MAX_IPC = 32;
+inline int kem_items_per_cta(int n, int sms) {
+    const int ipc = n / (8 * sms);
+    return ipc < 1 ? 1 : (ipc > KEM_MAX_IPC ? KEM_MAX_IPC : ipc);
+}
+
+__device__ __forceinline__ EncItem enc_item(const EncMap &em, int it, int pk_bytes, int ct_bytes) {
     EncItem item;
     if (em.tab) {
         item = em.tab[it];
@@ -57,70 +52,113 @@ k_encap(EncMap em, int n, int pk_bytes, int ct_bytes, EncSched Spk, EncSched Sct
         item.ct = em.ct + (size_t)it * ct_bytes;
         item.ss = em.ss + (size_t)it * 32;
     }
-    for (int b = tid; b < pk_bytes; b += KEM_THREADS) pkb[b] = item.pk[b];
-    __syncthreads();
-    const int cur = mixed_decode<G::pad>(pkb, Spk, R);
-    for (int i = tid; i < G::pad; i += KEM_THREADS) hs[i] = (i < P) ? (int)R[cur][i] - G::half : 0;
-    __syncthreads();
-    fill_E<P, int>(hs, Es);
-    uint32_t v[4];
-    short_sorted_words<P>(em.seed, item.k, STREAM_ENC, v, xs);
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int j = 4 * tid + r;
-        if (j < Tp<P>::p8) As[j] = (j < P) ? (int)(v[r] & 3u) - 1 : 0;
-    }
-    if (tid < G::small_bytes) {
-        uint32_t byte = 0;
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-            if (4 * tid + r < P) byte |= (v[r] & 3u) << (2 * r);
-        renc[tid] = (uint8_t)byte;
-    }
-    __syncthreads();
-    // c = Round(h r)
-    int acc[1][8];
-    const int *const A1[1] = {As};
-    toeplitz_split<P, 1, KEM_SPLIT>(A1, Es, part, acc);
-    const int tloc = tid % NT;
-    const bool active = tid < NT;
-    const int bl[1] = {hs[P - 1]};
-    toeplitz_finish<P, 1>(A1, bl, acc, tloc, active);
-    if (active) {
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int j = 8 * tloc + t;
-            if (j < P) {
-                const int c = acc[0][t] - cmod<3>(acc[0][t]);
-                R[0][j] = (uint32_t)((c + G::half) / 3);
-            }
-        }
-    }
-    __syncthreads();
-    mixed_encode<G::pad>(R, Sct, ctb);
-    const int rb = ct_bytes - 32;
-    if (tid == 0) {
-        if (item.cache)
-            for (int b = 0; b < 32; ++b) hh[0][b] = item.cache[b];
-        else
-            sha512_prefixed(4, pkb, pk_bytes, nullptr, 0, hh[0]);
-    }
-    if (tid == 32) sha512_prefixed(3, renc, G::small_bytes, nullptr, 0, hh[1]);
-    __syncthreads();
-    if (tid == 0) {
-        sha512_prefixed(2, hh[1], 32, hh[0], 32, ctb + rb);
-        sha512_prefixed(1, hh[1], 32, ctb, ct_bytes, hh[2]);
-    }
-    __syncthreads();
-    for (int b = tid; b < ct_bytes; b += KEM_THREADS) item.ct[b] = ctb[b];
-    if (tid < 32) item.ss[tid] = hh[2][tid];
+    return item;
 }
 
 template <int P>
 __global__ void __launch_bounds__(KEM_THREADS, 4)
-k_decap(DecMap dm, int n, int pk_bytes, int sk_bytes, int ct_bytes, EncSched Spk, EncSched Sct) {
+k_encap(EncMap em, int n, int ipc, int pk_bytes, int ct_bytes, EncSched Spk, EncSched Sct) {
     using G = Geo<P>;
-    constexpr int NT = Tp<P>::NT, Q = G::q;
+    constexpr int NT = Tp<P>::NT;
+    __shared__ __align__(16) uint8_t pkb[1344];
+    __shared__ __align__(16) uint8_t ctb[1216];
+    __shared__ __align__(16) int As[Tp<P>::p8];
+    __shared__ __align__(16) int Es[Tp<P>::ESZ];
+    __shared__ int part[(KEM_SPLIT - 1) * Tp<P>::p8];
+    __shared__ uint32_t R[2][G::pad];
+    __shared__ __align__(16) uint32_t xs[1024];
+    __shared__ int hs[G::pad];
+    __shared__ uint8_t renc[KEM_MAX_IPC][G::small_bytes];
+    const int first = blockIdx.x * ipc;
+    const int cnt = min(ipc, n - first);
+    if (cnt <= 0) return;
+    const int tid = threadIdx.x;
+    const int rb = ct_bytes - 32;
+    for (int r = 0; r < cnt; ++r) {
+        const EncItem item = enc_item(em, first + r, pk_bytes, ct_bytes);
+        for (int b = tid; b < pk_bytes; b += KEM_THREADS) pkb[b] = item.pk[b];
+        __syncthreads();
+        const int cur = mixed_decode<G::pad>(pkb, Spk, R);
+        for (int i = tid; i < G::pad; i += KEM_THREADS) hs[i] = (i < P) ? (int)R[cur][i] - G::half : 0;
+        __syncthreads();
+        fill_E<P, int>(hs, Es);
+        uint32_t v[4];
+        short_sorted_words<P>(em.seed, item.k, STREAM_ENC, v, xs);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = 4 * tid + q;
+            if (j < Tp<P>::p8) As[j] = (j < P) ? (int)(v[q] & 3u) - 1 : 0;
+        }
+        if (tid < G::small_bytes) {
+            uint32_t byte = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (4 * tid + q < P) byte |= (v[q] & 3u) << (2 * q);
+            renc[r][tid] = (uint8_t)byte;
+        }
+        __syncthreads();
+        // c = Round(h r)
+        int acc[1][8];
+        const int *const A1[1] = {As};
+        toeplitz_split<P, 1, KEM_SPLIT>(A1, Es, part, acc);
+        const int tloc = tid % NT;
+        const bool active = tid < NT;
+        const int bl[1] = {hs[P - 1]};
+        toeplitz_finish<P, 1>(A1, bl, acc, tloc, active);
+        if (active) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int j = 8 * tloc + t;
+                if (j < P) {
+                    const int c = acc[0][t] - cmod<3>(acc[0][t]);
+                    R[0][j] = (uint32_t)((c + G::half) / 3);
+                }
+            }
+        }
+        __syncthreads();
+        mixed_encode<G::pad>(R, Sct, ctb);
+        // the rounded encoding now; its confirmation hash below
+        for (int b = tid; b < rb; b += KEM_THREADS) item.ct[b] = ctb[b];
+        __syncthreads();  // buffers free for the next item; ct visible to warp 0
+    }
+    // hashes, lane r for item r:
+    //   h3 = Hash_prefix(3, r_enc); h4 = Hash_prefix(4, pk) (or the cached copy);
+    //   ct = C | Hash_prefix(2, h3 | h4); ss = Hash_prefix(1, h3 | ct)
+    // (each lane reads back only its own item's ct, written before by the
+    // CTA behind the barrier above or by the lane itself)
+    if (tid >= cnt) return;
+    const EncItem item = enc_item(em, first + tid, pk_bytes, ct_bytes);
+    uint8_t h3[32], h4[32], conf[32], ss[32];
+    if (item.cache) {
+        for (int b = 0; b < 32; ++b) h4[b] = item.cache[b];
+    } else {
+        sha512_prefixed(4, item.pk, pk_bytes, nullptr, 0, h4);
+    }
+    sha512_prefixed(3, renc[tid], G::small_bytes, nullptr, 0, h3);
+    sha512_prefixed(2, h3, 32, h4, 32, conf);
+    for (int b = 0; b < 32; ++b) item.ct[rb + b] = conf[b];
+    sha512_prefixed(1, h3, 32, item.ct, ct_bytes, ss);
+    for (int b = 0; b < 32; ++b) item.ss[b] = ss[b];
+}
+
+__device__ __forceinline__ DecItem dec_item(const DecMap &dm, int it, int sk_bytes, int ct_bytes) {
+    DecItem item;
+    if (dm.tab) {
+        item = dm.tab[it];
+    } else {
+        item.sk = dm.sk + (size_t)it * sk_bytes;
+        item.ct = dm.ct + (size_t)it * ct_bytes;
+        item.ss = dm.ss + (size_t)it * 32;
+    }
+    return item;
+}
+
+template <int P>
+__global__ void __launch_bounds__(KEM_THREADS, 4)
+k_decap(DecMap dm, int n, int ipc, int pk_bytes, int sk_bytes, int ct_bytes, EncSched Spk,
+        EncSched Sct) {
+    using G = Geo<P>;
+    constexpr int NT = Tp<P>::NT;
     constexpr int SB = G::small_bytes;
     __shared__ __align__(16) uint8_t skb[2016];
     __shared__ __align__(16) uint8_t ctb[1216];
@@ -132,137 +170,161 @@ k_decap(DecMap dm, int n, int pk_bytes, int sk_bytes, int ct_bytes, EncSched Spk
     __shared__ int hs[G::pad];
     __shared__ int8_t vv[G::pad];
     __shared__ int8_t rr[G::pad];
-    __shared__ uint8_t renc[SB];
-    __shared__ uint8_t hh[4][32];  // h3(r'), h3(rho), selected, ss
+    __shared__ uint8_t renc[KEM_MAX_IPC][SB];
+    __shared__ int cmatch[KEM_MAX_IPC];  // the re-encryption's rounded part equals ct's
     __shared__ int weight;
-    const int it = blockIdx.x;
-    if (it >= n) return;
+    const int first = blockIdx.x * ipc;
+    const int cnt = min(ipc, n - first);
+    if (cnt <= 0) return;
     const int tid = threadIdx.x;
-    DecItem item;
-    if (dm.tab) {
-        item = dm.tab[it];
-    } else {
-        item.sk = dm.sk + (size_t)it * sk_bytes;
-        item.ct = dm.ct + (size_t)it * ct_bytes;
-        item.ss = dm.ss + (size_t)it * 32;
-    }
-    for (int b = tid; b < sk_bytes; b += KEM_THREADS) skb[b] = item.sk[b];
-    for (int b = tid; b < ct_bytes; b += KEM_THREADS) ctb[b] = item.ct[b];
-    if (tid == 0) weight = 0;
-    __syncthreads();
-    const uint8_t *pkb = skb + 2 * SB, *rho = skb + 2 * SB + pk_bytes,
-                  *cache = skb + 3 * SB + pk_bytes;
-    // c = Rounded_decode(C); a = 3f; v
-    int cur = mixed_decode<G::pad>(ctb, Sct, R);
-    for (int i = tid; i < G::pad; i += KEM_THREADS) {
-        hs[i] = (i < P) ? 3 * (int)R[cur][i] - G::half : 0;
-        vv[i] = (int8_t)((i < P) ? (int)((skb[SB + i / 4] >> (2 * (i % 4))) & 3u) - 1 : 0);
-    }
-    for (int i = tid; i < Tp<P>::p8; i += KEM_THREADS)
-        As[i] = (i < P) ? 3 * ((int)((skb[i / 4] >> (2 * (i % 4))) & 3u) - 1) : 0;
-    __syncthreads();
-    fill_E<P, int>(hs, Es);
-    __syncthreads();
-    const int tloc = tid % NT;
-    const bool active = tid < NT;
-    int acc[1][8];
-    const int *const A1[1] = {As};
-    {   // e = 3 f c in R/q, then mod 3
-        toeplitz_split<P, 1, KEM_SPLIT>(A1, Es, part, acc);
-        const int bl[1] = {hs[P - 1]};
-        toeplitz_finish<P, 1>(A1, bl, acc, tloc, active);
-    }
-    __syncthreads();  // all reads of As / Es done
-    if (active) {
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int j = 8 * tloc + t;
-            if (j < Tp<P>::p8) As[j] = (j < P) ? cmod<3>(acc[0][t]) : 0;
-        }
-    }
-    fill_E<P, int8_t, 3>(vv, Es);
-    __syncthreads();
-    {   // r' = e v in R/3
-        toeplitz_split<P, 1, KEM_SPLIT, 3>(A1, Es, part, acc);
-        const int bl[1] = {(int)vv[P - 1]};
-        toeplitz_finish<P, 1, 3>(A1, bl, acc, tloc, active);
-    }
-    if (active) {
-        int cnt = 0;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int j = 8 * tloc + t;
-            if (j < P) {
-                rr[j] = (int8_t)acc[0][t];
-                cnt += (acc[0][t] != 0);
-            }
-        }
-        atomicAdd(&weight, cnt);
-    }
-    __syncthreads();
-    const bool wok = (weight == G::w);
-    for (int j = tid; j < G::pad; j += KEM_THREADS) {
-        const int8_t dflt = (int8_t)(j < G::w ? 1 : 0);
-        rr[j] = (j < P) ? (wok ? rr[j] : dflt) : (int8_t)0;
-    }
-    __syncthreads();
-    // re-encrypt r': h from pk, c' = Round(h r')
-    cur = mixed_decode<G::pad>(pkb, Spk, R);
-    for (int i = tid; i < G::pad; i += KEM_THREADS) hs[i] = (i < P) ? (int)R[cur][i] - G::half : 0;
-    for (int i = tid; i < Tp<P>::p8; i += KEM_THREADS) As[i] = (i < P) ? (int)rr[i] : 0;
-    for (int b = tid; b < SB; b += KEM_THREADS) {
-        uint32_t byte = 0;
-        for (int r = 0; r < 4; ++r)
-            if (4 * b + r < P) byte |= (uint32_t)(rr[4 * b + r] + 1) << (2 * r);
-        renc[b] = (uint8_t)byte;
-    }
-    __syncthreads();
-    fill_E<P, int>(hs, Es);
-    __syncthreads();
-    {
-        toeplitz_split<P, 1, KEM_SPLIT>(A1, Es, part, acc);
-        const int bl[1] = {hs[P - 1]};
-        toeplitz_finish<P, 1>(A1, bl, acc, tloc, active);
-    }
-    if (active) {
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int j = 8 * tloc + t;
-            if (j < P) {
-                const int c = acc[0][t] - cmod<3>(acc[0][t]);
-                R[0][j] = (uint32_t)((c + G::half) / 3);
-            }
-        }
-    }
-    __syncthreads();
-    mixed_encode<G::pad>(R, Sct, ct2);
     const int rb = ct_bytes - 32;
-    if (tid == 0) sha512_prefixed(3, renc, SB, nullptr, 0, hh[0]);
-    if (tid == 32) sha512_prefixed(3, rho, SB, nullptr, 0, hh[1]);
-    __syncthreads();
-    if (tid == 0) sha512_prefixed(2, hh[0], 32, cache, 32, ct2 + rb);
-    __syncthreads();
-    uint32_t diff = 0;
-    for (int b = tid; b < ct_bytes; b += KEM_THREADS) diff |= (uint32_t)(ct2[b] ^ ctb[b]);
-    const bool accept = __syncthreads_or(diff != 0) == 0;
-    if (tid < 32) hh[2][tid] = accept ? hh[0][tid] : hh[1][tid];
-    __syncthreads();
-    if (tid == 0) sha512_prefixed(accept ? 1 : 0, hh[2], 32, ctb, ct_bytes, hh[3]);
-    __syncthreads();
-    if (tid < 32) item.ss[tid] = hh[3][tid];
+    for (int it_r = 0; it_r < cnt; ++it_r) {
+        const DecItem item = dec_item(dm, first + it_r, sk_bytes, ct_bytes);
+        for (int b = tid; b < sk_bytes; b += KEM_THREADS) skb[b] = item.sk[b];
+        for (int b = tid; b < ct_bytes; b += KEM_THREADS) ctb[b] = item.ct[b];
+        if (tid == 0) weight = 0;
+        __syncthreads();
+        const uint8_t *pkb = skb + 2 * SB;
+        // c = Rounded_decode(C); a = 3f; v
+        int cur = mixed_decode<G::pad>(ctb, Sct, R);
+        for (int i = tid; i < G::pad; i += KEM_THREADS) {
+            hs[i] = (i < P) ? 3 * (int)R[cur][i] - G::half : 0;
+            vv[i] = (int8_t)((i < P) ? (int)((skb[SB + i / 4] >> (2 * (i % 4))) & 3u) - 1 : 0);
+        }
+        for (int i = tid; i < Tp<P>::p8; i += KEM_THREADS)
+            As[i] = (i < P) ? 3 * ((int)((skb[i / 4] >> (2 * (i % 4))) & 3u) - 1) : 0;
+        __syncthreads();
+        fill_E<P, int>(hs, Es);
+        __syncthreads();
+        const int tloc = tid % NT;
+        const bool active = tid < NT;
+        int acc[1][8];
+        const int *const A1[1] = {As};
+        {   // e = 3 f c in R/q, then mod 3
+            toeplitz_split<P, 1, KEM_SPLIT>(A1, Es, part, acc);
+            const int bl[1] = {hs[P - 1]};
+            toeplitz_finish<P, 1>(A1, bl, acc, tloc, active);
+        }
+        __syncthreads();  // all reads of As / Es done
+        if (active) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int j = 8 * tloc + t;
+                if (j < Tp<P>::p8) As[j] = (j < P) ? cmod<3>(acc[0][t]) : 0;
+            }
+        }
+        fill_E<P, int8_t, 3>(vv, Es);
+        __syncthreads();
+        {   // r' = e v in R/3
+            toeplitz_split<P, 1, KEM_SPLIT, 3>(A1, Es, part, acc);
+            const int bl[1] = {(int)vv[P - 1]};
+            toeplitz_finish<P, 1, 3>(A1, bl, acc, tloc, active);
+        }
+        if (active) {
+            int cnt = 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int j = 8 * tloc + t;
+                if (j < P) {
+                    rr[j] = (int8_t)acc[0][t];
+                    cnt += (acc[0][t] != 0);
+                }
+            }
+            atomicAdd(&weight, cnt);
+        }
+        __syncthreads();
+        const bool wok = (weight == G::w);
+        for (int j = tid; j < G::pad; j += KEM_THREADS) {
+            const int8_t dflt = (int8_t)(j < G::w ? 1 : 0);
+            rr[j] = (j < P) ? (wok ? rr[j] : dflt) : (int8_t)0;
+        }
+        __syncthreads();
+        // re-encrypt r': h from pk, c' = Round(h r')
+        cur = mixed_decode<G::pad>(pkb, Spk, R);
+        for (int i = tid; i < G::pad; i += KEM_THREADS) hs[i] = (i < P) ? (int)R[cur][i] - G::half : 0;
+        for (int i = tid; i < Tp<P>::p8; i += KEM_THREADS) As[i] = (i < P) ? (int)rr[i] : 0;
+        for (int b = tid; b < SB; b += KEM_THREADS) {
+            uint32_t byte = 0;
+            for (int r = 0; r < 4; ++r)
+                if (4 * b + r < P) byte |= (uint32_t)(rr[4 * b + r] + 1) << (2 * r);
+            renc[it_r][b] = (uint8_t)byte;
+        }
+        __syncthreads();
+        fill_E<P, int>(hs, Es);
+        __syncthreads();
+        {
+            toeplitz_split<P, 1, KEM_SPLIT>(A1, Es, part, acc);
+            const int bl[1] = {hs[P - 1]};
+            toeplitz_finish<P, 1>(A1, bl, acc, tloc, active);
+        }
+        if (active) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int j = 8 * tloc + t;
+                if (j < P) {
+                    const int c = acc[0][t] - cmod<3>(acc[0][t]);
+                    R[0][j] = (uint32_t)((c + G::half) / 3);
+                }
+            }
+        }
+        __syncthreads();
+        mixed_encode<G::pad>(R, Sct, ct2);
+        uint32_t diff = 0;
+        for (int b = tid; b < rb; b += KEM_THREADS) diff |= (uint32_t)(ct2[b] ^ ctb[b]);
+        const int same = __syncthreads_or(diff != 0) == 0;
+        if (tid == 0) cmatch[it_r] = same;
+        __syncthreads();  // buffers free for the next item
+    }
+    // hashes, lane r for item r: h3 = Hash_prefix(3, r'_enc), h3rho =
+    // Hash_prefix(3, rho); the re-encryption's confirmation Hash_prefix(2, h3 |
+    // Hash_prefix(4, pk)) against ct's; ss = Hash_prefix(1, h3 | ct) if the
+    // re-encryption equals ct, else Hash_prefix(0, h3rho | ct) (selected
+    // without branches)
+    if (tid >= cnt) return;
+    const DecItem item = dec_item(dm, first + tid, sk_bytes, ct_bytes);
+    const uint8_t *rho = item.sk + 2 * SB + pk_bytes, *cache = item.sk + 3 * SB + pk_bytes;
+    uint8_t h3[32], h3rho[32], conf[32], sel[32], ss[32];
+    sha512_prefixed(3, renc[tid], SB, nullptr, 0, h3);
+    sha512_prefixed(3, rho, SB, nullptr, 0, h3rho);
+    sha512_prefixed(2, h3, 32, cache, 32, conf);
+    uint32_t cd = 0;
+    for (int b = 0; b < 32; ++b) cd |= (uint32_t)(conf[b] ^ item.ct[rb + b]);
+    const uint32_t accept = (uint32_t)(cmatch[tid] != 0) & (uint32_t)(cd == 0);
+    const uint32_t mask = 0u - accept;  // all ones if accepted
+    for (int b = 0; b < 32; ++b) sel[b] = (uint8_t)((h3[b] & mask) | (h3rho[b] & ~mask));
+    sha512_prefixed((uint8_t)accept, sel, 32, item.ct, ct_bytes, ss);
+    for (int b = 0; b < 32; ++b) item.ss[b] = ss[b];
+}
+
+// SMs of the current device (host state, read once per device).
+static int kem_sms() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cache[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 152;
+        cache[dev] = v;
+    }
+    return cache[dev];
 }
 
 template <int P>
 cudaError_t launch_encap(const EncMap &em, int n, int pk_bytes, int ct_bytes, const EncSched &Spk,
                          const EncSched &Sct, cudaStream_t st) {
-    k_encap<P><<<n, KEM_THREADS, 0, st>>>(em, n, pk_bytes, ct_bytes, Spk, Sct);
+    const int ipc = kem_items_per_cta(n, kem_sms());
+    k_encap<P><<<(n + ipc - 1) / ipc, KEM_THREADS, 0, st>>>(em, n, ipc, pk_bytes, ct_bytes, Spk,
+                                                           Sct);
     return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t launch_decap(const DecMap &dm, int n, int pk_bytes, int sk_bytes, int ct_bytes,
                          const EncSched &Spk, const EncSched &Sct, cudaStream_t st) {
-    k_decap<P><<<n, KEM_THREADS, 0, st>>>(dm, n, pk_bytes, sk_bytes, ct_bytes, Spk, Sct);
+    const int ipc = kem_items_per_cta(n, kem_sms());
+    k_decap<P><<<(n + ipc - 1) / ipc, KEM_THREADS, 0, st>>>(dm, n, ipc, pk_bytes, sk_bytes,
+                                                           ct_bytes, Spk, Sct);
     return cudaGetLastError();
 }
 
