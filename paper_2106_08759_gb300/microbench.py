@@ -32,7 +32,13 @@ def main():
                     help="only run batch keygen of B keys --reps times with the default "
                          "options (a small, fixed target for a profiler)")
     ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
-                    help="context option for --keygen-only, e.g. R3_MODE=1 (SNT_OPT_ prefix implied)")
+                    help="context option for --keygen-only / --ragged-only, e.g. R3_MODE=1 "
+                         "(SNT_OPT_ prefix implied)")
+    ap.add_argument("--ragged-only", type=int, default=0, metavar="N",
+                    help="only run the 256-batch ragged workload N times with the given options "
+                         "(a small, fixed target for a profiler)")
+    ap.add_argument("--kem-only", type=int, default=0, metavar="N",
+                    help="only run N encapsulations and decapsulations of sntrup761 keys, twice")
     args = ap.parse_args()
 
     import numpy as np
@@ -65,6 +71,45 @@ def main():
     def t(x, dt):
         return torch.from_numpy(np.ascontiguousarray(x)).to(dtype=dt, device=dev)
 
+    if args.ragged_only:
+        from synth import ragged_batches
+        sizes, ps = ragged_batches(256, 2048, 42)
+        pks, sks = [], []
+        for P_, B_ in zip(ps, sizes):
+            pkb_, skb_, _, _ = snt.snt_param_sizes(int(P_))
+            pks.append(torch.empty(int(B_) * pkb_, dtype=torch.uint8, device=dev))
+            sks.append(torch.empty(int(B_) * skb_, dtype=torch.uint8, device=dev))
+        firsts = [int(x) for x in np.cumsum([0] + list(sizes[:-1]))]
+        with snt.Context(0, 1 << 30) as rc:
+            for o in args.opt:
+                name, val = o.split("=")
+                rc.set_option(getattr(snt, "SNT_OPT_" + name), int(val))
+            for it in range(args.ragged_only):
+                snt.snt_batch_keygen_ragged(rc, [int(x) for x in ps], [int(x) for x in sizes],
+                                            [it * 1000 + i for i in range(256)], firsts, pks, sks)
+            rc.sync()
+        print(json.dumps({"ragged_only": args.ragged_only, "keys": int(sizes.sum())}))
+        ctx.close()
+        return
+    if args.kem_only:
+        n = args.kem_only
+        pkb, skb, ctb, _ = snt.snt_param_sizes(P)
+        pk = torch.empty(n * pkb, dtype=torch.uint8, device=dev)
+        sk = torch.empty(n * skb, dtype=torch.uint8, device=dev)
+        for i in range(0, n, 4096):
+            m = min(4096, n - i)
+            snt.snt_batch_keygen(ctx, P, 3, i, m, pk[i * pkb:(i + m) * pkb],
+                                 sk[i * skb:(i + m) * skb])
+        ct = torch.empty(n * ctb, dtype=torch.uint8, device=dev)
+        ss = torch.empty(n * 32, dtype=torch.uint8, device=dev)
+        ss2 = torch.empty(n * 32, dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            snt.snt_enc(ctx, P, n, pk, 5, 0, ct, ss)
+            snt.snt_dec(ctx, P, n, sk, ct, ss2)
+        ctx.sync()
+        print(json.dumps({"kem_only": n, "dec_matches_enc": bool(torch.equal(ss, ss2))}))
+        ctx.close()
+        return
     if args.keygen_only:
         for o in args.opt:
             name, val = o.split("=")
