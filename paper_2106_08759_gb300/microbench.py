@@ -39,6 +39,11 @@ def main():
                          "(a small, fixed target for a profiler)")
     ap.add_argument("--kem-only", type=int, default=0, metavar="N",
                     help="only run N encapsulations and decapsulations of sntrup761 keys, twice")
+    ap.add_argument("--mul-only", type=int, default=0, metavar="N",
+                    help="only run N general R/q products twice with the given options "
+                         "(e.g. RQ_ENGINE=2)")
+    ap.add_argument("--tc05-only", type=int, default=0, metavar="NCOLS",
+                    help="only run the tcgen05.mma rate measurement at N = NCOLS")
     args = ap.parse_args()
 
     import numpy as np
@@ -89,6 +94,25 @@ def main():
                                             [it * 1000 + i for i in range(256)], firsts, pks, sks)
             rc.sync()
         print(json.dumps({"ragged_only": args.ragged_only, "keys": int(sizes.sum())}))
+        ctx.close()
+        return
+    if args.tc05_only:
+        rate, sms = snt.snt_measure_tc05(0, args.tc05_only)
+        print(json.dumps({"tc05_n": args.tc05_only, "tmacs": rate / 1e12, "sms": sms}))
+        ctx.close()
+        return
+    if args.mul_only:
+        for o in args.opt:
+            name, val = o.split("=")
+            ctx.set_option(getattr(snt, "SNT_OPT_" + name), int(val))
+        n = args.mul_only
+        A = t(rq_uniform(P, n, 1).ravel(), torch.int16)
+        Bm = t(rq_uniform(P, n, 2).ravel(), torch.int16)
+        C = torch.empty(n * p, dtype=torch.int16, device=dev)
+        for _ in range(2):
+            snt.snt_rq_mul(ctx, P, n, A, Bm, C)
+        torch.cuda.synchronize()
+        print(json.dumps({"mul_only": n}))
         ctx.close()
         return
     if args.kem_only:
