@@ -292,7 +292,11 @@ typedef enum {
      * transforms over K = (Z/q)[x]/(x^64 + 1) whose twiddles are powers of x
      * (shifts and negations), 48 pointwise products in K for p <= 768 (64 for
      * sntrup857) on the IMAD pipe, for the tree's general x general levels
-     * (its leaf levels and h stay on the tensor cores) and snt_rq_mul */
+     * (its leaf levels and h stay on the tensor cores) and snt_rq_mul; 3 the
+     * tensor cores with one limb on the vector side of the general products:
+     * each residue taken as its representative exact in f16 (an odd residue
+     * above 2048 in magnitude moved by q), two MMAs per step instead of four,
+     * the f32 partial sums moved into int32 sums every 8 steps */
     SNT_OPT_RQ_ENGINE = 5,
     /* tensor-core engine: MMA tiles (128 outputs each) per warp, 1, 2 or 3;
      * a product's tiles are spread over the warps of one CTA */
@@ -351,7 +355,8 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
  * same P and ceil(log2 B) (and for the ragged call's parameter sets whose
  * largest batch falls in that bucket); it overrides the snt_ctx_set_option
  * values there.  Candidates: R/3 lanes (4, 8, 32) x R/3 overlap (0, 1, 2) x
- * { tensor-core engine with 1 or 2 MMA tiles per warp, forests of 1, 4, 16,
+ * { tensor-core engine (1, and each of its candidates again as 3) with 1 or
+ * 2 MMA tiles per warp, forests of 1, 4, 16,
  * 64, 128 or 256 subtrees (SNT_OPT_ROOTS) and R/3 mode 0, 1 or 2; CUDA-core
  * Toeplitz engine with tree split 4 or 8; transform multiplier (engine 2)
  * with forests of 1, 16, 64 or 128 subtrees and R/3 mode 0 or 2; the

@@ -105,8 +105,10 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         r3mode = tu.r3mode; parts = tu.parts;
     }
     // engine 2: the general x general levels by the transform multiplier,
-    // the small-operand levels (leaves) and h on the tensor cores
-    const bool mma = engine != 0, ntt = engine == 2;
+    // the small-operand levels (leaves) and h on the tensor cores; engine 3:
+    // the tensor cores with one exact f16 limb on the vector side of the
+    // general levels
+    const bool mma = engine != 0, ntt = engine == 2, wide = engine == 3;
     // R/3 batch inversion (the per-key path keeps per-key divsteps):
     //   mode 1 (Sec. 3.1.1): isInvertible per key (redrawing g until it is),
     //          then one Montgomery forest in R/3; h waits for the final g's;
@@ -241,7 +243,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                     else
                         SNT_CUDA(launch_tree_up_mma<P>(nodes + rows(l - 1, q) * pi.pad, lmap(l), nq,
                                                        nodes + rows(l, q) * pi.pad, sq, mma_tiles,
-                                                       l == 1, ctx->mma_ksplit));
+                                                       l == 1, ctx->mma_ksplit, wide));
                 }
                 if (q == 0 && !forked) {
                     const snt_status s3 = fork_r3();
@@ -270,7 +272,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                     else
                         SNT_CUDA(launch_tree_down_mma<P>(nodes + rows(l, q) * pi.pad, lmap(l), nq,
                                                          nodes + rows(l - 1, q) * pi.pad, sq,
-                                                         mma_tiles, l == 1, ctx->mma_ksplit));
+                                                         mma_tiles, l == 1, ctx->mma_ksplit, wide));
                 }
                 if (tm && q == 0) SNT_CUDA(cudaEventRecord(ev[6], sq));
                 if (r3chk && !joined) SNT_CUDA(cudaStreamWaitEvent(sq, ctx->ev_gready, 0));
@@ -322,7 +324,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                 SNT_CUDA(launch_tree_up_mma<P>(nodes + (size_t)t.off[l - 1] * pi.pad,
                                                lmap(l), t.n[l],
                                                nodes + (size_t)t.off[l] * pi.pad, st, mma_tiles,
-                                               l == 1, ctx->mma_ksplit));
+                                               l == 1, ctx->mma_ksplit, wide));
             else if (narrow && t.n[l] <= kSegMaxNodes)
                 SNT_CUDA(launch_tree_up_seg<P>(nodes + (size_t)t.off[l - 1] * pi.pad,
                                                lmap(l), t.n[l],
@@ -361,7 +363,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                 par = lch;
             } else if (mma) {  // in place on every level
                 SNT_CUDA(launch_tree_down_mma<P>(par, lmap(l), t.n[l], lch, st,
-                                                 mma_tiles, l == 1, ctx->mma_ksplit));
+                                                 mma_tiles, l == 1, ctx->mma_ksplit, wide));
                 par = lch;
             } else if (narrow && t.n[l] <= kSegMaxNodes) {
                 int16_t *out = pp[ping];
@@ -682,13 +684,13 @@ snt_status snt_rq_mul(snt_ctx *ctx, int P, size_t n, const int16_t *a_dev, const
     const int eng = ctx->rq_engine;
     switch (P) {
         case 653: SNT_CUDA(eng == 2 ? launch_mul_batch_ntt<653>((int)n, a_dev, b_dev, c_dev, st)
-                           : eng == 1 ? launch_mul_batch_mma<653>((int)n, a_dev, b_dev, c_dev, st)
+                           : eng != 0 ? launch_mul_batch_mma<653>((int)n, a_dev, b_dev, c_dev, st, eng == 3)
                                       : launch_mul_batch<653>((int)n, a_dev, b_dev, c_dev, st)); break;
         case 761: SNT_CUDA(eng == 2 ? launch_mul_batch_ntt<761>((int)n, a_dev, b_dev, c_dev, st)
-                           : eng == 1 ? launch_mul_batch_mma<761>((int)n, a_dev, b_dev, c_dev, st)
+                           : eng != 0 ? launch_mul_batch_mma<761>((int)n, a_dev, b_dev, c_dev, st, eng == 3)
                                       : launch_mul_batch<761>((int)n, a_dev, b_dev, c_dev, st)); break;
         case 857: SNT_CUDA(eng == 2 ? launch_mul_batch_ntt<857>((int)n, a_dev, b_dev, c_dev, st)
-                           : eng == 1 ? launch_mul_batch_mma<857>((int)n, a_dev, b_dev, c_dev, st)
+                           : eng != 0 ? launch_mul_batch_mma<857>((int)n, a_dev, b_dev, c_dev, st, eng == 3)
                                       : launch_mul_batch<857>((int)n, a_dev, b_dev, c_dev, st)); break;
         default: return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     }
@@ -785,7 +787,7 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             ctx->narrow_seg = value;
             return SNT_OK;
         case SNT_OPT_RQ_ENGINE:
-            if (value < 0 || value > 2) return set_error(SNT_EINVAL, "R/q engine is 0, 1 or 2");
+            if (value < 0 || value > 3) return set_error(SNT_EINVAL, "R/q engine is 0, 1, 2 or 3");
             ctx->rq_engine = value;
             return SNT_OK;
         case SNT_OPT_MMA_TILES:
@@ -905,6 +907,14 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
                             cands.push_back(c);
                         }
             }
+        }
+    // every tensor-core candidate also with one wide limb on the vector side
+    const size_t ncand = cands.size();
+    for (size_t i = 0; i < ncand; ++i)
+        if (cands[i].engine == 1) {
+            snt_ctx::Tuned c = cands[i];
+            c.engine = 3;
+            cands.push_back(c);
         }
     snt_ctx::Tuned best;
     float best_ms = 1e30f;

@@ -158,10 +158,12 @@ cudaError_t launch_mul_batch(int n, const int16_t *a, const int16_t *b, int16_t 
 // (64) products split each product's sum over 2 (4) warps, up to kmax.
 template <int P>
 cudaError_t launch_tree_up_mma(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
-                               cudaStream_t st, int tiles, bool leaves, int kmax = 4);
+                               cudaStream_t st, int tiles, bool leaves, int kmax = 4,
+                               bool wide = false);
 template <int P>
 cudaError_t launch_tree_down_mma(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t *lch,
-                                 cudaStream_t st, int tiles, bool leaves, int kmax = 4);
+                                 cudaStream_t st, int tiles, bool leaves, int kmax = 4,
+                                 bool wide = false);
 // R/3 trees for the batch inversion of the g's (coefficients mod 3).
 template <int P>
 cudaError_t launch_tree_up_mma3(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lout,
@@ -171,7 +173,7 @@ cudaError_t launch_tree_down_mma3(const int16_t *lpar, const LevelMap &lm, int n
                                   cudaStream_t st, int kmax);
 template <int P>
 cudaError_t launch_mul_batch_mma(int n, const int16_t *a, const int16_t *b, int16_t *c,
-                                 cudaStream_t st);
+                                 cudaStream_t st, bool wide = false);
 // R/q products by the paper's multiplier (Sec. 3.3): truncated transforms
 // over K = (Z/q)[x]/(x^64 + 1) with x as the root of unity, pointwise products
 // in K on the IMAD pipe (rqntt.cu).  Same layouts as the other engines.

@@ -40,6 +40,16 @@
 // takes a step from 20 wavefronts and 12 tensor-pipe cycles (two products
 // per CTA) to 12 wavefronts and 16 cycles.
 //
+// One wide limb on the vector side (MODE_GW).  Every residue mod q has a
+// representative that f16 holds exactly: the integers up to 2048 and the
+// even ones up to 4096; an odd residue above 2048 in magnitude moves by q
+// (odd) to an even value of magnitude at most q - 2049 (3118 for sntrup857).  With that
+// value as the vector side's only limb, P_1 = sum h_E b' and P_2 = sum l_E b'
+// need two MMAs per step (row = 64 P_1 + P_2), but a term now reaches
+// 40 * 3118, so the f32 sums are exact only over 128 terms (8 steps:
+// 128 * 40 * 3118 < 2^24): every 8 steps they are converted (exactly) and
+// added into int32 sums.
+//
 // Small operands.  A leaf of the tree is 3f with coefficients in {-3, 0, 3}:
 // its high limb is zero.  MODE_SA (vector side small) needs only
 // P_1 = sum h_E l_a and P_2 = sum l_E l_a (row = 64 P_1 + P_2, two MMAs);
@@ -51,7 +61,10 @@
 
 namespace snt {
 
-enum : int { MODE_GEN = 0, MODE_SA = 1, MODE_SAE = 2 };
+enum : int { MODE_GEN = 0, MODE_SA = 1, MODE_SAE = 2, MODE_GW = 3 };
+
+// Steps between the f32-to-int32 conversions of MODE_GW.
+constexpr int kGwFlush = 8;
 
 template <int P, int NT> struct MmaGeo {
     static constexpr int p = Prm<P>::p, q = Prm<P>::q;
@@ -126,6 +139,20 @@ template <int P, int Q = Prm<P>::q> __device__ __forceinline__ int mma_E(const i
     return v;
 }
 
+// f16x2 of two integers exact in f16: |x| <= 2048, or x even and |x| <= 4096.
+__device__ __forceinline__ uint32_t h2_int(int lo, int hi) {
+    const __half2 h = __halves2half2(__int2half_rn(lo), __int2half_rn(hi));
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// A representative of the centred residue x (|x| <= (Q-1)/2) exact in f16:
+// x itself unless x is odd and |x| > 2048, then x -+ Q (even, |.| <= Q - 2049).
+template <int Q> __device__ __forceinline__ int f16_rep(int x) {
+    static_assert(Q % 2 == 1 && Q - 2049 <= 4096, "representative must be exact in f16");
+    const bool move = (x & 1) && (x > 2048 || x < -2048);
+    return move ? (x > 0 ? x - Q : x + Q) : x;
+}
+
 // Vector side: a (global, centred int16 or int8, first p entries) into
 // shared memory, threads tid = 0 .. nth-1 of the group.
 template <int P, int NT, int MODE = MODE_GEN, typename T = int16_t>
@@ -143,7 +170,11 @@ __device__ __forceinline__ void mma_fill_a(const T *__restrict__ a, MmaA<P, NT> 
                 s.a[k] = (int16_t)v[u];
             }
         }
-        if constexpr (MODE != MODE_GEN) {  // small coefficients: the value is its own l limb
+        if constexpr (MODE == MODE_GW) {  // one wide limb: a representative exact in f16
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = f16_rep<Prm<P>::q>(v[u]);
+            s.u.sl[r] = make_uint2(h2_int(v[0], v[1]), h2_int(v[2], v[3]));
+        } else if constexpr (MODE != MODE_GEN) {  // small coefficients: the value is its own l limb
             s.u.sl[r] = make_uint2(h2_small(v[0], v[1]), h2_small(v[2], v[3]));
         } else {
             int h[4], l[4];
@@ -155,11 +186,6 @@ __device__ __forceinline__ void mma_fill_a(const T *__restrict__ a, MmaA<P, NT> 
     }
 }
 
-// f16x2 of two integers |lo|, |hi| <= 2048 (exact conversions).
-__device__ __forceinline__ uint32_t h2_int(int lo, int hi) {
-    const __half2 h = __halves2half2(__int2half_rn(lo), __int2half_rn(hi));
-    return *reinterpret_cast<const uint32_t *>(&h);
-}
 
 // Vector side with one limb of magnitude up to 2048 (a product of two small
 // elements), from int16 in any memory: the MODE_SA records with the value
@@ -279,6 +305,108 @@ __device__ __forceinline__ void mma_tiles(const MmaE<P, NT> &E, const MmaA<P, NT
             }
         A2 = A1;
     }
+}
+
+// MODE_GW: tiles [T0, T0 + NT) of NPR products sharing one E side, by one
+// warp, into int32 sums P_1 = sum h_E b', P_2 = sum l_E b' (f32 partial sums
+// over kGwFlush steps, converted exactly).  ks / nks as for mma_tiles.
+template <int P, int NT, int NPR>
+__device__ __forceinline__ void mma_tiles_gw(const MmaE<P, NT> &E, const MmaA<P, NT> *const (&A)[NPR],
+                                             int T0, int lane, int (&iacc)[NT][NPR][2][4], int ks = 0,
+                                             int nks = 1) {
+    using M = MmaGeo<P, NT>;
+    const int g = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int tt = 0; tt < NT; ++tt)
+#pragma unroll
+        for (int pr = 0; pr < NPR; ++pr)
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) iacc[tt][pr][m][c] = 0;
+    const int dall = 8 * T0 - (M::NBLK - 1);
+    const int dn = 8 * (NT - 1) + 7 + M::NBLK;
+    const int part = (dn + nks - 1) / nks;
+    const int dlo = dall + ks * part;
+    const int dhi = min(dall + dn, dlo + part) - 1;
+    const int x0 = 16 * dlo + g - 2 * tig + M::p - 1 - M::XLO;
+    int rec = 4 * (8 * T0 + g - dlo + M::PADB) + tig;
+    const uint2 *pe = E.t.pe + x0;
+    uint2 A2 = pe[-8];
+    for (int d0 = dlo; d0 <= dhi; d0 += kGwFlush) {
+        float acc[NT][NPR][2][4];
+#pragma unroll
+        for (int tt = 0; tt < NT; ++tt)
+#pragma unroll
+            for (int pr = 0; pr < NPR; ++pr)
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[tt][pr][m][c] = 0.f;
+        const int d1 = min(d0 + kGwFlush - 1, dhi);
+#pragma unroll 2
+        for (int D = d0; D <= d1; ++D, pe += 16, rec -= 4) {
+            const uint2 A0 = pe[0], A1 = pe[8];
+#pragma unroll
+            for (int tt = 0; tt < NT; ++tt)
+#pragma unroll
+                for (int pr = 0; pr < NPR; ++pr) {
+                    const uint2 b = A[pr]->u.sl[rec + 32 * tt];
+                    mma16816(acc[tt][pr][0], A0.x, A1.x, A2.x, A0.x, b.x, b.y);  // h_E b'
+                    mma16816(acc[tt][pr][1], A0.y, A1.y, A2.y, A0.y, b.x, b.y);  // l_E b'
+                }
+            A2 = A1;
+        }
+#pragma unroll
+        for (int tt = 0; tt < NT; ++tt)
+#pragma unroll
+            for (int pr = 0; pr < NPR; ++pr)
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) iacc[tt][pr][m][c] += __float2int_rn(acc[tt][pr][m][c]);
+    }
+}
+
+// K-split sum of MODE_GW's int32 sums (same layout of red as
+// mma_ksplit_reduce; 8 of its 12 words per tile and product).  Contains a
+// barrier: every thread of the CTA must call it.
+template <int NT, int NPR>
+__device__ __forceinline__ void mma_ksplit_reduce_gw(int (&iacc)[NT][NPR][2][4], int *red, int ks,
+                                                     int nks, int tw, int nw, int lane) {
+    constexpr int NV = NT * NPR * 8, NR = NT * NPR * 12;
+    int *flat = &iacc[0][0][0][0];
+    if (ks > 0) {
+        int *dst = red + ((size_t)((ks - 1) * nw + tw) * 32 + lane) * NR;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dst[v] = flat[v];
+    }
+    __syncthreads();
+    if (ks == 0)
+        for (int k = 1; k < nks; ++k) {
+            const int *src = red + ((size_t)((k - 1) * nw + tw) * 32 + lane) * NR;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) flat[v] += src[v];
+        }
+}
+
+// MODE_GW row sums of tiles [T0, T0 + NT) of product pr into A.u.stage.
+template <int P, int NT, int NPR>
+__device__ __forceinline__ void mma_stage_gw(MmaA<P, NT> &A, int T0, int lane, int pr,
+                                             const int (&iacc)[NT][NPR][2][4]) {
+    using M = MmaGeo<P, NT>;
+    constexpr int Q = Prm<P>::q;
+    const int g = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int tt = 0; tt < NT; ++tt)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int J = 8 * (T0 + tt) + 2 * tig + (c & 1);
+            if (J >= M::NBLK) continue;
+            const int j = 16 * J + g + 8 * (c >> 1);
+            // |P_1| <= 864 * 40 * 3118 < 2^27: reduced before the factor 64
+            A.u.stage[stage_slot(j)] = cmod<Q>(64 * cmod<Q>(iacc[tt][pr][0][c]) + iacc[tt][pr][1][c]);
+        }
 }
 
 // Sum of a K-split: warps with ks > 0 store their partial sums in red

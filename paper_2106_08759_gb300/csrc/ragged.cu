@@ -54,7 +54,7 @@ struct Group {
     int lanes = 4, split = 8, tiles = 1, kpt = 1, ksplit = 4;
     // r3batch: R/3 inverses by the batch forest; r3first: on the first draws
     // (invertibility from each batch's root, a failed batch redone per key)
-    bool mma = true, ntt = false, r3batch = false, r3first = false, fuse = false;
+    bool mma = true, ntt = false, wide = false, r3batch = false, r3first = false, fuse = false;
     size_t off_r3ok = 0;  // one root flag per batch (r3first)
     R3Factors fac;
     // table offsets (bytes, from the start of the uploaded table block)
@@ -177,7 +177,7 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
         else if (g.mma)
             SNT_CUDA_R(launch_tree_up_mma<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lmap(l),
                                              n_out, nodes + (size_t)g.lev_off[l] * pi.pad, st,
-                                             g.tiles, l == 1, g.ksplit));
+                                             g.tiles, l == 1, g.ksplit, g.wide));
         else
             SNT_CUDA_R(launch_tree_up<P>(nodes + (size_t)g.lev_off[l - 1] * pi.pad, lmap(l), n_out,
                                          nodes + (size_t)g.lev_off[l] * pi.pad, st, g.split));
@@ -192,7 +192,7 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
         else if (g.mma)
             SNT_CUDA_R(launch_tree_down_mma<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lmap(l),
                                                n_par, nodes + (size_t)g.lev_off[l - 1] * pi.pad,
-                                               st, g.tiles, l == 1, g.ksplit));
+                                               st, g.tiles, l == 1, g.ksplit, g.wide));
         else
             SNT_CUDA_R(launch_tree_down<P>(nodes + (size_t)g.lev_off[l] * pi.pad, lmap(l), n_par,
                                            nodes + (size_t)g.lev_off[l - 1] * pi.pad, st, g.split));
@@ -273,12 +273,14 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         const snt_ctx::Tuned &tu = ctx->tuned[pidx(g.P)][bbucket(bmax)];
         g.lanes = ctx->r3_lanes; g.split = ctx->tree_split; g.tiles = ctx->mma_tiles;
         g.kpt = ctx->r3_kpt; g.mma = ctx->rq_engine != 0; g.ntt = ctx->rq_engine == 2;
+        g.wide = ctx->rq_engine == 3;
         g.r3batch = ctx->r3_mode != 0;
         g.r3first = ctx->r3_mode == 2;
         g.ksplit = ctx->mma_ksplit;
         if (tu.lanes) {
             g.lanes = tu.lanes; g.split = tu.split; g.tiles = tu.tiles; g.kpt = tu.kpt;
-            g.mma = tu.engine != 0; g.ntt = tu.engine == 2; g.r3batch = tu.r3mode != 0;
+            g.mma = tu.engine != 0; g.ntt = tu.engine == 2; g.wide = tu.engine == 3;
+            g.r3batch = tu.r3mode != 0;
             g.r3first = tu.r3mode == 2;
         }
         // h from the level-1 inverses (the down-sweep's leaf level folded
@@ -362,7 +364,7 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         sig.push_back(g.lanes);
         sig.push_back(g.split);
         sig.push_back(g.mma ? g.tiles : 0);
-        sig.push_back(g.ntt ? 1 : 0);
+        sig.push_back(g.ntt ? 1 : g.wide ? 2 : 0);
         sig.push_back(g.kpt);
         sig.push_back(g.ksplit);
         sig.push_back(g.r3batch ? (g.r3first ? 2 : 1) : 0);

@@ -42,13 +42,15 @@ def _rq_cases(p, q, rng, n):
     return a, b
 
 
-@pytest.mark.parametrize("engine", [0, 1, 2])
+@pytest.mark.parametrize("engine", [0, 1, 2, 3])
 @pytest.mark.parametrize("P", [653, 761, 857])
 def test_rq_mul_matches_oracle(snt, ctx, P, engine):
     # engine 0: CUDA-core Toeplitz products; 1: the same products as warp MMAs
     # on exact f16 limbs (extreme operands exercise the limb and sum bounds);
     # 2: the transform multiplier over K = (Z/q)[x]/(x^64 + 1) (extreme
-    # operands exercise the growth bounds of the butterflies)
+    # operands exercise the growth bounds of the butterflies); 3: warp MMAs
+    # with one wide f16 limb on the vector side (all-max operands reach the
+    # int32 sums' bound; odd residues above 2048 take the moved representative)
     import torch
     p, q, _ = oracle.PARAMS[P]
     rng = np.random.default_rng(P)
@@ -154,15 +156,17 @@ def test_microbench_products_vs_oracle(snt, ctx, pool):
     c2 = torch.empty(n * p, dtype=torch.int16, device="cuda")
     snt.snt_rq_mul(ctx, 761, n, da, db, c)
     snt.snt_rq_mul(ctx, 761, n, da, ds, c2)
-    # the transform multiplier gives every one of the 2^20 + 2^20 products
-    # the tensor-core engine gives (both are checked against the oracle below)
+    # the transform multiplier and the one-wide-limb tensor-core form give
+    # every one of the 2^20 + 2^20 products the tensor-core engine gives (which
+    # is checked against the oracle below)
     c3 = torch.empty_like(c)
-    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 2)
     try:
-        snt.snt_rq_mul(ctx, 761, n, da, db, c3)
-        assert torch.equal(c, c3)
-        snt.snt_rq_mul(ctx, 761, n, da, ds, c3)
-        assert torch.equal(c2, c3)
+        for engine in (2, 3):
+            ctx.set_option(snt.SNT_OPT_RQ_ENGINE, engine)
+            snt.snt_rq_mul(ctx, 761, n, da, db, c3)
+            assert torch.equal(c, c3), engine
+            snt.snt_rq_mul(ctx, 761, n, da, ds, c3)
+            assert torch.equal(c2, c3), engine
     finally:
         ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
     del c3

@@ -120,15 +120,17 @@ def test_r3_two_elements_per_lane_group_give_the_same_keys(snt, ctx, lanes, kpt)
     assert first_mismatch(inj[0], rpk) is None and first_mismatch(inj[1], rsk) is None
 
 
+@pytest.mark.parametrize("engine", [2, 3])
 @pytest.mark.parametrize("P,B", [(761, 300), (653, 77), (857, 130), (761, 2), (761, 5)])
-def test_transform_engine_gives_the_same_keys(snt, ctx, P, B):
-    # general x general tree levels by the transform multiplier (engine 2)
-    # against the CUDA-core Toeplitz engine; B = 2 and 5 have few or no
-    # general levels (the leaf levels stay on the tensor cores)
+def test_transform_engine_gives_the_same_keys(snt, ctx, P, B, engine):
+    # general x general tree levels by the transform multiplier (engine 2) or
+    # by warp MMAs with one wide limb on the vector side (engine 3, narrow
+    # levels K-split too) against the CUDA-core Toeplitz engine; B = 2 and 5
+    # have few or no general levels (the leaf levels stay small-operand forms)
     ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 0)
     try:
         ref = gpu_keygen(snt, ctx, P, 5, 40, B)
-        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 2)
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, engine)
         got = gpu_keygen(snt, ctx, P, 5, 40, B)
     finally:
         ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
@@ -140,23 +142,27 @@ def test_transform_engine_gives_the_same_keys(snt, ctx, P, B):
 
 @pytest.mark.parametrize("tiles", [1, 2, 3])
 @pytest.mark.parametrize("P,B", [(761, 300), (653, 77), (857, 130)])
-def test_tensor_core_engine_gives_the_same_keys(snt, ctx, P, B, tiles):
+@pytest.mark.parametrize("wide", [False, True])
+def test_tensor_core_engine_gives_the_same_keys(snt, ctx, P, B, tiles, wide):
     # tree products as warp MMAs on exact f16 limbs, 1, 2 or 3 tiles of 128
-    # outputs per warp (ragged last warp for 653 and 857)
+    # outputs per warp (ragged last warp for 653 and 857); wide: one f16 limb
+    # on the vector side of the general levels (engine 3)
     ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 0)
     try:
         ref = gpu_keygen(snt, ctx, P, 5, 40, B)
     finally:
         ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
     ctx.set_option(snt.SNT_OPT_MMA_TILES, tiles)
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 3 if wide else 1)
     try:
         got = gpu_keygen(snt, ctx, P, 5, 40, B)
     finally:
         ctx.set_option(snt.SNT_OPT_MMA_TILES, 1)
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
 
 
-@pytest.mark.parametrize("engine", [1, 0, 2])
+@pytest.mark.parametrize("engine", [1, 0, 2, 3])
 @pytest.mark.parametrize("roots,B", [(2, 96), (32, 96), (1024, 96), (4, 300), (8, 7), (64, 4096)])
 def test_forest_of_subtrees_gives_the_same_keys(snt, ctx, engine, roots, B):
     # Montgomery's trick over K equal subtrees with K root inversions in one
