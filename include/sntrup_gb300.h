@@ -411,14 +411,15 @@ snt_status snt_measure_int_peak(int device, int kind, double *ops_per_s, int *sm
 
 /* Measures the 5th-generation tensor-core MMA (tcgen05.mma kind::f16: f16
  * operands from shared memory, f32 accumulator in tensor memory) at M = 128,
- * K = 16 and N = n (16, 32, 64, 128 or 256): one CTA per SM issuing
- * back-to-back MMAs into one accumulator, the result checked against its
- * closed form.  Writes multiply-adds per second (all SMs) to *macs_per_s and
+ * K = 16 and N = n (16, 32, 64, 128 or 256): ctas_per_sm (1, 2 or 4; at most
+ * 512 tensor-memory columns per SM, max(32, n) per CTA) CTAs per SM, each
+ * with one thread issuing back-to-back MMAs into its accumulator, the result
+ * checked against its closed form.  Writes multiply-adds per second (all SMs) to *macs_per_s and
  * the SM count to *sms.  The rate at small N bounds what a tcgen05 form of
  * the R/q Toeplitz products could reach (no calls of key generation use
  * it).  Returns SNT_EINTERNAL if the accumulator is wrong, SNT_ETIMEOUT if
  * the MMAs did not complete in about two seconds.  Synchronous. */
-snt_status snt_measure_tc05(int device, int n, double *macs_per_s, int *sms);
+snt_status snt_measure_tc05(int device, int n, int ctas_per_sm, double *macs_per_s, int *sms);
 
 /* One-line description of the last error on this host thread. */
 const char *snt_last_error_string(void);

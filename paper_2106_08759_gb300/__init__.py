@@ -108,7 +108,7 @@ def load():
         "snt_ctx_phase_times": [P, P, i32],
         "snt_measure_int_peak": [i32, i32, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int)],
-        "snt_measure_tc05": [i32, i32, ctypes.POINTER(ctypes.c_double),
+        "snt_measure_tc05": [i32, i32, i32, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sigs.items():
@@ -381,12 +381,13 @@ def snt_measure_int_peak(device=0, kind=0):
     return v.value, n.value
 
 
-def snt_measure_tc05(device=0, n=16):
+def snt_measure_tc05(device=0, n=16, ctas_per_sm=1):
     """(multiply-adds/s, SM count) of back-to-back tcgen05.mma kind::f16 at
-    M = 128, K = 16, N = n, operands in shared memory (result checked)."""
+    M = 128, K = 16, N = n, operands in shared memory, ctas_per_sm issuing
+    CTAs per SM (result checked)."""
     v = ctypes.c_double()
     k = ctypes.c_int()
-    _check(load().snt_measure_tc05(device, n, ctypes.byref(v), ctypes.byref(k)))
+    _check(load().snt_measure_tc05(device, n, ctas_per_sm, ctypes.byref(v), ctypes.byref(k)))
     return v.value, k.value
 
 

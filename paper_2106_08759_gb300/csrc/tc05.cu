@@ -6,8 +6,9 @@
 // operand tile (one product's output blocks), so its rate at small N is the
 // number that matters.
 //
-// One CTA per SM (the dynamic shared memory request admits one), 128
-// threads: thread 0 issues `iters` MMAs into one accumulator and commits
+// k CTAs per SM (the dynamic shared memory request admits k; k = 1, 2 or 4,
+// so that several issuing threads share one SM's tensor core), 128 threads
+// each: thread 0 issues `iters` MMAs into one accumulator and commits
 // them to an mbarrier; every thread waits for it (bounded by the SM clock),
 // then each warp reads its 32 accumulator rows and checks them: with
 // A[m][k] = (k == m mod 16) and B[n][k] = (n + 3 k) mod 8 (exact in f16),
@@ -19,7 +20,8 @@
 namespace {
 
 constexpr int kM = 128, kK = 16;
-constexpr int kDynSmem = 200 * 1024;  // admits one CTA per SM
+// dynamic shared memory that admits k CTAs per SM
+inline int dyn_smem_for(int k) { return k == 1 ? 200 * 1024 : k == 2 ? 100 * 1024 : 50 * 1024; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -151,18 +153,23 @@ __global__ void __launch_bounds__(128, 1) k_tc05_rate(int iters, int *err) {
 }
 
 template <int N>
-cudaError_t run_tc05(int blocks, int iters, int *err, cudaStream_t st) {
+cudaError_t run_tc05(int blocks, int dyn, int iters, int *err, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_tc05_rate<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kDynSmem);
+                                         200 * 1024);
     if (e != cudaSuccess) return e;
-    k_tc05_rate<N><<<blocks, 128, kDynSmem, st>>>(iters, err);
+    k_tc05_rate<N><<<blocks, 128, dyn, st>>>(iters, err);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-extern "C" snt_status snt_measure_tc05(int device, int n, double *macs_per_s, int *sms) {
+extern "C" snt_status snt_measure_tc05(int device, int n, int ctas_per_sm, double *macs_per_s,
+                                       int *sms) {
     if (!macs_per_s || (n != 16 && n != 32 && n != 64 && n != 128 && n != 256)) return SNT_EINVAL;
+    // k CTAs of max(32, n) tensor-memory columns each must fit the SM's 512
+    if ((ctas_per_sm != 1 && ctas_per_sm != 2 && ctas_per_sm != 4) ||
+        ctas_per_sm * (n < 32 ? 32 : n) > 512)
+        return SNT_EINVAL;
     int prev = 0;
     if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return SNT_ECUDA;
     cudaDeviceProp prop;
@@ -173,17 +180,17 @@ extern "C" snt_status snt_measure_tc05(int device, int n, double *macs_per_s, in
     if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    const int blocks = prop.multiProcessorCount;
+    const int blocks = prop.multiProcessorCount * ctas_per_sm, dyn = dyn_smem_for(ctas_per_sm);
     const int iters = (1 << 19) / (n / 16);  // iters * 7 stays exact in f32
     float best = 1e30f;
     for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
         cudaEventRecord(t0);
         switch (n) {
-            case 16: e = run_tc05<16>(blocks, iters, err, nullptr); break;
-            case 32: e = run_tc05<32>(blocks, iters, err, nullptr); break;
-            case 64: e = run_tc05<64>(blocks, iters, err, nullptr); break;
-            case 128: e = run_tc05<128>(blocks, iters, err, nullptr); break;
-            default: e = run_tc05<256>(blocks, iters, err, nullptr); break;
+            case 16: e = run_tc05<16>(blocks, dyn, iters, err, nullptr); break;
+            case 32: e = run_tc05<32>(blocks, dyn, iters, err, nullptr); break;
+            case 64: e = run_tc05<64>(blocks, dyn, iters, err, nullptr); break;
+            case 128: e = run_tc05<128>(blocks, dyn, iters, err, nullptr); break;
+            default: e = run_tc05<256>(blocks, dyn, iters, err, nullptr); break;
         }
         if (e != cudaSuccess) break;
         cudaEventRecord(t1);

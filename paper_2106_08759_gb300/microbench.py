@@ -97,7 +97,7 @@ def main():
         ctx.close()
         return
     if args.tc05_only:
-        rate, sms = snt.snt_measure_tc05(0, args.tc05_only)
+        rate, sms = snt.snt_measure_tc05(0, args.tc05_only, 1)
         print(json.dumps({"tc05_n": args.tc05_only, "tmacs": rate / 1e12, "sms": sms}))
         ctx.close()
         return

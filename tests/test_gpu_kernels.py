@@ -219,9 +219,12 @@ def test_microbench_all_rq_inversions(snt, ctx, pool, latency):
     assert pool.bad_inverses(p, q, x, outh, okh) == []
 
 
-@pytest.mark.parametrize("n", [16, 64, 256])
-def test_tcgen05_measurement_checks_its_accumulator(snt, n):
+@pytest.mark.parametrize("n,k", [(16, 1), (64, 1), (256, 1), (16, 4), (128, 4), (256, 2)])
+def test_tcgen05_measurement_checks_its_accumulator(snt, n, k):
     # the tcgen05.mma rate measurement (engine choice; not on the keygen path)
-    # verifies D = A B^T against its closed form before reporting a rate
-    rate, sms = snt.snt_measure_tc05(0, n)
+    # verifies D = A B^T against its closed form before reporting a rate;
+    # k CTAs per SM share the tensor core (k * max(32, n) <= 512 columns)
+    rate, sms = snt.snt_measure_tc05(0, n, k)
     assert rate > 0 and sms > 0
+    with pytest.raises(snt.SntError):
+        snt.snt_measure_tc05(0, 256, 4)  # 1024 tensor-memory columns: refused
