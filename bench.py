@@ -36,7 +36,7 @@ def fused_leaf(tuned, p=None):
     """Whether the library forms h from the level-1 inverses (its default on
     the tensor-core engine for p = 653, 761: the leaf level of the down-sweep
     folded into the h kernel)."""
-    return tuned.get("rq_engine") == 1 and (p or P) in (653, 761)
+    return tuned.get("rq_engine") in (1, 2, 3) and (p or P) in (653, 761)
 
 
 def launches_per_call(B, tuned):
@@ -80,9 +80,12 @@ def kernel_of(phase, tuned):
         if tuned.get("r3_mode", 0) == 0:
             return "k_r3_keygen<761, %d>" % tuned.get("r3_lanes", 4)
         return "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>"
-    mma = tuned.get("rq_engine") == 1
-    return {"tree_up": "k_tree_up_mma" if mma else "k_tree_up",
-            "tree_down": "k_tree_down_mma" if mma else "k_tree_down",
+    eng = tuned.get("rq_engine")
+    mma = eng in (1, 2, 3)
+    tree = {1: "%s_mma", 2: "%s_ntt + %s_mma (leaf level)", 3: "%s_mma (one wide limb)"}
+    name = lambda k: (tree[eng].replace("%s", k) if mma else k)
+    return {"tree_up": name("k_tree_up"),
+            "tree_down": name("k_tree_down"),
             "h_encode": ("k_finalize_pair<761>" if fused_leaf(tuned) else "k_finalize_mma<761>")
                         if mma else "k_finalize<761>",
             "root_inv": "k_rq_inv_jump<761, 4591>"}[phase]
@@ -391,10 +394,11 @@ def measure_micro(snt, torch, ctx, dev, stream, flush, reps):
     out["rq_mul_short"] = {"n": n, "ms": round(ms, 3), "products_per_s": round(n / ms * 1e3),
                            "gop_per_s": round(n * P * W / ms / 1e6, 1)}
     # the same general products on each engine: 0 CUDA-core Toeplitz (IMAD),
-    # 1 tensor-core Toeplitz (f16 limbs), 2 the transform multiplier (IMAD)
+    # 1 tensor-core Toeplitz (f16 limbs), 2 the transform multiplier (IMAD),
+    # 3 tensor-core Toeplitz with one wide limb on the vector side
     eng = ctx.get_option(snt.SNT_OPT_RQ_ENGINE)
     by_engine = {}
-    for e in (0, 1, 2):
+    for e in (0, 1, 2, 3):
         ctx.set_option(snt.SNT_OPT_RQ_ENGINE, e)
         ms = event_ms(torch, stream, flush, lambda: snt.snt_rq_mul(ctx, P, n, a, b, c, stream),
                       reps)
@@ -563,7 +567,7 @@ def run_ours(args):
         ms = phase.get(ph, 0.0)
         if ms <= 0:
             return None
-        if tuned.get("rq_engine") == 1 and ph in tensor_phases:
+        if tuned.get("rq_engine") in (1, 3) and ph in tensor_phases:
             achieved = 2.0 * ops[ph] / (ms * 1e-3) / 1e12  # TFLOP/s of the p^2 products
             peak = peaks.get("bf16_tflops") or 1900.0
             return {

@@ -522,8 +522,8 @@ template <int P>
 cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_keys,
                          const int8_t *gfix, const int16_t *ainv, int pk_bytes, int sk_bytes,
                          int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st,
-                         const int16_t *leaves, LevelMap lm1) {
-    k_fixup<P><<<8, Tp<P>::NT, 0, st>>>(km, fix_count, fix_keys, gfix, ainv, pk_bytes, sk_bytes,
+                         const int16_t *leaves, LevelMap lm1, int grid) {
+    k_fixup<P><<<grid, Tp<P>::NT, 0, st>>>(km, fix_count, fix_keys, gfix, ainv, pk_bytes, sk_bytes,
                                         sk_pk_off, hash_off, S, leaves, lm1);
     return cudaGetLastError();
 }
@@ -586,7 +586,7 @@ cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_b
                                             int, int, int, const EncSched &, cudaStream_t, bool); \
     template cudaError_t launch_fixup<P>(const KeyMap &, const int *, const int *, const int8_t *, \
                                          const int16_t *, int, int, int, int, const EncSched &,   \
-                                         cudaStream_t, const int16_t *, LevelMap);                \
+                                         cudaStream_t, const int16_t *, LevelMap, int);           \
     template cudaError_t launch_finalize_pair<P>(const KeyMap &, int, const int8_t *,            \
                                                  const int16_t *, const int16_t *, LevelMap, int, \
                                                  int, int, const EncSched &, cudaStream_t,        \

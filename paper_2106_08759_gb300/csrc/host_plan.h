@@ -98,6 +98,16 @@ inline bool param_info(int P, ParamInfo &pi) {
     return true;
 }
 
+// CTAs of the fix-up of redrawn keys for a call of n keys: the list is
+// usually empty (a zero divisor among the first draws has probability
+// 3^-19 per key for sntrup761), but x^653 - x - 1 has a factor of degree 3
+// over F_3, so about one sntrup653 key in 27 is redrawn when the R/3 forest
+// runs on the first draws.
+inline int fixup_grid(size_t n) {
+    const size_t g = n / 16;
+    return (int)(g < 8 ? 8 : g > 608 ? 608 : g);
+}
+
 // Product-tree levels over B leaves: level 0 = leaves, level l has
 // ceil(n_(l-1) / 2) nodes, the last level has one.  Offsets in nodes.
 struct Tree {

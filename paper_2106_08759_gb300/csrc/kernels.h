@@ -211,12 +211,14 @@ template <int P>
 cudaError_t launch_r3_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
                                cudaStream_t st, const int *idx = nullptr);
-// Keys on the resampling list: h with the final g, pk, sk's copy and hash.
+// Keys on the resampling list: h with the final g, pk, sk's copy and hash;
+// `grid` CTAs take list entries in turn (the list's length is on the device:
+// size it by how many keys can be redrawn).
 template <int P>
 cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_keys,
                          const int8_t *gfix, const int16_t *ainv, int pk_bytes, int sk_bytes,
                          int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st,
-                         const int16_t *leaves = nullptr, LevelMap lm1 = LevelMap{});
+                         const int16_t *leaves = nullptr, LevelMap lm1 = LevelMap{}, int grid = 8);
 // sbuf (optional): the leaf-pair products s of launch_leaf_s, else formed here.
 template <int P>
 cudaError_t launch_finalize_pair(const KeyMap &km, int n1, const int8_t *gbuf,

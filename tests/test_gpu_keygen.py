@@ -466,3 +466,27 @@ def test_pipelined_parts_redraw_injected_zero_divisors(snt, ctx):
         snt.snt_debug_inject_g(ctx, 761, [], np.zeros((0, 761), np.int8))
     rpk, rsk = oracle.keygen_batch(761, 4, 300, 96, g_inject=dict(zip(offs, bads[:2])))
     assert first_mismatch(pk, rpk) is None and first_mismatch(sk, rsk) is None
+
+
+def test_sntrup653_first_draw_batch_with_many_redraws(snt, ctx, pool):
+    # x^653 - x - 1 has a factor of degree 3 over F_3, so about one first draw
+    # of g in 27 is a zero divisor: with the R/3 forest on the first draws most
+    # 32-key subtrees fail, their keys go to the per-key fall-back and dozens
+    # of keys to the fix-up; all keys equal the per-key path's, and the
+    # redrawn ones (and others) the oracle's
+    B, seed = 2048, 17
+    ctx.set_option(snt.SNT_OPT_R3_MODE, 2)
+    ctx.set_option(snt.SNT_OPT_ROOTS, 64)
+    try:
+        pk, sk = gpu_keygen(snt, ctx, 653, seed, 0, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_R3_MODE, 0)
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+    pk2, sk2 = gpu_keygen(snt, ctx, 653, seed, 0, B, perkey=True)
+    assert first_mismatch(pk, pk2) is None and first_mismatch(sk, sk2) is None
+    # keys among the first 600 whose first draw is not invertible (about 22)
+    redrawn = [k for k in range(600)
+               if not oracle.ring_inv(653, 3, oracle.sample_small(653, seed, k, 0))[0]]
+    assert len(redrawn) > 10  # the fix-up had real work
+    idx = np.array(sorted(set(redrawn) | {0, 1, B - 1}))
+    assert pool.bad_keys(653, seed, idx, pk[idx], sk[idx]) == []
