@@ -341,6 +341,11 @@ def measure_b32(snt, torch, dev, stream, flush, seed, steps):
         for name, fn in (("batched", snt.snt_batch_keygen), ("perkey", snt.snt_keygen_perkey)):
             ms = event_ms(torch, stream, flush, call(fn), steps)
             out[name] = {"keys_per_s": round(B / ms * 1e3, 1), "ms_per_call": round(ms, 4)}
+        c.set_option(snt.SNT_OPT_PDL, 0)
+        ms = event_ms(torch, stream, flush, call(snt.snt_batch_keygen), steps)
+        out["batched_plain_launch"] = {"keys_per_s": round(B / ms * 1e3, 1),
+                                       "ms_per_call": round(ms, 4)}
+        c.set_option(snt.SNT_OPT_PDL, 1)
         c.sync()
     out["roots"] = tuned["roots"]
     out["r3_mode"] = tuned["r3_mode"]
@@ -515,11 +520,22 @@ def run_ours(args):
     def perkey(first):
         snt.snt_keygen_perkey(ctx, P, args.seed, first, B, pk, sk, stream)
 
+    # the timed steps run back to back (the phase events, which wait for
+    # every step, are taken in a separate run below)
     with ClockSampler(local) as clk:
-        total_ms, phase = timed(batched, args.steps, max(3, args.warmup), phases=True)
+        total_ms, _ = timed(batched, args.steps, max(3, args.warmup))
     clocks = clk.summary()
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(world, B, args.steps, total_ms * 1e-3)
+    ph_steps = max(3, min(args.steps, 10))
+    _, phase = timed(batched, ph_steps, 3, phases=True)
+    # the same steps with every kernel launched plainly (no programmatic
+    # dependent launch): what the launch mode is worth
+    ctx.set_option(snt.SNT_OPT_PDL, 0)
+    plain_ms, _ = timed(batched, ph_steps, 3)
+    ctx.set_option(snt.SNT_OPT_PDL, 1)
+    launch_modes = {"pdl_ms_per_step": round(ms_per_step, 4),
+                    "plain_ms_per_step": round(plain_ms / ph_steps, 4)}
 
     pk_steps = args.perkey_steps or max(3, args.steps // 10)
     pk_ms, _ = timed(perkey, pk_steps, 3)
@@ -693,6 +709,7 @@ def run_ours(args):
                        "batched_speedup": round(value / perkey_rate, 3)},
     }
     line.update(extra)
+    line["launch_modes"] = launch_modes
     line["phases_ms"] = {k: round(v, 4) for k, v in phase.items()}
     line["tuned"] = tuned
     ctx.close()

@@ -343,7 +343,14 @@ typedef enum {
      * latency-bound root inversions overlap another group's wide tree levels
      * (tensor-core or transform engine; ignored unless the forest's subtree
      * count is a multiple of it).  Same products, same bytes. */
-    SNT_OPT_PARTS = 13
+    SNT_OPT_PARTS = 13,
+    /* 1 (default) or 0: launch the kernels of each stream's chain with
+     * programmatic stream serialization, so that a kernel's CTAs are
+     * scheduled while its predecessor's last wave runs and start the moment
+     * it completes (each such kernel waits for its predecessor's completion
+     * before its first memory access); 0 launches them plainly.  Same bytes
+     * either way; a ragged graph is captured again when it changes. */
+    SNT_OPT_PDL = 14
 } snt_option;
 
 snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);

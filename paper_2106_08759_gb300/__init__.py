@@ -25,6 +25,7 @@ SNT_OPT_R3_LANES, SNT_OPT_TREE_SPLIT, SNT_OPT_R3_OVERLAP, SNT_OPT_NARROW_SEG = 1
 SNT_OPT_RQ_ENGINE, SNT_OPT_MMA_TILES, SNT_OPT_R3_KPT, SNT_OPT_MMA_KSPLIT = 5, 6, 7, 8
 SNT_OPT_ROOTS, SNT_OPT_R3_MODE, SNT_OPT_FUSE_LEAF, SNT_OPT_PERKEY_INV = 9, 10, 11, 12
 SNT_OPT_PARTS = 13
+SNT_OPT_PDL = 14
 
 # phase names of snt_ctx_phase_times (SNT_NPHASES entries)
 PHASES = ("sample_f", "r3_inv", "tree_up", "root_inv", "tree_down", "h_encode", "sha512",

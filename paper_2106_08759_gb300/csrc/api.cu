@@ -20,6 +20,7 @@
 #include "ctx.h"
 #include "host_plan.h"
 #include "kernels.h"
+#include "pdl.cuh"
 #include "sntrup_gb300.h"
 
 using namespace snt;
@@ -60,6 +61,7 @@ template <int P>
 snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t first, size_t B,
                       uint8_t *pk, uint8_t *sk, cudaStream_t st, bool batched, uint8_t *arena,
                       bool inline_stream = false) {
+    const PdlScope pdl_scope(ctx->pdl != 0);
     const Tree tb = make_tree(B);  // the scratch layout (any forest of B fits its rows)
     int16_t *nodes = reinterpret_cast<int16_t *>(arena);
     int8_t *gbuf = reinterpret_cast<int8_t *>(arena + align256(tb.total * pi.pad * sizeof(int16_t)));
@@ -824,6 +826,10 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
                 return set_error(SNT_EINVAL, "pipelined parts is 1, 2 or 4");
             ctx->parts = value;
             return SNT_OK;
+        case SNT_OPT_PDL:
+            if (value != 0 && value != 1) return set_error(SNT_EINVAL, "PDL is 0 or 1");
+            ctx->pdl = value;
+            return SNT_OK;
         default:
             return set_error(SNT_EINVAL, "unknown option %d", option);
     }
@@ -845,6 +851,7 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
         case SNT_OPT_FUSE_LEAF: *value = ctx->fuse_leaf; return SNT_OK;
         case SNT_OPT_PERKEY_INV: *value = ctx->perkey_inv; return SNT_OK;
         case SNT_OPT_PARTS: *value = ctx->parts; return SNT_OK;
+        case SNT_OPT_PDL: *value = ctx->pdl; return SNT_OK;
         default: return set_error(SNT_EINVAL, "unknown option %d", option);
     }
 }

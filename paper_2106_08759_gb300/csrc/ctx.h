@@ -60,6 +60,7 @@ struct snt_ctx {
     int fuse_leaf = 1;  // h from the level-1 inverses (where FuseLeaf<P>::ok)
     int perkey_inv = 1; // per-key path: 1 jump divsteps, 0 one divstep per barrier
     int parts = 1;      // pipelined parts of a batch keygen call (SNT_OPT_PARTS)
+    int pdl = 1;        // programmatic dependent launches (SNT_OPT_PDL)
     cudaStream_t part[snt::kMaxParts - 1] = {};  // streams of parts 1 .. kMaxParts-1
     cudaEvent_t ev_pfork = nullptr, ev_pdone[snt::kMaxParts] = {};
     cudaEvent_t ev_psfork[snt::kMaxParts] = {}, ev_psready[snt::kMaxParts] = {};

@@ -18,6 +18,7 @@
 #include "sha512.cuh"
 #include "mixed.cuh"
 #include "mma_mul.cuh"
+#include "pdl.cuh"
 
 namespace snt {
 
@@ -25,6 +26,7 @@ template <int P>
 __global__ void __launch_bounds__(Tp<P>::NT)
 k_finalize(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__restrict__ ainv,
            int pk_bytes, int sk_bytes, int sk_pk_off, EncSched S) {
+    pdl_enter();
     using G = Geo<P>;
     __shared__ __align__(16) int As[Tp<P>::p8];
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
@@ -64,6 +66,7 @@ template <int P>
 __global__ void __launch_bounds__(32 * MmaGeo<P, 1>::NW)
 k_finalize_mma(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__restrict__ ainv,
                int pk_bytes, int sk_bytes, int sk_pk_off, EncSched S) {
+    pdl_enter();
     using G = Geo<P>;
     using M = MmaGeo<P, 1>;
     static_assert(2 * G::pad * sizeof(uint32_t) + 1344 <= sizeof(MmaE<P, 1>), "encode buffers");
@@ -141,6 +144,7 @@ template <int P>
 __global__ void __launch_bounds__(32 * MmaGeo<P, 1>::NW)
 k_leaf_s(const int8_t *__restrict__ gbuf, const int16_t *__restrict__ leaves, LevelMap lm1,
          int16_t *__restrict__ sbuf) {
+    pdl_enter();
     using G = Geo<P>;
     extern __shared__ __align__(16) uint8_t sm[];
     MmaE<P, 1> &E = *reinterpret_cast<MmaE<P, 1> *>(sm);
@@ -174,6 +178,7 @@ __global__ void __launch_bounds__(32 * MmaGeo<P, 1>::NW)
 k_finalize_pair(KeyMap km, const int8_t *__restrict__ gbuf, const int16_t *__restrict__ leaves,
                 const int16_t *__restrict__ inv1, LevelMap lm1, int pk_bytes, int sk_bytes,
                 int sk_pk_off, EncSched S, const int16_t *__restrict__ sbuf) {
+    pdl_enter();
     using G = Geo<P>;
     using M = MmaGeo<P, 1>;
     static_assert(FuseLeaf<P>::ok, "limb sums of the fused leaf level exceed 2^24");
@@ -303,6 +308,7 @@ k_fixup(KeyMap km, const int *__restrict__ fix_count, const int *__restrict__ fi
         const int8_t *__restrict__ gfix, const int16_t *__restrict__ ainv, int pk_bytes,
         int sk_bytes, int sk_pk_off, int hash_off, EncSched S,
         const int16_t *__restrict__ leaves, LevelMap lm1) {
+    pdl_enter();
     using G = Geo<P>;
     __shared__ __align__(16) int As[Tp<P>::p8];
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
@@ -391,9 +397,8 @@ __device__ __forceinline__ void nbar_arrive(int id, int n) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// Two warps hash 32 keys, one key per lane.  The 32 public keys are
-// consecutive rows, i.e. one contiguous span, copied to shared memory with
-// 16-byte loads when the span is 16-byte aligned (byte loads otherwise).
+// Two warps hash 32 keys, one key per lane, after copying the 32 public
+// keys to shared memory (runs of contiguous rows, see below).
 //
 // A block's 80 rounds form one serial chain per key, and a single warp runs
 // the whole compression at about three cycles per instruction, so the work
@@ -404,40 +409,85 @@ __device__ __forceinline__ void nbar_arrive(int id, int n) {
 // the table.  Named barriers 1, 2 mark slot 0, 1 full, 3, 4 mark it free
 // again; each is used in a fixed order by both warps, once per block.
 constexpr int kShaWkBytes = 2 * 80 * 32 * 8;
+// rows of 32 public keys; a run starts at most 15 + 15 bytes after the
+// previous run's end (rounding up to 16, then its source's phase)
+constexpr int sha_blk_bytes(int pk_bytes) { return 32 * pk_bytes + 32 * 32; }
+constexpr int kShaBlkMax = sha_blk_bytes(1322);  // the opt-in size: sntrup857's 1322-byte pk
 
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(64, 1)
 k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
+    pdl_enter();
     extern __shared__ __align__(16) uint8_t sm[];
     uint64_t(*wk)[80][32] = reinterpret_cast<uint64_t(*)[80][32]>(sm);  // [slot][round][key]
+    __shared__ uint64_t ks[80];  // the round constants
+    for (int i = threadIdx.x; i < 80; i += 64) ks[i] = c_sha512_k[i];
     uint8_t *blk = sm + kShaWkBytes;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int base = blockIdx.x * 32;
     const int nkeys = min(32, B - base);
-    const int nbytes = nkeys * pk_bytes;
-    if (km.nb > 0) {  // keys from a batch table: copy row by row
-        for (int j = 0; j < nkeys; ++j) {
-            const BatchDesc d = key_batch(km, base + j);
-            const uint8_t *row = d.pk + (size_t)(base + j - d.key_base) * pk_bytes;
-            for (int b = tid; b < pk_bytes; b += 64) blk[j * pk_bytes + b] = row[b];
+    // The keys form runs whose rows are contiguous in device memory (one run
+    // for a single batch).  A run goes to a shared-memory offset congruent
+    // to its source address mod 16, so that its middle moves in aligned
+    // 16-byte words and only its two ends bytewise; rowoff[j] is the offset
+    // of key base + j's row.  Warp 0 finds the runs, a lane per key.
+    __shared__ int rowoff[32];
+    __shared__ const uint8_t *run_src[32];
+    __shared__ int run_dst[32], run_first[33];
+    __shared__ int nruns;
+    if (warp == 0) {
+        uintptr_t row = 0;
+        if (lane < nkeys) {
+            const BatchDesc d = key_batch(km, base + lane);
+            row = reinterpret_cast<uintptr_t>(d.pk + (size_t)(base + lane - d.key_base) * pk_bytes);
         }
+        const uintptr_t prev = __shfl_up_sync(0xffffffffu, (unsigned long long)row, 1);
+        const bool start = lane < nkeys && (lane == 0 || row != prev + (uintptr_t)pk_bytes);
+        const unsigned starts = __ballot_sync(0xffffffffu, start);
+        const int r = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;  // this lane's run
+        if (start) {
+            run_src[r] = reinterpret_cast<const uint8_t *>(row);
+            run_first[r] = lane;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const int n = __popc(starts);
+            run_first[n] = nkeys;
+            int off = 0;
+            for (int q = 0; q < n; ++q) {
+                off = ((off + 15) & ~15) + (int)(reinterpret_cast<uintptr_t>(run_src[q]) & 15);
+                run_dst[q] = off;
+                off += (run_first[q + 1] - run_first[q]) * pk_bytes;
+            }
+            nruns = n;
+        }
+        __syncwarp();
+        if (lane < nkeys) rowoff[lane] = run_dst[r] + (lane - run_first[r]) * pk_bytes;
     }
-    const uint8_t *src = km.one.pk + (size_t)base * pk_bytes;
-    int done = (km.nb > 0) ? nbytes : 0;
-    if (km.nb == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-        const int n16 = nbytes / 16;
-        const int4 *s4 = reinterpret_cast<const int4 *>(src);
-        int4 *d4 = reinterpret_cast<int4 *>(blk);
-#pragma unroll 4
-        for (int i = tid; i < n16; i += 64) d4[i] = s4[i];
-        done = n16 * 16;
+    __syncthreads();
+    for (int q = 0; q < nruns; ++q) {
+        const uint8_t *src = run_src[q];
+        uint8_t *dst = blk + run_dst[q];
+        const int len = (run_first[q + 1] - run_first[q]) * pk_bytes;
+        const int head = min(len, (int)((16 - (reinterpret_cast<uintptr_t>(src) & 15)) & 15));
+        const int n16 = (len - head) / 16;
+        // the middle as asynchronous 16-byte copies: all in flight at once
+        // (a load / store loop through registers would wait for each load,
+        // the compiler not knowing that the two buffers never overlap)
+        const uint32_t d16 = (uint32_t)__cvta_generic_to_shared(dst + head);
+        for (int i = tid; i < n16; i += 64)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d16 + 16u * (uint32_t)i),
+                         "l"(src + head + 16 * (size_t)i)
+                         : "memory");
+        for (int i = tid; i < head; i += 64) dst[i] = src[i];
+        for (int i = head + 16 * n16 + tid; i < len; i += 64) dst[i] = src[i];
     }
-    for (int i = done + tid; i < nbytes; i += 64) blk[i] = src[i];
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     const int len = pk_bytes + 1;
     const int nblk = (len + 1 + 16 + 127) / 128;
     if (warp == 1) {
         // lanes past the last key repeat it; their digests are not stored
-        const uint8_t *row = blk + min(lane, nkeys - 1) * pk_bytes;  // byte pos (1..pk_bytes) at row[pos - 1]
+        const uint8_t *row = blk + rowoff[min(lane, nkeys - 1)];  // byte pos (1..pk_bytes) at row[pos - 1]
         const uint64_t bitlen = (uint64_t)len * 8u;
         for (int b0 = 0; b0 < nblk; ++b0) {
             const int slot = b0 & 1;
@@ -448,8 +498,15 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
                 const int pos = 128 * b0 + 8 * t;
                 uint64_t v = 0;
                 if (pos >= 1 && pos + 8 <= len) {
-#pragma unroll
-                    for (int b = 0; b < 8; ++b) v = (v << 8) | row[pos + b - 1];
+                    // message bytes pos .. pos + 7 = row bytes pos - 1 .. pos + 6,
+                    // big-endian: three aligned words (at most 4 bytes past the
+                    // row, inside the buffer's slack), funnel-shifted, reversed
+                    const uintptr_t at = reinterpret_cast<uintptr_t>(row + pos - 1);
+                    const uint32_t *a0 = reinterpret_cast<const uint32_t *>(at & ~(uintptr_t)3);
+                    const uint32_t sh = 8u * (uint32_t)(at & 3u);
+                    const uint32_t w0 = a0[0], w1 = a0[1], w2 = a0[2];
+                    const uint32_t lo = __funnelshift_r(w0, w1, sh), hi = __funnelshift_r(w1, w2, sh);
+                    v = ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | __byte_perm(hi, 0, 0x0123);
                 } else {
 #pragma unroll
                     for (int b = 0; b < 8; ++b) {
@@ -474,7 +531,7 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
                         const uint64_t s1 = rotr(w2, 19) ^ rotr(w2, 61) ^ (w2 >> 6);
                         W[tt] += s0 + W[(tt + 9) & 15] + s1;
                     }
-                    wk[slot][r + tt][lane] = W[tt] + c_sha512_k[r + tt];
+                    wk[slot][r + tt][lane] = W[tt] + ks[r + tt];
                 }
             }
             nbar_arrive(1 + slot, 64);
@@ -510,10 +567,11 @@ cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, con
                 k_finalize_mma<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
         }
-        k_finalize_mma<P><<<nkeys, 32 * MmaGeo<P, 1>::NW, sm, st>>>(km, gbuf, ainv, pk_bytes,
-                                                                    sk_bytes, sk_pk_off, S);
+        SNT_LAUNCH(k_finalize_mma<P>, nkeys, 32 * MmaGeo<P, 1>::NW, sm, st, km, gbuf, ainv,
+            pk_bytes, sk_bytes, sk_pk_off, S);
     } else {
-        k_finalize<P><<<nkeys, Tp<P>::NT, 0, st>>>(km, gbuf, ainv, pk_bytes, sk_bytes, sk_pk_off, S);
+        SNT_LAUNCH(k_finalize<P>, nkeys, Tp<P>::NT, 0, st, km, gbuf, ainv, pk_bytes, sk_bytes,
+            sk_pk_off, S);
     }
     return cudaGetLastError();
 }
@@ -523,8 +581,8 @@ cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_
                          const int8_t *gfix, const int16_t *ainv, int pk_bytes, int sk_bytes,
                          int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st,
                          const int16_t *leaves, LevelMap lm1, int grid) {
-    k_fixup<P><<<grid, Tp<P>::NT, 0, st>>>(km, fix_count, fix_keys, gfix, ainv, pk_bytes, sk_bytes,
-                                        sk_pk_off, hash_off, S, leaves, lm1);
+    SNT_LAUNCH(k_fixup<P>, grid, Tp<P>::NT, 0, st, km, fix_count, fix_keys, gfix, ainv, pk_bytes,
+        sk_bytes, sk_pk_off, hash_off, S, leaves, lm1);
     return cudaGetLastError();
 }
 
@@ -542,9 +600,8 @@ cudaError_t launch_finalize_pair(const KeyMap &km, int n1, const int8_t *gbuf,
                 k_finalize_pair<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
         }
-        k_finalize_pair<P><<<n1, 32 * MmaGeo<P, 1>::NW, sm, st>>>(km, gbuf, leaves, inv1, lm1,
-                                                                  pk_bytes, sk_bytes, sk_pk_off, S,
-                                                                  sbuf);
+        SNT_LAUNCH(k_finalize_pair<P>, n1, 32 * MmaGeo<P, 1>::NW, sm, st, km, gbuf, leaves, inv1,
+            lm1, pk_bytes, sk_bytes, sk_pk_off, S, sbuf);
         return cudaGetLastError();
     }
 }
@@ -556,14 +613,14 @@ cudaError_t launch_leaf_s(int n1, const int8_t *gbuf, const int16_t *leaves, Lev
         return cudaErrorNotSupported;
     } else {
         const size_t sm = sizeof(MmaE<P, 1>) + sizeof(MmaA<P, 1>);
-        k_leaf_s<P><<<n1, 32 * MmaGeo<P, 1>::NW, sm, st>>>(gbuf, leaves, lm1, sbuf);
+        SNT_LAUNCH(k_leaf_s<P>, n1, 32 * MmaGeo<P, 1>::NW, sm, st, gbuf, leaves, lm1, sbuf);
         return cudaGetLastError();
     }
 }
 
 cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
                              int hash_off, cudaStream_t st) {
-    const int smem = kShaWkBytes + (32 * pk_bytes + 15) / 16 * 16;
+    const int smem = kShaWkBytes + sha_blk_bytes(pk_bytes);
     // the opt-in above 48 KB, once per device at the largest size any
     // parameter set needs (host state, not stream work)
     static std::atomic<uint64_t> opted{0};
@@ -572,12 +629,13 @@ cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_b
     if (e != cudaSuccess) return e;
     if (!(opted.load() & (1ull << (dev & 63)))) {
         e = cudaFuncSetAttribute(k_sha512_pk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kShaWkBytes + 32 * 1344);
+                                 kShaWkBytes + kShaBlkMax);
         if (e != cudaSuccess) return e;
         opted.fetch_or(1ull << (dev & 63));
     }
-    if (smem > kShaWkBytes + 32 * 1344) return cudaErrorInvalidValue;
-    k_sha512_pk<<<(nkeys + 31) / 32, 64, smem, st>>>(km, nkeys, pk_bytes, sk_bytes, hash_off);
+    if (smem > kShaWkBytes + kShaBlkMax) return cudaErrorInvalidValue;
+    SNT_LAUNCH(k_sha512_pk, (nkeys + 31) / 32, 64, smem, st, km, nkeys, pk_bytes, sk_bytes,
+        hash_off);
     return cudaGetLastError();
 }
 

@@ -36,6 +36,25 @@ constexpr int KEM_SPLIT = 2;  // products use 2 * p8/8 <= 256 threads
 // leave the CTA waiting; 32 lanes hash 32 items for the instructions of one).
 // Small launches keep one item per CTA for latency.
 constexpr int KEM_MAX_IPC = 32;
+
+// Bytes [0, n) of src (device memory) to dst (shared memory), n <= 256 K:
+// every load is issued before the first store (a load / store loop would
+// wait for each load in turn, the compiler not knowing that the two buffers
+// never overlap).
+template <int K>
+__device__ __forceinline__ void g2s_bytes(uint8_t *dst, const uint8_t *src, int n, int tid) {
+    uint32_t v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int b = tid + k * KEM_THREADS;
+        v[k] = b < n ? src[b] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int b = tid + k * KEM_THREADS;
+        if (b < n) dst[b] = (uint8_t)v[k];
+    }
+}
 inline int kem_items_per_cta(int n, int sms) {
     const int ipc = n / (8 * sms);
     return ipc < 1 ? 1 : (ipc > KEM_MAX_IPC ? KEM_MAX_IPC : ipc);
@@ -76,7 +95,7 @@ k_encap(EncMap em, int n, int ipc, int pk_bytes, int ct_bytes, EncSched Spk, Enc
     const int rb = ct_bytes - 32;
     for (int r = 0; r < cnt; ++r) {
         const EncItem item = enc_item(em, first + r, pk_bytes, ct_bytes);
-        for (int b = tid; b < pk_bytes; b += KEM_THREADS) pkb[b] = item.pk[b];
+        g2s_bytes<(sizeof(pkb) + KEM_THREADS - 1) / KEM_THREADS>(pkb, item.pk, pk_bytes, tid);
         __syncthreads();
         const int cur = mixed_decode<G::pad>(pkb, Spk, R);
         for (int i = tid; i < G::pad; i += KEM_THREADS) hs[i] = (i < P) ? (int)R[cur][i] - G::half : 0;
@@ -180,8 +199,8 @@ k_decap(DecMap dm, int n, int ipc, int pk_bytes, int sk_bytes, int ct_bytes, Enc
     const int rb = ct_bytes - 32;
     for (int it_r = 0; it_r < cnt; ++it_r) {
         const DecItem item = dec_item(dm, first + it_r, sk_bytes, ct_bytes);
-        for (int b = tid; b < sk_bytes; b += KEM_THREADS) skb[b] = item.sk[b];
-        for (int b = tid; b < ct_bytes; b += KEM_THREADS) ctb[b] = item.ct[b];
+        g2s_bytes<(sizeof(skb) + KEM_THREADS - 1) / KEM_THREADS>(skb, item.sk, sk_bytes, tid);
+        g2s_bytes<(sizeof(ctb) + KEM_THREADS - 1) / KEM_THREADS>(ctb, item.ct, ct_bytes, tid);
         if (tid == 0) weight = 0;
         __syncthreads();
         const uint8_t *pkb = skb + 2 * SB;

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "pdl.cuh"
 
 namespace snt {
 
@@ -203,6 +204,7 @@ template <int P>
 __global__ void __launch_bounds__(128)
 k_r3_check(KeyMap km, int B, int8_t *__restrict__ gbuf, int16_t *__restrict__ leaves3,
            R3Factors fac, int *__restrict__ err) {
+    pdl_enter();
     using G = Geo<P>;
     constexpr int W = (P + 31) / 32;  // words of a degree < p polynomial
     extern __shared__ uint32_t fw[];   // the factors' planes
@@ -295,6 +297,7 @@ template <int P>
 __global__ void __launch_bounds__(256)
 k_r3_encode_v(KeyMap km, int B, const int16_t *__restrict__ v3, int sk_bytes, int sk_off,
               const int *__restrict__ sub_ok, int sub_size) {
+    pdl_enter();
     using G = Geo<P>;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int key = idx / G::small_bytes, b = idx % G::small_bytes;
@@ -314,8 +317,8 @@ k_r3_encode_v(KeyMap km, int B, const int16_t *__restrict__ v3, int sk_bytes, in
 template <int P>
 cudaError_t launch_r3_check(const KeyMap &km, int B, int8_t *gbuf, int16_t *leaves3,
                             const R3Factors &fac, int *err, cudaStream_t st) {
-    k_r3_check<P><<<(B + 3) / 4, 128, fac.total_words * sizeof(uint32_t), st>>>(km, B, gbuf, leaves3,
-                                                                             fac, err);
+    SNT_LAUNCH(k_r3_check<P>, (B + 3) / 4, 128, fac.total_words * sizeof(uint32_t), st, km, B, gbuf,
+        leaves3, fac, err);
     return cudaGetLastError();
 }
 
@@ -323,8 +326,8 @@ template <int P>
 cudaError_t launch_r3_encode_v(const KeyMap &km, int B, const int16_t *v3, int sk_bytes,
                                int sk_off, cudaStream_t st, const int *sub_ok, int sub_size) {
     const long n = (long)B * Geo<P>::small_bytes;
-    k_r3_encode_v<P><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(km, B, v3, sk_bytes, sk_off,
-                                                                  sub_ok, sub_size);
+    SNT_LAUNCH(k_r3_encode_v<P>, (unsigned)((n + 255) / 256), 256, 0, st, km, B, v3, sk_bytes,
+        sk_off, sub_ok, sub_size);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@
 // serves 32 KPT / LK elements and each lane has KPT independent chains.
 #include "common.cuh"
 #include "kernels.h"
+#include "pdl.cuh"
 
 namespace snt {
 
@@ -237,19 +238,21 @@ k_r3_keygen(KeyMap km, int B, int8_t *__restrict__ g_out, int sk_bytes, int sk_o
             int n_inj, int *__restrict__ err, int8_t *__restrict__ gfix,
             int *__restrict__ fix_count, int *__restrict__ fix_keys,
             const int *__restrict__ sub_ok, int sub_size) {
+    pdl_enter();
     using Gm = Geo<P>;
     using RG = R3Geo<P, LKT, KPT>;
     constexpr int WL = RG::WL, LK = RG::LK, EPW = RG::EPW, GPW = RG::GPW;
+    static_assert(EPW <= 32, "one lane per key of the warp");
     __shared__ __align__(16) int8_t smem[RG::EPB][RG::ROW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = lane & (LK - 1), grp = lane / LK;
     const int ebase = blockIdx.x * RG::EPB + warp * EPW;  // first element of this warp
     if (ebase >= B) return;                               // warp-uniform
     if (sub_ok) {  // fall-back form: only warps with a key in a failed subtree
-        bool all_ok = true;
-        for (int e = ebase; e < min(ebase + EPW, B); ++e)
-            all_ok = all_ok && sub_ok[key_subtree(km, e, sub_size)] != 0;
-        if (all_ok) return;
+        // lane e tests the warp's key e (the table searches run in parallel)
+        const bool mine = lane >= EPW || ebase + lane >= B ||
+                          sub_ok[key_subtree(km, ebase + lane, sub_size)] != 0;
+        if (__all_sync(FULL, mine)) return;
     }
     // this group's elements: warp slots grp + k GPW
     const bool deferred = gfix != nullptr;
@@ -361,12 +364,18 @@ k_r3_keygen(KeyMap km, int B, int8_t *__restrict__ g_out, int sk_bytes, int sk_o
 #pragma unroll
     for (int k = 0; k < KPT; ++k) reversed_to_smem<P, LKT>(om[k], os[k], gsm[k]);
     __syncwarp();
-    // Small_encode(1/g)
+    // Small_encode(1/g); lane e looks up the sk row of the warp's key e (the
+    // table searches run in parallel, not one per loop step)
+    unsigned long long skrow = 0;
+    if (lane < EPW && ebase + lane < B) {
+        const BatchDesc be = key_batch(km, ebase + lane);
+        skrow = reinterpret_cast<unsigned long long>(
+            be.sk + (size_t)(ebase + lane - be.key_base) * sk_bytes + sk_off);
+    }
     for (int e = 0; e < EPW; ++e) {
         if (ebase + e >= B) break;
         const int8_t *src = smem[warp * EPW + e];
-        const BatchDesc be = key_batch(km, ebase + e);
-        uint8_t *skk = be.sk + (size_t)(ebase + e - be.key_base) * sk_bytes + sk_off;
+        uint8_t *skk = reinterpret_cast<uint8_t *>(__shfl_sync(FULL, skrow, e));
         for (int b = lane; b < Gm::small_bytes; b += 32) {
             uint32_t byte = 0;
 #pragma unroll
@@ -432,9 +441,9 @@ cudaError_t launch_r3_keygen_lk(const KeyMap &km, int B, int8_t *g_out, int sk_b
                                 cudaStream_t st, int8_t *gfix, int *fix_count, int *fix_keys,
                                 const int *sub_ok, int sub_size) {
     using RG = R3Geo<P, LK, KPT>;
-    k_r3_keygen<P, LK, KPT><<<(B + RG::EPB - 1) / RG::EPB, 32 * RG::WARPS, 0, st>>>(
-        km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, gfix, fix_count, fix_keys,
-        sub_ok, sub_size);
+    SNT_LAUNCH(k_r3_keygen<P, LK, KPT>, (B + RG::EPB - 1) / RG::EPB, 32 * RG::WARPS, 0, st, km, B,
+        g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, gfix, fix_count, fix_keys, sub_ok,
+        sub_size);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "pdl.cuh"
 
 using namespace snt;
 
@@ -371,12 +372,14 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         sig.push_back(g.fuse ? 1 : 0);
         sig.push_back(ctx->inj_P == g.P ? ctx->n_inj : 0);
     }
+    sig.push_back(ctx->pdl);
     if (!(rg.exec && rg.sig == sig && rg.table_off == table_off)) {
         if (rg.exec) cudaGraphExecDestroy(rg.exec);
         rg.exec = nullptr;
         rg.sig.clear();
         const snt_status ss = ensure_ragged_streams(ctx);
         if (ss != SNT_OK) return ss;
+        const PdlScope pdl_scope(ctx->pdl != 0);
         // capture from the tree stream: each parameter set forks onto its
         // own pair of streams (its R/3 work onto the second) and joins back
         SNT_CUDA_R(cudaStreamBeginCapture(ctx->tree, cudaStreamCaptureModeThreadLocal));

@@ -24,6 +24,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "mma_mul.cuh"
+#include "pdl.cuh"
 
 namespace snt {
 
@@ -107,6 +108,7 @@ template <int P, int NT, typename TIn>
 __global__ void __launch_bounds__(NT)
 k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
          int32_t *__restrict__ okv, int *__restrict__ err, int err_bit) {
+    pdl_enter();
     __shared__ int buf[4][InvGeo<P>::LEN];
     const int e = blockIdx.x;
     if (e >= n) return;
@@ -335,6 +337,7 @@ template <int P, int Q = Geo<P>::q>
 __global__ void __launch_bounds__(JumpGeo<P, Q>::NT, 1)
 k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_stride,
               int32_t *__restrict__ okv, int *__restrict__ err, int err_bit, const int *idx) {
+    pdl_enter();
     using JG = JumpGeo<P, Q>;
     constexpr int LEN = JG::LEN, OFF = JG::OFF, NT = JG::NT;
     constexpr bool SMALL = Q < 64;  // every value in {-1, 0, 1}: the l limbs only
@@ -533,8 +536,8 @@ template <int P>
 cudaError_t launch_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
                                cudaStream_t st, const int *idx) {
-    k_rq_inv_jump<P><<<n, JumpGeo<P>::NT, 0, st>>>(n, in, in_stride, out, out_stride, ok, err,
-                                                   err_bit, idx);
+    SNT_LAUNCH(k_rq_inv_jump<P>, n, JumpGeo<P>::NT, 0, st, n, in, in_stride, out, out_stride, ok,
+        err, err_bit, idx);
     return cudaGetLastError();
 }
 
@@ -542,8 +545,8 @@ template <int P>
 cudaError_t launch_r3_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out,
                                long out_stride, int32_t *ok, int *err, int err_bit,
                                cudaStream_t st, const int *idx) {
-    k_rq_inv_jump<P, 3><<<n, JumpGeo<P, 3>::NT, 0, st>>>(n, in, in_stride, out, out_stride, ok, err,
-                                                      err_bit, idx);
+    SNT_LAUNCH(k_rq_inv_jump<P, 3>, n, JumpGeo<P, 3>::NT, 0, st, n, in, in_stride, out, out_stride,
+        ok, err, err_bit, idx);
     return cudaGetLastError();
 }
 
@@ -551,7 +554,8 @@ template <int P>
 cudaError_t launch_rq_inv(int n, const int16_t *in, long in_stride, int16_t *out,
                           long out_stride, int32_t *ok, int *err, int err_bit, cudaStream_t st) {
     constexpr int NT = inv_threads<P>();
-    k_rq_inv<P, NT, int16_t><<<n, NT, 0, st>>>(n, in, in_stride, out, out_stride, ok, err, err_bit);
+    SNT_LAUNCH(k_rq_inv<P, NT, int16_t>, n, NT, 0, st, n, in, in_stride, out, out_stride, ok, err,
+        err_bit);
     return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 
 #include "kernels.h"
 #include "mma_mul.cuh"
+#include "pdl.cuh"
 
 namespace snt {
 
@@ -29,6 +30,7 @@ template <typename K> cudaError_t allow_smem(K kern, size_t bytes) {
 template <int P, int NT, int MODE, int KS, int Q = Prm<P>::q>
 __global__ void __launch_bounds__(32 * MmaGeo<P, NT>::NW * KS)
 k_tree_up_mma(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict__ lout) {
+    pdl_enter();
     using G = Geo<P>;
     using M = MmaGeo<P, NT>;
     extern __shared__ __align__(16) uint8_t sm[];
@@ -72,6 +74,7 @@ k_tree_up_mma(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict_
 template <int P, int NT, int MODE, int KS, int Q = Prm<P>::q>
 __global__ void __launch_bounds__(32 * MmaGeo<P, NT>::NW * KS)
 k_tree_down_mma(const int16_t *__restrict__ lpar, LevelMap lm, int16_t *__restrict__ lch) {
+    pdl_enter();
     using G = Geo<P>;
     using M = MmaGeo<P, NT>;
     extern __shared__ __align__(16) uint8_t sm[];
@@ -163,7 +166,7 @@ cudaError_t up_nt(const int16_t *lin, const LevelMap &lm, int n_out, int16_t *lo
                       (size_t)(KS - 1) * M::NW * 32 * NT * 12 * sizeof(float);
     cudaError_t e = allow_smem(k_tree_up_mma<P, NT, MODE, KS, Q>, sm);
     if (e != cudaSuccess) return e;
-    k_tree_up_mma<P, NT, MODE, KS, Q><<<n_out, 32 * M::NW * KS, sm, st>>>(lin, lm, lout);
+    SNT_LAUNCH(k_tree_up_mma<P, NT, MODE, KS, Q>, n_out, 32 * M::NW * KS, sm, st, lin, lm, lout);
     return cudaGetLastError();
 }
 template <int P, int NT, int MODE, int KS = 1, int Q = Prm<P>::q>
@@ -173,7 +176,7 @@ cudaError_t down_nt(const int16_t *lpar, const LevelMap &lm, int n_par, int16_t 
                       (size_t)(KS - 1) * M::NW * 32 * NT * 2 * 12 * sizeof(float);
     cudaError_t e = allow_smem(k_tree_down_mma<P, NT, MODE, KS, Q>, sm);
     if (e != cudaSuccess) return e;
-    k_tree_down_mma<P, NT, MODE, KS, Q><<<n_par, 32 * M::NW * KS, sm, st>>>(lpar, lm, lch);
+    SNT_LAUNCH(k_tree_down_mma<P, NT, MODE, KS, Q>, n_par, 32 * M::NW * KS, sm, st, lpar, lm, lch);
     return cudaGetLastError();
 }
 // K-split of a level of n products (at most kmax): latency-bound levels only.

@@ -16,6 +16,7 @@
 // Every polynomial is int16, centred, stride Geo<P>::pad.
 #include "kernels.h"
 #include "toeplitz.cuh"
+#include "pdl.cuh"
 
 namespace snt {
 
@@ -25,6 +26,7 @@ namespace snt {
 template <int P, int K>
 __global__ void __launch_bounds__(Tp<P>::NT * K)
 k_tree_up(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict__ lout) {
+    pdl_enter();
     using G = Geo<P>;
     constexpr int NT = Tp<P>::NT;
     __shared__ __align__(16) int As[Tp<P>::p8];
@@ -56,6 +58,7 @@ k_tree_up(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict__ lo
 template <int P, int K>
 __global__ void __launch_bounds__(Tp<P>::NT * K)
 k_tree_down(const int16_t *__restrict__ lpar, LevelMap lm, int16_t *__restrict__ lch) {
+    pdl_enter();
     using G = Geo<P>;
     constexpr int NT = Tp<P>::NT;
     __shared__ __align__(16) int Xs[Tp<P>::p8];
@@ -97,6 +100,7 @@ k_tree_down(const int16_t *__restrict__ lpar, LevelMap lm, int16_t *__restrict__
 template <int P, int S, int K>
 __global__ void __launch_bounds__(SegGeo<P, S>::TS * K)
 k_tree_up_seg(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict__ lout) {
+    pdl_enter();
     using G = Geo<P>;
     __shared__ __align__(16) int As[Tp<P>::p8];
     __shared__ __align__(16) int Es[Tp<P>::ESZ];
@@ -127,6 +131,7 @@ template <int P, int S, int K>
 __global__ void __launch_bounds__(SegGeo<P, S>::TS * K)
 k_tree_down_seg(const int16_t *__restrict__ lpar, LevelMap lm, const int16_t *__restrict__ lch,
                 int16_t *__restrict__ lout) {
+    pdl_enter();
     using G = Geo<P>;
     __shared__ __align__(16) int Xs[Tp<P>::p8];
     __shared__ __align__(16) int Ys[Tp<P>::p8];
@@ -176,8 +181,9 @@ cudaError_t launch_tree_up_seg(const int16_t *lin, const LevelMap &lm, int n_out
                                cudaStream_t st) {
     int S, K;
     seg_plan(n_out, S, K);
-#define SNT_UP_SEG(SS, KK) \
-    k_tree_up_seg<P, SS, KK><<<dim3(n_out, SS), SegGeo<P, SS>::TS * KK, 0, st>>>(lin, lm, lout)
+#define SNT_UP_SEG(SS, KK)                                                             \
+    SNT_LAUNCH(k_tree_up_seg<P, SS, KK>, dim3(n_out, SS), SegGeo<P, SS>::TS * KK, 0, st, \
+               lin, lm, lout)
     switch (S) {
         case 12: SNT_UP_SEG(12, 16); break;
         case 8: SNT_UP_SEG(8, 16); break;
@@ -194,9 +200,9 @@ cudaError_t launch_tree_down_seg(const int16_t *lpar, const LevelMap &lm, int n_
                                  const int16_t *lch, int16_t *lout, cudaStream_t st) {
     int S, K;
     seg_plan(n_par, S, K);
-#define SNT_DOWN_SEG(SS, KK)                                                              \
-    k_tree_down_seg<P, SS, KK><<<dim3(n_par, SS), SegGeo<P, SS>::TS * KK, 0, st>>>(lpar, lm, \
-                                                                                  lch, lout)
+#define SNT_DOWN_SEG(SS, KK)                                                           \
+    SNT_LAUNCH(k_tree_down_seg<P, SS, KK>, dim3(n_par, SS), SegGeo<P, SS>::TS * KK, 0, st, \
+               lpar, lm, lch, lout)
     switch (S) {
         case 12: SNT_DOWN_SEG(12, 16); break;
         case 8: SNT_DOWN_SEG(8, 16); break;
@@ -243,10 +249,10 @@ cudaError_t launch_tree_up(const int16_t *lin, const LevelMap &lm, int n_out, in
                            cudaStream_t st, int max_split) {
     constexpr int NT = Tp<P>::NT;
     switch (split_for(n_out, max_split)) {
-        case 8: k_tree_up<P, 8><<<n_out, NT * 8, 0, st>>>(lin, lm, lout); break;
-        case 4: k_tree_up<P, 4><<<n_out, NT * 4, 0, st>>>(lin, lm, lout); break;
-        case 2: k_tree_up<P, 2><<<n_out, NT * 2, 0, st>>>(lin, lm, lout); break;
-        default: k_tree_up<P, 1><<<n_out, NT, 0, st>>>(lin, lm, lout); break;
+        case 8: SNT_LAUNCH(k_tree_up<P, 8>, n_out, NT * 8, 0, st, lin, lm, lout); break;
+        case 4: SNT_LAUNCH(k_tree_up<P, 4>, n_out, NT * 4, 0, st, lin, lm, lout); break;
+        case 2: SNT_LAUNCH(k_tree_up<P, 2>, n_out, NT * 2, 0, st, lin, lm, lout); break;
+        default: SNT_LAUNCH(k_tree_up<P, 1>, n_out, NT, 0, st, lin, lm, lout); break;
     }
     return cudaGetLastError();
 }
@@ -256,10 +262,10 @@ cudaError_t launch_tree_down(const int16_t *lpar, const LevelMap &lm, int n_par,
                              cudaStream_t st, int max_split) {
     constexpr int NT = Tp<P>::NT;
     switch (split_for(n_par, max_split)) {
-        case 8: k_tree_down<P, 8><<<n_par, NT * 8, 0, st>>>(lpar, lm, lch); break;
-        case 4: k_tree_down<P, 4><<<n_par, NT * 4, 0, st>>>(lpar, lm, lch); break;
-        case 2: k_tree_down<P, 2><<<n_par, NT * 2, 0, st>>>(lpar, lm, lch); break;
-        default: k_tree_down<P, 1><<<n_par, NT, 0, st>>>(lpar, lm, lch); break;
+        case 8: SNT_LAUNCH(k_tree_down<P, 8>, n_par, NT * 8, 0, st, lpar, lm, lch); break;
+        case 4: SNT_LAUNCH(k_tree_down<P, 4>, n_par, NT * 4, 0, st, lpar, lm, lch); break;
+        case 2: SNT_LAUNCH(k_tree_down<P, 2>, n_par, NT * 2, 0, st, lpar, lm, lch); break;
+        default: SNT_LAUNCH(k_tree_down<P, 1>, n_par, NT, 0, st, lpar, lm, lch); break;
     }
     return cudaGetLastError();
 }

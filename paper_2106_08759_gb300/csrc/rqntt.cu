@@ -38,6 +38,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "pdl.cuh"
 
 namespace snt {
 
@@ -331,6 +332,7 @@ k_mul_batch_ntt(const int16_t *__restrict__ a, const int16_t *__restrict__ b,
 template <int P>
 __global__ void __launch_bounds__(ntt_threads<P, 1>())
 k_tree_up_ntt(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict__ lout) {
+    pdl_enter();
     using G = Geo<P>;
     extern __shared__ __align__(16) int ntt_dyn[];
     auto &sm = *reinterpret_cast<NttSmem<P, 1> *>(ntt_dyn);
@@ -354,6 +356,7 @@ k_tree_up_ntt(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict_
 template <int P>
 __global__ void __launch_bounds__(ntt_threads<P, 2>())
 k_tree_down_ntt(const int16_t *__restrict__ lpar, LevelMap lm, int16_t *__restrict__ lch) {
+    pdl_enter();
     using G = Geo<P>;
     extern __shared__ __align__(16) int ntt_dyn[];
     auto &sm = *reinterpret_cast<NttSmem<P, 2> *>(ntt_dyn);
@@ -403,7 +406,8 @@ cudaError_t launch_tree_up_ntt(const int16_t *lin, const LevelMap &lm, int n_out
                                cudaStream_t st) {
     cudaError_t e = ntt_prepare<P, 1>(k_tree_up_ntt<P>);
     if (e != cudaSuccess) return e;
-    k_tree_up_ntt<P><<<n_out, ntt_threads<P, 1>(), sizeof(NttSmem<P, 1>), st>>>(lin, lm, lout);
+    SNT_LAUNCH(k_tree_up_ntt<P>, n_out, ntt_threads<P, 1>(), sizeof(NttSmem<P, 1>), st, lin, lm,
+        lout);
     return cudaGetLastError();
 }
 
@@ -412,7 +416,8 @@ cudaError_t launch_tree_down_ntt(const int16_t *lpar, const LevelMap &lm, int n_
                                  cudaStream_t st) {
     cudaError_t e = ntt_prepare<P, 2>(k_tree_down_ntt<P>);
     if (e != cudaSuccess) return e;
-    k_tree_down_ntt<P><<<n_par, ntt_threads<P, 2>(), sizeof(NttSmem<P, 2>), st>>>(lpar, lm, lch);
+    SNT_LAUNCH(k_tree_down_ntt<P>, n_par, ntt_threads<P, 2>(), sizeof(NttSmem<P, 2>), st, lpar, lm,
+        lch);
     return cudaGetLastError();
 }
 

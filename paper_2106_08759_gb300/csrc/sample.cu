@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "short.cuh"
+#include "pdl.cuh"
 
 namespace snt {
 
@@ -27,6 +28,7 @@ k_sample_f(KeyMap km, int nkeys, int16_t *__restrict__ leaves, int sk_bytes, int
            int8_t *__restrict__ g_out, const uint64_t *__restrict__ inj_idx,
            const int8_t *__restrict__ inj_g, int n_inj, int *__restrict__ fix_count,
            int16_t *__restrict__ g16_out) {
+    pdl_enter();
     using G = Geo<P>;
     static_assert(G::pad % 32 == 0 && G::pad <= 1024, "row padding");
     const int lane = threadIdx.x & 31;
@@ -124,8 +126,8 @@ cudaError_t launch_sample_f(const KeyMap &km, int nkeys, int16_t *leaves, int sk
                             int rho_off, cudaStream_t st, int8_t *g_out,
                             const uint64_t *inj_idx, const int8_t *inj_g, int n_inj,
                             int *fix_count, int16_t *g16_out) {
-    k_sample_f<P><<<(nkeys + 3) / 4, 128, 0, st>>>(km, nkeys, leaves, sk_bytes, rho_off, g_out, inj_idx,
-                                         inj_g, n_inj, fix_count, g16_out);
+    SNT_LAUNCH(k_sample_f<P>, (nkeys + 3) / 4, 128, 0, st, km, nkeys, leaves, sk_bytes, rho_off,
+        g_out, inj_idx, inj_g, n_inj, fix_count, g16_out);
     return cudaGetLastError();
 }
 

@@ -64,15 +64,19 @@ __device__ __forceinline__ void sha512_block(uint64_t (&H)[8], uint64_t (&W)[16]
 }
 
 // The 80 rounds of one block with W_t + K_t given per round (wk[t][lane]):
-// the same round as sha512_block, the schedule computed elsewhere.
+// the same round as sha512_block, the schedule computed elsewhere.  The 16
+// table entries of a group of rounds are read before the group runs.
 __device__ __forceinline__ void sha512_rounds_wk(uint64_t (&H)[8], const uint64_t (*wk)[32],
                                                  int lane) {
     uint64_t a = H[0], b = H[1], c = H[2], d = H[3], e = H[4], f = H[5], g = H[6], h = H[7];
 #pragma unroll 1
     for (int r = 0; r < 80; r += 16) {
+        uint64_t kw[16];
+#pragma unroll
+        for (int tt = 0; tt < 16; ++tt) kw[tt] = wk[r + tt][lane];
 #pragma unroll
         for (int tt = 0; tt < 16; ++tt) {
-            const uint64_t hkw = h + wk[r + tt][lane];
+            const uint64_t hkw = h + kw[tt];
             const uint64_t dhkw = d + hkw;
             const uint64_t S1 = rotr(e, 14) ^ rotr(e, 18) ^ rotr(e, 41);
             const uint64_t ch = (e & f) ^ (~e & g);

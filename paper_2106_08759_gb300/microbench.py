@@ -37,6 +37,13 @@ def main():
     ap.add_argument("--ragged-only", type=int, default=0, metavar="N",
                     help="only run the 256-batch ragged workload N times with the given options "
                          "(a small, fixed target for a profiler)")
+    ap.add_argument("--tuned", action="store_true",
+                    help="with --ragged-only: autotune each parameter set for batches of up to "
+                         "2048 keys first, as the bench does; with --keygen-only: autotune "
+                         "(761, B) first.  The last call is bracketed by cudaProfilerStart/Stop "
+                         "(ncu --profile-from-start off captures it alone).  Under a profiler "
+                         "the autotuner times serialised kernels and picks other layouts: pin "
+                         "the layouts with --opt for a profile")
     ap.add_argument("--kem-only", type=int, default=0, metavar="N",
                     help="only run N encapsulations and decapsulations of sntrup761 keys, twice")
     ap.add_argument("--mul-only", type=int, default=0, metavar="N",
@@ -89,10 +96,19 @@ def main():
             for o in args.opt:
                 name, val = o.split("=")
                 rc.set_option(getattr(snt, "SNT_OPT_" + name), int(val))
+            if args.tuned:
+                for x in (653, 761, 857):
+                    rc.autotune(x, 2048)
+            rc.sync()
             for it in range(args.ragged_only):
+                last = it == args.ragged_only - 1
+                if last:
+                    torch.cuda.profiler.start()
                 snt.snt_batch_keygen_ragged(rc, [int(x) for x in ps], [int(x) for x in sizes],
                                             [it * 1000 + i for i in range(256)], firsts, pks, sks)
-            rc.sync()
+                rc.sync()
+                if last:
+                    torch.cuda.profiler.stop()
         print(json.dumps({"ragged_only": args.ragged_only, "keys": int(sizes.sum())}))
         ctx.close()
         return
@@ -139,15 +155,24 @@ def main():
             name, val = o.split("=")
             ctx.set_option(getattr(snt, "SNT_OPT_" + name), int(val))
         B = args.keygen_only
+        tuned = ctx.autotune(P, B) if args.tuned else None
         pkb, skb, _, _ = snt.snt_param_sizes(P)
         pk = torch.empty(B * pkb, dtype=torch.uint8, device=dev)
         sk = torch.empty(B * skb, dtype=torch.uint8, device=dev)
         for i in range(args.reps):
             flush.zero_()
+            last = i == args.reps - 1
+            if last:
+                torch.cuda.synchronize()
+                torch.cuda.profiler.start()
             snt.snt_batch_keygen(ctx, P, 1, i * B, B, pk, sk, st)
+            if last:
+                torch.cuda.synchronize()
+                ctx.sync()
+                torch.cuda.profiler.stop()
         torch.cuda.synchronize()
         ctx.sync()
-        print(json.dumps({"keygen_only": B, "reps": args.reps}))
+        print(json.dumps({"keygen_only": B, "reps": args.reps, "tuned": tuned}))
         ctx.close()
         return
 

@@ -490,3 +490,44 @@ def test_sntrup653_first_draw_batch_with_many_redraws(snt, ctx, pool):
     assert len(redrawn) > 10  # the fix-up had real work
     idx = np.array(sorted(set(redrawn) | {0, 1, B - 1}))
     assert pool.bad_keys(653, seed, idx, pk[idx], sk[idx]) == []
+
+
+@pytest.mark.parametrize("B,roots,r3mode,engine", [
+    (4096, 64, 2, 3), (4096, 64, 1, 1), (96, 8, 0, 1), (33, 1, 1, 0), (5, 1, 2, 2), (1, 1, 0, 3)])
+def test_programmatic_dependent_launch_gives_the_same_keys(snt, ctx, B, roots, r3mode, engine):
+    # the chain kernels launched with programmatic stream serialization (the
+    # default) and plainly: same bytes, and the oracle's on a few keys
+    assert ctx.get_option(snt.SNT_OPT_PDL) == 1
+    ctx.set_option(snt.SNT_OPT_ROOTS, roots)
+    ctx.set_option(snt.SNT_OPT_R3_MODE, r3mode)
+    ctx.set_option(snt.SNT_OPT_RQ_ENGINE, engine)
+    try:
+        on = gpu_keygen(snt, ctx, 761, 21, 7, B)
+        ctx.set_option(snt.SNT_OPT_PDL, 0)
+        off = gpu_keygen(snt, ctx, 761, 21, 7, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_PDL, 1)
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+        ctx.set_option(snt.SNT_OPT_R3_MODE, 0)
+        ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 1)
+    assert np.array_equal(on[0], off[0]) and np.array_equal(on[1], off[1])
+    for j in sorted({0, B // 2, B - 1}):
+        opk, osk, _ = oracle.keygen(761, 21, 7 + j)
+        assert np.array_equal(on[0][j], opk) and np.array_equal(on[1][j], osk), j
+
+
+@pytest.mark.parametrize("shift", [1, 6, 13])
+def test_unaligned_output_buffers(snt, ctx, shift):
+    # pk / sk at an odd or unaligned device address: the hash kernel copies
+    # the public keys with 16-byte words in phase with the source address
+    import torch
+    B = 70
+    pkb, skb, _, _ = snt.snt_param_sizes(761)
+    ref = gpu_keygen(snt, ctx, 761, 8, 123, B)
+    pk = torch.zeros(B * pkb + 64, dtype=torch.uint8, device="cuda")
+    sk = torch.zeros(B * skb + 64, dtype=torch.uint8, device="cuda")
+    snt.snt_batch_keygen(ctx, 761, 8, 123, B, pk[shift:shift + B * pkb], sk[shift:shift + B * skb])
+    ctx.sync()
+    got_pk = pk.cpu().numpy()[shift:shift + B * pkb].reshape(B, pkb)
+    got_sk = sk.cpu().numpy()[shift:shift + B * skb].reshape(B, skb)
+    assert np.array_equal(got_pk, ref[0]) and np.array_equal(got_sk, ref[1])

@@ -114,3 +114,55 @@ def test_ragged_redraws_injected_zero_divisors(snt, r3_mode):
         inj = {k - f: b for k, b in zip(keys, bads) if P == 761 and f <= k < f + B}
         rpk, rsk = oracle.keygen_batch(P, s, f, B, g_inject=inj)
         assert np.array_equal(pk, rpk) and np.array_equal(sk, rsk), (P, B)
+
+
+def test_ragged_with_and_without_programmatic_launch(snt):
+    # the graph is captured again when the launch mode changes; same bytes
+    Ps = [653, 761, 857, 761, 653]
+    Bs = [40, 129, 7, 1, 300]
+    seeds = [31, 32, 33, 34, 35]
+    firsts = [0, 50, 200, 300, 400]
+    with snt.Context(0, 256 << 20) as ctx:
+        ctx.set_option(snt.SNT_OPT_R3_MODE, 2)
+        on = _run_ragged(snt, ctx, Ps, Bs, seeds, firsts)
+        ctx.set_option(snt.SNT_OPT_PDL, 0)
+        off = _run_ragged(snt, ctx, Ps, Bs, seeds, firsts)
+        for (a, b), (c, d) in zip(on, off):
+            assert np.array_equal(a, c) and np.array_equal(b, d)
+        for i in (0, 2, 4):
+            opk, osk, _ = oracle.keygen(Ps[i], seeds[i], firsts[i] + Bs[i] - 1)
+            assert np.array_equal(on[i][0][-1], opk) and np.array_equal(on[i][1][-1], osk)
+
+
+def test_ragged_batches_in_one_buffer_at_odd_offsets(snt):
+    # every batch's rows inside one buffer, some batches adjacent (their rows
+    # form one contiguous run for the hash kernel), some separated by an odd
+    # gap; each batch must equal its single-batch call
+    import torch
+    Ps = [761, 761, 761, 653, 653, 857, 761]
+    Bs = [3, 40, 1, 20, 17, 9, 33]
+    gaps = [5, 0, 0, 3, 0, 1, 7]
+    seeds = [41, 42, 43, 44, 45, 46, 47]
+    firsts = [0, 10, 60, 70, 100, 130, 150]
+    pk_all = torch.zeros(1 << 18, dtype=torch.uint8, device="cuda")
+    sk_all = torch.zeros(1 << 18, dtype=torch.uint8, device="cuda")
+    pks, sks, offs = [], [], []
+    o_pk = o_sk = 0
+    for P, B, gap in zip(Ps, Bs, gaps):
+        pkb, skb, _, _ = snt.snt_param_sizes(P)
+        o_pk += gap
+        o_sk += gap
+        pks.append(pk_all[o_pk:o_pk + B * pkb])
+        sks.append(sk_all[o_sk:o_sk + B * skb])
+        offs.append((o_pk, o_sk, pkb, skb))
+        o_pk += B * pkb
+        o_sk += B * skb
+    with snt.Context(0, 256 << 20) as ctx:
+        snt.snt_batch_keygen_ragged(ctx, Ps, Bs, seeds, firsts, pks, sks)
+        ctx.sync()
+        hp, hs = pk_all.cpu().numpy(), sk_all.cpu().numpy()
+        for i, (P, B) in enumerate(zip(Ps, Bs)):
+            a, b, pkb, skb = offs[i]
+            rpk, rsk = _single(snt, ctx, P, B, seeds[i], firsts[i])
+            assert np.array_equal(hp[a:a + B * pkb].reshape(B, pkb), rpk), i
+            assert np.array_equal(hs[b:b + B * skb].reshape(B, skb), rsk), i
