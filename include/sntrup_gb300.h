@@ -275,11 +275,12 @@ typedef enum {
     /* largest number of thread groups one R/q product of a narrow tree level
      * is split over: 1, 2, 4 or 8 */
     SNT_OPT_TREE_SPLIT = 2,
-    /* where the per-key R/3 inversions run: 0 first, on the tree's stream;
-     * 1 on a second stream concurrent with the whole tree; 2 on that
-     * stream from the up-sweep's first narrow level (fewer than
-     * 256 products) up to the down-sweep's first wide level, so they fill the
-     * SMs the narrow levels and the root inversion leave idle */
+    /* where the R/3 inversions (per key or batched) run: 0 first, on the
+     * tree's stream; 1 on a second stream concurrent with the whole tree; 2
+     * on that stream from the up-sweep's first narrow level (fewer than 256
+     * products), so they fill the SMs the narrow levels and the root
+     * inversion leave idle; 3 on that stream from the end of the up-sweep,
+     * so that the R/3 work starts beside the root inversions */
     SNT_OPT_R3_OVERLAP = 3,
     /* 1: each product of a tree level with at most 64 products is split by
      * output segments over several CTAs (up to 12 SMs per product) instead of

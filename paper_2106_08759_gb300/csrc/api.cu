@@ -77,6 +77,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     // resampling list of the deferred R/3 kernel
     int *fix_count = reinterpret_cast<int *>(arena + fix_offset(pi, B));
     int *fix_keys = fix_count + 1;
+    int *fix_slot = fix_keys + B;  // by key: the R/3 screen's slot, or -1
     int8_t *gfix = reinterpret_cast<int8_t *>(arena + fix_offset(pi, B) + fix_list_bytes(B));
     const int Bi = (int)B;
     const int sb = pi.small_bytes;
@@ -92,6 +93,10 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     //   overlap 2: on the auxiliary stream from the up-sweep's first narrow
     //              level (fewer than kNarrow products), so they fill the SMs
     //              that the narrow levels and the root inversion leave idle;
+    //   overlap 3: on the auxiliary stream from the end of the up-sweep, so
+    //              that the R/3 forest's wide levels fill the SMs the root
+    //              inversions leave idle and its own (latency-bound) roots
+    //              run beside the R/q down-sweep;
     // and are joined at the end of the call, before the fix-up of the listed
     // keys (h, pk and the pk hash again with the final g).
     const cudaStream_t caller = st;
@@ -125,6 +130,14 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
         const snt_status sf = r3_factors_for(ctx, P, fac);
         if (sf != SNT_OK) return sf;
     }
+    // mode 2: the first draws screened against the small factors first
+    // (sntrup653's cubic divides one g in 27: without the screen most
+    // subtrees' roots would fail)
+    R3Screen scr;
+    if (r3opt) {
+        const snt_status ss = r3_screen_for(ctx, P, scr);
+        if (ss != SNT_OK) return ss;
+    }
     int16_t *nodes3 = reinterpret_cast<int16_t *>(arena + r3_offset(pi, B));
     int32_t *r3ok = reinterpret_cast<int32_t *>(arena + r3_offset(pi, B) + r3_scratch(pi, B) -
                                                 kR3OkBytes);
@@ -144,6 +157,9 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
                 SNT_CUDA(launch_r3_check<P>(km, Bi, gbuf, nodes3, fac, ctx->d_err, r3s));
                 SNT_CUDA(cudaEventRecord(ctx->ev_gready, r3s));
             }
+            if (r3opt && scr.n > 0)
+                SNT_CUDA(launch_r3_screen<P>(km, Bi, gbuf, nodes3, scr, gfix, fix_count, fix_keys,
+                                             fix_slot, ctx->d_err, r3s));
             const Forest f3 = make_forest(B, roots);
             const int sub3 = (int)(B / f3.K);
             const Tree &t3 = f3.t;
@@ -167,7 +183,8 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
             if (r3opt)  // subtrees whose root did not invert: per key, with redraws
                 SNT_CUDA(launch_r3_keygen<P>(km, Bi, gbuf, pi.sk_bytes, sb, ctx->d_inj_idx,
                                              ctx->d_inj_g, n_inj, ctx->d_err, r3s, lanes, kpt,
-                                             gfix, fix_count, fix_keys, r3ok, sub3));
+                                             gfix, fix_count, fix_keys, r3ok, sub3,
+                                             scr.n > 0 ? fix_slot : nullptr));
         } else {
             SNT_CUDA(launch_r3_keygen<P>(km, Bi, gbuf, pi.sk_bytes, sb, ctx->d_inj_idx,
                                          ctx->d_inj_g, n_inj, ctx->d_err, r3s, lanes, kpt, gfix,
@@ -233,7 +250,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
             for (int q = 0; q < nparts; ++q) {
                 const cudaStream_t sq = ps[q];
                 for (int l = 1; l <= L; ++l) {
-                    if (q == 0 && !forked && t.n[l] < kNarrow) {
+                    if (q == 0 && !forked && mode == 2 && t.n[l] < kNarrow) {
                         const snt_status s3 = fork_r3();
                         if (s3 != SNT_OK) return s3;
                         forked = true;
@@ -314,7 +331,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
             return SNT_OK;
         }
         for (int l = 1; l <= L; ++l) {
-            if (!forked && t.n[l] < kNarrow) {
+            if (!forked && mode == 2 && t.n[l] < kNarrow) {
                 const snt_status s3 = fork_r3();
                 if (s3 != SNT_OK) return s3;
                 forked = true;
@@ -565,6 +582,8 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     if (ctx->ev_sready) cudaEventDestroy(ctx->ev_sready);
     for (uint32_t *f : ctx->d_r3fac)
         if (f) cudaFree(f);
+    for (uint32_t *f : ctx->d_r3screen)
+        if (f) cudaFree(f);
     if (ctx->ragged.exec) cudaGraphExecDestroy(ctx->ragged.exec);
     for (int j = 0; j < 3; ++j) {
         if (ctx->rg_main[j]) cudaStreamDestroy(ctx->rg_main[j]);
@@ -781,7 +800,7 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             ctx->tree_split = value;
             return SNT_OK;
         case SNT_OPT_R3_OVERLAP:
-            if (value < 0 || value > 2) return set_error(SNT_EINVAL, "R/3 overlap is 0, 1 or 2");
+            if (value < 0 || value > 3) return set_error(SNT_EINVAL, "R/3 overlap is 0 .. 3");
             ctx->r3_overlap = value;
             return SNT_OK;
         case SNT_OPT_NARROW_SEG:
@@ -877,7 +896,7 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
     std::vector<snt_ctx::Tuned> cands;
     for (int la : {4, 8, 32})
         for (int kp : {1}) {  // two elements per lane group measured slower at every size
-            for (int ov : {0, 1, 2}) {
+            for (int ov : {0, 1, 2, 3}) {
                 for (int ti : {1, 2})
                     for (int rt : {1, 4, 16, 64, 128, 256})
                         for (int r3m : {0, 1, 2}) {

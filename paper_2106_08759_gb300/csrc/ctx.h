@@ -45,6 +45,7 @@ struct snt_ctx {
     cudaStream_t side = nullptr;  // low priority: leaf-pair products s beside the root inversions
     cudaEvent_t ev_sfork = nullptr, ev_sready = nullptr;  // fork to / join from the side stream
     uint32_t *d_r3fac[3] = {nullptr, nullptr, nullptr};  // F_3 factors per parameter set
+    uint32_t *d_r3screen[3] = {nullptr, nullptr, nullptr};  // small factors' remainder tables
     bool timing = false;
     cudaEvent_t ev_phase[snt::kPhaseEvents] = {};
     int r3_lanes = snt::kDefaultR3Lanes;
@@ -90,4 +91,5 @@ inline int bbucket(size_t B) {
 // Device copy of the F_3 factors of x^P - x - 1 for the R/3 batch path
 // (computed on the host on first use; r3batch.cu).
 snt_status r3_factors_for(snt_ctx *ctx, int P, R3Factors &out);
+snt_status r3_screen_for(snt_ctx *ctx, int P, R3Screen &out);
 }  // namespace snt

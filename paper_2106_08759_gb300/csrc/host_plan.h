@@ -178,8 +178,9 @@ inline size_t narrow_scratch(const ParamInfo &pi) {
     return 2 * align256((size_t)2 * kSegMaxNodes * pi.pad * sizeof(int16_t));
 }
 // ... then the resampling list of the deferred R/3 kernel: a count, B key
-// indices and B rows of g (int8, stride pad).
-inline size_t fix_list_bytes(size_t B) { return align256(sizeof(int) * (1 + B)); }
+// indices, B slot indices by key (the R/3 screen's, for the per-key
+// fall-back) and B rows of g (int8, stride pad).
+inline size_t fix_list_bytes(size_t B) { return align256(sizeof(int) * (1 + 2 * B)); }
 inline size_t fix_scratch(const ParamInfo &pi, size_t B) {
     return fix_list_bytes(B) + align256(B * pi.pad);
 }

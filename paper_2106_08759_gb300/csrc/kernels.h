@@ -43,6 +43,15 @@ struct R3Factors {
     int deg[kMaxR3Factors] = {}, words[kMaxR3Factors] = {}, off[kMaxR3Factors] = {};
     const uint32_t *w = nullptr;
 };
+// Remainder tables of the factors of degree <= kScreenMaxDeg: for factor j
+// and 0 <= i < p, t[2 (j p + i)] and t[2 (j p + i) + 1] are the bit planes
+// (coefficient nonzero, coefficient -1) of x^i mod m_j.
+constexpr int kScreenMaxDeg = 16;
+constexpr int kMaxScreen = 2;
+struct R3Screen {
+    int n = 0;
+    const uint32_t *t = nullptr;
+};
 
 // Nodes of one tree level.  nb > 0: a forest of batches with per-level node
 // prefix sums (pre_in / pre_out, nb + 1 entries each).  Otherwise equal
@@ -120,14 +129,16 @@ cudaError_t launch_sample_f(const KeyMap &km, int nkeys, int16_t *leaves, int sk
 // gfix != null: deferred form (attempt 0 read from g_out, g_out untouched,
 // resampled keys appended to fix_keys / gfix rows, *fix_count of them).
 // sub_ok != null: fall-back form, only warps holding a key of a subtree
-// (sub_size keys each) whose flag is 0 do any work.
+// (sub_size keys each) whose flag is 0 do any work.  fix_slot (optional): a
+// key with fix_slot[key] >= 0 reuses that slot of the list instead of
+// appending one.
 template <int P>
 cudaError_t launch_r3_keygen(const KeyMap &km, int nkeys, int8_t *g_out, int sk_bytes,
                              int sk_off, const uint64_t *inj_idx, const int8_t *inj_g, int n_inj,
                              int *err, cudaStream_t st, int lanes, int kpt = 1,
                              int8_t *gfix = nullptr, int *fix_count = nullptr,
                              int *fix_keys = nullptr, const int *sub_ok = nullptr,
-                             int sub_size = 0);
+                             int sub_size = 0, const int *fix_slot = nullptr);
 template <int P>
 cudaError_t launch_r3_inv(int n, const int8_t *g, int8_t *out, int32_t *ok, cudaStream_t st,
                           int lanes, int kpt = 1);
@@ -204,6 +215,16 @@ template <int P>
 cudaError_t launch_r3_encode_v(const KeyMap &km, int B, const int16_t *v3, int sk_bytes,
                                int sk_off, cudaStream_t st, const int *sub_ok = nullptr,
                                int sub_size = 0);
+// Screen of the first draws before the R/3 forest of mode 2 (warp per key):
+// g is redrawn while a factor of degree <= kScreenMaxDeg divides it; a
+// redrawn key gets its final-screen g in its R/3 leaf, a slot of the
+// resampling list (fix_keys, gfix rows, *fix_count) and fix_slot[key] = the
+// slot (-1 for a key kept), so that the per-key fall-back of a subtree whose
+// root still fails can reuse the slot.
+template <int P>
+cudaError_t launch_r3_screen(const KeyMap &km, int B, const int8_t *gbuf, int16_t *leaves3,
+                             const R3Screen &scr, int8_t *gfix, int *fix_count, int *fix_keys,
+                             int *fix_slot, int *err, cudaStream_t st);
 // Jump-divstep inversions in R/3 (entries mod 3, centred int16 rows); ok
 // (optional) receives 1 per invertible element; err (optional) gets err_bit
 // for a non-invertible one.

@@ -122,7 +122,31 @@ struct HostFactors {
     bool done = false, ok = false;
     R3Factors f;             // host copy of the metadata (pointer filled per device)
     std::vector<uint32_t> w; // planes of all factors
+    int screen_n = 0;        // factors of degree <= kScreenMaxDeg
+    std::vector<uint32_t> screen;  // their remainder tables (R3Screen layout)
 };
+
+// Remainder table of factor m (degree d <= kScreenMaxDeg): the planes of
+// x^i mod m for 0 <= i < p, appended to t.  x^(i+1) mod m is x (x^i mod m)
+// with its degree-d term folded back (m monic: x^d = x^d - m).
+void screen_table(const Poly &m, int p, std::vector<uint32_t> &t) {
+    const int d = deg(m);
+    Poly r(d, 0);
+    r[0] = 1;  // x^0
+    for (int i = 0; i < p; ++i) {
+        uint32_t pm = 0, ps = 0;
+        for (int k = 0; k < d; ++k) {
+            pm |= (uint32_t)(r[k] != 0) << k;
+            ps |= (uint32_t)(r[k] == 2) << k;
+        }
+        t.push_back(pm);
+        t.push_back(ps);
+        const uint8_t top = r[d - 1];
+        for (int k = d - 1; k > 0; --k) r[k] = r[k - 1];
+        r[0] = 0;
+        for (int k = 0; k < d; ++k) r[k] = (uint8_t)((r[k] + 3 * 3 - top * m[k]) % 3);
+    }
+}
 
 // Bit planes of the factors: per factor, its words of m (coefficient
 // nonzero) then its words of s (coefficient is -1 = 2).
@@ -150,6 +174,10 @@ HostFactors build_factors(int p) {
                 H.w.push_back(v);
             }
         off += 2 * words;
+        if (d <= kScreenMaxDeg && H.screen_n < kMaxScreen) {
+            screen_table(fs[i], p, H.screen);
+            ++H.screen_n;
+        }
     }
     H.f.total_words = off;
     H.ok = true;
@@ -185,6 +213,37 @@ snt_status r3_factors_for(snt_ctx *ctx, int P, R3Factors &out) {
         }
     }
     out.w = ctx->d_r3fac[pi_];
+    return SNT_OK;
+}
+
+// Remainder tables of the small factors of parameter set P for this context
+// (none for sntrup761 and sntrup857, whose smallest factors have degree 19
+// and 25; sntrup653's of degree 3 and 16).
+snt_status r3_screen_for(snt_ctx *ctx, int P, R3Screen &out) {
+    const int pi_ = pidx(P);
+    std::vector<uint32_t> t;
+    {
+        std::lock_guard<std::mutex> lk(g_fac_mu);
+        if (!g_fac[pi_].done) g_fac[pi_] = build_factors(P);
+        if (!g_fac[pi_].ok)
+            return set_error(SNT_EINTERNAL, "x^%d - x - 1 has repeated factor degrees over F_3", P);
+        out.n = g_fac[pi_].screen_n;
+        t = g_fac[pi_].screen;
+    }
+    out.t = nullptr;
+    if (out.n == 0) return SNT_OK;
+    if (!ctx->d_r3screen[pi_]) {
+        cudaError_t e = cudaMalloc(&ctx->d_r3screen[pi_], t.size() * sizeof(uint32_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ctx->d_r3screen[pi_], t.data(), t.size() * sizeof(uint32_t),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (ctx->d_r3screen[pi_]) cudaFree(ctx->d_r3screen[pi_]);
+            ctx->d_r3screen[pi_] = nullptr;
+            return set_error(SNT_ECUDA, "R/3 screen table: %s", cudaGetErrorString(e));
+        }
+    }
+    out.t = ctx->d_r3screen[pi_];
     return SNT_OK;
 }
 
@@ -290,6 +349,115 @@ k_r3_check(KeyMap km, int B, int8_t *__restrict__ gbuf, int16_t *__restrict__ le
     }
 }
 
+// a + b in F_3 on 32 trits as bit planes (m: nonzero, s: -1, s within m).
+__device__ __forceinline__ void f3_add(uint32_t &am, uint32_t &as, uint32_t bm, uint32_t bs) {
+    const uint32_t both = am & bm;
+    const uint32_t nm = (am | bm) & ~(both & (as ^ bs));
+    const uint32_t ns = ((am & (as ^ bm)) | (~am & bs)) & nm;
+    am = nm;
+    as = ns;
+}
+
+// The screen before the R/3 forest of mode 2: one warp per key, lane L
+// holding trits 32 L .. 32 L + 31 of g as bit planes.  For attempt a = 0, 1,
+// ... (a = 0: the first draw from gbuf; otherwise stream 0 attempt a), the
+// remainder of g modulo each small factor m_j is sum_i g_i (x^i mod m_j),
+// each lane adding its own terms from the table and the warp adding the
+// lanes' sums; g passes when no remainder is zero (about 1 - 1/27 per draw
+// for sntrup653, whose cubic factor divides one draw in 27).
+template <int P>
+__global__ void __launch_bounds__(128)
+k_r3_screen(KeyMap km, int B, const int8_t *__restrict__ gbuf, int16_t *__restrict__ leaves3,
+            R3Screen scr, int8_t *__restrict__ gfix, int *__restrict__ fix_count,
+            int *__restrict__ fix_keys, int *__restrict__ fix_slot, int *__restrict__ err) {
+    pdl_enter();
+    using G = Geo<P>;
+    constexpr int W = (P + 31) / 32;
+    extern __shared__ uint32_t tab[];  // scr.n tables of P plane pairs
+    for (int i = threadIdx.x; i < 2 * P * scr.n; i += blockDim.x) tab[i] = scr.t[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int key = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (key >= B) return;  // whole warp
+    const BatchDesc bd = key_batch(km, key);
+    const uint64_t kidx = bd.first + (uint64_t)(key - bd.key_base);
+    const int8_t *grow = gbuf + (size_t)key * G::pad;
+    bool ok = false;
+    uint32_t gm = 0, gs = 0;
+    int att = 0;
+    for (; att < kMaxGAttempts && !ok; ++att) {
+        gm = 0; gs = 0;
+        if (lane < W) {
+            if (att == 0) {
+                for (int b = 0; b < 32; ++b) {
+                    const int i = 32 * lane + b;
+                    const int c = i < P ? grow[i] : 0;
+                    gm |= (uint32_t)(c != 0) << b;
+                    gs |= (uint32_t)(c < 0) << b;
+                }
+            } else {
+                // g_i = floor(3 (u_i mod 2^30) / 2^30) - 1, word u_i of stream 0, attempt att
+                for (int blk = 8 * lane; blk < 8 * lane + 8; ++blk) {
+                    uint32_t r[4];
+                    rand_block(bd.seed, kidx, STREAM_G, (uint32_t)att, (uint32_t)blk, r);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int i = 4 * blk + j;
+                        if (i < P) {
+                            const int c = (int)(((unsigned long long)(r[j] & 0x3fffffffu) * 3u) >> 30) - 1;
+                            gm |= (uint32_t)(c != 0) << (i & 31);
+                            gs |= (uint32_t)(c < 0) << (i & 31);
+                        }
+                    }
+                }
+            }
+        }
+        ok = true;
+        for (int j = 0; j < scr.n; ++j) {
+            const uint32_t *tj = tab + 2 * P * j;
+            uint32_t am = 0, as = 0;
+            if (lane < W)
+                for (int b = 0; b < 32; ++b) {
+                    const int i = 32 * lane + b;
+                    if (i < P && ((gm >> b) & 1u)) {
+                        const uint32_t tm = tj[2 * i];
+                        const uint32_t ts = tj[2 * i + 1] ^ (((gs >> b) & 1u) ? tm : 0u);
+                        f3_add(am, as, tm, ts);
+                    }
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint32_t om = __shfl_xor_sync(kFull, am, o), os = __shfl_xor_sync(kFull, as, o);
+                f3_add(am, as, om, os);
+            }
+            ok = ok && am != 0u;  // the same sum in every lane
+        }
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(err, ERR_RESAMPLE);
+        gm = 0; gs = 0;
+    }
+    const bool redrawn = att > 1;
+    int slot = -1;
+    if (redrawn && lane == 0) {
+        slot = atomicAdd(fix_count, 1);
+        fix_keys[slot] = key;
+    }
+    slot = __shfl_sync(kFull, slot, 0);
+    if (lane == 0) fix_slot[key] = slot;
+    if (!redrawn) return;
+    // the final-screen g into the R/3 leaf and the resampling list
+    int16_t *leaf = leaves3 + (size_t)key * G::pad;
+    int8_t *fg = gfix + (size_t)slot * G::pad;
+    for (int i = lane; i < G::pad; i += 32) {
+        const int w = i >> 5, b = i & 31;
+        const uint32_t m = __shfl_sync(kFull, gm, w & 31), s = __shfl_sync(kFull, gs, w & 31);
+        const int c = (i < P && w < W) ? (((m >> b) & 1u) ? (((s >> b) & 1u) ? -1 : 1) : 0) : 0;
+        leaf[i] = (int16_t)c;
+        fg[i] = (int8_t)c;
+    }
+}
+
 // Small_encode(1/g) into the secret key from the inverted R/3 leaves (keys of
 // subtrees whose root did not invert skipped: sub_ok[key / sub_size] == 0, or
 // with sub_size 0 the flag of the key's batch).
@@ -323,6 +491,16 @@ cudaError_t launch_r3_check(const KeyMap &km, int B, int8_t *gbuf, int16_t *leav
 }
 
 template <int P>
+cudaError_t launch_r3_screen(const KeyMap &km, int B, const int8_t *gbuf, int16_t *leaves3,
+                             const R3Screen &scr, int8_t *gfix, int *fix_count, int *fix_keys,
+                             int *fix_slot, int *err, cudaStream_t st) {
+    if (scr.n <= 0 || scr.n > kMaxScreen) return cudaErrorInvalidValue;
+    SNT_LAUNCH(k_r3_screen<P>, (B + 3) / 4, 128, (size_t)2 * P * scr.n * sizeof(uint32_t), st, km,
+        B, gbuf, leaves3, scr, gfix, fix_count, fix_keys, fix_slot, err);
+    return cudaGetLastError();
+}
+
+template <int P>
 cudaError_t launch_r3_encode_v(const KeyMap &km, int B, const int16_t *v3, int sk_bytes,
                                int sk_off, cudaStream_t st, const int *sub_ok, int sub_size) {
     const long n = (long)B * Geo<P>::small_bytes;
@@ -335,7 +513,10 @@ cudaError_t launch_r3_encode_v(const KeyMap &km, int B, const int16_t *v3, int s
     template cudaError_t launch_r3_check<P>(const KeyMap &, int, int8_t *, int16_t *,        \
                                             const R3Factors &, int *, cudaStream_t);         \
     template cudaError_t launch_r3_encode_v<P>(const KeyMap &, int, const int16_t *, int, int, \
-                                               cudaStream_t, const int *, int);
+                                               cudaStream_t, const int *, int);                \
+    template cudaError_t launch_r3_screen<P>(const KeyMap &, int, const int8_t *, int16_t *,  \
+                                             const R3Screen &, int8_t *, int *, int *, int *, \
+                                             int *, cudaStream_t);
 SNT_R3B_INST(653)
 SNT_R3B_INST(761)
 SNT_R3B_INST(857)

@@ -237,7 +237,7 @@ k_r3_keygen(KeyMap km, int B, int8_t *__restrict__ g_out, int sk_bytes, int sk_o
             const uint64_t *__restrict__ inj_idx, const int8_t *__restrict__ inj_g,
             int n_inj, int *__restrict__ err, int8_t *__restrict__ gfix,
             int *__restrict__ fix_count, int *__restrict__ fix_keys,
-            const int *__restrict__ sub_ok, int sub_size) {
+            const int *__restrict__ sub_ok, int sub_size, const int *__restrict__ fix_slot) {
     pdl_enter();
     using Gm = Geo<P>;
     using RG = R3Geo<P, LKT, KPT>;
@@ -343,7 +343,8 @@ k_r3_keygen(KeyMap km, int B, int8_t *__restrict__ g_out, int sk_bytes, int sk_o
             int slot = 0;
             const bool fix = e < B && ok[k] && !first_ok[k];
             if (fix && sub == 0) {
-                slot = atomicAdd(fix_count, 1);
+                const int prev = fix_slot ? fix_slot[e] : -1;  // listed by the screen
+                slot = prev >= 0 ? prev : atomicAdd(fix_count, 1);
                 fix_keys[slot] = e;
             }
             slot = __shfl_sync(FULL, slot, 0, LK);
@@ -439,11 +440,11 @@ template <int P, int LK, int KPT>
 cudaError_t launch_r3_keygen_lk(const KeyMap &km, int B, int8_t *g_out, int sk_bytes, int sk_off,
                                 const uint64_t *inj_idx, const int8_t *inj_g, int n_inj, int *err,
                                 cudaStream_t st, int8_t *gfix, int *fix_count, int *fix_keys,
-                                const int *sub_ok, int sub_size) {
+                                const int *sub_ok, int sub_size, const int *fix_slot) {
     using RG = R3Geo<P, LK, KPT>;
     SNT_LAUNCH(k_r3_keygen<P, LK, KPT>, (B + RG::EPB - 1) / RG::EPB, 32 * RG::WARPS, 0, st, km, B,
         g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, gfix, fix_count, fix_keys, sub_ok,
-        sub_size);
+        sub_size, fix_slot);
     return cudaGetLastError();
 }
 
@@ -451,10 +452,11 @@ template <int P>
 cudaError_t launch_r3_keygen(const KeyMap &km, int B, int8_t *g_out, int sk_bytes, int sk_off,
                              const uint64_t *inj_idx, const int8_t *inj_g, int n_inj, int *err,
                              cudaStream_t st, int lanes, int kpt, int8_t *gfix, int *fix_count,
-                             int *fix_keys, const int *sub_ok, int sub_size) {
+                             int *fix_keys, const int *sub_ok, int sub_size,
+                             const int *fix_slot) {
 #define SNT_R3K(LK, KP)                                                                     \
     launch_r3_keygen_lk<P, LK, KP>(km, B, g_out, sk_bytes, sk_off, inj_idx, inj_g, n_inj, err, st, \
-                                   gfix, fix_count, fix_keys, sub_ok, sub_size)
+                                   gfix, fix_count, fix_keys, sub_ok, sub_size, fix_slot)
     if (kpt == 2) {
         switch (lanes) {
             case 4: return SNT_R3K(4, 2);
@@ -498,7 +500,7 @@ cudaError_t launch_r3_inv(int n, const int8_t *g, int8_t *out, int32_t *ok, cuda
     template cudaError_t launch_r3_keygen<P>(const KeyMap &, int, int8_t *, int, int,       \
                                              const uint64_t *, const int8_t *, int, int *,  \
                                              cudaStream_t, int, int, int8_t *, int *, int *, \
-                                             const int *, int);                              \
+                                             const int *, int, const int *);                 \
     template cudaError_t launch_r3_inv<P>(int, const int8_t *, int8_t *, int32_t *, cudaStream_t, int, \
                                           int);
 SNT_R3_INST(653)

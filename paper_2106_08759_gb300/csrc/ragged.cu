@@ -58,6 +58,7 @@ struct Group {
     bool mma = true, ntt = false, wide = false, r3batch = false, r3first = false, fuse = false;
     size_t off_r3ok = 0;  // one root flag per batch (r3first)
     R3Factors fac;
+    R3Screen scr;  // the small factors' remainder tables (mode 2)
     // table offsets (bytes, from the start of the uploaded table block)
     size_t t_desc = 0, t_pre = 0, t_root = 0;
 };
@@ -109,6 +110,7 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
     int8_t *gbuf = reinterpret_cast<int8_t *>(ctx->arena + g.off_g);
     int *fix_count = reinterpret_cast<int *>(ctx->arena + g.off_fix);
     int *fix_keys = fix_count + 1;
+    int *fix_slot = fix_keys + g.nkeys;  // by key: the R/3 screen's slot, or -1
     int8_t *gfix = reinterpret_cast<int8_t *>(ctx->arena + g.off_gfix);
     int *r3ok = reinterpret_cast<int *>(ctx->arena + g.off_r3ok);
     KeyMap km;
@@ -145,6 +147,9 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
         if (!g.r3first) {
             SNT_CUDA_R(launch_r3_check<P>(km, g.nkeys, gbuf, nodes3, g.fac, ctx->d_err, aux));
             SNT_CUDA_R(cudaEventRecord(ev_gready, aux));
+        } else if (g.scr.n > 0) {  // first draws screened against the small factors
+            SNT_CUDA_R(launch_r3_screen<P>(km, g.nkeys, gbuf, nodes3, g.scr, gfix, fix_count,
+                                           fix_keys, fix_slot, ctx->d_err, aux));
         }
         for (int l = 1; l <= g.L; ++l)
             SNT_CUDA_R(launch_tree_up_mma3<P>(nodes3 + (size_t)g.lev_off[l - 1] * pi.pad, lmap(l),
@@ -163,7 +168,8 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
         if (g.r3first)  // batches whose root did not invert: per key, with redraws
             SNT_CUDA_R(launch_r3_keygen<P>(km, g.nkeys, gbuf, pi.sk_bytes, sb, ctx->d_inj_idx,
                                            ctx->d_inj_g, n_inj, ctx->d_err, aux, g.lanes, g.kpt,
-                                           gfix, fix_count, fix_keys, r3ok, 0));
+                                           gfix, fix_count, fix_keys, r3ok, 0,
+                                           g.scr.n > 0 ? fix_slot : nullptr));
     } else {
         SNT_CUDA_R(launch_r3_keygen<P>(km, g.nkeys, gbuf, pi.sk_bytes, sb, ctx->d_inj_idx,
                                        ctx->d_inj_g, n_inj, ctx->d_err, aux, g.lanes, g.kpt, gfix,
@@ -295,13 +301,16 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
         g.off_g = arena_off;
         arena_off += align_up((size_t)g.nkeys * g.pi.pad, 256);
         g.off_fix = arena_off;
-        arena_off += align_up(sizeof(int) * (1 + (size_t)g.nkeys), 256);
+        arena_off += align_up(sizeof(int) * (1 + 2 * (size_t)g.nkeys), 256);
         g.off_gfix = arena_off;
         arena_off += align_up((size_t)g.nkeys * g.pi.pad, 256);
         if (g.r3batch) {
             if (!g.r3first) {
                 const snt_status sf = r3_factors_for(ctx, g.P, g.fac);
                 if (sf != SNT_OK) return sf;
+            } else {
+                const snt_status ss = r3_screen_for(ctx, g.P, g.scr);
+                if (ss != SNT_OK) return ss;
             }
             g.off_nodes3 = arena_off;
             arena_off += align_up(g.nodes * g.pi.pad * sizeof(int16_t), 256);

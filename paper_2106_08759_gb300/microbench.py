@@ -260,7 +260,7 @@ def main():
             return {"ms": round(tot / args.reps, 4), "phases": {k: round(v, 4) for k, v in ph.items()}}
         ctx.set_option(snt.SNT_OPT_R3_LANES, 4)
         ctx.set_option(snt.SNT_OPT_TREE_SPLIT, 8)
-        for overlap in (0, 1, 2):
+        for overlap in (0, 1, 2, 3):
             ctx.set_option(snt.SNT_OPT_R3_OVERLAP, overlap)
             for roots in (1, 4, 16, 64):
                 for r3mode in (0, 1, 2):
@@ -273,7 +273,7 @@ def main():
         ctx.set_option(snt.SNT_OPT_R3_MODE, 0)
         ctx.set_option(snt.SNT_OPT_RQ_ENGINE, 0)
         for narrow in (0, 1):
-            for overlap in (0, 1, 2):
+            for overlap in (0, 1, 2, 3):
                 for lanes in (4, 8):
                     for split in (4, 8):
                         ctx.set_option(snt.SNT_OPT_NARROW_SEG, narrow)

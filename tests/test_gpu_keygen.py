@@ -61,7 +61,8 @@ def test_ragged_tree_shapes(snt, ctx, B):
     assert first_mismatch(sk, rsk) is None
 
 
-@pytest.mark.parametrize("opts", [(4, 8, 1), (8, 1, 0), (32, 2, 2), (4, 4, 0), (8, 8, 2)])
+@pytest.mark.parametrize("opts", [(4, 8, 1), (8, 1, 0), (32, 2, 2), (4, 4, 0), (8, 8, 2),
+                                  (8, 8, 3), (4, 2, 3)])
 def test_tuning_options_do_not_change_keys(snt, ctx, opts):
     # R/3 lanes per element, tree split, R/3 overlap: layouts only
     lanes, split, overlap = opts
@@ -283,7 +284,7 @@ def test_output_split_narrow_levels_vs_oracle(snt, ctx, P, B):
 def test_autotuned_layouts_give_the_same_keys(snt):
     with snt.Context(0, 64 << 20) as c:
         choice = c.autotune(761, 48)
-        assert choice["r3_lanes"] in (4, 8, 32) and choice["r3_overlap"] in (0, 1, 2)
+        assert choice["r3_lanes"] in (4, 8, 32) and choice["r3_overlap"] in (0, 1, 2, 3)
         pk, sk = gpu_keygen(snt, c, 761, 31, 7, 48)
     rpk, rsk = oracle.keygen_batch(761, 31, 7, 48)
     assert first_mismatch(pk, rpk) is None and first_mismatch(sk, rsk) is None
@@ -470,10 +471,10 @@ def test_pipelined_parts_redraw_injected_zero_divisors(snt, ctx):
 
 def test_sntrup653_first_draw_batch_with_many_redraws(snt, ctx, pool):
     # x^653 - x - 1 has a factor of degree 3 over F_3, so about one first draw
-    # of g in 27 is a zero divisor: with the R/3 forest on the first draws most
-    # 32-key subtrees fail, their keys go to the per-key fall-back and dozens
-    # of keys to the fix-up; all keys equal the per-key path's, and the
-    # redrawn ones (and others) the oracle's
+    # of g in 27 is a zero divisor: the screen against the factors of degree 3
+    # and 16 redraws those before the R/3 forest (without it most 32-key
+    # subtrees would fail) and dozens of keys go to the fix-up; all keys equal
+    # the per-key path's, and the redrawn ones (and others) the oracle's
     B, seed = 2048, 17
     ctx.set_option(snt.SNT_OPT_R3_MODE, 2)
     ctx.set_option(snt.SNT_OPT_ROOTS, 64)
@@ -531,3 +532,22 @@ def test_unaligned_output_buffers(snt, ctx, shift):
     got_pk = pk.cpu().numpy()[shift:shift + B * pkb].reshape(B, pkb)
     got_sk = sk.cpu().numpy()[shift:shift + B * skb].reshape(B, skb)
     assert np.array_equal(got_pk, ref[0]) and np.array_equal(got_sk, ref[1])
+
+
+@pytest.mark.parametrize("r3mode,roots,B", [(2, 16, 4096), (1, 16, 300), (0, 4, 300), (2, 1, 33)])
+def test_r3_from_the_end_of_the_up_sweep(snt, ctx, r3mode, roots, B):
+    # R/3 overlap 3: the R/3 work forked when the R/q up-sweep ends
+    ctx.set_option(snt.SNT_OPT_ROOTS, roots)
+    ctx.set_option(snt.SNT_OPT_R3_MODE, r3mode)
+    try:
+        ref = gpu_keygen(snt, ctx, 761, 33, 1000, B)
+        ctx.set_option(snt.SNT_OPT_R3_OVERLAP, 3)
+        got = gpu_keygen(snt, ctx, 761, 33, 1000, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_R3_OVERLAP, 1)
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+        ctx.set_option(snt.SNT_OPT_R3_MODE, 0)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    for j in sorted({0, B // 3, B - 1}):
+        opk, osk, _ = oracle.keygen(761, 33, 1000 + j)
+        assert np.array_equal(got[0][j], opk) and np.array_equal(got[1][j], osk), j
