@@ -49,16 +49,23 @@ def launches_per_call(B, tuned):
     and the encoding; R/3 first-draw batch: the forest, the encoding, the
     fall-back kernel and the fix-up."""
     K = forest_roots(B, tuned.get("roots", 1))
-    L, n = 0, B // K
-    while n > 1:
-        n = (n + 1) // 2
-        L += 1
+    K3 = forest_roots(B, tuned.get("r3_roots") or tuned.get("roots", 1))
+    L, L3 = tree_levels(B // K), tree_levels(B // K3)
     fused = fused_leaf(tuned) and L >= 1
     down = L - 1 if fused else L
     side = 1 if (fused and tuned.get("r3_mode", 0) != 1) else 0  # leaf-pair products s
     rq = 1 + L + 1 + down + 1 + 1 + side
-    r3 = {0: 2, 1: 1 + 2 * L + 1 + 1, 2: 2 * L + 1 + 1 + 1 + 1}[tuned.get("r3_mode", 0)]
+    r3 = {0: 2, 1: 1 + 2 * L3 + 1 + 1, 2: 2 * L3 + 1 + 1 + 1 + 1}[tuned.get("r3_mode", 0)]
     return rq + r3
+
+
+def tree_levels(n):
+    """Product levels above the leaves of a subtree of n leaves."""
+    L = 0
+    while n > 1:
+        n = (n + 1) // 2
+        L += 1
+    return L
 
 # DRAM bytes (read + write) per call of a phase's kernels at B = 4096 under
 # the tuned layouts (64 roots, R/3 forest), summed over the phase's launches
@@ -230,7 +237,7 @@ def _measured_peaks():
         return {}
 
 
-def ops_per_call(B, K=1, r3_mode=0, p=P, fused=False, s_side=False):
+def ops_per_call(B, K=1, r3_mode=0, p=P, fused=False, s_side=False, K3=None):
     """Algorithmic integer operations of each phase for one call of B keys in
     K subtrees.
 
@@ -243,8 +250,10 @@ def ops_per_call(B, K=1, r3_mode=0, p=P, fused=False, s_side=False):
     side stream beside the root inversions (no phase time of their own);
     the per-key R/3 divsteps count 6 word operations per 32-trit word for each
     of the two polynomial updates per step (bit-sliced F_3 multiply-add), the
-    R/3 batch paths their 3(B - K) products mod 3; a root inversion counts 2
-    multiply-reduce updates of p + 1 coefficients per step."""
+    R/3 batch paths their 3(B - K3) products mod 3 (K3 subtrees, default K);
+    a root inversion counts 2 multiply-reduce updates of p + 1 coefficients
+    per step."""
+    K3 = K if K3 is None else K3
     steps = 2 * p - 1
     mac = p * p
     n0 = B // K
@@ -262,7 +271,7 @@ def ops_per_call(B, K=1, r3_mode=0, p=P, fused=False, s_side=False):
     else:
         down, h = 2 * (B - K), B
     ops = {
-        "r3_inv": B * steps * 2 * WORDS * 6 if r3_mode == 0 else 3 * (B - K) * mac,
+        "r3_inv": B * steps * 2 * WORDS * 6 if r3_mode == 0 else 3 * (B - K3) * mac,
         "tree_up": (B - K) * mac,
         "tree_down": down * mac,
         "h_encode": h * mac,
@@ -566,15 +575,12 @@ def run_ours(args):
     # cores.  "roofline" is the longest phase on the critical path; the R/3
     # phase runs beside the tree (auxiliary stream) unless its overlap is 0.
     K = forest_roots(B, tuned.get("roots", 1))
+    K3 = forest_roots(B, tuned.get("r3_roots") or tuned.get("roots", 1))
     r3m = tuned.get("r3_mode", 0)
     fused = fused_leaf(tuned)
-    ops = ops_per_call(B, K, r3m, fused=fused, s_side=fused and r3m != 1)
-    Lk = 0
-    n = B // K
-    while n > 1:
-        n = (n + 1) // 2
-        Lk += 1
-    launches_of = {"r3_inv": 1 if r3m == 0 else 2 * Lk + 3, "tree_up": Lk,
+    ops = ops_per_call(B, K, r3m, fused=fused, s_side=fused and r3m != 1, K3=K3)
+    Lk = tree_levels(B // K)
+    launches_of = {"r3_inv": 1 if r3m == 0 else 2 * tree_levels(B // K3) + 3, "tree_up": Lk,
                    "tree_down": Lk - 1 if (fused and Lk >= 1) else Lk,
                    "h_encode": 1, "root_inv": 1, "leaf_s": 1}
     tensor_phases = TENSOR_PHASES + (("r3_inv",) if r3m else ())

@@ -351,7 +351,13 @@ typedef enum {
      * it completes (each such kernel waits for its predecessor's completion
      * before its first memory access); 0 launches them plainly.  Same bytes
      * either way; a ragged graph is captured again when it changes. */
-    SNT_OPT_PDL = 14
+    SNT_OPT_PDL = 14,
+    /* 0 (default) or a power of two in [1, 1024]: subtrees of the R/3
+     * forest of R/3 modes 1 and 2 (0: as many as the R/q forest,
+     * SNT_OPT_ROOTS).  The R/3 work runs beside the R/q chain, so a forest of
+     * few subtrees (few latency-bound R/3 root inversions holding SMs) can
+     * pair with an R/q forest of many.  Same bytes. */
+    SNT_OPT_R3_ROOTS = 15
 } snt_option;
 
 snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);
@@ -362,10 +368,11 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
  * and keeps the fastest for every later keygen call of this context with the
  * same P and ceil(log2 B) (and for the ragged call's parameter sets whose
  * largest batch falls in that bucket); it overrides the snt_ctx_set_option
- * values there.  Candidates: R/3 lanes (4, 8, 32) x R/3 overlap (0, 1, 2) x
+ * values there.  Candidates: R/3 lanes (4, 8, 32) x R/3 overlap (0 .. 3) x
  * { tensor-core engine (1, and each of its candidates again as 3) with 1 or
- * 2 MMA tiles per warp, forests of 1, 4, 16,
- * 64, 128 or 256 subtrees (SNT_OPT_ROOTS) and R/3 mode 0, 1 or 2; CUDA-core
+ * 2 MMA tiles per warp, forests of 1, 4, 16, 64, 128 or 256 subtrees
+ * (SNT_OPT_ROOTS) and R/3 mode 0, 1 or 2 (modes 1 and 2 also with an R/3
+ * forest of 1 or 4 subtrees, SNT_OPT_R3_ROOTS); CUDA-core
  * Toeplitz engine with tree split 4 or 8; transform multiplier (engine 2)
  * with forests of 1, 16, 64 or 128 subtrees and R/3 mode 0 or 2; the
  * tensor-core engine in 2 or 4 pipelined parts (SNT_OPT_PARTS) with forests
@@ -376,8 +383,9 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
 snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice);
 
 /* The layouts the autotuner kept for (P, ceil(log2 B)) on this context:
- * out[0 .. min(n, 9)) = lanes, split, overlap, engine, tiles, kpt, roots,
- * r3 mode, parts (all zero if it has not run for that bucket). */
+ * out[0 .. min(n, 10)) = lanes, split, overlap, engine, tiles, kpt, roots,
+ * r3 mode, parts, R/3 roots (0: as roots) (all zero if it has not run for
+ * that bucket). */
 snt_status snt_ctx_tuned(snt_ctx *ctx, int P, size_t B, int *out, int n);
 
 /* snt_autotune_ex returning lanes, split and overlap only. */

@@ -26,6 +26,7 @@ SNT_OPT_RQ_ENGINE, SNT_OPT_MMA_TILES, SNT_OPT_R3_KPT, SNT_OPT_MMA_KSPLIT = 5, 6,
 SNT_OPT_ROOTS, SNT_OPT_R3_MODE, SNT_OPT_FUSE_LEAF, SNT_OPT_PERKEY_INV = 9, 10, 11, 12
 SNT_OPT_PARTS = 13
 SNT_OPT_PDL = 14
+SNT_OPT_R3_ROOTS = 15
 
 # phase names of snt_ctx_phase_times (SNT_NPHASES entries)
 PHASES = ("sample_f", "r3_inv", "tree_up", "root_inv", "tree_down", "h_encode", "sha512",
@@ -203,11 +204,11 @@ class Context:
 
     def tuned(self, P, B):
         """The layouts the autotuner kept for (P, B) on this context."""
-        c = (ctypes.c_int * 9)()
-        _check(load().snt_ctx_tuned(self.handle, P, B, c, 9))
+        c = (ctypes.c_int * 10)()
+        _check(load().snt_ctx_tuned(self.handle, P, B, c, 10))
         return {"r3_lanes": c[0], "tree_split": c[1], "r3_overlap": c[2], "rq_engine": c[3],
                 "mma_tiles": c[4], "r3_kpt": c[5], "roots": c[6], "r3_mode": c[7],
-                "parts": c[8]}
+                "parts": c[8], "r3_roots": c[9]}
 
     def set_timing(self, on=True):
         _check(load().snt_ctx_set_timing(self.handle, 1 if on else 0))

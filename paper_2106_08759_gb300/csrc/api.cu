@@ -104,13 +104,14 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     const bool narrow = ctx->narrow_seg != 0;
     int engine = ctx->rq_engine;
     int mma_tiles = ctx->mma_tiles, kpt = ctx->r3_kpt, roots = ctx->roots, r3mode = ctx->r3_mode;
-    int parts = ctx->parts;
+    int parts = ctx->parts, r3roots = ctx->r3_roots;
     const snt_ctx::Tuned &tu = ctx->tuned[pidx(P)][bbucket(B)];
     if (tu.lanes) {
         mode = tu.overlap; lanes = tu.lanes; split = tu.split;
         engine = tu.engine; mma_tiles = tu.tiles; kpt = tu.kpt; roots = tu.roots;
-        r3mode = tu.r3mode; parts = tu.parts;
+        r3mode = tu.r3mode; parts = tu.parts; r3roots = tu.r3roots;
     }
+    if (r3roots == 0) r3roots = roots;
     // engine 2: the general x general levels by the transform multiplier,
     // the small-operand levels (leaves) and h on the tensor cores; engine 3:
     // the tensor cores with one exact f16 limb on the vector side of the
@@ -160,7 +161,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
             if (r3opt && scr.n > 0)
                 SNT_CUDA(launch_r3_screen<P>(km, Bi, gbuf, nodes3, scr, gfix, fix_count, fix_keys,
                                              fix_slot, ctx->d_err, r3s));
-            const Forest f3 = make_forest(B, roots);
+            const Forest f3 = make_forest(B, r3roots);
             const int sub3 = (int)(B / f3.K);
             const Tree &t3 = f3.t;
             const int L3 = (int)t3.n.size() - 1;
@@ -849,6 +850,11 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value) {
             if (value != 0 && value != 1) return set_error(SNT_EINVAL, "PDL is 0 or 1");
             ctx->pdl = value;
             return SNT_OK;
+        case SNT_OPT_R3_ROOTS:
+            if (value < 0 || value > 1024 || (value & (value - 1)))
+                return set_error(SNT_EINVAL, "R/3 roots is 0 or a power of two in [1, 1024]");
+            ctx->r3_roots = value;
+            return SNT_OK;
         default:
             return set_error(SNT_EINVAL, "unknown option %d", option);
     }
@@ -871,6 +877,7 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value) {
         case SNT_OPT_PERKEY_INV: *value = ctx->perkey_inv; return SNT_OK;
         case SNT_OPT_PARTS: *value = ctx->parts; return SNT_OK;
         case SNT_OPT_PDL: *value = ctx->pdl; return SNT_OK;
+        case SNT_OPT_R3_ROOTS: *value = ctx->r3_roots; return SNT_OK;
         default: return set_error(SNT_EINVAL, "unknown option %d", option);
     }
 }
@@ -934,6 +941,17 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
                         }
             }
         }
+    // every tensor-core candidate with an R/3 forest also with one of 1 or 4
+    // subtrees (fewer latency-bound R/3 roots beside the R/q chain)
+    const size_t nbase = cands.size();
+    for (size_t i = 0; i < nbase; ++i)
+        if (cands[i].engine == 1 && cands[i].r3mode != 0 && cands[i].roots > 1)
+            for (int r3r : {1, 4})
+                if (r3r < cands[i].roots) {
+                    snt_ctx::Tuned c = cands[i];
+                    c.r3roots = r3r;
+                    cands.push_back(c);
+                }
     // every tensor-core candidate also with one wide limb on the vector side
     const size_t ncand = cands.size();
     for (size_t i = 0; i < ncand; ++i)
@@ -987,9 +1005,9 @@ snt_status snt_ctx_tuned(snt_ctx *ctx, int P, size_t B, int *out, int n) {
     if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     if (B == 0 || B > kMaxB) return set_error(SNT_EINVAL, "batch size %zu out of range", B);
     const snt_ctx::Tuned &t = ctx->tuned[pidx(P)][bbucket(B)];
-    const int v[9] = {t.lanes, t.split, t.overlap, t.engine, t.tiles, t.kpt, t.roots, t.r3mode,
-                      t.parts};
-    for (int i = 0; i < n && i < 9; ++i) out[i] = v[i];
+    const int v[10] = {t.lanes, t.split, t.overlap, t.engine, t.tiles, t.kpt, t.roots, t.r3mode,
+                       t.parts, t.r3roots};
+    for (int i = 0; i < n && i < 10; ++i) out[i] = v[i];
     return SNT_OK;
 }
 

@@ -62,13 +62,14 @@ struct snt_ctx {
     int perkey_inv = 1; // per-key path: 1 jump divsteps, 0 one divstep per barrier
     int parts = 1;      // pipelined parts of a batch keygen call (SNT_OPT_PARTS)
     int pdl = 1;        // programmatic dependent launches (SNT_OPT_PDL)
+    int r3_roots = 0;   // subtrees of the R/3 forest (SNT_OPT_R3_ROOTS; 0: as the R/q forest)
     cudaStream_t part[snt::kMaxParts - 1] = {};  // streams of parts 1 .. kMaxParts-1
     cudaEvent_t ev_pfork = nullptr, ev_pdone[snt::kMaxParts] = {};
     cudaEvent_t ev_psfork[snt::kMaxParts] = {}, ev_psready[snt::kMaxParts] = {};
     // autotuned options per (parameter set, ceil(log2 B)); lanes == 0: none
     struct Tuned {
         int lanes = 0, split = 0, overlap = 0, engine = 0, tiles = 1, kpt = 1, roots = 1, r3mode = 0;
-        int parts = 1;
+        int parts = 1, r3roots = 0;
     };
     Tuned tuned[3][25];
     cudaStream_t tune = nullptr;  // stream used while autotuning

@@ -101,11 +101,13 @@ inline bool param_info(int P, ParamInfo &pi) {
 // CTAs of the fix-up of redrawn keys for a call of n keys: the list is
 // usually empty (a zero divisor among the first draws has probability
 // 3^-19 per key for sntrup761), but x^653 - x - 1 has a factor of degree 3
-// over F_3, so about one sntrup653 key in 27 is redrawn when the R/3 forest
-// runs on the first draws.
+// over F_3, so about one sntrup653 key in 27 is redrawn.  A CTA spends most
+// of an entry's time in the single-thread hash of the new public key, so
+// the grid (n / 16, up to 16 CTAs per SM) gives every expected entry a CTA
+// of its own; CTAs without an entry exit after one read.
 inline int fixup_grid(size_t n) {
     const size_t g = n / 16;
-    return (int)(g < 8 ? 8 : g > 608 ? 608 : g);
+    return (int)(g < 8 ? 8 : g > 2432 ? 2432 : g);
 }
 
 // Product-tree levels over B leaves: level 0 = leaves, level l has

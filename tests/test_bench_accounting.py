@@ -77,3 +77,15 @@ def test_bench_line_at_the_headline_config():
     assert (ops["tree_up"] // mac, ops["tree_down"] // mac, ops["leaf_s"] // mac,
             ops["h_encode"] // mac) == (4032, 3968, 4096, 4096)
     assert bench.launches_per_call(4096, {"roots": 64, "r3_mode": 2, "rq_engine": 1}) == 32
+
+
+def test_r3_forest_with_its_own_root_count():
+    # R/q forest of 16 subtrees of 256 keys (8 levels), R/3 forest of 4
+    # subtrees of 1024 (10 levels): 20 R/q launches (sample, 8 up, roots, 7
+    # down, h, hash, leaf-pair products) and 24 R/3 ones (2 per level, roots,
+    # encoding, fall-back, fix-up); the R/3 products are 3 (4096 - 4)
+    tuned = {"roots": 16, "r3_roots": 4, "r3_mode": 2, "rq_engine": 3}
+    assert bench.launches_per_call(4096, tuned) == 20 + 24
+    ops = bench.ops_per_call(4096, 16, 2, fused=True, s_side=True, K3=4)
+    assert ops["r3_inv"] == 3 * (4096 - 4) * bench.P * bench.P
+    assert bench.launches_per_call(4096, dict(tuned, r3_roots=0)) == 20 + 2 * 8 + 4

@@ -551,3 +551,29 @@ def test_r3_from_the_end_of_the_up_sweep(snt, ctx, r3mode, roots, B):
     for j in sorted({0, B // 3, B - 1}):
         opk, osk, _ = oracle.keygen(761, 33, 1000 + j)
         assert np.array_equal(got[0][j], opk) and np.array_equal(got[1][j], osk), j
+
+
+@pytest.mark.parametrize("P,roots,r3roots,mode,B", [
+    (761, 64, 4, 2, 4096), (761, 128, 16, 1, 1024), (653, 64, 1, 2, 300), (857, 4, 16, 2, 96)])
+def test_r3_forest_with_its_own_root_count(snt, ctx, P, roots, r3roots, mode, B):
+    # the R/3 forest with another number of subtrees than the R/q forest, with
+    # one injected zero divisor per factor (the screen, the failing R/3
+    # subtree and its per-key fall-back): same bytes as the per-key R/3 path
+    p = oracle.PARAMS[P][0]
+    bads = _zero_divisors(p, np.random.default_rng(P + r3roots))
+    offs = [1 + 7 * i for i in range(len(bads))]
+    snt.snt_debug_inject_g(ctx, P, [50 + o for o in offs], np.stack(bads))
+    try:
+        ref = gpu_keygen(snt, ctx, P, 6, 50, B)
+        ctx.set_option(snt.SNT_OPT_ROOTS, roots)
+        ctx.set_option(snt.SNT_OPT_R3_ROOTS, r3roots)
+        ctx.set_option(snt.SNT_OPT_R3_MODE, mode)
+        got = gpu_keygen(snt, ctx, P, 6, 50, B)
+    finally:
+        ctx.set_option(snt.SNT_OPT_R3_ROOTS, 0)
+        ctx.set_option(snt.SNT_OPT_ROOTS, 1)
+        ctx.set_option(snt.SNT_OPT_R3_MODE, 0)
+        snt.snt_debug_inject_g(ctx, P, [], np.zeros((0, p), np.int8))
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    rpk, rsk = oracle.keygen_batch(P, 6, 50, min(B, 64), g_inject=dict(zip(offs, bads)))
+    assert first_mismatch(got[0][:64], rpk) is None and first_mismatch(got[1][:64], rsk) is None
