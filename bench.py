@@ -67,17 +67,20 @@ def tree_levels(n):
         L += 1
     return L
 
-# DRAM bytes (read + write) per call of a phase's kernels at B = 4096 under
-# the tuned layouts (64 roots, R/3 forest), summed over the phase's launches
-# of one call, from the committed ncu launch-list capture of one keygen call,
-# keyed by kernel; a kernel is absent until a capture of its current code
-# exists.  Writes stay in L2.
+# DRAM bytes (read + write) per call of a phase's kernels at B = 4096,
+# summed over the phase's launches of one call, from the committed ncu
+# launch-list capture of one keygen call (caches flushed by ncu before each
+# launch), keyed by kernel; a kernel is absent until a capture of its current
+# code exists.  Writes stay in L2.  Engine 3 and the R/3 forest: 16 subtrees
+# (the layout of the capture); engine 1: 64 subtrees.
 NCU_TRAFFIC_BYTES = {
     "k_tree_up_mma": 12532992,
     "k_tree_down_mma": 9324544,
-    "k_rq_inv_jump<761, 4591>": 165632,
-    "k_finalize_pair<761>": 9501440,
-    "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 37790976,
+    "k_tree_up_mma (one wide limb)": 12725760,
+    "k_tree_down_mma (one wide limb)": 9619200,
+    "k_rq_inv_jump<761, 4591>": 111104,
+    "k_finalize_pair<761>": 9502720,
+    "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 38189056,
 }
 
 
