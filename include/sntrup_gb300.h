@@ -364,8 +364,10 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);
 snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
 
 /* Autotuner: times batch keygen of B keys of parameter set P on this GPU
- * (CUDA events, best of three after a warm-up) under each candidate layout
- * and keeps the fastest for every later keygen call of this context with the
+ * (CUDA events, best of three single calls after a warm-up) under each
+ * candidate layout, times the six fastest again as rounds of six calls
+ * issued back to back (best of two rounds after a warm-up round), and keeps
+ * the fastest of those for every later keygen call of this context with the
  * same P and ceil(log2 B) (and for the ragged call's parameter sets whose
  * largest batch falls in that bucket); it overrides the snt_ctx_set_option
  * values there.  Candidates: R/3 lanes (4, 8, 32) x R/3 overlap (0 .. 3) x

@@ -9,6 +9,7 @@
 //   stream X : (after the fork) sample g + R/3 divstep inverse per key
 // The two branches only meet at the h stage, so the per-key R/3 inversions
 // overlap the latency-bound top of the tree and the root inversion.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -960,11 +961,13 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
             c.engine = 3;
             cands.push_back(c);
         }
+    // stage 1: every candidate, best of three single calls after a warm-up
     snt_ctx::Tuned best;
-    float best_ms = 1e30f;
     snt_status st = SNT_OK;
-    for (const snt_ctx::Tuned &cand : cands) {
-        ctx->tuned[pidx(P)][bbucket(B)] = cand;
+    std::vector<std::pair<float, size_t>> timed;
+    timed.reserve(cands.size());
+    for (size_t ci = 0; ci < cands.size() && st == SNT_OK; ++ci) {
+        ctx->tuned[pidx(P)][bbucket(B)] = cands[ci];
         float best_c = 1e30f;
         for (int rep = 0; rep < 4 && st == SNT_OK; ++rep) {
             if (cudaEventRecord(e0, ctx->tune) != cudaSuccess) { st = SNT_ECUDA; break; }
@@ -976,8 +979,31 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep > 0 && ms < best_c) best_c = ms;  // first run warms up
         }
-        if (st != SNT_OK) break;
-        if (best_c < best_ms) { best_ms = best_c; best = cand; }
+        timed.emplace_back(best_c, ci);
+    }
+    // stage 2: the six fastest again, each as calls issued back to back (the
+    // steady state of a caller that keeps the GPU busy), best of two rounds
+    // of kRound calls; stage-1 differences of a percent are within its noise
+    constexpr int kRound = 6;
+    std::sort(timed.begin(), timed.end());
+    float best_ms = 1e30f;
+    for (size_t k = 0; k < timed.size() && k < 6 && st == SNT_OK; ++k) {
+        const snt_ctx::Tuned &cand = cands[timed[k].second];
+        ctx->tuned[pidx(P)][bbucket(B)] = cand;
+        float best_c = 1e30f;
+        for (int round = 0; round < 3 && st == SNT_OK; ++round) {
+            if (cudaEventRecord(e0, ctx->tune) != cudaSuccess) { st = SNT_ECUDA; break; }
+            for (int i = 0; i < kRound && st == SNT_OK; ++i)
+                st = keygen_common(ctx, P, 0x5eed, (uint64_t)(round * kRound + i) * B, B, dpk,
+                                   dsk, ts, true, false);
+            if (st != SNT_OK) break;
+            if (cudaEventRecord(e1, ctx->tune) != cudaSuccess ||
+                cudaEventSynchronize(e1) != cudaSuccess) { st = SNT_ECUDA; break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (round > 0 && ms / kRound < best_c) best_c = ms / kRound;  // first round warms up
+        }
+        if (st == SNT_OK && best_c < best_ms) { best_ms = best_c; best = cand; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -416,7 +416,6 @@ constexpr int kShaBlkMax = sha_blk_bytes(1322);  // the opt-in size: sntrup857's
 
 __global__ void __launch_bounds__(64, 1)
 k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
-    pdl_enter();
     extern __shared__ __align__(16) uint8_t sm[];
     uint64_t(*wk)[80][32] = reinterpret_cast<uint64_t(*)[80][32]>(sm);  // [slot][round][key]
     __shared__ uint64_t ks[80];  // the round constants
@@ -463,6 +462,9 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
         __syncwarp();
         if (lane < nkeys) rowoff[lane] = run_dst[r] + (lane - run_first[r]) * pk_bytes;
     }
+    // the row lookups above read only the batch table; the rows themselves
+    // are the previous kernel's output
+    pdl_enter();
     __syncthreads();
     for (int q = 0; q < nruns; ++q) {
         const uint8_t *src = run_src[q];

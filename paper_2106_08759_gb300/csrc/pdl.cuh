@@ -25,6 +25,14 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// A kernel of the chain starts when every CTA of its predecessor has passed
+// pdl_enter, that is, when the kernel before that has completed: so a kernel
+// may read, before its own pdl_enter, data written by kernels two or more
+// launches back in its own stream, never data of its immediate predecessor,
+// and never data of another stream joined by an event (captured in a graph,
+// that edge too may become programmatic); it may write nothing there.  Each
+// CTA still calls pdl_enter before it exits.
+
 // Whether launches on this host thread use the attribute: set for the
 // duration of one library call from its context's option (PdlScope).
 inline thread_local bool tl_pdl = false;

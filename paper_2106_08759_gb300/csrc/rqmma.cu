@@ -74,7 +74,6 @@ k_tree_up_mma(const int16_t *__restrict__ lin, LevelMap lm, int16_t *__restrict_
 template <int P, int NT, int MODE, int KS, int Q = Prm<P>::q>
 __global__ void __launch_bounds__(32 * MmaGeo<P, NT>::NW * KS)
 k_tree_down_mma(const int16_t *__restrict__ lpar, LevelMap lm, int16_t *__restrict__ lch) {
-    pdl_enter();
     using G = Geo<P>;
     using M = MmaGeo<P, NT>;
     extern __shared__ __align__(16) uint8_t sm[];
@@ -90,11 +89,15 @@ k_tree_down_mma(const int16_t *__restrict__ lpar, LevelMap lm, int16_t *__restri
     int16_t *x = lch + (size_t)(base + 2 * idx) * G::pad;
     int16_t *y = x + G::pad;
     if (2 * idx + 1 >= n_ch) {  // unpaired child: its inverse is the parent's
+        pdl_enter();
         for (int i = threadIdx.x; i < G::pad; i += nth) x[i] = T[i];
         return;
     }
+    // the children were written by the up-sweep, several kernels back: their
+    // tables are filled before the wait for the parent level
     mma_fill_a<P, NT, MODE>(y, A[0], threadIdx.x, nth);  // 1/x = T * y
     mma_fill_a<P, NT, MODE>(x, A[1], threadIdx.x, nth);  // 1/y = T * x
+    pdl_enter();
     mma_fill_b<P, NT>(T, E, threadIdx.x, nth);
     __syncthreads();  // both children are in shared memory before either is overwritten
     // the parent T is small only in R/3 (MODE_SAE), never in R/q
