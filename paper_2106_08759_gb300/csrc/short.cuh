@@ -75,27 +75,53 @@ __device__ __forceinline__ void short_sorted_words(uint64_t seed, uint64_t k, ui
 
 }
 
-// One compare-exchange stage inside a lane: slots r and r | S (r & S == 0)
-// of v, ascending when SIZE > 0 and (r & SIZE) == 0 (the direction of small
-// bitonic blocks is fixed by the slot) or, when SIZE == 0, when asc.
-template <int S, int SIZE>
-__device__ __forceinline__ void bitonic_lane_stage(uint32_t (&v)[32], bool asc) {
+// The warp sort below runs the bitonic network in its all-ascending form:
+// to merge two sorted halves of a block of `size` slots, slot i is first
+// compared with its mirror i ^ (size - 1) (the upper half read backwards),
+// then the block's halves, quarters, ... are cleaned with partners i ^ S,
+// every comparator putting the minimum at the lower slot.  It sorts the same
+// values into the same order as the alternating-direction network, and no
+// comparator's direction depends on the slot.
+
+// In-lane flip stage of blocks of SIZE <= 32 slots: slots r and r ^ (SIZE - 1).
+template <int SIZE>
+__device__ __forceinline__ void bitonic_lane_flip(uint32_t (&v)[32]) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+        if ((r & (SIZE >> 1)) == 0) {
+            const int o = r ^ (SIZE - 1);
+            const uint32_t x = v[r], y = v[o];
+            v[r] = min(x, y);
+            v[o] = max(x, y);
+        }
+}
+
+// In-lane half-cleaner stage: slots r and r | S (r & S == 0), ascending.
+template <int S>
+__device__ __forceinline__ void bitonic_lane_stage(uint32_t (&v)[32]) {
 #pragma unroll
     for (int r = 0; r < 32; ++r)
         if ((r & S) == 0) {
-            const bool a = SIZE ? ((r & SIZE) == 0) : asc;
             const uint32_t x = v[r], y = v[r | S];
-            const uint32_t mn = min(x, y), mx = max(x, y);
-            v[r] = a ? mn : mx;
-            v[r | S] = a ? mx : mn;
+            v[r] = min(x, y);
+            v[r | S] = max(x, y);
         }
+}
+
+// The half-cleaners of an in-lane block of SIZE slots after its flip.
+template <int SIZE>
+__device__ __forceinline__ void bitonic_lane_clean(uint32_t (&v)[32]) {
+    if constexpr (SIZE >= 4) {
+        bitonic_lane_stage<SIZE / 4>(v);
+        bitonic_lane_clean<SIZE / 2>(v);
+    }
 }
 
 // The same Short draw by one warp: lane L holds slots 32L .. 32L+31 of the
 // 1024-slot network in registers, so partners closer than 32 slots are in
-// the same lane (compare-exchanges, their direction a constant for blocks
-// up to 16 slots) and the rest one lane-xor shuffle away; no shared memory
-// and no barrier.  On return lane L holds sorted slots 32L .. 32L+31.
+// the same lane (compare-exchanges whose slots are constants) and the rest
+// one lane-xor shuffle away; no shared memory and no barrier.  On return
+// lane L holds sorted slots 32L .. 32L+31.
 template <int P>
 __device__ __forceinline__ void short_sorted_warp(uint64_t seed, uint64_t k, uint32_t stream,
                                                   uint32_t (&v)[32]) {
@@ -116,34 +142,46 @@ __device__ __forceinline__ void short_sorted_warp(uint64_t seed, uint64_t k, uin
             v[4 * b + j] = x;
         }
     }
-    bitonic_lane_stage<1, 2>(v, true);
-    bitonic_lane_stage<2, 4>(v, true);
-    bitonic_lane_stage<1, 4>(v, true);
-    bitonic_lane_stage<4, 8>(v, true);
-    bitonic_lane_stage<2, 8>(v, true);
-    bitonic_lane_stage<1, 8>(v, true);
-    bitonic_lane_stage<8, 16>(v, true);
-    bitonic_lane_stage<4, 16>(v, true);
-    bitonic_lane_stage<2, 16>(v, true);
-    bitonic_lane_stage<1, 16>(v, true);
+    // blocks of 2 .. 32 slots: inside the lane
+    bitonic_lane_flip<2>(v);
+    bitonic_lane_flip<4>(v);
+    bitonic_lane_clean<4>(v);
+    bitonic_lane_flip<8>(v);
+    bitonic_lane_clean<8>(v);
+    bitonic_lane_flip<16>(v);
+    bitonic_lane_clean<16>(v);
+    bitonic_lane_flip<32>(v);
+    bitonic_lane_clean<32>(v);
+    // blocks of 64 .. 1024 slots: the flip and the half-cleaners of 32 slots
+    // and more across lanes, then the in-lane half-cleaners
 #pragma unroll 1
-    for (int size = 32; size <= 1024; size <<= 1) {
-        const bool asc = ((32 * lane) & size) == 0;
+    for (int size = 64; size <= 1024; size <<= 1) {
+        {
+            // mirror of slot 32 L + r: lane L ^ (size / 32 - 1), register 31 - r;
+            // the lower slot is in the lane whose bit size / 64 is clear
+            const int m = (size >> 5) - 1;
+            const bool keep_min = (lane & (size >> 6)) == 0;
+            uint32_t o[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) o[r] = __shfl_xor_sync(0xffffffffu, v[31 - r], m);
+#pragma unroll
+            for (int r = 0; r < 32; ++r) v[r] = keep_min ? min(v[r], o[r]) : max(v[r], o[r]);
+        }
 #pragma unroll 1
-        for (int stride = size >> 1; stride >= 32; stride >>= 1) {
+        for (int stride = size >> 2; stride >= 32; stride >>= 1) {
             const int m = stride >> 5;
-            const bool keep_min = ((lane & m) == 0) == asc;  // lower slot of an ascending pair
+            const bool keep_min = (lane & m) == 0;
 #pragma unroll
             for (int r = 0; r < 32; ++r) {
                 const uint32_t o = __shfl_xor_sync(0xffffffffu, v[r], m);
                 v[r] = keep_min ? min(v[r], o) : max(v[r], o);
             }
         }
-        bitonic_lane_stage<16, 0>(v, asc);
-        bitonic_lane_stage<8, 0>(v, asc);
-        bitonic_lane_stage<4, 0>(v, asc);
-        bitonic_lane_stage<2, 0>(v, asc);
-        bitonic_lane_stage<1, 0>(v, asc);
+        bitonic_lane_stage<16>(v);
+        bitonic_lane_stage<8>(v);
+        bitonic_lane_stage<4>(v);
+        bitonic_lane_stage<2>(v);
+        bitonic_lane_stage<1>(v);
     }
 }
 

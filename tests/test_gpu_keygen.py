@@ -577,3 +577,22 @@ def test_r3_forest_with_its_own_root_count(snt, ctx, P, roots, r3roots, mode, B)
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
     rpk, rsk = oracle.keygen_batch(P, 6, 50, min(B, 64), g_inject=dict(zip(offs, bads)))
     assert first_mismatch(got[0][:64], rpk) is None and first_mismatch(got[1][:64], rsk) is None
+
+
+def test_option_values_are_checked(snt, ctx):
+    # every option rejects values outside its documented range and keeps the
+    # old value
+    bad = [(snt.SNT_OPT_PDL, 2), (snt.SNT_OPT_PDL, -1), (snt.SNT_OPT_R3_ROOTS, 3),
+           (snt.SNT_OPT_R3_ROOTS, 2048), (snt.SNT_OPT_R3_OVERLAP, 4), (snt.SNT_OPT_ROOTS, 6),
+           (snt.SNT_OPT_PARTS, 3), (snt.SNT_OPT_R3_MODE, 3)]
+    for opt, val in bad:
+        before = ctx.get_option(opt)
+        with pytest.raises(snt.SntError) as e:
+            ctx.set_option(opt, val)
+        assert e.value.status == -1, (opt, val)
+        assert ctx.get_option(opt) == before
+    for opt, val in [(snt.SNT_OPT_PDL, 0), (snt.SNT_OPT_R3_ROOTS, 4), (snt.SNT_OPT_R3_OVERLAP, 3)]:
+        before = ctx.get_option(opt)
+        ctx.set_option(opt, val)
+        assert ctx.get_option(opt) == val
+        ctx.set_option(opt, before)
