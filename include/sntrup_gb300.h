@@ -364,13 +364,17 @@ snt_status snt_ctx_set_option(snt_ctx *ctx, int option, int value);
 snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
 
 /* Autotuner: times batch keygen of B keys of parameter set P on this GPU
- * (CUDA events, best of three single calls after a warm-up) under each
- * candidate layout, times the six fastest again as rounds of six calls
- * issued back to back (best of two rounds after a warm-up round), and keeps
- * the fastest of those for every later keygen call of this context with the
+ * (CUDA events around calls issued back to back: a warm-up call, then the
+ * best of two rounds of two calls) under each candidate layout, times the
+ * eight fastest again (the best of two rounds of six calls after a warm-up
+ * round), and keeps the fastest of those for every later keygen call of
+ * this context with the
  * same P and ceil(log2 B) (and for the ragged call's parameter sets whose
  * largest batch falls in that bucket); it overrides the snt_ctx_set_option
- * values there.  Candidates: R/3 lanes (4, 8, 32) x R/3 overlap (0 .. 3) x
+ * values there.  Before each timed call, when the context's scratch has
+ * 160 MiB to spare beyond the call's own, a memset of them evicts the L2
+ * (outside the call's timed span).  Candidates: R/3 lanes (4, 8, 32) x R/3
+ * overlap (0 .. 3) x
  * { tensor-core engine (1, and each of its candidates again as 3) with 1 or
  * 2 MMA tiles per warp, forests of 1, 4, 16, 64, 128 or 256 subtrees
  * (SNT_OPT_ROOTS) and R/3 mode 0, 1 or 2 (modes 1 and 2 also with an R/3
