@@ -122,6 +122,22 @@ snt_status snt_batch_keygen_host(snt_ctx *ctx, int P, uint64_t seed,
                                  uint64_t first_key_index, size_t B,
                                  uint8_t *pk_host, uint8_t *sk_host);
 
+/* The same into host memory without waiting: enqueues the generation on
+ * `stream` (as snt_batch_keygen, into a staging slot of the context's
+ * scratch) and the two device-to-host copies on the context's copy streams,
+ * and returns.  The keys are in pk_host / sk_host once snt_ctx_sync(ctx,
+ * stream) has returned SNT_OK.  With room in the budget for two staging
+ * slots (snt_ctx_max_batch counts one) consecutive calls alternate between
+ * them, so one call's copies overlap the next call's generation; a call
+ * waits on the device for the copies of the call that last used its slot.
+ * pk_host / sk_host should be page-locked (cudaHostAlloc or registered) for
+ * the copies to run asynchronously; they must stay valid and untouched
+ * until the sync.  Errors of the arguments are returned at once, device
+ * errors by the sync. */
+snt_status snt_batch_keygen_host_async(snt_ctx *ctx, int P, uint64_t seed,
+                                       uint64_t first_key_index, size_t B, uint8_t *pk_host,
+                                       uint8_t *sk_host, snt_stream stream);
+
 /* Batch key generation for callers that cannot allocate device memory (the
  * paper has no counterpart; it is a deployment variant of snt_batch_keygen).
  * Who needs it: code running while a framework's caching allocator owns the

@@ -90,6 +90,7 @@ def load():
         "snt_batch_keygen": [P, i32, u64, u64, sz, P, P, P],
         "snt_keygen_perkey": [P, i32, u64, u64, sz, P, P, P],
         "snt_batch_keygen_host": [P, i32, u64, u64, sz, P, P],
+        "snt_batch_keygen_host_async": [P, i32, u64, u64, sz, P, P, P],
         "snt_batch_keygen_static": [i32, i32, u64, u64, sz, P, P, P],
         "snt_batch_keygen_ragged": [P, sz, P, P, P, P, P, P, P],
         "snt_rq_mul": [P, i32, sz, P, P, P, P],
@@ -298,6 +299,23 @@ def snt_batch_keygen_host(ctx, P, seed, first_key_index, B, pk_host=None, sk_hos
     _check(load().snt_batch_keygen_host(ctx.handle, P, seed, first_key_index, B,
                                         pk_host.ctypes.data_as(ctypes.c_void_p),
                                         sk_host.ctypes.data_as(ctypes.c_void_p)))
+    return pk_host, sk_host
+
+
+def snt_batch_keygen_host_async(ctx, P, seed, first_key_index, B, pk_host, sk_host, stream=None):
+    """Enqueues the generation of B keys into host numpy buffers and returns;
+    the keys are there once ctx.sync(stream) has returned.  The buffers
+    should be page-locked (e.g. a pinned torch tensor's numpy view) and must
+    stay alive and untouched until the sync."""
+    pkb, skb, _, _ = snt_param_sizes(P)
+    if not (pk_host.flags.c_contiguous and pk_host.nbytes >= B * pkb):
+        raise ValueError("pk_host must be contiguous with room for %d keys" % B)
+    if not (sk_host.flags.c_contiguous and sk_host.nbytes >= B * skb):
+        raise ValueError("sk_host must be contiguous with room for %d keys" % B)
+    _check(load().snt_batch_keygen_host_async(ctx.handle, P, seed, first_key_index, B,
+                                              pk_host.ctypes.data_as(ctypes.c_void_p),
+                                              sk_host.ctypes.data_as(ctypes.c_void_p),
+                                              _stream(stream)))
     return pk_host, sk_host
 
 

@@ -440,6 +440,17 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     return SNT_OK;
 }
 
+}  // namespace
+
+snt_status snt::order_after_copies(snt_ctx *ctx, cudaStream_t st) {
+    if (!ctx->copies_pending) return SNT_OK;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_staged[i][j], 0));
+    return SNT_OK;
+}
+
+namespace {
+
 snt_status keygen_common(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, size_t B,
                          uint8_t *pk, uint8_t *sk, snt_stream stream, bool batched,
                          bool host_out) {
@@ -455,6 +466,10 @@ snt_status keygen_common(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, siz
     DeviceGuard dg(ctx->device);
     if (!dg.ok) return set_error(SNT_ECUDA, "cannot select device %d", ctx->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    {
+        const snt_status so = order_after_copies(ctx, st);
+        if (so != SNT_OK) return so;
+    }
     uint8_t *dpk = pk, *dsk = sk;
     if (host_out) {
         const size_t o = staging_offset(pi, B);
@@ -477,6 +492,60 @@ snt_status keygen_common(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, siz
     return snt_ctx_sync(ctx, stream);
 }
 
+// Host-buffer call that does not wait: generation into staging slot s of
+// the scratch (two slots when the budget has room, else one), then the two
+// device-to-host copies on the context's copy streams.  A slot is written
+// only after the copies of the call that last used it (events on the
+// caller's stream, so the whole call orders after them).
+snt_status keygen_host_async(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, size_t B,
+                             uint8_t *pk_host, uint8_t *sk_host, snt_stream stream) {
+    if (!ctx) return set_error(SNT_EINVAL, "null context");
+    ParamInfo pi;
+    if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
+    if (B == 0 || B > kMaxB) return set_error(SNT_EINVAL, "batch size %zu outside [1, %zu]", B, kMaxB);
+    if (!pk_host || !sk_host) return set_error(SNT_EINVAL, "null output buffer");
+    const size_t one = keygen_arena(pi, B, true);
+    const size_t slot = align256(B * pi.pk_bytes) + align256(B * pi.sk_bytes);
+    if (one > ctx->budget)
+        return set_error(SNT_ENOMEM, "batch of %zu keys needs %zu scratch bytes, budget %zu", B, one,
+                         ctx->budget);
+    const int nslots = (one + slot <= ctx->budget) ? 2 : 1;
+    const int s = nslots == 2 ? (ctx->stage_next & 1) : 0;
+    ctx->stage_next = s ^ 1;
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return set_error(SNT_ECUDA, "cannot select device %d", ctx->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t *dpk = ctx->arena + staging_offset(pi, B) + (size_t)s * slot;
+    uint8_t *dsk = dpk + align256(B * pi.pk_bytes);
+    if (ctx->copies_pending && (ctx->async_P != P || ctx->async_B != B)) {
+        // another layout of the scratch: after every pending copy
+        const snt_status so = order_after_copies(ctx, st);
+        if (so != SNT_OK) return so;
+    } else {
+        SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_staged[s][0], 0));
+        SNT_CUDA(cudaStreamWaitEvent(st, ctx->ev_staged[s][1], 0));
+    }
+    ctx->copies_pending = true;
+    ctx->async_P = P;
+    ctx->async_B = B;
+    snt_status r;
+    switch (P) {
+        case 653: r = run_keygen<653>(ctx, pi, seed, first, B, dpk, dsk, st, true, ctx->arena); break;
+        case 761: r = run_keygen<761>(ctx, pi, seed, first, B, dpk, dsk, st, true, ctx->arena); break;
+        default:  r = run_keygen<857>(ctx, pi, seed, first, B, dpk, dsk, st, true, ctx->arena); break;
+    }
+    if (r != SNT_OK) return r;
+    SNT_CUDA(cudaEventRecord(ctx->ev_kdone, st));
+    for (int i = 0; i < 2; ++i) {
+        SNT_CUDA(cudaStreamWaitEvent(ctx->copy[i], ctx->ev_kdone, 0));
+        SNT_CUDA(cudaMemcpyAsync(i ? sk_host : pk_host, i ? dsk : dpk,
+                                 B * (i ? pi.sk_bytes : pi.pk_bytes), cudaMemcpyDeviceToHost,
+                                 ctx->copy[i]));
+        SNT_CUDA(cudaEventRecord(ctx->ev_staged[s][i], ctx->copy[i]));
+    }
+    return SNT_OK;
+}
+
 }  // namespace
 
 snt_status snt::keygen_into(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, size_t B,
@@ -485,6 +554,10 @@ snt_status snt::keygen_into(snt_ctx *ctx, int P, uint64_t seed, uint64_t first, 
     if (!param_info(P, pi)) return set_error(SNT_EINVAL, "unknown parameter set %d", P);
     if (B == 0 || B > kMaxB) return set_error(SNT_EINVAL, "batch size %zu", B);
     if (keygen_arena(pi, B, false) > ctx->budget) return set_error(SNT_ENOMEM, "budget");
+    {
+        const snt_status so = order_after_copies(ctx, stream);
+        if (so != SNT_OK) return so;
+    }
     switch (P) {
         case 653: return run_keygen<653>(ctx, pi, seed, first, B, pk, sk, stream, true, ctx->arena, true);
         case 761: return run_keygen<761>(ctx, pi, seed, first, B, pk, sk, stream, true, ctx->arena, true);
@@ -531,6 +604,12 @@ snt_status snt_ctx_create(int device, size_t mem_budget, snt_ctx **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->tree, cudaStreamNonBlocking, prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->tune, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_low);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&c->copy[i], cudaStreamNonBlocking);
+        for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+            e = cudaEventCreateWithFlags(&c->ev_staged[i][j], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_kdone, cudaEventDisableTiming);
     // pipelined parts after the first, each a step below the one before
     for (int q = 0; q < kMaxParts - 1 && e == cudaSuccess; ++q)
         e = cudaStreamCreateWithPriority(&c->part[q], cudaStreamNonBlocking,
@@ -564,6 +643,8 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     if (ctx->tree) cudaStreamSynchronize(ctx->tree);
     if (ctx->side) cudaStreamSynchronize(ctx->side);
     for (cudaStream_t q : ctx->part)
+        if (q) cudaStreamSynchronize(q);
+    for (cudaStream_t q : ctx->copy)
         if (q) cudaStreamSynchronize(q);
     cudaDeviceSynchronize();
     if (ctx->arena) {
@@ -600,6 +681,12 @@ snt_status snt_ctx_destroy(snt_ctx *ctx) {
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     for (cudaStream_t q : ctx->part)
         if (q) cudaStreamDestroy(q);
+    for (int i = 0; i < 2; ++i) {
+        if (ctx->copy[i]) cudaStreamDestroy(ctx->copy[i]);
+        for (cudaEvent_t ev : ctx->ev_staged[i])
+            if (ev) cudaEventDestroy(ev);
+    }
+    if (ctx->ev_kdone) cudaEventDestroy(ctx->ev_kdone);
     if (ctx->ev_pfork) cudaEventDestroy(ctx->ev_pfork);
     for (int q = 0; q < kMaxParts; ++q) {
         if (ctx->ev_pdone[q]) cudaEventDestroy(ctx->ev_pdone[q]);
@@ -631,6 +718,8 @@ snt_status snt_ctx_sync(snt_ctx *ctx, snt_stream stream) {
     SNT_CUDA(cudaStreamSynchronize(ctx->tree));
     SNT_CUDA(cudaStreamSynchronize(ctx->side));
     for (cudaStream_t q : ctx->part) SNT_CUDA(cudaStreamSynchronize(q));
+    for (cudaStream_t q : ctx->copy) SNT_CUDA(cudaStreamSynchronize(q));
+    ctx->copies_pending = false;
     int err = 0;
     SNT_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
@@ -656,6 +745,12 @@ snt_status snt_keygen_perkey(snt_ctx *ctx, int P, uint64_t seed, uint64_t first_
 snt_status snt_batch_keygen_host(snt_ctx *ctx, int P, uint64_t seed, uint64_t first_key_index,
                                  size_t B, uint8_t *pk_host, uint8_t *sk_host) {
     return keygen_common(ctx, P, seed, first_key_index, B, pk_host, sk_host, nullptr, true, true);
+}
+
+snt_status snt_batch_keygen_host_async(snt_ctx *ctx, int P, uint64_t seed,
+                                       uint64_t first_key_index, size_t B, uint8_t *pk_host,
+                                       uint8_t *sk_host, snt_stream stream) {
+    return keygen_host_async(ctx, P, seed, first_key_index, B, pk_host, sk_host, stream);
 }
 
 snt_status snt_enc(snt_ctx *ctx, int P, size_t n, const uint8_t *pk_dev, uint64_t seed,
@@ -895,6 +990,8 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
     const size_t o = staging_offset(pi, B);
     uint8_t *dpk = ctx->arena + o, *dsk = ctx->arena + o + align256(B * pi.pk_bytes);
     snt_stream ts = reinterpret_cast<snt_stream>(ctx->tune);
+    SNT_CUDA(cudaStreamSynchronize(ctx->copy[0]));  // the flush overwrites staging slots
+    SNT_CUDA(cudaStreamSynchronize(ctx->copy[1]));
     const snt_ctx::Tuned saved = ctx->tuned[pidx(P)][bbucket(B)];
     // candidates: R/3 lanes x overlap x (tensor-core engine with 1 or 2 tiles
     // per warp, or CUDA-core engine with tree split 4 or 8)

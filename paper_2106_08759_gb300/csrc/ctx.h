@@ -43,6 +43,16 @@ struct snt_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr, ev_r3fork = nullptr;
     cudaEvent_t ev_gready = nullptr;       // R/3 batch path: every g final
     cudaStream_t side = nullptr;  // low priority: leaf-pair products s beside the root inversions
+    // host-buffer calls that do not wait (snt_batch_keygen_host_async): two
+    // staging slots, the copy streams, per slot the events of its pk and sk
+    // copies, and the event the copies start from
+    cudaStream_t copy[2] = {};
+    cudaEvent_t ev_staged[2][2] = {};
+    cudaEvent_t ev_kdone = nullptr;
+    int stage_next = 0;
+    bool copies_pending = false;  // such copies may be in flight (until snt_ctx_sync)
+    int async_P = 0;              // parameter set and batch size of the last such call
+    size_t async_B = 0;
     cudaEvent_t ev_sfork = nullptr, ev_sready = nullptr;  // fork to / join from the side stream
     uint32_t *d_r3fac[3] = {nullptr, nullptr, nullptr};  // F_3 factors per parameter set
     uint32_t *d_r3screen[3] = {nullptr, nullptr, nullptr};  // small factors' remainder tables
@@ -92,5 +102,9 @@ inline int bbucket(size_t B) {
 // Device copy of the F_3 factors of x^P - x - 1 for the R/3 batch path
 // (computed on the host on first use; r3batch.cu).
 snt_status r3_factors_for(snt_ctx *ctx, int P, R3Factors &out);
+// Orders stream st after the copies of snt_batch_keygen_host_async calls
+// that may still read their staging slots, before st's work overwrites
+// scratch (any call that uses the context's scratch calls it first).
+snt_status order_after_copies(snt_ctx *ctx, cudaStream_t st);
 snt_status r3_screen_for(snt_ctx *ctx, int P, R3Screen &out);
 }  // namespace snt

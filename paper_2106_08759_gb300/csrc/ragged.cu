@@ -357,6 +357,10 @@ extern "C" snt_status snt_batch_keygen_ragged(snt_ctx *ctx, size_t n_batches, co
     if (!dg.ok) return set_error(SNT_ECUDA, "cannot select device %d", ctx->device);
     cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
     uint8_t *tables = ctx->arena + table_off;
+    {
+        const snt_status so = order_after_copies(ctx, caller);
+        if (so != SNT_OK) return so;
+    }
     // per-call data first (pageable source: staged before the call returns)
     SNT_CUDA_R(cudaMemcpyAsync(tables, host.data(), tbytes, cudaMemcpyHostToDevice, caller));
 

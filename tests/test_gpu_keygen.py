@@ -596,3 +596,31 @@ def test_option_values_are_checked(snt, ctx):
         ctx.set_option(opt, val)
         assert ctx.get_option(opt) == val
         ctx.set_option(opt, before)
+
+
+def test_host_async_calls_overlap_and_match(snt):
+    # several calls that do not wait, into pinned host buffers, alternating
+    # staging slots, then a change of batch size (every pending copy first)
+    # and a device-buffer call in between; every batch equals the device
+    # call's keys once the context is synced
+    import torch
+    calls = [(761, 300, 11, 0), (761, 300, 12, 300), (761, 300, 13, 600), (653, 64, 14, 0),
+             (761, 300, 15, 900)]
+    with snt.Context(0, 256 << 20) as c:
+        outs = []
+        for P, B, seed, first in calls:
+            pkb, skb, _, _ = snt.snt_param_sizes(P)
+            hpk = torch.zeros(B * pkb, dtype=torch.uint8).pin_memory().numpy().reshape(B, pkb)
+            hsk = torch.zeros(B * skb, dtype=torch.uint8).pin_memory().numpy().reshape(B, skb)
+            snt.snt_batch_keygen_host_async(c, P, seed, first, B, hpk, hsk)
+            outs.append((hpk, hsk))
+            if seed == 12:  # a device call while copies may be pending
+                ref_mid = gpu_keygen(snt, c, 857, 3, 0, 5)
+        c.sync()
+        for (P, B, seed, first), (hpk, hsk) in zip(calls, outs):
+            rpk, rsk = gpu_keygen(snt, c, P, seed, first, B)
+            assert np.array_equal(hpk, rpk) and np.array_equal(hsk, rsk), (P, B, seed)
+        opk, osk = oracle.keygen_batch(857, 3, 0, 5)
+        assert first_mismatch(ref_mid[0], opk) is None and first_mismatch(ref_mid[1], osk) is None
+    opk, osk, _ = oracle.keygen(761, 15, 900 + 299)
+    assert np.array_equal(outs[-1][0][-1], opk) and np.array_equal(outs[-1][1][-1], osk)
