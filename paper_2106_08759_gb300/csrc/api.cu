@@ -326,7 +326,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
             if (!r3chk)  // keys whose g was redrawn by the deferred per-key R/3 kernel
                 SNT_CUDA(launch_fixup<P>(km, fix_count, fix_keys, gfix, inv_leaves, pi.pk_bytes,
                                          pi.sk_bytes, 2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st,
-                                         fuse ? leaves : nullptr, lm1, fixup_grid(B)));
+                                         fuse ? leaves : nullptr, lm1, fixup_grid(B), Bi));
             if (tm) SNT_CUDA(cudaEventRecord(ev[10], st));
             SNT_CUDA(cudaEventRecord(ctx->ev_done, st));
             SNT_CUDA(cudaStreamWaitEvent(caller, ctx->ev_done, 0));
@@ -431,7 +431,7 @@ snt_status run_keygen(snt_ctx *ctx, const ParamInfo &pi, uint64_t seed, uint64_t
     if (!r3chk)  // keys whose g was redrawn by the deferred per-key R/3 kernel
         SNT_CUDA(launch_fixup<P>(km, fix_count, fix_keys, gfix, inv_leaves, pi.pk_bytes,
                                  pi.sk_bytes, 2 * sb, 3 * sb + pi.pk_bytes, pi.sched, st,
-                                 fuse ? leaves : nullptr, lm1, fixup_grid(B)));
+                                 fuse ? leaves : nullptr, lm1, fixup_grid(B), Bi));
     if (tm) SNT_CUDA(cudaEventRecord(ev[10], st));
     if (!inline_stream) {  // join back into the caller's stream
         SNT_CUDA(cudaEventRecord(ctx->ev_done, st));

@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(Tp<P>::NT)
 k_fixup(KeyMap km, const int *__restrict__ fix_count, const int *__restrict__ fix_keys,
         const int8_t *__restrict__ gfix, const int16_t *__restrict__ ainv, int pk_bytes,
         int sk_bytes, int sk_pk_off, int hash_off, EncSched S,
-        const int16_t *__restrict__ leaves, LevelMap lm1) {
+        const int16_t *__restrict__ leaves, LevelMap lm1, bool hash_here) {
     pdl_enter();
     using G = Geo<P>;
     __shared__ __align__(16) int As[Tp<P>::p8];
@@ -378,7 +378,7 @@ k_fixup(KeyMap km, const int *__restrict__ fix_count, const int *__restrict__ fi
             pkk[b] = ob[b];
             skk[sk_pk_off + b] = ob[b];
         }
-        if (threadIdx.x == 0) sha512_prefixed(4, ob, pk_bytes, nullptr, 0, skk + hash_off);
+        if (hash_here && threadIdx.x == 0) sha512_prefixed(4, ob, pk_bytes, nullptr, 0, skk + hash_off);
     }
 }
 
@@ -414,8 +414,13 @@ constexpr int kShaWkBytes = 2 * 80 * 32 * 8;
 constexpr int sha_blk_bytes(int pk_bytes) { return 32 * pk_bytes + 32 * 32; }
 constexpr int kShaBlkMax = sha_blk_bytes(1322);  // the opt-in size: sntrup857's 1322-byte pk
 
+// With list != null the CTA's keys are list[base .. base + 31] of the first
+// *list_n entries (the fix-up's list): the list is another kernel's output,
+// so the kernel waits for its predecessors first, and a CTA past the list's
+// end does nothing.
 __global__ void __launch_bounds__(64, 1)
-k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
+k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off,
+            const int *__restrict__ list, const int *__restrict__ list_n) {
     extern __shared__ __align__(16) uint8_t sm[];
     uint64_t(*wk)[80][32] = reinterpret_cast<uint64_t(*)[80][32]>(sm);  // [slot][round][key]
     __shared__ uint64_t ks[80];  // the round constants
@@ -423,7 +428,14 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
     uint8_t *blk = sm + kShaWkBytes;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int base = blockIdx.x * 32;
+    if (list) {
+        pdl_enter();
+        B = min(B, *list_n);
+        if (base >= B) return;  // CTA-uniform
+    }
     const int nkeys = min(32, B - base);
+    // key of lane j of this CTA
+    auto key_of = [&](int j) { return list ? list[base + j] : base + j; };
     // The keys form runs whose rows are contiguous in device memory (one run
     // for a single batch).  A run goes to a shared-memory offset congruent
     // to its source address mod 16, so that its middle moves in aligned
@@ -436,8 +448,9 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
     if (warp == 0) {
         uintptr_t row = 0;
         if (lane < nkeys) {
-            const BatchDesc d = key_batch(km, base + lane);
-            row = reinterpret_cast<uintptr_t>(d.pk + (size_t)(base + lane - d.key_base) * pk_bytes);
+            const int key = key_of(lane);
+            const BatchDesc d = key_batch(km, key);
+            row = reinterpret_cast<uintptr_t>(d.pk + (size_t)(key - d.key_base) * pk_bytes);
         }
         const uintptr_t prev = __shfl_up_sync(0xffffffffu, (unsigned long long)row, 1);
         const bool start = lane < nkeys && (lane == 0 || row != prev + (uintptr_t)pk_bytes);
@@ -462,9 +475,9 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
         __syncwarp();
         if (lane < nkeys) rowoff[lane] = run_dst[r] + (lane - run_first[r]) * pk_bytes;
     }
-    // the row lookups above read only the batch table; the rows themselves
-    // are the previous kernel's output
-    pdl_enter();
+    // the row lookups above read only the batch table (and the list, after
+    // the wait); the rows themselves are the previous kernel's output
+    if (!list) pdl_enter();
     __syncthreads();
     for (int q = 0; q < nruns; ++q) {
         const uint8_t *src = run_src[q];
@@ -550,8 +563,9 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off) {
         if (b0 + 2 < nblk) nbar_arrive(3 + slot, 64);
     }
     if (lane >= nkeys) return;
-    const BatchDesc dk = key_batch(km, base + lane);
-    uint8_t *out = dk.sk + (size_t)(base + lane - dk.key_base) * sk_bytes + hash_off;
+    const int key = key_of(lane);
+    const BatchDesc dk = key_batch(km, key);
+    uint8_t *out = dk.sk + (size_t)(key - dk.key_base) * sk_bytes + hash_off;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -582,9 +596,18 @@ template <int P>
 cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_keys,
                          const int8_t *gfix, const int16_t *ainv, int pk_bytes, int sk_bytes,
                          int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st,
-                         const int16_t *leaves, LevelMap lm1, int grid) {
+                         const int16_t *leaves, LevelMap lm1, int grid, int nkeys) {
+    // sntrup653 redraws about one g in 27: its fix-up hashes the new public
+    // keys afterwards a lane per key; for the others (a redraw about once in
+    // 3^19 keys) each fix-up CTA hashes its key itself
+    const bool hash_here = P != 653;
     SNT_LAUNCH(k_fixup<P>, grid, Tp<P>::NT, 0, st, km, fix_count, fix_keys, gfix, ainv, pk_bytes,
-        sk_bytes, sk_pk_off, hash_off, S, leaves, lm1);
+        sk_bytes, sk_pk_off, hash_off, S, leaves, lm1, hash_here);
+    if (!hash_here) {
+        const cudaError_t e = launch_sha512_pk(km, nkeys, pk_bytes, sk_bytes, hash_off, st,
+                                               fix_keys, fix_count);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 
@@ -621,7 +644,7 @@ cudaError_t launch_leaf_s(int n1, const int8_t *gbuf, const int16_t *leaves, Lev
 }
 
 cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
-                             int hash_off, cudaStream_t st) {
+                             int hash_off, cudaStream_t st, const int *list, const int *list_n) {
     const int smem = kShaWkBytes + sha_blk_bytes(pk_bytes);
     // the opt-in above 48 KB, once per device at the largest size any
     // parameter set needs (host state, not stream work)
@@ -637,7 +660,7 @@ cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_b
     }
     if (smem > kShaWkBytes + kShaBlkMax) return cudaErrorInvalidValue;
     SNT_LAUNCH(k_sha512_pk, (nkeys + 31) / 32, 64, smem, st, km, nkeys, pk_bytes, sk_bytes,
-        hash_off);
+        hash_off, list, list_n);
     return cudaGetLastError();
 }
 
@@ -646,7 +669,7 @@ cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_b
                                             int, int, int, const EncSched &, cudaStream_t, bool); \
     template cudaError_t launch_fixup<P>(const KeyMap &, const int *, const int *, const int8_t *, \
                                          const int16_t *, int, int, int, int, const EncSched &,   \
-                                         cudaStream_t, const int16_t *, LevelMap, int);           \
+                                         cudaStream_t, const int16_t *, LevelMap, int, int);      \
     template cudaError_t launch_finalize_pair<P>(const KeyMap &, int, const int8_t *,            \
                                                  const int16_t *, const int16_t *, LevelMap, int, \
                                                  int, int, const EncSched &, cudaStream_t,        \

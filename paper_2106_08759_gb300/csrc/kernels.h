@@ -234,12 +234,13 @@ cudaError_t launch_r3_inv_jump(int n, const int16_t *in, long in_stride, int16_t
                                cudaStream_t st, const int *idx = nullptr);
 // Keys on the resampling list: h with the final g, pk, sk's copy and hash;
 // `grid` CTAs take list entries in turn (the list's length is on the device:
-// size it by how many keys can be redrawn).
+// size it by how many keys can be redrawn); nkeys: the call's key count, the
+// list's largest possible length.
 template <int P>
 cudaError_t launch_fixup(const KeyMap &km, const int *fix_count, const int *fix_keys,
                          const int8_t *gfix, const int16_t *ainv, int pk_bytes, int sk_bytes,
                          int sk_pk_off, int hash_off, const EncSched &S, cudaStream_t st,
-                         const int16_t *leaves = nullptr, LevelMap lm1 = LevelMap{}, int grid = 8);
+                         const int16_t *leaves, LevelMap lm1, int grid, int nkeys);
 // sbuf (optional): the leaf-pair products s of launch_leaf_s, else formed here.
 template <int P>
 cudaError_t launch_finalize_pair(const KeyMap &km, int n1, const int8_t *gbuf,
@@ -256,8 +257,11 @@ template <int P>
 cudaError_t launch_finalize(const KeyMap &km, int nkeys, const int8_t *gbuf, const int16_t *ainv,
                             int pk_bytes, int sk_bytes, int sk_pk_off, const EncSched &S,
                             cudaStream_t st, bool mma = false);
+// list (optional): hash the keys list[0 .. *list_n) (at most nkeys) instead
+// of keys 0 .. nkeys - 1.
 cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
-                             int hash_off, cudaStream_t st);
+                             int hash_off, cudaStream_t st, const int *list = nullptr,
+                             const int *list_n = nullptr);
 template <int P>
 cudaError_t launch_encap(const EncMap &em, int n, int pk_bytes, int ct_bytes, const EncSched &Spk,
                          const EncSched &Sct, cudaStream_t st);

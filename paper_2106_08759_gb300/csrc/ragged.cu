@@ -220,7 +220,7 @@ snt_status launch_group(snt_ctx *ctx, const Group &g, uint8_t *tables, cudaStrea
         SNT_CUDA_R(launch_fixup<P>(km, fix_count, fix_keys, gfix,
                                    g.fuse ? nodes + (size_t)g.lev_off[1] * pi.pad : nodes,
                                    pi.pk_bytes, pi.sk_bytes, 2 * sb, 3 * sb + pi.pk_bytes, pi.sched,
-                                   st, g.fuse ? nodes : nullptr, lmap(1), fixup_grid(g.nkeys)));
+                                   st, g.fuse ? nodes : nullptr, lmap(1), fixup_grid(g.nkeys), g.nkeys));
     return SNT_OK;
 }
 
