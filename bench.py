@@ -71,16 +71,16 @@ def tree_levels(n):
 # summed over the phase's launches of one call, from the committed ncu
 # launch-list capture of one keygen call (caches flushed by ncu before each
 # launch), keyed by kernel; a kernel is absent until a capture of its current
-# code exists.  Writes stay in L2.  Engine 3 and the R/3 forest: 16 subtrees
+# code exists.  Writes stay in L2.  Engine 3: 16 subtrees, the R/3 forest 4
 # (the layout of the capture); engine 1: 64 subtrees.
 NCU_TRAFFIC_BYTES = {
     "k_tree_up_mma": 12532992,
     "k_tree_down_mma": 9324544,
-    "k_tree_up_mma (one wide limb)": 12725760,
-    "k_tree_down_mma (one wide limb)": 9619200,
-    "k_rq_inv_jump<761, 4591>": 111104,
-    "k_finalize_pair<761>": 9502720,
-    "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 38189056,
+    "k_tree_up_mma (one wide limb)": 12721152,
+    "k_tree_down_mma (one wide limb)": 9627904,
+    "k_rq_inv_jump<761, 4591>": 113664,
+    "k_finalize_pair<761>": 9503232,
+    "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 38448384,
 }
 
 
