@@ -72,8 +72,10 @@ snt_status snt_ctx_destroy(snt_ctx *ctx);
 /* Largest B accepted by the keygen calls of this context for parameter set P. */
 snt_status snt_ctx_max_batch(snt_ctx *ctx, int P, size_t *max_B);
 
-/* Wait for all work the context issued on `stream` and read (then clear) the
- * device error word.  Returns SNT_OK if no device-side failure occurred. */
+/* Wait for all work the context issued on `stream` (and on its own streams,
+ * the host copies of snt_batch_keygen_host_async included) and read (then
+ * clear) the device error word.  Returns SNT_OK if no device-side failure
+ * occurred. */
 snt_status snt_ctx_sync(snt_ctx *ctx, snt_stream stream);
 
 /* Batch key generation (Algorithm 1 with a product tree for batchInv in R/q).
