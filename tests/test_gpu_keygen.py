@@ -408,7 +408,7 @@ def test_benchmarked_layout_b4096_vs_perkey_and_oracle(snt, pool):
     # forest rule of the library: for B = 4096 every power of two up to 256
     # divides B and fits the node rows, so K = the tuned root count
     K = tuned["roots"]
-    assert K in (1, 4, 16, 64, 128, 256)
+    assert K in (1, 4, 16, 32, 64, 128, 256)
     sub = B // K
     ends = [x for j in range(K) for x in (j * sub, j * sub + sub - 1)]
     rng = np.random.default_rng(3)
@@ -554,7 +554,8 @@ def test_r3_from_the_end_of_the_up_sweep(snt, ctx, r3mode, roots, B):
 
 
 @pytest.mark.parametrize("P,roots,r3roots,mode,B", [
-    (761, 64, 4, 2, 4096), (761, 128, 16, 1, 1024), (653, 64, 1, 2, 300), (857, 4, 16, 2, 96)])
+    (761, 64, 4, 2, 4096), (761, 32, 4, 2, 4096), (761, 128, 16, 1, 1024), (653, 64, 1, 2, 300),
+    (857, 4, 16, 2, 96)])
 def test_r3_forest_with_its_own_root_count(snt, ctx, P, roots, r3roots, mode, B):
     # the R/3 forest with another number of subtrees than the R/q forest, with
     # one injected zero divisor per factor (the screen, the failing R/3
