@@ -232,7 +232,8 @@ class ClockSampler:
 
 # --------------------------------------------------------- algorithmic ops
 def _measured_peaks():
-    """The measured peaks of this GPU pool, if the file is present."""
+    """The measured copy and GEMM peaks of this GPU model (MEASURED_PEAKS.json),
+    if the file is present."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
