@@ -23,12 +23,11 @@
 #include "mixed.cuh"
 #include "sha512.cuh"
 #include "short.cuh"
-#include "toeplitz.cuh"
+#include "mma_mul.cuh"
 
 namespace snt {
 
 constexpr int KEM_THREADS = 256;
-constexpr int KEM_SPLIT = 2;  // products use 2 * p8/8 <= 256 threads
 
 // Items per CTA: a CTA runs the arithmetic of its items one after another
 // with all its threads, then warp 0 computes their hashes, one lane per item
@@ -55,6 +54,44 @@ __device__ __forceinline__ void g2s_bytes(uint8_t *dst, const uint8_t *src, int 
         if (b < n) dst[b] = (uint8_t)v[k];
     }
 }
+// One ring product out = a * b in R/q (Q = q) or R/3 (Q = 3), Sec. 2.1's
+// x^p = x + 1, on the tensor cores (mma_mul.cuh): a is small (coefficients of
+// magnitude at most 3) and takes the vector side, b the Toeplitz side (any
+// centred residue for R/q; -1, 0, 1 for R/3).  a, b and out are centred int16
+// rows of Geo<P>::pad entries in shared memory; out may be a or b (both are
+// copied into the product's tables first) and is written up to the pad with
+// zeros beyond p.  Called by every thread of the CTA; the MMA warps are the
+// first MmaGeo<P, 1>::NW of its 8.
+template <int P, int Q>
+__device__ __forceinline__ void kem_mul(const int16_t *a, const int16_t *b, int16_t *out,
+                                        MmaE<P, 1> &E, MmaA<P, 1> &A) {
+    using M = MmaGeo<P, 1>;
+    static_assert(M::NW <= KEM_THREADS / 32, "one warp per MMA tile");
+    constexpr int MA = Q == 3 ? MODE_SAE : MODE_SA;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __syncthreads();  // a and b written
+    mma_fill_a<P, 1, MA>(a, A, tid, KEM_THREADS);
+    mma_fill_b<P, 1>(b, E, tid, KEM_THREADS);
+    __syncthreads();
+    mma_fill_pe<P, 1, MA, Q>(E, tid, KEM_THREADS);
+    __syncthreads();
+    const MmaA<P, 1> *const As[1] = {&A};
+    float acc[1][1][3][4];
+    if (warp < M::NW) mma_tiles<P, 1, 1, MA>(E, As, warp, lane, acc);
+    __syncthreads();  // the vector records are read; the staging area overlays them
+    if (warp < M::NW) mma_stage<P, 1, 1, MA, Q>(A, warp, lane, 0, acc);
+    __syncthreads();
+    mma_finish<P, 1, Q>(A, (int)E.b[M::p - 1], out, Geo<P>::pad, tid, KEM_THREADS);
+    __syncthreads();  // out complete; the tables free
+}
+
+// The two product tables of a KEM CTA, in one shared buffer.
+template <int P> struct KemMul {
+    static constexpr size_t eoff = 0;
+    static constexpr size_t aoff = (sizeof(MmaE<P, 1>) + 15) / 16 * 16;
+    static constexpr size_t bytes = aoff + sizeof(MmaA<P, 1>);
+};
+
 inline int kem_items_per_cta(int n, int sms) {
     const int ipc = n / (8 * sms);
     return ipc < 1 ? 1 : (ipc > KEM_MAX_IPC ? KEM_MAX_IPC : ipc);
@@ -78,16 +115,16 @@ template <int P>
 __global__ void __launch_bounds__(KEM_THREADS, 4)
 k_encap(EncMap em, int n, int ipc, int pk_bytes, int ct_bytes, EncSched Spk, EncSched Sct) {
     using G = Geo<P>;
-    constexpr int NT = Tp<P>::NT;
     __shared__ __align__(16) uint8_t pkb[1344];
     __shared__ __align__(16) uint8_t ctb[1216];
-    __shared__ __align__(16) int As[Tp<P>::p8];
-    __shared__ __align__(16) int Es[Tp<P>::ESZ];
-    __shared__ int part[(KEM_SPLIT - 1) * Tp<P>::p8];
+    __shared__ __align__(16) uint8_t mm[KemMul<P>::bytes];
     __shared__ uint32_t R[2][G::pad];
     __shared__ __align__(16) uint32_t xs[1024];
-    __shared__ int hs[G::pad];
+    __shared__ __align__(16) int16_t hv[G::pad];
+    __shared__ __align__(16) int16_t rv[G::pad];
     __shared__ uint8_t renc[KEM_MAX_IPC][G::small_bytes];
+    MmaE<P, 1> &mE = *reinterpret_cast<MmaE<P, 1> *>(mm + KemMul<P>::eoff);
+    MmaA<P, 1> &mA = *reinterpret_cast<MmaA<P, 1> *>(mm + KemMul<P>::aoff);
     const int first = blockIdx.x * ipc;
     const int cnt = min(ipc, n - first);
     if (cnt <= 0) return;
@@ -98,15 +135,14 @@ k_encap(EncMap em, int n, int ipc, int pk_bytes, int ct_bytes, EncSched Spk, Enc
         g2s_bytes<(sizeof(pkb) + KEM_THREADS - 1) / KEM_THREADS>(pkb, item.pk, pk_bytes, tid);
         __syncthreads();
         const int cur = mixed_decode<G::pad>(pkb, Spk, R);
-        for (int i = tid; i < G::pad; i += KEM_THREADS) hs[i] = (i < P) ? (int)R[cur][i] - G::half : 0;
-        __syncthreads();
-        fill_E<P, int>(hs, Es);
+        for (int i = tid; i < G::pad; i += KEM_THREADS)
+            hv[i] = (int16_t)((i < P) ? (int)R[cur][i] - G::half : 0);
         uint32_t v[4];
         short_sorted_words<P>(em.seed, item.k, STREAM_ENC, v, xs);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int j = 4 * tid + q;
-            if (j < Tp<P>::p8) As[j] = (j < P) ? (int)(v[q] & 3u) - 1 : 0;
+            if (j < G::pad) rv[j] = (int16_t)((j < P) ? (int)(v[q] & 3u) - 1 : 0);
         }
         if (tid < G::small_bytes) {
             uint32_t byte = 0;
@@ -115,24 +151,11 @@ k_encap(EncMap em, int n, int ipc, int pk_bytes, int ct_bytes, EncSched Spk, Enc
                 if (4 * tid + q < P) byte |= (v[q] & 3u) << (2 * q);
             renc[r][tid] = (uint8_t)byte;
         }
-        __syncthreads();
         // c = Round(h r)
-        int acc[1][8];
-        const int *const A1[1] = {As};
-        toeplitz_split<P, 1, KEM_SPLIT>(A1, Es, part, acc);
-        const int tloc = tid % NT;
-        const bool active = tid < NT;
-        const int bl[1] = {hs[P - 1]};
-        toeplitz_finish<P, 1>(A1, bl, acc, tloc, active);
-        if (active) {
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int j = 8 * tloc + t;
-                if (j < P) {
-                    const int c = acc[0][t] - cmod<3>(acc[0][t]);
-                    R[0][j] = (uint32_t)((c + G::half) / 3);
-                }
-            }
+        kem_mul<P, G::q>(rv, hv, hv, mE, mA);
+        for (int j = tid; j < P; j += KEM_THREADS) {
+            const int c = (int)hv[j] - cmod<3>((int)hv[j]);
+            R[0][j] = (uint32_t)((c + G::half) / 3);
         }
         __syncthreads();
         mixed_encode<G::pad>(R, Sct, ctb);
@@ -177,21 +200,19 @@ __global__ void __launch_bounds__(KEM_THREADS, 4)
 k_decap(DecMap dm, int n, int ipc, int pk_bytes, int sk_bytes, int ct_bytes, EncSched Spk,
         EncSched Sct) {
     using G = Geo<P>;
-    constexpr int NT = Tp<P>::NT;
     constexpr int SB = G::small_bytes;
     __shared__ __align__(16) uint8_t skb[2016];
     __shared__ __align__(16) uint8_t ctb[1216];
     __shared__ __align__(16) uint8_t ct2[1216];
-    __shared__ __align__(16) int As[Tp<P>::p8];
-    __shared__ __align__(16) int Es[Tp<P>::ESZ];
-    __shared__ int part[(KEM_SPLIT - 1) * Tp<P>::p8];
+    __shared__ __align__(16) uint8_t mm[KemMul<P>::bytes];
     __shared__ uint32_t R[2][G::pad];
-    __shared__ int hs[G::pad];
-    __shared__ int8_t vv[G::pad];
-    __shared__ int8_t rr[G::pad];
+    __shared__ __align__(16) int16_t va[G::pad];
+    __shared__ __align__(16) int16_t vb[G::pad];
     __shared__ uint8_t renc[KEM_MAX_IPC][SB];
     __shared__ int cmatch[KEM_MAX_IPC];  // the re-encryption's rounded part equals ct's
     __shared__ int weight;
+    MmaE<P, 1> &mE = *reinterpret_cast<MmaE<P, 1> *>(mm + KemMul<P>::eoff);
+    MmaA<P, 1> &mA = *reinterpret_cast<MmaA<P, 1> *>(mm + KemMul<P>::aoff);
     const int first = blockIdx.x * ipc;
     const int cnt = min(ipc, n - first);
     if (cnt <= 0) return;
@@ -204,87 +225,44 @@ k_decap(DecMap dm, int n, int ipc, int pk_bytes, int sk_bytes, int ct_bytes, Enc
         if (tid == 0) weight = 0;
         __syncthreads();
         const uint8_t *pkb = skb + 2 * SB;
-        // c = Rounded_decode(C); a = 3f; v
+        // e = 3 f c in R/q (c = Rounded_decode(C)), then mod 3
         int cur = mixed_decode<G::pad>(ctb, Sct, R);
         for (int i = tid; i < G::pad; i += KEM_THREADS) {
-            hs[i] = (i < P) ? 3 * (int)R[cur][i] - G::half : 0;
-            vv[i] = (int8_t)((i < P) ? (int)((skb[SB + i / 4] >> (2 * (i % 4))) & 3u) - 1 : 0);
+            vb[i] = (int16_t)((i < P) ? 3 * (int)R[cur][i] - G::half : 0);
+            va[i] = (int16_t)((i < P) ? 3 * ((int)((skb[i / 4] >> (2 * (i % 4))) & 3u) - 1) : 0);
         }
-        for (int i = tid; i < Tp<P>::p8; i += KEM_THREADS)
-            As[i] = (i < P) ? 3 * ((int)((skb[i / 4] >> (2 * (i % 4))) & 3u) - 1) : 0;
-        __syncthreads();
-        fill_E<P, int>(hs, Es);
-        __syncthreads();
-        const int tloc = tid % NT;
-        const bool active = tid < NT;
-        int acc[1][8];
-        const int *const A1[1] = {As};
-        {   // e = 3 f c in R/q, then mod 3
-            toeplitz_split<P, 1, KEM_SPLIT>(A1, Es, part, acc);
-            const int bl[1] = {hs[P - 1]};
-            toeplitz_finish<P, 1>(A1, bl, acc, tloc, active);
+        kem_mul<P, G::q>(va, vb, va, mE, mA);
+        for (int i = tid; i < G::pad; i += KEM_THREADS) {
+            va[i] = (int16_t)cmod<3>((int)va[i]);
+            vb[i] = (int16_t)((i < P) ? (int)((skb[SB + i / 4] >> (2 * (i % 4))) & 3u) - 1 : 0);
         }
-        __syncthreads();  // all reads of As / Es done
-        if (active) {
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int j = 8 * tloc + t;
-                if (j < Tp<P>::p8) As[j] = (j < P) ? cmod<3>(acc[0][t]) : 0;
-            }
-        }
-        fill_E<P, int8_t, 3>(vv, Es);
-        __syncthreads();
-        {   // r' = e v in R/3
-            toeplitz_split<P, 1, KEM_SPLIT, 3>(A1, Es, part, acc);
-            const int bl[1] = {(int)vv[P - 1]};
-            toeplitz_finish<P, 1, 3>(A1, bl, acc, tloc, active);
-        }
-        if (active) {
-            int cnt = 0;
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int j = 8 * tloc + t;
-                if (j < P) {
-                    rr[j] = (int8_t)acc[0][t];
-                    cnt += (acc[0][t] != 0);
-                }
-            }
-            atomicAdd(&weight, cnt);
+        // r' = e v in R/3, and its weight
+        kem_mul<P, 3>(va, vb, va, mE, mA);
+        {
+            int nz = 0;
+            for (int j = tid; j < P; j += KEM_THREADS) nz += (va[j] != 0);
+            nz = __reduce_add_sync(0xffffffffu, nz);
+            if ((tid & 31) == 0) atomicAdd(&weight, nz);
         }
         __syncthreads();
         const bool wok = (weight == G::w);
-        for (int j = tid; j < G::pad; j += KEM_THREADS) {
-            const int8_t dflt = (int8_t)(j < G::w ? 1 : 0);
-            rr[j] = (j < P) ? (wok ? rr[j] : dflt) : (int8_t)0;
-        }
+        if (!wok)
+            for (int j = tid; j < P; j += KEM_THREADS) va[j] = (int16_t)(j < G::w ? 1 : 0);
         __syncthreads();
         // re-encrypt r': h from pk, c' = Round(h r')
         cur = mixed_decode<G::pad>(pkb, Spk, R);
-        for (int i = tid; i < G::pad; i += KEM_THREADS) hs[i] = (i < P) ? (int)R[cur][i] - G::half : 0;
-        for (int i = tid; i < Tp<P>::p8; i += KEM_THREADS) As[i] = (i < P) ? (int)rr[i] : 0;
+        for (int i = tid; i < G::pad; i += KEM_THREADS)
+            vb[i] = (int16_t)((i < P) ? (int)R[cur][i] - G::half : 0);
         for (int b = tid; b < SB; b += KEM_THREADS) {
             uint32_t byte = 0;
             for (int r = 0; r < 4; ++r)
-                if (4 * b + r < P) byte |= (uint32_t)(rr[4 * b + r] + 1) << (2 * r);
+                if (4 * b + r < P) byte |= (uint32_t)(va[4 * b + r] + 1) << (2 * r);
             renc[it_r][b] = (uint8_t)byte;
         }
-        __syncthreads();
-        fill_E<P, int>(hs, Es);
-        __syncthreads();
-        {
-            toeplitz_split<P, 1, KEM_SPLIT>(A1, Es, part, acc);
-            const int bl[1] = {hs[P - 1]};
-            toeplitz_finish<P, 1>(A1, bl, acc, tloc, active);
-        }
-        if (active) {
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int j = 8 * tloc + t;
-                if (j < P) {
-                    const int c = acc[0][t] - cmod<3>(acc[0][t]);
-                    R[0][j] = (uint32_t)((c + G::half) / 3);
-                }
-            }
+        kem_mul<P, G::q>(va, vb, vb, mE, mA);
+        for (int j = tid; j < P; j += KEM_THREADS) {
+            const int c = (int)vb[j] - cmod<3>((int)vb[j]);
+            R[0][j] = (uint32_t)((c + G::half) / 3);
         }
         __syncthreads();
         mixed_encode<G::pad>(R, Sct, ct2);
