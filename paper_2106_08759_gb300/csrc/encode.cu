@@ -418,9 +418,17 @@ constexpr int kShaBlkMax = sha_blk_bytes(1322);  // the opt-in size: sntrup857's
 // *list_n entries (the fix-up's list): the list is another kernel's output,
 // so the kernel waits for its predecessors first, and a CTA past the list's
 // end does nothing.
+//
+// The kernel is compiled per public-key size: with the message length a
+// constant the producer's per-block word assembly folds to a short
+// instruction stream, and the producer, which sets the pace of the pair, keeps
+// up with the rounds warp (a run-time length made both warps about 40%
+// slower, measured on sntrup761).
+template <int PKB>
 __global__ void __launch_bounds__(64, 1)
-k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off,
-            const int *__restrict__ list, const int *__restrict__ list_n) {
+k_sha512_pk(KeyMap km, int B, int sk_bytes, int hash_off, const int *__restrict__ list,
+            const int *__restrict__ list_n) {
+    constexpr int pk_bytes = PKB;
     extern __shared__ __align__(16) uint8_t sm[];
     uint64_t(*wk)[80][32] = reinterpret_cast<uint64_t(*)[80][32]>(sm);  // [slot][round][key]
     __shared__ uint64_t ks[80];  // the round constants
@@ -498,8 +506,8 @@ k_sha512_pk(KeyMap km, int B, int pk_bytes, int sk_bytes, int hash_off,
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    const int len = pk_bytes + 1;
-    const int nblk = (len + 1 + 16 + 127) / 128;
+    constexpr int len = pk_bytes + 1;
+    constexpr int nblk = (len + 1 + 16 + 127) / 128;
     if (warp == 1) {
         // lanes past the last key repeat it; their digests are not stored
         const uint8_t *row = blk + rowoff[min(lane, nkeys - 1)];  // byte pos (1..pk_bytes) at row[pos - 1]
@@ -643,25 +651,34 @@ cudaError_t launch_leaf_s(int n1, const int8_t *gbuf, const int16_t *leaves, Lev
     }
 }
 
-cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
-                             int hash_off, cudaStream_t st, const int *list, const int *list_n) {
-    const int smem = kShaWkBytes + sha_blk_bytes(pk_bytes);
-    // the opt-in above 48 KB, once per device at the largest size any
-    // parameter set needs (host state, not stream work)
+template <int PKB>
+static cudaError_t launch_sha512_pk_t(const KeyMap &km, int nkeys, int sk_bytes, int hash_off,
+                                      cudaStream_t st, const int *list, const int *list_n) {
+    constexpr int smem = kShaWkBytes + sha_blk_bytes(PKB);
+    static_assert(smem <= kShaWkBytes + kShaBlkMax, "public key larger than the opt-in size");
+    // the opt-in above 48 KB, once per device (host state, not stream work)
     static std::atomic<uint64_t> opted{0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (!(opted.load() & (1ull << (dev & 63)))) {
-        e = cudaFuncSetAttribute(k_sha512_pk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kShaWkBytes + kShaBlkMax);
+        e = cudaFuncSetAttribute(k_sha512_pk<PKB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         opted.fetch_or(1ull << (dev & 63));
     }
-    if (smem > kShaWkBytes + kShaBlkMax) return cudaErrorInvalidValue;
-    SNT_LAUNCH(k_sha512_pk, (nkeys + 31) / 32, 64, smem, st, km, nkeys, pk_bytes, sk_bytes,
-        hash_off, list, list_n);
+    SNT_LAUNCH(k_sha512_pk<PKB>, (nkeys + 31) / 32, 64, smem, st, km, nkeys, sk_bytes, hash_off,
+        list, list_n);
     return cudaGetLastError();
+}
+
+cudaError_t launch_sha512_pk(const KeyMap &km, int nkeys, int pk_bytes, int sk_bytes,
+                             int hash_off, cudaStream_t st, const int *list, const int *list_n) {
+    switch (pk_bytes) {  // Rq_encode sizes of sntrup653, sntrup761, sntrup857
+    case 994: return launch_sha512_pk_t<994>(km, nkeys, sk_bytes, hash_off, st, list, list_n);
+    case 1158: return launch_sha512_pk_t<1158>(km, nkeys, sk_bytes, hash_off, st, list, list_n);
+    case 1322: return launch_sha512_pk_t<1322>(km, nkeys, sk_bytes, hash_off, st, list, list_n);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 #define SNT_FIN_INST(P)                                                                       \
