@@ -146,10 +146,12 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 // outputs, zeroing what the older state left above them in the target
 // buffer.  F, G shrink while V, R grow, their extents summing to about
 // p + 2, so a chunk applies the matrix to about p + 34 coefficients rather
-// than to four full-length polynomials.  Every warp but the leader is an
-// applier: the appliers set the chunk time, so the tensor units and issue
-// slots of the leader's scheduler are worth more to them than a scheduler
-// of its own is to the leader (measured: 119 -> 113 us per root).
+// than to four full-length polynomials.  The appliers run on the three
+// schedulers that are not the leader's: with two MMAs per operand pair they
+// no longer set the chunk time, and the leader's chain runs faster on a
+// scheduler of its own (measured, sntrup761 at B = 4096: the root phase
+// 104.7 -> 100.5 us; with the three-MMA products the appliers had set the
+// chunk time and were given the leader's scheduler too: 119 -> 113 us).
 //
 // The application on the tensor cores.  Each output of a pair is a sum of
 // two Toeplitz products with the chunk matrix: with T_e[i][j] = e[i - j + o],
@@ -157,20 +159,21 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 //     V' = T_u V + T_v R,  R' = T_w V + T_z R   (o = 0, +1, -1, 0),
 // the form of the tensor-core R/q product (mma_mul.cuh): for 16-coefficient
 // blocks the block (I, J) of T_e depends only on D = I - J, so an m16n8k16
-// MMA takes A from a pair table of e ((e[x], e[x-1]) per x, built by the
-// applier warps from the matrix at the start of the chunk) and as B eight
-// 16-coefficient blocks of the state (read as int pairs, split into 6-bit
-// limbs in f16).  The state is kept in that form: each coefficient is one
-// word holding its h and l limbs as two f16 values, written once by the
-// application that produces it, so a B fragment is two 8-byte loads and four
-// byte permutes; the leader reads an int copy of the low 64 coefficients of
-// F and G, and the inverse is read back from V's limbs at the end.  An item
-// is one 128-output tile of one pair (at most eight per chunk, one per applier
-// warp, two per scheduler): D runs over
-// the 3 or 4 values where some T_e block is nonzero, three limb products per
-// operand pair (Karatsuba: h h', l l', (h + l)(h' + l'); one, l l', when every
-// value is in {-1, 0, 1}); a sum has at most 64 terms, so every limb sum is
-// exact in f32 and 4096 P_hh + 64 P_x + P_ll stays below 2^31.
+// MMA takes A from a pair table of e ((e[x], e[x-1]) per x as 6-bit limbs
+// h, l in f16, built by the applier warps from the matrix at the start of
+// the chunk) and as B eight 16-coefficient blocks of the state.  The state
+// is kept as one f16 value per coefficient, a representative of its residue
+// that f16 holds exactly (the residue itself, or the residue -+ q when it is
+// odd and above 2048 in magnitude: at most q - 2049), written once by the
+// application that produces it and laid out so that a lane's B fragment is
+// one 8-byte load (spos); the leader reads an int copy of the low 64
+// coefficients of F and G, and the inverse is read back from V at the end.
+// An item is one 128-output tile of one pair (at most eight per chunk, one
+// per applier warp, two per scheduler): D runs over the 3 or 4 values where
+// some T_e block is nonzero, two MMAs per operand pair (h_e b' and l_e b';
+// one, l_e b', when every value is in {-1, 0, 1}); a sum has at most 64
+// terms, 64 * 41 * 3118 < 2^24, so every limb sum is exact in f32, and
+// 64 P_h + P_l stays below 2^31.
 //
 // Ranges: inside the leader's steps values are lazily reduced to [-q, 2q)
 // (G(0) = 0 mod q iff G(0) is -q, 0 or q); the matrix and the state are
@@ -179,14 +182,14 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 template <int P, int Q = Geo<P>::q> struct JumpGeo {
     static constexpr int M = 31;                        // steps per chunk
     static constexpr int OFF = 32;                      // zero margin below index 0
-    // applier warps: in R/q every warp but the leader (ids 1-11); in R/3 an
-    // operand pair is one MMA, and six appliers on the three schedulers that
-    // are not the leader's (ids 1-3, 5-7; warp 4 idle) keep up with the leader
-    // while leaving its scheduler, and SM resources, to others
-    static constexpr bool SPARE = Q < 64;
-    static constexpr int NWA = SPARE ? 6 : 11;
+    // applier warps on the three schedulers that are not the leader's, so
+    // that its divstep chain has a scheduler to itself: in R/q ids 1-3, 5-7,
+    // 9-11 (warps 4 and 8 idle; at most eight items per chunk), in R/3, where
+    // an operand pair is one MMA, ids 1-3, 5-7 (warp 4 idle)
+    static constexpr bool SPARE = true;
+    static constexpr int NW = Q < 64 ? 8 : 12;          // leader, appliers, idle
+    static constexpr int NWA = NW - NW / 4;
     static constexpr int NA = 32 * NWA;                 // applier threads
-    static constexpr int NW = SPARE ? 8 : 12;           // leader, appliers, idle
     static constexpr int NT = 32 * NW;
     // a tile reads blocks up to two past its last output block (D >= -2)
     static constexpr int LEN = (OFF + P + 160 + 31) / 32 * 32;  // slots per polynomial
@@ -274,61 +277,32 @@ __device__ __forceinline__ void put_matrix(int (*An)[40], int lane, int u, int v
     An[2][4 + lane] = w; An[3][4 + lane] = z;
 }
 
-// Shared-memory slot of state word j: bit 3 flipped by bit 5, so the B
-// fragment loads of a half-warp (four blocks 16 words apart) hit 32 distinct
-// banks and the application's stores (rows 32 words apart) at most two
-// lanes per bank; pairs (2k, 2k + 1) stay adjacent.
-__device__ __forceinline__ int ssl(int j) { return j ^ (((j >> 5) & 1) << 3); }
-
-// A coefficient as one state word: its limbs h (low half) and l (high half)
-// as f16.
-__device__ __forceinline__ uint32_t limb_word(int x) {
-    int h, l;
-    limbs64(x, h, l);
-    return h2_small(h, l);
-}
-__device__ __forceinline__ int word_value(uint32_t w) {
-    const __half2 v = *reinterpret_cast<const __half2 *>(&w);
-    return 64 * __half2int_rn(__low2half(v)) + __half2int_rn(__high2half(v));
+// Position of state coefficient j in its row: within each block of 16
+// coefficients, 2t, 2t + 1, 2t + 8 and 2t + 9 sit at 4t .. 4t + 3, so the B
+// fragment of a lane (those four coefficients of one block) is one 8-byte
+// load and the loads of a half-warp (four consecutive tig, two blocks) are
+// one contiguous 128-byte run.
+__device__ __forceinline__ int spos(int j) {
+    const int k = j & 15;
+    return (j & ~15) | (((k & 7) >> 1) << 2) | (k & 1) | ((k >> 3) << 1);
 }
 
-// The B fragment words (h01, h89, l01, l89, s01, s89; s = h + l) of a block
-// of state words: j is the word of coefficient 2 tig of the block (even).
-__device__ __forceinline__ uint32_t hadd2_u(uint32_t a, uint32_t b) {
-    uint32_t d;
-    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
+// A coefficient as stored: the f16 bits of a representative of the centred
+// residue x that f16 holds exactly (x itself, or x -+ Q when x is odd and
+// above 2048 in magnitude).
+template <int Q> __device__ __forceinline__ uint16_t state_half(int x) {
+    return __half_as_ushort(__int2half_rn(f16_rep<Q>(x)));
 }
+__device__ __forceinline__ int half_value(uint16_t h) { return __half2int_rn(__ushort_as_half(h)); }
+
+// acc[0] += l_e b' and (unless SMALL) acc[1] += h_e b': A from the pair-table
+// words at x, x + 8, x - 8 of e's limbs, B the block's four state values.
 template <bool SMALL>
-__device__ __forceinline__ void jump_frag_b(const uint32_t *X, int j, uint32_t (&b)[6]) {
-    const uint2 lo = *reinterpret_cast<const uint2 *>(X + ssl(j));
-    const uint2 hi = *reinterpret_cast<const uint2 *>(X + ssl(j + 8));
-    b[2] = __byte_perm(lo.x, lo.y, 0x7632);
-    b[3] = __byte_perm(hi.x, hi.y, 0x7632);
-    if (!SMALL) {
-        b[0] = __byte_perm(lo.x, lo.y, 0x5410);
-        b[1] = __byte_perm(hi.x, hi.y, 0x5410);
-        b[4] = hadd2_u(b[0], b[2]);
-        b[5] = hadd2_u(b[1], b[3]);
-    }
-}
-
-// acc[0..2] += the Karatsuba limb products h h', l l' and (h + l)(h' + l')
-// of A (pair-table words at x, x + 8, x - 8) and the B words b (h01, h89,
-// l01, l89, s01, s89); the sums are formed in f16, exact for these small
-// integers.  Only l l' when SMALL.
-template <bool SMALL>
-__device__ __forceinline__ void jump_mma(float (&acc)[SMALL ? 1 : 3][4], const uint2 *pt, int x,
-                                         const uint32_t (&b)[6]) {
+__device__ __forceinline__ void jump_mma(float (&acc)[SMALL ? 1 : 2][4], const uint2 *pt, int x,
+                                         uint2 b) {
     const uint2 a0 = pt[x], a1 = pt[x + 8], a2 = pt[x - 8];
-    if (SMALL) {
-        mma16816(acc[0], a0.y, a1.y, a2.y, a0.y, b[2], b[3]);
-    } else {
-        const uint32_t s0 = hadd2_u(a0.x, a0.y), s1 = hadd2_u(a1.x, a1.y), s2 = hadd2_u(a2.x, a2.y);
-        mma16816(acc[0], a0.x, a1.x, a2.x, a0.x, b[0], b[1]);
-        mma16816(acc[1], a0.y, a1.y, a2.y, a0.y, b[2], b[3]);
-        mma16816(acc[2], s0, s1, s2, s0, b[4], b[5]);
-    }
+    mma16816(acc[0], a0.y, a1.y, a2.y, a0.y, b.x, b.y);
+    if (!SMALL) mma16816(acc[SMALL ? 0 : 1], a0.x, a1.x, a2.x, a0.x, b.x, b.y);
 }
 
 // Q: the coefficient modulus (q: R/q; 3: R/3, for the root inversions of
@@ -342,9 +316,9 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     constexpr int LEN = JG::LEN, OFF = JG::OFF, NT = JG::NT;
     constexpr bool SMALL = Q < 64;  // every value in {-1, 0, 1}: the l limbs only
     constexpr int NCH = (2 * P - 1 + JG::M - 1) / JG::M;
-    // state words (limbs as f16 pairs) [buffer][F, G, V, R][index + OFF], and
-    // int copies of F, G at indices -32 .. 63 for the leader's prologue
-    __shared__ __align__(16) uint32_t st[2][4][LEN];
+    // state values (f16) [buffer][F, G, V, R][spos(index + OFF)], and int
+    // copies of F, G at indices -32 .. 63 for the leader's prologue
+    __shared__ __align__(16) uint16_t st[2][4][LEN];
     __shared__ int lowfg[2][2][96];
     // chunk matrix [buffer][u, v, w, z][4 + k], 16-byte rows for vector
     // loads, zero outside k = 0..31
@@ -362,7 +336,7 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     const bool leader = tid < 32;
     const int row = idx ? idx[e] : e;
     const int16_t *a = in + (size_t)row * in_stride;
-    for (int i = tid; i < 2 * 4 * LEN; i += NT) (&st[0][0][0])[i] = 0u;  // f16 zeros
+    for (int i = tid; i < 2 * 4 * LEN; i += NT) (&st[0][0][0])[i] = 0;  // f16 zeros
     for (int i = tid; i < 2 * 2 * 96; i += NT) (&lowfg[0][0][0])[i] = 0;
     for (int i = tid; i < 2 * 4 * 40; i += NT) (&mat[0][0][0])[i] = 0;
     for (int i = tid; i < 4 * JG::PTX; i += NT) (&pt[0][0])[i] = make_uint2(0u, 0u);
@@ -370,14 +344,14 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     __syncthreads();
     for (int i = tid; i < P; i += NT) {
         const int g = (int)a[P - 1 - i];
-        st[0][1][ssl(OFF + i)] = limb_word(g);
+        st[0][1][spos(OFF + i)] = state_half<Q>(g);
         if (i < 64) lowfg[0][1][32 + i] = g;
     }
     if (tid == 0) {
-        st[0][0][ssl(OFF)] = limb_word(1);
-        st[0][0][ssl(OFF + P - 1)] = limb_word(-1);
-        st[0][0][ssl(OFF + P)] = limb_word(-1);
-        st[0][3][ssl(OFF)] = limb_word(1);
+        st[0][0][spos(OFF)] = state_half<Q>(1);
+        st[0][0][spos(OFF + P - 1)] = state_half<Q>(-1);
+        st[0][0][spos(OFF + P)] = state_half<Q>(-1);
+        st[0][3][spos(OFF)] = state_half<Q>(1);
         lowfg[0][0][32] = 1;
         ext[0][0] = P + 1;
         ext[0][1] = 1;
@@ -427,13 +401,13 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
             // live ranges of the outputs and what the target buffer held
             const int rfg = ext[c & 3][0], rvr = min(ext[c & 3][1] + m + 1, P + 1);
             const int ofg = ext[(c + 3) & 3][0], ovr = ext[(c + 3) & 3][1];
-            uint32_t *T = &st[cur ^ 1][0][0];
+            uint16_t *T = &st[cur ^ 1][0][0];
             for (int i = rfg + at; i < ofg; i += JG::NA) {
-                T[ssl(OFF + i)] = 0u; T[LEN + ssl(OFF + i)] = 0u;
+                T[spos(OFF + i)] = 0; T[LEN + spos(OFF + i)] = 0;
                 if (i < 64) { lowfg[cur ^ 1][0][32 + i] = 0; lowfg[cur ^ 1][1][32 + i] = 0; }
             }
             for (int i = rvr + at; i < ovr; i += JG::NA) {
-                T[2 * LEN + ssl(OFF + i)] = 0u; T[3 * LEN + ssl(OFF + i)] = 0u;
+                T[2 * LEN + spos(OFF + i)] = 0; T[3 * LEN + spos(OFF + i)] = 0;
             }
             if (at == 0) { ext[(c + 2) & 3][0] = 0; ext[(c + 2) & 3][1] = 0; }
             // pair tables of this chunk's matrix, then the appliers' barrier
@@ -452,12 +426,13 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
             for (int it = ai; it < nit; it += JG::NWA) {  // one tile of one pair per warp
                 const int pr = it >= nfg;
                 const int T0 = pr ? it - nfg : it, r = pr ? rvr : rfg;
-                const uint32_t *X = st[cur][2 * pr], *Y = st[cur][2 * pr + 1];
+                const uint2 *X = reinterpret_cast<const uint2 *>(st[cur][2 * pr]);
+                const uint2 *Y = reinterpret_cast<const uint2 *>(st[cur][2 * pr + 1]);
                 // offsets o of T_u, T_v, T_w, T_z and the D range where some
                 // block is nonzero: 0 <= 16 D + (row - col) + o <= 31
                 const int ou = pr ? 0 : m, ov = pr ? 1 : m, ow = pr ? -1 : m;
                 const int dlo = pr ? -1 : -((15 + m) >> 4), dhi = pr ? 2 : (46 - m) >> 4;
-                constexpr int NL = SMALL ? 1 : 3;  // limb products h h', l l', s s'
+                constexpr int NL = SMALL ? 1 : 2;  // limb products l_e b', h_e b'
                 float acc[2][NL][4];                // [output][limb product]
 #pragma unroll
                 for (int o = 0; o < 2; ++o)
@@ -469,10 +444,8 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
                 for (int dd = 0; dd < 4; ++dd) {  // at most four D values
                     const int D = dlo + dd;
                     if (D > dhi) break;
-                    const int jb = OFF + 16 * (8 * T0 + g - D) + 2 * tig;  // input block I - D
-                    uint32_t bx[6], by[6];
-                    jump_frag_b<SMALL>(X, jb, bx);
-                    jump_frag_b<SMALL>(Y, jb, by);
+                    const int jb = 4 * ((OFF >> 4) + 8 * T0 + g - D) + tig;  // input block I - D
+                    const uint2 bx = X[jb], by = Y[jb];
                     const int x = JG::PT0 + 16 * D + g - 2 * tig;
                     // X terms of both outputs first, so the two MMAs that
                     // meet in one accumulator are apart
@@ -481,7 +454,7 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
                     jump_mma<SMALL>(acc[0], pt[1], x + ov, by);
                     jump_mma<SMALL>(acc[1], pt[3], x + ou, by);
                 }
-                uint32_t *X2 = st[cur ^ 1][2 * pr], *Y2 = st[cur ^ 1][2 * pr + 1];
+                uint16_t *X2 = st[cur ^ 1][2 * pr], *Y2 = st[cur ^ 1][2 * pr + 1];
                 int top = 0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -494,14 +467,12 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
                             if (SMALL) {
                                 v[o] = cmod<Q>(__float2int_rn(acc[o][0][q]));
                             } else {
-                                // P_x = P_ss - P_hh - P_ll; |64 P_x + P_ll| < 2^24
-                                const float phh = acc[o][0][q], pll = acc[o][1][q];
-                                const int t = __float2int_rn(fmaf(64.f, acc[o][2][q] - phh - pll, pll));
-                                v[o] = cmod<Q>(4096 * __float2int_rn(phh) + t);
+                                v[o] = cmod<Q>(64 * __float2int_rn(acc[o][1][q]) +
+                                               __float2int_rn(acc[o][0][q]));
                             }
                         }
-                        X2[ssl(OFF + i)] = limb_word(v[0]);
-                        Y2[ssl(OFF + i)] = limb_word(v[1]);
+                        X2[spos(OFF + i)] = state_half<Q>(v[0]);
+                        Y2[spos(OFF + i)] = state_half<Q>(v[1]);
                         if (!pr && i < 64) { lowfg[cur ^ 1][0][32 + i] = v[0]; lowfg[cur ^ 1][1][32 + i] = v[1]; }
                         if (v[0] | v[1]) top = max(top, i + 1);
                     }
@@ -523,7 +494,7 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     const int sc = ok ? inv_mod<Q>(f0) : 0;
     int16_t *o = out + (size_t)row * out_stride;
     for (int i = tid; i < P; i += NT) {
-        const int v = freeze_lazy<Q>(word_value(st[cur][2][ssl(OFF + P - 1 - i)]));
+        const int v = freeze_lazy<Q>(half_value(st[cur][2][spos(OFF + P - 1 - i)]));
         o[i] = (int16_t)cmod<Q>(sc * v);
     }
     if (tid == 0) {
