@@ -147,11 +147,14 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 // buffer.  F, G shrink while V, R grow, their extents summing to about
 // p + 2, so a chunk applies the matrix to about p + 34 coefficients rather
 // than to four full-length polynomials.  The appliers run on the three
-// schedulers that are not the leader's: with two MMAs per operand pair they
-// no longer set the chunk time, and the leader's chain runs faster on a
-// scheduler of its own (measured, sntrup761 at B = 4096: the root phase
-// 104.7 -> 100.5 us; with the three-MMA products the appliers had set the
-// chunk time and were given the leader's scheduler too: 119 -> 113 us).
+// schedulers that are not the leader's, and the other warps on the leader's
+// scheduler compute half of the leader's prologue (the low coefficients of
+// F', G') beside it.  Measured on one sntrup761 root alone (clock stamps,
+// cycles per chunk): leader prologue 786 -> 516 and steps 2609 -> 2168 (84
+// -> 70 per step); the appliers, ~480 of tables and ~2600 for the scheduler
+// that holds three of the usual seven tiles, now set the chunk (3651).
+// Giving the helpers tiles too (so that no scheduler holds three) slowed the
+// leader back to 83 cycles per step and the chunk to ~3730.
 //
 // The application on the tensor cores.  Each output of a pair is a sum of
 // two Toeplitz products with the chunk matrix: with T_e[i][j] = e[i - j + o],
@@ -184,12 +187,14 @@ template <int P, int Q = Geo<P>::q> struct JumpGeo {
     static constexpr int OFF = 32;                      // zero margin below index 0
     // applier warps on the three schedulers that are not the leader's, so
     // that its divstep chain has a scheduler to itself: in R/q ids 1-3, 5-7,
-    // 9-11 (warps 4 and 8 idle; at most eight items per chunk), in R/3, where
-    // an operand pair is one MMA, ids 1-3, 5-7 (warp 4 idle)
-    static constexpr bool SPARE = true;
-    static constexpr int NW = Q < 64 ? 8 : 12;          // leader, appliers, idle
+    // 9-11 (at most eight items per chunk), in R/3, where an operand pair is
+    // one MMA, ids 1-3, 5-7; the other warps on the leader's scheduler (4 and
+    // 8, or 4) compute part of the leader's prologue
+    static constexpr int NW = Q < 64 ? 8 : 12;          // leader, appliers, helpers
     static constexpr int NWA = NW - NW / 4;
     static constexpr int NA = 32 * NWA;                 // applier threads
+    static constexpr int NH = NW / 4 - 1;               // helper warps
+    static constexpr int LG = 2, HG = 2 / NH;           // prologue groups of 8 terms: leader, helper
     static constexpr int NT = 32 * NW;
     // a tile reads blocks up to two past its last output block (D >= -2)
     static constexpr int LEN = (OFF + P + 160 + 31) / 32 * 32;  // slots per polynomial
@@ -305,6 +310,30 @@ __device__ __forceinline__ void jump_mma(float (&acc)[SMALL ? 1 : 2][4], const u
     if (!SMALL) mma16816(acc[SMALL ? 0 : 1], a0.x, a1.x, a2.x, a0.x, b.x, b.y);
 }
 
+// Part of the leader's prologue: for lane i, the sums over the matrix
+// coefficients k = kb0 .. kb0 + 8 NG - 1 of u_k F[hi - k] + v_k G[hi - k]
+// (into sf) and w_k F[hi - k] + z_k G[hi - k] (into sg).
+template <int NG>
+__device__ __forceinline__ void prologue_part(const int (*A)[40], const int *F, const int *G,
+                                              int hi, int kb0, int &sf, int &sg) {
+    int af[2] = {0, 0}, ag[2] = {0, 0};
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi) {
+        const int kb = kb0 + 8 * gi;
+        int c0[8], c1[8], c2[8], c3[8];
+        load8(c0, &A[0][4 + kb]); load8(c1, &A[1][4 + kb]);
+        load8(c2, &A[2][4 + kb]); load8(c3, &A[3][4 + kb]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int fv = F[hi - kb - j], gv = G[hi - kb - j];
+            af[j & 1] += c0[j] * fv + c1[j] * gv;
+            ag[j & 1] += c2[j] * fv + c3[j] * gv;
+        }
+    }
+    sf = af[0] + af[1];
+    sg = ag[0] + ag[1];
+}
+
 // Q: the coefficient modulus (q: R/q; 3: R/3, for the root inversions of
 // the R/3 batch inversion).
 template <int P, int Q = Geo<P>::q>
@@ -329,6 +358,7 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     // extents of the state after chunk c - 1 in ext[c % 4]: [0] F, G and
     // [1] V, R (one past the highest nonzero coefficient)
     __shared__ int ext[4][2];
+    __shared__ int pro[2][2][32];  // the helpers' prologue sums [helper][F', G'][lane]
     __shared__ int s_ok;
     const int e = blockIdx.x;
     if (e >= n) return;
@@ -371,32 +401,26 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
         const int(*A)[40] = mat[c & 1];
         if (leader) {
             if (c + 1 < NCH) {
-                // low 32 coefficients of F', G' (lane i), then chunk c + 1
-                const int *F = lowfg[cur][0], *G = lowfg[cur][1];
-                int af[2] = {0, 0}, ag[2] = {0, 0};
-                const int hi = 32 + lane + m;
+                // low 32 coefficients of F', G' (lane i): the first LG groups
+                // of matrix terms here, the rest from the helpers; then chunk
+                // c + 1
+                int sf, sg;
+                prologue_part<JG::LG>(A, lowfg[cur][0], lowfg[cur][1], 32 + lane + m, 0, sf, sg);
+                asm volatile("bar.sync 2, %0;" ::"n"(32 * (1 + JG::NH)) : "memory");
 #pragma unroll
-                for (int kb = 0; kb < 32; kb += 8) {
-                    int c0[8], c1[8], c2[8], c3[8];
-                    load8(c0, &A[0][4 + kb]); load8(c1, &A[1][4 + kb]);
-                    load8(c2, &A[2][4 + kb]); load8(c3, &A[3][4 + kb]);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int fv = F[hi - kb - j], gv = G[hi - kb - j];
-                        af[j & 1] += c0[j] * fv + c1[j] * gv;
-                        ag[j & 1] += c2[j] * fv + c3[j] * gv;
-                    }
+                for (int h = 0; h < JG::NH; ++h) {
+                    sf += pro[h][0][lane];
+                    sg += pro[h][1][lane];
                 }
                 const int m1 = min(JG::M, 2 * P - 1 - (c + 1) * JG::M);
                 int u, v, w, z;
-                leader_chunk<Q, JG::M>(m1, delta, cmod<Q>(af[0] + af[1]), cmod<Q>(ag[0] + ag[1]), u, v, w,
-                                z);
+                leader_chunk<Q, JG::M>(m1, delta, cmod<Q>(sf), cmod<Q>(sg), u, v, w, z);
                 put_matrix(mat[(c + 1) & 1], lane, u, v, w, z);
             } else if (lane == 0) {
                 s_ok = (delta == 0);
             }
-        } else if (!JG::SPARE || ((tid >> 5) & 3)) {
-            const int w = tid >> 5, ai = JG::SPARE ? w - 1 - (w - 1) / 4 : w - 1;
+        } else if ((tid >> 5) & 3) {
+            const int w = tid >> 5, ai = w - 1 - (w - 1) / 4;
             const int at = 32 * ai + lane;
             // live ranges of the outputs and what the target buffer held
             const int rfg = ext[c & 3][0], rvr = min(ext[c & 3][1] + m + 1, P + 1);
@@ -485,6 +509,14 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
                 atomicMax(&ext[(c + 1) & 3][0], top_fg);
                 atomicMax(&ext[(c + 1) & 3][1], top_vr);
             }
+        } else if (c + 1 < NCH) {  // helper h: groups LG + h HG .. of the leader's prologue
+            const int h = (tid >> 5) / 4 - 1;
+            int sf, sg;
+            prologue_part<JG::HG>(A, lowfg[cur][0], lowfg[cur][1], 32 + lane + m,
+                                  8 * (JG::LG + h * JG::HG), sf, sg);
+            pro[h][0][lane] = sf;
+            pro[h][1][lane] = sg;
+            asm volatile("bar.arrive 2, %0;" ::"n"(32 * (1 + JG::NH)) : "memory");
         }
         __syncthreads();
         cur ^= 1;
