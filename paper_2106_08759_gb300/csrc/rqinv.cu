@@ -147,12 +147,15 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 // buffer.  F, G shrink while V, R grow, their extents summing to about
 // p + 2, so a chunk applies the matrix to about p + 34 coefficients rather
 // than to four full-length polynomials.  The appliers run on the three
-// schedulers that are not the leader's, and the other warps on the leader's
-// scheduler compute half of the leader's prologue (the low coefficients of
-// F', G') beside it.  Measured on one sntrup761 root alone (clock stamps,
-// cycles per chunk): leader prologue 786 -> 516 and steps 2609 -> 2168 (84
-// -> 70 per step); the appliers, ~480 of tables and ~2600 for the scheduler
-// that holds three of the usual seven tiles, now set the chunk (3651).
+// schedulers that are not the leader's; the other warps on the leader's
+// scheduler (the helpers) compute half of the leader's prologue (the low
+// coefficients of F', G') beside it, then wait for its next matrix and
+// build that matrix's limb pair tables, so that the appliers find them
+// ready.  Measured on one sntrup761 root alone (clock stamps, cycles per
+// chunk): 3663 with the leader alone on its scheduler (prologue 786, steps
+// 2609), 3651 with the helpers' prologue (516 and 2168: the appliers, ~480
+// of set-up and ~2600 for the scheduler that holds three of the usual seven
+// tiles, then set the chunk), 3404 with the tables built ahead (set-up 331).
 // Giving the helpers tiles too (so that no scheduler holds three) slowed the
 // leader back to 83 cycles per step and the chunk to ~3730.
 //
@@ -334,6 +337,21 @@ __device__ __forceinline__ void prologue_part(const int (*A)[40], const int *F, 
     sg = ag[0] + ag[1];
 }
 
+// The limb pair tables of a chunk matrix (rows u, v, w, z of A) into P,
+// entries k = 0 .. 32 of each (the rest stay zero), by threads t0, t0 + nt, ...
+template <int PTX, int PT0>
+__device__ __forceinline__ void build_pair_tables(const int (*A)[40], uint2 (*P)[PTX], int t0,
+                                                  int nt) {
+    for (int pe = t0; pe < 4 * 33; pe += nt) {
+        const int en = pe / 33, k = pe % 33;
+        const int e0 = A[en][4 + k], e1 = A[en][3 + k];  // e[k], e[k-1]; zero at 32 and -1
+        int h0, l0, h1, l1;
+        limbs64(e0, h0, l0);
+        limbs64(e1, h1, l1);
+        P[en][PT0 + k] = make_uint2(h2_small(h0, h1), h2_small(l0, l1));
+    }
+}
+
 // Q: the coefficient modulus (q: R/q; 3: R/3, for the root inversions of
 // the R/3 batch inversion).
 template <int P, int Q = Geo<P>::q>
@@ -352,9 +370,11 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     // chunk matrix [buffer][u, v, w, z][4 + k], 16-byte rows for vector
     // loads, zero outside k = 0..31
     __shared__ __align__(16) int mat[2][4][40];
-    // limb pair tables of u, v, w, z for the appliers: entry PT0 + x holds
-    // (h, l) of (e[x], e[x-1]) as f16x2 words, zero outside x = 0..32
-    __shared__ __align__(16) uint2 pt[4][JG::PTX];
+    // limb pair tables of u, v, w, z for the appliers, [buffer][u, v, w, z]:
+    // entry PT0 + x holds (h, l) of (e[x], e[x-1]) as f16x2 words, zero
+    // outside x = 0..32; chunk c's in pt[c & 1], built by the helpers while
+    // the appliers apply chunk c - 1
+    __shared__ __align__(16) uint2 pt[2][4][JG::PTX];
     // extents of the state after chunk c - 1 in ext[c % 4]: [0] F, G and
     // [1] V, R (one past the highest nonzero coefficient)
     __shared__ int ext[4][2];
@@ -369,7 +389,7 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
     for (int i = tid; i < 2 * 4 * LEN; i += NT) (&st[0][0][0])[i] = 0;  // f16 zeros
     for (int i = tid; i < 2 * 2 * 96; i += NT) (&lowfg[0][0][0])[i] = 0;
     for (int i = tid; i < 2 * 4 * 40; i += NT) (&mat[0][0][0])[i] = 0;
-    for (int i = tid; i < 4 * JG::PTX; i += NT) (&pt[0][0])[i] = make_uint2(0u, 0u);
+    for (int i = tid; i < 2 * 4 * JG::PTX; i += NT) (&pt[0][0][0])[i] = make_uint2(0u, 0u);
     if (tid < 8) (&ext[0][0])[tid] = 0;
     __syncthreads();
     for (int i = tid; i < P; i += NT) {
@@ -395,10 +415,13 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
         put_matrix(mat[0], lane, u, v, w, z);
     }
     __syncthreads();
+    build_pair_tables<JG::PTX, JG::PT0>(mat[0], pt[0], tid, NT);
+    __syncthreads();
     int cur = 0;
     for (int c = 0; c < NCH; ++c) {
         const int m = min(JG::M, 2 * P - 1 - c * JG::M);
         const int(*A)[40] = mat[c & 1];
+        const uint2(*PT)[JG::PTX] = pt[c & 1];
         if (leader) {
             if (c + 1 < NCH) {
                 // low 32 coefficients of F', G' (lane i): the first LG groups
@@ -416,6 +439,7 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
                 int u, v, w, z;
                 leader_chunk<Q, JG::M>(m1, delta, cmod<Q>(sf), cmod<Q>(sg), u, v, w, z);
                 put_matrix(mat[(c + 1) & 1], lane, u, v, w, z);
+                asm volatile("bar.arrive 3, %0;" ::"n"(32 * (1 + JG::NH)) : "memory");
             } else if (lane == 0) {
                 s_ok = (delta == 0);
             }
@@ -434,16 +458,6 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
                 T[2 * LEN + spos(OFF + i)] = 0; T[3 * LEN + spos(OFF + i)] = 0;
             }
             if (at == 0) { ext[(c + 2) & 3][0] = 0; ext[(c + 2) & 3][1] = 0; }
-            // pair tables of this chunk's matrix, then the appliers' barrier
-            for (int pe = at; pe < 4 * 33; pe += JG::NA) {
-                const int en = pe / 33, k = pe % 33;
-                const int e0 = A[en][4 + k], e1 = A[en][3 + k];  // e[k], e[k-1]; zero at 32 and -1
-                int h0, l0, h1, l1;
-                limbs64(e0, h0, l0);
-                limbs64(e1, h1, l1);
-                pt[en][JG::PT0 + k] = make_uint2(h2_small(h0, h1), h2_small(l0, l1));
-            }
-            asm volatile("bar.sync 1, %0;" ::"n"(JG::NA) : "memory");
             const int g = lane >> 2, tig = lane & 3;
             const int nfg = (rfg + 127) / 128, nit = nfg + (rvr + 127) / 128;
             int top_fg = 0, top_vr = 0;
@@ -473,10 +487,10 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
                     const int x = JG::PT0 + 16 * D + g - 2 * tig;
                     // X terms of both outputs first, so the two MMAs that
                     // meet in one accumulator are apart
-                    jump_mma<SMALL>(acc[0], pt[0], x + ou, bx);
-                    jump_mma<SMALL>(acc[1], pt[2], x + ow, bx);
-                    jump_mma<SMALL>(acc[0], pt[1], x + ov, by);
-                    jump_mma<SMALL>(acc[1], pt[3], x + ou, by);
+                    jump_mma<SMALL>(acc[0], PT[0], x + ou, bx);
+                    jump_mma<SMALL>(acc[1], PT[2], x + ow, bx);
+                    jump_mma<SMALL>(acc[0], PT[1], x + ov, by);
+                    jump_mma<SMALL>(acc[1], PT[3], x + ou, by);
                 }
                 uint16_t *X2 = st[cur ^ 1][2 * pr], *Y2 = st[cur ^ 1][2 * pr + 1];
                 int top = 0;
@@ -517,6 +531,10 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
             pro[h][0][lane] = sf;
             pro[h][1][lane] = sg;
             asm volatile("bar.arrive 2, %0;" ::"n"(32 * (1 + JG::NH)) : "memory");
+            // then, once the leader has the next matrix, its pair tables
+            asm volatile("bar.sync 3, %0;" ::"n"(32 * (1 + JG::NH)) : "memory");
+            build_pair_tables<JG::PTX, JG::PT0>(mat[(c + 1) & 1], pt[(c + 1) & 1], 32 * h + lane,
+                                                32 * JG::NH);
         }
         __syncthreads();
         cur ^= 1;
