@@ -461,7 +461,11 @@ k_rq_inv_jump(int n, const int16_t *in, long in_stride, int16_t *out, long out_s
             const int g = lane >> 2, tig = lane & 3;
             const int nfg = (rfg + 127) / 128, nit = nfg + (rvr + 127) / 128;
             int top_fg = 0, top_vr = 0;
-            for (int it = ai; it < nit; it += JG::NWA) {  // one tile of one pair per warp
+            for (int sl = ai; sl < nit; sl += JG::NWA) {  // one tile of one pair per warp
+                // with seven tiles (the usual count) the scheduler of slots 0,
+                // 3 and 6 holds three: give it tiles 0, 1, 2, the F, G tiles
+                // while there are three (three D steps, against four for V, R)
+                const int it = (nit == 7 && sl < 7) ? (0x2641530 >> (4 * sl)) & 15 : sl;
                 const int pr = it >= nfg;
                 const int T0 = pr ? it - nfg : it, r = pr ? rvr : rfg;
                 const uint2 *X = reinterpret_cast<const uint2 *>(st[cur][2 * pr]);
