@@ -72,13 +72,14 @@ def tree_levels(n):
 # launch-list capture of one keygen call (caches flushed by ncu before each
 # launch), keyed by kernel; a kernel is absent until a capture of its current
 # code exists.  Writes stay in L2.  Engine 3: 16 subtrees, the R/3 forest 4
-# (the layout of the capture); engine 1: 64 subtrees.
+# (the layout of the capture); engine 1: 64 subtrees; the R/q root inversion:
+# 32 roots (its inputs, 32 rows).
 NCU_TRAFFIC_BYTES = {
     "k_tree_up_mma": 12532992,
     "k_tree_down_mma": 9324544,
     "k_tree_up_mma (one wide limb)": 12721152,
     "k_tree_down_mma (one wide limb)": 9627904,
-    "k_rq_inv_jump<761, 4591>": 113664,
+    "k_rq_inv_jump<761, 4591>": 115456,
     "k_finalize_pair<761>": 9503232,
     "k_tree_up_mma / k_tree_down_mma (mod 3) + k_rq_inv_jump<761, 3>": 38448384,
 }
