@@ -394,7 +394,7 @@ snt_status snt_ctx_get_option(snt_ctx *ctx, int option, int *value);
  * (outside the call's timed span).  Candidates: R/3 lanes (4, 8, 32) x R/3
  * overlap (0 .. 3) x
  * { tensor-core engine (1, and each of its candidates again as 3) with 1 or
- * 2 MMA tiles per warp, forests of 1, 4, 16, 32, 64, 128 or 256 subtrees
+ * 2 MMA tiles per warp, forests of 1, 4, 8, 16, 32, 64, 128 or 256 subtrees
  * (SNT_OPT_ROOTS) and R/3 mode 0, 1 or 2 (modes 1 and 2 also with an R/3
  * forest of 1 or 4 subtrees, SNT_OPT_R3_ROOTS); CUDA-core
  * Toeplitz engine with tree split 4 or 8; transform multiplier (engine 2)

@@ -1000,7 +1000,7 @@ snt_status snt_autotune_ex(snt_ctx *ctx, int P, size_t B, int *choice) {
         for (int kp : {1}) {  // two elements per lane group measured slower at every size
             for (int ov : {0, 1, 2, 3}) {
                 for (int ti : {1, 2})
-                    for (int rt : {1, 4, 16, 32, 64, 128, 256})
+                    for (int rt : {1, 4, 8, 16, 32, 64, 128, 256})
                         for (int r3m : {0, 1, 2}) {
                             if (rt > 1 && (la == 32 || ti == 2)) continue;
                             if (r3m == 1 && (la != 4 || ti == 2)) continue;  // lanes: per-key only

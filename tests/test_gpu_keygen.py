@@ -408,7 +408,7 @@ def test_benchmarked_layout_b4096_vs_perkey_and_oracle(snt, pool):
     # forest rule of the library: for B = 4096 every power of two up to 256
     # divides B and fits the node rows, so K = the tuned root count
     K = tuned["roots"]
-    assert K in (1, 4, 16, 32, 64, 128, 256)
+    assert K in (1, 4, 8, 16, 32, 64, 128, 256)
     sub = B // K
     ends = [x for j in range(K) for x in (j * sub, j * sub + sub - 1)]
     rng = np.random.default_rng(3)
