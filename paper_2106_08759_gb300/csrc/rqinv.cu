@@ -134,9 +134,10 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 //     V' = u V + (v / x) R,     R' = x w V + z R,
 // the last two because V is multiplied by x before each step's swap, which
 // conjugates A by diag(1, x).  The chunks are pipelined: while the appliers
-// apply chunk c, the leader computes the 32 low coefficients of F', G' itself
-// and runs the divsteps of chunk c + 1, so a chunk costs about the larger of
-// the two.  One barrier per chunk, ceil((2p-1)/31) chunks.
+// apply chunk c, the leader (with the helper warps) computes the 32 low
+// coefficients of F', G' and runs the divsteps of chunk c + 1, so a chunk
+// costs about the larger of the two.  One barrier per chunk,
+// ceil((2p-1)/31) chunks.
 //
 // Live extents.  A chunk's matrix entries have degree at most m, so F', G'
 // are zero wherever F and G are (index i of F' reads F at i + m - k, k <= m),
@@ -155,9 +156,10 @@ k_rq_inv(int n, const TIn *in, long in_stride, int16_t *out, long out_stride,
 // chunk): 3663 with the leader alone on its scheduler (prologue 786, steps
 // 2609), 3651 with the helpers' prologue (516 and 2168: the appliers, ~480
 // of set-up and ~2600 for the scheduler that holds three of the usual seven
-// tiles, then set the chunk), 3404 with the tables built ahead (set-up 331).
-// Giving the helpers tiles too (so that no scheduler holds three) slowed the
-// leader back to 83 cycles per step and the chunk to ~3730.
+// tiles, then set the chunk), 3404 with the tables built ahead (set-up 331),
+// 3302 with the F, G tiles on that scheduler.  Giving the helpers tiles too
+// (so that no scheduler holds three) slowed the leader back to 83 cycles per
+// step and the chunk to ~3730.
 //
 // The application on the tensor cores.  Each output of a pair is a sum of
 // two Toeplitz products with the chunk matrix: with T_e[i][j] = e[i - j + o],
@@ -190,9 +192,10 @@ template <int P, int Q = Geo<P>::q> struct JumpGeo {
     static constexpr int OFF = 32;                      // zero margin below index 0
     // applier warps on the three schedulers that are not the leader's, so
     // that its divstep chain has a scheduler to itself: in R/q ids 1-3, 5-7,
-    // 9-11 (at most eight items per chunk), in R/3, where an operand pair is
-    // one MMA, ids 1-3, 5-7; the other warps on the leader's scheduler (4 and
-    // 8, or 4) compute part of the leader's prologue
+    // 9-11 (seven or eight tiles per chunk for sntrup761), in R/3, where an
+    // operand pair is one MMA, ids 1-3, 5-7; the other warps on the leader's
+    // scheduler (4 and 8, or 4) compute part of the leader's prologue and
+    // build the pair tables of its next matrix
     static constexpr int NW = Q < 64 ? 8 : 12;          // leader, appliers, helpers
     static constexpr int NWA = NW - NW / 4;
     static constexpr int NA = 32 * NWA;                 // applier threads
